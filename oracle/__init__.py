@@ -1,0 +1,285 @@
+"""FP64 CPU oracle for the tangent-space normal bake (Sec. 6.4).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  It
+shares no code with the CUDA path (``paper_2605_26137_b300``): the two meet
+only in the seeded input generators (``paper_2605_26137_b300.synth``), which
+hold none of the baking arithmetic.
+
+The arithmetic lives in ``oracle.c`` (plain C, double precision, compiled
+with -ffp-contract=off); this module only marshals numpy arrays.
+
+Pins (see tests/test_oracle_*.py): every function here is checked against
+closed forms, brute force or invariants that a wrong sign, index or dropped
+term would break.  No function of the oracle is left unpinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (plain C, FP64, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.or_vertex_normals.argtypes = [_P, _I64, _P, _I64, _P]
+        lib.or_vertex_normals.restype = None
+        lib.or_snap.argtypes = [ctypes.c_float, _I]
+        lib.or_snap.restype = _I64
+        lib.or_raster.argtypes = [_P, _I64, _I, _I, _I, _P, _P, _P]
+        lib.or_raster.restype = _I
+        lib.or_face_frames.argtypes = [_P, _P, _I64, _P, _I, _I, _P, _P, _P, _P]
+        lib.or_face_frames.restype = None
+        lib.or_bvh_build.argtypes = [_P, _P, _I64]
+        lib.or_bvh_build.restype = _P
+        lib.or_bvh_free.argtypes = [_P]
+        lib.or_bvh_free.restype = None
+        lib.or_closest_hit.argtypes = [_P, _P, _I64, _P, _P, _P, _D, _P]
+        lib.or_closest_hit.restype = _I
+        lib.or_trace.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
+                                 _I, _I, _D, _D, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P]
+        lib.or_trace.restype = _I
+        lib.or_encode.argtypes = [_P, _P, _I64, _P]
+        lib.or_encode.restype = None
+        lib.or_dilate.argtypes = [_I, _I, _I, _P, _P, _P]
+        lib.or_dilate.restype = _I
+        lib.or_loss_grad.argtypes = [_P, _P, _P, _P, _I64, _P, _I64, _P, _P, _P, _I64, _D, _P]
+        lib.or_loss_grad.restype = _D
+        _lib = lib
+        return lib
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+# ----------------------------------------------------------------- pieces
+
+def vertex_normals(V, F):
+    """Area-weighted unit vertex normals, FP64 [nv,3]."""
+    lib = _load()
+    V = _c(V, np.float32)
+    F = _c(F, np.int32)
+    N = np.zeros((len(V), 3), np.float64)
+    lib.or_vertex_normals(_p(V), len(V), _p(F), len(F), _p(N))
+    return N
+
+
+def snap(u: float, W: int) -> int:
+    return int(_load().or_snap(ctypes.c_float(u), W))
+
+
+def raster(uv, W: int, H: int, brute: bool = False):
+    """Texel -> (owning low face, barycentrics).  Returns (face i32 [H,W],
+    bary f64 [H,W,3], a2 i64 [F]) with a2 = twice the signed UV area in
+    snapped (1/256 texel) units."""
+    lib = _load()
+    uv = _c(uv, np.float32)
+    nf = uv.shape[0]
+    face = np.empty((H, W), np.int32)
+    bary = np.empty((H, W, 3), np.float64)
+    a2 = np.empty(nf, np.int64)
+    if lib.or_raster(_p(uv), nf, W, H, int(brute), _p(face), _p(bary), _p(a2)) != 0:
+        raise MemoryError("oracle raster: allocation failed")
+    return face, bary, a2
+
+
+def face_frames(V, F, uv, W, H, N):
+    """Per-corner unit tangents [F,3,3], handedness [F], degenerate flag [F]."""
+    lib = _load()
+    V = _c(V, np.float32)
+    F = _c(F, np.int32)
+    uv = _c(uv, np.float32)
+    N = _c(N, np.float64)
+    T = np.empty((len(F), 3, 3), np.float64)
+    w = np.empty(len(F), np.float64)
+    dg = np.empty(len(F), np.uint8)
+    lib.or_face_frames(_p(V), _p(F), len(F), _p(uv), W, H, _p(N), _p(T), _p(w), _p(dg))
+    return T, w, dg
+
+
+class Bvh:
+    """Median-split binary BVH over a triangle mesh (FP64 bounds)."""
+
+    def __init__(self, V, F):
+        self._lib = _load()
+        self.V = _c(V, np.float32)
+        self.F = _c(F, np.int32)
+        self.h = self._lib.or_bvh_build(_p(self.V), _p(self.F), len(self.F))
+        if not self.h:
+            raise MemoryError("oracle BVH build failed")
+
+    def __del__(self):
+        h, self.h = getattr(self, "h", None), None
+        if h:
+            self._lib.or_bvh_free(h)
+
+
+def closest_hit(V, F, o, d, tmax, bvh: Bvh | None = None):
+    """Closest |t| hit of the line o + t d, |t| <= tmax.  Returns (tri, t, b[3])
+    with tri = -1 on a miss."""
+    lib = _load()
+    if bvh is not None:
+        V, F = bvh.V, bvh.F
+    else:
+        V, F = _c(V, np.float32), _c(F, np.int32)
+    o = _c(o, np.float64)
+    d = _c(d, np.float64)
+    out = np.zeros(5, np.float64)
+    lib.or_closest_hit(_p(V), _p(F), len(F), bvh.h if bvh is not None else None, _p(o), _p(d), float(tmax), _p(out))
+    return int(out[0]), float(out[1]), out[2:5].copy()
+
+
+def encode(nts, filled):
+    lib = _load()
+    nts = _c(nts, np.float64)
+    filled = _c(filled, np.uint8)
+    n = filled.size
+    rgba = np.empty(n * 4, np.uint8)
+    lib.or_encode(_p(nts), _p(filled), n, _p(rgba))
+    return rgba.reshape(filled.shape + (4,))
+
+
+def dilate(W, H, gutter, filled, nts, disp):
+    """In place on copies; returns (filled, nts, disp)."""
+    lib = _load()
+    filled = _c(filled, np.uint8).copy()
+    nts = _c(nts, np.float64).copy()
+    disp = _c(disp, np.float64).copy()
+    if lib.or_dilate(W, H, gutter, _p(filled), _p(nts), _p(disp)) != 0:
+        raise MemoryError("oracle dilate: allocation failed")
+    return filled, nts, disp
+
+
+# ----------------------------------------------------------------- full bake
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+def bake(high_v, high_f, low_v, low_f, low_uv, W, H, max_dist, gutter=2, *,
+         diam=None, use_bvh=True, sample=None, nthreads=None, bvh: Bvh | None = None):
+    """The whole bake in FP64.  With ``sample`` (texel ids), only those texels
+    are traced and dilation is skipped.  Returns a dict of numpy arrays."""
+    lib = _load()
+    hv = _c(high_v, np.float32)
+    hf = _c(high_f, np.int32)
+    lv = _c(low_v, np.float32)
+    lf = _c(low_f, np.int32)
+    luv = _c(low_uv, np.float32)
+    if diam is None:
+        diam = float(np.linalg.norm(hv.astype(np.float64).max(0) - hv.astype(np.float64).min(0)))
+    hn = vertex_normals(hv, hf)
+    ln = vertex_normals(lv, lf)
+    face, bary, a2 = raster(luv, W, H)
+    T, w, dg = face_frames(lv, lf, luv, W, H, ln)
+    if use_bvh and bvh is None:
+        bvh = Bvh(hv, hf)
+    n = W * H
+    mask = np.zeros(n, np.uint8)
+    nts = np.zeros((n, 3), np.float64)
+    nts[:, 2] = 1.0
+    disp = np.zeros(n, np.float64)
+    hit_tri = np.full(n, -1, np.int32)
+    hit_t = np.zeros(n, np.float64)
+    hit_b = np.zeros((n, 3), np.float64)
+    flags = np.zeros(n, np.uint8)
+    if sample is not None:
+        texels = _c(sample, np.int64)
+    else:
+        texels = np.flatnonzero(face.reshape(-1) >= 0).astype(np.int64)
+    nth = nthreads or default_threads()
+    rc = lib.or_trace(_p(hv), len(hv), _p(hf), len(hf), _p(hn), bvh.h if use_bvh else None,
+                      _p(lv), _p(lf), _p(ln), _p(luv), _p(T), _p(w), _p(dg),
+                      _p(face), _p(bary), W, H, float(max_dist), float(diam),
+                      _p(texels), len(texels), nth,
+                      _p(mask), _p(nts), _p(disp), _p(hit_tri), _p(hit_t), _p(hit_b), _p(flags))
+    if rc != 0:
+        raise RuntimeError("oracle trace: thread start failed")
+    filled = (face.reshape(-1) >= 0).astype(np.uint8)
+    out = dict(face=face, bary=bary, a2=a2, degen=dg, tangents=T, wsign=w, low_normals=ln, high_normals=hn,
+               mask=mask.reshape(H, W), hit_tri=hit_tri.reshape(H, W), hit_t=hit_t.reshape(H, W),
+               hit_b=hit_b.reshape(H, W, 3), flags=flags.reshape(H, W), texels=texels, diam=diam)
+    if sample is None:
+        filled, nts, disp = dilate(W, H, gutter, filled, nts, disp)
+    out["filled"] = filled.reshape(H, W)
+    out["nts"] = nts.reshape(H, W, 3)
+    out["disp"] = disp.reshape(H, W)
+    out["rgba8"] = encode(nts, filled).reshape(H, W, 4)
+    out["disp16"] = disp.astype(np.float16).reshape(H, W)
+    return out
+
+
+def bake_asset(asset, **kw):
+    return bake(asset.high_v, asset.high_f, asset.low_v, asset.low_f, asset.low_uv,
+                asset.W, asset.H, asset.max_dist, asset.gutter, diam=asset.diam, **kw)
+
+
+# ----------------------------------------------------------------- loss / gradient
+
+def loss_grad(high_v, high_f, high_normals, low_v64, low_f, face, bary, hit_tri, lam, want_grad=True):
+    """Baking loss over hit texels with hit triangles held fixed, and its
+    analytic gradient w.r.t. the low positions (FP64)."""
+    lib = _load()
+    hv = _c(high_v, np.float32)
+    hf = _c(high_f, np.int32)
+    hn = _c(high_normals, np.float64)
+    lv = _c(low_v64, np.float64)
+    lf = _c(low_f, np.int32)
+    face = _c(face, np.int32).reshape(-1)
+    bary = _c(bary, np.float64).reshape(-1, 3)
+    hit_tri = _c(hit_tri, np.int32).reshape(-1)
+    g = np.zeros(lv.shape, np.float64) if want_grad else None
+    L = lib.or_loss_grad(_p(hv), _p(hf), _p(hn), _p(lv), len(lv), _p(lf), len(lf),
+                         _p(face), _p(bary), _p(hit_tri), len(face), float(lam), _p(g))
+    return L, g
+
+
+def fd_grad(high_v, high_f, high_normals, low_v64, low_f, face, bary, hit_tri, lam, h=1e-4, coords=None):
+    """Central finite differences (FP64, step h) of the fixed-hit loss."""
+    lv = np.array(low_v64, dtype=np.float64)
+    g = np.zeros_like(lv)
+    idx = range(lv.size) if coords is None else coords
+    flat = lv.reshape(-1)
+    for c in idx:
+        old = flat[c]
+        flat[c] = old + h
+        lp, _ = loss_grad(high_v, high_f, high_normals, lv, low_f, face, bary, hit_tri, lam, False)
+        flat[c] = old - h
+        lm, _ = loss_grad(high_v, high_f, high_normals, lv, low_f, face, bary, hit_tri, lam, False)
+        flat[c] = old
+        g.reshape(-1)[c] = (lp - lm) / (2 * h)
+    return g

@@ -1,0 +1,755 @@
+/*
+ * FP64 CPU oracle for tangent-space normal baking (Sec. 6.4, "Normal Map
+ * Baking").  TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark call it; the product path never does.
+ * It shares no code, header, table or constant with the CUDA path.
+ *
+ * What it computes, step by step, in the order Sec. 6.4 lists them:
+ *   1. area-weighted smooth vertex normals of both meshes;
+ *   2. the low-poly mesh rasterised into its own UV space: per texel the
+ *      owning low face and barycentrics (exact fixed-point predicates);
+ *   3. per-face tangent frames from the UV gradients, and the
+ *      "degenerate UV" reliability flag;
+ *   4. per ray texel: origin p = sum b_i v_i, direction d = normalize(sum b_i n_i),
+ *      the closest hit (minimum |t|, |t| <= max_dist) of the line p + t d
+ *      against every high-poly triangle (brute force, or a median-split BVH
+ *      that is pinned bit-for-bit to brute force);
+ *   5. the hit's barycentric smooth normal projected into the texel frame;
+ *   6. RGB8 encoding and gutter dilation;
+ *   7. the baking loss mean(t^2) + lambda*mean(1 - n_hit . d) over hit texels
+ *      and its analytic gradient with respect to the low-poly positions.
+ *
+ * Readings of points the paper leaves open are stated where they are used.
+ * Everything is double precision except the UV snapping, which is exact
+ * integer arithmetic by definition (texel coordinates * 256, rounded half
+ * away from zero).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ vectors */
+typedef struct { double x, y, z; } d3;
+static d3 mk(double x, double y, double z) { d3 r = {x, y, z}; return r; }
+static d3 add(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static d3 sub(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static d3 scl(d3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static d3 cross(d3 a, d3 b) { return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+static double norm(d3 a) { return sqrt(dot(a, a)); }
+static d3 normalize(d3 a) { double n = norm(a); return n > 0 ? scl(a, 1.0 / n) : a; }
+static d3 ldf(const float *p, int64_t i) { return mk(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
+static d3 ldd(const double *p, int64_t i) { return mk(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
+static void std3(double *p, int64_t i, d3 v) { p[3 * i] = v.x; p[3 * i + 1] = v.y; p[3 * i + 2] = v.z; }
+static double comp(d3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+/* ------------------------------------------------- 1. vertex normals (Sec. 6.4)
+ * "smooth normal": n_i = normalize(sum over faces f containing i of
+ * (v1 - v0) x (v2 - v0)); the unnormalised cross product weights each face
+ * by its area (reading). */
+void or_vertex_normals(const float *V, int64_t nv, const int32_t *F, int64_t nf, double *N) {
+    memset(N, 0, sizeof(double) * 3 * (size_t)nv);
+    for (int64_t f = 0; f < nf; ++f) {
+        int32_t a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
+        d3 va = ldf(V, a), vb = ldf(V, b), vc = ldf(V, c);
+        d3 n = cross(sub(vb, va), sub(vc, va));
+        for (int k = 0; k < 3; ++k) {
+            int32_t i = F[3 * f + k];
+            std3(N, i, add(ldd(N, i), n));
+        }
+    }
+    for (int64_t i = 0; i < nv; ++i) std3(N, i, normalize(ldd(N, i)));
+}
+
+/* ------------------------------------------------- 2. UV-space raster (Sec. 6.4)
+ * Reading of "rasterizes the low-poly mesh into its own UV space":
+ *  - texel (x, y) has centre (x + 1/2, y + 1/2) in texel units, x = u*W,
+ *    y = v*H (v not flipped);
+ *  - UVs are snapped to 1/256 texel: X = round_half_away(u * W * 256);
+ *  - owner: the lowest-id face whose closed triangle contains the centre;
+ *  - otherwise (conservative coverage) among faces whose triangle overlaps the
+ *    texel square with positive area, the one nearest the centre, with squared
+ *    distances compared at a resolution of 2^-16 (1/256 texel)^2 units
+ *    (floor), ties to the lowest id; barycentrics are those of the closest
+ *    point of that triangle;
+ *  - zero-area faces own nothing; faces with |UV area| < 1e-4 texel^2
+ *    (|2*area| <= 13 in snapped units) are flagged "degenerate UV".
+ */
+int64_t or_snap(float u, int W) {
+    double x = (double)u * (double)W * 256.0; /* exact: 24-bit mantissa x <= 22-bit integer */
+    return x >= 0 ? (int64_t)floor(x + 0.5) : -(int64_t)floor(-x + 0.5);
+}
+
+typedef struct { int64_t X[3], Y[3], a2; } uvtri;
+
+static void load_uvtri(const float *uv, int64_t f, int W, int H, uvtri *t) {
+    for (int k = 0; k < 3; ++k) {
+        t->X[k] = or_snap(uv[6 * f + 2 * k], W);
+        t->Y[k] = or_snap(uv[6 * f + 2 * k + 1], H);
+    }
+    t->a2 = (t->X[1] - t->X[0]) * (t->Y[2] - t->Y[0]) - (t->Y[1] - t->Y[0]) * (t->X[2] - t->X[0]);
+}
+
+static int64_t orient2(int64_t ax, int64_t ay, int64_t bx, int64_t by, int64_t cx, int64_t cy) {
+    return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+}
+
+/* e[i] = twice the signed area opposite vertex i; inside closed triangle iff
+ * all e[i] have the sign of a2 or are zero */
+static int uv_inside(const uvtri *t, int64_t cx, int64_t cy, int64_t e[3]) {
+    if (t->a2 == 0) return 0;
+    e[0] = orient2(t->X[1], t->Y[1], t->X[2], t->Y[2], cx, cy);
+    e[1] = orient2(t->X[2], t->Y[2], t->X[0], t->Y[0], cx, cy);
+    e[2] = orient2(t->X[0], t->Y[0], t->X[1], t->Y[1], cx, cy);
+    if (t->a2 > 0) return e[0] >= 0 && e[1] >= 0 && e[2] >= 0;
+    return e[0] <= 0 && e[1] <= 0 && e[2] <= 0;
+}
+
+/* interiors of the triangle and of the square [sx, sx+256] x [sy, sy+256]
+ * intersect iff no axis from either polygon's edge normals separates them */
+static int uv_overlap(const uvtri *t, int64_t sx, int64_t sy) {
+    if (t->a2 == 0) return 0;
+    int64_t mnx = t->X[0], mxx = t->X[0], mny = t->Y[0], mxy = t->Y[0];
+    for (int k = 1; k < 3; ++k) {
+        if (t->X[k] < mnx) mnx = t->X[k];
+        if (t->X[k] > mxx) mxx = t->X[k];
+        if (t->Y[k] < mny) mny = t->Y[k];
+        if (t->Y[k] > mxy) mxy = t->Y[k];
+    }
+    if (mxx <= sx || mnx >= sx + 256 || mxy <= sy || mny >= sy + 256) return 0;
+    int64_t cxs[4] = {sx, sx + 256, sx, sx + 256}, cys[4] = {sy, sy, sy + 256, sy + 256};
+    for (int k = 0; k < 3; ++k) {
+        int a = k, b = (k + 1) % 3, c = (k + 2) % 3;
+        int64_t nx = -(t->Y[b] - t->Y[a]), ny = t->X[b] - t->X[a];
+        int64_t pe = nx * t->X[a] + ny * t->Y[a];
+        int64_t po = nx * t->X[c] + ny * t->Y[c];
+        int64_t tmn = pe < po ? pe : po, tmx = pe < po ? po : pe;
+        int64_t smn = 0, smx = 0;
+        for (int q = 0; q < 4; ++q) {
+            int64_t p = nx * cxs[q] + ny * cys[q];
+            if (q == 0 || p < smn) smn = p;
+            if (q == 0 || p > smx) smx = p;
+        }
+        if (smx <= tmn || smn >= tmx) return 0;
+    }
+    return 1;
+}
+
+/* squared distance from (cx,cy) to edge k of t, quantised: floor(d^2 * 65536)
+ * in snapped units; UINT64_MAX when d > 256 units (one texel).  Also returns
+ * the closest point's parameter along the edge. */
+static uint64_t edge_qdist(const uvtri *t, int k, int64_t cx, int64_t cy, double *param) {
+    int a = k, b = (k + 1) % 3;
+    int64_t wx = cx - t->X[a], wy = cy - t->Y[a];
+    int64_t dx = t->X[b] - t->X[a], dy = t->Y[b] - t->Y[a];
+    int64_t wd = wx * dx + wy * dy, dd = dx * dx + dy * dy;
+    unsigned __int128 num, den;
+    if (dd == 0 || wd <= 0) {
+        num = (unsigned __int128)(wx * wx + wy * wy); den = 1; *param = 0.0;
+    } else if (wd >= dd) {
+        int64_t ux = cx - t->X[b], uy = cy - t->Y[b];
+        num = (unsigned __int128)(ux * ux + uy * uy); den = 1; *param = 1.0;
+    } else {
+        int64_t cr = wx * dy - wy * dx;
+        unsigned __int128 c2 = (unsigned __int128)(cr < 0 ? -cr : cr);
+        num = c2 * c2; den = (unsigned __int128)dd; *param = (double)wd / (double)dd;
+    }
+    if (num > den * 65536u) return UINT64_MAX;
+    return (uint64_t)((num * 65536u) / den);
+}
+
+static uint64_t tri_qdist(const uvtri *t, int64_t cx, int64_t cy, int *best_edge, double *best_param) {
+    uint64_t best = UINT64_MAX;
+    *best_edge = -1;
+    for (int k = 0; k < 3; ++k) {
+        double p;
+        uint64_t q = edge_qdist(t, k, cx, cy, &p);
+        if (q < best) { best = q; *best_edge = k; *best_param = p; }
+    }
+    return best;
+}
+
+#define KEY_NONE UINT64_MAX
+#define KEY_CONSERVATIVE (1ull << 63)
+
+static uint64_t texel_key(const uvtri *t, int64_t f, int x, int y) {
+    int64_t cx = 256 * (int64_t)x + 128, cy = 256 * (int64_t)y + 128, e[3];
+    if (uv_inside(t, cx, cy, e)) return (uint64_t)f;
+    if (uv_overlap(t, 256 * (int64_t)x, 256 * (int64_t)y)) {
+        int be; double bp;
+        uint64_t q = tri_qdist(t, cx, cy, &be, &bp);
+        if (q == UINT64_MAX) return KEY_NONE; /* cannot happen for an overlapping square */
+        return KEY_CONSERVATIVE | (q << 31) | (uint64_t)f;
+    }
+    return KEY_NONE;
+}
+
+static int64_t fdiv(int64_t a, int64_t b) { int64_t q = a / b; if ((a % b != 0) && ((a < 0) != (b < 0))) --q; return q; }
+
+/* face[H*W] (-1 empty), bary[H*W*3], a2[nf]; brute != 0 evaluates every
+ * (texel, face) pair, otherwise only texels within one texel of each face's
+ * bounding box (the predicates are identical). */
+int or_raster(const float *uv, int64_t nf, int W, int H, int brute, int32_t *face, double *bary, int64_t *a2_out) {
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)W * H);
+    if (!key) return -1;
+    for (int64_t i = 0; i < (int64_t)W * H; ++i) key[i] = KEY_NONE;
+    for (int64_t f = 0; f < nf; ++f) {
+        uvtri t;
+        load_uvtri(uv, f, W, H, &t);
+        if (a2_out) a2_out[f] = t.a2;
+        int x0 = 0, x1 = W - 1, y0 = 0, y1 = H - 1;
+        if (!brute) {
+            int64_t mnx = t.X[0], mxx = t.X[0], mny = t.Y[0], mxy = t.Y[0];
+            for (int k = 1; k < 3; ++k) {
+                if (t.X[k] < mnx) mnx = t.X[k];
+                if (t.X[k] > mxx) mxx = t.X[k];
+                if (t.Y[k] < mny) mny = t.Y[k];
+                if (t.Y[k] > mxy) mxy = t.Y[k];
+            }
+            int64_t a = fdiv(mnx, 256) - 1, b = fdiv(mxx, 256) + 1, c = fdiv(mny, 256) - 1, d = fdiv(mxy, 256) + 1;
+            x0 = a < 0 ? 0 : (int)(a > W - 1 ? W : a);
+            x1 = b > W - 1 ? W - 1 : (int)b;
+            y0 = c < 0 ? 0 : (int)(c > H - 1 ? H : c);
+            y1 = d > H - 1 ? H - 1 : (int)d;
+        }
+        for (int y = y0; y <= y1; ++y)
+            for (int x = x0; x <= x1; ++x) {
+                uint64_t k = texel_key(&t, f, x, y);
+                if (k < key[(int64_t)y * W + x]) key[(int64_t)y * W + x] = k;
+            }
+    }
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int64_t i = (int64_t)y * W + x;
+            uint64_t k = key[i];
+            if (k == KEY_NONE) { face[i] = -1; bary[3 * i] = bary[3 * i + 1] = bary[3 * i + 2] = 0.0; continue; }
+            int64_t f = (int64_t)(k & 0x7fffffffull);
+            face[i] = (int32_t)f;
+            uvtri t;
+            load_uvtri(uv, f, W, H, &t);
+            int64_t cx = 256 * (int64_t)x + 128, cy = 256 * (int64_t)y + 128, e[3];
+            if (!(k & KEY_CONSERVATIVE)) {
+                uv_inside(&t, cx, cy, e);
+                for (int q = 0; q < 3; ++q) bary[3 * i + q] = (double)e[q] / (double)t.a2;
+            } else {
+                int be; double bp = 0.0;
+                tri_qdist(&t, cx, cy, &be, &bp);
+                double b3[3] = {0, 0, 0};
+                b3[be] = 1.0 - bp;
+                b3[(be + 1) % 3] = bp;
+                for (int q = 0; q < 3; ++q) bary[3 * i + q] = b3[q];
+            }
+        }
+    free(key);
+    return 0;
+}
+
+/* ------------------------------------------------- 3. tangent frames (Sec. 6.4)
+ * The paper gives no tangent rule (reading): per face the UV-gradient
+ * tangent T_f = dp/du and bitangent B_f = dp/dv of the affine map from snapped
+ * UVs to positions; per corner T_f is Gram-Schmidt orthonormalised against
+ * the corner's vertex normal; the handedness w = sign((n_0 x T_f) . B_f) is
+ * taken from corner 0.  Faces with |UV area| < 1e-4 texel^2 are unreliable
+ * ("degenerate UV" filter): their output normal is (0,0,1) and their corner
+ * tangents come from the Duff et al. 2017 orthonormal basis of the normal. */
+static d3 onb_tangent(d3 n) {
+    double s = n.z >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (s + n.z);
+    double b = n.x * n.y * a;
+    return mk(1.0 + s * n.x * n.x * a, s * b, -s * n.x);
+}
+
+void or_face_frames(const float *V, const int32_t *F, int64_t nf, const float *uv, int W, int H,
+                    const double *N, double *T /*[nf*3*3]*/, double *wsign /*[nf]*/, uint8_t *degen /*[nf]*/) {
+    for (int64_t f = 0; f < nf; ++f) {
+        uvtri t;
+        load_uvtri(uv, f, W, H, &t);
+        int32_t i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+        d3 v0 = ldf(V, i0), v1 = ldf(V, i1), v2 = ldf(V, i2);
+        d3 e1 = sub(v1, v0), e2 = sub(v2, v0);
+        double du1 = (double)(t.X[1] - t.X[0]), dv1 = (double)(t.Y[1] - t.Y[0]);
+        double du2 = (double)(t.X[2] - t.X[0]), dv2 = (double)(t.Y[2] - t.Y[0]);
+        int bad = (t.a2 <= 13 && t.a2 >= -13);
+        d3 Tf = mk(0, 0, 0), Bf = mk(0, 0, 0);
+        if (!bad) {
+            double det = (double)t.a2;
+            Tf = scl(sub(scl(e1, dv2), scl(e2, dv1)), 1.0 / det);
+            Bf = scl(sub(scl(e2, du1), scl(e1, du2)), 1.0 / det);
+        }
+        int32_t ids[3] = {i0, i1, i2};
+        for (int k = 0; k < 3; ++k) {
+            d3 n = ldd(N, ids[k]);
+            d3 tk = bad ? mk(0, 0, 0) : sub(Tf, scl(n, dot(Tf, n)));
+            if (bad || norm(tk) == 0.0) { tk = onb_tangent(n); if (!bad) bad = 2; }
+            std3(T, 3 * f + k, normalize(tk));
+        }
+        double hs = dot(cross(ldd(N, i0), Tf), Bf);
+        wsign[f] = hs < 0.0 ? -1.0 : 1.0;
+        degen[f] = (uint8_t)(bad != 0);
+    }
+}
+
+/* ------------------------------------------------- 4. closest hit (Sec. 6.4)
+ * The paper locates a high-poly correspondence per texel and keeps hits within
+ * a distance filter.  Reading: the closest intersection of the line
+ * p + t d (both directions) with any high-poly triangle, |t| <= tmax
+ * inclusive, no back-face culling; ties: equal |t| prefers t >= 0, equal t
+ * prefers the lower triangle id.  The intersection is the watertight test of
+ * Woop, Benthin and Wald (2013) in double precision, with a zero edge
+ * function counted as inside. */
+typedef struct { int kx, ky, kz; double Sx, Sy, Sz; d3 o; } ray_t;
+
+static ray_t make_ray(d3 o, d3 d) {
+    ray_t r;
+    double ax = fabs(d.x), ay = fabs(d.y), az = fabs(d.z);
+    r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    r.kx = (r.kz + 1) % 3;
+    r.ky = (r.kx + 1) % 3;
+    if (comp(d, r.kz) < 0.0) { int tmp = r.kx; r.kx = r.ky; r.ky = tmp; }
+    r.Sx = comp(d, r.kx) / comp(d, r.kz);
+    r.Sy = comp(d, r.ky) / comp(d, r.kz);
+    r.Sz = 1.0 / comp(d, r.kz);
+    r.o = o;
+    return r;
+}
+
+typedef struct { int tri; double t, b[3]; } hit_t;
+
+static int isect(const ray_t *r, d3 A, d3 B, d3 C, double *t, double b[3]) {
+    d3 a = sub(A, r->o), bb = sub(B, r->o), c = sub(C, r->o);
+    double Ax = comp(a, r->kx) - r->Sx * comp(a, r->kz), Ay = comp(a, r->ky) - r->Sy * comp(a, r->kz);
+    double Bx = comp(bb, r->kx) - r->Sx * comp(bb, r->kz), By = comp(bb, r->ky) - r->Sy * comp(bb, r->kz);
+    double Cx = comp(c, r->kx) - r->Sx * comp(c, r->kz), Cy = comp(c, r->ky) - r->Sy * comp(c, r->kz);
+    double U = Cx * By - Cy * Bx;
+    double Vv = Ax * Cy - Ay * Cx;
+    double W = Bx * Ay - By * Ax;
+    if ((U < 0.0 || Vv < 0.0 || W < 0.0) && (U > 0.0 || Vv > 0.0 || W > 0.0)) return 0;
+    double det = U + Vv + W;
+    if (det == 0.0) return 0;
+    double Az = r->Sz * comp(a, r->kz), Bz = r->Sz * comp(bb, r->kz), Cz = r->Sz * comp(c, r->kz);
+    double T = U * Az + Vv * Bz + W * Cz;
+    *t = T / det;
+    b[0] = U / det; b[1] = Vv / det; b[2] = W / det;
+    return 1;
+}
+
+static int better(double t, int id, const hit_t *best) {
+    if (best->tri < 0) return 1;
+    double at = fabs(t), ab = fabs(best->t);
+    if (at != ab) return at < ab;
+    if ((t >= 0.0) != (best->t >= 0.0)) return t >= 0.0;
+    return id < best->tri;
+}
+
+static int shares_vertex(const int32_t *F, int a, int b) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (F[3 * a + i] == F[3 * b + j]) return 1;
+    return 0;
+}
+
+static void test_tri(const float *V, const int32_t *F, int tri, const ray_t *r, double tmax, int exclude, hit_t *best) {
+    if (exclude >= 0 && shares_vertex(F, tri, exclude)) return;
+    double t, b[3];
+    if (!isect(r, ldf(V, F[3 * tri]), ldf(V, F[3 * tri + 1]), ldf(V, F[3 * tri + 2]), &t, b)) return;
+    if (fabs(t) > tmax) return;
+    if (better(t, tri, best)) { best->tri = tri; best->t = t; best->b[0] = b[0]; best->b[1] = b[1]; best->b[2] = b[2]; }
+}
+
+/* --- median-split BVH (binary, FP64 exact vertex bounds, leaves <= 4) */
+typedef struct { double lo[3], hi[3]; int left, right, first, count; } bnode;
+typedef struct { bnode *nodes; int nn; int *idx; const float *V; const int32_t *F; int64_t nf; } obvh;
+
+static int cmp_axis;
+static const double *cmp_cent;
+static int cent_cmp(const void *a, const void *b) {
+    double x = cmp_cent[3 * *(const int *)a + cmp_axis], y = cmp_cent[3 * *(const int *)b + cmp_axis];
+    if (x < y) return -1;
+    if (x > y) return 1;
+    return *(const int *)a - *(const int *)b;
+}
+
+static int bvh_rec(obvh *b, double *cent, int first, int count) {
+    int id = b->nn++;
+    bnode *n = &b->nodes[id];
+    for (int k = 0; k < 3; ++k) { n->lo[k] = INFINITY; n->hi[k] = -INFINITY; }
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = first; i < first + count; ++i) {
+        int tr = b->idx[i];
+        for (int v = 0; v < 3; ++v) {
+            d3 p = ldf(b->V, b->F[3 * tr + v]);
+            for (int k = 0; k < 3; ++k) {
+                double c = comp(p, k);
+                if (c < n->lo[k]) n->lo[k] = c;
+                if (c > n->hi[k]) n->hi[k] = c;
+            }
+        }
+        for (int k = 0; k < 3; ++k) {
+            double c = cent[3 * tr + k];
+            if (c < clo[k]) clo[k] = c;
+            if (c > chi[k]) chi[k] = c;
+        }
+    }
+    if (count <= 4) { n->left = n->right = -1; n->first = first; n->count = count; return id; }
+    int ax = 0;
+    for (int k = 1; k < 3; ++k) if (chi[k] - clo[k] > chi[ax] - clo[ax]) ax = k;
+    cmp_axis = ax; cmp_cent = cent;
+    qsort(b->idx + first, (size_t)count, sizeof(int), cent_cmp);
+    int half = count / 2;
+    int l = bvh_rec(b, cent, first, half);
+    int r = bvh_rec(b, cent, first + half, count - half);
+    n = &b->nodes[id];
+    n->left = l; n->right = r; n->first = first; n->count = 0;
+    return id;
+}
+
+void *or_bvh_build(const float *V, const int32_t *F, int64_t nf) {
+    obvh *b = (obvh *)calloc(1, sizeof(obvh));
+    if (!b) return NULL;
+    b->V = V; b->F = F; b->nf = nf;
+    b->nodes = (bnode *)malloc(sizeof(bnode) * (size_t)(2 * nf + 1));
+    b->idx = (int *)malloc(sizeof(int) * (size_t)(nf > 0 ? nf : 1));
+    double *cent = (double *)malloc(sizeof(double) * 3 * (size_t)(nf > 0 ? nf : 1));
+    if (!b->nodes || !b->idx || !cent) { free(b->nodes); free(b->idx); free(cent); free(b); return NULL; }
+    for (int64_t i = 0; i < nf; ++i) {
+        b->idx[i] = (int)i;
+        d3 c = scl(add(add(ldf(V, F[3 * i]), ldf(V, F[3 * i + 1])), ldf(V, F[3 * i + 2])), 1.0 / 3.0);
+        std3(cent, i, c);
+    }
+    if (nf > 0) bvh_rec(b, cent, 0, (int)nf);
+    free(cent);
+    return b;
+}
+
+void or_bvh_free(void *p) {
+    obvh *b = (obvh *)p;
+    if (!b) return;
+    free(b->nodes); free(b->idx); free(b);
+}
+
+/* parameter interval of the line o + t d inside the box, widened so that
+ * rounding can only enlarge it; returns 0 when the line misses the box */
+static int box_interval(const bnode *n, d3 o, d3 d, double *t0, double *t1) {
+    double lo = -INFINITY, hi = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        double ok = comp(o, k), dk = comp(d, k);
+        if (dk == 0.0) {
+            if (ok < n->lo[k] || ok > n->hi[k]) return 0;
+            continue;
+        }
+        double a = (n->lo[k] - ok) / dk, b = (n->hi[k] - ok) / dk;
+        if (a > b) { double tmp = a; a = b; b = tmp; }
+        if (a > lo) lo = a;
+        if (b < hi) hi = b;
+    }
+    double eps = 1e-9 * (fabs(lo) + fabs(hi)) + 1e-12;
+    *t0 = lo - eps; *t1 = hi + eps;
+    return *t0 <= *t1;
+}
+
+static void bvh_closest(const obvh *b, const ray_t *r, d3 o, d3 d, double tmax, int exclude, hit_t *best) {
+    if (b->nf == 0) return;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const bnode *n = &b->nodes[stack[--sp]];
+        double t0, t1;
+        if (!box_interval(n, o, d, &t0, &t1)) continue;
+        double lim = best->tri >= 0 ? fabs(best->t) : tmax;
+        if (t0 > lim || t1 < -lim) continue;
+        if (n->left < 0) {
+            for (int i = n->first; i < n->first + n->count; ++i) test_tri(b->V, b->F, b->idx[i], r, tmax, exclude, best);
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+}
+
+static void closest(const float *V, const int32_t *F, int64_t nf, const obvh *bvh, d3 o, d3 d, double tmax, int exclude, hit_t *best) {
+    ray_t r = make_ray(o, d);
+    best->tri = -1; best->t = 0.0; best->b[0] = best->b[1] = best->b[2] = 0.0;
+    if (bvh) { bvh_closest(bvh, &r, o, d, tmax, exclude, best); return; }
+    for (int64_t i = 0; i < nf; ++i) test_tri(V, F, (int)i, &r, tmax, exclude, best);
+}
+
+/* exposed for pin tests: out = {tri, t, b0, b1, b2} */
+int or_closest_hit(const float *V, const int32_t *F, int64_t nf, void *bvh, const double *o, const double *d, double tmax, double *out) {
+    hit_t h;
+    closest(V, F, nf, (const obvh *)bvh, mk(o[0], o[1], o[2]), mk(d[0], d[1], d[2]), tmax, -1, &h);
+    out[0] = h.tri; out[1] = h.t; out[2] = h.b[0]; out[3] = h.b[1]; out[4] = h.b[2];
+    return h.tri >= 0;
+}
+
+/* ------------------------------------------------- 4-5. trace + shade
+ * Per ray texel (Sec. 6.4): ray from the texel's surface point along its
+ * interpolated normal, distance filter |t| <= max_dist, barycentric smooth
+ * hit normal, projection into the texel tangent frame.  Readings: misses and
+ * unreliable (degenerate-UV) texels get (0,0,1); disp = t on a hit, else 0.
+ * Exception flags (texels where several results are equally correct):
+ *   bit0 hit with min barycentric < 1e-5 (near a high-poly edge)
+ *   bit1 closest |t| within 1e-5*diam of max_dist
+ *   bit2 texel centre within 1e-5 texel of an edge of its low face
+ *   bit3 a triangle sharing no vertex with the hit lies within 1e-5*diam in |t|
+ */
+typedef struct {
+    const float *hv; const int32_t *hf; int64_t nhf; const double *hn; const obvh *bvh;
+    const float *lv; const int32_t *lf; const double *ln; const float *luv;
+    const double *T; const double *wsign; const uint8_t *degen;
+    const int32_t *face; const double *bary;
+    int W, H; double max_dist, diam;
+    const int64_t *texels; int64_t ntex;
+    uint8_t *mask; double *nts; double *disp; int32_t *hit_tri; double *hit_t; double *hit_b; uint8_t *flags;
+    int nthreads, tid;
+} trace_job;
+
+static double seg_dist_units(double cx, double cy, double ax, double ay, double bx, double by) {
+    double dx = bx - ax, dy = by - ay, wx = cx - ax, wy = cy - ay;
+    double dd = dx * dx + dy * dy, s = dd > 0 ? (wx * dx + wy * dy) / dd : 0.0;
+    if (s < 0) s = 0;
+    if (s > 1) s = 1;
+    double px = ax + s * dx - cx, py = ay + s * dy - cy;
+    return sqrt(px * px + py * py);
+}
+
+static void trace_one(const trace_job *j, int64_t tex) {
+    int32_t f = j->face[tex];
+    if (f < 0) return;
+    const double *b = j->bary + 3 * tex;
+    int32_t ids[3] = {j->lf[3 * f], j->lf[3 * f + 1], j->lf[3 * f + 2]};
+    d3 p = mk(0, 0, 0), s = mk(0, 0, 0), ts = mk(0, 0, 0);
+    for (int k = 0; k < 3; ++k) {
+        p = add(p, scl(ldf(j->lv, ids[k]), b[k]));
+        s = add(s, scl(ldd(j->ln, ids[k]), b[k]));
+        ts = add(ts, scl(ldd(j->T, 3 * f + k), b[k]));
+    }
+    d3 d = normalize(s);
+    double tol = 1e-5 * j->diam;
+    hit_t h;
+    closest(j->hv, j->hf, j->nhf, j->bvh, p, d, j->max_dist + tol, -1, &h);
+    uint8_t fl = 0;
+    int hit = h.tri >= 0 && fabs(h.t) <= j->max_dist;
+    if (h.tri >= 0 && fabs(h.t) >= j->max_dist - tol) fl |= 2;
+    if (hit) {
+        double mb = h.b[0] < h.b[1] ? h.b[0] : h.b[1];
+        if (h.b[2] < mb) mb = h.b[2];
+        if (mb < 1e-5) fl |= 1;
+        hit_t h2;
+        closest(j->hv, j->hf, j->nhf, j->bvh, p, d, fabs(h.t) + tol, h.tri, &h2);
+        if (h2.tri >= 0) fl |= 8;
+    }
+    {
+        int x = (int)(tex % j->W), y = (int)(tex / j->W);
+        double cx = 256.0 * x + 128.0, cy = 256.0 * y + 128.0;
+        double X[3], Y[3];
+        for (int k = 0; k < 3; ++k) {
+            X[k] = (double)or_snap(j->luv[6 * f + 2 * k], j->W);
+            Y[k] = (double)or_snap(j->luv[6 * f + 2 * k + 1], j->H);
+        }
+        for (int k = 0; k < 3; ++k)
+            if (seg_dist_units(cx, cy, X[k], Y[k], X[(k + 1) % 3], Y[(k + 1) % 3]) < 1e-5 * 256.0) fl |= 4;
+    }
+    d3 n_ts = mk(0, 0, 1);
+    if (hit && !j->degen[f]) {
+        d3 N = d;
+        d3 Tt = normalize(sub(ts, scl(N, dot(ts, N))));
+        d3 B = scl(cross(N, Tt), j->wsign[f]);
+        d3 m = mk(0, 0, 0);
+        for (int k = 0; k < 3; ++k) m = add(m, scl(ldd(j->hn, j->hf[3 * h.tri + k]), h.b[k]));
+        d3 nh = normalize(m);
+        n_ts = mk(dot(nh, Tt), dot(nh, B), dot(nh, N));
+    }
+    j->mask[tex] = (uint8_t)hit;
+    std3(j->nts, tex, n_ts);
+    j->disp[tex] = hit ? h.t : 0.0;
+    j->hit_tri[tex] = hit ? h.tri : -1;
+    j->hit_t[tex] = h.tri >= 0 ? h.t : 0.0;
+    for (int k = 0; k < 3; ++k) j->hit_b[3 * tex + k] = h.tri >= 0 ? h.b[k] : 0.0;
+    j->flags[tex] = fl;
+}
+
+static void *trace_worker(void *arg) {
+    trace_job *j = (trace_job *)arg;
+    for (int64_t i = j->tid; i < j->ntex; i += j->nthreads) trace_one(j, j->texels ? j->texels[i] : i);
+    return NULL;
+}
+
+int or_trace(const float *hv, int64_t nhv, const int32_t *hf, int64_t nhf, const double *hn, void *bvh,
+             const float *lv, const int32_t *lf, const double *ln, const float *luv,
+             const double *T, const double *wsign, const uint8_t *degen,
+             const int32_t *face, const double *bary, int W, int H, double max_dist, double diam,
+             const int64_t *texels, int64_t ntex, int nthreads,
+             uint8_t *mask, double *nts, double *disp, int32_t *hit_tri, double *hit_t, double *hit_b, uint8_t *flags) {
+    (void)nhv;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    trace_job base = {hv, hf, nhf, hn, (const obvh *)bvh, lv, lf, ln, luv, T, wsign, degen, face, bary,
+                      W, H, max_dist, diam, texels, texels ? ntex : (int64_t)W * H,
+                      mask, nts, disp, hit_tri, hit_t, hit_b, flags, nthreads, 0};
+    trace_job jobs[256];
+    pthread_t th[256];
+    for (int i = 0; i < nthreads; ++i) { jobs[i] = base; jobs[i].tid = i; }
+    for (int i = 1; i < nthreads; ++i)
+        if (pthread_create(&th[i], NULL, trace_worker, &jobs[i])) return -1;
+    trace_worker(&jobs[0]);
+    for (int i = 1; i < nthreads; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------- 6. encode + dilation
+ * "encoded as RGB8" (Sec. 6.4), reading: q = floor(clamp(c/2 + 1/2, 0, 1)*255 + 1/2);
+ * A = 255 on ray and dilated texels, else 0; untouched texels encode (0,0,1).
+ * "dilated at UV seam boundaries" (Sec. 6.4), reading: `gutter` passes; each
+ * pass gives every unfilled texel with at least one filled 8-neighbour (as of
+ * the previous pass) the renormalised mean of those neighbours' tangent-space
+ * normals and the mean of their displacements.  The hit mask is not dilated. */
+static uint8_t enc(double c) {
+    double v = 0.5 * c + 0.5;
+    if (v < 0) v = 0;
+    if (v > 1) v = 1;
+    return (uint8_t)floor(v * 255.0 + 0.5);
+}
+
+void or_encode(const double *nts, const uint8_t *filled, int64_t n, uint8_t *rgba) {
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < 3; ++k) rgba[4 * i + k] = enc(nts[3 * i + k]);
+        rgba[4 * i + 3] = filled[i] ? 255 : 0;
+    }
+}
+
+/* filled: 1 for ray texels on input; dilated texels get 2.  Untouched texels
+ * get nts = (0,0,1), disp = 0. */
+int or_dilate(int W, int H, int gutter, uint8_t *filled, double *nts, double *disp) {
+    int64_t n = (int64_t)W * H;
+    uint8_t *prev = (uint8_t *)malloc((size_t)n);
+    if (!prev) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        if (!filled[i]) { nts[3 * i] = 0; nts[3 * i + 1] = 0; nts[3 * i + 2] = 1; disp[i] = 0; }
+    for (int pass = 0; pass < gutter; ++pass) {
+        memcpy(prev, filled, (size_t)n);
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                int64_t i = (int64_t)y * W + x;
+                if (prev[i]) continue;
+                d3 m = mk(0, 0, 0);
+                double dsum = 0.0;
+                int cnt = 0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int xx = x + dx, yy = y + dy;
+                        if ((dx == 0 && dy == 0) || xx < 0 || yy < 0 || xx >= W || yy >= H) continue;
+                        int64_t q = (int64_t)yy * W + xx;
+                        if (!prev[q]) continue;
+                        m = add(m, ldd(nts, q));
+                        dsum += disp[q];
+                        ++cnt;
+                    }
+                if (!cnt) continue;
+                d3 mm = scl(m, 1.0 / cnt);
+                std3(nts, i, norm(mm) > 0 ? normalize(mm) : mk(0, 0, 1));
+                disp[i] = dsum / cnt;
+                filled[i] = 2;
+            }
+    }
+    free(prev);
+    return 0;
+}
+
+/* ------------------------------------------------- 7. loss + analytic gradient
+ * L = (1/|M|) sum_{k in M} t_k^2 + lambda (1/|M|) sum_{k in M} (1 - n_hit,k . d_k)
+ * over the hit texels M, the hit triangle of each texel held fixed; t is the
+ * intersection of the line with the hit triangle's plane and the hit
+ * barycentrics those of the intersection point, so L is smooth in the low
+ * positions.  grad [nlv*3] receives dL/dV_low (pass NULL for the loss only). */
+double or_loss_grad(const float *hv, const int32_t *hf, const double *hn,
+                    const double *lvd /* low positions in FP64 [nlv*3] */, int64_t nlv, const int32_t *lf, int64_t nlf,
+                    const int32_t *face, const double *bary, const int32_t *hit_tri, int64_t ntex,
+                    double lambda, double *grad) {
+    /* vertex normals of the (possibly perturbed) low mesh, FP64 */
+    double *acc = (double *)calloc((size_t)nlv * 3, sizeof(double));
+    double *gn = grad ? (double *)calloc((size_t)nlv * 3, sizeof(double)) : NULL;
+    for (int64_t f = 0; f < nlf; ++f) {
+        d3 a = ldd(lvd, lf[3 * f]), b = ldd(lvd, lf[3 * f + 1]), c = ldd(lvd, lf[3 * f + 2]);
+        d3 cr = cross(sub(b, a), sub(c, a));
+        for (int k = 0; k < 3; ++k) std3(acc, lf[3 * f + k], add(ldd(acc, lf[3 * f + k]), cr));
+    }
+    if (grad) memset(grad, 0, sizeof(double) * 3 * (size_t)nlv);
+    int64_t count = 0;
+    double sum_t = 0.0, sum_n = 0.0;
+    for (int64_t k = 0; k < ntex; ++k) if (face[k] >= 0 && hit_tri[k] >= 0) ++count;
+    if (count == 0) { free(acc); free(gn); return 0.0; }
+    double inv = 1.0 / (double)count;
+    for (int64_t k = 0; k < ntex; ++k) {
+        if (face[k] < 0 || hit_tri[k] < 0) continue;
+        int32_t f = face[k];
+        const double *b = bary + 3 * k;
+        int32_t ids[3] = {lf[3 * f], lf[3 * f + 1], lf[3 * f + 2]};
+        d3 p = mk(0, 0, 0), s = mk(0, 0, 0);
+        d3 nv[3];
+        for (int q = 0; q < 3; ++q) {
+            nv[q] = normalize(ldd(acc, ids[q]));
+            p = add(p, scl(ldd(lvd, ids[q]), b[q]));
+            s = add(s, scl(nv[q], b[q]));
+        }
+        double sl = norm(s);
+        d3 d = scl(s, 1.0 / sl);
+        int h = hit_tri[k];
+        d3 A = ldf(hv, hf[3 * h]), B = ldf(hv, hf[3 * h + 1]), C = ldf(hv, hf[3 * h + 2]);
+        d3 Nh = cross(sub(B, A), sub(C, A));
+        double nn = dot(Nh, Nh), dn = dot(d, Nh);
+        double t = dot(sub(A, p), Nh) / dn;
+        d3 x = add(p, scl(d, t));
+        double beta[3] = {dot(cross(sub(C, B), sub(x, B)), Nh) / nn,
+                          dot(cross(sub(A, C), sub(x, C)), Nh) / nn,
+                          dot(cross(sub(B, A), sub(x, A)), Nh) / nn};
+        d3 Nj[3] = {ldd(hn, hf[3 * h]), ldd(hn, hf[3 * h + 1]), ldd(hn, hf[3 * h + 2])};
+        d3 m = add(add(scl(Nj[0], beta[0]), scl(Nj[1], beta[1])), scl(Nj[2], beta[2]));
+        double ml = norm(m);
+        d3 nh = scl(m, 1.0 / ml);
+        sum_t += t * t;
+        sum_n += 1.0 - dot(nh, d);
+        if (!grad) continue;
+        /* adjoint, unscaled by 1/|M| until the end */
+        double gt = 2.0 * t;
+        d3 g_nh = scl(d, -lambda);
+        d3 g_d = scl(nh, -lambda);
+        d3 g_m = scl(sub(g_nh, scl(nh, dot(nh, g_nh))), 1.0 / ml);
+        double g_beta[3] = {dot(Nj[0], g_m), dot(Nj[1], g_m), dot(Nj[2], g_m)};
+        d3 gradb[3] = {scl(cross(Nh, sub(C, B)), 1.0 / nn), scl(cross(Nh, sub(A, C)), 1.0 / nn), scl(cross(Nh, sub(B, A)), 1.0 / nn)};
+        d3 g_x = add(add(scl(gradb[0], g_beta[0]), scl(gradb[1], g_beta[1])), scl(gradb[2], g_beta[2]));
+        double g_tt = gt + dot(g_x, d);
+        d3 g_p = sub(g_x, scl(Nh, g_tt / dn));
+        g_d = add(g_d, scl(g_p, t));
+        d3 g_s = scl(sub(g_d, scl(d, dot(d, g_d))), 1.0 / sl);
+        for (int q = 0; q < 3; ++q) {
+            std3(grad, ids[q], add(ldd(grad, ids[q]), scl(g_p, b[q])));
+            std3(gn, ids[q], add(ldd(gn, ids[q]), scl(g_s, b[q])));
+        }
+    }
+    if (grad) {
+        /* through n_i = normalize(a_i), a_i = sum of face cross products */
+        double *ga = (double *)calloc((size_t)nlv * 3, sizeof(double));
+        for (int64_t i = 0; i < nlv; ++i) {
+            d3 a = ldd(acc, i);
+            double al = norm(a);
+            if (al == 0.0) continue;
+            d3 n = scl(a, 1.0 / al), g = ldd(gn, i);
+            std3(ga, i, scl(sub(g, scl(n, dot(n, g))), 1.0 / al));
+        }
+        for (int64_t f = 0; f < nlf; ++f) {
+            int32_t i0 = lf[3 * f], i1 = lf[3 * f + 1], i2 = lf[3 * f + 2];
+            d3 g = add(add(ldd(ga, i0), ldd(ga, i1)), ldd(ga, i2));
+            d3 e1 = sub(ldd(lvd, i1), ldd(lvd, i0)), e2 = sub(ldd(lvd, i2), ldd(lvd, i0));
+            d3 g1 = cross(e2, g), g2 = cross(g, e1);
+            std3(grad, i1, add(ldd(grad, i1), g1));
+            std3(grad, i2, add(ldd(grad, i2), g2));
+            std3(grad, i0, sub(ldd(grad, i0), add(g1, g2)));
+        }
+        for (int64_t i = 0; i < 3 * nlv; ++i) grad[i] *= inv;
+        free(ga);
+    }
+    free(acc); free(gn);
+    return (sum_t + lambda * sum_n) * inv;
+}

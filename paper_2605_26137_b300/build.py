@@ -1,0 +1,93 @@
+"""In-tree build of the native parts.
+
+* ``libagbake.so``  - the CUDA baker behind the C ABI of ``include/ag.h``,
+  compiled by nvcc for sm_103a only.
+* ``synth/libsynth.so`` - the marching-tetrahedra fixture mesher (plain C).
+
+Both land next to their sources so that they travel with the repository
+snapshot; nothing is installed into site-packages.
+"""
+from __future__ import annotations
+
+import glob
+import os
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+LIB = os.path.join(PKG, "libagbake.so")
+SYNTH_SRC = os.path.join(PKG, "synth", "mt.c")
+SYNTH_LIB = os.path.join(PKG, "synth", "libsynth.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
+
+
+def _nvcc() -> str:
+    cand = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    return cand if os.path.exists(cand) else "nvcc"
+
+
+def _stale(target: str, sources) -> bool:
+    if not os.path.exists(target):
+        return True
+    t = os.path.getmtime(target)
+    return any(os.path.getmtime(s) > t for s in sources)
+
+
+def build_synth(force: bool = False) -> str:
+    if force or _stale(SYNTH_LIB, [SYNTH_SRC]):
+        tmp = SYNTH_LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-o", tmp, SYNTH_SRC])
+        os.replace(tmp, SYNTH_LIB)
+    return SYNTH_LIB
+
+
+def cuda_sources():
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def build_cuda(force: bool = False, verbose: bool = False, extra=()) -> str:
+    srcs = cuda_sources()
+    deps = srcs + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    if not (force or _stale(LIB, deps)):
+        return LIB
+    objdir = os.path.join(ROOT, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    objs = []
+    procs = []
+    for s in srcs:
+        o = os.path.join(objdir, os.path.basename(s) + ".o")
+        objs.append(o)
+        cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-dc", "-c", s, "-o", o]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    failed = []
+    for cmd, p in procs:
+        out, _ = p.communicate()
+        if verbose or p.returncode:
+            sys.stderr.write(out.decode(errors="replace"))
+        if p.returncode:
+            failed.append(" ".join(cmd))
+    if failed:
+        raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
+    tmp = LIB + f".tmp{os.getpid()}"
+    subprocess.check_call([_nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs,
+                           "-lcudart_static", "-lrt", "-ldl", "-lpthread"])
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def build_all(force: bool = False) -> None:
+    build_synth(force)
+    build_cuda(force)
+
+
+if __name__ == "__main__":
+    build_all(force="--force" in sys.argv)
+    print(LIB)
