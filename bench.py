@@ -1,0 +1,515 @@
+"""Benchmark of the B300 normal baker (one JSON line on rank 0).
+
+Headline workload: one asset shaped like the pipeline's output (Sec. 6 opening
+paragraph and Sec. 6.4): a marching-grid extraction of a seeded smooth union
+of 32 ellipsoids / rounded boxes with ~2M high-poly triangles, a ~30k-face
+low-poly extraction of the same field with the trivial grid atlas at 2048^2,
+max_dist = 2% of the high bbox diagonal, RGBA8 normal map + FP16
+displacement.  A step is one full bake (UV raster, tangent frames,
+closest-hit traversal with shading, dilation and encoding); the BVH is built
+once per high mesh and timed separately.  The metric is rays per second
+(ray texels baked per second, whole bake) and ms per bake; beside it the
+batched-vs-one-by-one speedup, the backward/forward time ratio and the
+quantised-vs-FP32 BVH comparison.
+
+--impl reference times the FP64 CPU oracle (the repository's plain,
+deliberately slow reference) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s & ms per 2048² bake on 2M-tri mesh; batched vs single; bwd/fwd ratio"
+UNIT = "Mrays/s"
+WORKLOAD = "single asset: SDF union of 32 primitives, ~2M-tri high mesh, ~30k-tri low mesh, 2048x2048 grid atlas"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--high-faces", type=int, default=2_000_000)
+    p.add_argument("--low-faces", type=int, default=30_000)
+    p.add_argument("--res", type=int, default=2048)
+    p.add_argument("--batch-assets", type=int, default=64, help="assets of the batched comparison (0 = skip)")
+    p.add_argument("--batch-scale", type=float, default=1.0, help="scale of the batched assets' face counts")
+    p.add_argument("--no-extras", action="store_true", help="headline only (no backward / layout / batch legs)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--schedule", default="auto")
+    p.add_argument("--json-out", default=None)
+    p.add_argument("--sdf-device", default=None, help="device for sampling the fixture SDF (default: the GPU)")
+    p.add_argument("--profile", action="store_true",
+                   help="profiling case for ncu: one BVH build and --steps plain bakes, nothing else")
+    p.add_argument("--layout", default="q8", choices=["q8", "f32"])
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def trace_source_hash():
+    h = hashlib.sha256()
+    for fn in ("trace.cu", "ag_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(layout_tag: str):
+    """DRAM bytes per trace launch from the committed ncu summary, or None if
+    the summary is missing or was taken on a different trace kernel source."""
+    path = os.path.join(ROOT, "profiles", "trace_kernel_2048_2M.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(rf"dram_bytes_per_launch_{layout_tag}:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != trace_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout=10.0):
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.05)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0=None, t1=None, margin=0.25):
+        """Samples taken within [t0 - margin, t1 + margin] (the timed region
+        plus one sampling period on each side)."""
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, ln in self.lines:
+            if t0 is not None and not (t0 - margin <= ts <= t1 + margin):
+                continue
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workload
+
+def make_asset(args, device):
+    from paper_2605_26137_b300 import synth
+    if args.sdf_device:
+        device = args.sdf_device
+    return synth.sdf_asset(args.seed, args.high_faces, args.low_faces, args.res, args.res, n_prims=32, device=device)
+
+
+def run_profile(args):
+    """Few launches: BVH build, then --steps bakes of the headline asset."""
+    import torch
+    import paper_2605_26137_b300 as pb
+    torch.cuda.set_device(0)
+    a = make_asset(args, "cuda")
+    hv, hf, lv, lf, uv = to_dev(a, torch)
+    bvh = pb.Bvh(hv, hf, layout=args.layout)
+    out = pb.alloc_outputs(args.res, args.res, hv.device)
+    for _ in range(args.steps):
+        pb.bake(bvh, lv, lf, uv, args.res, args.res, a.max_dist, out=out)
+    pb.sync_status()
+    print(json.dumps({"profile_case": WORKLOAD, "layout": args.layout, "high_tris": int(len(a.high_f)),
+                      "bakes": args.steps, "trace_source_hash": trace_source_hash()}))
+
+
+def to_dev(a, torch):
+    def t(x):
+        return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    return t(a.high_v), t(a.high_f), t(a.low_v), t(a.low_f), t(a.low_uv)
+
+
+def bytes_per_ray(node_size, nodes_per_ray, tris_per_ray, hit_frac):
+    """Algorithmic bytes one ray requests from memory in the trace kernel:
+    ray record 16, low face 16, 3 low positions + 3 low normals + 3 corner
+    tangents 144 (float4 each), node_size per node visit, 48 per triangle
+    test, on a hit the hit record 48 + 3 smooth normals 48, outputs 17
+    (float4 normal/displacement + mask byte)."""
+    return 16 + 16 + 144 + node_size * nodes_per_ray + 48 * tris_per_ray + hit_frac * (48 + 48) + 17
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    a = make_asset(args, dev)
+    cores = oracle.default_threads()
+    face, _, _ = oracle.raster(a.low_uv, a.W, a.H)
+    rays = np.flatnonzero(face.reshape(-1) >= 0)
+    bvh = oracle.Bvh(a.high_v, a.high_f)
+    rng = np.random.default_rng(0)
+    tt = []
+    for m in (500, 4000):
+        probe = rng.choice(rays, size=min(len(rays), m), replace=False)
+        t0 = time.perf_counter()
+        oracle.bake_asset(a, sample=probe, bvh=bvh, nthreads=cores)
+        tt.append(time.perf_counter() - t0)
+    per_ray = max((tt[1] - tt[0]) / 3500, 1e-9)
+    n = int(min(len(rays), max(1000, args.cpu_seconds / per_ray / max(1, args.steps + args.warmup))))
+    times = []
+    for i in range(args.warmup + args.steps):
+        samp = rng.choice(rays, size=n, replace=False)
+        t0 = time.perf_counter()
+        oracle.bake_asset(a, sample=samp, bvh=bvh, nthreads=cores)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    v = n * len(times) / sum(times) / 1e6
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "ray_texels": int(len(rays)), "high_tris": int(len(a.high_f)),
+                       "low_tris": int(len(a.low_f)), "atlas": a.W},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} random ray texels of the {len(rays)} per step (FP64 oracle, median-split BVH, "
+                                       f"raster + per-face frames + traced texels; BVH build untimed)"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(a, seconds):
+    """The FP64 oracle as it stands, on all host cores, over random ray texels
+    of the headline asset: the sample grows to about `seconds` of CPU work
+    (whole passes over all ray texels are repeated if one pass is shorter)."""
+    import oracle
+    cores = oracle.default_threads()
+    face, _, _ = oracle.raster(a.low_uv, a.W, a.H)
+    rays = np.flatnonzero(face.reshape(-1) >= 0)
+    bvh = oracle.Bvh(a.high_v, a.high_f)
+    rng = np.random.default_rng(1)
+    tt = []
+    for m in (500, 4000):
+        probe = rng.choice(rays, size=min(len(rays), m), replace=False)
+        t0 = time.perf_counter()
+        oracle.bake_asset(a, sample=probe, bvh=bvh, nthreads=cores)
+        tt.append(time.perf_counter() - t0)
+    per_ray = max((tt[1] - tt[0]) / 3500, 1e-9)
+    fixed = max(tt[0] - 500 * per_ray, 0.0)
+    n = int(min(len(rays), max(1000, (seconds - fixed) / per_ray)))
+    done, spent, passes = 0, 0.0, 0
+    while True:
+        samp = rng.choice(rays, size=n, replace=False) if n < len(rays) else rays
+        t0 = time.perf_counter()
+        oracle.bake_asset(a, sample=samp, bvh=bvh, nthreads=cores)
+        spent += time.perf_counter() - t0
+        done += len(samp)
+        passes += 1
+        if spent >= 0.8 * seconds or n < len(rays) or passes >= 50:
+            break
+    return {"value": done / spent / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{passes} x {len(samp)} ray texels of the {len(rays)} ({spent:.1f} s; FP64 oracle: raster, "
+                      f"frames, median-split BVH traversal, shading; all host cores; oracle BVH build untimed)"}
+
+
+# --------------------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    if args.profile:
+        run_profile(args)
+        return
+    import torch
+    import paper_2605_26137_b300 as pb
+    from paper_2605_26137_b300 import synth
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    pb.load_library()
+
+    a = make_asset(args, dev)
+    hv, hf, lv, lf, uv = to_dev(a, torch)
+    W = H = args.res
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bvh = pb.Bvh(hv, hf, layout="q8")
+    build_wall_ms = 1e3 * (time.perf_counter() - t0)
+    info = bvh.info()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    # counting build: exact node visits / triangle tests per ray
+    cnt = pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, counters=True, aux=True, schedule=args.schedule)
+    pb.sync_status()
+    c = cnt.counters.cpu().numpy().astype(np.float64)
+    n_rays = int(cnt.n_rays.item())
+    nodes_pr, tris_pr, hit_frac = c[1] / c[0], c[2] / c[0], c[3] / c[0]
+    bpr = bytes_per_ray(info["node_size"], nodes_pr, tris_pr, hit_frac)
+
+    out = pb.alloc_outputs(W, H, dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        clk.wait_first()
+        for _ in range(args.warmup):
+            pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, schedule=args.schedule)
+        pb.sync_status()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, schedule=args.schedule, events=ev[i])
+        torch.cuda.synchronize()
+        wall1 = time.perf_counter()
+        wall = wall1 - wall0
+        time.sleep(0.3)
+    pb.sync_status()
+    step_ms = [ev[i][0].elapsed_time(ev[i][3]) for i in range(args.steps)]
+    trace_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    prep_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    fin_ms = [ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps)]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = n_rays * args.steps * world / (tot_ms * 1e-3) / 1e6
+    trace_avg = statistics.mean(trace_ms)
+    hbm, peak_kind = peaks()
+    achieved = bpr * n_rays / (trace_avg * 1e-3) / 1e9
+    clocks = clk.summary(wall0, wall1)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "high_tris": int(len(a.high_f)), "low_tris": int(len(a.low_f)),
+                       "atlas": W, "ray_texels": n_rays, "max_dist": a.max_dist, "seed": args.seed,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "flushed between steps (512 MB write)", "bvh_layout": "q8",
+                       "outputs": "RGBA8 normal + FP16 displacement + mask"},
+            "ms_per_bake": tot_ms / args.steps,
+            "stages_ms": {"raster_tangent": statistics.mean(prep_ms), "trace": trace_avg,
+                          "dilate_encode": statistics.mean(fin_ms)},
+            "trace_mrays_s": n_rays / (trace_avg * 1e-3) / 1e6,
+            "wall_ms_per_step": 1e3 * wall / args.steps,
+            "bvh": {"build_ms": info["build_ms"], "build_wall_ms": build_wall_ms, "nodes": info["n_nodes"],
+                    "node_bytes": info["node_bytes"], "tri_bytes": info["tri_bytes"], "depth": info["max_depth"]},
+            "per_ray": {"nodes": nodes_pr, "tris": tris_pr, "hit_frac": hit_frac, "bytes": bpr},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": recorded_traffic("q8"),
+                         "kernel": "k_trace (closest-hit traversal + shading)", "peak_kind": peak_kind},
+            "clocks": clocks,
+            "gpu_launches": 7 * args.steps}
+
+    if not args.no_extras:
+        line.update(extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, step_ms))
+    line["e2e"] = e2e(args, pb, torch, a, W, H, dev, n_rays)
+    if rank == 0:
+        line["cpu_baseline"] = cpu_baseline(a, args.cpu_seconds)
+        s = json.dumps(line)
+        print(s, flush=True)
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                f.write(s + "\n")
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def timed(torch, fn, steps, warmup, flush=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ms]
+
+
+def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms):
+    res = {}
+    steps = max(3, args.steps // 2)
+    # backward vs forward (loss + gradient w.r.t. the low positions, hits recomputed)
+    bwd = timed(torch, lambda: pb.bake_backward(bvh, lv, lf, uv, W, H, a.max_dist, 0.1), steps, 2, flush)
+    pb.sync_status()
+    res["bwd_ms"] = statistics.mean(bwd)
+    res["bwd_fwd_ratio"] = statistics.mean(bwd) / statistics.mean(fwd_ms)
+    # FP32-node BVH vs 8-bit quantised nodes on the same asset
+    bf = pb.Bvh(hv, hf, layout="f32")
+    cnt = pb.bake(bf, lv, lf, uv, W, H, a.max_dist, counters=True, aux=True)
+    pb.sync_status()
+    c = cnt.counters.cpu().numpy().astype(np.float64)
+    out = pb.alloc_outputs(W, H, dev)
+    f32 = timed(torch, lambda: pb.bake(bf, lv, lf, uv, W, H, a.max_dist, out=out), steps, 2, flush)
+    n_rays = int(cnt.n_rays.item())
+    res["layout_f32"] = {"ms_per_bake": statistics.mean(f32), "mrays_s": n_rays / statistics.mean(f32) / 1e3,
+                         "bytes_per_ray": bytes_per_ray(bf.info()["node_size"], c[1] / c[0], c[2] / c[0], c[3] / c[0]),
+                         "node_bytes": bf.info()["node_bytes"], "nodes_per_ray": c[1] / c[0]}
+    bf.free()
+    if args.batch_assets > 0:
+        res["batch"] = batch_leg(args, pb, torch, dev, flush)
+    return res
+
+
+def batch_leg(args, pb, torch, dev, flush):
+    """64 assets of uneven size: one captured persistent batch vs 64 ag_bake calls."""
+    from paper_2605_26137_b300 import synth
+    rng = np.random.default_rng(1000 + args.seed)
+    assets, handles = [], []
+    total_tris = 0
+    for i in range(args.batch_assets):
+        nh = int(math.exp(rng.uniform(math.log(1e5), math.log(4e6))) * args.batch_scale)
+        nl = int(math.exp(rng.uniform(math.log(2e3), math.log(5e4))) * args.batch_scale)
+        res = int(rng.choice([512, 1024, 2048]))
+        npr = int(rng.integers(8, 65))
+        a = synth.sdf_asset(5000 + i, max(nh, 2000), max(nl, 200), res, res, n_prims=npr, device=dev)
+        hv, hf, lv, lf, uv = to_dev(a, torch)
+        bvh = pb.Bvh(hv, hf)
+        handles.append(bvh)
+        total_tris += len(a.high_f)
+        assets.append(pb.Asset(bvh, lv, lf, uv, a.W, a.H, a.max_dist))
+    seq_out = [pb.alloc_outputs(x.W, x.H, dev) for x in assets]
+
+    def seq():
+        for x, o in zip(assets, seq_out):
+            pb.bake(x.bvh, x.low_verts, x.low_faces, x.low_uv, x.W, x.H, x.max_dist, out=o)
+
+    plan = pb.BatchPlan(assets)
+    steps = max(3, args.steps // 2)
+    t_seq = timed(torch, seq, steps, 1, flush)
+    t_bat = timed(torch, plan.launch, steps, 1, flush)
+    pb.sync_status()
+    rays = 0
+    # ray count from one aux bake per asset
+    for x in assets:
+        o = pb.bake(x.bvh, x.low_verts, x.low_faces, x.low_uv, x.W, x.H, x.max_dist, aux=True)
+        rays += int(o.n_rays.item())
+    plan.free()
+    for h in handles:
+        h.free()
+    ms_seq, ms_bat = statistics.mean(t_seq), statistics.mean(t_bat)
+    return {"assets": len(assets), "high_tris_total": total_tris, "rays_total": rays, "ms_sequential": ms_seq,
+            "ms_batched": ms_bat, "speedup": ms_seq / ms_bat, "mrays_s_batched": rays / ms_bat / 1e3,
+            "mrays_s_sequential": rays / ms_seq / 1e3}
+
+
+def e2e(args, pb, torch, a, W, H, dev, n_rays):
+    """Through the public API from pinned HOST buffers: upload high and low
+    meshes, build the BVH, bake, read the maps back, every step."""
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+           for k, v in (("hv", a.high_v), ("hf", a.high_f), ("lv", a.low_v), ("lf", a.low_f), ("uv", a.low_uv))}
+    rgba_h = torch.empty((H, W, 4), dtype=torch.uint8).pin_memory()
+    mask_h = torch.empty((H, W), dtype=torch.uint8).pin_memory()
+    disp_h = torch.empty((H, W), dtype=torch.float16).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in pin.values())
+    d2h = rgba_h.numel() + mask_h.numel() + disp_h.numel() * 2
+
+    def step():
+        d = {k: v.to(dev, non_blocking=True) for k, v in pin.items()}
+        bvh = pb.Bvh(d["hv"], d["hf"])
+        out = pb.bake(bvh, d["lv"], d["lf"], d["uv"], W, H, a.max_dist)
+        rgba_h.copy_(out.normal_rgba8, non_blocking=True)
+        mask_h.copy_(out.mask, non_blocking=True)
+        disp_h.copy_(out.disp, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        bvh.free()
+
+    steps = max(3, args.steps // 2)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": n_rays / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_asset": 1e3 * dt, "includes": "H2D of both meshes, BVH build, bake, D2H of the three maps"}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,239 @@
+/*
+ * ag.h - C ABI of the B300 tangent-space normal baker.
+ *
+ * The operation is the normal-baking stage of AssetGen's geometry
+ * post-processing (Sec. 6.4, "Normal Map Baking"): the low-poly mesh is
+ * rasterised into its own UV space; for every covered texel a ray is cast
+ * from the texel's surface point along its interpolated smooth normal against
+ * a BVH over the dense high-poly mesh; the closest hit within the distance
+ * filter gives a barycentric smooth normal that is written in the texel's
+ * tangent frame (RGB8), with a hit mask and a signed displacement, and the
+ * map is dilated across UV seams.  Texels of faces with a degenerate UV
+ * parameterisation get the neutral normal (0,0,1).
+ *
+ * Conventions shared by every call
+ *  - All mesh and image pointers are DEVICE pointers (CUDA global memory on
+ *    the current device) owned by the caller; the library never frees them.
+ *  - Vertices are float32 xyz, tightly packed ([n*3]); faces are int32 vertex
+ *    indices ([n*3]); UVs are per face corner ([n_faces*3*2], u then v, in
+ *    [0,1] atlas units; texel (x,y) has centre ((x+0.5)/W, (y+0.5)/H)).
+ *  - Images are row-major, H rows of W texels, texel index y*W + x.
+ *  - Every call is ordered on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) and returns after enqueueing work; nothing synchronises
+ *    the host except ag_bvh_build (it reads back level sizes while
+ *    collapsing the tree) and ag_sync_status.
+ *  - Argument errors are detected on the host before any work is enqueued
+ *    and returned as AG_ERR_INVALID_ARG / AG_ERR_BAD_HANDLE; the message is
+ *    available from ag_last_error() on the calling thread.
+ *  - Device-side limits (traversal step cap, traversal stack overflow) set a
+ *    per-process status word that ag_sync_status() returns and clears.
+ *  - Scratch memory is taken from the device's stream-ordered memory pool
+ *    (cudaMallocAsync) and returned on the same stream.
+ */
+#ifndef AG_H
+#define AG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(_WIN32)
+#define AG_API __declspec(dllexport)
+#else
+#define AG_API __attribute__((visibility("default")))
+#endif
+
+typedef struct ag_bvh *ag_bvh_t;               /* opaque; owns the BVH's device memory */
+typedef struct ag_batch_plan *ag_batch_plan_t; /* opaque; owns scratch + a CUDA graph */
+typedef void *ag_stream_t;                     /* a cudaStream_t */
+
+typedef enum {
+    AG_OK = 0,
+    AG_ERR_INVALID_ARG = 1,     /* bad pointer, size or option; nothing was enqueued */
+    AG_ERR_OOM = 2,             /* device or host allocation failed */
+    AG_ERR_CUDA = 3,            /* a CUDA runtime call failed (message has the CUDA error) */
+    AG_ERR_TRAVERSAL_LIMIT = 4, /* a ray hit the step cap or overflowed its stack (results invalid) */
+    AG_ERR_BAD_HANDLE = 5       /* NULL, freed or foreign handle */
+} ag_status;
+
+enum { AG_BVH_Q8 = 0, AG_BVH_F32 = 1 };
+enum { AG_SCHED_AUTO = -1, AG_SCHED_THREAD = 0, AG_SCHED_WARP = 1 };
+
+/* Options.  Zero-initialise then call ag_opts_default, or pass NULL for the
+ * defaults. */
+typedef struct {
+    int32_t bvh_layout;  /* ag_bvh_build: AG_BVH_Q8 (80-byte nodes, 8-bit child boxes rounded
+                            outward) or AG_BVH_F32 (208-byte nodes, exact FP32 child boxes) */
+    int32_t gutter;      /* dilation passes, 0..8 (default 2) */
+    int32_t disp_fp16;   /* 1: d_disp is IEEE binary16 [H*W] (default); 0: float32 [H*W] */
+    int32_t schedule;    /* traversal schedule, AG_SCHED_* (default AG_SCHED_AUTO) */
+    int32_t block_size;  /* trace threads per block, 64..1024, multiple of 32 (0 = schedule default) */
+    int32_t blocks_per_sm; /* persistent trace CTAs per SM (0 = schedule default) */
+    int32_t max_steps;   /* per-ray traversal step cap (0 = 1<<20); exceeding it sets
+                            AG_ERR_TRAVERSAL_LIMIT */
+    int32_t reserved[9];
+} ag_opts;
+
+/* Optional extra outputs of ag_bake (any member may be NULL). */
+typedef struct {
+    float *normal_ts;   /* [H*W*3] tangent-space normal, float32, after dilation */
+    float *disp_f32;    /* [H*W] displacement, float32, after dilation */
+    int32_t *face;      /* [H*W] owning low face of the UV raster, -1 where empty */
+    float *bary;        /* [H*W*3] raster barycentrics of the texel's surface point */
+    int32_t *hit_tri;   /* [H*W] high-poly triangle id of the closest hit, -1 on miss/empty */
+    float *hit_t;       /* [H*W] signed ray parameter of the hit (0 on miss/empty) */
+    uint64_t *counters; /* [4] device, accumulated (not cleared): rays traced, node visits,
+                           triangle tests, hits.  Non-NULL selects the counting build of the
+                           traversal (slower; used to measure bytes per ray). */
+    int32_t *n_rays;    /* [1] device: number of ray texels */
+    void **events;      /* HOST array of 4 cudaEvent_t created by the caller, recorded on
+                           `stream`: before the UV raster, before the traversal, after the
+                           traversal, after dilation/encoding (per-stage timing) */
+} ag_bake_aux;
+
+/* One asset of a batched bake: the arguments of ag_bake. */
+typedef struct {
+    ag_bvh_t bvh;
+    const float *lverts;     /* [n_lverts*3] */
+    const float *lnormals;   /* [n_lverts*3] or NULL (area-weighted normals are derived) */
+    const float *luv;        /* [n_lfaces*3*2] */
+    const int32_t *lfaces;   /* [n_lfaces*3] */
+    int64_t n_lverts, n_lfaces;
+    int32_t W, H;
+    float max_dist;
+    uint8_t *normal_rgba8;   /* [H*W*4] */
+    uint8_t *mask;           /* [H*W] */
+    void *disp;              /* [H*W] half or float (ag_opts.disp_fp16) */
+} ag_asset_desc;
+
+/* Size and shape of a built BVH. */
+typedef struct {
+    int64_t n_tris, n_verts, n_nodes;
+    int64_t node_bytes, tri_bytes, normal_bytes; /* device bytes of each array */
+    int32_t layout, node_size, max_depth, reserved;
+    float scene_lo[3], scene_hi[3];
+    float diam;                                  /* bbox diagonal of the high mesh */
+    float build_ms;                              /* device time of the last build */
+} ag_bvh_info_t;
+
+/* Fill `o` with the defaults listed above. */
+AG_API void ag_opts_default(ag_opts *o);
+
+/*
+ * ag_bvh_build - acceleration structure over the high-poly mesh
+ * (Sec. 6.4: "A GPU BVH built on the high-poly mesh").
+ * d_verts [n_verts*3] float32, d_faces [n_faces*3] int32 (0 <= index < n_verts;
+ * checked on the device: out-of-range faces are reported as AG_ERR_INVALID_ARG).
+ * Builds a linear BVH (30-bit Morton codes of triangle centroids, device radix
+ * sort, Karras hierarchy), collapses it to 8-wide nodes with leaves of <= 3
+ * triangles, stores child boxes per opts->bvh_layout, reorders triangles into
+ * leaf order and computes area-weighted smooth vertex normals.  The handle
+ * keeps its own copies; the inputs may be freed after the call returns.
+ * Synchronises `stream`.  1 <= n_faces < 2^29, 3 <= n_verts < 2^31.
+ */
+AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
+                              int64_t n_faces, const ag_opts *opts, ag_stream_t stream,
+                              ag_bvh_t *out);
+
+/* Free a handle (synchronises the device first).  NULL is a no-op. */
+AG_API ag_status ag_bvh_free(ag_bvh_t h);
+
+/* Query sizes of a built BVH. */
+AG_API ag_status ag_bvh_info(ag_bvh_t h, ag_bvh_info_t *out);
+
+/*
+ * ag_bvh_copy_out - copy a built BVH to HOST buffers (diagnostics and tests;
+ * synchronises the device).  Any pointer may be NULL.  Sizes follow
+ * ag_bvh_info: nodes [node_bytes] in the layout's node format (80-byte
+ * quantised nodes or 208-byte FP32 nodes, see the node description in
+ * paper_2605_26137_b300/csrc/ag_internal.cuh), tris [n_tris*12] float (three
+ * vertices per leaf-order record, each xyz + the vertex index's bits),
+ * tri_ids [n_tris] original triangle of each record, vnormals [n_verts*4]
+ * float (unit smooth normal xyz, 0).
+ */
+AG_API ag_status ag_bvh_copy_out(ag_bvh_t h, void *nodes, float *tris, int32_t *tri_ids, float *vnormals);
+
+/*
+ * ag_bake - one tangent-space normal bake (Sec. 6.4, all four stages).
+ * Low mesh: d_lverts [n_lverts*3], d_lnormals [n_lverts*3] or NULL
+ * (area-weighted vertex normals are derived), d_luv per corner
+ * [n_lfaces*3*2], d_lfaces [n_lfaces*3].  W, H in 1..16384 texels; UV
+ * coordinates must lie in [-1, 2].  max_dist > 0: hits with |t| > max_dist
+ * are rejected (the distance filter).
+ * Outputs (caller-owned device buffers, fully overwritten):
+ *   d_normal_rgba8 [H*W*4]: RGB = 128 + round(127 * n_ts) (codes 1..255,
+ *     half-way cases away from zero), A = 255 on covered and dilated texels,
+ *     else 0; empty texels encode (0,0,1) = (128,128,255);
+ *   d_mask [H*W]: 1 where a ray texel found a hit, else 0 (not dilated);
+ *   d_disp [H*W]: signed hit distance t (0 on miss), dilated like the normal;
+ *     binary16 or float32 per opts->disp_fp16.
+ * `aux` (NULL allowed) adds the optional outputs of ag_bake_aux.
+ */
+AG_API ag_status ag_bake(ag_bvh_t h, const float *d_lverts, const float *d_lnormals,
+                         const float *d_luv, const int32_t *d_lfaces, int64_t n_lverts,
+                         int64_t n_lfaces, int32_t W, int32_t H, float max_dist,
+                         const ag_opts *opts, ag_stream_t stream, uint8_t *d_normal_rgba8,
+                         uint8_t *d_mask, void *d_disp, const ag_bake_aux *aux);
+
+/*
+ * ag_bake_batch - bake n_assets (1..4096) independent assets with one
+ * persistent traversal launch over a global ray queue (batch-level analogue
+ * of the pipelined serving of Sec. 8).  `descs` is a HOST array; each entry
+ * carries the arguments and outputs of one ag_bake call.  Results are those
+ * of n_assets separate ag_bake calls.
+ */
+AG_API ag_status ag_bake_batch(int32_t n_assets, const ag_asset_desc *descs, const ag_opts *opts,
+                               ag_stream_t stream);
+
+/*
+ * Captured batch: ag_batch_plan_create validates `descs`, allocates all
+ * scratch once and captures the batched bake into a CUDA graph (it
+ * synchronises `stream` once).  ag_batch_plan_launch replays the graph on
+ * `stream` (inputs are re-read on every launch, so they may change between
+ * launches as long as pointers and sizes do not).  ag_batch_plan_free
+ * synchronises the device and releases everything.
+ */
+AG_API ag_status ag_batch_plan_create(int32_t n_assets, const ag_asset_desc *descs,
+                                      const ag_opts *opts, ag_stream_t stream,
+                                      ag_batch_plan_t *out);
+AG_API ag_status ag_batch_plan_launch(ag_batch_plan_t p, ag_stream_t stream);
+AG_API ag_status ag_batch_plan_free(ag_batch_plan_t p);
+
+/*
+ * ag_bake_backward - loss and gradient for cage optimisation (not in the
+ * paper; the adjoint of the bake above).  With M the ray texels that hit,
+ *   L = (1/|M|) sum_M t^2 + lambda (1/|M|) sum_M (1 - n_hit . d)
+ * where d is the texel's interpolated unit normal (the ray direction) and
+ * n_hit the hit's smooth normal, both in world space.  Hits are recomputed
+ * (same traversal as ag_bake); the hit triangle and M are held fixed, so the
+ * result is the derivative of the piecewise-smooth loss.  Low vertex normals
+ * are always the area-weighted ones (their dependence on d_lverts is
+ * differentiated).  d_loss [1] float and/or d_grad [n_lverts*3] float (fully
+ * overwritten) may be NULL; both NULL is an argument error.
+ */
+AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float *d_luv,
+                                  const int32_t *d_lfaces, int64_t n_lverts, int64_t n_lfaces,
+                                  int32_t W, int32_t H, float max_dist, float lambda,
+                                  const ag_opts *opts, ag_stream_t stream, float *d_loss,
+                                  float *d_grad);
+
+/* Synchronise `stream`, then return and clear the device status word
+ * (AG_ERR_TRAVERSAL_LIMIT if any ray since the last call hit a limit, or
+ * AG_ERR_INVALID_ARG for out-of-range face indices seen by ag_bvh_build), or
+ * AG_ERR_CUDA if the stream reported an error. */
+AG_API ag_status ag_sync_status(ag_stream_t stream);
+
+/* Message for the last failing call on this thread ("" if none). */
+AG_API const char *ag_last_error(void);
+/* Static name of a status code. */
+AG_API const char *ag_status_string(ag_status s);
+/* ABI version: major*10000 + minor*100 + patch. */
+AG_API int32_t ag_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AG_H */

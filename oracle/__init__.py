@@ -239,7 +239,8 @@ def bake(high_v, high_f, low_v, low_f, low_uv, W, H, max_dist, gutter=2, *,
     out["nts"] = nts.reshape(H, W, 3)
     out["disp"] = disp.reshape(H, W)
     out["rgba8"] = encode(nts, filled).reshape(H, W, 4)
-    out["disp16"] = disp.astype(np.float16).reshape(H, W)
+    # binary16 is decided in the kernel's precision: FP64 -> FP32 -> FP16 (RNE)
+    out["disp16"] = disp.astype(np.float32).astype(np.float16).reshape(H, W)
     return out
 
 

@@ -599,17 +599,27 @@ int or_trace(const float *hv, int64_t nhv, const int32_t *hf, int64_t nhf, const
 }
 
 /* ------------------------------------------------- 6. encode + dilation
- * "encoded as RGB8" (Sec. 6.4), reading: q = floor(clamp(c/2 + 1/2, 0, 1)*255 + 1/2);
- * A = 255 on ray and dilated texels, else 0; untouched texels encode (0,0,1).
+ * "encoded as RGB8" (Sec. 6.4), reading: q = 128 + round_half_away(127*c)
+ * for c clamped to [-1, 1] (codes 1..255, 128 = 0).  The unsigned mapping
+ * floor((c/2 + 1/2)*255 + 1/2) would put the 127/128 code boundary exactly at
+ * c = 0, the value every texel takes where the high surface runs parallel to
+ * the low one, leaving that code to rounding noise; here 0 sits in the middle
+ * of code 128.  A = 255 on ray and dilated texels, else 0; untouched texels
+ * encode (0,0,1) = (128,128,255).
  * "dilated at UV seam boundaries" (Sec. 6.4), reading: `gutter` passes; each
  * pass gives every unfilled texel with at least one filled 8-neighbour (as of
  * the previous pass) the renormalised mean of those neighbours' tangent-space
  * normals and the mean of their displacements.  The hit mask is not dilated. */
+/* The 8-bit code is an integer decided by floating point, so it is taken in
+ * the precision of the GPU kernel it is compared with: the FP64 value is
+ * rounded to FP32 and every step below is one FP32 rounding. */
 static uint8_t enc(double c) {
-    double v = 0.5 * c + 0.5;
-    if (v < 0) v = 0;
-    if (v > 1) v = 1;
-    return (uint8_t)floor(v * 255.0 + 0.5);
+    float v = (float)c;
+    if (v < -1.0f) v = -1.0f;
+    if (v > 1.0f) v = 1.0f;
+    float r = v * 127.0f;
+    float q = r >= 0.0f ? floorf(r + 0.5f) : -floorf(-r + 0.5f);
+    return (uint8_t)(128 + (int)q);
 }
 
 void or_encode(const double *nts, const uint8_t *filled, int64_t n, uint8_t *rgba) {

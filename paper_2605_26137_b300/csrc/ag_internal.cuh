@@ -1,0 +1,206 @@
+// Internal declarations of the B300 normal baker (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "ag.h"
+
+// ------------------------------------------------------------------ status
+// Bits of the per-device status word written by kernels (atomicOr).
+enum : unsigned {
+    AGS_STEP_CAP = 1u,      // a ray exceeded ag_opts.max_steps
+    AGS_STACK = 2u,         // a traversal stack overflowed
+    AGS_BAD_FACE = 4u,      // a face index was out of range (build)
+    AGS_BAD_UV = 8u,        // a UV was NaN or outside [-1, 2] (bake; face dropped)
+};
+
+namespace ag {
+
+// ------------------------------------------------------------------ host error plumbing
+ag_status set_error(ag_status s, const char *fmt, ...);
+ag_status cuda_error(cudaError_t e, const char *what);
+#define AG_CUDA(call)                                              \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return ag::cuda_error(e_, #call);   \
+    } while (0)
+#define AG_CUDA_LAUNCH(what)                                       \
+    do {                                                           \
+        cudaError_t e_ = cudaGetLastError();                       \
+        if (e_ != cudaSuccess) return ag::cuda_error(e_, what);    \
+    } while (0)
+
+unsigned *device_status_word(int device);      // 1 word per device, zero-initialised
+cudaMemPool_t device_pool(int device);         // library-private stream-ordered pool
+int device_sm_count(int device);
+
+// stream-ordered scratch from the private pool
+struct Scratch {
+    cudaStream_t stream;
+    int device;
+    void *ptrs[32];
+    int n = 0;
+    explicit Scratch(cudaStream_t s, int dev) : stream(s), device(dev) {}
+    cudaError_t alloc(void **p, size_t bytes);
+    ~Scratch();
+};
+
+// ------------------------------------------------------------------ BVH layouts
+// 80-byte node: origin, per-axis power-of-two scale, and 8 child boxes as
+// 8-bit offsets on that grid, rounded outward at build time so the decoded
+// box always contains the exact FP32 child box.
+struct __align__(16) QNode {
+    float ox, oy, oz;
+    uint8_t ex, ey, ez, nchild;   // scale = 2^(e-127) (float exponent bits)
+    uint32_t child_base;          // index of the first internal child
+    uint32_t tri_base;            // first triangle record of the leaf children
+    uint8_t meta[8];              // per child slot, see meta_* below
+    uint8_t qlox[8], qloy[8], qloz[8], qhix[8], qhiy[8], qhiz[8];
+};
+static_assert(sizeof(QNode) == 80, "QNode must be 80 bytes");
+
+// 208-byte node with exact FP32 child boxes (precision-study layout).
+struct __align__(16) FNode {
+    uint32_t child_base, tri_base;
+    uint8_t meta[8];
+    float lox[8], loy[8], loz[8], hix[8], hiy[8], hiz[8];
+};
+static_assert(sizeof(FNode) == 208, "FNode must be 208 bytes");
+
+// meta byte: 0 = empty slot; internal child: 0x80 | rank among internal
+// children (node = child_base + rank); leaf child: (count << 5) | offset,
+// count in 1..3, offset in 0..23 (records tri_base + offset ...).
+__host__ __device__ inline bool meta_internal(uint8_t m) { return (m & 0x80u) != 0; }
+__host__ __device__ inline bool meta_leaf(uint8_t m) { return m != 0 && (m & 0x80u) == 0; }
+__host__ __device__ inline int meta_rank(uint8_t m) { return m & 0x7f; }
+__host__ __device__ inline int meta_count(uint8_t m) { return (m >> 5) & 3; }
+__host__ __device__ inline int meta_offset(uint8_t m) { return m & 31; }
+
+constexpr int LEAF_MAX = 3;
+
+// Triangle record (48 B, leaf order): three float4 (vertex xyz, vertex index
+// bits in .w).  The original triangle id is kept in a parallel array.
+
+// traversal stack entry reference: bit31 leaf flag; leaf: bits 29..30 =
+// count-1, bits 0..28 = first record; internal: node index.
+__host__ __device__ inline uint32_t ref_leaf(uint32_t first, int count) {
+    return 0x80000000u | ((uint32_t)(count - 1) << 29) | first;
+}
+__host__ __device__ inline bool ref_is_leaf(uint32_t r) { return (r & 0x80000000u) != 0; }
+__host__ __device__ inline uint32_t ref_first(uint32_t r) { return r & 0x1fffffffu; }
+__host__ __device__ inline int ref_count(uint32_t r) { return (int)((r >> 29) & 3u) + 1; }
+
+}  // namespace ag
+
+struct ag_bvh {
+    uint64_t magic;
+    int device;
+    int layout;
+    int64_t n_tris, n_verts, n_nodes;
+    void *nodes;           // QNode[] or FNode[]
+    float4 *tris;          // [n_tris*3]
+    int32_t *tri_ids;      // [n_tris]
+    float4 *vnormals;      // [n_verts] (xyz unit, w = 0)
+    float lo[3], hi[3];
+    float diam;
+    int max_depth;
+    float build_ms;
+};
+constexpr uint64_t AG_BVH_MAGIC = 0x4147425648414e44ull;
+
+namespace ag {
+
+// ------------------------------------------------------------------ per-asset bake job
+// Everything the trace needs for one asset (device-resident table).
+struct TraceJob {
+    const void *nodes;
+    const float4 *tris;
+    const int32_t *tri_ids;
+    const float4 *hnormals;
+    const float4 *lpos;     // [V] low positions (w unused)
+    const float4 *lnrm;     // [V] low unit vertex normals
+    const int4 *lface;      // [F] (i0, i1, i2, flags)
+    const float4 *ltan;     // [F*3] per-corner unit tangent, w = handedness
+    const int4 *rays;       // this asset's rays: (texel, face, b1 bits, b2 bits)
+    float4 *ntsd;           // [H*W] out: tangent-space normal xyz, displacement w
+    uint8_t *mask;          // [H*W] out
+    int32_t *hit_tri;       // [H*W] optional
+    float *hit_t;           // [H*W] optional
+    float *g_pos;           // backward: [V*3] unscaled dL/dV via p
+    float *g_nrm;           // backward: [V*3] unscaled dL/dn_i
+    float *loss_acc;        // backward: [4] sum t^2, sum (1 - n.d), hit count, pad
+    long long ray_begin;    // first ray of this asset in the global ray list
+    int W, H;
+    float max_dist;
+    float lambda;
+};
+
+constexpr int FACE_DEGEN = 1;   // lface.w bit: unreliable UVs -> (0,0,1)
+constexpr int FACE_INVALID = 2; // lface.w bit: dropped (bad UV)
+
+// ------------------------------------------------------------------ launch helpers (defined per .cu)
+// area-weighted vertex normals (deterministic, exact edge differences);
+// `given` replaces the derived normals (normalised), acc_out [3nv] receives
+// the unnormalised sums, pos [nv] (optional) the positions as float4
+size_t vertex_normal_scratch_bytes(int64_t nv, int64_t nf);
+cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, int64_t nf,
+                                  const float *given, float *acc_out, float4 *nrm, float4 *pos,
+                                  void *scratch, cudaStream_t s);
+cudaError_t launch_face_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W,
+                              int H, const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan,
+                              int4 *uvfix, unsigned *status, cudaStream_t s);
+cudaError_t launch_raster(const int4 *uvfix, const int4 *lface, int64_t nf, int W, int H,
+                          unsigned long long *keys, cudaStream_t s);
+cudaError_t launch_resolve(const unsigned long long *keys, const int4 *uvfix, int W, int H,
+                           int32_t *face_map, float *aux_bary, int4 *rays, long long *n_rays,
+                           cudaStream_t s);
+
+struct TraceLaunch {
+    TraceJob job0;              // the job of a single-asset launch (n_jobs == 1)
+    const TraceJob *jobs;       // device table (n_jobs > 1)
+    const long long *job_begin; // device [n_jobs+1] exclusive ray offsets (n_jobs > 1)
+    int n_jobs;
+    const long long *n_rays_dev; // device total ray count
+    unsigned long long *ray_counter;
+    unsigned *status;
+    int max_steps;
+    unsigned long long *counters;  // non-NULL -> counting build
+    int layout;
+    int schedule;
+    int block_size, blocks_per_sm;
+    bool backward;
+};
+cudaError_t launch_trace(const TraceLaunch &L, cudaStream_t s);
+
+cudaError_t launch_finalize(const float4 *ntsd, const int32_t *face_map, int W, int H, int gutter,
+                            int disp_fp16, uint8_t *rgba, uint8_t *mask, void *disp,
+                            float *aux_nts, float *aux_disp, int32_t *aux_hit_tri, float *aux_hit_t,
+                            cudaStream_t s);
+
+cudaError_t launch_backward_finish(const float4 *lpos, const int4 *lface, int64_t nv, int64_t nf,
+                                   const float *acc_nrm /*[V*3] unnormalised normal sums*/,
+                                   float *g_pos, const float *g_nrm, float *g_a,
+                                   const float *loss_acc, float lambda, float *d_loss,
+                                   float *d_grad, cudaStream_t s);
+
+}  // namespace ag
+
+// ------------------------------------------------------------------ device math
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return make_float3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float s) { return make_float3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize3(float3 a) {
+    float l2 = dot3(a, a);
+    return l2 > 0.f ? a * (1.0f / sqrtf(l2)) : a;
+}

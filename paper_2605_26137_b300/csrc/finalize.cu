@@ -1,0 +1,180 @@
+// Output stage (Sec. 6.4: "encoded as RGB8, and dilated at UV seam
+// boundaries"): `gutter` Jacobi dilation passes run in shared memory on a
+// 32x8 output tile with a halo of `gutter` texels, then every texel of the
+// tile is encoded (RGBA8, binary16/float32 displacement) in the same pass.
+// Also the final reductions of the backward pass.
+#include "ag_internal.cuh"
+
+#include <algorithm>
+
+namespace ag {
+namespace {
+
+constexpr int TW = 32, TH = 8, MAXG = 8;
+constexpr int SW = TW + 2 * MAXG, SH = TH + 2 * MAXG;
+
+// RGB8 code of c in [-1,1]: 128 + round_half_away(127 c) (codes 1..255,
+// 128 = 0, so the frequent value c = 0 is in the middle of a code rather than
+// on a code boundary); every step one FP32 rounding (no contraction).
+__device__ __forceinline__ unsigned enc8(float c) {
+    float v = fminf(fmaxf(c, -1.f), 1.f);
+    float r = __fmul_rn(v, 127.f);
+    float q = r >= 0.f ? floorf(__fadd_rn(r, 0.5f)) : -floorf(__fadd_rn(-r, 0.5f));
+    return (unsigned)(128 + (int)q);
+}
+
+__global__ void __launch_bounds__(256) k_finalize(const float4 *__restrict__ ntsd, const int32_t *__restrict__ face_map,
+                                                  int W, int H, int g, int disp_fp16, uchar4 *__restrict__ rgba,
+                                                  uint8_t *__restrict__ mask, void *__restrict__ disp,
+                                                  float *__restrict__ aux_nts, float *__restrict__ aux_disp,
+                                                  int32_t *__restrict__ aux_hit_tri, float *__restrict__ aux_hit_t) {
+    __shared__ float4 sv[2][SH][SW];
+    __shared__ uint8_t sf[2][SH][SW];   // 0 empty, 1 ray texel, 2 dilated, 3 outside the image
+    const int bw = TW + 2 * g, bh = TH + 2 * g;
+    const int x0 = blockIdx.x * TW - g, y0 = blockIdx.y * TH - g;
+    for (int i = threadIdx.x; i < bw * bh; i += blockDim.x) {
+        int lx = i % bw, ly = i / bw;
+        int x = x0 + lx, y = y0 + ly;
+        float4 v = make_float4(0.f, 0.f, 1.f, 0.f);
+        uint8_t f = 3;
+        if (x >= 0 && y >= 0 && x < W && y < H) {
+            size_t t = (size_t)y * W + x;
+            f = face_map[t] >= 0 ? 1 : 0;
+            if (f) v = ntsd[t];
+        }
+        sv[0][ly][lx] = v;
+        sf[0][ly][lx] = f;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (int p = 0; p < g; ++p) {
+        for (int i = threadIdx.x; i < bw * bh; i += blockDim.x) {
+            int lx = i % bw, ly = i / bw;
+            float4 v = sv[cur][ly][lx];
+            uint8_t f = sf[cur][ly][lx];
+            if (f == 0 && lx > 0 && ly > 0 && lx < bw - 1 && ly < bh - 1) {
+                float sx = 0.f, sy = 0.f, sz = 0.f, sd = 0.f;
+                int cnt = 0;
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        if (dx == 0 && dy == 0) continue;
+                        uint8_t nf = sf[cur][ly + dy][lx + dx];
+                        if (nf == 1 || nf == 2) {
+                            float4 nv = sv[cur][ly + dy][lx + dx];
+                            sx += nv.x; sy += nv.y; sz += nv.z; sd += nv.w;
+                            ++cnt;
+                        }
+                    }
+                if (cnt) {
+                    float inv = 1.0f / (float)cnt;
+                    float3 m = make_float3(sx * inv, sy * inv, sz * inv);
+                    float l2 = dot3(m, m);
+                    float3 n = l2 > 0.f ? m * (1.0f / sqrtf(l2)) : make_float3(0.f, 0.f, 1.f);
+                    v = make_float4(n.x, n.y, n.z, sd * inv);
+                    f = 2;
+                }
+            }
+            sv[cur ^ 1][ly][lx] = v;
+            sf[cur ^ 1][ly][lx] = f;
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    int lx = g + (threadIdx.x % TW), ly = g + (threadIdx.x / TW);
+    int x = blockIdx.x * TW + (threadIdx.x % TW), y = blockIdx.y * TH + (threadIdx.x / TW);
+    if (x >= W || y >= H) return;
+    size_t t = (size_t)y * W + x;
+    float4 v = sv[cur][ly][lx];
+    uint8_t f = sf[cur][ly][lx];
+    bool filled = f == 1 || f == 2;
+    if (!filled) v = make_float4(0.f, 0.f, 1.f, 0.f);
+    rgba[t] = make_uchar4((unsigned char)enc8(v.x), (unsigned char)enc8(v.y), (unsigned char)enc8(v.z),
+                          filled ? 255 : 0);
+    if (disp_fp16) ((__half *)disp)[t] = __float2half_rn(v.w);
+    else ((float *)disp)[t] = v.w;
+    if (f != 1) {
+        mask[t] = 0;
+        if (aux_hit_tri) aux_hit_tri[t] = -1;
+        if (aux_hit_t) aux_hit_t[t] = 0.f;
+    }
+    if (aux_nts) {
+        aux_nts[3 * t] = v.x;
+        aux_nts[3 * t + 1] = v.y;
+        aux_nts[3 * t + 2] = v.z;
+    }
+    if (aux_disp) aux_disp[t] = v.w;
+}
+
+// dL/da_i = (I - n n^T) g_n / |a_i| (a_i: unnormalised area-weighted normal sum)
+__global__ void k_bwd_vertex(const float *__restrict__ acc, const float *__restrict__ g_nrm, int64_t nv,
+                             float *__restrict__ g_a) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    float3 a = make_float3(acc[3 * i], acc[3 * i + 1], acc[3 * i + 2]);
+    float al = sqrtf(dot3(a, a));
+    float3 r = make_float3(0.f, 0.f, 0.f);
+    if (al > 0.f) {
+        float3 n = a * (1.0f / al);
+        float3 g = make_float3(g_nrm[3 * i], g_nrm[3 * i + 1], g_nrm[3 * i + 2]);
+        r = (g - n * dot3(n, g)) * (1.0f / al);
+    }
+    g_a[3 * i] = r.x;
+    g_a[3 * i + 1] = r.y;
+    g_a[3 * i + 2] = r.z;
+}
+
+// a_i = sum over faces of (v1 - v0) x (v2 - v0): scatter the face cross-product adjoint
+__global__ void k_bwd_face(const float4 *__restrict__ lpos, const int4 *__restrict__ lface, int64_t nf,
+                           const float *__restrict__ g_a, float *__restrict__ g_pos) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int4 fi = lface[f];
+    if (fi.w & FACE_INVALID) return;
+    int id[3] = {fi.x, fi.y, fi.z};
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    for (int k = 0; k < 3; ++k) g = g + make_float3(g_a[3 * id[k]], g_a[3 * id[k] + 1], g_a[3 * id[k] + 2]);
+    float3 p0 = f3(lpos[id[0]]), p1 = f3(lpos[id[1]]), p2 = f3(lpos[id[2]]);
+    float3 e1 = p1 - p0, e2 = p2 - p0;
+    float3 g1 = cross3(e2, g), g2 = cross3(g, e1);
+    atomicAdd(&g_pos[3 * id[1]], g1.x); atomicAdd(&g_pos[3 * id[1] + 1], g1.y); atomicAdd(&g_pos[3 * id[1] + 2], g1.z);
+    atomicAdd(&g_pos[3 * id[2]], g2.x); atomicAdd(&g_pos[3 * id[2] + 1], g2.y); atomicAdd(&g_pos[3 * id[2] + 2], g2.z);
+    atomicAdd(&g_pos[3 * id[0]], -(g1.x + g2.x));
+    atomicAdd(&g_pos[3 * id[0] + 1], -(g1.y + g2.y));
+    atomicAdd(&g_pos[3 * id[0] + 2], -(g1.z + g2.z));
+}
+
+__global__ void k_bwd_scale(const float *__restrict__ g_pos, int64_t n3, const float *__restrict__ loss_acc,
+                            float lambda, float *__restrict__ d_loss, float *__restrict__ d_grad) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float cnt = loss_acc[2];
+    float inv = cnt > 0.f ? 1.0f / cnt : 0.f;
+    if (d_grad && i < n3) d_grad[i] = g_pos[i] * inv;
+    if (d_loss && i == 0) d_loss[0] = (loss_acc[0] + lambda * loss_acc[1]) * inv;
+}
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+cudaError_t launch_finalize(const float4 *ntsd, const int32_t *face_map, int W, int H, int gutter, int disp_fp16,
+                            uint8_t *rgba, uint8_t *mask, void *disp, float *aux_nts, float *aux_disp,
+                            int32_t *aux_hit_tri, float *aux_hit_t, cudaStream_t s) {
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH);
+    k_finalize<<<grid, TW * TH, 0, s>>>(ntsd, face_map, W, H, gutter, disp_fp16, (uchar4 *)rgba, mask, disp, aux_nts,
+                                         aux_disp, aux_hit_tri, aux_hit_t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward_finish(const float4 *lpos, const int4 *lface, int64_t nv, int64_t nf, const float *acc_nrm,
+                                   float *g_pos, const float *g_nrm, float *g_a, const float *loss_acc, float lambda,
+                                   float *d_loss, float *d_grad, cudaStream_t s) {
+    if (d_grad) {
+        k_bwd_vertex<<<grid_for(nv, 256), 256, 0, s>>>(acc_nrm, g_nrm, nv, g_a);
+        k_bwd_face<<<grid_for(nf, 256), 256, 0, s>>>(lpos, lface, nf, g_a, g_pos);
+    }
+    k_bwd_scale<<<grid_for(std::max<int64_t>(1, 3 * nv), 256), 256, 0, s>>>(g_pos, 3 * nv, loss_acc, lambda, d_loss,
+                                                                           d_grad);
+    return cudaGetLastError();
+}
+
+}  // namespace ag

@@ -1,0 +1,126 @@
+// Area-weighted smooth vertex normals (Sec. 6.4: the G-buffer's "smooth
+// normal" of the low-poly mesh and the high-poly "interpolated smooth
+// normal"), computed deterministically and accurately in FP32:
+//   - each face term (v1 - v0) x (v2 - v0) uses exact edge differences
+//     (TwoSum: hi + lo) and a compensated 2x2 determinant (FMA error term), so
+//     sliver triangles of marching-grid meshes keep a correct direction;
+//   - each vertex sums its incident face terms in face-id order through a
+//     CSR adjacency (degree count, exclusive scan, fill, per-vertex sort), so
+//     the result does not depend on scheduling (no float atomics).
+#include "ag_internal.cuh"
+#include "exact.cuh"
+
+namespace ag {
+
+namespace {
+
+__device__ __forceinline__ float3 ldv(const float *V, int64_t i) {
+    return make_float3(V[3 * i], V[3 * i + 1], V[3 * i + 2]);
+}
+
+__device__ __forceinline__ bool face_ok(const int32_t *F, int64_t f, int64_t nv, int32_t id[3]) {
+    id[0] = F[3 * f]; id[1] = F[3 * f + 1]; id[2] = F[3 * f + 2];
+    return id[0] >= 0 && id[0] < nv && id[1] >= 0 && id[1] < nv && id[2] >= 0 && id[2] < nv;
+}
+
+__global__ void k_degree(const int32_t *__restrict__ F, int64_t nf, int64_t nv, unsigned *__restrict__ deg) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int32_t id[3];
+    if (!face_ok(F, f, nv, id)) return;
+    for (int k = 0; k < 3; ++k) atomicAdd(&deg[id[k]], 1u);
+}
+
+__global__ void k_fill(const int32_t *__restrict__ F, int64_t nf, int64_t nv, const unsigned *__restrict__ off,
+                       unsigned *__restrict__ fill, int32_t *__restrict__ list) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int32_t id[3];
+    if (!face_ok(F, f, nv, id)) return;
+    for (int k = 0; k < 3; ++k) {
+        unsigned slot = atomicAdd(&fill[id[k]], 1u);
+        list[off[id[k]] + slot] = (int32_t)f;
+    }
+}
+
+__global__ void k_gather(const float *__restrict__ V, const int32_t *__restrict__ F, int64_t nv,
+                         const unsigned *__restrict__ off, int32_t *__restrict__ list, const float *__restrict__ given,
+                         float *__restrict__ acc_out, float4 *__restrict__ nrm, float4 *__restrict__ pos) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    float3 s = make_float3(0.f, 0.f, 0.f);
+    if (!given) {
+        unsigned b = off[v], e = off[v + 1];
+        // insertion sort of this vertex's faces by id (degrees are small)
+        for (unsigned i = b + 1; i < e; ++i) {
+            int32_t x = list[i];
+            unsigned j = i;
+            while (j > b && list[j - 1] > x) { list[j] = list[j - 1]; --j; }
+            list[j] = x;
+        }
+        for (unsigned i = b; i < e; ++i) {
+            int64_t f = list[i];
+            float3 c = face_cross(ldv(V, F[3 * f]), ldv(V, F[3 * f + 1]), ldv(V, F[3 * f + 2]));
+            s = make_float3(__fadd_rn(s.x, c.x), __fadd_rn(s.y, c.y), __fadd_rn(s.z, c.z));
+        }
+    } else {
+        s = ldv(given, v);
+    }
+    if (acc_out) {
+        acc_out[3 * v] = s.x;
+        acc_out[3 * v + 1] = s.y;
+        acc_out[3 * v + 2] = s.z;
+    }
+    float3 n = normalize3(s);
+    nrm[v] = make_float4(n.x, n.y, n.z, 0.f);
+    if (pos) {
+        float3 p = ldv(V, v);
+        pos[v] = make_float4(p.x, p.y, p.z, 0.f);
+    }
+}
+
+// single-block exclusive scan of m unsigned values, a[m] receives the total
+__global__ void k_scan_total(unsigned *__restrict__ a, int64_t m) {
+    __shared__ unsigned sums[1024];
+    int t = threadIdx.x, T = blockDim.x;
+    int64_t chunk = (m + T - 1) / T;
+    int64_t b = t * chunk, e = min(m, b + chunk);
+    unsigned s = 0;
+    for (int64_t i = b; i < e; ++i) s += a[i];
+    sums[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        unsigned run = 0;
+        for (int k = 0; k < T; ++k) { unsigned v = sums[k]; sums[k] = run; run += v; }
+        a[m] = run;
+    }
+    __syncthreads();
+    unsigned run = sums[t];
+    for (int64_t i = b; i < e; ++i) { unsigned v = a[i]; a[i] = run; run += v; }
+}
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+size_t vertex_normal_scratch_bytes(int64_t nv, int64_t nf) {
+    return sizeof(unsigned) * (size_t)(2 * nv + 1) + sizeof(int32_t) * (size_t)(3 * nf);
+}
+
+cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, int64_t nf, const float *given,
+                                  float *acc_out, float4 *nrm, float4 *pos, void *scratch, cudaStream_t s) {
+    unsigned *off = static_cast<unsigned *>(scratch);   // [nv+1]
+    unsigned *fill = off + nv + 1;                      // [nv]
+    int32_t *list = reinterpret_cast<int32_t *>(fill + nv);  // [3nf]
+    cudaError_t e;
+    if (!given) {
+        if ((e = cudaMemsetAsync(off, 0, sizeof(unsigned) * (size_t)(2 * nv + 1), s)) != cudaSuccess) return e;
+        k_degree<<<grid_for(nf, 256), 256, 0, s>>>(F, nf, nv, off);
+        k_scan_total<<<1, 1024, 0, s>>>(off, nv);
+        k_fill<<<grid_for(nf, 256), 256, 0, s>>>(F, nf, nv, off, fill, list);
+    }
+    k_gather<<<grid_for(nv, 128), 128, 0, s>>>(V, F, nv, off, list, given, acc_out, nrm, pos);
+    return cudaGetLastError();
+}
+
+}  // namespace ag

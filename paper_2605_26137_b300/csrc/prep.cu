@@ -1,0 +1,308 @@
+// Low-poly side of the bake (Sec. 6.4, first stage: the G-buffer of the
+// low-poly mesh rasterised into its own UV space):
+//   area-weighted vertex normals -> per-face UV snapping, reliability flag and
+//   corner tangent frames -> conservative UV raster (exact fixed-point keys,
+//   atomicMin per texel) -> resolve to (face, barycentrics) and compact the
+//   covered texels into a tile-ordered ray list.
+#include "ag_internal.cuh"
+#include "exact.cuh"
+
+namespace ag {
+namespace {
+
+constexpr unsigned long long KEY_NONE = ~0ull;
+constexpr unsigned long long KEY_CONS = 1ull << 63;
+
+// round_half_away(u * W * 256), exact: the float's 24-bit significand times
+// W*256 fits in 64 bits, and the shift rounds on the exact product.
+__device__ __forceinline__ long long snap_exact(float u, int W) {
+    unsigned bits = __float_as_uint(u);
+    int e = (bits >> 23) & 255;
+    if (e == 0) return 0;                       // zero / subnormal: |u*W*256| < 2^-100
+    unsigned long long man = (bits & 0x7fffffu) | 0x800000u;
+    unsigned long long P = man * (unsigned long long)W * 256ull;
+    int sh = 150 - e;                           // value = P * 2^-sh ; sh >= 22 for |u| <= 2
+    unsigned long long r = sh >= 63 ? 0ull : (P + (1ull << (sh - 1))) >> sh;
+    return (bits >> 31) ? -(long long)r : (long long)r;
+}
+
+__global__ void k_face_setup(const float *__restrict__ uv, const int32_t *__restrict__ F, int64_t nf, int64_t nv,
+                             int W, int H, const float4 *__restrict__ lpos, const float4 *__restrict__ lnrm,
+                             int4 *__restrict__ lface, float4 *__restrict__ ltan, int4 *__restrict__ uvfix,
+                             unsigned *__restrict__ status) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int32_t id[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+    float u[3], v[3];
+    bool bad = false;
+    for (int k = 0; k < 3; ++k) {
+        u[k] = uv[6 * f + 2 * k];
+        v[k] = uv[6 * f + 2 * k + 1];
+        if (!(u[k] >= -1.f && u[k] <= 2.f && v[k] >= -1.f && v[k] <= 2.f)) bad = true;
+        if (id[k] < 0 || id[k] >= nv) bad = true;
+    }
+    if (bad) {
+        atomicOr(status, AGS_BAD_UV);
+        lface[f] = make_int4(0, 0, 0, FACE_INVALID);
+        uvfix[2 * f] = make_int4(0, 0, 0, 0);
+        uvfix[2 * f + 1] = make_int4(0, 0, 0, 0);
+        for (int k = 0; k < 3; ++k) ltan[3 * f + k] = make_float4(1.f, 0.f, 0.f, 1.f);
+        return;
+    }
+    long long X[3], Y[3];
+    for (int k = 0; k < 3; ++k) {
+        X[k] = snap_exact(u[k], W);
+        Y[k] = snap_exact(v[k], H);
+    }
+    long long a2 = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+    int flags = (a2 <= 13 && a2 >= -13) ? FACE_DEGEN : 0;
+    float3 p0 = f3(lpos[id[0]]), p1 = f3(lpos[id[1]]), p2 = f3(lpos[id[2]]);
+    float3 l1, l2;
+    float3 h1 = exact_edge_hi(p1, p0, l1), h2 = exact_edge_hi(p2, p0, l2);
+    float du1 = (float)(X[1] - X[0]), dv1 = (float)(Y[1] - Y[0]);
+    float du2 = (float)(X[2] - X[0]), dv2 = (float)(Y[2] - Y[0]);
+    float sg = a2 < 0 ? -1.f : 1.f;
+    // dp/du and dp/dv of the affine UV map, up to the positive factor 1/|a2|
+    // (snapped UV deltas are exact integers; edges are exact hi + lo pairs)
+    float3 Tf = lincomb_edges(dv2, h1, l1, dv1, h2, l2) * sg;
+    float3 Bf = lincomb_edges(du1, h2, l2, du2, h1, l1) * sg;
+    float3 T[3];
+    for (int k = 0; k < 3; ++k) {
+        float3 n = f3(lnrm[id[k]]);
+        float3 t = Tf - n * dot3(Tf, n);
+        if (!flags && dot3(t, t) > 0.f) {
+            T[k] = normalize3(t);
+        } else {
+            flags |= FACE_DEGEN;
+            // Duff et al. 2017 orthonormal basis, FP64 (bookkeeping only:
+            // unreliable texels output (0,0,1))
+            double nx = n.x, ny = n.y, nz = n.z;
+            double s = nz >= 0.0 ? 1.0 : -1.0;
+            double a = -1.0 / (s + nz);
+            double b = nx * ny * a;
+            double tx = 1.0 + s * nx * nx * a, ty = s * b, tz = -s * nx;
+            double l = sqrt(tx * tx + ty * ty + tz * tz);
+            T[k] = make_float3((float)(tx / l), (float)(ty / l), (float)(tz / l));
+        }
+    }
+    float hs = dot3(cross3(f3(lnrm[id[0]]), Tf), Bf);
+    float w = hs < 0.f ? -1.f : 1.f;
+    for (int k = 0; k < 3; ++k) ltan[3 * f + k] = make_float4(T[k].x, T[k].y, T[k].z, w);
+    lface[f] = make_int4(id[0], id[1], id[2], flags);
+    uvfix[2 * f] = make_int4((int)X[0], (int)Y[0], (int)X[1], (int)Y[1]);
+    uvfix[2 * f + 1] = make_int4((int)X[2], (int)Y[2], (int)(unsigned)(a2 & 0xffffffffll), (int)(a2 >> 32));
+}
+
+struct UvTri {
+    long long X[3], Y[3], a2;
+};
+
+__device__ __forceinline__ UvTri load_uvtri(const int4 *uvfix, int64_t f) {
+    int4 a = uvfix[2 * f], b = uvfix[2 * f + 1];
+    UvTri t;
+    t.X[0] = a.x; t.Y[0] = a.y; t.X[1] = a.z; t.Y[1] = a.w; t.X[2] = b.x; t.Y[2] = b.y;
+    t.a2 = (long long)(((unsigned long long)(unsigned)b.w << 32) | (unsigned long long)(unsigned)b.z);
+    return t;
+}
+
+__device__ __forceinline__ long long orient2(long long ax, long long ay, long long bx, long long by, long long cx,
+                                             long long cy) {
+    return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+}
+
+__device__ __forceinline__ bool uv_inside(const UvTri &t, long long cx, long long cy, long long e[3]) {
+    e[0] = orient2(t.X[1], t.Y[1], t.X[2], t.Y[2], cx, cy);
+    e[1] = orient2(t.X[2], t.Y[2], t.X[0], t.Y[0], cx, cy);
+    e[2] = orient2(t.X[0], t.Y[0], t.X[1], t.Y[1], cx, cy);
+    if (t.a2 > 0) return e[0] >= 0 && e[1] >= 0 && e[2] >= 0;
+    return e[0] <= 0 && e[1] <= 0 && e[2] <= 0;
+}
+
+// open interiors of the triangle and the texel square [sx,sx+256]x[sy,sy+256]
+// intersect iff no separating axis among the square's and the triangle's edge normals
+__device__ bool uv_overlap(const UvTri &t, long long sx, long long sy) {
+    long long mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
+    long long mny = min(t.Y[0], min(t.Y[1], t.Y[2])), mxy = max(t.Y[0], max(t.Y[1], t.Y[2]));
+    if (mxx <= sx || mnx >= sx + 256 || mxy <= sy || mny >= sy + 256) return false;
+    for (int k = 0; k < 3; ++k) {
+        int a = k, b = (k + 1) % 3, c = (k + 2) % 3;
+        long long nx = -(t.Y[b] - t.Y[a]), ny = t.X[b] - t.X[a];
+        long long pe = nx * t.X[a] + ny * t.Y[a];
+        long long po = nx * t.X[c] + ny * t.Y[c];
+        long long tmn = min(pe, po), tmx = max(pe, po);
+        long long p0 = nx * sx + ny * sy, p1 = nx * (sx + 256) + ny * sy;
+        long long p2 = nx * sx + ny * (sy + 256), p3 = nx * (sx + 256) + ny * (sy + 256);
+        long long smn = min(min(p0, p1), min(p2, p3)), smx = max(max(p0, p1), max(p2, p3));
+        if (smx <= tmn || smn >= tmx) return false;
+    }
+    return true;
+}
+
+// floor(d^2 * 65536) for the distance from (cx,cy) to edge k (snapped units),
+// ~0 when farther than one texel; *param = closest point's edge parameter.
+__device__ unsigned long long edge_qdist(const UvTri &t, int k, long long cx, long long cy, float *param) {
+    int a = k, b = (k + 1) % 3;
+    long long wx = cx - t.X[a], wy = cy - t.Y[a];
+    long long dx = t.X[b] - t.X[a], dy = t.Y[b] - t.Y[a];
+    long long wd = wx * dx + wy * dy, dd = dx * dx + dy * dy;
+    unsigned __int128 num, den;
+    if (dd == 0 || wd <= 0) {
+        num = (unsigned __int128)(unsigned long long)(wx * wx + wy * wy);
+        den = 1;
+        *param = 0.f;
+    } else if (wd >= dd) {
+        long long ux = cx - t.X[b], uy = cy - t.Y[b];
+        num = (unsigned __int128)(unsigned long long)(ux * ux + uy * uy);
+        den = 1;
+        *param = 1.f;
+    } else {
+        long long cr = wx * dy - wy * dx;
+        unsigned long long ac = (unsigned long long)(cr < 0 ? -cr : cr);
+        num = (unsigned __int128)ac * ac;
+        den = (unsigned __int128)(unsigned long long)dd;
+        *param = (float)wd / (float)dd;
+    }
+    if (num > den * 65536u) return KEY_NONE;
+    return (unsigned long long)((num * 65536u) / den);
+}
+
+__device__ unsigned long long tri_qdist(const UvTri &t, long long cx, long long cy, int *be, float *bp) {
+    unsigned long long best = KEY_NONE;
+    *be = -1;
+    *bp = 0.f;
+    for (int k = 0; k < 3; ++k) {
+        float p;
+        unsigned long long q = edge_qdist(t, k, cx, cy, &p);
+        if (q < best) { best = q; *be = k; *bp = p; }
+    }
+    return best;
+}
+
+__device__ __forceinline__ long long floordiv256(long long a) { return a >= 0 ? a / 256 : -((-a + 255) / 256); }
+
+// one warp per face: every texel within one texel of the face's UV bbox
+__global__ void k_raster(const int4 *__restrict__ uvfix, const int4 *__restrict__ lface, int64_t nf, int W, int H,
+                         unsigned long long *__restrict__ keys) {
+    int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (f >= nf) return;
+    if (lface[f].w & FACE_INVALID) return;
+    UvTri t = load_uvtri(uvfix, f);
+    if (t.a2 == 0) return;
+    long long mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
+    long long mny = min(t.Y[0], min(t.Y[1], t.Y[2])), mxy = max(t.Y[0], max(t.Y[1], t.Y[2]));
+    long long x0 = max(0ll, floordiv256(mnx) - 1), x1 = min((long long)W - 1, floordiv256(mxx) + 1);
+    long long y0 = max(0ll, floordiv256(mny) - 1), y1 = min((long long)H - 1, floordiv256(mxy) + 1);
+    if (x0 > x1 || y0 > y1) return;
+    long long nx = x1 - x0 + 1, cnt = nx * (y1 - y0 + 1);
+    for (long long idx = lane; idx < cnt; idx += 32) {
+        long long x = x0 + idx % nx, y = y0 + idx / nx;
+        long long cx = 256 * x + 128, cy = 256 * y + 128, e[3];
+        unsigned long long key = KEY_NONE;
+        if (uv_inside(t, cx, cy, e)) {
+            key = (unsigned long long)f;
+        } else if (uv_overlap(t, 256 * x, 256 * y)) {
+            int be;
+            float bp;
+            unsigned long long q = tri_qdist(t, cx, cy, &be, &bp);
+            if (q != KEY_NONE) key = KEY_CONS | (q << 31) | (unsigned long long)f;
+        }
+        if (key != KEY_NONE) atomicMin(&keys[y * W + x], key);
+    }
+}
+
+// Texels in 8x8-tile order (row-major tiles, row-major inside a tile), so a
+// warp's 32 consecutive rays come from a 8x4 patch of the atlas.
+__global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__restrict__ keys,
+                                                 const int4 *__restrict__ uvfix, int W, int H,
+                                                 int32_t *__restrict__ face_map, float *__restrict__ aux_bary,
+                                                 int4 *__restrict__ rays, long long *__restrict__ n_rays) {
+    __shared__ int s_warp[8];
+    __shared__ long long s_base;
+    int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    long long g = (long long)blockIdx.x * 256 + tid;
+    long long tile = g >> 6;
+    int within = (int)(g & 63);
+    int ntx = (W + 7) >> 3;
+    long long tx = tile % ntx, ty = tile / ntx;
+    long long x = tx * 8 + (within & 7), y = ty * 8 + (within >> 3);
+    bool valid = x < W && y < H;
+    unsigned long long key = valid ? keys[y * W + x] : KEY_NONE;
+    bool has = key != KEY_NONE;
+    int4 rec = make_int4(0, 0, 0, 0);
+    if (has) {
+        int f = (int)(key & 0x7fffffffull);
+        UvTri t = load_uvtri(uvfix, f);
+        long long cx = 256 * x + 128, cy = 256 * y + 128;
+        float b[3];
+        if (!(key & KEY_CONS)) {
+            long long e[3];
+            uv_inside(t, cx, cy, e);
+            float inv = 1.0f / (float)t.a2;
+            b[1] = (float)e[1] * inv;
+            b[2] = (float)e[2] * inv;
+        } else {
+            int be;
+            float bp;
+            tri_qdist(t, cx, cy, &be, &bp);
+            float bb[3] = {0.f, 0.f, 0.f};
+            bb[be] = 1.f - bp;
+            bb[(be + 1) % 3] = bp;
+            b[1] = bb[1];
+            b[2] = bb[2];
+        }
+        b[0] = 1.f - b[1] - b[2];
+        rec = make_int4((int)(y * W + x), f, __float_as_int(b[1]), __float_as_int(b[2]));
+        if (aux_bary) {
+            aux_bary[3 * (y * W + x)] = b[0];
+            aux_bary[3 * (y * W + x) + 1] = b[1];
+            aux_bary[3 * (y * W + x) + 2] = b[2];
+        }
+    }
+    if (valid) {
+        face_map[y * W + x] = has ? (int)(key & 0x7fffffffull) : -1;
+        if (aux_bary && !has) {
+            aux_bary[3 * (y * W + x)] = 0.f;
+            aux_bary[3 * (y * W + x) + 1] = 0.f;
+            aux_bary[3 * (y * W + x) + 2] = 0.f;
+        }
+    }
+    unsigned bal = __ballot_sync(0xffffffffu, has);
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int w = 0; w < 8; ++w) { int c = s_warp[w]; s_warp[w] = run; run += c; }
+        s_base = run ? (long long)atomicAdd((unsigned long long *)n_rays, (unsigned long long)run) : 0;
+    }
+    __syncthreads();
+    if (has) rays[s_base + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = rec;
+}
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+cudaError_t launch_face_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W, int H,
+                              const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan, int4 *uvfix,
+                              unsigned *status, cudaStream_t s) {
+    k_face_setup<<<grid_for(nf, 128), 128, 0, s>>>(luv, lfaces, nf, nv, W, H, lpos, lnrm, lface, ltan, uvfix, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster(const int4 *uvfix, const int4 *lface, int64_t nf, int W, int H, unsigned long long *keys,
+                          cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)W * H, s);
+    if (e != cudaSuccess) return e;
+    k_raster<<<grid_for(nf * 32, 256), 256, 0, s>>>(uvfix, lface, nf, W, H, keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resolve(const unsigned long long *keys, const int4 *uvfix, int W, int H, int32_t *face_map,
+                           float *aux_bary, int4 *rays, long long *n_rays, cudaStream_t s) {
+    long long ntiles = (long long)((W + 7) / 8) * ((H + 7) / 8);
+    k_resolve<<<grid_for(ntiles * 64, 256), 256, 0, s>>>(keys, uvfix, W, H, face_map, aux_bary, rays, n_rays);
+    return cudaGetLastError();
+}
+
+}  // namespace ag

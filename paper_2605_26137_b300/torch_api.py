@@ -1,0 +1,289 @@
+"""torch-facing wrappers of the C ABI (device memory and streams from torch;
+every step of the bake runs in libagbake.so's kernels).
+
+All tensors are CUDA tensors on the current device: vertices float32 [n,3],
+faces int32 [m,3], per-corner UVs float32 [m,3,2].  Calls are ordered on the
+current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+from ._lib import AgAssetDesc, AgBakeAux, AgBvhInfo, check, default_opts
+
+_LAYOUTS = {"q8": _lib.AG_BVH_Q8, "f32": _lib.AG_BVH_F32}
+_SCHED = {"auto": _lib.AG_SCHED_AUTO, "thread": _lib.AG_SCHED_THREAD, "warp": _lib.AG_SCHED_WARP}
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _need(t: torch.Tensor, name: str, dtype, shape_tail=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and tuple(t.shape[-len(shape_tail):]) != tuple(shape_tail):
+        raise ValueError(f"{name} must have trailing shape {shape_tail}, got {tuple(t.shape)}")
+    return t
+
+
+def _opts(layout="q8", gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0):
+    return default_opts(bvh_layout=_LAYOUTS[layout], gutter=gutter, disp_fp16=int(bool(disp_fp16)),
+                        schedule=_SCHED[schedule] if isinstance(schedule, str) else schedule,
+                        block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps)
+
+
+class Bvh:
+    """8-wide BVH over a high-poly mesh (owns its device memory)."""
+
+    def __init__(self, verts: torch.Tensor, faces: torch.Tensor, layout: str = "q8", stream=None):
+        lib = _lib.load()
+        _need(verts, "verts", torch.float32, (3,))
+        _need(faces, "faces", torch.int32, (3,))
+        h = ctypes.c_void_p()
+        o = _opts(layout=layout)
+        check(lib.ag_bvh_build(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0],
+                               ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        self.layout = layout
+
+    @property
+    def handle(self) -> int:
+        if not self._h:
+            raise ValueError("BVH has been freed")
+        return self._h.value
+
+    def info(self) -> dict:
+        inf = AgBvhInfo()
+        check(self._lib.ag_bvh_info(self.handle, ctypes.byref(inf)))
+        return {"n_tris": inf.n_tris, "n_verts": inf.n_verts, "n_nodes": inf.n_nodes,
+                "node_bytes": inf.node_bytes, "tri_bytes": inf.tri_bytes, "normal_bytes": inf.normal_bytes,
+                "layout": inf.layout, "node_size": inf.node_size, "max_depth": inf.max_depth,
+                "scene_lo": list(inf.scene_lo), "scene_hi": list(inf.scene_hi), "diam": inf.diam,
+                "build_ms": inf.build_ms}
+
+    def copy_out(self):
+        """Host copies (numpy) of nodes (raw bytes), leaf-order triangle records
+        [n,3,4] float32 (xyz + vertex index bits), original ids, vertex normals."""
+        import numpy as np
+        inf = self.info()
+        nodes = np.empty(inf["node_bytes"], np.uint8)
+        tris = np.empty((inf["n_tris"], 3, 4), np.float32)
+        ids = np.empty(inf["n_tris"], np.int32)
+        vn = np.empty((inf["n_verts"], 4), np.float32)
+        check(self._lib.ag_bvh_copy_out(self.handle, nodes.ctypes.data, tris.ctypes.data, ids.ctypes.data,
+                                        vn.ctypes.data))
+        return nodes, tris, ids, vn
+
+    def free(self) -> None:
+        if self._h:
+            check(self._lib.ag_bvh_free(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                self._lib.ag_bvh_free(self._h)
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+@dataclass
+class BakeOutputs:
+    normal_rgba8: torch.Tensor      # uint8 [H,W,4]
+    mask: torch.Tensor              # uint8 [H,W]
+    disp: torch.Tensor              # float16 or float32 [H,W]
+    normal_ts: torch.Tensor | None = None   # float32 [H,W,3]
+    disp_f32: torch.Tensor | None = None    # float32 [H,W]
+    face: torch.Tensor | None = None        # int32 [H,W]
+    bary: torch.Tensor | None = None        # float32 [H,W,3]
+    hit_tri: torch.Tensor | None = None     # int32 [H,W]
+    hit_t: torch.Tensor | None = None       # float32 [H,W]
+    counters: torch.Tensor | None = None    # int64 [4]: rays, node visits, triangle tests, hits
+    n_rays: torch.Tensor | None = None      # int32 [1]
+
+
+def _check_low(low_verts, low_faces, low_uv, low_normals):
+    _need(low_verts, "low_verts", torch.float32, (3,))
+    _need(low_faces, "low_faces", torch.int32, (3,))
+    _need(low_uv, "low_uv", torch.float32, (3, 2))
+    if low_uv.shape[0] != low_faces.shape[0]:
+        raise ValueError("low_uv must have one [3,2] entry per face")
+    if low_normals is not None:
+        _need(low_normals, "low_normals", torch.float32, (3,))
+        if low_normals.shape[0] != low_verts.shape[0]:
+            raise ValueError("low_normals must match low_verts")
+
+
+def alloc_outputs(W: int, H: int, device, disp_fp16=True, aux=False, counters=False) -> BakeOutputs:
+    out = BakeOutputs(torch.empty((H, W, 4), dtype=torch.uint8, device=device),
+                      torch.empty((H, W), dtype=torch.uint8, device=device),
+                      torch.empty((H, W), dtype=torch.float16 if disp_fp16 else torch.float32, device=device))
+    if aux:
+        out.normal_ts = torch.empty((H, W, 3), dtype=torch.float32, device=device)
+        out.disp_f32 = torch.empty((H, W), dtype=torch.float32, device=device)
+        out.face = torch.empty((H, W), dtype=torch.int32, device=device)
+        out.bary = torch.empty((H, W, 3), dtype=torch.float32, device=device)
+        out.hit_tri = torch.empty((H, W), dtype=torch.int32, device=device)
+        out.hit_t = torch.empty((H, W), dtype=torch.float32, device=device)
+        out.n_rays = torch.empty(1, dtype=torch.int32, device=device)
+    if counters:
+        out.counters = torch.zeros(4, dtype=torch.int64, device=device)
+    return out
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def bake(bvh: Bvh, low_verts, low_faces, low_uv, W: int, H: int, max_dist: float, *, low_normals=None,
+         gutter: int = 2, disp_fp16: bool = True, aux: bool = False, counters: bool = False,
+         out: BakeOutputs | None = None, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
+         stream=None, events=None) -> BakeOutputs:
+    """One bake.  ``aux`` adds float tangent-space normals, raster and hit
+    outputs; ``counters`` selects the counting traversal build; ``events``
+    (4 torch.cuda.Event) are recorded before the raster, before and after the
+    traversal and after the encoding."""
+    lib = _lib.load()
+    _check_low(low_verts, low_faces, low_uv, low_normals)
+    if out is None:
+        out = alloc_outputs(W, H, low_verts.device, disp_fp16, aux, counters)
+    o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
+              blocks_per_sm=blocks_per_sm, max_steps=max_steps)
+    ev = None
+    if events is not None:
+        if len(events) != 4:
+            raise ValueError("events must hold 4 torch.cuda.Event")
+        for e in events:
+            if not e.cuda_event:   # torch creates the CUDA event lazily, on first record
+                e.record()
+        ev = (ctypes.c_void_p * 4)(*[e.cuda_event for e in events])
+    ax = AgBakeAux(_ptr(out.normal_ts), _ptr(out.disp_f32), _ptr(out.face), _ptr(out.bary), _ptr(out.hit_tri),
+                   _ptr(out.hit_t), _ptr(out.counters), _ptr(out.n_rays),
+                   ctypes.cast(ev, ctypes.c_void_p) if ev is not None else None)
+    check(lib.ag_bake(bvh.handle, low_verts.data_ptr(), _ptr(low_normals), low_uv.data_ptr(), low_faces.data_ptr(),
+                      low_verts.shape[0], low_faces.shape[0], W, H, float(max_dist), ctypes.byref(o), _stream(stream),
+                      out.normal_rgba8.data_ptr(), out.mask.data_ptr(), out.disp.data_ptr(), ctypes.byref(ax)))
+    return out
+
+
+def bake_backward(bvh: Bvh, low_verts, low_faces, low_uv, W: int, H: int, max_dist: float, lam: float, *,
+                  want_loss=True, want_grad=True, stream=None, schedule="auto", block_size=0, blocks_per_sm=0):
+    """(loss [1] float32 or None, dL/dV [n,3] float32 or None)."""
+    lib = _lib.load()
+    _check_low(low_verts, low_faces, low_uv, None)
+    loss = torch.empty(1, dtype=torch.float32, device=low_verts.device) if want_loss else None
+    grad = torch.empty_like(low_verts) if want_grad else None
+    o = _opts(schedule=schedule, block_size=block_size, blocks_per_sm=blocks_per_sm)
+    check(lib.ag_bake_backward(bvh.handle, low_verts.data_ptr(), low_uv.data_ptr(), low_faces.data_ptr(),
+                               low_verts.shape[0], low_faces.shape[0], W, H, float(max_dist), float(lam),
+                               ctypes.byref(o), _stream(stream), _ptr(loss), _ptr(grad)))
+    return loss, grad
+
+
+class BakeLoss(torch.autograd.Function):
+    """L(low_verts) = mean_hit(t^2) + lam * mean_hit(1 - n_hit . d).
+    Forward evaluates L with one traversal; backward recomputes the hits and
+    runs the adjoint kernels (ag_bake_backward)."""
+
+    @staticmethod
+    def forward(ctx, low_verts, bvh, low_faces, low_uv, W, H, max_dist, lam):
+        loss, _ = bake_backward(bvh, low_verts.detach().contiguous(), low_faces, low_uv, W, H, max_dist, lam,
+                                want_grad=False)
+        ctx.save_for_backward(low_verts)
+        ctx.args = (bvh, low_faces, low_uv, W, H, max_dist, lam)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (low_verts,) = ctx.saved_tensors
+        bvh, low_faces, low_uv, W, H, max_dist, lam = ctx.args
+        _, grad = bake_backward(bvh, low_verts.detach().contiguous(), low_faces, low_uv, W, H, max_dist, lam,
+                                want_loss=False)
+        return grad * g, None, None, None, None, None, None, None
+
+
+def bake_loss(bvh, low_verts, low_faces, low_uv, W, H, max_dist, lam):
+    return BakeLoss.apply(low_verts, bvh, low_faces, low_uv, W, H, max_dist, lam)
+
+
+@dataclass
+class Asset:
+    bvh: Bvh
+    low_verts: torch.Tensor
+    low_faces: torch.Tensor
+    low_uv: torch.Tensor
+    W: int
+    H: int
+    max_dist: float
+    low_normals: torch.Tensor | None = None
+    out: BakeOutputs | None = None
+
+
+def _descs(assets, disp_fp16):
+    arr = (AgAssetDesc * len(assets))()
+    for i, a in enumerate(assets):
+        _check_low(a.low_verts, a.low_faces, a.low_uv, a.low_normals)
+        if a.out is None:
+            a.out = alloc_outputs(a.W, a.H, a.low_verts.device, disp_fp16)
+        arr[i] = AgAssetDesc(a.bvh.handle, a.low_verts.data_ptr(), _ptr(a.low_normals), a.low_uv.data_ptr(),
+                             a.low_faces.data_ptr(), a.low_verts.shape[0], a.low_faces.shape[0], a.W, a.H,
+                             float(a.max_dist), a.out.normal_rgba8.data_ptr(), a.out.mask.data_ptr(),
+                             a.out.disp.data_ptr())
+    return arr
+
+
+def bake_batch(assets: list[Asset], *, gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0,
+               stream=None):
+    lib = _lib.load()
+    arr = _descs(assets, disp_fp16)
+    o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
+              blocks_per_sm=blocks_per_sm)
+    check(lib.ag_bake_batch(len(assets), arr, ctypes.byref(o), _stream(stream)))
+    return [a.out for a in assets]
+
+
+class BatchPlan:
+    """A batch captured once into a CUDA graph; ``launch`` replays it."""
+
+    def __init__(self, assets: list[Asset], *, gutter=2, disp_fp16=True, schedule="auto", block_size=0,
+                 blocks_per_sm=0, stream=None):
+        self._lib = _lib.load()
+        self.assets = assets
+        arr = _descs(assets, disp_fp16)
+        o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
+                  blocks_per_sm=blocks_per_sm)
+        h = ctypes.c_void_p()
+        check(self._lib.ag_batch_plan_create(len(assets), arr, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        check(self._lib.ag_batch_plan_launch(self._h, _stream(stream)))
+        return [a.out for a in self.assets]
+
+    def free(self):
+        if self._h:
+            check(self._lib.ag_batch_plan_free(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None):
+                self._lib.ag_batch_plan_free(self._h)
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def sync_status(stream=None) -> None:
+    """Synchronise and raise AgError if a device-side limit was hit."""
+    check(_lib.load().ag_sync_status(_stream(stream)))

@@ -1,0 +1,107 @@
+"""GPU-vs-oracle comparison of one bake, with the tolerances the build is
+held to (tangent-space components 1e-4 absolute, displacement 1e-5 of the
+high-mesh bbox diagonal, hit masks equal except where several answers are
+equally correct, 8-bit maps off by at most one code on at most 0.01% of
+texels, exact integer raster).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TOL_NTS = 1e-4
+TOL_DISP_REL = 1e-5
+RGBA_FRAC = 1e-4
+
+
+def to_numpy(out) -> dict:
+    d = {}
+    for k in ("normal_rgba8", "mask", "disp", "normal_ts", "disp_f32", "face", "bary", "hit_tri", "hit_t"):
+        v = getattr(out, k, None)
+        if v is not None:
+            d[k] = v.detach().cpu().numpy()
+    return d
+
+
+def _dilate_ring(m: np.ndarray, r: int) -> np.ndarray:
+    out = m.copy()
+    for _ in range(r):
+        p = np.pad(out, 1)
+        acc = np.zeros_like(out)
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                acc |= p[1 + dy:1 + dy + out.shape[0], 1 + dx:1 + dx + out.shape[1]]
+        out = acc
+    return out
+
+
+def compare(g: dict, o: dict, diam: float, gutter: int = 2, sample=None) -> dict:
+    """Statistics of the comparison; ``check`` asserts them."""
+    H, W = o["face"].shape
+    st = {}
+    st["face_equal"] = bool(np.array_equal(g["face"], o["face"]))
+    ray = o["face"] >= 0
+    if sample is not None:
+        sel = np.zeros(H * W, bool)
+        sel[np.asarray(sample)] = True
+        sel = sel.reshape(H, W) & ray
+    else:
+        sel = ray
+    st["n_ray"] = int(ray.sum())
+    st["n_compared"] = int(sel.sum())
+    st["bary_max"] = float(np.abs(g["bary"][ray] - o["bary"][ray]).max()) if ray.any() else 0.0
+    flags = o["flags"]
+    exc = (flags & 0b1111) != 0
+    gm, om = g["mask"].astype(bool), o["mask"].astype(bool)
+    mism = sel & (gm != om)
+    st["n_except"] = int((sel & exc).sum())
+    st["mask_mismatch"] = int(mism.sum())
+    st["mask_mismatch_unexcused"] = int((mism & ~exc).sum())
+    same = sel & (gm == om) & ((flags & 0b1000) == 0)
+    dn = np.abs(g["normal_ts"] - o["nts"])
+    st["nts_max"] = float(dn[same].max()) if same.any() else 0.0
+    dd = np.abs(g["disp_f32"] - o["disp"])
+    st["disp_max_rel"] = float(dd[same].max() / diam) if same.any() else 0.0
+    ht = g["hit_tri"] == o["hit_tri"]
+    st["hit_tri_equal_frac"] = float(ht[same & om].mean()) if (same & om).any() else 1.0
+    # encoded maps: texels whose value legitimately differs (mask mismatch or
+    # ambiguous closest hit) and, for dilated texels, their neighbourhoods
+    bad = mism | (sel & ((flags & 0b1000) != 0))
+    if sample is None:
+        excl = _dilate_ring(bad, gutter) & ~ray | bad
+        filled = o["filled"] > 0
+        dil = (o["filled"] == 2) & ~excl
+        st["dil_nts_max"] = float(dn[dil].max()) if dil.any() else 0.0
+        st["dil_disp_max_rel"] = float(dd[dil].max() / diam) if dil.any() else 0.0
+        region = ~excl
+        st["alpha_equal"] = bool(np.array_equal(g["normal_rgba8"][..., 3], o["rgba8"][..., 3]))
+        st["filled_equal"] = bool(np.array_equal(g["normal_rgba8"][..., 3] == 255, filled))
+    else:
+        region = sel & ~bad
+    d8 = np.abs(g["normal_rgba8"][..., :3].astype(np.int32) - o["rgba8"][..., :3].astype(np.int32))
+    diff_tex = (d8.max(-1) > 0) & region
+    st["rgba_max"] = int(d8[region].max()) if region.any() else 0
+    st["rgba_diff_texels"] = int(diff_tex.sum())
+    st["rgba_region"] = int(region.sum())
+    st["rgba_diff_frac"] = float(diff_tex.sum() / max(1, region.sum()))
+    g16 = g["disp"].astype(np.float64)
+    o16 = o["disp16"].astype(np.float64)
+    ulp = np.spacing(np.abs(o16).astype(np.float16)).astype(np.float64)
+    dd16 = np.abs(g16 - o16)
+    st["disp16_max_ulps"] = float((dd16[region] / np.maximum(ulp[region], 1e-30)).max()) if region.any() else 0.0
+    return st
+
+
+def check(st: dict, *, rgba_frac=RGBA_FRAC, min_texels_for_frac=20000):
+    assert st["face_equal"], "raster face map differs"
+    assert st["bary_max"] < 2e-6, f"raster barycentrics off by {st['bary_max']}"
+    assert st["mask_mismatch_unexcused"] == 0, f"{st['mask_mismatch_unexcused']} hit-mask mismatches outside the exceptions"
+    assert st["nts_max"] <= TOL_NTS, f"tangent-space normal off by {st['nts_max']}"
+    assert st["disp_max_rel"] <= TOL_DISP_REL, f"displacement off by {st['disp_max_rel']} of diam"
+    if "dil_nts_max" in st:
+        assert st["dil_nts_max"] <= TOL_NTS, f"dilated normal off by {st['dil_nts_max']}"
+        assert st["dil_disp_max_rel"] <= TOL_DISP_REL, f"dilated displacement off by {st['dil_disp_max_rel']}"
+    assert st["rgba_max"] <= 1, f"8-bit map off by {st['rgba_max']} codes"
+    # on small maps 0.01% is below one texel; allow one texel there
+    allowed = max(1, int(rgba_frac * st["rgba_region"])) if st["rgba_region"] < min_texels_for_frac else rgba_frac * st["rgba_region"]
+    assert st["rgba_diff_texels"] <= allowed, f"{st['rgba_diff_texels']} texels off by one code (allowed {allowed})"
+    assert st["disp16_max_ulps"] <= 1.0, f"fp16 displacement off by {st['disp16_max_ulps']} ulp"

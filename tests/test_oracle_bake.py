@@ -133,8 +133,8 @@ def test_unit_length_and_encoding():
     r = oracle.bake_asset(a)
     assert np.abs(np.linalg.norm(r["nts"], axis=-1) - 1).max() < 1e-12
     filled = r["filled"] > 0
-    dec = r["rgba8"][..., :3].astype(np.float64) / 255 * 2 - 1
-    assert np.abs(dec - r["nts"]).max() <= 1.0 / 255 + 1e-12
+    dec = (r["rgba8"][..., :3].astype(np.float64) - 128) / 127
+    assert np.abs(dec - r["nts"]).max() <= 0.5 / 127 + 1e-6
     assert np.all(r["rgba8"][..., 3][filled] == 255) and np.all(r["rgba8"][..., 3][~filled] == 0)
 
 
@@ -142,8 +142,14 @@ def test_encode_exact_values():
     vals = np.array([-1.0, 1.0, 0.0, -2.0, 2.0, 1 / 255, -1 / 255, 0.5])
     nts = np.stack([vals, vals, vals], -1)
     rgba = oracle.encode(nts, np.ones(len(vals), np.uint8))
-    # floor(clamp(c/2+1/2,0,1)*255 + 1/2)
-    assert rgba[:, 0].tolist() == [0, 255, 128, 0, 255, 128, 127, 191]
+    # 128 + round_half_away(127 * clamp(c, -1, 1))
+    assert rgba[:, 0].tolist() == [1, 255, 128, 1, 255, 128, 128, 192]
+    # zero lies in the middle of code 128: noise of either sign keeps the code
+    tiny = np.array([[1e-7, -1e-7, 3e-3], [-3e-3, 0.0, -0.0]])
+    assert oracle.encode(tiny, np.ones(2, np.uint8))[:, :3].tolist() == [[128, 128, 128], [128, 128, 128]]
+    # half-way cases round away from zero
+    half = np.array([[0.5 / 127, -0.5 / 127, 1.5 / 127]])
+    assert oracle.encode(half, np.ones(1, np.uint8))[0, :3].tolist() == [129, 127, 130]
 
 
 def test_tangent_is_dp_du_on_affine_plane():
