@@ -219,6 +219,34 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
                                   const ag_opts *opts, ag_stream_t stream, float *d_loss,
                                   float *d_grad);
 
+/*
+ * ag_vertex_normals_noalloc - area-weighted unit vertex normals of a mesh
+ * (the same normals ag_bvh_build computes for the high-poly mesh), without
+ * allocating anything.  The paper has no counterpart: this call exists for
+ * callers that cannot allocate device memory at the point where they need
+ * normals - code running inside a host application that owns the whole
+ * device-memory budget through its own allocator, a plugin that must not
+ * touch the CUDA allocator, or a latency-critical loop where an allocation's
+ * implicit synchronisation or pool growth is not acceptable.
+ * d_verts [n_verts*3] float32, d_faces [n_faces*3] int32 (indices outside
+ * [0, n_verts) are skipped), d_normals [n_verts*4] float32, 16-byte aligned,
+ * receives xyz = unit normal, w = 0.  The caller owns all three buffers.
+ * Limits: 3 <= n_verts <= 131,072 and 1 <= n_faces <= 262,144; larger meshes
+ * are rejected with AG_ERR_INVALID_ARG (use ag_bvh_build instead).
+ * Scratch: one static device array of about 4.2 MB inside this library,
+ * present on every device that loads the library until the process exits.
+ * No cudaMalloc, cudaFree or pool allocation is made.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), which
+ * may initialise the library's device code; make that first call before
+ * capturing a stream into a CUDA graph.  All calls share the one array and
+ * each call clears the parts that must start at zero, so calls that overlap
+ * on the GPU (other streams or other host threads) race and must be
+ * serialised by the caller.  Ordered on `stream`; does not synchronise.
+ */
+AG_API ag_status ag_vertex_normals_noalloc(const float *d_verts, int64_t n_verts,
+                                           const int32_t *d_faces, int64_t n_faces,
+                                           float *d_normals, ag_stream_t stream);
+
 /* Synchronise `stream`, then return and clear the device status word
  * (AG_ERR_TRAVERSAL_LIMIT if any ray since the last call hit a limit, or
  * AG_ERR_INVALID_ARG for out-of-range face indices seen by ag_bvh_build), or

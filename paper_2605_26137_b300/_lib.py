@@ -28,7 +28,7 @@ AG_SCHED_WARP = 1
 # every symbol include/ag.h declares
 EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
            "ag_batch_plan_create", "ag_batch_plan_launch", "ag_batch_plan_free", "ag_bake_backward",
-           "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version")
+           "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc")
 
 
 class AgOpts(ctypes.Structure):

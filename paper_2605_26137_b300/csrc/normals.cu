@@ -10,6 +10,8 @@
 #include "ag_internal.cuh"
 #include "exact.cuh"
 
+#include <mutex>
+
 namespace ag {
 
 namespace {
@@ -123,4 +125,71 @@ cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Vertex normals without any allocation, for callers that cannot allocate
+// device memory themselves or through this library (see
+// ag_vertex_normals_noalloc in include/ag.h).  The adjacency scratch lives in
+// one file-scope device array, sized for the limits below; every device that
+// loads this library keeps it until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t NOALLOC_MAX_VERTS = 1 << 17;  // 131,072 vertices
+constexpr int64_t NOALLOC_MAX_FACES = 1 << 18;  // 262,144 triangles
+constexpr size_t NOALLOC_SCRATCH_BYTES =
+    sizeof(unsigned) * (size_t)(2 * NOALLOC_MAX_VERTS + 1) + sizeof(int32_t) * (size_t)(3 * NOALLOC_MAX_FACES);
+
+// shared by every call: calls that overlap on the GPU (two streams, or two
+// host threads) race on it
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAXDEV = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAXDEV] = {nullptr};
+
+// Device address of the array on the current device.  In host code the
+// symbol g_noalloc_scratch is only a host-side stand-in, so the address is
+// looked up once per device with that device current, and cached.
+ag_status noalloc_scratch_on_current_device(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "ag_vertex_normals_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= NOALLOC_MAXDEV)
+        return set_error(AG_ERR_INVALID_ARG, "ag_vertex_normals_noalloc: device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_error(e, "ag_vertex_normals_noalloc: cudaGetSymbolAddress");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return AG_OK;
+}
+
+}  // namespace
 }  // namespace ag
+
+extern "C" AG_API ag_status ag_vertex_normals_noalloc(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
+                                                      int64_t n_faces, float *d_normals, ag_stream_t stream) {
+    using namespace ag;
+    if (!d_verts || !d_faces || !d_normals)
+        return set_error(AG_ERR_INVALID_ARG, "ag_vertex_normals_noalloc: pointers must be non-NULL");
+    if (n_verts < 3 || n_verts > NOALLOC_MAX_VERTS)
+        return set_error(AG_ERR_INVALID_ARG, "ag_vertex_normals_noalloc: n_verts must be in 3..%lld (static scratch limit)",
+                         (long long)NOALLOC_MAX_VERTS);
+    if (n_faces < 1 || n_faces > NOALLOC_MAX_FACES)
+        return set_error(AG_ERR_INVALID_ARG, "ag_vertex_normals_noalloc: n_faces must be in 1..%lld (static scratch limit)",
+                         (long long)NOALLOC_MAX_FACES);
+    if (reinterpret_cast<uintptr_t>(d_normals) % 16)
+        return set_error(AG_ERR_INVALID_ARG, "ag_vertex_normals_noalloc: d_normals must be 16-byte aligned");
+    void *scratch = nullptr;
+    ag_status st = noalloc_scratch_on_current_device(&scratch);
+    if (st != AG_OK) return st;
+    // the degree/offset/fill counters are cleared inside (they must start at zero)
+    cudaError_t e = launch_vertex_normals(d_verts, d_faces, n_verts, n_faces, nullptr, nullptr,
+                                          reinterpret_cast<float4 *>(d_normals), nullptr, scratch,
+                                          (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_error(e, "ag_vertex_normals_noalloc");
+    return AG_OK;
+}
