@@ -79,11 +79,9 @@ def peaks():
 
 
 def trace_source_hash():
-    h = hashlib.sha256()
-    for fn in ("trace.cu", "ag_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", fn), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+    """Hash of the traversal kernel's source file (the profiled kernel)."""
+    with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", "trace.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 def recorded_traffic(layout_tag: str):
