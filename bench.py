@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--no-extras", action="store_true", help="headline only (no backward / layout / batch legs)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--schedule", default="auto")
+    p.add_argument("--block-size", type=int, default=0)
+    p.add_argument("--blocks-per-sm", type=int, default=0)
     p.add_argument("--json-out", default=None)
     p.add_argument("--sdf-device", default=None, help="device for sampling the fixture SDF (default: the GPU)")
     p.add_argument("--profile", action="store_true",
@@ -326,7 +328,7 @@ def main():
     with ClockSampler(local) as clk:
         clk.wait_first()
         for _ in range(args.warmup):
-            pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, schedule=args.schedule)
+            pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, schedule=args.schedule, block_size=args.block_size, blocks_per_sm=args.blocks_per_sm)
         pb.sync_status()
         if world > 1:
             torch.distributed.barrier()
@@ -334,7 +336,7 @@ def main():
         wall0 = time.perf_counter()
         for i in range(args.steps):
             flush.zero_()
-            pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, schedule=args.schedule, events=ev[i])
+            pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, schedule=args.schedule, block_size=args.block_size, blocks_per_sm=args.blocks_per_sm, events=ev[i])
         torch.cuda.synchronize()
         wall1 = time.perf_counter()
         wall = wall1 - wall0

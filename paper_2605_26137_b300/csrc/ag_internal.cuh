@@ -139,6 +139,7 @@ struct TraceJob {
     int W, H;
     float max_dist;
     float lambda;
+    float scene_abs;        // largest |coordinate| of the high mesh bbox
 };
 
 constexpr int FACE_DEGEN = 1;   // lface.w bit: unreliable UVs -> (0,0,1)

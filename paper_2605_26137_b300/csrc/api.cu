@@ -199,6 +199,8 @@ TraceJob make_job(ag_bvh_t h, const AssetScratch &a, int W, int H, float max_dis
     j.W = W;
     j.H = H;
     j.max_dist = max_dist;
+    j.scene_abs = 0.f;
+    for (int k = 0; k < 3; ++k) j.scene_abs = fmaxf(j.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
     return j;
 }
 

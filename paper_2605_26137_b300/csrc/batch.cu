@@ -128,6 +128,8 @@ void fill_tables(int n, const ag_asset_desc *d, const std::vector<AssetBufs> &b,
         j.W = d[a].W;
         j.H = d[a].H;
         j.max_dist = d[a].max_dist;
+        j.scene_abs = 0.f;
+        for (int k = 0; k < 3; ++k) j.scene_abs = fmaxf(j.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
         counts[a] = b[a].n_rays;
     }
 }

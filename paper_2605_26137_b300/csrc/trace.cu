@@ -27,15 +27,18 @@ namespace ag {
 namespace {
 
 constexpr int STACK = 64;
-constexpr float BOX_REL = 9.5367431640625e-07f;  // 2^-20 relative interval widening
+constexpr float EPS_REL = 4.76837158203125e-07f;  // 2^-21: widening per unit of coordinate magnitude
 
 struct Ray {
+    // exact-origin triangle test: permuted axes, shear, origin as base + offset
     int kx, ky, kz;
     float Sx, Sy, Sz;
-    float bx, by, bz;     // base (vertex 0 of the low face), permuted
-    float ox, oy, oz;     // offset from base, permuted
-    float3 plo, phi;      // padded origins for box planes (lo plane, hi plane)
-    float3 inv;           // 1/d, zero components replaced by tiny values
+    float bx, by, bz;
+    float ox, oy, oz;
+    // box test: rounded origin, 1/d with zero components made tiny, direction signs
+    float px, py, pz;
+    float ix, iy, iz;
+    bool nx, ny, nz;
 };
 
 __device__ __forceinline__ float pick(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
@@ -54,30 +57,14 @@ __device__ __forceinline__ Ray make_ray(float3 base, float3 off, float3 d) {
     r.bx = pick(base, r.kx); r.by = pick(base, r.ky); r.bz = pick(base, r.kz);
     r.ox = pick(off, r.kx); r.oy = pick(off, r.ky); r.oz = pick(off, r.kz);
     float3 p = base + off;
-    float m = fmaxf(fabsf(p.x), fmaxf(fabsf(p.y), fabsf(p.z)));
-    float dl = m * 9.5367431640625e-07f + 1e-30f;   // ~8 ulp of the largest coordinate
-    r.plo = make_float3(p.x + dl, p.y + dl, p.z + dl);
-    r.phi = make_float3(p.x - dl, p.y - dl, p.z - dl);
+    r.px = p.x; r.py = p.y; r.pz = p.z;
     float3 dd = d;
     if (fabsf(dd.x) < 1e-30f) dd.x = copysignf(1e-30f, dd.x);
     if (fabsf(dd.y) < 1e-30f) dd.y = copysignf(1e-30f, dd.y);
     if (fabsf(dd.z) < 1e-30f) dd.z = copysignf(1e-30f, dd.z);
-    r.inv = make_float3(1.0f / dd.x, 1.0f / dd.y, 1.0f / dd.z);
+    r.ix = 1.0f / dd.x; r.iy = 1.0f / dd.y; r.iz = 1.0f / dd.z;
+    r.nx = r.ix < 0.f; r.ny = r.iy < 0.f; r.nz = r.iz < 0.f;
     return r;
-}
-
-// line interval of a box; returns the nearest |t| in [-lim, lim] or +inf
-__device__ __forceinline__ float box_dist(const Ray &r, float lx, float ly, float lz, float hx, float hy, float hz,
-                                          float lim) {
-    float ax = (lx - r.plo.x) * r.inv.x, bx = (hx - r.phi.x) * r.inv.x;
-    float ay = (ly - r.plo.y) * r.inv.y, by = (hy - r.phi.y) * r.inv.y;
-    float az = (lz - r.plo.z) * r.inv.z, bz = (hz - r.phi.z) * r.inv.z;
-    float t0 = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fminf(az, bz));
-    float t1 = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fmaxf(az, bz));
-    t0 = t0 - fabsf(t0) * BOX_REL;
-    t1 = t1 + fabsf(t1) * BOX_REL;
-    if (!(t0 <= t1) || t0 > lim || t1 < -lim) return __int_as_float(0x7f800000);
-    return t0 > 0.f ? t0 : (t1 < 0.f ? -t1 : 0.f);
 }
 
 // vertex in ray space: (v - base) - offset, permuted and sheared
@@ -112,6 +99,8 @@ __device__ __forceinline__ void test_tri(const Ray &r, const float4 *__restrict_
     float det = U + V + W;
     if (det == 0.f) return;
     float T = U * Az + V * Bz + W * Cz;
+    // |T / det| <= babs, tested without the division (with slack; exact below)
+    if (fabsf(T) > b.babs * fabsf(det) * 1.0000010f) return;
     float t = T / det;
     float at = fabsf(t);
     if (!(at <= b.babs)) return;
@@ -125,94 +114,120 @@ __device__ __forceinline__ void test_tri(const Ray &r, const float4 *__restrict_
     b.t = t; b.babs = at; b.rec = rec; b.U = U; b.V = V; b.W = W; b.det = det; b.found = true;
 }
 
+// byte k of w as an exact float: 2^23 + byte in the bits, minus 2^23
+__device__ __forceinline__ float byte_f(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (unsigned)k)) - 8388608.0f;
+}
+
+// Traversal bookkeeping of one node visit: the nearest relevant child becomes
+// the next node (no stack round trip); every other relevant child is pushed.
+struct Next {
+    uint32_t ref;
+    float dist;
+    bool has;
+};
+
+__device__ __forceinline__ void offer(uint32_t ref, float d, Next &nx, uint2 *stack, int &sp, unsigned *status) {
+    uint32_t pr = ref;
+    float pd = d;
+    if (!nx.has || d < nx.dist) {
+        pr = nx.ref;
+        pd = nx.dist;
+        nx.ref = ref;
+        nx.dist = d;
+        if (!nx.has) { nx.has = true; return; }
+    }
+    if (sp < STACK) stack[sp++] = make_uint2(pr, __float_as_uint(pd));
+    else atomicOr(status, AGS_STACK);
+}
+
+__device__ __forceinline__ uint32_t child_ref(uint32_t m, uint32_t child_base, uint32_t tri_base) {
+    return (m & 0x80u) ? child_base + (m & 0x7fu) : ref_leaf(tri_base + (m & 31u), (int)((m >> 5) & 3u));
+}
+
 template <int LAYOUT>
 struct NodeOps;
 
+// 80-byte quantised node.  Per node and axis the child planes become one FMA
+// each: t(q) = q * a + b with a = 2^e / d and b = (origin - p) / d.  The
+// intervals are widened by eps = 2^-21 (|origin| + |p| + 255 * 2^e) / |d|,
+// which bounds every rounding on the way (decoded plane, a, b, the FMA, the
+// rounded ray origin) by a factor of at least 4, so a box the exact line
+// meets is never rejected.
 template <>
 struct NodeOps<AG_BVH_Q8> {
-    // returns child refs / dists (dist = +inf for none)
-    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim,
-                                                 float dist[8], uint32_t ref[8]) {
+    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim, Next &nx,
+                                                 uint2 *stack, int &sp, unsigned *status) {
         const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const QNode *>(nodes) + idx);
         uint4 w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2), w3 = __ldg(p + 3), w4 = __ldg(p + 4);
         float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
         float sx = __uint_as_float((w0.w & 0xffu) << 23);
         float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
         float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
+        float ax = sx * r.ix, ay = sy * r.iy, az = sz * r.iz;
+        float bx = (ox - r.px) * r.ix, by = (oy - r.py) * r.iy, bz = (oz - r.pz) * r.iz;
+        float ex = EPS_REL * (fabsf(ox) + fabsf(r.px) + 255.f * sx) * fabsf(r.ix);
+        float ey = EPS_REL * (fabsf(oy) + fabsf(r.py) + 255.f * sy) * fabsf(r.iy);
+        float ez = EPS_REL * (fabsf(oz) + fabsf(r.pz) + 255.f * sz) * fabsf(r.iz);
+        float bnx = bx - ex, bfx = bx + ex, bny = by - ey, bfy = by + ey, bnz = bz - ez, bfz = bz + ez;
+        // near-plane bytes: lo for d > 0, hi for d < 0
+        uint32_t nx0 = r.nx ? w3.z : w2.x, nx1 = r.nx ? w3.w : w2.y, fx0 = r.nx ? w2.x : w3.z, fx1 = r.nx ? w2.y : w3.w;
+        uint32_t ny0 = r.ny ? w4.x : w2.z, ny1 = r.ny ? w4.y : w2.w, fy0 = r.ny ? w2.z : w4.x, fy1 = r.ny ? w2.w : w4.y;
+        uint32_t nz0 = r.nz ? w4.z : w3.x, nz1 = r.nz ? w4.w : w3.y, fz0 = r.nz ? w3.x : w4.z, fz1 = r.nz ? w3.y : w4.w;
         uint32_t child_base = w1.x, tri_base = w1.y;
-        uint32_t meta_lo = w1.z, meta_hi = w1.w;
-        uint32_t qlx[2] = {w2.x, w2.y}, qly[2] = {w2.z, w2.w};
-        uint32_t qlz[2] = {w3.x, w3.y}, qhx[2] = {w3.z, w3.w};
-        uint32_t qhy[2] = {w4.x, w4.y}, qhz[2] = {w4.z, w4.w};
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-            int wd = c >> 2, sh = (c & 3) * 8;
-            uint32_t m = ((c < 4 ? meta_lo : meta_hi) >> sh) & 0xffu;
-            float lx = __fmaf_rn((float)((qlx[wd] >> sh) & 0xffu), sx, ox);
-            float ly = __fmaf_rn((float)((qly[wd] >> sh) & 0xffu), sy, oy);
-            float lz = __fmaf_rn((float)((qlz[wd] >> sh) & 0xffu), sz, oz);
-            float hx = __fmaf_rn((float)((qhx[wd] >> sh) & 0xffu), sx, ox);
-            float hy = __fmaf_rn((float)((qhy[wd] >> sh) & 0xffu), sy, oy);
-            float hz = __fmaf_rn((float)((qhz[wd] >> sh) & 0xffu), sz, oz);
-            float dd = box_dist(r, lx, ly, lz, hx, hy, hz, lim);
-            if (m == 0) dd = __int_as_float(0x7f800000);
-            dist[c] = dd;
-            ref[c] = (m & 0x80u) ? child_base + (m & 0x7fu)
-                                 : ref_leaf(tri_base + (m & 31u), (int)((m >> 5) & 3u) == 0 ? 1 : (int)((m >> 5) & 3u));
+            const int k = c & 3;
+            const bool hi = c >= 4;
+            uint32_t m = ((hi ? w1.w : w1.z) >> (8 * k)) & 0xffu;
+            float tnx = __fmaf_rn(byte_f(hi ? nx1 : nx0, k), ax, bnx);
+            float tfx = __fmaf_rn(byte_f(hi ? fx1 : fx0, k), ax, bfx);
+            float tny = __fmaf_rn(byte_f(hi ? ny1 : ny0, k), ay, bny);
+            float tfy = __fmaf_rn(byte_f(hi ? fy1 : fy0, k), ay, bfy);
+            float tnz = __fmaf_rn(byte_f(hi ? nz1 : nz0, k), az, bnz);
+            float tfz = __fmaf_rn(byte_f(hi ? fz1 : fz0, k), az, bfz);
+            float te = fmaxf(fmaxf(tnx, tny), tnz);
+            float tx = fminf(fminf(tfx, tfy), tfz);
+            if (m != 0 && te <= tx && te <= lim && tx >= -lim)
+                offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status);
         }
     }
 };
 
+// 208-byte node with exact FP32 child boxes: t = plane / d - p / d, widened by
+// eps = 2^-21 (scene bound + |p|) / |d| per axis.
 template <>
 struct NodeOps<AG_BVH_F32> {
-    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim,
-                                                 float dist[8], uint32_t ref[8]) {
-        const FNode *nd = static_cast<const FNode *>(nodes) + idx;
-        const uint4 *p = reinterpret_cast<const uint4 *>(nd);
+    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim, Next &nx,
+                                                 uint2 *stack, int &sp, unsigned *status, float scene_abs) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const FNode *>(nodes) + idx);
         uint4 h = __ldg(p);
-        uint32_t child_base = h.x, tri_base = h.y, meta_lo = h.z, meta_hi = h.w;
-        float lo[3][8], hi[3][8];
+        uint32_t child_base = h.x, tri_base = h.y;
+        float ex = EPS_REL * (scene_abs + fabsf(r.px)) * fabsf(r.ix);
+        float ey = EPS_REL * (scene_abs + fabsf(r.py)) * fabsf(r.iy);
+        float ez = EPS_REL * (scene_abs + fabsf(r.pz)) * fabsf(r.iz);
+        float cx = -r.px * r.ix, cy = -r.py * r.iy, cz = -r.pz * r.iz;
+        float cnx = cx - ex, cfx = cx + ex, cny = cy - ey, cfy = cy + ey, cnz = cz - ez, cfz = cz + ez;
 #pragma unroll
-        for (int q = 0; q < 12; ++q) {
-            uint4 w = __ldg(p + 1 + q);
-            float *dst = (q < 6) ? &lo[q / 2][(q & 1) * 4] : &hi[(q - 6) / 2][(q & 1) * 4];
-            dst[0] = __uint_as_float(w.x); dst[1] = __uint_as_float(w.y);
-            dst[2] = __uint_as_float(w.z); dst[3] = __uint_as_float(w.w);
-        }
+        for (int half = 0; half < 2; ++half) {
+            uint4 lx = __ldg(p + 1 + half), ly = __ldg(p + 3 + half), lz = __ldg(p + 5 + half);
+            uint4 hx = __ldg(p + 7 + half), hy = __ldg(p + 9 + half), hz = __ldg(p + 11 + half);
+            const uint32_t LX[4] = {lx.x, lx.y, lx.z, lx.w}, LY[4] = {ly.x, ly.y, ly.z, ly.w}, LZ[4] = {lz.x, lz.y, lz.z, lz.w};
+            const uint32_t HX[4] = {hx.x, hx.y, hx.z, hx.w}, HY[4] = {hy.x, hy.y, hy.z, hy.w}, HZ[4] = {hz.x, hz.y, hz.z, hz.w};
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            uint32_t m = ((c < 4 ? meta_lo : meta_hi) >> ((c & 3) * 8)) & 0xffu;
-            float dd = box_dist(r, lo[0][c], lo[1][c], lo[2][c], hi[0][c], hi[1][c], hi[2][c], lim);
-            if (m == 0) dd = __int_as_float(0x7f800000);
-            dist[c] = dd;
-            ref[c] = (m & 0x80u) ? child_base + (m & 0x7fu)
-                                 : ref_leaf(tri_base + (m & 31u), (int)((m >> 5) & 3u) == 0 ? 1 : (int)((m >> 5) & 3u));
+            for (int k = 0; k < 4; ++k) {
+                uint32_t m = ((half ? h.w : h.z) >> (8 * k)) & 0xffu;
+                float plx = __uint_as_float(r.nx ? HX[k] : LX[k]), pfx = __uint_as_float(r.nx ? LX[k] : HX[k]);
+                float ply = __uint_as_float(r.ny ? HY[k] : LY[k]), pfy = __uint_as_float(r.ny ? LY[k] : HY[k]);
+                float plz = __uint_as_float(r.nz ? HZ[k] : LZ[k]), pfz = __uint_as_float(r.nz ? LZ[k] : HZ[k]);
+                float te = fmaxf(fmaxf(__fmaf_rn(plx, r.ix, cnx), __fmaf_rn(ply, r.iy, cny)), __fmaf_rn(plz, r.iz, cnz));
+                float tx = fminf(fminf(__fmaf_rn(pfx, r.ix, cfx), __fmaf_rn(pfy, r.iy, cfy)), __fmaf_rn(pfz, r.iz, cfz));
+                if (m != 0 && te <= tx && te <= lim && tx >= -lim)
+                    offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status);
+            }
         }
     }
 };
-
-__device__ __forceinline__ void cswap(float &da, uint32_t &ra, float &db, uint32_t &rb) {
-    bool sw = db < da;
-    float td = sw ? db : da;
-    uint32_t tr = sw ? rb : ra;
-    db = sw ? da : db;
-    rb = sw ? ra : rb;
-    da = td;
-    ra = tr;
-}
-
-__device__ __forceinline__ void sort8(float d[8], uint32_t r[8]) {
-    cswap(d[0], r[0], d[1], r[1]); cswap(d[2], r[2], d[3], r[3]);
-    cswap(d[4], r[4], d[5], r[5]); cswap(d[6], r[6], d[7], r[7]);
-    cswap(d[0], r[0], d[2], r[2]); cswap(d[1], r[1], d[3], r[3]);
-    cswap(d[4], r[4], d[6], r[6]); cswap(d[5], r[5], d[7], r[7]);
-    cswap(d[1], r[1], d[2], r[2]); cswap(d[5], r[5], d[6], r[6]);
-    cswap(d[0], r[0], d[4], r[4]); cswap(d[3], r[3], d[7], r[7]);
-    cswap(d[1], r[1], d[5], r[5]); cswap(d[2], r[2], d[6], r[6]);
-    cswap(d[1], r[1], d[4], r[4]); cswap(d[3], r[3], d[6], r[6]);
-    cswap(d[2], r[2], d[4], r[4]); cswap(d[3], r[3], d[5], r[5]);
-    cswap(d[3], r[3], d[4], r[4]);
-}
 
 struct TraceArgs {
     TraceJob job0;
@@ -271,35 +286,32 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs A) {
         int steps = 0;
         if (COUNT) ++c_rays;
         for (;;) {
+            Next nx;
+            nx.has = false;
+            nx.ref = 0;
+            nx.dist = 0.f;
             if (ref_is_leaf(cur)) {
                 uint32_t first = ref_first(cur);
                 int cnt = ref_count(cur);
                 for (int k = 0; k < cnt; ++k) test_tri(ray, J.tris, J.tri_ids, first + k, best);
                 if (COUNT) c_tris += cnt;
             } else {
-                float dist[8];
-                uint32_t ref[8];
-                NodeOps<LAYOUT>::visit(J.nodes, cur, ray, best.babs, dist, ref);
+                if (LAYOUT == AG_BVH_Q8)
+                    NodeOps<AG_BVH_Q8>::visit(J.nodes, cur, ray, best.babs, nx, stack, sp, A.status);
+                else
+                    NodeOps<AG_BVH_F32>::visit(J.nodes, cur, ray, best.babs, nx, stack, sp, A.status, J.scene_abs);
                 if (COUNT) ++c_nodes;
-                sort8(dist, ref);
-#pragma unroll
-                for (int c = 7; c >= 0; --c) {
-                    if (dist[c] <= best.babs) {
-                        if (sp < STACK) {
-                            stack[sp++] = make_uint2(ref[c], __float_as_uint(dist[c]));
-                        } else {
-                            atomicOr(A.status, AGS_STACK);
-                        }
-                    }
+            }
+            if (nx.has) {
+                cur = nx.ref;
+            } else {
+                bool done = true;
+                while (sp > 0) {
+                    uint2 e = stack[--sp];
+                    if (__uint_as_float(e.y) <= best.babs) { cur = e.x; done = false; break; }
                 }
+                if (done) break;
             }
-            bool done = false;
-            for (;;) {
-                if (sp == 0) { done = true; break; }
-                uint2 e = stack[--sp];
-                if (__uint_as_float(e.y) <= best.babs) { cur = e.x; break; }
-            }
-            if (done) break;
             if (++steps > A.max_steps) { atomicOr(A.status, AGS_STEP_CAP); break; }
         }
         const bool hit = best.found;
