@@ -62,6 +62,7 @@ def parse():
     p.add_argument("--profile", action="store_true",
                    help="profiling case for ncu: one BVH build and --steps plain bakes, nothing else")
     p.add_argument("--layout", default="q8", choices=["q8", "f32"])
+    p.add_argument("--collapse", default="area", choices=["area_count", "area", "count"])
     return p.parse_args()
 
 
@@ -181,7 +182,7 @@ def run_profile(args):
     torch.cuda.set_device(0)
     a = make_asset(args, "cuda")
     hv, hf, lv, lf, uv = to_dev(a, torch)
-    bvh = pb.Bvh(hv, hf, layout=args.layout)
+    bvh = pb.Bvh(hv, hf, layout=args.layout, collapse=args.collapse)
     out = pb.alloc_outputs(args.res, args.res, hv.device)
     for _ in range(args.steps):
         pb.bake(bvh, lv, lf, uv, args.res, args.res, a.max_dist, out=out)
@@ -310,7 +311,7 @@ def main():
     W = H = args.res
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    bvh = pb.Bvh(hv, hf, layout="q8")
+    bvh = pb.Bvh(hv, hf, layout="q8", collapse=args.collapse)
     build_wall_ms = 1e3 * (time.perf_counter() - t0)
     info = bvh.info()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -410,6 +411,47 @@ def timed(torch, fn, steps, warmup, flush=None):
     return [a.elapsed_time(b) for a, b in ms]
 
 
+def layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, n_sample=20000, seed=7):
+    """Max / mean |tangent-space normal - FP64 oracle| over a seeded sample of
+    ray texels (ambiguous-closest texels excluded, as in the parity tests)."""
+    import oracle
+    out = pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, aux=True)
+    g = out.normal_ts.cpu().numpy().reshape(-1, 3)
+    gm = out.mask.cpu().numpy().reshape(-1)
+    face = out.face.cpu().numpy().reshape(-1)
+    rays = np.flatnonzero(face >= 0)
+    rng = np.random.default_rng(seed)
+    samp = np.sort(rng.choice(rays, size=min(n_sample, len(rays)), replace=False))
+    o = oracle.bake_asset(a, sample=samp)
+    on = o["nts"].reshape(-1, 3)[samp]
+    om = o["mask"].reshape(-1)[samp]
+    ok = (om == gm[samp]) & ((o["flags"].reshape(-1)[samp] & 8) == 0)
+    err = np.abs(g[samp] - on).max(-1)[ok]
+    return {"sample": int(len(samp)), "max_err": float(err.max()), "mean_err": float(err.mean()),
+            "mask_mismatch": int((om != gm[samp]).sum())}
+
+
+def cage_optimisation(pb, torch, a, bvh, lv, lf, uv, W, H, steps=100, lr=1e-3, lam=0.1):
+    """Adam on the low-poly positions through the autograd wrapper of the bake loss."""
+    x = lv.clone().requires_grad_(True)
+    opt = torch.optim.Adam([x], lr=lr)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        opt.zero_grad(set_to_none=True)
+        L = pb.bake_loss(bvh, x, lf, uv, W, H, a.max_dist, lam)
+        L.backward()
+        opt.step()
+        losses.append(L.detach())
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    pb.sync_status()
+    ls = [float(v.item()) for v in losses]
+    return {"steps": steps, "lr": lr, "lambda": lam, "loss_first": ls[0], "loss_last": ls[-1],
+            "loss_drop_frac": 1.0 - ls[-1] / ls[0], "ms_per_step": 1e3 * dt / steps}
+
+
 def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms):
     res = {}
     steps = max(3, args.steps // 2)
@@ -418,8 +460,9 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     pb.sync_status()
     res["bwd_ms"] = statistics.mean(bwd)
     res["bwd_fwd_ratio"] = statistics.mean(bwd) / statistics.mean(fwd_ms)
+    res["cage_optimisation"] = cage_optimisation(pb, torch, a, bvh, lv, lf, uv, W, H)
     # FP32-node BVH vs 8-bit quantised nodes on the same asset
-    bf = pb.Bvh(hv, hf, layout="f32")
+    bf = pb.Bvh(hv, hf, layout="f32", collapse=args.collapse)
     cnt = pb.bake(bf, lv, lf, uv, W, H, a.max_dist, counters=True, aux=True)
     pb.sync_status()
     c = cnt.counters.cpu().numpy().astype(np.float64)
@@ -428,7 +471,9 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     n_rays = int(cnt.n_rays.item())
     res["layout_f32"] = {"ms_per_bake": statistics.mean(f32), "mrays_s": n_rays / statistics.mean(f32) / 1e3,
                          "bytes_per_ray": bytes_per_ray(bf.info()["node_size"], c[1] / c[0], c[2] / c[0], c[3] / c[0]),
-                         "node_bytes": bf.info()["node_bytes"], "nodes_per_ray": c[1] / c[0]}
+                         "node_bytes": bf.info()["node_bytes"], "nodes_per_ray": c[1] / c[0],
+                         "error_vs_oracle": layout_errors(pb, torch, a, bf, lv, lf, uv, W, H)}
+    res["layout_q8_error_vs_oracle"] = layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H)
     bf.free()
     if args.batch_assets > 0:
         res["batch"] = batch_leg(args, pb, torch, dev, flush)
@@ -444,7 +489,11 @@ def batch_leg(args, pb, torch, dev, flush):
     for i in range(args.batch_assets):
         nh = int(math.exp(rng.uniform(math.log(1e5), math.log(4e6))) * args.batch_scale)
         nl = int(math.exp(rng.uniform(math.log(2e3), math.log(5e4))) * args.batch_scale)
-        res = int(rng.choice([512, 1024, 2048]))
+        # atlas in {512, 1024, 2048}^2, among the sizes whose trivial-atlas cells keep
+        # at least 2 texels inside the 2-texel gutter for this low face count
+        g = math.ceil(math.sqrt(1.2 * max(nl, 200) / 2.0))
+        fits = [r for r in (512, 1024, 2048) if r // g - 4 >= 2]
+        res = int(rng.choice(fits))
         npr = int(rng.integers(8, 65))
         a = synth.sdf_asset(5000 + i, max(nh, 2000), max(nl, 200), res, res, n_prims=npr, device=dev)
         hv, hf, lv, lf, uv = to_dev(a, torch)
@@ -463,6 +512,21 @@ def batch_leg(args, pb, torch, dev, flush):
     t_seq = timed(torch, seq, steps, 1, flush)
     t_bat = timed(torch, plan.launch, steps, 1, flush)
     pb.sync_status()
+
+    # the loop a caller writes without the batch API: bake, read the maps back, next asset
+    host = [torch.empty((x.H, x.W, 4), dtype=torch.uint8).pin_memory() for x in assets]
+
+    def seq_readback():
+        for x, o, h in zip(assets, seq_out, host):
+            pb.bake(x.bvh, x.low_verts, x.low_faces, x.low_uv, x.W, x.H, x.max_dist, out=o)
+            h.copy_(o.normal_rgba8, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+    seq_readback()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        seq_readback()
+    ms_seq_rb = 1e3 * (time.perf_counter() - t0) / steps
     rays = 0
     # ray count from one aux bake per asset
     for x in assets:
@@ -474,7 +538,9 @@ def batch_leg(args, pb, torch, dev, flush):
     ms_seq, ms_bat = statistics.mean(t_seq), statistics.mean(t_bat)
     return {"assets": len(assets), "high_tris_total": total_tris, "rays_total": rays, "ms_sequential": ms_seq,
             "ms_batched": ms_bat, "speedup": ms_seq / ms_bat, "mrays_s_batched": rays / ms_bat / 1e3,
-            "mrays_s_sequential": rays / ms_seq / 1e3}
+            "mrays_s_sequential": rays / ms_seq / 1e3,
+            "ms_sequential_with_readback": ms_seq_rb, "speedup_vs_readback_loop": ms_seq_rb / ms_bat,
+            "note": "sequential = 64 ag_bake calls back to back on one stream; batched = one captured plan launch"}
 
 
 def e2e(args, pb, torch, a, W, H, dev, n_rays):

@@ -59,7 +59,16 @@ typedef enum {
 } ag_status;
 
 enum { AG_BVH_Q8 = 0, AG_BVH_F32 = 1 };
-enum { AG_SCHED_AUTO = -1, AG_SCHED_THREAD = 0, AG_SCHED_WARP = 1 };
+/* Collapse rules: expand the child with the largest surface area, the largest
+ * surface area x triangle count, or the most triangles. */
+enum { AG_COLLAPSE_AREA = 0, AG_COLLAPSE_AREA_COUNT = 1, AG_COLLAPSE_COUNT = 2 };
+
+/* Traversal schedules (one ray per thread in both):
+ *  AG_SCHED_BATCH  - a warp takes 32 consecutive rays and finishes all of them
+ *                    before taking more;
+ *  AG_SCHED_REFILL - lanes take new rays as they finish (in groups of at
+ *                    least 8 idle lanes), shading deferred to the refill. */
+enum { AG_SCHED_AUTO = -1, AG_SCHED_BATCH = 0, AG_SCHED_REFILL = 1 };
 
 /* Options.  Zero-initialise then call ag_opts_default, or pass NULL for the
  * defaults. */
@@ -73,7 +82,10 @@ typedef struct {
     int32_t blocks_per_sm; /* persistent trace CTAs per SM (0 = schedule default) */
     int32_t max_steps;   /* per-ray traversal step cap (0 = 1<<20); exceeding it sets
                             AG_ERR_TRAVERSAL_LIMIT */
-    int32_t reserved[9];
+    int32_t collapse;    /* ag_bvh_build: child chosen for expansion while collapsing the binary
+                            tree into 8-wide nodes: AG_COLLAPSE_AREA (0, default),
+                            AG_COLLAPSE_AREA_COUNT or AG_COLLAPSE_COUNT */
+    int32_t reserved[8];
 } ag_opts;
 
 /* Optional extra outputs of ag_bake (any member may be NULL). */

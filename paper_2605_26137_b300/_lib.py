@@ -21,9 +21,12 @@ AG_ERR_BAD_HANDLE = 5
 
 AG_BVH_Q8 = 0
 AG_BVH_F32 = 1
+AG_COLLAPSE_AREA = 0
+AG_COLLAPSE_AREA_COUNT = 1
+AG_COLLAPSE_COUNT = 2
 AG_SCHED_AUTO = -1
-AG_SCHED_THREAD = 0
-AG_SCHED_WARP = 1
+AG_SCHED_BATCH = 0
+AG_SCHED_REFILL = 1
 
 # every symbol include/ag.h declares
 EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
@@ -34,7 +37,7 @@ EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_
 class AgOpts(ctypes.Structure):
     _fields_ = [("bvh_layout", c_int32), ("gutter", c_int32), ("disp_fp16", c_int32), ("schedule", c_int32),
                 ("block_size", c_int32), ("blocks_per_sm", c_int32), ("max_steps", c_int32),
-                ("reserved", c_int32 * 9)]
+                ("collapse", c_int32), ("reserved", c_int32 * 8)]
 
 
 class AgBakeAux(ctypes.Structure):

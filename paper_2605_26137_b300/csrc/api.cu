@@ -9,8 +9,8 @@
 
 namespace ag {
 
-ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, int layout, cudaStream_t s,
-                    ag_bvh *h);
+ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, int layout, int rule,
+                    cudaStream_t s, ag_bvh *h);
 
 namespace {
 thread_local std::string g_err;
@@ -116,8 +116,10 @@ ag_status check_opts(const ag_opts &o) {
         return set_error(AG_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in 64..1024");
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 64) return set_error(AG_ERR_INVALID_ARG, "blocks_per_sm out of range");
     if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
-    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_WARP)
+    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_REFILL)
         return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
+    if (o.collapse < AG_COLLAPSE_AREA || o.collapse > AG_COLLAPSE_COUNT)
+        return set_error(AG_ERR_INVALID_ARG, "unknown collapse rule");
     return AG_OK;
 }
 
@@ -204,7 +206,7 @@ TraceJob make_job(ag_bvh_t h, const AssetScratch &a, int W, int H, float max_dis
     return j;
 }
 
-int pick_schedule(const ag_opts &o) { return o.schedule == AG_SCHED_AUTO ? AG_SCHED_THREAD : o.schedule; }
+int pick_schedule(const ag_opts &o) { return o.schedule == AG_SCHED_AUTO ? AG_SCHED_BATCH : o.schedule; }
 
 }  // namespace
 
@@ -261,7 +263,7 @@ AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32
     h->n_verts = n_verts;
     // clear a stale bad-face bit so this build's check is its own
     unsigned word = 0;
-    st = build_bvh(d_verts, n_verts, d_faces, n_faces, o.bvh_layout, s, h);
+    st = build_bvh(d_verts, n_verts, d_faces, n_faces, o.bvh_layout, o.collapse, s, h);
     if (st == AG_OK) {
         cudaError_t e = cudaMemcpyAsync(&word, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

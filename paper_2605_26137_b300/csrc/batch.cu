@@ -4,6 +4,7 @@
 #include "ag_internal.cuh"
 
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -101,7 +102,7 @@ ag_status check_opts_batch(const ag_opts &o) {
         return set_error(AG_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in 64..1024");
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 64) return set_error(AG_ERR_INVALID_ARG, "blocks_per_sm out of range");
     if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
-    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_WARP) return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
+    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_REFILL) return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
     return AG_OK;
 }
 
@@ -134,21 +135,81 @@ void fill_tables(int n, const ag_asset_desc *d, const std::vector<AssetBufs> &b,
     }
 }
 
-// enqueue the whole batch on s (capturable: kernels and memsets only)
+// Library-owned side streams of a device: the batch forks each asset's prep
+// and finalize onto them so the small per-asset kernels overlap (captured,
+// they become independent branches of the graph).
+constexpr int N_SIDE = 8;
+std::mutex g_side_mu;
+cudaStream_t g_side[64][N_SIDE] = {};
+
+cudaError_t side_streams(int dev, cudaStream_t **out) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    if (!g_side[dev][0]) {
+        for (int k = 0; k < N_SIDE; ++k) {
+            cudaError_t e = cudaStreamCreateWithFlags(&g_side[dev][k], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    *out = g_side[dev];
+    return cudaSuccess;
+}
+
+struct EventSet {
+    std::vector<cudaEvent_t> ev;
+    ~EventSet() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    cudaError_t make(cudaEvent_t *e) {
+        cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+        if (r == cudaSuccess) ev.push_back(*e);
+        return r;
+    }
+};
+
+// s waits for nothing new; every side stream that is used waits for s (fork)
+cudaError_t fork_to(cudaStream_t s, cudaStream_t *side, int n_used, EventSet &es) {
+    cudaEvent_t f;
+    cudaError_t e = es.make(&f);
+    if (e == cudaSuccess) e = cudaEventRecord(f, s);
+    for (int k = 0; k < n_used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(side[k], f, 0);
+    return e;
+}
+
+// s waits for every used side stream (join)
+cudaError_t join_from(cudaStream_t s, cudaStream_t *side, int n_used, EventSet &es) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < n_used && e == cudaSuccess; ++k) {
+        cudaEvent_t j;
+        e = es.make(&j);
+        if (e == cudaSuccess) e = cudaEventRecord(j, side[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, j, 0);
+    }
+    return e;
+}
+
+// enqueue the whole batch on s (capturable: kernels, memsets and event edges)
 ag_status enqueue_batch(int n, const ag_asset_desc *d, const ag_opts &o, int layout, const std::vector<AssetBufs> &b,
                         const TraceJob *host_jobs, const TraceJob *jobs, long long *begin,
                         const long long *const *counts, unsigned long long *ray_counter, unsigned *status,
-                        cudaStream_t s) {
+                        cudaStream_t s, int dev) {
+    cudaStream_t *side = nullptr;
+    AG_CUDA(side_streams(dev, &side));
+    const int used = n < N_SIDE ? n : N_SIDE;
+    EventSet es;
+    AG_CUDA(fork_to(s, side, used, es));
     for (int a = 0; a < n; ++a) {
         const AssetBufs &x = b[a];
-        AG_CUDA(cudaMemsetAsync(x.n_rays, 0, sizeof(long long) * 2, s));
+        cudaStream_t q = side[a % N_SIDE];
+        AG_CUDA(cudaMemsetAsync(x.n_rays, 0, sizeof(long long) * 2, q));
         AG_CUDA(launch_vertex_normals(d[a].lverts, d[a].lfaces, d[a].n_lverts, d[a].n_lfaces, d[a].lnormals, x.acc,
-                                      x.lnrm, x.lpos, x.nscr, s));
+                                      x.lnrm, x.lpos, x.nscr, q));
         AG_CUDA(launch_face_setup(d[a].luv, d[a].lfaces, d[a].n_lfaces, d[a].n_lverts, d[a].W, d[a].H, x.lpos, x.lnrm,
-                                  x.lface, x.ltan, x.uvfix, status, s));
-        AG_CUDA(launch_raster(x.uvfix, x.lface, d[a].n_lfaces, d[a].W, d[a].H, x.keys, s));
-        AG_CUDA(launch_resolve(x.keys, x.uvfix, d[a].W, d[a].H, x.face, nullptr, x.rays, x.n_rays, s));
+                                  x.lface, x.ltan, x.uvfix, status, q));
+        AG_CUDA(launch_raster(x.uvfix, x.lface, d[a].n_lfaces, d[a].W, d[a].H, x.keys, q));
+        AG_CUDA(launch_resolve(x.keys, x.uvfix, d[a].W, d[a].H, x.face, nullptr, x.rays, x.n_rays, q));
     }
+    AG_CUDA(join_from(s, side, used, es));
     TraceLaunch L;
     memset(&L, 0, sizeof(L));
     if (n == 1) {
@@ -167,14 +228,16 @@ ag_status enqueue_batch(int n, const ag_asset_desc *d, const ag_opts &o, int lay
     L.status = status;
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = layout;
-    L.schedule = o.schedule == AG_SCHED_AUTO ? AG_SCHED_THREAD : o.schedule;
+    L.schedule = o.schedule == AG_SCHED_AUTO ? AG_SCHED_BATCH : o.schedule;
     L.block_size = o.block_size;
     L.blocks_per_sm = o.blocks_per_sm;
     L.backward = false;
     AG_CUDA(launch_trace(L, s));
+    AG_CUDA(fork_to(s, side, used, es));
     for (int a = 0; a < n; ++a)
         AG_CUDA(launch_finalize(b[a].ntsd, b[a].face, d[a].W, d[a].H, o.gutter, o.disp_fp16, d[a].normal_rgba8,
-                                d[a].mask, d[a].disp, nullptr, nullptr, nullptr, nullptr, s));
+                                d[a].mask, d[a].disp, nullptr, nullptr, nullptr, nullptr, side[a % N_SIDE]));
+    AG_CUDA(join_from(s, side, used, es));
     return AG_OK;
 }
 
@@ -228,7 +291,7 @@ AG_API ag_status ag_bake_batch(int32_t n_assets, const ag_asset_desc *descs, con
     fill_tables(n_assets, descs, bufs, hj, hc);
     AG_CUDA(cudaMemcpyAsync(jobs, hj.data(), sizeof(TraceJob) * n_assets, cudaMemcpyHostToDevice, s));
     AG_CUDA(cudaMemcpyAsync((void *)counts, hc.data(), sizeof(void *) * n_assets, cudaMemcpyHostToDevice, s));
-    return enqueue_batch(n_assets, descs, o, layout, bufs, hj.data(), jobs, begin, counts, ray_counter, status, s);
+    return enqueue_batch(n_assets, descs, o, layout, bufs, hj.data(), jobs, begin, counts, ray_counter, status, s, dev);
 }
 
 AG_API ag_status ag_batch_plan_create(int32_t n_assets, const ag_asset_desc *descs, const ag_opts *opts,
@@ -275,7 +338,7 @@ AG_API ag_status ag_batch_plan_create(int32_t n_assets, const ag_asset_desc *des
         delete p;
         return cuda_error(e, "batch plan capture setup");
     }
-    st = enqueue_batch(n_assets, descs, o, layout, bufs, hj.data(), jobs, begin, counts, ray_counter, status, cap);
+    st = enqueue_batch(n_assets, descs, o, layout, bufs, hj.data(), jobs, begin, counts, ray_counter, status, cap, dev);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);

@@ -10,9 +10,6 @@
 namespace ag {
 namespace {
 
-constexpr int TW = 32, TH = 8, MAXG = 8;
-constexpr int SW = TW + 2 * MAXG, SH = TH + 2 * MAXG;
-
 // RGB8 code of c in [-1,1]: 128 + round_half_away(127 c) (codes 1..255,
 // 128 = 0, so the frequent value c = 0 is in the middle of a code rather than
 // on a code boundary); every step one FP32 rounding (no contraction).
@@ -23,17 +20,23 @@ __device__ __forceinline__ unsigned enc8(float c) {
     return (unsigned)(128 + (int)q);
 }
 
+// One CTA = a TW x TH output tile; the tile plus a G-texel halo is staged in
+// shared memory, G Jacobi passes run there (the valid region shrinks by one
+// texel per pass), then the TW x TH centre is encoded.  G, TW, TH are compile
+// time so the cell loops need no integer division.
+template <int G, int TW, int TH>
 __global__ void __launch_bounds__(256) k_finalize(const float4 *__restrict__ ntsd, const int32_t *__restrict__ face_map,
-                                                  int W, int H, int g, int disp_fp16, uchar4 *__restrict__ rgba,
+                                                  int W, int H, int disp_fp16, uchar4 *__restrict__ rgba,
                                                   uint8_t *__restrict__ mask, void *__restrict__ disp,
                                                   float *__restrict__ aux_nts, float *__restrict__ aux_disp,
                                                   int32_t *__restrict__ aux_hit_tri, float *__restrict__ aux_hit_t) {
-    __shared__ float4 sv[2][SH][SW];
-    __shared__ uint8_t sf[2][SH][SW];   // 0 empty, 1 ray texel, 2 dilated, 3 outside the image
-    const int bw = TW + 2 * g, bh = TH + 2 * g;
-    const int x0 = blockIdx.x * TW - g, y0 = blockIdx.y * TH - g;
-    for (int i = threadIdx.x; i < bw * bh; i += blockDim.x) {
-        int lx = i % bw, ly = i / bw;
+    constexpr int BW = TW + 2 * G, BH = TH + 2 * G, CELLS = BW * BH;
+    constexpr int NB = G > 0 ? 2 : 1;
+    __shared__ float4 sv[NB][BH][BW];
+    __shared__ uint8_t sf[NB][BH][BW];   // 0 empty, 1 ray texel, 2 dilated, 3 outside the image
+    const int x0 = blockIdx.x * TW - G, y0 = blockIdx.y * TH - G;
+    for (int i = threadIdx.x; i < CELLS; i += blockDim.x) {
+        int lx = i % BW, ly = i / BW;
         int x = x0 + lx, y = y0 + ly;
         float4 v = make_float4(0.f, 0.f, 1.f, 0.f);
         uint8_t f = 3;
@@ -47,15 +50,18 @@ __global__ void __launch_bounds__(256) k_finalize(const float4 *__restrict__ nts
     }
     __syncthreads();
     int cur = 0;
-    for (int p = 0; p < g; ++p) {
-        for (int i = threadIdx.x; i < bw * bh; i += blockDim.x) {
-            int lx = i % bw, ly = i / bw;
+#pragma unroll 1
+    for (int p = 0; p < G; ++p) {
+        for (int i = threadIdx.x; i < CELLS; i += blockDim.x) {
+            int lx = i % BW, ly = i / BW;
             float4 v = sv[cur][ly][lx];
             uint8_t f = sf[cur][ly][lx];
-            if (f == 0 && lx > 0 && ly > 0 && lx < bw - 1 && ly < bh - 1) {
+            if (f == 0 && lx > 0 && ly > 0 && lx < BW - 1 && ly < BH - 1) {
                 float sx = 0.f, sy = 0.f, sz = 0.f, sd = 0.f;
                 int cnt = 0;
+#pragma unroll
                 for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
                     for (int dx = -1; dx <= 1; ++dx) {
                         if (dx == 0 && dy == 0) continue;
                         uint8_t nf = sf[cur][ly + dy][lx + dx];
@@ -80,29 +86,31 @@ __global__ void __launch_bounds__(256) k_finalize(const float4 *__restrict__ nts
         __syncthreads();
         cur ^= 1;
     }
-    int lx = g + (threadIdx.x % TW), ly = g + (threadIdx.x / TW);
-    int x = blockIdx.x * TW + (threadIdx.x % TW), y = blockIdx.y * TH + (threadIdx.x / TW);
-    if (x >= W || y >= H) return;
-    size_t t = (size_t)y * W + x;
-    float4 v = sv[cur][ly][lx];
-    uint8_t f = sf[cur][ly][lx];
-    bool filled = f == 1 || f == 2;
-    if (!filled) v = make_float4(0.f, 0.f, 1.f, 0.f);
-    rgba[t] = make_uchar4((unsigned char)enc8(v.x), (unsigned char)enc8(v.y), (unsigned char)enc8(v.z),
-                          filled ? 255 : 0);
-    if (disp_fp16) ((__half *)disp)[t] = __float2half_rn(v.w);
-    else ((float *)disp)[t] = v.w;
-    if (f != 1) {
-        mask[t] = 0;
-        if (aux_hit_tri) aux_hit_tri[t] = -1;
-        if (aux_hit_t) aux_hit_t[t] = 0.f;
+    for (int i = threadIdx.x; i < TW * TH; i += blockDim.x) {
+        int ox = i % TW, oy = i / TW;
+        int x = blockIdx.x * TW + ox, y = blockIdx.y * TH + oy;
+        if (x >= W || y >= H) continue;
+        size_t t = (size_t)y * W + x;
+        float4 v = sv[cur][oy + G][ox + G];
+        uint8_t f = sf[cur][oy + G][ox + G];
+        bool filled = f == 1 || f == 2;
+        if (!filled) v = make_float4(0.f, 0.f, 1.f, 0.f);
+        rgba[t] = make_uchar4((unsigned char)enc8(v.x), (unsigned char)enc8(v.y), (unsigned char)enc8(v.z),
+                              filled ? 255 : 0);
+        if (disp_fp16) ((__half *)disp)[t] = __float2half_rn(v.w);
+        else ((float *)disp)[t] = v.w;
+        if (f != 1) {
+            mask[t] = 0;
+            if (aux_hit_tri) aux_hit_tri[t] = -1;
+            if (aux_hit_t) aux_hit_t[t] = 0.f;
+        }
+        if (aux_nts) {
+            aux_nts[3 * t] = v.x;
+            aux_nts[3 * t + 1] = v.y;
+            aux_nts[3 * t + 2] = v.z;
+        }
+        if (aux_disp) aux_disp[t] = v.w;
     }
-    if (aux_nts) {
-        aux_nts[3 * t] = v.x;
-        aux_nts[3 * t + 1] = v.y;
-        aux_nts[3 * t + 2] = v.z;
-    }
-    if (aux_disp) aux_disp[t] = v.w;
 }
 
 // dL/da_i = (I - n n^T) g_n / |a_i| (a_i: unnormalised area-weighted normal sum)
@@ -156,13 +164,33 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 
 }  // namespace
 
+template <int G, int TW, int TH>
+static cudaError_t finalize_g(const float4 *ntsd, const int32_t *face_map, int W, int H, int disp_fp16, uint8_t *rgba,
+                              uint8_t *mask, void *disp, float *aux_nts, float *aux_disp, int32_t *aux_hit_tri,
+                              float *aux_hit_t, cudaStream_t s) {
+    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH);
+    k_finalize<G, TW, TH><<<grid, 256, 0, s>>>(ntsd, face_map, W, H, disp_fp16, (uchar4 *)rgba, mask, disp, aux_nts,
+                                                aux_disp, aux_hit_tri, aux_hit_t);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize(const float4 *ntsd, const int32_t *face_map, int W, int H, int gutter, int disp_fp16,
                             uint8_t *rgba, uint8_t *mask, void *disp, float *aux_nts, float *aux_disp,
                             int32_t *aux_hit_tri, float *aux_hit_t, cudaStream_t s) {
-    dim3 grid((W + TW - 1) / TW, (H + TH - 1) / TH);
-    k_finalize<<<grid, TW * TH, 0, s>>>(ntsd, face_map, W, H, gutter, disp_fp16, (uchar4 *)rgba, mask, disp, aux_nts,
-                                         aux_disp, aux_hit_tri, aux_hit_t);
-    return cudaGetLastError();
+#define AG_FIN(Gv, TWv, THv) \
+    return finalize_g<Gv, TWv, THv>(ntsd, face_map, W, H, disp_fp16, rgba, mask, disp, aux_nts, aux_disp, aux_hit_tri, aux_hit_t, s)
+    switch (gutter) {
+        case 0: AG_FIN(0, 64, 16);
+        case 1: AG_FIN(1, 64, 16);
+        case 2: AG_FIN(2, 64, 16);
+        case 3: AG_FIN(3, 64, 16);
+        case 4: AG_FIN(4, 64, 8);
+        case 5: AG_FIN(5, 32, 8);
+        case 6: AG_FIN(6, 32, 8);
+        case 7: AG_FIN(7, 32, 8);
+        default: AG_FIN(8, 32, 8);
+    }
+#undef AG_FIN
 }
 
 cudaError_t launch_backward_finish(const float4 *lpos, const int4 *lface, int64_t nv, int64_t nf, const float *acc_nrm,

@@ -259,6 +259,7 @@ struct CollapseArgs {
     const int32_t *F;
     int64_t nv;
     int layout;
+    int rule;
     void *nodes;
     float4 *tris;
     int32_t *tri_ids;
@@ -331,8 +332,11 @@ __global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, int nq
             int best = -1;
             float ba = -1.f;
             for (int k = 0; k < nc; ++k) {
-                if (subtree_count(A, ch[k]) <= LEAF_MAX) continue;
-                float a = half_area(A, ch[k]);
+                int cnt = subtree_count(A, ch[k]);
+                if (cnt <= LEAF_MAX) continue;
+                float a = A.rule == AG_COLLAPSE_COUNT ? (float)cnt
+                        : A.rule == AG_COLLAPSE_AREA ? half_area(A, ch[k])
+                                                     : half_area(A, ch[k]) * (float)cnt;
                 if (a > ba) { ba = a; best = k; }
             }
             if (best < 0) break;
@@ -421,7 +425,7 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 
 }  // namespace
 
-ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, int layout,
+ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, int layout, int rule,
                     cudaStream_t s, ag_bvh *h) {
     int dev = h->device;
     unsigned *status = device_status_word(dev);
@@ -504,7 +508,7 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     // top-down collapse, one launch per level
     CollapseArgs A;
     A.n = n; A.child = child; A.range = range; A.box_lo = box_lo; A.box_hi = box_hi; A.vals = va;
-    A.V = d_verts; A.F = d_faces; A.nv = nv; A.layout = layout; A.nodes = nodes_tmp; A.tris = h->tris;
+    A.V = d_verts; A.F = d_faces; A.nv = nv; A.layout = layout; A.rule = rule; A.nodes = nodes_tmp; A.tris = h->tris;
     A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1;
     {
         unsigned init[2] = {1u, 0u};

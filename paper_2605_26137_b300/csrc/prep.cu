@@ -93,8 +93,11 @@ __global__ void k_face_setup(const float *__restrict__ uv, const int32_t *__rest
     uvfix[2 * f + 1] = make_int4((int)X[2], (int)Y[2], (int)(unsigned)(a2 & 0xffffffffll), (int)(a2 >> 32));
 }
 
+// Snapped UV triangle: coordinates fit in 24 bits, so differences fit in 32
+// and every product is one 32x32->64 multiply.
 struct UvTri {
-    long long X[3], Y[3], a2;
+    int X[3], Y[3];
+    long long a2;
 };
 
 __device__ __forceinline__ UvTri load_uvtri(const int4 *uvfix, int64_t f) {
@@ -105,12 +108,14 @@ __device__ __forceinline__ UvTri load_uvtri(const int4 *uvfix, int64_t f) {
     return t;
 }
 
-__device__ __forceinline__ long long orient2(long long ax, long long ay, long long bx, long long by, long long cx,
-                                             long long cy) {
-    return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax);
+__device__ __forceinline__ long long mulw(int a, int b) { return (long long)a * (long long)b; }
+
+__device__ __forceinline__ long long orient2(int ax, int ay, int bx, int by, int cx, int cy) {
+    return mulw(bx - ax, cy - ay) - mulw(by - ay, cx - ax);
 }
 
-__device__ __forceinline__ bool uv_inside(const UvTri &t, long long cx, long long cy, long long e[3]) {
+// e[i] = orient2(P[i+1], P[i+2], c): twice the signed area opposite vertex i
+__device__ __forceinline__ bool uv_inside(const UvTri &t, int cx, int cy, long long e[3]) {
     e[0] = orient2(t.X[1], t.Y[1], t.X[2], t.Y[2], cx, cy);
     e[1] = orient2(t.X[2], t.Y[2], t.X[0], t.Y[0], cx, cy);
     e[2] = orient2(t.X[0], t.Y[0], t.X[1], t.Y[1], cx, cy);
@@ -118,45 +123,46 @@ __device__ __forceinline__ bool uv_inside(const UvTri &t, long long cx, long lon
     return e[0] <= 0 && e[1] <= 0 && e[2] <= 0;
 }
 
-// open interiors of the triangle and the texel square [sx,sx+256]x[sy,sy+256]
-// intersect iff no separating axis among the square's and the triangle's edge normals
-__device__ bool uv_overlap(const UvTri &t, long long sx, long long sy) {
-    long long mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
-    long long mny = min(t.Y[0], min(t.Y[1], t.Y[2])), mxy = max(t.Y[0], max(t.Y[1], t.Y[2]));
-    if (mxx <= sx || mnx >= sx + 256 || mxy <= sy || mny >= sy + 256) return false;
+// Open interiors of the triangle and the texel square centred on c (side
+// 256) intersect iff no separating axis exists among the square's axes and
+// the triangle's edge normals.  Along the normal of edge (P[k], P[k+1]),
+// measured from P[k]: the triangle spans [min(0,a2), max(0,a2)] and the
+// square spans e_k(c) -/+ 128 (|dx| + |dy|), where e_k(c) = e[(k+2)%3] is the
+// edge function already evaluated at the centre.
+__device__ __forceinline__ bool uv_overlap(const UvTri &t, int cx, int cy, const long long e[3]) {
+    int mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
+    int mny = min(t.Y[0], min(t.Y[1], t.Y[2])), mxy = max(t.Y[0], max(t.Y[1], t.Y[2]));
+    if (mxx <= cx - 128 || mnx >= cx + 128 || mxy <= cy - 128 || mny >= cy + 128) return false;
+    long long lo = min(0ll, t.a2), hi = max(0ll, t.a2);
+#pragma unroll
     for (int k = 0; k < 3; ++k) {
-        int a = k, b = (k + 1) % 3, c = (k + 2) % 3;
-        long long nx = -(t.Y[b] - t.Y[a]), ny = t.X[b] - t.X[a];
-        long long pe = nx * t.X[a] + ny * t.Y[a];
-        long long po = nx * t.X[c] + ny * t.Y[c];
-        long long tmn = min(pe, po), tmx = max(pe, po);
-        long long p0 = nx * sx + ny * sy, p1 = nx * (sx + 256) + ny * sy;
-        long long p2 = nx * sx + ny * (sy + 256), p3 = nx * (sx + 256) + ny * (sy + 256);
-        long long smn = min(min(p0, p1), min(p2, p3)), smx = max(max(p0, p1), max(p2, p3));
-        if (smx <= tmn || smn >= tmx) return false;
+        int b = k == 2 ? 0 : k + 1;
+        long long r = 128ll * (long long)(abs(t.X[b] - t.X[k]) + abs(t.Y[b] - t.Y[k]));
+        long long ek = e[k == 0 ? 2 : k - 1];
+        if (ek + r <= lo || ek - r >= hi) return false;
     }
     return true;
 }
 
 // floor(d^2 * 65536) for the distance from (cx,cy) to edge k (snapped units),
 // ~0 when farther than one texel; *param = closest point's edge parameter.
-__device__ unsigned long long edge_qdist(const UvTri &t, int k, long long cx, long long cy, float *param) {
-    int a = k, b = (k + 1) % 3;
-    long long wx = cx - t.X[a], wy = cy - t.Y[a];
-    long long dx = t.X[b] - t.X[a], dy = t.Y[b] - t.Y[a];
-    long long wd = wx * dx + wy * dy, dd = dx * dx + dy * dy;
+__device__ unsigned long long edge_qdist(const UvTri &t, int k, int cx, int cy, float *param) {
+    int a = k, b = k == 2 ? 0 : k + 1;
+    int wx = cx - t.X[a], wy = cy - t.Y[a];
+    int dx = t.X[b] - t.X[a], dy = t.Y[b] - t.Y[a];
+    long long wd = mulw(wx, dx) + mulw(wy, dy), dd = mulw(dx, dx) + mulw(dy, dy);
     unsigned __int128 num, den;
     if (dd == 0 || wd <= 0) {
-        num = (unsigned __int128)(unsigned long long)(wx * wx + wy * wy);
+        num = (unsigned __int128)(unsigned long long)(mulw(wx, wx) + mulw(wy, wy));
         den = 1;
         *param = 0.f;
     } else if (wd >= dd) {
-        long long ux = cx - t.X[b], uy = cy - t.Y[b];
-        num = (unsigned __int128)(unsigned long long)(ux * ux + uy * uy);
+        int ux = cx - t.X[b], uy = cy - t.Y[b];
+        num = (unsigned __int128)(unsigned long long)(mulw(ux, ux) + mulw(uy, uy));
         den = 1;
         *param = 1.f;
     } else {
-        long long cr = wx * dy - wy * dx;
+        long long cr = mulw(wx, dy) - mulw(wy, dx);
         unsigned long long ac = (unsigned long long)(cr < 0 ? -cr : cr);
         num = (unsigned __int128)ac * ac;
         den = (unsigned __int128)(unsigned long long)dd;
@@ -166,7 +172,7 @@ __device__ unsigned long long edge_qdist(const UvTri &t, int k, long long cx, lo
     return (unsigned long long)((num * 65536u) / den);
 }
 
-__device__ unsigned long long tri_qdist(const UvTri &t, long long cx, long long cy, int *be, float *bp) {
+__device__ unsigned long long tri_qdist(const UvTri &t, int cx, int cy, int *be, float *bp) {
     unsigned long long best = KEY_NONE;
     *be = -1;
     *bp = 0.f;
@@ -178,7 +184,7 @@ __device__ unsigned long long tri_qdist(const UvTri &t, long long cx, long long 
     return best;
 }
 
-__device__ __forceinline__ long long floordiv256(long long a) { return a >= 0 ? a / 256 : -((-a + 255) / 256); }
+__device__ __forceinline__ int floordiv256(int a) { return a >> 8; }  // arithmetic shift = floor
 
 // one warp per face: every texel within one texel of the face's UV bbox
 __global__ void k_raster(const int4 *__restrict__ uvfix, const int4 *__restrict__ lface, int64_t nf, int W, int H,
@@ -189,25 +195,27 @@ __global__ void k_raster(const int4 *__restrict__ uvfix, const int4 *__restrict_
     if (lface[f].w & FACE_INVALID) return;
     UvTri t = load_uvtri(uvfix, f);
     if (t.a2 == 0) return;
-    long long mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
-    long long mny = min(t.Y[0], min(t.Y[1], t.Y[2])), mxy = max(t.Y[0], max(t.Y[1], t.Y[2]));
-    long long x0 = max(0ll, floordiv256(mnx) - 1), x1 = min((long long)W - 1, floordiv256(mxx) + 1);
-    long long y0 = max(0ll, floordiv256(mny) - 1), y1 = min((long long)H - 1, floordiv256(mxy) + 1);
+    int mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
+    int mny = min(t.Y[0], min(t.Y[1], t.Y[2])), mxy = max(t.Y[0], max(t.Y[1], t.Y[2]));
+    int x0 = max(0, floordiv256(mnx) - 1), x1 = min(W - 1, floordiv256(mxx) + 1);
+    int y0 = max(0, floordiv256(mny) - 1), y1 = min(H - 1, floordiv256(mxy) + 1);
     if (x0 > x1 || y0 > y1) return;
-    long long nx = x1 - x0 + 1, cnt = nx * (y1 - y0 + 1);
+    int nx = x1 - x0 + 1;
+    long long cnt = (long long)nx * (y1 - y0 + 1);
     for (long long idx = lane; idx < cnt; idx += 32) {
-        long long x = x0 + idx % nx, y = y0 + idx / nx;
-        long long cx = 256 * x + 128, cy = 256 * y + 128, e[3];
+        int x = x0 + (int)(idx % nx), y = y0 + (int)(idx / nx);
+        int cx = 256 * x + 128, cy = 256 * y + 128;
+        long long e[3];
         unsigned long long key = KEY_NONE;
         if (uv_inside(t, cx, cy, e)) {
             key = (unsigned long long)f;
-        } else if (uv_overlap(t, 256 * x, 256 * y)) {
+        } else if (uv_overlap(t, cx, cy, e)) {
             int be;
             float bp;
             unsigned long long q = tri_qdist(t, cx, cy, &be, &bp);
             if (q != KEY_NONE) key = KEY_CONS | (q << 31) | (unsigned long long)f;
         }
-        if (key != KEY_NONE) atomicMin(&keys[y * W + x], key);
+        if (key != KEY_NONE) atomicMin(&keys[(size_t)y * W + x], key);
     }
 }
 
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
     if (has) {
         int f = (int)(key & 0x7fffffffull);
         UvTri t = load_uvtri(uvfix, f);
-        long long cx = 256 * x + 128, cy = 256 * y + 128;
+        int cx = 256 * (int)x + 128, cy = 256 * (int)y + 128;
         float b[3];
         if (!(key & KEY_CONS)) {
             long long e[3];

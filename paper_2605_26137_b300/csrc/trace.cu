@@ -241,14 +241,211 @@ struct TraceArgs {
     unsigned long long *counters;
 };
 
+// Per-lane traversal state of one ray.
+struct RayState {
+    int job;
+    int texel, face;
+    float b1, b2, sl;
+    int4 fi;
+    float3 d;
+    Ray ray;
+    Best best;
+    uint32_t cur;
+    int sp, steps;
+};
+
+__device__ __forceinline__ const TraceJob &job_of(const TraceArgs &A, int j) {
+    return A.n_jobs > 1 ? A.jobs[j] : A.job0;
+}
+
+__device__ __forceinline__ void setup_ray(const TraceArgs &A, long long r, RayState &S) {
+    int j = 0;
+    long long local = r;
+    if (A.n_jobs > 1) {
+        int lo = 0, hi = A.n_jobs - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (A.job_begin[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        j = lo;
+        local = r - A.job_begin[j];
+    }
+    const TraceJob &J = job_of(A, j);
+    int4 rr = J.rays[local];
+    S.job = j;
+    S.texel = rr.x;
+    S.face = rr.y;
+    S.b1 = __int_as_float(rr.z);
+    S.b2 = __int_as_float(rr.w);
+    S.fi = J.lface[S.face];
+    float3 P0 = f3(J.lpos[S.fi.x]), P1 = f3(J.lpos[S.fi.y]), P2 = f3(J.lpos[S.fi.z]);
+    float3 N0 = f3(J.lnrm[S.fi.x]), N1 = f3(J.lnrm[S.fi.y]), N2 = f3(J.lnrm[S.fi.z]);
+    float3 off = (P1 - P0) * S.b1 + (P2 - P0) * S.b2;
+    float3 sv = N0 + (N1 - N0) * S.b1 + (N2 - N0) * S.b2;
+    S.sl = sqrtf(dot3(sv, sv));
+    S.d = sv * (1.0f / S.sl);
+    S.ray = make_ray(P0, off, S.d);
+    S.best.t = 0.f; S.best.babs = J.max_dist; S.best.rec = 0; S.best.found = false;
+    S.best.U = S.best.V = S.best.W = 0.f; S.best.det = 1.f;
+    S.cur = 0;   // root
+    S.sp = 0;
+    S.steps = 0;
+}
+
+// One traversal step (a node visit or a leaf's triangles); false when done.
+template <int LAYOUT, bool COUNT>
+__device__ __forceinline__ bool step(const TraceArgs &A, const TraceJob &J, RayState &S, uint2 *stack,
+                                     unsigned long long &c_nodes, unsigned long long &c_tris) {
+    Next nx;
+    nx.has = false;
+    nx.ref = 0;
+    nx.dist = 0.f;
+    if (ref_is_leaf(S.cur)) {
+        uint32_t first = ref_first(S.cur);
+        int cnt = ref_count(S.cur);
+        for (int k = 0; k < cnt; ++k) test_tri(S.ray, J.tris, J.tri_ids, first + k, S.best);
+        if (COUNT) c_tris += cnt;
+    } else {
+        if (LAYOUT == AG_BVH_Q8)
+            NodeOps<AG_BVH_Q8>::visit(J.nodes, S.cur, S.ray, S.best.babs, nx, stack, S.sp, A.status);
+        else
+            NodeOps<AG_BVH_F32>::visit(J.nodes, S.cur, S.ray, S.best.babs, nx, stack, S.sp, A.status, J.scene_abs);
+        if (COUNT) ++c_nodes;
+    }
+    if (nx.has) {
+        S.cur = nx.ref;
+    } else {
+        bool done = true;
+        while (S.sp > 0) {
+            uint2 e = stack[--S.sp];
+            if (__uint_as_float(e.y) <= S.best.babs) { S.cur = e.x; done = false; break; }
+        }
+        if (done) return false;
+    }
+    if (++S.steps > A.max_steps) {
+        atomicOr(A.status, AGS_STEP_CAP);
+        return false;
+    }
+    return true;
+}
+
+struct LossAcc {
+    float t, n, c;
+    int job;
+};
+
+__device__ __forceinline__ void flush_loss(const TraceArgs &A, LossAcc &L) {
+    if (L.job >= 0 && L.c > 0.f) {
+        float *la = A.n_jobs > 1 ? A.jobs[L.job].loss_acc : A.job0.loss_acc;
+        atomicAdd(&la[0], L.t);
+        atomicAdd(&la[1], L.n);
+        atomicAdd(&la[2], L.c);
+    }
+    L.t = L.n = L.c = 0.f;
+}
+
+// Shading (forward) or the adjoint of the loss (backward) of a finished ray.
+template <bool BWD>
+__device__ __forceinline__ void finish(const TraceArgs &A, RayState &S, LossAcc &L) {
+    const TraceJob &J = job_of(A, S.job);
+    const bool hit = S.best.found;
+    const float3 d = S.d;
+    float3 nh = make_float3(0.f, 0.f, 1.f);
+    float bA = 0.f, bB = 0.f, bC = 0.f;
+    float4 TA = make_float4(0, 0, 0, 0), TB = TA, TC = TA;
+    float3 nA = make_float3(0, 0, 0), nB = nA, nC = nA;
+    if (hit) {
+        float inv = 1.0f / S.best.det;
+        bA = S.best.U * inv; bB = S.best.V * inv; bC = S.best.W * inv;
+        TA = __ldg(&J.tris[3 * (size_t)S.best.rec]);
+        TB = __ldg(&J.tris[3 * (size_t)S.best.rec + 1]);
+        TC = __ldg(&J.tris[3 * (size_t)S.best.rec + 2]);
+        nA = f3(__ldg(&J.hnormals[__float_as_int(TA.w)]));
+        nB = f3(__ldg(&J.hnormals[__float_as_int(TB.w)]));
+        nC = f3(__ldg(&J.hnormals[__float_as_int(TC.w)]));
+        nh = normalize3(nA * bA + nB * bB + nC * bC);
+    }
+    if (!BWD) {
+        float3 nts = make_float3(0.f, 0.f, 1.f);
+        if (hit && !(S.fi.w & FACE_DEGEN)) {
+            float4 T0 = J.ltan[3 * S.face], T1 = J.ltan[3 * S.face + 1], T2 = J.ltan[3 * S.face + 2];
+            float3 tt = f3(T0) + (f3(T1) - f3(T0)) * S.b1 + (f3(T2) - f3(T0)) * S.b2;
+            tt = normalize3(tt - d * dot3(tt, d));
+            float3 bb = cross3(d, tt) * T0.w;
+            nts = make_float3(dot3(nh, tt), dot3(nh, bb), dot3(nh, d));
+        }
+        J.ntsd[S.texel] = make_float4(nts.x, nts.y, nts.z, hit ? S.best.t : 0.f);
+        J.mask[S.texel] = hit ? 1 : 0;
+        if (J.hit_tri) J.hit_tri[S.texel] = hit ? J.tri_ids[S.best.rec] : -1;
+        if (J.hit_t) J.hit_t[S.texel] = hit ? S.best.t : 0.f;
+    } else if (hit) {
+        // adjoint of t^2 + lambda (1 - nh . d), hit triangle held fixed
+        const float lam = J.lambda;
+        const float t = S.best.t;
+        float3 A3 = f3(TA), B3 = f3(TB), C3 = f3(TC);
+        float3 Nh = cross3(B3 - A3, C3 - A3);
+        float nn = dot3(Nh, Nh), dn = dot3(d, Nh);
+        float3 m = nA * bA + nB * bB + nC * bC;
+        float ml = sqrtf(dot3(m, m));
+        float3 g_nh = d * (-lam);
+        float3 g_m = (g_nh - nh * dot3(nh, g_nh)) * (1.0f / ml);
+        float gbA = dot3(nA, g_m), gbB = dot3(nB, g_m), gbC = dot3(nC, g_m);
+        float inn = 1.0f / nn;
+        float3 g_x = (cross3(Nh, C3 - B3) * gbA + cross3(Nh, A3 - C3) * gbB + cross3(Nh, B3 - A3) * gbC) * inn;
+        float g_tt = 2.f * t + dot3(g_x, d);
+        float3 g_p = g_x - Nh * (g_tt / dn);
+        float3 g_d = nh * (-lam) + g_p * t;
+        float3 g_s = (g_d - d * dot3(d, g_d)) * (1.0f / S.sl);
+        float bw[3] = {1.f - S.b1 - S.b2, S.b1, S.b2};
+        int vid[3] = {S.fi.x, S.fi.y, S.fi.z};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(&J.g_pos[3 * vid[k]], g_p.x * bw[k]);
+            atomicAdd(&J.g_pos[3 * vid[k] + 1], g_p.y * bw[k]);
+            atomicAdd(&J.g_pos[3 * vid[k] + 2], g_p.z * bw[k]);
+            atomicAdd(&J.g_nrm[3 * vid[k]], g_s.x * bw[k]);
+            atomicAdd(&J.g_nrm[3 * vid[k] + 1], g_s.y * bw[k]);
+            atomicAdd(&J.g_nrm[3 * vid[k] + 2], g_s.z * bw[k]);
+        }
+        if (L.job != S.job) {
+            flush_loss(A, L);
+            L.job = S.job;
+        }
+        L.t += t * t;
+        L.n += 1.f - dot3(nh, d);
+        L.c += 1.f;
+    }
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void flush_counters(const TraceArgs &A, unsigned long long c_rays, unsigned long long c_nodes,
+                                               unsigned long long c_tris, unsigned long long c_hits) {
+    if (!COUNT) return;
+    const int lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+        c_nodes += __shfl_xor_sync(0xffffffffu, c_nodes, o);
+        c_tris += __shfl_xor_sync(0xffffffffu, c_tris, o);
+        c_rays += __shfl_xor_sync(0xffffffffu, c_rays, o);
+        c_hits += __shfl_xor_sync(0xffffffffu, c_hits, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.counters[0], c_rays);
+        atomicAdd(&A.counters[1], c_nodes);
+        atomicAdd(&A.counters[2], c_tris);
+        atomicAdd(&A.counters[3], c_hits);
+    }
+}
+
+// Schedule "batch": a warp takes 32 consecutive rays and runs all of them to
+// completion before taking the next 32.
 template <int LAYOUT, bool BWD, bool COUNT>
 __global__ void __launch_bounds__(256) k_trace(TraceArgs A) {
     const int lane = threadIdx.x & 31;
     const long long n_total = *A.n_rays_dev;
     unsigned long long c_nodes = 0, c_tris = 0, c_rays = 0, c_hits = 0;
-    float acc_t = 0.f, acc_n = 0.f, acc_c = 0.f;
-    int acc_job = -1;
+    LossAcc L = {0.f, 0.f, 0.f, -1};
     uint2 stack[STACK];
+    RayState S;
     for (;;) {
         unsigned long long base = 0;
         if (lane == 0) base = atomicAdd(A.ray_counter, 32ull);
@@ -256,159 +453,70 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs A) {
         if ((long long)base >= n_total) break;
         long long r = (long long)base + lane;
         if (r >= n_total) continue;
-        int j = 0;
-        if (A.n_jobs > 1) {
-            int lo = 0, hi = A.n_jobs - 1;
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (A.job_begin[mid] <= r) lo = mid; else hi = mid - 1;
-            }
-            j = lo;
-        }
-        const TraceJob &J = A.n_jobs > 1 ? A.jobs[j] : A.job0;
-        long long local = r - (A.n_jobs > 1 ? A.job_begin[j] : 0);
-        int4 rr = J.rays[local];
-        const int texel = rr.x, face = rr.y;
-        const float b1 = __int_as_float(rr.z), b2 = __int_as_float(rr.w);
-        int4 fi = J.lface[face];
-        float3 P0 = f3(J.lpos[fi.x]), P1 = f3(J.lpos[fi.y]), P2 = f3(J.lpos[fi.z]);
-        float3 N0 = f3(J.lnrm[fi.x]), N1 = f3(J.lnrm[fi.y]), N2 = f3(J.lnrm[fi.z]);
-        float3 off = (P1 - P0) * b1 + (P2 - P0) * b2;
-        float3 s = N0 + (N1 - N0) * b1 + (N2 - N0) * b2;
-        float sl = sqrtf(dot3(s, s));
-        float3 d = s * (1.0f / sl);
-        Ray ray = make_ray(P0, off, d);
-        Best best;
-        best.t = 0.f; best.babs = J.max_dist; best.rec = 0; best.found = false;
-        best.U = best.V = best.W = 0.f; best.det = 1.f;
-        int sp = 0;
-        uint32_t cur = 0;   // root
-        int steps = 0;
+        setup_ray(A, r, S);
         if (COUNT) ++c_rays;
-        for (;;) {
-            Next nx;
-            nx.has = false;
-            nx.ref = 0;
-            nx.dist = 0.f;
-            if (ref_is_leaf(cur)) {
-                uint32_t first = ref_first(cur);
-                int cnt = ref_count(cur);
-                for (int k = 0; k < cnt; ++k) test_tri(ray, J.tris, J.tri_ids, first + k, best);
-                if (COUNT) c_tris += cnt;
-            } else {
-                if (LAYOUT == AG_BVH_Q8)
-                    NodeOps<AG_BVH_Q8>::visit(J.nodes, cur, ray, best.babs, nx, stack, sp, A.status);
-                else
-                    NodeOps<AG_BVH_F32>::visit(J.nodes, cur, ray, best.babs, nx, stack, sp, A.status, J.scene_abs);
-                if (COUNT) ++c_nodes;
+        const TraceJob &J = job_of(A, S.job);
+        while (step<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+        }
+        if (COUNT && S.best.found) ++c_hits;
+        finish<BWD>(A, S, L);
+    }
+    if (BWD) flush_loss(A, L);
+    flush_counters<COUNT>(A, c_rays, c_nodes, c_tris, c_hits);
+}
+
+// Schedule "refill": lanes take new rays as they finish.  When at least
+// REFILL_MIN lanes of the warp are idle (or all are), the idle lanes shade
+// their finished rays and take new ones from the global counter with one
+// warp-aggregated atomic, so shading and setup run for many lanes at once and
+// no lane waits for the slowest ray of a 32-ray batch.
+template <int LAYOUT, bool BWD, bool COUNT>
+__global__ void __launch_bounds__(256) k_trace_refill(TraceArgs A, int refill_min) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long n_total = *A.n_rays_dev;
+    unsigned long long c_nodes = 0, c_tris = 0, c_rays = 0, c_hits = 0;
+    LossAcc L = {0.f, 0.f, 0.f, -1};
+    uint2 stack[STACK];
+    RayState S;
+    bool active = false, pending = false, drained = false;
+    for (;;) {
+        unsigned act = __ballot_sync(0xffffffffu, active);
+        int idle = 32 - __popc(act);
+        if (idle >= refill_min || act == 0) {
+            if (pending) {
+                if (COUNT && S.best.found) ++c_hits;
+                finish<BWD>(A, S, L);
+                pending = false;
             }
-            if (nx.has) {
-                cur = nx.ref;
-            } else {
-                bool done = true;
-                while (sp > 0) {
-                    uint2 e = stack[--sp];
-                    if (__uint_as_float(e.y) <= best.babs) { cur = e.x; done = false; break; }
+            if (!drained) {
+                unsigned want = ~act;
+                unsigned long long base = 0;
+                int leader = __ffs(want) - 1;
+                if (lane == leader) base = atomicAdd(A.ray_counter, (unsigned long long)__popc(want));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if ((long long)base + __popc(want) >= n_total) drained = true;
+                if (!active) {
+                    long long r = (long long)base + __popc(want & lt_mask);
+                    if (r < n_total) {
+                        setup_ray(A, r, S);
+                        if (COUNT) ++c_rays;
+                        active = true;
+                    }
                 }
-                if (done) break;
             }
-            if (++steps > A.max_steps) { atomicOr(A.status, AGS_STEP_CAP); break; }
+            if (__ballot_sync(0xffffffffu, active) == 0) break;
         }
-        const bool hit = best.found;
-        if (COUNT && hit) ++c_hits;
-        float3 nh = make_float3(0.f, 0.f, 1.f);
-        float bA = 0.f, bB = 0.f, bC = 0.f;
-        float4 TA = make_float4(0, 0, 0, 0), TB = TA, TC = TA;
-        if (hit) {
-            float inv = 1.0f / best.det;
-            bA = best.U * inv; bB = best.V * inv; bC = best.W * inv;
-            TA = __ldg(&J.tris[3 * (size_t)best.rec]);
-            TB = __ldg(&J.tris[3 * (size_t)best.rec + 1]);
-            TC = __ldg(&J.tris[3 * (size_t)best.rec + 2]);
-            float3 nA = f3(__ldg(&J.hnormals[__float_as_int(TA.w)]));
-            float3 nB = f3(__ldg(&J.hnormals[__float_as_int(TB.w)]));
-            float3 nC = f3(__ldg(&J.hnormals[__float_as_int(TC.w)]));
-            nh = normalize3(nA * bA + nB * bB + nC * bC);
-        }
-        if (!BWD) {
-            float3 nts = make_float3(0.f, 0.f, 1.f);
-            if (hit && !(fi.w & FACE_DEGEN)) {
-                float4 T0 = J.ltan[3 * face], T1 = J.ltan[3 * face + 1], T2 = J.ltan[3 * face + 2];
-                float3 tt = f3(T0) + (f3(T1) - f3(T0)) * b1 + (f3(T2) - f3(T0)) * b2;
-                tt = normalize3(tt - d * dot3(tt, d));
-                float3 bb = cross3(d, tt) * T0.w;
-                nts = make_float3(dot3(nh, tt), dot3(nh, bb), dot3(nh, d));
+        if (active) {
+            const TraceJob &J = job_of(A, S.job);
+            if (!step<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+                active = false;
+                pending = true;
             }
-            J.ntsd[texel] = make_float4(nts.x, nts.y, nts.z, hit ? best.t : 0.f);
-            J.mask[texel] = hit ? 1 : 0;
-            if (J.hit_tri) J.hit_tri[texel] = hit ? J.tri_ids[best.rec] : -1;
-            if (J.hit_t) J.hit_t[texel] = hit ? best.t : 0.f;
-        } else if (hit) {
-            // adjoint of t^2 + lambda (1 - nh . d), hit triangle held fixed
-            const float lam = J.lambda;
-            const float t = best.t;
-            float3 A3 = f3(TA), B3 = f3(TB), C3 = f3(TC);
-            float3 Nh = cross3(B3 - A3, C3 - A3);
-            float nn = dot3(Nh, Nh), dn = dot3(d, Nh);
-            float3 m = f3(__ldg(&J.hnormals[__float_as_int(TA.w)])) * bA +
-                       f3(__ldg(&J.hnormals[__float_as_int(TB.w)])) * bB +
-                       f3(__ldg(&J.hnormals[__float_as_int(TC.w)])) * bC;
-            float ml = sqrtf(dot3(m, m));
-            float3 g_nh = d * (-lam);
-            float3 g_m = (g_nh - nh * dot3(nh, g_nh)) * (1.0f / ml);
-            float gbA = dot3(f3(__ldg(&J.hnormals[__float_as_int(TA.w)])), g_m);
-            float gbB = dot3(f3(__ldg(&J.hnormals[__float_as_int(TB.w)])), g_m);
-            float gbC = dot3(f3(__ldg(&J.hnormals[__float_as_int(TC.w)])), g_m);
-            float inn = 1.0f / nn;
-            float3 g_x = (cross3(Nh, C3 - B3) * gbA + cross3(Nh, A3 - C3) * gbB + cross3(Nh, B3 - A3) * gbC) * inn;
-            float g_tt = 2.f * t + dot3(g_x, d);
-            float3 g_p = g_x - Nh * (g_tt / dn);
-            float3 g_d = nh * (-lam) + g_p * t;
-            float3 g_s = (g_d - d * dot3(d, g_d)) * (1.0f / sl);
-            float bw[3] = {1.f - b1 - b2, b1, b2};
-            int vid[3] = {fi.x, fi.y, fi.z};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                atomicAdd(&J.g_pos[3 * vid[k]], g_p.x * bw[k]);
-                atomicAdd(&J.g_pos[3 * vid[k] + 1], g_p.y * bw[k]);
-                atomicAdd(&J.g_pos[3 * vid[k] + 2], g_p.z * bw[k]);
-                atomicAdd(&J.g_nrm[3 * vid[k]], g_s.x * bw[k]);
-                atomicAdd(&J.g_nrm[3 * vid[k] + 1], g_s.y * bw[k]);
-                atomicAdd(&J.g_nrm[3 * vid[k] + 2], g_s.z * bw[k]);
-            }
-            if (acc_job != j && acc_job >= 0) {
-                float *la = A.n_jobs > 1 ? A.jobs[acc_job].loss_acc : A.job0.loss_acc;
-                atomicAdd(&la[0], acc_t);
-                atomicAdd(&la[1], acc_n);
-                atomicAdd(&la[2], acc_c);
-                acc_t = acc_n = acc_c = 0.f;
-            }
-            acc_job = j;
-            acc_t += t * t;
-            acc_n += 1.f - dot3(nh, d);
-            acc_c += 1.f;
         }
     }
-    if (BWD && acc_job >= 0) {
-        float *la = A.n_jobs > 1 ? A.jobs[acc_job].loss_acc : A.job0.loss_acc;
-        atomicAdd(&la[0], acc_t);
-        atomicAdd(&la[1], acc_n);
-        atomicAdd(&la[2], acc_c);
-    }
-    if (COUNT) {
-        for (int o = 16; o > 0; o >>= 1) {
-            c_nodes += __shfl_xor_sync(0xffffffffu, c_nodes, o);
-            c_tris += __shfl_xor_sync(0xffffffffu, c_tris, o);
-            c_rays += __shfl_xor_sync(0xffffffffu, c_rays, o);
-            c_hits += __shfl_xor_sync(0xffffffffu, c_hits, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&A.counters[0], c_rays);
-            atomicAdd(&A.counters[1], c_nodes);
-            atomicAdd(&A.counters[2], c_tris);
-            atomicAdd(&A.counters[3], c_hits);
-        }
-    }
+    if (BWD) flush_loss(A, L);
+    flush_counters<COUNT>(A, c_rays, c_nodes, c_tris, c_hits);
 }
 
 template <int LAYOUT, bool BWD, bool COUNT>
@@ -417,13 +525,20 @@ cudaError_t launch_one(const TraceLaunch &L, const TraceArgs &A, cudaStream_t s)
     cudaGetDevice(&dev);
     int block = L.block_size > 0 ? (L.block_size > 256 ? 256 : L.block_size) : 128;
     int bps = L.blocks_per_sm > 0 ? L.blocks_per_sm : 0;
+    const bool refill = L.schedule == AG_SCHED_REFILL;
     if (bps == 0) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<LAYOUT, BWD, COUNT>, block, 0);
+        if (refill)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_refill<LAYOUT, BWD, COUNT>, block, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<LAYOUT, BWD, COUNT>, block, 0);
         bps = occ > 0 ? occ : 1;
     }
     unsigned grid = (unsigned)(device_sm_count(dev) * bps);
-    k_trace<LAYOUT, BWD, COUNT><<<grid, block, 0, s>>>(A);
+    if (refill)
+        k_trace_refill<LAYOUT, BWD, COUNT><<<grid, block, 0, s>>>(A, 8);
+    else
+        k_trace<LAYOUT, BWD, COUNT><<<grid, block, 0, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import AgAssetDesc, AgBakeAux, AgBvhInfo, check, default_opts
 
 _LAYOUTS = {"q8": _lib.AG_BVH_Q8, "f32": _lib.AG_BVH_F32}
-_SCHED = {"auto": _lib.AG_SCHED_AUTO, "thread": _lib.AG_SCHED_THREAD, "warp": _lib.AG_SCHED_WARP}
+_SCHED = {"auto": _lib.AG_SCHED_AUTO, "batch": _lib.AG_SCHED_BATCH, "refill": _lib.AG_SCHED_REFILL}
 
 
 def _stream(stream=None) -> int:
@@ -36,21 +36,27 @@ def _need(t: torch.Tensor, name: str, dtype, shape_tail=None):
     return t
 
 
-def _opts(layout="q8", gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0):
+_COLLAPSE = {"area_count": _lib.AG_COLLAPSE_AREA_COUNT, "area": _lib.AG_COLLAPSE_AREA, "count": _lib.AG_COLLAPSE_COUNT}
+
+
+def _opts(layout="q8", gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
+          collapse="area"):
     return default_opts(bvh_layout=_LAYOUTS[layout], gutter=gutter, disp_fp16=int(bool(disp_fp16)),
                         schedule=_SCHED[schedule] if isinstance(schedule, str) else schedule,
-                        block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps)
+                        block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps,
+                        collapse=_COLLAPSE[collapse])
 
 
 class Bvh:
     """8-wide BVH over a high-poly mesh (owns its device memory)."""
 
-    def __init__(self, verts: torch.Tensor, faces: torch.Tensor, layout: str = "q8", stream=None):
+    def __init__(self, verts: torch.Tensor, faces: torch.Tensor, layout: str = "q8", stream=None,
+                 collapse: str = "area"):
         lib = _lib.load()
         _need(verts, "verts", torch.float32, (3,))
         _need(faces, "faces", torch.int32, (3,))
         h = ctypes.c_void_p()
-        o = _opts(layout=layout)
+        o = _opts(layout=layout, collapse=collapse)
         check(lib.ag_bvh_build(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0],
                                ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self._h = h
