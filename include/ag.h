@@ -63,6 +63,9 @@ enum { AG_BVH_Q8 = 0, AG_BVH_F32 = 1 };
  * surface area x triangle count, or the most triangles. */
 enum { AG_COLLAPSE_AREA = 0, AG_COLLAPSE_AREA_COUNT = 1, AG_COLLAPSE_COUNT = 2 };
 
+/* Ray-list tile shapes (texels), see ag_opts.ray_tile. */
+enum { AG_TILE_8x8 = 0, AG_TILE_16x16 = 1, AG_TILE_32x8 = 2, AG_TILE_4x4 = 3 };
+
 /* Traversal schedules (one ray per thread in both):
  *  AG_SCHED_BATCH  - a warp takes 32 consecutive rays and finishes all of them
  *                    before taking more;
@@ -85,7 +88,9 @@ typedef struct {
     int32_t collapse;    /* ag_bvh_build: child chosen for expansion while collapsing the binary
                             tree into 8-wide nodes: AG_COLLAPSE_AREA (0, default),
                             AG_COLLAPSE_AREA_COUNT or AG_COLLAPSE_COUNT */
-    int32_t reserved[8];
+    int32_t ray_tile;    /* ag_bake*: atlas tile shape that orders the ray list, AG_TILE_*
+                            (a warp's 32 rays come from one tile; default AG_TILE_8x8) */
+    int32_t reserved[7];
 } ag_opts;
 
 /* Optional extra outputs of ag_bake (any member may be NULL). */
@@ -258,6 +263,21 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
 AG_API ag_status ag_vertex_normals_noalloc(const float *d_verts, int64_t n_verts,
                                            const int32_t *d_faces, int64_t n_faces,
                                            float *d_normals, ag_stream_t stream);
+
+/*
+ * ag_autotune - choose the launch configuration of ag_bake for one asset:
+ * every combination of schedule (AG_SCHED_BATCH, AG_SCHED_REFILL), trace
+ * block size (64, 128, 256) and ray tile (AG_TILE_*) is timed with CUDA
+ * events on `stream` over whole bakes of this asset (1 warm-up + 3 timed,
+ * median), and the fastest is written into *inout (schedule, block_size,
+ * blocks_per_sm = 0, ray_tile; other fields are kept).  *best_ms (optional)
+ * receives its median bake time.  Arguments as ag_bake; outputs go to
+ * scratch.  Synchronises `stream`.  Results do not depend on the choice.
+ */
+AG_API ag_status ag_autotune(ag_bvh_t h, const float *d_lverts, const float *d_lnormals,
+                             const float *d_luv, const int32_t *d_lfaces, int64_t n_lverts,
+                             int64_t n_lfaces, int32_t W, int32_t H, float max_dist,
+                             ag_stream_t stream, ag_opts *inout, float *best_ms);
 
 /* Synchronise `stream`, then return and clear the device status word
  * (AG_ERR_TRAVERSAL_LIMIT if any ray since the last call hit a limit, or

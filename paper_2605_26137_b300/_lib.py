@@ -24,6 +24,10 @@ AG_BVH_F32 = 1
 AG_COLLAPSE_AREA = 0
 AG_COLLAPSE_AREA_COUNT = 1
 AG_COLLAPSE_COUNT = 2
+AG_TILE_8x8 = 0
+AG_TILE_16x16 = 1
+AG_TILE_32x8 = 2
+AG_TILE_4x4 = 3
 AG_SCHED_AUTO = -1
 AG_SCHED_BATCH = 0
 AG_SCHED_REFILL = 1
@@ -31,13 +35,14 @@ AG_SCHED_REFILL = 1
 # every symbol include/ag.h declares
 EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
            "ag_batch_plan_create", "ag_batch_plan_launch", "ag_batch_plan_free", "ag_bake_backward",
-           "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc")
+           "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc",
+           "ag_autotune")
 
 
 class AgOpts(ctypes.Structure):
     _fields_ = [("bvh_layout", c_int32), ("gutter", c_int32), ("disp_fp16", c_int32), ("schedule", c_int32),
                 ("block_size", c_int32), ("blocks_per_sm", c_int32), ("max_steps", c_int32),
-                ("collapse", c_int32), ("reserved", c_int32 * 8)]
+                ("collapse", c_int32), ("ray_tile", c_int32), ("reserved", c_int32 * 7)]
 
 
 class AgBakeAux(ctypes.Structure):
@@ -106,6 +111,9 @@ def load():
         lib.ag_bake_backward.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
                                          c_float, c_float, POINTER(AgOpts), c_void_p, c_void_p, c_void_p]
         lib.ag_bake_backward.restype = S
+        lib.ag_autotune.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int32,
+                                    c_int32, c_float, c_void_p, POINTER(AgOpts), POINTER(c_float)]
+        lib.ag_autotune.restype = S
         lib.ag_sync_status.argtypes = [c_void_p]
         lib.ag_sync_status.restype = S
         lib.ag_last_error.argtypes = []

@@ -159,8 +159,8 @@ cudaError_t launch_face_setup(const float *luv, const int32_t *lfaces, int64_t n
 cudaError_t launch_raster(const int4 *uvfix, const int4 *lface, int64_t nf, int W, int H,
                           unsigned long long *keys, cudaStream_t s);
 cudaError_t launch_resolve(const unsigned long long *keys, const int4 *uvfix, int W, int H,
-                           int32_t *face_map, float *aux_bary, int4 *rays, long long *n_rays,
-                           cudaStream_t s);
+                           int ray_tile, int32_t *face_map, float *aux_bary, int4 *rays,
+                           long long *n_rays, cudaStream_t s);
 
 struct TraceLaunch {
     TraceJob job0;              // the job of a single-asset launch (n_jobs == 1)

@@ -120,6 +120,7 @@ ag_status check_opts(const ag_opts &o) {
         return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
     if (o.collapse < AG_COLLAPSE_AREA || o.collapse > AG_COLLAPSE_COUNT)
         return set_error(AG_ERR_INVALID_ARG, "unknown collapse rule");
+    if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
     return AG_OK;
 }
 
@@ -172,12 +173,12 @@ ag_status alloc_asset(Scratch &sc, int64_t nv, int64_t nf, int W, int H, bool ow
 }
 
 ag_status run_prep(const float *lv, const float *ln, const float *luv, const int32_t *lf, int64_t nv, int64_t nf,
-                   int W, int H, float *aux_bary, unsigned *status, AssetScratch &a, cudaStream_t s) {
+                   int W, int H, int ray_tile, float *aux_bary, unsigned *status, AssetScratch &a, cudaStream_t s) {
     AG_CUDA(cudaMemsetAsync(a.n_rays, 0, sizeof(long long) * 2, s));
     AG_CUDA(launch_vertex_normals(lv, lf, nv, nf, ln, a.acc, a.lnrm, a.lpos, a.nscr, s));
     AG_CUDA(launch_face_setup(luv, lf, nf, nv, W, H, a.lpos, a.lnrm, a.lface, a.ltan, a.uvfix, status, s));
     AG_CUDA(launch_raster(a.uvfix, a.lface, nf, W, H, a.keys, s));
-    AG_CUDA(launch_resolve(a.keys, a.uvfix, W, H, a.face, aux_bary, a.rays, a.n_rays, s));
+    AG_CUDA(launch_resolve(a.keys, a.uvfix, W, H, ray_tile, a.face, aux_bary, a.rays, a.n_rays, s));
     return AG_OK;
 }
 
@@ -366,7 +367,9 @@ AG_API ag_status ag_bake(ag_bvh_t h, const float *d_lverts, const float *d_lnorm
     AG_CUDA(sc.alloc((void **)&ray_counter, sizeof(unsigned long long)));
     cudaEvent_t *ev = reinterpret_cast<cudaEvent_t *>(ax.events);
     if (ev) AG_CUDA(cudaEventRecord(ev[0], s));
-    if ((st = run_prep(d_lverts, d_lnormals, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, ax.bary, status, a, s))) return st;
+    if ((st = run_prep(d_lverts, d_lnormals, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, o.ray_tile, ax.bary, status, a,
+                       s)))
+        return st;
     if (ev) AG_CUDA(cudaEventRecord(ev[1], s));
     TraceLaunch L;
     memset(&L, 0, sizeof(L));
@@ -420,11 +423,13 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
     AG_CUDA(cudaMemsetAsync(g_pos, 0, sizeof(float) * 3 * n_lverts, s));
     AG_CUDA(cudaMemsetAsync(g_nrm, 0, sizeof(float) * 3 * n_lverts, s));
     AG_CUDA(cudaMemsetAsync(loss_acc, 0, sizeof(float) * 4, s));
-    if ((st = run_prep(d_lverts, nullptr, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, nullptr, status, a, s))) return st;
+    if ((st = run_prep(d_lverts, nullptr, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, o.ray_tile, nullptr, status, a,
+                       s)))
+        return st;
     TraceLaunch L;
     memset(&L, 0, sizeof(L));
     L.job0 = make_job(h, a, W, H, max_dist, nullptr, nullptr, nullptr);
-    L.job0.g_pos = g_pos;
+    L.job0.g_pos = d_grad ? g_pos : nullptr;   // loss only: no adjoint scatter
     L.job0.g_nrm = g_nrm;
     L.job0.loss_acc = loss_acc;
     L.job0.lambda = lambda;

@@ -103,6 +103,7 @@ ag_status check_opts_batch(const ag_opts &o) {
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 64) return set_error(AG_ERR_INVALID_ARG, "blocks_per_sm out of range");
     if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
     if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_REFILL) return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
+    if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
     return AG_OK;
 }
 
@@ -207,7 +208,7 @@ ag_status enqueue_batch(int n, const ag_asset_desc *d, const ag_opts &o, int lay
         AG_CUDA(launch_face_setup(d[a].luv, d[a].lfaces, d[a].n_lfaces, d[a].n_lverts, d[a].W, d[a].H, x.lpos, x.lnrm,
                                   x.lface, x.ltan, x.uvfix, status, q));
         AG_CUDA(launch_raster(x.uvfix, x.lface, d[a].n_lfaces, d[a].W, d[a].H, x.keys, q));
-        AG_CUDA(launch_resolve(x.keys, x.uvfix, d[a].W, d[a].H, x.face, nullptr, x.rays, x.n_rays, q));
+        AG_CUDA(launch_resolve(x.keys, x.uvfix, d[a].W, d[a].H, o.ray_tile, x.face, nullptr, x.rays, x.n_rays, q));
     }
     AG_CUDA(join_from(s, side, used, es));
     TraceLaunch L;

@@ -219,21 +219,22 @@ __global__ void k_raster(const int4 *__restrict__ uvfix, const int4 *__restrict_
     }
 }
 
-// Texels in 8x8-tile order (row-major tiles, row-major inside a tile), so a
-// warp's 32 consecutive rays come from a 8x4 patch of the atlas.
+// Texels in tile order (row-major tiles of 2^lw x 2^lh texels, row-major
+// inside a tile), so a warp's 32 consecutive rays come from one patch of the
+// atlas; the tile shape is a launch option (ag_opts.ray_tile).
 __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__restrict__ keys,
-                                                 const int4 *__restrict__ uvfix, int W, int H,
+                                                 const int4 *__restrict__ uvfix, int W, int H, int lw, int lh,
                                                  int32_t *__restrict__ face_map, float *__restrict__ aux_bary,
                                                  int4 *__restrict__ rays, long long *__restrict__ n_rays) {
     __shared__ int s_warp[8];
     __shared__ long long s_base;
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     long long g = (long long)blockIdx.x * 256 + tid;
-    long long tile = g >> 6;
-    int within = (int)(g & 63);
-    int ntx = (W + 7) >> 3;
+    long long tile = g >> (lw + lh);
+    int within = (int)(g & ((1ll << (lw + lh)) - 1));
+    int ntx = (W + (1 << lw) - 1) >> lw;
     long long tx = tile % ntx, ty = tile / ntx;
-    long long x = tx * 8 + (within & 7), y = ty * 8 + (within >> 3);
+    long long x = (tx << lw) + (within & ((1 << lw) - 1)), y = (ty << lh) + (within >> lw);
     bool valid = x < W && y < H;
     unsigned long long key = valid ? keys[y * W + x] : KEY_NONE;
     bool has = key != KEY_NONE;
@@ -306,10 +307,22 @@ cudaError_t launch_raster(const int4 *uvfix, const int4 *lface, int64_t nf, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_resolve(const unsigned long long *keys, const int4 *uvfix, int W, int H, int32_t *face_map,
-                           float *aux_bary, int4 *rays, long long *n_rays, cudaStream_t s) {
-    long long ntiles = (long long)((W + 7) / 8) * ((H + 7) / 8);
-    k_resolve<<<grid_for(ntiles * 64, 256), 256, 0, s>>>(keys, uvfix, W, H, face_map, aux_bary, rays, n_rays);
+void ray_tile_shape(int ray_tile, int *lw, int *lh) {
+    switch (ray_tile) {
+        case AG_TILE_16x16: *lw = 4; *lh = 4; break;
+        case AG_TILE_32x8: *lw = 5; *lh = 3; break;
+        case AG_TILE_4x4: *lw = 2; *lh = 2; break;
+        default: *lw = 3; *lh = 3; break;  // AG_TILE_8x8
+    }
+}
+
+cudaError_t launch_resolve(const unsigned long long *keys, const int4 *uvfix, int W, int H, int ray_tile,
+                           int32_t *face_map, float *aux_bary, int4 *rays, long long *n_rays, cudaStream_t s) {
+    int lw, lh;
+    ray_tile_shape(ray_tile, &lw, &lh);
+    long long ntiles = (long long)((W + (1 << lw) - 1) >> lw) * ((H + (1 << lh) - 1) >> lh);
+    k_resolve<<<grid_for(ntiles << (lw + lh), 256), 256, 0, s>>>(keys, uvfix, W, H, lw, lh, face_map, aux_bary, rays,
+                                                                n_rays);
     return cudaGetLastError();
 }
 

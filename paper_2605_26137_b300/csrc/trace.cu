@@ -399,7 +399,7 @@ __device__ __forceinline__ void finish(const TraceArgs &A, RayState &S, LossAcc 
         float bw[3] = {1.f - S.b1 - S.b2, S.b1, S.b2};
         int vid[3] = {S.fi.x, S.fi.y, S.fi.z};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < 3 && J.g_pos; ++k) {
             atomicAdd(&J.g_pos[3 * vid[k]], g_p.x * bw[k]);
             atomicAdd(&J.g_pos[3 * vid[k] + 1], g_p.y * bw[k]);
             atomicAdd(&J.g_pos[3 * vid[k] + 2], g_p.z * bw[k]);

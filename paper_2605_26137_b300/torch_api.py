@@ -39,12 +39,16 @@ def _need(t: torch.Tensor, name: str, dtype, shape_tail=None):
 _COLLAPSE = {"area_count": _lib.AG_COLLAPSE_AREA_COUNT, "area": _lib.AG_COLLAPSE_AREA, "count": _lib.AG_COLLAPSE_COUNT}
 
 
+_TILES = {"8x8": _lib.AG_TILE_8x8, "16x16": _lib.AG_TILE_16x16, "32x8": _lib.AG_TILE_32x8, "4x4": _lib.AG_TILE_4x4}
+
+
 def _opts(layout="q8", gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
-          collapse="area"):
+          collapse="area", ray_tile="8x8"):
     return default_opts(bvh_layout=_LAYOUTS[layout], gutter=gutter, disp_fp16=int(bool(disp_fp16)),
                         schedule=_SCHED[schedule] if isinstance(schedule, str) else schedule,
                         block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps,
-                        collapse=_COLLAPSE[collapse])
+                        collapse=_COLLAPSE[collapse],
+                        ray_tile=_TILES[ray_tile] if isinstance(ray_tile, str) else ray_tile)
 
 
 class Bvh:
@@ -155,7 +159,7 @@ def _ptr(t):
 def bake(bvh: Bvh, low_verts, low_faces, low_uv, W: int, H: int, max_dist: float, *, low_normals=None,
          gutter: int = 2, disp_fp16: bool = True, aux: bool = False, counters: bool = False,
          out: BakeOutputs | None = None, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
-         stream=None, events=None) -> BakeOutputs:
+         stream=None, events=None, ray_tile="8x8") -> BakeOutputs:
     """One bake.  ``aux`` adds float tangent-space normals, raster and hit
     outputs; ``counters`` selects the counting traversal build; ``events``
     (4 torch.cuda.Event) are recorded before the raster, before and after the
@@ -165,7 +169,7 @@ def bake(bvh: Bvh, low_verts, low_faces, low_uv, W: int, H: int, max_dist: float
     if out is None:
         out = alloc_outputs(W, H, low_verts.device, disp_fp16, aux, counters)
     o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
-              blocks_per_sm=blocks_per_sm, max_steps=max_steps)
+              blocks_per_sm=blocks_per_sm, max_steps=max_steps, ray_tile=ray_tile)
     ev = None
     if events is not None:
         if len(events) != 4:
@@ -250,11 +254,11 @@ def _descs(assets, disp_fp16):
 
 
 def bake_batch(assets: list[Asset], *, gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0,
-               stream=None):
+               stream=None, ray_tile="8x8"):
     lib = _lib.load()
     arr = _descs(assets, disp_fp16)
     o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
-              blocks_per_sm=blocks_per_sm)
+              blocks_per_sm=blocks_per_sm, ray_tile=ray_tile)
     check(lib.ag_bake_batch(len(assets), arr, ctypes.byref(o), _stream(stream)))
     return [a.out for a in assets]
 
@@ -263,12 +267,12 @@ class BatchPlan:
     """A batch captured once into a CUDA graph; ``launch`` replays it."""
 
     def __init__(self, assets: list[Asset], *, gutter=2, disp_fp16=True, schedule="auto", block_size=0,
-                 blocks_per_sm=0, stream=None):
+                 blocks_per_sm=0, stream=None, ray_tile="8x8"):
         self._lib = _lib.load()
         self.assets = assets
         arr = _descs(assets, disp_fp16)
         o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
-                  blocks_per_sm=blocks_per_sm)
+                  blocks_per_sm=blocks_per_sm, ray_tile=ray_tile)
         h = ctypes.c_void_p()
         check(self._lib.ag_batch_plan_create(len(assets), arr, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self._h = h

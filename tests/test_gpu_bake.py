@@ -275,3 +275,33 @@ def test_full_size_asset_sampled_parity():
         m = acc / cnt
         assert np.abs(n[y, x] - m / np.linalg.norm(m)).max() < 1e-5
     bvh.free()
+
+
+def test_launch_configurations_give_identical_bakes_and_autotune(tmp_path, monkeypatch):
+    """Schedules, block sizes and ray tiles change only the speed: every
+    configuration produces the same bytes; the autotuner picks one of them
+    and caches it."""
+    import paper_2605_26137_b300 as pb
+    from paper_2605_26137_b300 import autotune
+    a = synth.sdf_asset(5, 40_000, 2_000, 256, 192, n_prims=10)
+    bvh = pb.Bvh(_t(a.high_v), _t(a.high_f))
+    lv, lf, uv = _t(a.low_v), _t(a.low_f), _t(a.low_uv)
+    ref = None
+    for sched in ("batch", "refill"):
+        for tile in ("8x8", "16x16", "32x8", "4x4"):
+            for block in (64, 256):
+                o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, schedule=sched, ray_tile=tile, block_size=block)
+                pb.sync_status()
+                got = (o.normal_rgba8.cpu().numpy(), o.mask.cpu().numpy(), o.disp.cpu().numpy().view(np.uint16))
+                if ref is None:
+                    ref = got
+                for x, y in zip(got, ref):
+                    assert np.array_equal(x, y), (sched, tile, block)
+    monkeypatch.setenv("AGBAKE_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    e = autotune.tune(bvh, lv, lf, uv, a.W, a.H, a.max_dist)
+    assert not e["cached"] and e["ms"] > 0
+    assert e["schedule"] in (0, 1) and e["block_size"] in (64, 128, 256) and e["ray_tile"] in (0, 1, 2, 3)
+    e2 = autotune.tune(bvh, lv, lf, uv, a.W, a.H, a.max_dist)
+    assert e2["cached"] and e2["schedule"] == e["schedule"]
+    o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, **autotune.launch_kwargs(e))
+    assert np.array_equal(o.normal_rgba8.cpu().numpy(), ref[0])
