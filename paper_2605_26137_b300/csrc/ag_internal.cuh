@@ -146,6 +146,10 @@ constexpr int FACE_DEGEN = 1;   // lface.w bit: unreliable UVs -> (0,0,1)
 constexpr int FACE_INVALID = 2; // lface.w bit: dropped (bad UV)
 
 // ------------------------------------------------------------------ launch helpers (defined per .cu)
+// in-place exclusive prefix sum of n unsigned values; *total (device, may be
+// NULL) receives the sum; scratch of scan_scratch_bytes(n)
+size_t scan_scratch_bytes(int64_t n);
+cudaError_t launch_scan_exclusive(unsigned *d, int64_t n, unsigned *total, void *scratch, cudaStream_t s);
 // area-weighted vertex normals (deterministic, exact edge differences);
 // `given` replaces the derived normals (normalised), acc_out [3nv] receives
 // the unnormalised sums, pos [nv] (optional) the positions as float4

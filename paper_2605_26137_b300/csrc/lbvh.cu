@@ -128,25 +128,6 @@ __global__ void k_rs_hist(const unsigned *__restrict__ keys, int64_t n, int shif
     for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
 }
 
-// single-block exclusive scan of m unsigned values (in place)
-__global__ void k_scan_exclusive(unsigned *__restrict__ a, int64_t m) {
-    __shared__ unsigned sums[1024];
-    int t = threadIdx.x, T = blockDim.x;
-    int64_t chunk = (m + T - 1) / T;
-    int64_t b = t * chunk, e = min(m, b + chunk);
-    unsigned s = 0;
-    for (int64_t i = b; i < e; ++i) s += a[i];
-    sums[t] = s;
-    __syncthreads();
-    if (t == 0) {
-        unsigned run = 0;
-        for (int k = 0; k < T; ++k) { unsigned v = sums[k]; sums[k] = run; run += v; }
-    }
-    __syncthreads();
-    unsigned run = sums[t];
-    for (int64_t i = b; i < e; ++i) { unsigned v = a[i]; a[i] = run; run += v; }
-}
-
 __global__ void __launch_bounds__(RS_BLOCK) k_rs_scatter(const unsigned *__restrict__ kin,
                                                          const unsigned *__restrict__ vin,
                                                          unsigned *__restrict__ kout, unsigned *__restrict__ vout,
@@ -448,6 +429,8 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     AG_CUDA(sc.alloc((void **)&k1, sizeof(unsigned) * n));
     AG_CUDA(sc.alloc((void **)&v1, sizeof(unsigned) * n));
     AG_CUDA(sc.alloc((void **)&hist, sizeof(unsigned) * 256 * (size_t)nblocks));
+    void *scan_tmp = nullptr;
+    AG_CUDA(sc.alloc(&scan_tmp, scan_scratch_bytes((int64_t)256 * nblocks)));
     AG_CUDA(sc.alloc((void **)&child, sizeof(int2) * std::max<int64_t>(1, n - 1)));
     AG_CUDA(sc.alloc((void **)&range, sizeof(int2) * std::max<int64_t>(1, n - 1)));
     AG_CUDA(sc.alloc((void **)&parent, sizeof(int) * nbin));
@@ -490,8 +473,7 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
         int shift = pass * 8;
         k_rs_hist<<<nblocks, RS_BLOCK, 0, s>>>(ka, n, shift, hist, nblocks);
         AG_CUDA_LAUNCH("k_rs_hist");
-        k_scan_exclusive<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nblocks);
-        AG_CUDA_LAUNCH("k_scan_exclusive");
+        AG_CUDA(launch_scan_exclusive(hist, (int64_t)256 * nblocks, nullptr, scan_tmp, s));
         k_rs_scatter<<<nblocks, RS_BLOCK, 0, s>>>(ka, va, kb, vb, n, shift, hist, nblocks);
         AG_CUDA_LAUNCH("k_rs_scatter");
         std::swap(ka, kb);

@@ -81,32 +81,12 @@ __global__ void k_gather(const float *__restrict__ V, const int32_t *__restrict_
     }
 }
 
-// single-block exclusive scan of m unsigned values, a[m] receives the total
-__global__ void k_scan_total(unsigned *__restrict__ a, int64_t m) {
-    __shared__ unsigned sums[1024];
-    int t = threadIdx.x, T = blockDim.x;
-    int64_t chunk = (m + T - 1) / T;
-    int64_t b = t * chunk, e = min(m, b + chunk);
-    unsigned s = 0;
-    for (int64_t i = b; i < e; ++i) s += a[i];
-    sums[t] = s;
-    __syncthreads();
-    if (t == 0) {
-        unsigned run = 0;
-        for (int k = 0; k < T; ++k) { unsigned v = sums[k]; sums[k] = run; run += v; }
-        a[m] = run;
-    }
-    __syncthreads();
-    unsigned run = sums[t];
-    for (int64_t i = b; i < e; ++i) { unsigned v = a[i]; a[i] = run; run += v; }
-}
-
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 }  // namespace
 
 size_t vertex_normal_scratch_bytes(int64_t nv, int64_t nf) {
-    return sizeof(unsigned) * (size_t)(2 * nv + 1) + sizeof(int32_t) * (size_t)(3 * nf);
+    return sizeof(unsigned) * (size_t)(2 * nv + 1) + sizeof(int32_t) * (size_t)(3 * nf) + scan_scratch_bytes(nv);
 }
 
 cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, int64_t nf, const float *given,
@@ -114,11 +94,12 @@ cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, 
     unsigned *off = static_cast<unsigned *>(scratch);   // [nv+1]
     unsigned *fill = off + nv + 1;                      // [nv]
     int32_t *list = reinterpret_cast<int32_t *>(fill + nv);  // [3nf]
+    unsigned *scan_tmp = reinterpret_cast<unsigned *>(list + 3 * nf);
     cudaError_t e;
     if (!given) {
         if ((e = cudaMemsetAsync(off, 0, sizeof(unsigned) * (size_t)(2 * nv + 1), s)) != cudaSuccess) return e;
         k_degree<<<grid_for(nf, 256), 256, 0, s>>>(F, nf, nv, off);
-        k_scan_total<<<1, 1024, 0, s>>>(off, nv);
+        if ((e = launch_scan_exclusive(off, nv, off + nv, scan_tmp, s)) != cudaSuccess) return e;
         k_fill<<<grid_for(nf, 256), 256, 0, s>>>(F, nf, nv, off, fill, list);
     }
     k_gather<<<grid_for(nv, 128), 128, 0, s>>>(V, F, nv, off, list, given, acc_out, nrm, pos);
@@ -136,8 +117,11 @@ namespace {
 
 constexpr int64_t NOALLOC_MAX_VERTS = 1 << 17;  // 131,072 vertices
 constexpr int64_t NOALLOC_MAX_FACES = 1 << 18;  // 262,144 triangles
-constexpr size_t NOALLOC_SCRATCH_BYTES =
-    sizeof(unsigned) * (size_t)(2 * NOALLOC_MAX_VERTS + 1) + sizeof(int32_t) * (size_t)(3 * NOALLOC_MAX_FACES);
+// adjacency of vertex_normal_scratch_bytes(NOALLOC_MAX_VERTS, NOALLOC_MAX_FACES): offsets, fill
+// counters, face lists, and the prefix-sum chunk totals (2048 counts per chunk)
+constexpr size_t NOALLOC_SCRATCH_BYTES = sizeof(unsigned) * (size_t)(2 * NOALLOC_MAX_VERTS + 1) +
+                                         sizeof(int32_t) * (size_t)(3 * NOALLOC_MAX_FACES) +
+                                         sizeof(unsigned) * (size_t)((NOALLOC_MAX_VERTS + 2047) / 2048 + 1);
 
 // shared by every call: calls that overlap on the GPU (two streams, or two
 // host threads) race on it
@@ -186,6 +170,8 @@ extern "C" AG_API ag_status ag_vertex_normals_noalloc(const float *d_verts, int6
     void *scratch = nullptr;
     ag_status st = noalloc_scratch_on_current_device(&scratch);
     if (st != AG_OK) return st;
+    if (vertex_normal_scratch_bytes(n_verts, n_faces) > NOALLOC_SCRATCH_BYTES)
+        return set_error(AG_ERR_INVALID_ARG, "ag_vertex_normals_noalloc: mesh exceeds the static scratch");
     // the degree/offset/fill counters are cleared inside (they must start at zero)
     cudaError_t e = launch_vertex_normals(d_verts, d_faces, n_verts, n_faces, nullptr, nullptr,
                                           reinterpret_cast<float4 *>(d_normals), nullptr, scratch,
