@@ -166,6 +166,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The slowest rank's value (replicas run the same work; the job takes as
+    long as its slowest rank)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(rays_per_rank: int, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job Mrays/s: every rank bakes its own replica of the workload."""
+    return rays_per_rank * steps * world / (slowest_ms * 1e-3) / 1e6
+
+
 # --------------------------------------------------------------------------- workload
 
 def make_asset(args, device):
@@ -355,12 +372,8 @@ def main():
     trace_ms = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
     prep_ms = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
     fin_ms = [ev[i][2].elapsed_time(ev[i][3]) for i in range(args.steps)]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = n_rays * args.steps * world / (tot_ms * 1e-3) / 1e6
+    tot_ms = max_over_ranks(sum(step_ms), world, dev)
+    value = job_throughput(n_rays, args.steps, world, tot_ms)
     trace_avg = statistics.mean(trace_ms)
     hbm, peak_kind = peaks()
     achieved = bpr * n_rays / (trace_avg * 1e-3) / 1e9

@@ -200,10 +200,11 @@ __global__ void k_raster(const int4 *__restrict__ uvfix, const int4 *__restrict_
     int x0 = max(0, floordiv256(mnx) - 1), x1 = min(W - 1, floordiv256(mxx) + 1);
     int y0 = max(0, floordiv256(mny) - 1), y1 = min(H - 1, floordiv256(mxy) + 1);
     if (x0 > x1 || y0 > y1) return;
-    int nx = x1 - x0 + 1;
-    long long cnt = (long long)nx * (y1 - y0 + 1);
-    for (long long idx = lane; idx < cnt; idx += 32) {
-        int x = x0 + (int)(idx % nx), y = y0 + (int)(idx / nx);
+    const unsigned nx = (unsigned)(x1 - x0 + 1);
+    const unsigned cnt = nx * (unsigned)(y1 - y0 + 1);   // bbox area <= 16384^2 < 2^32
+    for (unsigned idx = lane; idx < cnt; idx += 32) {
+        unsigned row = idx / nx;
+        int x = x0 + (int)(idx - row * nx), y = y0 + (int)row;
         int cx = 256 * x + 128, cy = 256 * y + 128;
         long long e[3];
         unsigned long long key = KEY_NONE;
@@ -229,20 +230,22 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
     __shared__ int s_warp[8];
     __shared__ long long s_base;
     int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    long long g = (long long)blockIdx.x * 256 + tid;
-    long long tile = g >> (lw + lh);
-    int within = (int)(g & ((1ll << (lw + lh)) - 1));
-    int ntx = (W + (1 << lw) - 1) >> lw;
-    long long tx = tile % ntx, ty = tile / ntx;
-    long long x = (tx << lw) + (within & ((1 << lw) - 1)), y = (ty << lh) + (within >> lw);
+    // texel count <= 16384^2 = 2^28: 32-bit index math throughout
+    const unsigned g = blockIdx.x * 256u + (unsigned)tid;
+    const unsigned tile = g >> (lw + lh);
+    const int within = (int)(g & ((1u << (lw + lh)) - 1u));
+    const unsigned ntx = (unsigned)((W + (1 << lw) - 1) >> lw);
+    const unsigned ty = tile / ntx, tx = tile - ty * ntx;
+    const int x = (int)(tx << lw) + (within & ((1 << lw) - 1)), y = (int)(ty << lh) + (within >> lw);
     bool valid = x < W && y < H;
-    unsigned long long key = valid ? keys[y * W + x] : KEY_NONE;
+    const size_t tix = (size_t)y * W + x;
+    unsigned long long key = valid ? keys[tix] : KEY_NONE;
     bool has = key != KEY_NONE;
     int4 rec = make_int4(0, 0, 0, 0);
     if (has) {
         int f = (int)(key & 0x7fffffffull);
         UvTri t = load_uvtri(uvfix, f);
-        int cx = 256 * (int)x + 128, cy = 256 * (int)y + 128;
+        int cx = 256 * x + 128, cy = 256 * y + 128;
         float b[3];
         if (!(key & KEY_CONS)) {
             long long e[3];
@@ -261,19 +264,19 @@ __global__ void __launch_bounds__(256) k_resolve(const unsigned long long *__res
             b[2] = bb[2];
         }
         b[0] = 1.f - b[1] - b[2];
-        rec = make_int4((int)(y * W + x), f, __float_as_int(b[1]), __float_as_int(b[2]));
+        rec = make_int4((int)tix, f, __float_as_int(b[1]), __float_as_int(b[2]));
         if (aux_bary) {
-            aux_bary[3 * (y * W + x)] = b[0];
-            aux_bary[3 * (y * W + x) + 1] = b[1];
-            aux_bary[3 * (y * W + x) + 2] = b[2];
+            aux_bary[3 * tix] = b[0];
+            aux_bary[3 * tix + 1] = b[1];
+            aux_bary[3 * tix + 2] = b[2];
         }
     }
     if (valid) {
-        face_map[y * W + x] = has ? (int)(key & 0x7fffffffull) : -1;
+        face_map[tix] = has ? (int)(key & 0x7fffffffull) : -1;
         if (aux_bary && !has) {
-            aux_bary[3 * (y * W + x)] = 0.f;
-            aux_bary[3 * (y * W + x) + 1] = 0.f;
-            aux_bary[3 * (y * W + x) + 2] = 0.f;
+            aux_bary[3 * tix] = 0.f;
+            aux_bary[3 * tix + 1] = 0.f;
+            aux_bary[3 * tix + 2] = 0.f;
         }
     }
     unsigned bal = __ballot_sync(0xffffffffu, has);

@@ -1,0 +1,61 @@
+"""Host-side pieces of bench.py: the reference arm end to end on a small
+workload (CPU only), and the multi-rank aggregation under a 2-process gloo
+group (replicas: whole-job rays over the slowest rank's time)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch
+    import torch.distributed as tdist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    tdist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    local_ms = 10.0 + 5.0 * rank          # rank 1 is slower
+    slowest = bench.max_over_ranks(local_ms, world, torch.device("cpu"))
+    value = bench.job_throughput(1000, 4, world, slowest)
+    out[rank] = (slowest, value)
+    tdist.barrier()
+    tdist.destroy_process_group()
+
+
+def test_two_rank_gloo_aggregation():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[0] == res[1]
+    slowest, value = res[0]
+    assert slowest == 15.0
+    assert value == pytest.approx(1000 * 4 * 2 / 15e-3 / 1e6)
+
+
+@pytest.mark.slow
+def test_reference_arm_runs_on_cpu():
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2", "--warmup", "1",
+           "--high-faces", "20000", "--low-faces", "1500", "--res", "256", "--cpu-seconds", "1"]
+    p = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert p.returncode == 0, p.stderr[-2000:]
+    line = json.loads([x for x in p.stdout.splitlines() if x.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "Mrays/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["steps"] == 2 and line["higher_is_better"] is True

@@ -305,3 +305,52 @@ def test_launch_configurations_give_identical_bakes_and_autotune(tmp_path, monke
     assert e2["cached"] and e2["schedule"] == e["schedule"]
     o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, **autotune.launch_kwargs(e))
     assert np.array_equal(o.normal_rgba8.cpu().numpy(), ref[0])
+
+
+def test_empty_and_degenerate_atlases():
+    """No covered texel: UVs outside the atlas, or every face with zero UV
+    area.  The bake still writes every output (neutral normal, alpha 0)."""
+    import paper_2605_26137_b300 as pb
+    a = synth.tiny_asset(0)
+    bvh = pb.Bvh(_t(a.high_v), _t(a.high_f))
+    lv, lf = _t(a.low_v), _t(a.low_f)
+    outside = (a.low_uv * 0.4 + 1.5).astype(np.float32)            # in [1.5, 1.9]: valid, off the atlas
+    flat = np.repeat(a.low_uv[:, :1, :], 3, axis=1).copy()          # zero UV area everywhere
+    for uv in (outside, flat):
+        o = pb.bake(bvh, lv, lf, _t(uv), a.W, a.H, a.max_dist, aux=True)
+        pb.sync_status()
+        rgba = o.normal_rgba8.cpu().numpy()
+        assert (rgba == np.array([128, 128, 255, 0], np.uint8)).all()
+        assert not o.mask.cpu().numpy().any() and not o.disp.cpu().numpy().any()
+        assert int(o.n_rays.item()) == 0 and (o.face.cpu().numpy() == -1).all()
+
+
+@pytest.mark.parametrize("W,H", [(16384, 64), (64, 16384)])
+def test_maximum_atlas_width_and_height(W, H):
+    """The largest atlas dimension the ABI accepts, on a thin atlas."""
+    lv, lf = synth.icosphere(2)
+    hv, hf = synth.sh_displaced_sphere(4, 9)
+    uv = synth.grid_atlas(len(lf), W, H, gutter=1)
+    a = synth.Asset(hv, hf, lv, lf, uv, W, H, 0.15, 2)
+    o = oracle.bake_asset(a)
+    _, g, _ = gpu_bake(a)
+    st = parity.compare(g, o, a.diam, a.gutter)
+    print(st)
+    parity.check(st)
+    assert st["n_ray"] > 10_000
+
+
+@pytest.mark.parametrize("n_high", [1, 2, 3, 4, 9])
+def test_tiny_high_meshes(n_high):
+    """BVHs of one to a few triangles (a root that is itself a leaf)."""
+    lv = np.array([[-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0]], np.float32)
+    lf = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    rng = np.random.default_rng(n_high)
+    hv = (rng.uniform(-1.2, 1.2, size=(3 * n_high, 3)) * [1, 1, 0.05]).astype(np.float32)
+    hf = np.arange(3 * n_high, dtype=np.int32).reshape(-1, 3)
+    uv = synth.grid_atlas(2, 32, 32, 2)
+    a = synth.Asset(hv, hf, lv, lf, uv, 32, 32, 0.5, 2)
+    o = oracle.bake_asset(a, use_bvh=False)
+    _, g, _ = gpu_bake(a)
+    st = parity.compare(g, o, a.diam, a.gutter)
+    parity.check(st)
