@@ -37,6 +37,13 @@ sys.path.insert(0, ROOT)
 METRIC = "Mrays/s & ms per 2048² bake on 2M-tri mesh; batched vs single; bwd/fwd ratio"
 UNIT = "Mrays/s"
 WORKLOAD = "single asset: SDF union of 32 primitives, ~2M-tri high mesh, ~30k-tri low mesh, 2048x2048 grid atlas"
+
+
+def workload_name(args) -> str:
+    if args.high_faces == 2_000_000 and args.low_faces == 30_000 and args.res == 2048:
+        return WORKLOAD
+    return (f"single asset: SDF union of 32 primitives, ~{args.high_faces / 1e6:g}M-tri high mesh, "
+            f"~{args.low_faces / 1e3:g}k-tri low mesh, {args.res}x{args.res} grid atlas")
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -62,6 +69,8 @@ def parse():
     p.add_argument("--profile", action="store_true",
                    help="profiling case for ncu: one BVH build and --steps plain bakes, nothing else")
     p.add_argument("--layout", default="q8", choices=["q8", "f32"])
+    p.add_argument("--error-sample", type=float, default=20000,
+                   help="ray texels compared with the oracle per layout (a value < 1 is a fraction of them)")
     p.add_argument("--collapse", default="area", choices=["area_count", "area", "count"])
     return p.parse_args()
 
@@ -87,16 +96,20 @@ def trace_source_hash():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic(layout_tag: str):
+def recorded_traffic(layout_tag: str, res: int, high_tris: int):
     """DRAM bytes per trace launch from the committed ncu summary, or None if
-    the summary is missing or was taken on a different trace kernel source."""
+    the summary is missing, was taken on a different trace kernel source, or
+    on another workload."""
     path = os.path.join(ROOT, "profiles", "trace_kernel_2048_2M.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     t = re.search(rf"dram_bytes_per_launch_{layout_tag}:\s*([0-9.eE+]+)", txt)
-    if not m or not t or m.group(1) != trace_source_hash():
+    w = re.search(r"workload:\s*(\d+)\s+(\d+)", txt)
+    if not m or not t or not w or m.group(1) != trace_source_hash():
+        return None
+    if int(w.group(1)) != res or int(w.group(2)) != high_tris:
         return None
     return float(t.group(1))
 
@@ -204,7 +217,7 @@ def run_profile(args):
     for _ in range(args.steps):
         pb.bake(bvh, lv, lf, uv, args.res, args.res, a.max_dist, out=out)
     pb.sync_status()
-    print(json.dumps({"profile_case": WORKLOAD, "layout": args.layout, "high_tris": int(len(a.high_f)),
+    print(json.dumps({"profile_case": workload_name(args), "layout": args.layout, "high_tris": int(len(a.high_f)),
                       "bakes": args.steps, "trace_source_hash": trace_source_hash()}))
 
 
@@ -258,7 +271,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "ray_texels": int(len(rays)), "high_tris": int(len(a.high_f)),
+            "config": {"workload": workload_name(args), "ray_texels": int(len(rays)), "high_tris": int(len(a.high_f)),
                        "low_tris": int(len(a.low_f)), "atlas": a.W},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{n} random ray texels of the {len(rays)} per step (FP64 oracle, median-split BVH, "
@@ -382,7 +395,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "high_tris": int(len(a.high_f)), "low_tris": int(len(a.low_f)),
+            "config": {"workload": workload_name(args), "high_tris": int(len(a.high_f)), "low_tris": int(len(a.low_f)),
                        "atlas": W, "ray_texels": n_rays, "max_dist": a.max_dist, "seed": args.seed,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "flushed between steps (512 MB write)", "bvh_layout": "q8",
@@ -398,7 +411,7 @@ def main():
                     "node_bytes": info["node_bytes"], "tri_bytes": info["tri_bytes"], "depth": info["max_depth"]},
             "per_ray": {"nodes": nodes_pr, "tris": tris_pr, "hit_frac": hit_frac, "bytes": bpr},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": recorded_traffic("q8"),
+                         "frac": achieved / hbm, "traffic": recorded_traffic("q8", W, int(len(a.high_f))),
                          "kernel": "k_trace (closest-hit traversal + shading)", "peak_kind": peak_kind},
             "clocks": clocks,
             "gpu_launches": 7 * args.steps}
@@ -434,7 +447,7 @@ def timed(torch, fn, steps, warmup, flush=None):
     return [a.elapsed_time(b) for a, b in ms]
 
 
-def layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, n_sample=20000, seed=7):
+def layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, n_sample=20000.0, seed=7):
     """Max / mean |tangent-space normal - FP64 oracle| over a seeded sample of
     ray texels (ambiguous-closest texels excluded, as in the parity tests)."""
     import oracle
@@ -444,7 +457,8 @@ def layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, n_sample=20000, seed=7):
     face = out.face.cpu().numpy().reshape(-1)
     rays = np.flatnonzero(face >= 0)
     rng = np.random.default_rng(seed)
-    samp = np.sort(rng.choice(rays, size=min(n_sample, len(rays)), replace=False))
+    k = int(n_sample * len(rays)) if n_sample < 1 else int(n_sample)
+    samp = np.sort(rng.choice(rays, size=min(max(k, 1), len(rays)), replace=False))
     o = oracle.bake_asset(a, sample=samp)
     on = o["nts"].reshape(-1, 3)[samp]
     om = o["mask"].reshape(-1)[samp]
@@ -500,8 +514,8 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     res["layout_f32"] = {"ms_per_bake": statistics.mean(f32), "mrays_s": n_rays / statistics.mean(f32) / 1e3,
                          "bytes_per_ray": bytes_per_ray(bf.info()["node_size"], c[1] / c[0], c[2] / c[0], c[3] / c[0]),
                          "node_bytes": bf.info()["node_bytes"], "nodes_per_ray": c[1] / c[0],
-                         "error_vs_oracle": layout_errors(pb, torch, a, bf, lv, lf, uv, W, H)}
-    res["layout_q8_error_vs_oracle"] = layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H)
+                         "error_vs_oracle": layout_errors(pb, torch, a, bf, lv, lf, uv, W, H, args.error_sample)}
+    res["layout_q8_error_vs_oracle"] = layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, args.error_sample)
     bf.free()
     if args.batch_assets > 0:
         res["batch"] = batch_leg(args, pb, torch, dev, flush)
