@@ -65,8 +65,10 @@ def _load():
         lib.or_bvh_free.restype = None
         lib.or_closest_hit.argtypes = [_P, _P, _I64, _P, _P, _P, _D, _P]
         lib.or_closest_hit.restype = _I
+        lib.or_closest_point.argtypes = [_P, _P, _I64, _P, _P, _D, _P]
+        lib.or_closest_point.restype = _I
         lib.or_trace.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                 _I, _I, _D, _D, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P]
+                                 _I, _I, _D, _D, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _I]
         lib.or_trace.restype = _I
         lib.or_encode.argtypes = [_P, _P, _I64, _P]
         lib.or_encode.restype = None
@@ -163,6 +165,23 @@ def closest_hit(V, F, o, d, tmax, bvh: Bvh | None = None):
     return int(out[0]), float(out[1]), out[2:5].copy()
 
 
+def closest_point(V, F, p, rmax, bvh: Bvh | None = None):
+    """Closest point of the triangle mesh to p within distance rmax.
+    Returns (tri, d2, x[3], b[3]) with tri = -1 when nothing is that close."""
+    lib = _load()
+    if bvh is not None:
+        V, F = bvh.V, bvh.F
+    else:
+        V, F = _c(V, np.float32), _c(F, np.int32)
+    p = _c(p, np.float64)
+    out = np.zeros(8, np.float64)
+    lib.or_closest_point(_p(V), _p(F), len(F), bvh.h if bvh is not None else None, _p(p), float(rmax), _p(out))
+    return int(out[0]), float(out[1]), out[2:5].copy(), out[5:8].copy()
+
+
+QUERIES = {"ray": 0, "closest": 1}
+
+
 def encode(nts, filled):
     lib = _load()
     nts = _c(nts, np.float64)
@@ -191,9 +210,12 @@ def default_threads() -> int:
 
 
 def bake(high_v, high_f, low_v, low_f, low_uv, W, H, max_dist, gutter=2, *,
-         diam=None, use_bvh=True, sample=None, nthreads=None, bvh: Bvh | None = None):
+         diam=None, use_bvh=True, sample=None, nthreads=None, bvh: Bvh | None = None, query="ray"):
     """The whole bake in FP64.  With ``sample`` (texel ids), only those texels
-    are traced and dilation is skipped.  Returns a dict of numpy arrays."""
+    are traced and dilation is skipped.  ``query`` is "ray" (the line along
+    the texel normal) or "closest" (the nearest point of the high surface);
+    ``hit_t`` is then the signed ray parameter or the signed distance.
+    Returns a dict of numpy arrays."""
     lib = _load()
     hv = _c(high_v, np.float32)
     hf = _c(high_f, np.int32)
@@ -226,7 +248,8 @@ def bake(high_v, high_f, low_v, low_f, low_uv, W, H, max_dist, gutter=2, *,
                       _p(lv), _p(lf), _p(ln), _p(luv), _p(T), _p(w), _p(dg),
                       _p(face), _p(bary), W, H, float(max_dist), float(diam),
                       _p(texels), len(texels), nth,
-                      _p(mask), _p(nts), _p(disp), _p(hit_tri), _p(hit_t), _p(hit_b), _p(flags))
+                      _p(mask), _p(nts), _p(disp), _p(hit_tri), _p(hit_t), _p(hit_b), _p(flags),
+                      QUERIES[query])
     if rc != 0:
         raise RuntimeError("oracle trace: thread start failed")
     filled = (face.reshape(-1) >= 0).astype(np.uint8)

@@ -13,7 +13,8 @@
  *   4. per ray texel: origin p = sum b_i v_i, direction d = normalize(sum b_i n_i),
  *      the closest hit (minimum |t|, |t| <= max_dist) of the line p + t d
  *      against every high-poly triangle (brute force, or a median-split BVH
- *      that is pinned bit-for-bit to brute force);
+ *      that is pinned bit-for-bit to brute force); or, as Sec. 6.4 words it,
+ *      the closest point of the high surface to p (same two searches);
  *   5. the hit's barycentric smooth normal projected into the texel frame;
  *   6. RGB8 encoding and gutter dilation;
  *   7. the baking loss mean(t^2) + lambda*mean(1 - n_hit . d) over hit texels
@@ -483,16 +484,162 @@ int or_closest_hit(const float *V, const int32_t *F, int64_t nf, void *bvh, cons
     return h.tri >= 0;
 }
 
+/* ------------------------------------------------- 4b. closest-point query
+ * Sec. 6.4 as written: the BVH "locates, for each texel's world-space
+ * position, the closest point on the high-poly surface".  Definition used:
+ * over every high-poly triangle (a closed set) the point x minimising
+ * |x - p|.  A triangle's own closest point is the foot of the perpendicular
+ * from p when the foot lies in the closed triangle, else the nearest of the
+ * clamped projections of p onto its three edges (a zero-area triangle has
+ * only its edges).  Equal distances prefer the lower triangle id.  The
+ * distance filter of Sec. 6.4 keeps |x - p| <= max_dist (inclusive). */
+typedef struct { int tri; double d2; d3 x; double b[3]; } cpt_t;
+
+static double tri_closest(d3 p, d3 A, d3 B, d3 C, d3 *x, double b[3]) {
+    d3 n = cross(sub(B, A), sub(C, A));
+    double nn = dot(n, n);
+    if (nn > 0.0) {
+        double h = dot(sub(p, A), n);
+        d3 f = sub(p, scl(n, h / nn));
+        double ba = dot(cross(sub(C, B), sub(f, B)), n) / nn;
+        double bb = dot(cross(sub(A, C), sub(f, C)), n) / nn;
+        double bc = dot(cross(sub(B, A), sub(f, A)), n) / nn;
+        if (ba >= 0.0 && bb >= 0.0 && bc >= 0.0) {
+            *x = f;
+            b[0] = ba; b[1] = bb; b[2] = bc;
+            return h * h / nn;
+        }
+    }
+    const d3 P[3] = {A, B, C};
+    double best = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        d3 a = P[k], e = sub(P[(k + 1) % 3], a);
+        double ee = dot(e, e), s = ee > 0.0 ? dot(sub(p, a), e) / ee : 0.0;
+        if (s < 0.0) s = 0.0;
+        if (s > 1.0) s = 1.0;
+        d3 y = add(a, scl(e, s));
+        d3 w = sub(p, y);
+        double d2 = dot(w, w);
+        if (d2 < best) {
+            best = d2;
+            *x = y;
+            b[k] = 1.0 - s; b[(k + 1) % 3] = s; b[(k + 2) % 3] = 0.0;
+        }
+    }
+    return best;
+}
+
+static void cp_test(const float *V, const int32_t *F, int tri, d3 p, double r2, cpt_t *best) {
+    d3 x;
+    double b[3];
+    double d2 = tri_closest(p, ldf(V, F[3 * tri]), ldf(V, F[3 * tri + 1]), ldf(V, F[3 * tri + 2]), &x, b);
+    if (d2 > r2) return;
+    if (best->tri >= 0 && (d2 > best->d2 || (d2 == best->d2 && tri > best->tri))) return;
+    best->tri = tri; best->d2 = d2; best->x = x;
+    best->b[0] = b[0]; best->b[1] = b[1]; best->b[2] = b[2];
+}
+
+static double box_d2(const bnode *n, d3 p) {
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double c = comp(p, k), e = 0.0;
+        if (c < n->lo[k]) e = n->lo[k] - c;
+        else if (c > n->hi[k]) e = c - n->hi[k];
+        s += e * e;
+    }
+    return s;
+}
+
+/* a box is skipped only when it lies farther than the bound plus a relative
+ * 1e-9 and an absolute 1e-24, which covers every rounding of the box and
+ * triangle distances: the result is bit for bit that of brute force */
+static int box_beyond(double bd2, double lim) { return bd2 > lim * (1.0 + 1e-9) + 1e-24; }
+
+static void bvh_cp(const obvh *b, d3 p, double r2, cpt_t *best) {
+    if (b->nf == 0) return;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const bnode *n = &b->nodes[stack[--sp]];
+        if (box_beyond(box_d2(n, p), best->tri >= 0 ? best->d2 : r2)) continue;
+        if (n->left < 0) {
+            for (int i = n->first; i < n->first + n->count; ++i) cp_test(b->V, b->F, b->idx[i], p, r2, best);
+        } else {
+            /* nearer child last, so it is popped first */
+            double dl = box_d2(&b->nodes[n->left], p), dr = box_d2(&b->nodes[n->right], p);
+            stack[sp++] = dl <= dr ? n->right : n->left;
+            stack[sp++] = dl <= dr ? n->left : n->right;
+        }
+    }
+}
+
+static void closest_point(const float *V, const int32_t *F, int64_t nf, const obvh *bvh, d3 p, double rmax, cpt_t *best) {
+    best->tri = -1; best->d2 = 0.0; best->x = p; best->b[0] = best->b[1] = best->b[2] = 0.0;
+    double r2 = rmax * rmax;
+    if (bvh) { bvh_cp(bvh, p, r2, best); return; }
+    for (int64_t i = 0; i < nf; ++i) cp_test(V, F, (int)i, p, r2, best);
+}
+
+/* every triangle whose closest point lies within distance r of p */
+typedef void (*cp_visit_fn)(void *ctx, int tri, d3 x, const double b[3]);
+static void cp_range(const float *V, const int32_t *F, int64_t nf, const obvh *bvh, d3 p, double r, cp_visit_fn fn, void *ctx) {
+    double r2 = r * r;
+    if (!bvh) {
+        for (int64_t i = 0; i < nf; ++i) {
+            d3 x; double b[3];
+            if (tri_closest(p, ldf(V, F[3 * i]), ldf(V, F[3 * i + 1]), ldf(V, F[3 * i + 2]), &x, b) <= r2) fn(ctx, (int)i, x, b);
+        }
+        return;
+    }
+    if (bvh->nf == 0) return;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const bnode *n = &bvh->nodes[stack[--sp]];
+        if (box_beyond(box_d2(n, p), r2)) continue;
+        if (n->left < 0) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int t = bvh->idx[i];
+                d3 x; double b[3];
+                if (tri_closest(p, ldf(V, F[3 * t]), ldf(V, F[3 * t + 1]), ldf(V, F[3 * t + 2]), &x, b) <= r2) fn(ctx, t, x, b);
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+}
+
+/* exposed for pin tests: out = {tri, d2, x[3], b[3]} */
+int or_closest_point(const float *V, const int32_t *F, int64_t nf, void *bvh, const double *p, double rmax, double *out) {
+    cpt_t c;
+    closest_point(V, F, nf, (const obvh *)bvh, mk(p[0], p[1], p[2]), rmax, &c);
+    out[0] = c.tri; out[1] = c.d2;
+    out[2] = c.x.x; out[3] = c.x.y; out[4] = c.x.z;
+    out[5] = c.b[0]; out[6] = c.b[1]; out[7] = c.b[2];
+    return c.tri >= 0;
+}
+
 /* ------------------------------------------------- 4-5. trace + shade
- * Per ray texel (Sec. 6.4): ray from the texel's surface point along its
- * interpolated normal, distance filter |t| <= max_dist, barycentric smooth
- * hit normal, projection into the texel tangent frame.  Readings: misses and
- * unreliable (degenerate-UV) texels get (0,0,1); disp = t on a hit, else 0.
+ * Per ray texel (Sec. 6.4): the correspondence on the high surface within the
+ * distance filter, its barycentric smooth normal, the projection into the
+ * texel tangent frame.  Two correspondence queries:
+ *   ray (query 0): the line from the texel's surface point p along its
+ *     interpolated normal d, closest |t| <= max_dist, disp = t;
+ *   closest point (query 1): the point x of the high surface nearest to p,
+ *     |x - p| <= max_dist, disp = |x - p| signed by (x - p) . d (>= 0 is +).
+ * Readings: misses and unreliable (degenerate-UV) texels get (0,0,1);
+ * disp = 0 on a miss.
  * Exception flags (texels where several results are equally correct):
- *   bit0 hit with min barycentric < 1e-5 (near a high-poly edge)
- *   bit1 closest |t| within 1e-5*diam of max_dist
+ *   bit0 ray: hit with min barycentric < 1e-5 (near a high-poly edge)
+ *   bit1 closest |t| or distance within 1e-5*diam of max_dist
  *   bit2 texel centre within 1e-5 texel of an edge of its low face
- *   bit3 a triangle sharing no vertex with the hit lies within 1e-5*diam in |t|
+ *   bit3 ray: a triangle sharing no vertex with the hit lies within
+ *        1e-5*diam in |t|; closest point: another triangle within 1e-7*diam
+ *        of the distance gives a hit normal more than 1e-5 away or, at a
+ *        distance above 5e-7*diam, the other displacement sign; or there
+ *        (x - p) . d is within 1e-7*diam of zero (the sign is a rounding
+ *        decision).  Below 5e-7*diam either sign is within the tolerance.
  */
 typedef struct {
     const float *hv; const int32_t *hf; int64_t nhf; const double *hn; const obvh *bvh;
@@ -502,6 +649,7 @@ typedef struct {
     int W, H; double max_dist, diam;
     const int64_t *texels; int64_t ntex;
     uint8_t *mask; double *nts; double *disp; int32_t *hit_tri; double *hit_t; double *hit_b; uint8_t *flags;
+    int query;
     int nthreads, tid;
 } trace_job;
 
@@ -512,6 +660,26 @@ static double seg_dist_units(double cx, double cy, double ax, double ay, double 
     if (s > 1) s = 1;
     double px = ax + s * dx - cx, py = ay + s * dy - cy;
     return sqrt(px * px + py * py);
+}
+
+/* barycentric smooth normal of the high mesh on triangle tri */
+static d3 hit_normal(const trace_job *j, int tri, const double b[3]) {
+    d3 m = mk(0, 0, 0);
+    for (int k = 0; k < 3; ++k) m = add(m, scl(ldd(j->hn, j->hf[3 * tri + k]), b[k]));
+    return normalize(m);
+}
+
+/* the other triangles near the closest distance (flag bit3) */
+typedef struct { const trace_job *j; int tri; d3 nh, p, d; int pos, sign_matters; int ambiguous; } cp_amb_t;
+
+static void cp_amb_visit(void *ctx, int tri, d3 x, const double b[3]) {
+    cp_amb_t *a = (cp_amb_t *)ctx;
+    if (tri == a->tri || a->ambiguous) return;
+    d3 nh = hit_normal(a->j, tri, b);
+    d3 e = sub(nh, a->nh);
+    double dev = fmax(fabs(e.x), fmax(fabs(e.y), fabs(e.z)));
+    int pos = dot(sub(x, a->p), a->d) >= 0.0;
+    if (dev > 1e-5 || (a->sign_matters && pos != a->pos)) a->ambiguous = 1;
 }
 
 static void trace_one(const trace_job *j, int64_t tex) {
@@ -527,18 +695,42 @@ static void trace_one(const trace_job *j, int64_t tex) {
     }
     d3 d = normalize(s);
     double tol = 1e-5 * j->diam;
-    hit_t h;
-    closest(j->hv, j->hf, j->nhf, j->bvh, p, d, j->max_dist + tol, -1, &h);
     uint8_t fl = 0;
-    int hit = h.tri >= 0 && fabs(h.t) <= j->max_dist;
-    if (h.tri >= 0 && fabs(h.t) >= j->max_dist - tol) fl |= 2;
-    if (hit) {
-        double mb = h.b[0] < h.b[1] ? h.b[0] : h.b[1];
-        if (h.b[2] < mb) mb = h.b[2];
-        if (mb < 1e-5) fl |= 1;
-        hit_t h2;
-        closest(j->hv, j->hf, j->nhf, j->bvh, p, d, fabs(h.t) + tol, h.tri, &h2);
-        if (h2.tri >= 0) fl |= 8;
+    int hit = 0, tri = -1;
+    double disp = 0.0, hb[3] = {0.0, 0.0, 0.0};
+    if (j->query == 0) {
+        hit_t h;
+        closest(j->hv, j->hf, j->nhf, j->bvh, p, d, j->max_dist + tol, -1, &h);
+        hit = h.tri >= 0 && fabs(h.t) <= j->max_dist;
+        if (h.tri >= 0 && fabs(h.t) >= j->max_dist - tol) fl |= 2;
+        if (hit) {
+            double mb = h.b[0] < h.b[1] ? h.b[0] : h.b[1];
+            if (h.b[2] < mb) mb = h.b[2];
+            if (mb < 1e-5) fl |= 1;
+            hit_t h2;
+            closest(j->hv, j->hf, j->nhf, j->bvh, p, d, fabs(h.t) + tol, h.tri, &h2);
+            if (h2.tri >= 0) fl |= 8;
+        }
+        tri = h.tri;
+        disp = h.tri >= 0 ? h.t : 0.0;
+        for (int k = 0; k < 3; ++k) hb[k] = h.tri >= 0 ? h.b[k] : 0.0;
+    } else {
+        cpt_t c;
+        closest_point(j->hv, j->hf, j->nhf, j->bvh, p, j->max_dist + tol, &c);
+        double dist = sqrt(c.d2);
+        hit = c.tri >= 0 && dist <= j->max_dist;
+        if (c.tri >= 0 && dist >= j->max_dist - tol) fl |= 2;
+        if (c.tri >= 0) {
+            double along = dot(sub(c.x, p), d);
+            double tolc = 1e-7 * j->diam;
+            int sign_matters = dist > 5.0 * tolc;
+            cp_amb_t a = {j, c.tri, hit_normal(j, c.tri, c.b), p, d, along >= 0.0, sign_matters, 0};
+            cp_range(j->hv, j->hf, j->nhf, j->bvh, p, dist + tolc, cp_amb_visit, &a);
+            if (a.ambiguous || (sign_matters && fabs(along) <= tolc)) fl |= 8;
+            disp = along >= 0.0 ? dist : -dist;
+        }
+        tri = c.tri;
+        for (int k = 0; k < 3; ++k) hb[k] = c.b[k];
     }
     {
         int x = (int)(tex % j->W), y = (int)(tex / j->W);
@@ -556,17 +748,15 @@ static void trace_one(const trace_job *j, int64_t tex) {
         d3 N = d;
         d3 Tt = normalize(sub(ts, scl(N, dot(ts, N))));
         d3 B = scl(cross(N, Tt), j->wsign[f]);
-        d3 m = mk(0, 0, 0);
-        for (int k = 0; k < 3; ++k) m = add(m, scl(ldd(j->hn, j->hf[3 * h.tri + k]), h.b[k]));
-        d3 nh = normalize(m);
+        d3 nh = hit_normal(j, tri, hb);
         n_ts = mk(dot(nh, Tt), dot(nh, B), dot(nh, N));
     }
     j->mask[tex] = (uint8_t)hit;
     std3(j->nts, tex, n_ts);
-    j->disp[tex] = hit ? h.t : 0.0;
-    j->hit_tri[tex] = hit ? h.tri : -1;
-    j->hit_t[tex] = h.tri >= 0 ? h.t : 0.0;
-    for (int k = 0; k < 3; ++k) j->hit_b[3 * tex + k] = h.tri >= 0 ? h.b[k] : 0.0;
+    j->disp[tex] = hit ? disp : 0.0;
+    j->hit_tri[tex] = hit ? tri : -1;
+    j->hit_t[tex] = tri >= 0 ? disp : 0.0;
+    for (int k = 0; k < 3; ++k) j->hit_b[3 * tex + k] = tri >= 0 ? hb[k] : 0.0;
     j->flags[tex] = fl;
 }
 
@@ -581,13 +771,14 @@ int or_trace(const float *hv, int64_t nhv, const int32_t *hf, int64_t nhf, const
              const double *T, const double *wsign, const uint8_t *degen,
              const int32_t *face, const double *bary, int W, int H, double max_dist, double diam,
              const int64_t *texels, int64_t ntex, int nthreads,
-             uint8_t *mask, double *nts, double *disp, int32_t *hit_tri, double *hit_t, double *hit_b, uint8_t *flags) {
+             uint8_t *mask, double *nts, double *disp, int32_t *hit_tri, double *hit_t, double *hit_b, uint8_t *flags,
+             int query) {
     (void)nhv;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     trace_job base = {hv, hf, nhf, hn, (const obvh *)bvh, lv, lf, ln, luv, T, wsign, degen, face, bary,
                       W, H, max_dist, diam, texels, texels ? ntex : (int64_t)W * H,
-                      mask, nts, disp, hit_tri, hit_t, hit_b, flags, nthreads, 0};
+                      mask, nts, disp, hit_tri, hit_t, hit_b, flags, query, nthreads, 0};
     trace_job jobs[256];
     pthread_t th[256];
     for (int i = 0; i < nthreads; ++i) { jobs[i] = base; jobs[i].tid = i; }
