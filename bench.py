@@ -9,8 +9,10 @@ displacement.  A step is one full bake (UV raster, tangent frames,
 closest-hit traversal with shading, dilation and encoding); the BVH is built
 once per high mesh and timed separately.  The metric is rays per second
 (ray texels baked per second, whole bake) and ms per bake; beside it the
-batched-vs-one-by-one speedup, the backward/forward time ratio and the
-quantised-vs-FP32 BVH comparison.
+batched-vs-one-by-one speedup, the backward/forward time ratio, the
+quantised-vs-FP32 BVH comparison and the closest-point correspondence (Sec.
+6.4 as worded) on the same asset, with its angular difference from the ray
+bake.
 
 --impl reference times the FP64 CPU oracle (the repository's plain,
 deliberately slow reference) on a bounded sample of the same workload.
@@ -69,6 +71,7 @@ def parse():
     p.add_argument("--profile", action="store_true",
                    help="profiling case for ncu: one BVH build and --steps plain bakes, nothing else")
     p.add_argument("--layout", default="q8", choices=["q8", "f32"])
+    p.add_argument("--query", default="ray", choices=["ray", "closest"], help="--profile: correspondence query")
     p.add_argument("--error-sample", type=float, default=20000,
                    help="ray texels compared with the oracle per layout (a value < 1 is a fraction of them)")
     p.add_argument("--collapse", default="area", choices=["area_count", "area", "count"])
@@ -91,9 +94,13 @@ def peaks():
 
 
 def trace_source_hash():
-    """Hash of the traversal kernel's source file (the profiled kernel)."""
-    with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", "trace.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """Hash of the traversal kernel's sources (the profiled kernel and the
+    traversal header it includes)."""
+    h = hashlib.sha256()
+    for name in ("trace.cu", "traverse.cuh"):
+        with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(layout_tag: str, res: int, high_tris: int):
@@ -215,10 +222,10 @@ def run_profile(args):
     bvh = pb.Bvh(hv, hf, layout=args.layout, collapse=args.collapse)
     out = pb.alloc_outputs(args.res, args.res, hv.device)
     for _ in range(args.steps):
-        pb.bake(bvh, lv, lf, uv, args.res, args.res, a.max_dist, out=out)
+        pb.bake(bvh, lv, lf, uv, args.res, args.res, a.max_dist, out=out, query=args.query)
     pb.sync_status()
     print(json.dumps({"profile_case": workload_name(args), "layout": args.layout, "high_tris": int(len(a.high_f)),
-                      "bakes": args.steps, "trace_source_hash": trace_source_hash()}))
+                      "query": args.query, "bakes": args.steps, "trace_source_hash": trace_source_hash()}))
 
 
 def to_dev(a, torch):
@@ -447,11 +454,11 @@ def timed(torch, fn, steps, warmup, flush=None):
     return [a.elapsed_time(b) for a, b in ms]
 
 
-def layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, n_sample=20000.0, seed=7):
+def layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, n_sample=20000.0, seed=7, query="ray"):
     """Max / mean |tangent-space normal - FP64 oracle| over a seeded sample of
     ray texels (ambiguous-closest texels excluded, as in the parity tests)."""
     import oracle
-    out = pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, aux=True)
+    out = pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, aux=True, query=query)
     g = out.normal_ts.cpu().numpy().reshape(-1, 3)
     gm = out.mask.cpu().numpy().reshape(-1)
     face = out.face.cpu().numpy().reshape(-1)
@@ -459,7 +466,7 @@ def layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, n_sample=20000.0, seed=7)
     rng = np.random.default_rng(seed)
     k = int(n_sample * len(rays)) if n_sample < 1 else int(n_sample)
     samp = np.sort(rng.choice(rays, size=min(max(k, 1), len(rays)), replace=False))
-    o = oracle.bake_asset(a, sample=samp)
+    o = oracle.bake_asset(a, sample=samp, query=query)
     on = o["nts"].reshape(-1, 3)[samp]
     om = o["mask"].reshape(-1)[samp]
     ok = (om == gm[samp]) & ((o["flags"].reshape(-1)[samp] & 8) == 0)
@@ -517,9 +524,58 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
                          "error_vs_oracle": layout_errors(pb, torch, a, bf, lv, lf, uv, W, H, args.error_sample)}
     res["layout_q8_error_vs_oracle"] = layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, args.error_sample)
     bf.free()
+    res["closest_point"] = closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush)
     if args.batch_assets > 0:
         res["batch"] = batch_leg(args, pb, torch, dev, flush)
     return res
+
+
+def closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush):
+    """The closest-point correspondence (the paper's wording of Sec. 6.4) on
+    the same asset and BVH: ms per bake and per stage, bytes per query and the
+    roofline of k_closest, error against the FP64 oracle on a sample, and the
+    angle between its tangent-space normals and the ray bake's where both
+    hit."""
+    from paper_2605_26137_b300 import autotune
+    tuned = autotune.tune(bvh, lv, lf, uv, W, H, a.max_dist, force=True, query="closest")
+    lk = autotune.launch_kwargs(tuned)
+    cnt = pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, counters=True, aux=True, query="closest", **lk)
+    pb.sync_status()
+    c = cnt.counters.cpu().numpy().astype(np.float64)
+    n = int(cnt.n_rays.item())
+    bpq = bytes_per_ray(bvh.info()["node_size"], c[1] / c[0], c[2] / c[0], c[3] / c[0])
+    out = pb.alloc_outputs(W, H, dev)
+    steps = max(3, args.steps // 2)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for _ in range(3):
+        pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, query="closest", **lk)
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out, events=ev[i], query="closest", **lk)
+    torch.cuda.synchronize()
+    pb.sync_status()
+    tot = statistics.mean(e[0].elapsed_time(e[3]) for e in ev)
+    tr = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    hbm, peak_kind = peaks()
+    achieved = bpq * n / (tr * 1e-3) / 1e9
+    ray = pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, aux=True)
+    pb.sync_status()
+    rm, cm = ray.mask.cpu().numpy().astype(bool), cnt.mask.cpu().numpy().astype(bool)
+    rn, cn = ray.normal_ts.cpu().numpy(), cnt.normal_ts.cpu().numpy()
+    both = rm & cm
+    ang = np.degrees(np.arccos(np.clip((rn[both] * cn[both]).sum(-1), -1.0, 1.0)))
+    rays = (cnt.face.cpu().numpy() >= 0)
+    return {"ms_per_bake": tot, "mrays_s": n / tot / 1e3, "trace_ms": tr, "trace_mrays_s": n / tr / 1e3,
+            "launch": {k: int(v) for k, v in lk.items()},
+            "per_query": {"nodes": c[1] / c[0], "tris": c[2] / c[0], "hit_frac": c[3] / c[0], "bytes": bpq},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "kernel": "k_closest (closest-point traversal + shading)", "peak_kind": peak_kind},
+            "error_vs_oracle": layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, args.error_sample,
+                                             query="closest"),
+            "vs_ray": {"hit_frac_ray": float(rm[rays].mean()), "hit_frac_closest": float(cm[rays].mean()),
+                       "angle_deg_mean": float(ang.mean()), "angle_deg_median": float(np.median(ang)),
+                       "angle_deg_p99": float(np.percentile(ang, 99)), "texels_compared": int(both.sum())}}
 
 
 def batch_leg(args, pb, torch, dev, flush):

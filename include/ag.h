@@ -73,6 +73,17 @@ enum { AG_TILE_8x8 = 0, AG_TILE_16x16 = 1, AG_TILE_32x8 = 2, AG_TILE_4x4 = 3 };
  *                    least 8 idle lanes), shading deferred to the refill. */
 enum { AG_SCHED_AUTO = -1, AG_SCHED_BATCH = 0, AG_SCHED_REFILL = 1 };
 
+/* Correspondence queries (ag_opts.query):
+ *  AG_QUERY_RAY     - the line from the texel's surface point p along its
+ *                     interpolated normal d, closest |t| <= max_dist (both
+ *                     directions); displacement = t;
+ *  AG_QUERY_CLOSEST - the point x of the high surface nearest to p (Sec. 6.4
+ *                     as worded), |x - p| <= max_dist; displacement = |x - p|
+ *                     signed by (x - p) . d.  Hit normal, filters and encoding
+ *                     are those of the ray query.  One schedule (batch);
+ *                     ag_bake_backward supports the ray query only. */
+enum { AG_QUERY_RAY = 0, AG_QUERY_CLOSEST = 1 };
+
 /* Options.  Zero-initialise then call ag_opts_default, or pass NULL for the
  * defaults. */
 typedef struct {
@@ -90,7 +101,8 @@ typedef struct {
                             AG_COLLAPSE_AREA_COUNT or AG_COLLAPSE_COUNT */
     int32_t ray_tile;    /* ag_bake*: atlas tile shape that orders the ray list, AG_TILE_*
                             (a warp's 32 rays come from one tile; default AG_TILE_8x8) */
-    int32_t reserved[7];
+    int32_t query;       /* ag_bake*, ag_autotune: AG_QUERY_RAY (0, default) or AG_QUERY_CLOSEST */
+    int32_t reserved[6];
 } ag_opts;
 
 /* Optional extra outputs of ag_bake (any member may be NULL). */

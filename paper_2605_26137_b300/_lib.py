@@ -31,6 +31,8 @@ AG_TILE_4x4 = 3
 AG_SCHED_AUTO = -1
 AG_SCHED_BATCH = 0
 AG_SCHED_REFILL = 1
+AG_QUERY_RAY = 0
+AG_QUERY_CLOSEST = 1
 
 # every symbol include/ag.h declares
 EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
@@ -42,7 +44,7 @@ EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_
 class AgOpts(ctypes.Structure):
     _fields_ = [("bvh_layout", c_int32), ("gutter", c_int32), ("disp_fp16", c_int32), ("schedule", c_int32),
                 ("block_size", c_int32), ("blocks_per_sm", c_int32), ("max_steps", c_int32),
-                ("collapse", c_int32), ("ray_tile", c_int32), ("reserved", c_int32 * 7)]
+                ("collapse", c_int32), ("ray_tile", c_int32), ("query", c_int32), ("reserved", c_int32 * 6)]
 
 
 class AgBakeAux(ctypes.Structure):

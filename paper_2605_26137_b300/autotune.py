@@ -26,11 +26,12 @@ def cache_path() -> str:
     return os.environ.get("AGBAKE_AUTOTUNE_CACHE", DEFAULT_CACHE)
 
 
-def bucket_key(bvh, W: int, H: int) -> str:
+def bucket_key(bvh, W: int, H: int, query: str = "ray") -> str:
     info = bvh.info()
     layout = "q8" if info["layout"] == _lib.AG_BVH_Q8 else "f32"
+    q = "" if query == "ray" else f"|{query}"
     return (f"{torch.cuda.get_device_name()}|{layout}|texels~2^{round(math.log2(max(1, W * H)))}"
-            f"|tris~2^{round(math.log2(max(1, info['n_tris'])))}")
+            f"|tris~2^{round(math.log2(max(1, info['n_tris'])))}{q}")
 
 
 def _load(path):
@@ -50,18 +51,19 @@ def _store(path, data):
 
 
 def tune(bvh, low_verts, low_faces, low_uv, W: int, H: int, max_dist: float, *, low_normals=None,
-         force: bool = False, path: str | None = None, stream=None) -> dict:
+         force: bool = False, path: str | None = None, stream=None, query: str = "ray") -> dict:
     """Launch configuration for bake()/BatchPlan: {"schedule", "block_size",
-    "blocks_per_sm", "ray_tile", "ms", "cached"}."""
-    from .torch_api import _check_low, _ptr, _stream
+    "blocks_per_sm", "ray_tile", "ms", "cached"}, for the given query
+    ("ray" or "closest")."""
+    from .torch_api import _QUERY, _check_low, _ptr, _stream
     path = path or cache_path()
-    key = bucket_key(bvh, W, H)
+    key = bucket_key(bvh, W, H, query)
     data = _load(path)
     if key in data and not force:
         return dict(data[key], cached=True)
     _check_low(low_verts, low_faces, low_uv, low_normals)
     lib = _lib.load()
-    o = _lib.default_opts()
+    o = _lib.default_opts(query=_QUERY[query])
     best = ctypes.c_float()
     check(lib.ag_autotune(bvh.handle, low_verts.data_ptr(), _ptr(low_normals), low_uv.data_ptr(),
                           low_faces.data_ptr(), low_verts.shape[0], low_faces.shape[0], W, H, float(max_dist),

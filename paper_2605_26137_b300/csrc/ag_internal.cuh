@@ -178,10 +178,14 @@ struct TraceLaunch {
     unsigned long long *counters;  // non-NULL -> counting build
     int layout;
     int schedule;
+    int query;                  // AG_QUERY_RAY / AG_QUERY_CLOSEST
     int block_size, blocks_per_sm;
     bool backward;
 };
+// ray query (trace.cu); dispatches to launch_closest for AG_QUERY_CLOSEST
 cudaError_t launch_trace(const TraceLaunch &L, cudaStream_t s);
+// closest-point query, forward only (closest.cu)
+cudaError_t launch_closest(const TraceLaunch &L, cudaStream_t s);
 
 cudaError_t launch_finalize(const float4 *ntsd, const int32_t *face_map, int W, int H, int gutter,
                             int disp_fp16, uint8_t *rgba, uint8_t *mask, void *disp,

@@ -121,6 +121,8 @@ ag_status check_opts(const ag_opts &o) {
     if (o.collapse < AG_COLLAPSE_AREA || o.collapse > AG_COLLAPSE_COUNT)
         return set_error(AG_ERR_INVALID_ARG, "unknown collapse rule");
     if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
+    if (o.query != AG_QUERY_RAY && o.query != AG_QUERY_CLOSEST)
+        return set_error(AG_ERR_INVALID_ARG, "query must be AG_QUERY_RAY or AG_QUERY_CLOSEST");
     return AG_OK;
 }
 
@@ -382,6 +384,7 @@ AG_API ag_status ag_bake(ag_bvh_t h, const float *d_lverts, const float *d_lnorm
     L.counters = reinterpret_cast<unsigned long long *>(ax.counters);
     L.layout = h->layout;
     L.schedule = pick_schedule(o);
+    L.query = o.query;
     L.block_size = o.block_size;
     L.blocks_per_sm = o.blocks_per_sm;
     L.backward = false;
@@ -406,6 +409,7 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
     if (!(lambda >= 0.f) || !(lambda < 3.0e38f)) return set_error(AG_ERR_INVALID_ARG, "lambda must be finite and >= 0");
     ag_opts o = resolve_opts(opts);
     if ((st = check_opts(o))) return st;
+    if (o.query != AG_QUERY_RAY) return set_error(AG_ERR_INVALID_ARG, "ag_bake_backward supports AG_QUERY_RAY only");
     cudaStream_t s = (cudaStream_t)stream;
     unsigned *status = device_status_word(h->device);
     if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
@@ -440,6 +444,7 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = h->layout;
     L.schedule = pick_schedule(o);
+    L.query = AG_QUERY_RAY;
     L.block_size = o.block_size;
     L.blocks_per_sm = o.blocks_per_sm;
     L.backward = true;

@@ -33,7 +33,8 @@ extern "C" AG_API ag_status ag_autotune(ag_bvh_t h, const float *d_lverts, const
     ag_opts best = *inout;
     float best_t = 3.0e38f;
     ag_status st = AG_OK;
-    for (int si = 0; si < 2 && st == AG_OK; ++si)
+    const int n_sched = inout->query == AG_QUERY_CLOSEST ? 1 : 2;   // the closest-point query has one schedule
+    for (int si = 0; si < n_sched && st == AG_OK; ++si)
         for (int bi = 0; bi < 3 && st == AG_OK; ++bi)
             for (int ti = 0; ti < 4 && st == AG_OK; ++ti) {
                 ag_opts o = *inout;

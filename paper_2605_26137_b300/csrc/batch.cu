@@ -104,6 +104,8 @@ ag_status check_opts_batch(const ag_opts &o) {
     if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
     if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_REFILL) return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
     if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
+    if (o.query != AG_QUERY_RAY && o.query != AG_QUERY_CLOSEST)
+        return set_error(AG_ERR_INVALID_ARG, "query must be AG_QUERY_RAY or AG_QUERY_CLOSEST");
     return AG_OK;
 }
 
@@ -230,6 +232,7 @@ ag_status enqueue_batch(int n, const ag_asset_desc *d, const ag_opts &o, int lay
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = layout;
     L.schedule = o.schedule == AG_SCHED_AUTO ? AG_SCHED_BATCH : o.schedule;
+    L.query = o.query;
     L.block_size = o.block_size;
     L.blocks_per_sm = o.blocks_per_sm;
     L.backward = false;

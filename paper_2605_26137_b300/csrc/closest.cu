@@ -1,0 +1,354 @@
+// Closest-point correspondence (Sec. 6.4 as worded: the BVH "locates, for
+// each texel's world-space position, the closest point on the high-poly
+// surface and retrieves its interpolated smooth normal via barycentric
+// weighting"), followed by the same distance filter, UV-reliability filter and
+// tangent-space shading as the ray query.
+//
+// One persistent launch per ray list; a warp takes 32 consecutive texels of
+// the tile-ordered list.  Per texel:
+//   - query point p = v0 + b1 (v1 - v0) + b2 (v2 - v0), kept as (v0, offset)
+//     so triangle vertices are taken relative to p with two roundings;
+//   - branch and bound over the 8-wide BVH: a child is entered only when the
+//     distance from p to its box (decoded exactly as built, shrunk by the
+//     rounding slack of the decode and of p, so never overestimated) is within
+//     the current best distance, the nearest child first; the bound starts at
+//     the distance filter max_dist (inclusive);
+//   - per triangle, the closest point by Voronoi-region classification
+//     (Ericson, Real-Time Collision Detection, 2005, Sec. 5.1.5): vertex,
+//     edge or face region from six dot products, barycentrics from the
+//     region's closed form; in the face region the point itself is the foot
+//     of the perpendicular, ((a . n) / (n . n)) n with n = (b - a) x (c - a),
+//     which keeps the distance accurate to a few FP32 ulps of the vertex
+//     offsets where the barycentric numerators cancel;
+//   - ties in squared distance prefer the lower original triangle id;
+//   - displacement = distance signed by (x - p) . d (d the texel normal,
+//     zero counts as +).
+#include "traverse.cuh"
+
+namespace ag {
+namespace {
+
+constexpr float LIM_REL = 1.0000010f;  // 1 + 2^-20: slack on squared-distance bounds
+
+struct PBest {
+    float d2;          // squared distance of the best point (or max_dist^2 before the first)
+    float bA, bB, bC;  // its barycentrics
+    float3 x;          // the point, relative to p
+    uint32_t rec;
+    bool found;
+};
+
+struct PointState {
+    int job;
+    int texel, face;
+    float b1, b2;
+    int4 fi;
+    float3 d;          // unit texel normal
+    float3 base, off;  // p = base + off
+    float3 p;          // p rounded to FP32 (box tests)
+    PBest best;
+    uint32_t cur;
+    int sp, steps;
+};
+
+// vertex relative to p: (v - base) - off
+__device__ __forceinline__ float3 rel(const PointState &S, float4 v) {
+    return make_float3(__fsub_rn(__fsub_rn(v.x, S.base.x), S.off.x), __fsub_rn(__fsub_rn(v.y, S.base.y), S.off.y),
+                       __fsub_rn(__fsub_rn(v.z, S.base.z), S.off.z));
+}
+
+// Closest point of triangle (a, b, c) to the origin, by Voronoi region:
+// barycentrics (u, v, w); returns REG_NONE for a triangle of zero area whose
+// region tests fall through (its edges belong to neighbouring triangles as
+// well), REG_FACE when the point is interior.
+enum { REG_NONE = 0, REG_EDGE = 1, REG_FACE = 2 };
+
+__device__ __forceinline__ int tri_closest(float3 a, float3 b, float3 c, float &u, float &v, float &w) {
+    float3 ab = b - a, ac = c - a;
+    float d1 = -dot3(ab, a), d2 = -dot3(ac, a);
+    if (d1 <= 0.f && d2 <= 0.f) { u = 1.f; v = 0.f; w = 0.f; return REG_EDGE; }
+    float d3 = -dot3(ab, b), d4 = -dot3(ac, b);
+    if (d3 >= 0.f && d4 <= d3) { u = 0.f; v = 1.f; w = 0.f; return REG_EDGE; }
+    float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+        float den = d1 - d3;
+        v = den > 0.f ? d1 / den : 0.f;
+        u = 1.f - v; w = 0.f;
+        return REG_EDGE;
+    }
+    float d5 = -dot3(ab, c), d6 = -dot3(ac, c);
+    if (d6 >= 0.f && d5 <= d6) { u = 0.f; v = 0.f; w = 1.f; return REG_EDGE; }
+    float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        float den = d2 - d6;
+        w = den > 0.f ? d2 / den : 0.f;
+        u = 1.f - w; v = 0.f;
+        return REG_EDGE;
+    }
+    float va = d3 * d6 - d5 * d4;
+    float e43 = d4 - d3, e56 = d5 - d6;
+    if (va <= 0.f && e43 >= 0.f && e56 >= 0.f) {
+        float den = e43 + e56;
+        w = den > 0.f ? e43 / den : 0.f;
+        v = 1.f - w; u = 0.f;
+        return REG_EDGE;
+    }
+    float den = va + vb + vc;   // = |ab x ac|^2 in exact arithmetic
+    if (!(den > 0.f)) return REG_NONE;
+    float inv = 1.0f / den;
+    v = vb * inv;
+    w = vc * inv;
+    u = 1.f - v - w;
+    return REG_FACE;
+}
+
+__device__ __forceinline__ void test_tri(PointState &S, const float4 *__restrict__ tris,
+                                         const int32_t *__restrict__ tri_ids, uint32_t rec) {
+    float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
+    float3 a = rel(S, A), b = rel(S, B), c = rel(S, C);
+    float u, v, w;
+    const int reg = tri_closest(a, b, c, u, v, w);
+    if (reg == REG_NONE) return;
+    float3 x;
+    if (reg == REG_FACE) {
+        float3 n = cross3(b - a, c - a);
+        float nn = dot3(n, n);
+        if (!(nn > 0.f)) return;
+        x = n * (dot3(a, n) / nn);
+    } else {
+        x = a * u + b * v + c * w;
+    }
+    float d2 = dot3(x, x);
+    if (!(d2 <= S.best.d2)) return;
+    if (S.best.found && d2 == S.best.d2 && tri_ids[rec] >= tri_ids[S.best.rec]) return;
+    S.best.d2 = d2; S.best.bA = u; S.best.bB = v; S.best.bC = w; S.best.x = x; S.best.rec = rec; S.best.found = true;
+}
+
+template <int LAYOUT>
+struct PointNode;
+
+// 80-byte quantised node.  Child planes decode as fmaf(q, 2^e, origin), the
+// arithmetic the build verified to enclose the exact child box; here the
+// origin is taken relative to p first, and every distance component is
+// shrunk by 2^-21 (|origin| + |p| + 255 * 2^e).  The roundings on the way
+// (p, origin - p, the slack subtraction, the FMA, and the half ulp by which
+// the build's rounded decode may exceed the exact plane) sum to at most
+// 2^-24 (4 |origin| + 4 |p| + 510 * 2^e), half of that slack.
+template <>
+struct PointNode<AG_BVH_Q8> {
+    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, float3 p, float lim, Next &nx,
+                                                 uint2 *stack, int &sp, unsigned *status, float) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(static_cast<const QNode *>(nodes) + idx);
+        uint4 w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2), w3 = __ldg(q + 3), w4 = __ldg(q + 4);
+        float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
+        float sx = __uint_as_float((w0.w & 0xffu) << 23);
+        float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
+        float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
+        float rx = ox - p.x, ry = oy - p.y, rz = oz - p.z;
+        float ex = EPS_REL * (fabsf(ox) + fabsf(p.x) + 255.f * sx);
+        float ey = EPS_REL * (fabsf(oy) + fabsf(p.y) + 255.f * sy);
+        float ez = EPS_REL * (fabsf(oz) + fabsf(p.z) + 255.f * sz);
+        // lo - p - e  and  p - hi - e  as one FMA each
+        float blx = rx - ex, bly = ry - ey, blz = rz - ez;
+        float bhx = -rx - ex, bhy = -ry - ey, bhz = -rz - ez;
+        uint32_t child_base = w1.x, tri_base = w1.y;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int k = c & 3;
+            const bool hi = c >= 4;
+            uint32_t m = ((hi ? w1.w : w1.z) >> (8 * k)) & 0xffu;
+            float gx = fmaxf(fmaxf(__fmaf_rn(byte_f(hi ? w2.y : w2.x, k), sx, blx),
+                                   __fmaf_rn(byte_f(hi ? w3.w : w3.z, k), -sx, bhx)), 0.f);
+            float gy = fmaxf(fmaxf(__fmaf_rn(byte_f(hi ? w2.w : w2.z, k), sy, bly),
+                                   __fmaf_rn(byte_f(hi ? w4.y : w4.x, k), -sy, bhy)), 0.f);
+            float gz = fmaxf(fmaxf(__fmaf_rn(byte_f(hi ? w3.y : w3.x, k), sz, blz),
+                                   __fmaf_rn(byte_f(hi ? w4.w : w4.z, k), -sz, bhz)), 0.f);
+            float g2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, gz * gz));
+            if (m != 0 && g2 <= lim) offer(child_ref(m, child_base, tri_base), g2, nx, stack, sp, status);
+        }
+    }
+};
+
+// 208-byte node with exact FP32 child boxes; the slack per axis is
+// 2^-21 (scene bound + |p|).
+template <>
+struct PointNode<AG_BVH_F32> {
+    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, float3 p, float lim, Next &nx,
+                                                 uint2 *stack, int &sp, unsigned *status, float scene_abs) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(static_cast<const FNode *>(nodes) + idx);
+        uint4 h = __ldg(q);
+        uint32_t child_base = h.x, tri_base = h.y;
+        float ex = EPS_REL * (scene_abs + fabsf(p.x));
+        float ey = EPS_REL * (scene_abs + fabsf(p.y));
+        float ez = EPS_REL * (scene_abs + fabsf(p.z));
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            uint4 lx = __ldg(q + 1 + half), ly = __ldg(q + 3 + half), lz = __ldg(q + 5 + half);
+            uint4 hx = __ldg(q + 7 + half), hy = __ldg(q + 9 + half), hz = __ldg(q + 11 + half);
+            const uint32_t LX[4] = {lx.x, lx.y, lx.z, lx.w}, LY[4] = {ly.x, ly.y, ly.z, ly.w}, LZ[4] = {lz.x, lz.y, lz.z, lz.w};
+            const uint32_t HX[4] = {hx.x, hx.y, hx.z, hx.w}, HY[4] = {hy.x, hy.y, hy.z, hy.w}, HZ[4] = {hz.x, hz.y, hz.z, hz.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint32_t m = ((half ? h.w : h.z) >> (8 * k)) & 0xffu;
+                float gx = fmaxf(fmaxf(__uint_as_float(LX[k]) - p.x, p.x - __uint_as_float(HX[k])) - ex, 0.f);
+                float gy = fmaxf(fmaxf(__uint_as_float(LY[k]) - p.y, p.y - __uint_as_float(HY[k])) - ey, 0.f);
+                float gz = fmaxf(fmaxf(__uint_as_float(LZ[k]) - p.z, p.z - __uint_as_float(HZ[k])) - ez, 0.f);
+                float g2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, gz * gz));
+                if (m != 0 && g2 <= lim) offer(child_ref(m, child_base, tri_base), g2, nx, stack, sp, status);
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ void setup_point(const TraceArgs &A, long long r, PointState &S) {
+    int j = 0;
+    long long local = r;
+    if (A.n_jobs > 1) {
+        int lo = 0, hi = A.n_jobs - 1;
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (A.job_begin[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        j = lo;
+        local = r - A.job_begin[j];
+    }
+    const TraceJob &J = job_of(A, j);
+    int4 rr = J.rays[local];
+    S.job = j;
+    S.texel = rr.x;
+    S.face = rr.y;
+    S.b1 = __int_as_float(rr.z);
+    S.b2 = __int_as_float(rr.w);
+    S.fi = J.lface[S.face];
+    float3 P0 = f3(J.lpos[S.fi.x]), P1 = f3(J.lpos[S.fi.y]), P2 = f3(J.lpos[S.fi.z]);
+    float3 N0 = f3(J.lnrm[S.fi.x]), N1 = f3(J.lnrm[S.fi.y]), N2 = f3(J.lnrm[S.fi.z]);
+    S.base = P0;
+    S.off = (P1 - P0) * S.b1 + (P2 - P0) * S.b2;
+    S.p = P0 + S.off;
+    float3 sv = N0 + (N1 - N0) * S.b1 + (N2 - N0) * S.b2;
+    S.d = sv * (1.0f / sqrtf(dot3(sv, sv)));
+    S.best.d2 = J.max_dist * J.max_dist;
+    S.best.bA = S.best.bB = S.best.bC = 0.f;
+    S.best.x = make_float3(0.f, 0.f, 0.f);
+    S.best.rec = 0;
+    S.best.found = false;
+    S.cur = 0;
+    S.sp = 0;
+    S.steps = 0;
+}
+
+template <int LAYOUT, bool COUNT>
+__device__ __forceinline__ bool step_point(const TraceArgs &A, const TraceJob &J, PointState &S, uint2 *stack,
+                                           unsigned long long &c_nodes, unsigned long long &c_tris) {
+    Next nx;
+    nx.has = false;
+    nx.ref = 0;
+    nx.dist = 0.f;
+    if (ref_is_leaf(S.cur)) {
+        uint32_t first = ref_first(S.cur);
+        int cnt = ref_count(S.cur);
+        for (int k = 0; k < cnt; ++k) test_tri(S, J.tris, J.tri_ids, first + k);
+        if (COUNT) c_tris += cnt;
+    } else {
+        PointNode<LAYOUT>::visit(J.nodes, S.cur, S.p, S.best.d2 * LIM_REL, nx, stack, S.sp, A.status, J.scene_abs);
+        if (COUNT) ++c_nodes;
+    }
+    if (nx.has) {
+        S.cur = nx.ref;
+    } else {
+        bool done = true;
+        const float lim = S.best.d2 * LIM_REL;
+        while (S.sp > 0) {
+            uint2 e = stack[--S.sp];
+            if (__uint_as_float(e.y) <= lim) { S.cur = e.x; done = false; break; }
+        }
+        if (done) return false;
+    }
+    if (++S.steps > A.max_steps) {
+        atomicOr(A.status, AGS_STEP_CAP);
+        return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void finish_point(const TraceArgs &A, const PointState &S) {
+    const TraceJob &J = job_of(A, S.job);
+    const bool hit = S.best.found;
+    float3 nh = make_float3(0.f, 0.f, 1.f);
+    float disp = 0.f;
+    int hit_id = -1;
+    if (hit) {
+        const size_t r3 = 3 * (size_t)S.best.rec;
+        float3 nA = f3(__ldg(&J.hnormals[__float_as_int(__ldg(&J.tris[r3]).w)]));
+        float3 nB = f3(__ldg(&J.hnormals[__float_as_int(__ldg(&J.tris[r3 + 1]).w)]));
+        float3 nC = f3(__ldg(&J.hnormals[__float_as_int(__ldg(&J.tris[r3 + 2]).w)]));
+        nh = normalize3(nA * S.best.bA + nB * S.best.bB + nC * S.best.bC);
+        float dist = sqrtf(S.best.d2);
+        disp = dot3(S.best.x, S.d) >= 0.f ? dist : -dist;
+        hit_id = J.tri_ids[S.best.rec];
+    }
+    store_forward(J, S.texel, S.face, S.fi, S.b1, S.b2, S.d, hit, nh, disp, hit_id);
+}
+
+template <int LAYOUT, bool COUNT>
+__global__ void __launch_bounds__(256) k_closest(TraceArgs A) {
+    const int lane = threadIdx.x & 31;
+    const long long n_total = *A.n_rays_dev;
+    unsigned long long c_nodes = 0, c_tris = 0, c_rays = 0, c_hits = 0;
+    uint2 stack[STACK];
+    PointState S;
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(A.ray_counter, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= n_total) break;
+        long long r = (long long)base + lane;
+        if (r >= n_total) continue;
+        setup_point(A, r, S);
+        if (COUNT) ++c_rays;
+        const TraceJob &J = job_of(A, S.job);
+        while (step_point<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+        }
+        if (COUNT && S.best.found) ++c_hits;
+        finish_point(A, S);
+    }
+    flush_counters<COUNT>(A, c_rays, c_nodes, c_tris, c_hits);
+}
+
+template <int LAYOUT, bool COUNT>
+cudaError_t launch_one(const TraceLaunch &L, const TraceArgs &A, cudaStream_t s) {
+    int dev;
+    cudaGetDevice(&dev);
+    int block = L.block_size > 0 ? (L.block_size > 256 ? 256 : L.block_size) : 128;
+    int bps = L.blocks_per_sm;
+    if (bps <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_closest<LAYOUT, COUNT>, block, 0);
+        bps = occ > 0 ? occ : 1;
+    }
+    unsigned grid = (unsigned)(device_sm_count(dev) * bps);
+    k_closest<LAYOUT, COUNT><<<grid, block, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_closest(const TraceLaunch &L, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(L.ray_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    TraceArgs A;
+    A.job0 = L.job0;
+    A.jobs = L.jobs;
+    A.job_begin = L.job_begin;
+    A.n_jobs = L.n_jobs;
+    A.n_rays_dev = L.n_rays_dev;
+    A.ray_counter = L.ray_counter;
+    A.status = L.status;
+    A.max_steps = L.max_steps;
+    A.counters = L.counters;
+    const bool cnt = L.counters != nullptr;
+    if (L.layout == AG_BVH_Q8) return cnt ? launch_one<AG_BVH_Q8, true>(L, A, s) : launch_one<AG_BVH_Q8, false>(L, A, s);
+    return cnt ? launch_one<AG_BVH_F32, true>(L, A, s) : launch_one<AG_BVH_F32, false>(L, A, s);
+}
+
+}  // namespace ag

@@ -21,13 +21,10 @@
 //     counts as inside;
 //   - ties: equal |t| prefers t >= 0, equal t the lower original id.
 // The backward variant replaces the shading with the adjoint of the loss.
-#include "ag_internal.cuh"
+#include "traverse.cuh"
 
 namespace ag {
 namespace {
-
-constexpr int STACK = 64;
-constexpr float EPS_REL = 4.76837158203125e-07f;  // 2^-21: widening per unit of coordinate magnitude
 
 struct Ray {
     // exact-origin triangle test: permuted axes, shear, origin as base + offset
@@ -114,37 +111,6 @@ __device__ __forceinline__ void test_tri(const Ray &r, const float4 *__restrict_
     b.t = t; b.babs = at; b.rec = rec; b.U = U; b.V = V; b.W = W; b.det = det; b.found = true;
 }
 
-// byte k of w as an exact float: 2^23 + byte in the bits, minus 2^23
-__device__ __forceinline__ float byte_f(uint32_t w, int k) {
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (unsigned)k)) - 8388608.0f;
-}
-
-// Traversal bookkeeping of one node visit: the nearest relevant child becomes
-// the next node (no stack round trip); every other relevant child is pushed.
-struct Next {
-    uint32_t ref;
-    float dist;
-    bool has;
-};
-
-__device__ __forceinline__ void offer(uint32_t ref, float d, Next &nx, uint2 *stack, int &sp, unsigned *status) {
-    uint32_t pr = ref;
-    float pd = d;
-    if (!nx.has || d < nx.dist) {
-        pr = nx.ref;
-        pd = nx.dist;
-        nx.ref = ref;
-        nx.dist = d;
-        if (!nx.has) { nx.has = true; return; }
-    }
-    if (sp < STACK) stack[sp++] = make_uint2(pr, __float_as_uint(pd));
-    else atomicOr(status, AGS_STACK);
-}
-
-__device__ __forceinline__ uint32_t child_ref(uint32_t m, uint32_t child_base, uint32_t tri_base) {
-    return (m & 0x80u) ? child_base + (m & 0x7fu) : ref_leaf(tri_base + (m & 31u), (int)((m >> 5) & 3u));
-}
-
 template <int LAYOUT>
 struct NodeOps;
 
@@ -229,18 +195,6 @@ struct NodeOps<AG_BVH_F32> {
     }
 };
 
-struct TraceArgs {
-    TraceJob job0;
-    const TraceJob *jobs;
-    const long long *job_begin;
-    int n_jobs;
-    const long long *n_rays_dev;
-    unsigned long long *ray_counter;
-    unsigned *status;
-    int max_steps;
-    unsigned long long *counters;
-};
-
 // Per-lane traversal state of one ray.
 struct RayState {
     int job;
@@ -253,10 +207,6 @@ struct RayState {
     uint32_t cur;
     int sp, steps;
 };
-
-__device__ __forceinline__ const TraceJob &job_of(const TraceArgs &A, int j) {
-    return A.n_jobs > 1 ? A.jobs[j] : A.job0;
-}
 
 __device__ __forceinline__ void setup_ray(const TraceArgs &A, long long r, RayState &S) {
     int j = 0;
@@ -366,18 +316,7 @@ __device__ __forceinline__ void finish(const TraceArgs &A, RayState &S, LossAcc 
         nh = normalize3(nA * bA + nB * bB + nC * bC);
     }
     if (!BWD) {
-        float3 nts = make_float3(0.f, 0.f, 1.f);
-        if (hit && !(S.fi.w & FACE_DEGEN)) {
-            float4 T0 = J.ltan[3 * S.face], T1 = J.ltan[3 * S.face + 1], T2 = J.ltan[3 * S.face + 2];
-            float3 tt = f3(T0) + (f3(T1) - f3(T0)) * S.b1 + (f3(T2) - f3(T0)) * S.b2;
-            tt = normalize3(tt - d * dot3(tt, d));
-            float3 bb = cross3(d, tt) * T0.w;
-            nts = make_float3(dot3(nh, tt), dot3(nh, bb), dot3(nh, d));
-        }
-        J.ntsd[S.texel] = make_float4(nts.x, nts.y, nts.z, hit ? S.best.t : 0.f);
-        J.mask[S.texel] = hit ? 1 : 0;
-        if (J.hit_tri) J.hit_tri[S.texel] = hit ? J.tri_ids[S.best.rec] : -1;
-        if (J.hit_t) J.hit_t[S.texel] = hit ? S.best.t : 0.f;
+        store_forward(J, S.texel, S.face, S.fi, S.b1, S.b2, d, hit, nh, S.best.t, hit ? J.tri_ids[S.best.rec] : -1);
     } else if (hit) {
         // adjoint of t^2 + lambda (1 - nh . d), hit triangle held fixed
         const float lam = J.lambda;
@@ -414,25 +353,6 @@ __device__ __forceinline__ void finish(const TraceArgs &A, RayState &S, LossAcc 
         L.t += t * t;
         L.n += 1.f - dot3(nh, d);
         L.c += 1.f;
-    }
-}
-
-template <bool COUNT>
-__device__ __forceinline__ void flush_counters(const TraceArgs &A, unsigned long long c_rays, unsigned long long c_nodes,
-                                               unsigned long long c_tris, unsigned long long c_hits) {
-    if (!COUNT) return;
-    const int lane = threadIdx.x & 31;
-    for (int o = 16; o > 0; o >>= 1) {
-        c_nodes += __shfl_xor_sync(0xffffffffu, c_nodes, o);
-        c_tris += __shfl_xor_sync(0xffffffffu, c_tris, o);
-        c_rays += __shfl_xor_sync(0xffffffffu, c_rays, o);
-        c_hits += __shfl_xor_sync(0xffffffffu, c_hits, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&A.counters[0], c_rays);
-        atomicAdd(&A.counters[1], c_nodes);
-        atomicAdd(&A.counters[2], c_tris);
-        atomicAdd(&A.counters[3], c_hits);
     }
 }
 
@@ -545,6 +465,7 @@ cudaError_t launch_one(const TraceLaunch &L, const TraceArgs &A, cudaStream_t s)
 }  // namespace
 
 cudaError_t launch_trace(const TraceLaunch &L, cudaStream_t s) {
+    if (L.query == AG_QUERY_CLOSEST) return launch_closest(L, s);
     cudaError_t e = cudaMemsetAsync(L.ray_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     TraceArgs A;

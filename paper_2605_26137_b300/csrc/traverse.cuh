@@ -1,0 +1,103 @@
+// Traversal pieces shared by the ray query (trace.cu) and the closest-point
+// query (closest.cu) over the same 8-wide BVH: launch arguments, the
+// nearest-child-next bookkeeping, the 8-bit plane decode, the counting build's
+// reduction and the forward shading store (Sec. 6.4: the hit normal projected
+// into the texel's tangent frame; the UV-reliability filter).
+#pragma once
+
+#include "ag_internal.cuh"
+
+namespace ag {
+namespace {
+
+constexpr int STACK = 64;
+constexpr float EPS_REL = 4.76837158203125e-07f;  // 2^-21: widening per unit of coordinate magnitude
+
+struct TraceArgs {
+    TraceJob job0;
+    const TraceJob *jobs;
+    const long long *job_begin;
+    int n_jobs;
+    const long long *n_rays_dev;
+    unsigned long long *ray_counter;
+    unsigned *status;
+    int max_steps;
+    unsigned long long *counters;
+};
+
+__device__ __forceinline__ const TraceJob &job_of(const TraceArgs &A, int j) {
+    return A.n_jobs > 1 ? A.jobs[j] : A.job0;
+}
+
+// byte k of w as an exact float: 2^23 + byte in the bits, minus 2^23
+__device__ __forceinline__ float byte_f(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (unsigned)k)) - 8388608.0f;
+}
+
+// Traversal bookkeeping of one node visit: the nearest relevant child becomes
+// the next node (no stack round trip); every other relevant child is pushed.
+struct Next {
+    uint32_t ref;
+    float dist;
+    bool has;
+};
+
+__device__ __forceinline__ void offer(uint32_t ref, float d, Next &nx, uint2 *stack, int &sp, unsigned *status) {
+    uint32_t pr = ref;
+    float pd = d;
+    if (!nx.has || d < nx.dist) {
+        pr = nx.ref;
+        pd = nx.dist;
+        nx.ref = ref;
+        nx.dist = d;
+        if (!nx.has) { nx.has = true; return; }
+    }
+    if (sp < STACK) stack[sp++] = make_uint2(pr, __float_as_uint(pd));
+    else atomicOr(status, AGS_STACK);
+}
+
+__device__ __forceinline__ uint32_t child_ref(uint32_t m, uint32_t child_base, uint32_t tri_base) {
+    return (m & 0x80u) ? child_base + (m & 0x7fu) : ref_leaf(tri_base + (m & 31u), (int)((m >> 5) & 3u));
+}
+
+template <bool COUNT>
+__device__ __forceinline__ void flush_counters(const TraceArgs &A, unsigned long long c_rays, unsigned long long c_nodes,
+                                               unsigned long long c_tris, unsigned long long c_hits) {
+    if (!COUNT) return;
+    const int lane = threadIdx.x & 31;
+    for (int o = 16; o > 0; o >>= 1) {
+        c_nodes += __shfl_xor_sync(0xffffffffu, c_nodes, o);
+        c_tris += __shfl_xor_sync(0xffffffffu, c_tris, o);
+        c_rays += __shfl_xor_sync(0xffffffffu, c_rays, o);
+        c_hits += __shfl_xor_sync(0xffffffffu, c_hits, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&A.counters[0], c_rays);
+        atomicAdd(&A.counters[1], c_nodes);
+        atomicAdd(&A.counters[2], c_tris);
+        atomicAdd(&A.counters[3], c_hits);
+    }
+}
+
+// Forward outputs of one texel: tangent-space normal of the hit normal nh in
+// the texel frame (N = d, T = the interpolated corner tangent made orthogonal
+// to N, B = w (N x T)), (0,0,1) on a miss or a degenerate-UV face, the signed
+// displacement, the mask and the optional hit id / displacement copies.
+__device__ __forceinline__ void store_forward(const TraceJob &J, int texel, int face, int4 fi, float b1, float b2,
+                                              float3 d, bool hit, float3 nh, float disp, int hit_id) {
+    float3 nts = make_float3(0.f, 0.f, 1.f);
+    if (hit && !(fi.w & FACE_DEGEN)) {
+        float4 T0 = J.ltan[3 * face], T1 = J.ltan[3 * face + 1], T2 = J.ltan[3 * face + 2];
+        float3 tt = f3(T0) + (f3(T1) - f3(T0)) * b1 + (f3(T2) - f3(T0)) * b2;
+        tt = normalize3(tt - d * dot3(tt, d));
+        float3 bb = cross3(d, tt) * T0.w;
+        nts = make_float3(dot3(nh, tt), dot3(nh, bb), dot3(nh, d));
+    }
+    J.ntsd[texel] = make_float4(nts.x, nts.y, nts.z, hit ? disp : 0.f);
+    J.mask[texel] = hit ? 1 : 0;
+    if (J.hit_tri) J.hit_tri[texel] = hit ? hit_id : -1;
+    if (J.hit_t) J.hit_t[texel] = hit ? disp : 0.f;
+}
+
+}  // namespace
+}  // namespace ag

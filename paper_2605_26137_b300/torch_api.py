@@ -42,13 +42,17 @@ _COLLAPSE = {"area_count": _lib.AG_COLLAPSE_AREA_COUNT, "area": _lib.AG_COLLAPSE
 _TILES = {"8x8": _lib.AG_TILE_8x8, "16x16": _lib.AG_TILE_16x16, "32x8": _lib.AG_TILE_32x8, "4x4": _lib.AG_TILE_4x4}
 
 
+_QUERY = {"ray": _lib.AG_QUERY_RAY, "closest": _lib.AG_QUERY_CLOSEST}
+
+
 def _opts(layout="q8", gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
-          collapse="area", ray_tile="8x8"):
+          collapse="area", ray_tile="8x8", query="ray"):
     return default_opts(bvh_layout=_LAYOUTS[layout], gutter=gutter, disp_fp16=int(bool(disp_fp16)),
                         schedule=_SCHED[schedule] if isinstance(schedule, str) else schedule,
                         block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps,
                         collapse=_COLLAPSE[collapse],
-                        ray_tile=_TILES[ray_tile] if isinstance(ray_tile, str) else ray_tile)
+                        ray_tile=_TILES[ray_tile] if isinstance(ray_tile, str) else ray_tile,
+                        query=_QUERY[query] if isinstance(query, str) else query)
 
 
 class Bvh:
@@ -159,17 +163,20 @@ def _ptr(t):
 def bake(bvh: Bvh, low_verts, low_faces, low_uv, W: int, H: int, max_dist: float, *, low_normals=None,
          gutter: int = 2, disp_fp16: bool = True, aux: bool = False, counters: bool = False,
          out: BakeOutputs | None = None, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
-         stream=None, events=None, ray_tile="8x8") -> BakeOutputs:
-    """One bake.  ``aux`` adds float tangent-space normals, raster and hit
-    outputs; ``counters`` selects the counting traversal build; ``events``
-    (4 torch.cuda.Event) are recorded before the raster, before and after the
-    traversal and after the encoding."""
+         stream=None, events=None, ray_tile="8x8", query="ray") -> BakeOutputs:
+    """One bake.  ``query`` is "ray" (the line along the texel normal) or
+    "closest" (the nearest point of the high surface, Sec. 6.4 as worded).
+    ``aux`` adds float tangent-space normals, raster and hit outputs (hit_t is
+    the signed ray parameter or signed distance); ``counters`` selects the
+    counting traversal build; ``events`` (4 torch.cuda.Event) are recorded
+    before the raster, before and after the traversal and after the
+    encoding."""
     lib = _lib.load()
     _check_low(low_verts, low_faces, low_uv, low_normals)
     if out is None:
         out = alloc_outputs(W, H, low_verts.device, disp_fp16, aux, counters)
     o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
-              blocks_per_sm=blocks_per_sm, max_steps=max_steps, ray_tile=ray_tile)
+              blocks_per_sm=blocks_per_sm, max_steps=max_steps, ray_tile=ray_tile, query=query)
     ev = None
     if events is not None:
         if len(events) != 4:
@@ -254,11 +261,11 @@ def _descs(assets, disp_fp16):
 
 
 def bake_batch(assets: list[Asset], *, gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0,
-               stream=None, ray_tile="8x8"):
+               stream=None, ray_tile="8x8", query="ray"):
     lib = _lib.load()
     arr = _descs(assets, disp_fp16)
     o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
-              blocks_per_sm=blocks_per_sm, ray_tile=ray_tile)
+              blocks_per_sm=blocks_per_sm, ray_tile=ray_tile, query=query)
     check(lib.ag_bake_batch(len(assets), arr, ctypes.byref(o), _stream(stream)))
     return [a.out for a in assets]
 
@@ -267,12 +274,12 @@ class BatchPlan:
     """A batch captured once into a CUDA graph; ``launch`` replays it."""
 
     def __init__(self, assets: list[Asset], *, gutter=2, disp_fp16=True, schedule="auto", block_size=0,
-                 blocks_per_sm=0, stream=None, ray_tile="8x8"):
+                 blocks_per_sm=0, stream=None, ray_tile="8x8", query="ray"):
         self._lib = _lib.load()
         self.assets = assets
         arr = _descs(assets, disp_fp16)
         o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
-                  blocks_per_sm=blocks_per_sm, ray_tile=ray_tile)
+                  blocks_per_sm=blocks_per_sm, ray_tile=ray_tile, query=query)
         h = ctypes.c_void_p()
         check(self._lib.ag_batch_plan_create(len(assets), arr, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self._h = h

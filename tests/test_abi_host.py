@@ -47,6 +47,8 @@ def test_opts_default(lib):
     o = _lib.default_opts()
     assert o.bvh_layout == _lib.AG_BVH_Q8 and o.gutter == 2 and o.disp_fp16 == 1
     assert o.schedule == _lib.AG_SCHED_AUTO and o.max_steps == 0
+    assert o.query == _lib.AG_QUERY_RAY
+    assert ctypes.sizeof(_lib.AgOpts) == 64   # 16 int32: the query took one reserved slot
 
 
 def test_host_argument_checks(lib):
@@ -61,6 +63,9 @@ def test_host_argument_checks(lib):
     bad = _lib.default_opts(gutter=99)
     assert lib.ag_bvh_build(1, 3, 1, 1, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.AG_ERR_INVALID_ARG
     assert b"gutter" in lib.ag_last_error()
+    bad = _lib.default_opts(query=7)
+    assert lib.ag_bvh_build(1, 3, 1, 1, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.AG_ERR_INVALID_ARG
+    assert b"query" in lib.ag_last_error()
     # bad handles
     assert lib.ag_bvh_free(None) == _lib.AG_OK
     info = _lib.AgBvhInfo()
