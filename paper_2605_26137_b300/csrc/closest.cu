@@ -5,7 +5,8 @@
 // tangent-space shading as the ray query.
 //
 // One persistent launch per ray list; a warp takes 32 consecutive texels of
-// the tile-ordered list.  Per texel:
+// the tile-ordered list (the "batch" schedule: a per-lane refill and a
+// while-while node/leaf split were both measured slower here).  Per texel:
 //   - query point p = v0 + b1 (v1 - v0) + b2 (v2 - v0), kept as (v0, offset)
 //     so triangle vertices are taken relative to p with two roundings;
 //   - branch and bound over the 8-wide BVH: a child is entered only when the
@@ -15,11 +16,9 @@
 //     the distance filter max_dist (inclusive);
 //   - per triangle, the closest point by Voronoi-region classification
 //     (Ericson, Real-Time Collision Detection, 2005, Sec. 5.1.5): vertex,
-//     edge or face region from six dot products, barycentrics from the
-//     region's closed form; in the face region the point itself is the foot
-//     of the perpendicular, ((a . n) / (n . n)) n with n = (b - a) x (c - a),
-//     which keeps the distance accurate to a few FP32 ulps of the vertex
-//     offsets where the barycentric numerators cancel;
+//     edge or face region from six dot products, evaluated branch-free (all
+//     lanes of a warp run the same instructions); the barycentrics are formed
+//     once, for the winning triangle, when shading;
 //   - ties in squared distance prefer the lower original triangle id;
 //   - displacement = distance signed by (x - p) . d (d the texel normal,
 //     zero counts as +).
@@ -32,9 +31,7 @@ constexpr float LIM_REL = 1.0000010f;  // 1 + 2^-20: slack on squared-distance b
 
 struct PBest {
     float d2;          // squared distance of the best point (or max_dist^2 before the first)
-    float bA, bB, bC;  // its barycentrics
-    float3 x;          // the point, relative to p
-    uint32_t rec;
+    uint32_t rec;      // its triangle record (point and barycentrics are recomputed when shading)
     bool found;
 };
 
@@ -57,71 +54,96 @@ __device__ __forceinline__ float3 rel(const PointState &S, float4 v) {
                        __fsub_rn(__fsub_rn(v.z, S.base.z), S.off.z));
 }
 
-// Closest point of triangle (a, b, c) to the origin, by Voronoi region:
-// barycentrics (u, v, w); returns REG_NONE for a triangle of zero area whose
-// region tests fall through (its edges belong to neighbouring triangles as
-// well), REG_FACE when the point is interior.
-enum { REG_NONE = 0, REG_EDGE = 1, REG_FACE = 2 };
+// Closest point of triangle (a, b, c) to the origin by Voronoi region, in a
+// branch-free form: every region's point is x = P + E * (num / den),
+//   vertex A / B / C:  P = that vertex, num = 0;
+//   edge AB / AC / BC: P = its first vertex, E = the edge, num / den = the
+//                      clamped projection parameter;
+//   face:              P = 0, E = n = (b - a) x (c - a), num / den = (a . n) / (n . n),
+//                      the foot of the perpendicular (accurate to a few FP32
+//                      ulps of the vertex offsets where the region's
+//                      barycentric numerators cancel).
+// The region tests are those of the classification, taken in its order of
+// precedence (later assignments below win).
+enum { REG_A = 0, REG_B, REG_C, REG_AB, REG_AC, REG_BC, REG_FACE };
 
-__device__ __forceinline__ int tri_closest(float3 a, float3 b, float3 c, float &u, float &v, float &w) {
-    float3 ab = b - a, ac = c - a;
-    float d1 = -dot3(ab, a), d2 = -dot3(ac, a);
-    if (d1 <= 0.f && d2 <= 0.f) { u = 1.f; v = 0.f; w = 0.f; return REG_EDGE; }
-    float d3 = -dot3(ab, b), d4 = -dot3(ac, b);
-    if (d3 >= 0.f && d4 <= d3) { u = 0.f; v = 1.f; w = 0.f; return REG_EDGE; }
-    float vc = d1 * d4 - d3 * d2;
-    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
-        float den = d1 - d3;
-        v = den > 0.f ? d1 / den : 0.f;
-        u = 1.f - v; w = 0.f;
-        return REG_EDGE;
+struct TriQ {
+    float3 P, E;
+    float num, den;
+    float va, vb, vc;   // face-region barycentric numerators (a, b, c)
+    int reg;
+};
+
+__device__ __forceinline__ void tri_query(float3 a, float3 b, float3 c, TriQ &q) {
+    const float3 ab = b - a, ac = c - a;
+    const float d1 = -dot3(ab, a), d2 = -dot3(ac, a);
+    const float d3 = -dot3(ab, b), d4 = -dot3(ac, b);
+    const float d5 = -dot3(ab, c), d6 = -dot3(ac, c);
+    q.vc = d1 * d4 - d3 * d2;
+    q.vb = d5 * d2 - d1 * d6;
+    q.va = d3 * d6 - d5 * d4;
+    const float e43 = d4 - d3, e56 = d5 - d6;
+    const float3 n = cross3(ab, ac);
+    const float3 zero = make_float3(0.f, 0.f, 0.f);
+    int reg = REG_FACE;
+    float3 P = zero, E = n;
+    float num = dot3(a, n), den = dot3(n, n);
+    const bool bc = q.va <= 0.f && e43 >= 0.f && e56 >= 0.f;
+    reg = bc ? REG_BC : reg; P = bc ? b : P; E = bc ? c - b : E; num = bc ? e43 : num; den = bc ? e43 + e56 : den;
+    const bool acr = q.vb <= 0.f && d2 >= 0.f && d6 <= 0.f;
+    reg = acr ? REG_AC : reg; P = acr ? a : P; E = acr ? ac : E; num = acr ? d2 : num; den = acr ? d2 - d6 : den;
+    const bool cv = d6 >= 0.f && d5 <= d6;
+    reg = cv ? REG_C : reg; P = cv ? c : P; num = cv ? 0.f : num; den = cv ? 1.f : den;
+    const bool abr = q.vc <= 0.f && d1 >= 0.f && d3 <= 0.f;
+    reg = abr ? REG_AB : reg; P = abr ? a : P; E = abr ? ab : E; num = abr ? d1 : num; den = abr ? d1 - d3 : den;
+    const bool bv = d3 >= 0.f && d4 <= d3;
+    reg = bv ? REG_B : reg; P = bv ? b : P; num = bv ? 0.f : num; den = bv ? 1.f : den;
+    const bool av = d1 <= 0.f && d2 <= 0.f;
+    reg = av ? REG_A : reg; P = av ? a : P; num = av ? 0.f : num; den = av ? 1.f : den;
+    q.P = P; q.E = E; q.num = num; q.den = den; q.reg = reg;
+}
+
+// the point of a query; false for a zero-area triangle in the face region
+// (its edges belong to neighbouring triangles as well)
+__device__ __forceinline__ bool tri_point(const TriQ &q, float3 &x) {
+    if (!(q.den > 0.f)) {
+        x = q.P;
+        return q.reg != REG_FACE;
     }
-    float d5 = -dot3(ab, c), d6 = -dot3(ac, c);
-    if (d6 >= 0.f && d5 <= d6) { u = 0.f; v = 0.f; w = 1.f; return REG_EDGE; }
-    float vb = d5 * d2 - d1 * d6;
-    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
-        float den = d2 - d6;
-        w = den > 0.f ? d2 / den : 0.f;
-        u = 1.f - w; v = 0.f;
-        return REG_EDGE;
+    x = q.P + q.E * (q.num / q.den);
+    return true;
+}
+
+// barycentrics (of a, b, c) of the query's point
+__device__ __forceinline__ float3 tri_bary(const TriQ &q) {
+    const float t = q.den > 0.f ? q.num / q.den : 0.f;
+    switch (q.reg) {
+        case REG_A: return make_float3(1.f, 0.f, 0.f);
+        case REG_B: return make_float3(0.f, 1.f, 0.f);
+        case REG_C: return make_float3(0.f, 0.f, 1.f);
+        case REG_AB: return make_float3(1.f - t, t, 0.f);
+        case REG_AC: return make_float3(1.f - t, 0.f, t);
+        case REG_BC: return make_float3(0.f, 1.f - t, t);
+        default: {
+            const float s = q.va + q.vb + q.vc;
+            if (!(s > 0.f)) return make_float3(1.f / 3.f, 1.f / 3.f, 1.f / 3.f);
+            const float v = q.vb / s, w = q.vc / s;
+            return make_float3(1.f - v - w, v, w);
+        }
     }
-    float va = d3 * d6 - d5 * d4;
-    float e43 = d4 - d3, e56 = d5 - d6;
-    if (va <= 0.f && e43 >= 0.f && e56 >= 0.f) {
-        float den = e43 + e56;
-        w = den > 0.f ? e43 / den : 0.f;
-        v = 1.f - w; u = 0.f;
-        return REG_EDGE;
-    }
-    float den = va + vb + vc;   // = |ab x ac|^2 in exact arithmetic
-    if (!(den > 0.f)) return REG_NONE;
-    float inv = 1.0f / den;
-    v = vb * inv;
-    w = vc * inv;
-    u = 1.f - v - w;
-    return REG_FACE;
 }
 
 __device__ __forceinline__ void test_tri(PointState &S, const float4 *__restrict__ tris,
                                          const int32_t *__restrict__ tri_ids, uint32_t rec) {
     float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
-    float3 a = rel(S, A), b = rel(S, B), c = rel(S, C);
-    float u, v, w;
-    const int reg = tri_closest(a, b, c, u, v, w);
-    if (reg == REG_NONE) return;
+    TriQ q;
+    tri_query(rel(S, A), rel(S, B), rel(S, C), q);
     float3 x;
-    if (reg == REG_FACE) {
-        float3 n = cross3(b - a, c - a);
-        float nn = dot3(n, n);
-        if (!(nn > 0.f)) return;
-        x = n * (dot3(a, n) / nn);
-    } else {
-        x = a * u + b * v + c * w;
-    }
+    if (!tri_point(q, x)) return;
     float d2 = dot3(x, x);
     if (!(d2 <= S.best.d2)) return;
     if (S.best.found && d2 == S.best.d2 && tri_ids[rec] >= tri_ids[S.best.rec]) return;
-    S.best.d2 = d2; S.best.bA = u; S.best.bB = v; S.best.bC = w; S.best.x = x; S.best.rec = rec; S.best.found = true;
+    S.best.d2 = d2; S.best.rec = rec; S.best.found = true;
 }
 
 template <int LAYOUT>
@@ -228,8 +250,6 @@ __device__ __forceinline__ void setup_point(const TraceArgs &A, long long r, Poi
     float3 sv = N0 + (N1 - N0) * S.b1 + (N2 - N0) * S.b2;
     S.d = sv * (1.0f / sqrtf(dot3(sv, sv)));
     S.best.d2 = J.max_dist * J.max_dist;
-    S.best.bA = S.best.bB = S.best.bC = 0.f;
-    S.best.x = make_float3(0.f, 0.f, 0.f);
     S.best.rec = 0;
     S.best.found = false;
     S.cur = 0;
@@ -279,12 +299,18 @@ __device__ __forceinline__ void finish_point(const TraceArgs &A, const PointStat
     int hit_id = -1;
     if (hit) {
         const size_t r3 = 3 * (size_t)S.best.rec;
-        float3 nA = f3(__ldg(&J.hnormals[__float_as_int(__ldg(&J.tris[r3]).w)]));
-        float3 nB = f3(__ldg(&J.hnormals[__float_as_int(__ldg(&J.tris[r3 + 1]).w)]));
-        float3 nC = f3(__ldg(&J.hnormals[__float_as_int(__ldg(&J.tris[r3 + 2]).w)]));
-        nh = normalize3(nA * S.best.bA + nB * S.best.bB + nC * S.best.bC);
-        float dist = sqrtf(S.best.d2);
-        disp = dot3(S.best.x, S.d) >= 0.f ? dist : -dist;
+        const float4 A = __ldg(&J.tris[r3]), B = __ldg(&J.tris[r3 + 1]), C = __ldg(&J.tris[r3 + 2]);
+        TriQ q;
+        tri_query(rel(S, A), rel(S, B), rel(S, C), q);
+        float3 x;
+        tri_point(q, x);
+        const float3 bw = tri_bary(q);
+        const float3 nA = f3(__ldg(&J.hnormals[__float_as_int(A.w)]));
+        const float3 nB = f3(__ldg(&J.hnormals[__float_as_int(B.w)]));
+        const float3 nC = f3(__ldg(&J.hnormals[__float_as_int(C.w)]));
+        nh = normalize3(nA * bw.x + nB * bw.y + nC * bw.z);
+        const float dist = sqrtf(S.best.d2);
+        disp = dot3(x, S.d) >= 0.f ? dist : -dist;
         hit_id = J.tri_ids[S.best.rec];
     }
     store_forward(J, S.texel, S.face, S.fi, S.b1, S.b2, S.d, hit, nh, disp, hit_id);
