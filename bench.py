@@ -93,28 +93,32 @@ def peaks():
     return 6400.0, "fallback"
 
 
-def trace_source_hash():
-    """Hash of the traversal kernel's sources (the profiled kernel and the
-    traversal header it includes)."""
+KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh"), "closest": ("closest.cu", "traverse.cuh")}
+PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_2048_2M.md"}
+
+
+def trace_source_hash(kernel: str = "trace"):
+    """Hash of a traversal kernel's sources (the profiled kernel's file and
+    the traversal header it includes)."""
     h = hashlib.sha256()
-    for name in ("trace.cu", "traverse.cuh"):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(layout_tag: str, res: int, high_tris: int):
-    """DRAM bytes per trace launch from the committed ncu summary, or None if
-    the summary is missing, was taken on a different trace kernel source, or
-    on another workload."""
-    path = os.path.join(ROOT, "profiles", "trace_kernel_2048_2M.md")
+def recorded_traffic(layout_tag: str, res: int, high_tris: int, kernel: str = "trace"):
+    """DRAM bytes per traversal launch from the committed ncu summary, or
+    None if the summary is missing, was taken on a different kernel source,
+    or on another workload."""
+    path = os.path.join(ROOT, "profiles", PROFILE_FILES[kernel])
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     t = re.search(rf"dram_bytes_per_launch_{layout_tag}:\s*([0-9.eE+]+)", txt)
     w = re.search(r"workload:\s*(\d+)\s+(\d+)", txt)
-    if not m or not t or not w or m.group(1) != trace_source_hash():
+    if not m or not t or not w or m.group(1) != trace_source_hash(kernel):
         return None
     if int(w.group(1)) != res or int(w.group(2)) != high_tris:
         return None
@@ -224,8 +228,9 @@ def run_profile(args):
     for _ in range(args.steps):
         pb.bake(bvh, lv, lf, uv, args.res, args.res, a.max_dist, out=out, query=args.query)
     pb.sync_status()
+    kernel = "closest" if args.query == "closest" else "trace"
     print(json.dumps({"profile_case": workload_name(args), "layout": args.layout, "high_tris": int(len(a.high_f)),
-                      "query": args.query, "bakes": args.steps, "trace_source_hash": trace_source_hash()}))
+                      "query": args.query, "bakes": args.steps, "kernel_source_hash": trace_source_hash(kernel)}))
 
 
 def to_dev(a, torch):
@@ -570,6 +575,7 @@ def closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush):
             "launch": {k: int(v) for k, v in lk.items()},
             "per_query": {"nodes": c[1] / c[0], "tris": c[2] / c[0], "hit_frac": c[3] / c[0], "bytes": bpq},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": recorded_traffic("q8", W, int(len(a.high_f)), "closest"),
                          "kernel": "k_closest (closest-point traversal + shading)", "peak_kind": peak_kind},
             "error_vs_oracle": layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, args.error_sample,
                                              query="closest"),
