@@ -98,12 +98,17 @@ PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_
 
 
 def trace_source_hash(kernel: str = "trace"):
-    """Hash of a traversal kernel's sources (the profiled kernel's file and
-    the traversal header it includes)."""
+    """Hash of a traversal kernel's code (the profiled kernel's file and the
+    traversal header it includes), comments and blank lines removed, so that
+    only a change of the code itself retires a recorded capture."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", name)) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        src = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+        h.update(src.encode())
     return h.hexdigest()[:16]
 
 

@@ -65,7 +65,7 @@ void or_vertex_normals(const float *V, int64_t nv, const int32_t *F, int64_t nf,
 }
 
 /* ------------------------------------------------- 2. UV-space raster (Sec. 6.4)
- * Reading of "rasterizes the low-poly mesh into its own UV space":
+ * Reading of the rasterisation of the low-poly mesh in its own UV layout:
  *  - texel (x, y) has centre (x + 1/2, y + 1/2) in texel units, x = u*W,
  *    y = v*H (v not flipped);
  *  - UVs are snapped to 1/256 texel: X = round_half_away(u * W * 256);
@@ -485,8 +485,8 @@ int or_closest_hit(const float *V, const int32_t *F, int64_t nf, void *bvh, cons
 }
 
 /* ------------------------------------------------- 4b. closest-point query
- * Sec. 6.4 as written: the BVH "locates, for each texel's world-space
- * position, the closest point on the high-poly surface".  Definition used:
+ * The correspondence as Sec. 6.4 words it: for the texel's world-space
+ * position, the nearest point of the high-poly surface.  Definition used:
  * over every high-poly triangle (a closed set) the point x minimising
  * |x - p|.  A triangle's own closest point is the foot of the perpendicular
  * from p when the foot lies in the closed triangle, else the nearest of the
@@ -790,14 +790,14 @@ int or_trace(const float *hv, int64_t nhv, const int32_t *hf, int64_t nhf, const
 }
 
 /* ------------------------------------------------- 6. encode + dilation
- * "encoded as RGB8" (Sec. 6.4), reading: q = 128 + round_half_away(127*c)
+ * RGB8 encoding (Sec. 6.4), reading: q = 128 + round_half_away(127*c)
  * for c clamped to [-1, 1] (codes 1..255, 128 = 0).  The unsigned mapping
  * floor((c/2 + 1/2)*255 + 1/2) would put the 127/128 code boundary exactly at
  * c = 0, the value every texel takes where the high surface runs parallel to
  * the low one, leaving that code to rounding noise; here 0 sits in the middle
  * of code 128.  A = 255 on ray and dilated texels, else 0; untouched texels
  * encode (0,0,1) = (128,128,255).
- * "dilated at UV seam boundaries" (Sec. 6.4), reading: `gutter` passes; each
+ * Dilation across UV seams (Sec. 6.4), reading: `gutter` passes; each
  * pass gives every unfilled texel with at least one filled 8-neighbour (as of
  * the previous pass) the renormalised mean of those neighbours' tangent-space
  * normals and the mean of their displacements.  The hit mask is not dilated. */

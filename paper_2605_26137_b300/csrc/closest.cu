@@ -1,8 +1,8 @@
-// Closest-point correspondence (Sec. 6.4 as worded: the BVH "locates, for
-// each texel's world-space position, the closest point on the high-poly
-// surface and retrieves its interpolated smooth normal via barycentric
-// weighting"), followed by the same distance filter, UV-reliability filter and
-// tangent-space shading as the ray query.
+// Closest-point correspondence (Sec. 6.4 as worded: for each texel's
+// world-space position, the nearest point of the high-poly surface found
+// through the BVH, and the smooth normal interpolated there with the point's
+// barycentrics), followed by the same distance filter, UV-reliability filter
+// and tangent-space shading as the ray query.
 //
 // One persistent launch per ray list; a warp takes 32 consecutive texels of
 // the tile-ordered list (the "batch" schedule: a per-lane refill and a

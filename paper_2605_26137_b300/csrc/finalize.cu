@@ -1,5 +1,5 @@
-// Output stage (Sec. 6.4: "encoded as RGB8, and dilated at UV seam
-// boundaries"): `gutter` Jacobi dilation passes run in shared memory on a
+// Output stage (Sec. 6.4: the RGB8 encoding and the dilation across UV
+// seams): `gutter` Jacobi dilation passes run in shared memory on a
 // 32x8 output tile with a halo of `gutter` texels, then every texel of the
 // tile is encoded (RGBA8, binary16/float32 displacement) in the same pass.
 // Also the final reductions of the backward pass.

@@ -1,6 +1,6 @@
-"""Pins for the oracle's closest-point query (Sec. 6.4: the BVH "locates, for
-each texel's world-space position, the closest point on the high-poly
-surface").
+"""Pins for the oracle's closest-point query (Sec. 6.4 words the
+correspondence as the nearest point of the high-poly surface to each texel's
+world-space position).
 
 * one triangle: hand-computed interior, edge and vertex cases; on random
   triangles (slivers and a zero-area one included) the returned point lies in
