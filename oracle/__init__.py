@@ -76,6 +76,12 @@ def _load():
         lib.or_dilate.restype = _I
         lib.or_loss_grad.argtypes = [_P, _P, _P, _P, _I64, _P, _I64, _P, _P, _P, _I64, _D, _P]
         lib.or_loss_grad.restype = _D
+        lib.or_view_basis.argtypes = [_I, _I, _P]
+        lib.or_view_basis.restype = None
+        lib.or_visibility.argtypes = [_P, _P, _I64, _P, _I, _I, _D, _I, _P, _P, _P, _P, _P, _P]
+        lib.or_visibility.restype = _I
+        lib.or_exterior_fill.argtypes = [_P, _P, _I64, _I64, _P, _P]
+        lib.or_exterior_fill.restype = _I
         _lib = lib
         return lib
 
@@ -307,3 +313,61 @@ def fd_grad(high_v, high_f, high_normals, low_v64, low_f, face, bary, hit_tri, l
         flat[c] = old
         g.reshape(-1)[c] = (lp - lm) / (2 * h)
     return g
+
+
+# ----------------------------------------------------------------- hidden-face removal (Sec. 6.2)
+
+MAX_CAND = 16
+
+
+def view_basis(k: int, n: int):
+    """View k of n: (u, e1, e2), u on the Fibonacci lattice, rays along -u."""
+    out = np.zeros(9, np.float64)
+    _load().or_view_basis(k, n, _p(out))
+    return out[:3].copy(), out[3:6].copy(), out[6:].copy()
+
+
+def visibility(V, F, n_views: int, res: int, *, tol_rel: float = 1e-5, candidates: bool = True,
+               bvh: Bvh | None = None, use_bvh: bool = True, nthreads=None):
+    """Per-face visibility from n_views orthographic res x res views.
+    Returns a dict: visible [nf] u8, hit [n_views, res, res] i32 (-1 miss),
+    and with ``candidates`` ncand [n_views, res, res], cand [..., 16] (faces
+    within tol_rel*R of the ray, no farther than its first hit + tol_rel*R;
+    -1 padded, ncand > 16 means the list is truncated), edge_near (the hit
+    point within tol_rel*R of its triangle's boundary); frame = (c, R)."""
+    lib = _load()
+    V = _c(V, np.float32)
+    F = _c(F, np.int32)
+    if use_bvh and bvh is None:
+        bvh = Bvh(V, F)
+    nf = len(F)
+    nr = n_views * res * res
+    visible = np.zeros(nf, np.uint8)
+    hit = np.empty(nr, np.int32)
+    ncand = np.zeros(nr, np.int32) if candidates else None
+    cand = np.full(nr * MAX_CAND, -1, np.int32) if candidates else None
+    near = np.zeros(nr, np.uint8) if candidates else None
+    frame = np.zeros(4, np.float64)
+    rc = lib.or_visibility(_p(V), _p(F), nf, bvh.h if use_bvh else None, n_views, res, float(tol_rel),
+                           nthreads or default_threads(), _p(visible), _p(hit), _p(ncand), _p(cand), _p(near),
+                           _p(frame))
+    if rc != 0:
+        raise RuntimeError("oracle visibility: thread start failed")
+    out = dict(visible=visible, hit=hit.reshape(n_views, res, res), frame=(frame[:3].copy(), float(frame[3])))
+    if candidates:
+        out.update(ncand=ncand.reshape(n_views, res, res), cand=cand.reshape(n_views, res, res, MAX_CAND),
+                   edge_near=near.reshape(n_views, res, res))
+    return out
+
+
+def exterior_fill(V, F, visible, nv=None):
+    """Exterior faces [nf] u8: every face linked to a visible face through
+    edge-adjacent faces whose normals have a positive dot product."""
+    lib = _load()
+    V = _c(V, np.float32)
+    F = _c(F, np.int32)
+    vis = _c(visible, np.uint8)
+    ext = np.zeros(len(F), np.uint8)
+    if lib.or_exterior_fill(_p(V), _p(F), nv if nv is not None else len(V), len(F), _p(vis), _p(ext)) != 0:
+        raise MemoryError("oracle exterior fill: allocation failed")
+    return ext

@@ -18,7 +18,9 @@
  *   5. the hit's barycentric smooth normal projected into the texel frame;
  *   6. RGB8 encoding and gutter dilation;
  *   7. the baking loss mean(t^2) + lambda*mean(1 - n_hit . d) over hit texels
- *      and its analytic gradient with respect to the low-poly positions.
+ *      and its analytic gradient with respect to the low-poly positions;
+ *   8. hidden-face removal (Sec. 6.2): per-face visibility from orthographic
+ *      views around the mesh, then the normal-gated exterior flood fill.
  *
  * Readings of points the paper leaves open are stated where they are used.
  * Everything is double precision except the UV snapping, which is exact
@@ -953,4 +955,244 @@ double or_loss_grad(const float *hv, const int32_t *hf, const double *hn,
     }
     free(acc); free(gn);
     return (sum_t + lambda * sum_n) * inv;
+}
+
+/* ------------------------------------------------- 8. hidden-face removal (Sec. 6.2)
+ * Visibility pass (the paper's viewpoints spread over a sphere around the
+ * mesh, one square image each), reading:
+ *  - view k of n looks along -u_k, u_k on the Fibonacci (golden-angle)
+ *    lattice: z = 1 - (2k+1)/n, phi = k * pi (3 - sqrt 5),
+ *    u = (sqrt(1 - z^2) cos phi, sqrt(1 - z^2) sin phi, z);
+ *  - image axes e1 = normalize(a x u), e2 = u x e1 with a = +z, or +x when
+ *    |u_z| >= 0.9;
+ *  - orthographic: the res x res pixels tile the square [-R, R]^2 of the
+ *    plane spanned by e1, e2 through c (c the centre of the vertex bounding
+ *    box, R half its diagonal); pixel (i, j) casts the ray from
+ *    c + 2R u + x e1 + y e2, x = (2 (i + 1/2) / res - 1) R,
+ *    y = (2 (j + 1/2) / res - 1) R, along -u;
+ *  - a face is visible when it is the first hit of at least one ray (the
+ *    closest-hit rules of section 4: watertight test, no culling, ties to
+ *    the lower id).
+ * Exterior flood fill, reading of the normal-gated breadth-first
+ * propagation: faces f and g are linked when they share an edge (two vertex
+ * indices) and n_f . n_g > 0, n = (B - A) x (C - A) in double precision with
+ * the operations in the order written here (the GPU evaluates the same
+ * expression in the same order, so the gate is decided identically); the
+ * exterior is every face linked, through any chain, to a visible face.
+ */
+static const double GOLDEN_ANGLE = 2.39996322972865332223;   /* pi (3 - sqrt 5) */
+
+void or_view_basis(int k, int n, double *out) {
+    double z = 1.0 - (2.0 * k + 1.0) / n;
+    double r = sqrt(fmax(0.0, 1.0 - z * z));
+    double phi = k * GOLDEN_ANGLE;
+    d3 u = mk(r * cos(phi), r * sin(phi), z);
+    d3 a = fabs(u.z) < 0.9 ? mk(0, 0, 1) : mk(1, 0, 0);
+    d3 e1 = normalize(cross(a, u));
+    d3 e2 = cross(u, e1);
+    out[0] = u.x; out[1] = u.y; out[2] = u.z;
+    out[3] = e1.x; out[4] = e1.y; out[5] = e1.z;
+    out[6] = e2.x; out[7] = e2.y; out[8] = e2.z;
+}
+
+/* distance between the line o + t d (|d| = 1) and the segment a + s e,
+ * s in [0, 1]; *t receives the line parameter of the closest point */
+static double line_seg_dist(d3 o, d3 d, d3 a, d3 e, double *t) {
+    d3 w0 = sub(a, o);
+    d3 ep = sub(e, scl(d, dot(e, d)));
+    d3 wp = sub(w0, scl(d, dot(w0, d)));
+    double ee = dot(ep, ep);
+    double s = ee > 0.0 ? -dot(wp, ep) / ee : 0.0;
+    if (s < 0.0) s = 0.0;
+    if (s > 1.0) s = 1.0;
+    d3 q = add(a, scl(e, s));
+    *t = dot(sub(q, o), d);
+    return norm(sub(q, add(o, scl(d, *t))));
+}
+
+/* distance between the line and triangle tri (0 when the line meets it) */
+static double line_tri_dist(const float *V, const int32_t *F, int tri, d3 o, d3 d, const ray_t *r, double *t) {
+    d3 A = ldf(V, F[3 * tri]), B = ldf(V, F[3 * tri + 1]), C = ldf(V, F[3 * tri + 2]);
+    double b[3];
+    if (isect(r, A, B, C, t, b)) return 0.0;
+    const d3 P[3] = {A, B, C};
+    double best = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        double tk, dk = line_seg_dist(o, d, P[k], sub(P[(k + 1) % 3], P[k]), &tk);
+        if (dk < best) { best = dk; *t = tk; }
+    }
+    return best;
+}
+
+typedef struct {
+    const float *V; const int32_t *F; int64_t nf; const obvh *bvh;
+    double c[3], R; int n_views, res; double delta;
+    int32_t *hit; int32_t *ncand; int32_t *cand; uint8_t *edge_near;
+    int64_t nrays; int nthreads, tid;
+} vis_job;
+
+#define OR_MAX_CAND 16
+
+static void cand_add(int32_t *list, int32_t *n, int tri) {
+    for (int i = 0; i < *n && i < OR_MAX_CAND; ++i) if (list[i] == tri) return;
+    if (*n < OR_MAX_CAND) list[*n] = tri;
+    ++*n;
+}
+
+/* every triangle within delta of the line whose nearest approach lies no
+ * later than tlim (brute force, or the BVH with boxes grown by delta) */
+static void candidates(const vis_job *j, d3 o, d3 d, const ray_t *r, double tlim, int32_t *list, int32_t *n) {
+    *n = 0;
+    if (!j->bvh) {
+        for (int64_t i = 0; i < j->nf; ++i) {
+            double t, dist = line_tri_dist(j->V, j->F, (int)i, o, d, r, &t);
+            if (dist <= j->delta && t <= tlim) cand_add(list, n, (int)i);
+        }
+        return;
+    }
+    const obvh *b = j->bvh;
+    if (b->nf == 0) return;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const bnode *nd = &b->nodes[stack[--sp]];
+        bnode g = *nd;
+        for (int k = 0; k < 3; ++k) { g.lo[k] -= j->delta; g.hi[k] += j->delta; }
+        double t0, t1;
+        if (!box_interval(&g, o, d, &t0, &t1) || t0 > tlim) continue;
+        if (nd->left < 0) {
+            for (int i = nd->first; i < nd->first + nd->count; ++i) {
+                int tri = b->idx[i];
+                double t, dist = line_tri_dist(j->V, j->F, tri, o, d, r, &t);
+                if (dist <= j->delta && t <= tlim) cand_add(list, n, tri);
+            }
+        } else {
+            stack[sp++] = nd->left;
+            stack[sp++] = nd->right;
+        }
+    }
+}
+
+static void vis_one(const vis_job *j, int64_t ray) {
+    int64_t per = (int64_t)j->res * j->res;
+    int k = (int)(ray / per);
+    int pix = (int)(ray % per);
+    int px = pix % j->res, py = pix / j->res;
+    double basis[9];
+    or_view_basis(k, j->n_views, basis);
+    d3 u = mk(basis[0], basis[1], basis[2]), e1 = mk(basis[3], basis[4], basis[5]), e2 = mk(basis[6], basis[7], basis[8]);
+    double x = (2.0 * (px + 0.5) / j->res - 1.0) * j->R;
+    double y = (2.0 * (py + 0.5) / j->res - 1.0) * j->R;
+    d3 o = add(add(add(mk(j->c[0], j->c[1], j->c[2]), scl(u, 2.0 * j->R)), scl(e1, x)), scl(e2, y));
+    d3 d = scl(u, -1.0);
+    hit_t h;
+    closest(j->V, j->F, j->nf, j->bvh, o, d, 4.0 * j->R, -1, &h);
+    j->hit[ray] = h.tri;
+    if (j->ncand) {
+        ray_t r = make_ray(o, d);
+        double tlim = (h.tri >= 0 ? h.t : 4.0 * j->R) + j->delta;
+        candidates(j, o, d, &r, tlim, j->cand + ray * OR_MAX_CAND, &j->ncand[ray]);
+        /* the hit point within delta of its own triangle's boundary */
+        uint8_t near = 0;
+        if (h.tri >= 0) {
+            d3 X = add(o, scl(d, h.t));
+            const int32_t *f = j->F + 3 * h.tri;
+            for (int m = 0; m < 3; ++m) {
+                d3 a = ldf(j->V, f[m]), e = sub(ldf(j->V, f[(m + 1) % 3]), a);
+                double ee = dot(e, e), s = ee > 0 ? dot(sub(X, a), e) / ee : 0.0;
+                if (s < 0) s = 0;
+                if (s > 1) s = 1;
+                if (norm(sub(X, add(a, scl(e, s)))) < j->delta) near = 1;
+            }
+        }
+        j->edge_near[ray] = near;
+    }
+}
+
+static void *vis_worker(void *arg) {
+    vis_job *j = (vis_job *)arg;
+    for (int64_t i = j->tid; i < j->nrays; i += j->nthreads) vis_one(j, i);
+    return NULL;
+}
+
+/* hit [n_views*res*res]: first-hit face per ray (-1 = miss); with ncand
+ * non-NULL also, per ray, the candidate faces within tol_rel*R (count in
+ * ncand, up to 16 ids in cand[ray*16..]) and edge_near (hit point within
+ * tol_rel*R of its triangle's boundary); visible [nf] is the union of hits */
+int or_visibility(const float *V, const int32_t *F, int64_t nf, void *bvh, int n_views, int res, double tol_rel,
+                  int nthreads, uint8_t *visible, int32_t *hit, int32_t *ncand, int32_t *cand, uint8_t *edge_near,
+                  double *frame /* out: c[3], R */) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t f = 0; f < nf; ++f)
+        for (int m = 0; m < 3; ++m) {
+            d3 p = ldf(V, F[3 * f + m]);
+            for (int k = 0; k < 3; ++k) {
+                double c = comp(p, k);
+                if (c < lo[k]) lo[k] = c;
+                if (c > hi[k]) hi[k] = c;
+            }
+        }
+    vis_job base;
+    memset(&base, 0, sizeof(base));
+    base.V = V; base.F = F; base.nf = nf; base.bvh = (const obvh *)bvh;
+    for (int k = 0; k < 3; ++k) base.c[k] = 0.5 * (lo[k] + hi[k]);
+    base.R = 0.5 * sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                        (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    base.n_views = n_views; base.res = res; base.delta = tol_rel * base.R;
+    base.hit = hit; base.ncand = ncand; base.cand = cand; base.edge_near = edge_near;
+    base.nrays = (int64_t)n_views * res * res;
+    base.nthreads = nthreads;
+    if (frame) { frame[0] = base.c[0]; frame[1] = base.c[1]; frame[2] = base.c[2]; frame[3] = base.R; }
+    vis_job jobs[256];
+    pthread_t th[256];
+    for (int i = 0; i < nthreads; ++i) { jobs[i] = base; jobs[i].tid = i; }
+    for (int i = 1; i < nthreads; ++i)
+        if (pthread_create(&th[i], NULL, vis_worker, &jobs[i])) return -1;
+    vis_worker(&jobs[0]);
+    for (int i = 1; i < nthreads; ++i) pthread_join(th[i], NULL);
+    memset(visible, 0, (size_t)nf);
+    for (int64_t r = 0; r < base.nrays; ++r) if (hit[r] >= 0) visible[hit[r]] = 1;
+    return 0;
+}
+
+/* exterior [nf] from visible [nf] by the gated flood fill above */
+int or_exterior_fill(const float *V, const int32_t *F, int64_t nv, int64_t nf, const uint8_t *visible,
+                     uint8_t *exterior) {
+    double *nrm = (double *)malloc(sizeof(double) * 3 * (size_t)(nf > 0 ? nf : 1));
+    int64_t *deg = (int64_t *)calloc((size_t)nv + 1, sizeof(int64_t));
+    int32_t *list = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(nf > 0 ? nf : 1));
+    int64_t *fillp = (int64_t *)calloc((size_t)nv + 1, sizeof(int64_t));
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nf > 0 ? nf : 1));
+    if (!nrm || !deg || !list || !fillp || !queue) { free(nrm); free(deg); free(list); free(fillp); free(queue); return -1; }
+    for (int64_t f = 0; f < nf; ++f) {
+        d3 A = ldf(V, F[3 * f]), B = ldf(V, F[3 * f + 1]), C = ldf(V, F[3 * f + 2]);
+        std3(nrm, f, cross(sub(B, A), sub(C, A)));
+        for (int m = 0; m < 3; ++m) ++deg[F[3 * f + m] + 1];
+    }
+    for (int64_t v = 0; v < nv; ++v) deg[v + 1] += deg[v];
+    for (int64_t f = 0; f < nf; ++f)
+        for (int m = 0; m < 3; ++m) { int32_t v = F[3 * f + m]; list[deg[v] + fillp[v]++] = (int32_t)f; }
+    int64_t qh = 0, qt = 0;
+    for (int64_t f = 0; f < nf; ++f) {
+        exterior[f] = visible[f] ? 1 : 0;
+        if (exterior[f]) queue[qt++] = (int32_t)f;
+    }
+    while (qh < qt) {
+        int32_t f = queue[qh++];
+        d3 nf_ = ldd(nrm, f);
+        for (int m = 0; m < 3; ++m) {
+            int32_t a = F[3 * f + m], b = F[3 * f + (m + 1) % 3];
+            if (a == b) continue;
+            for (int64_t i = deg[a]; i < deg[a + 1]; ++i) {
+                int32_t g = list[i];
+                if (g == f || exterior[g]) continue;
+                if (F[3 * g] != b && F[3 * g + 1] != b && F[3 * g + 2] != b) continue;
+                if (dot(nf_, ldd(nrm, g)) > 0.0) { exterior[g] = 1; queue[qt++] = g; }
+            }
+        }
+    }
+    free(nrm); free(deg); free(list); free(fillp); free(queue);
+    return 0;
 }
