@@ -295,6 +295,53 @@ AG_API ag_status ag_autotune(ag_bvh_t h, const float *d_lverts, const float *d_l
  * (AG_ERR_TRAVERSAL_LIMIT if any ray since the last call hit a limit, or
  * AG_ERR_INVALID_ARG for out-of-range face indices seen by ag_bvh_build), or
  * AG_ERR_CUDA if the stream reported an error. */
+/*
+ * Hidden-face removal (Sec. 6.2 of the paper): a visibility pass over a BVH
+ * of the mesh, then a normal-gated flood fill.
+ *
+ * ag_visibility - per-face visibility of the mesh the handle was built on.
+ *   View k of n_views looks along -u_k, u_k on the Fibonacci (golden-angle)
+ *   lattice: z = 1 - (2k+1)/n_views, phi = k * pi (3 - sqrt 5),
+ *   u = (sqrt(1-z^2) cos phi, sqrt(1-z^2) sin phi, z).  Its image axes are
+ *   e1 = normalize(a x u), e2 = u x e1 (a = +z, or +x when |u_z| >= 0.9);
+ *   the res x res pixels tile [-R, R]^2 in that plane through c, the centre
+ *   of the vertex bounding box (R = half its diagonal), and pixel (i, j)
+ *   casts an orthographic ray from c + 2R u + x e1 + y e2,
+ *   x = (2 (i + 1/2) / res - 1) R, y likewise with j, along -u.  A face is
+ *   visible when it is the first hit of at least one ray (the closest-hit
+ *   rules of ag_bake's ray query: watertight test, no culling, ties to the
+ *   lower id).
+ *   d_visible  [n_faces] u8, device: overwritten with 1 (visible) / 0.
+ *   d_hit_ids  optional [n_views * res * res] int32, device: the first-hit
+ *              face of pixel (i, j) of view k at k*res*res + j*res + i, -1
+ *              on a miss (for tests and debugging; 4 bytes per ray).
+ *   d_counters optional [4] u64, device, accumulated: rays, node visits,
+ *              triangle tests, hits (selects the counting build).
+ *   opts: block_size (64..256), blocks_per_sm, max_steps are used.
+ *   Errors: AG_ERR_BAD_HANDLE, AG_ERR_INVALID_ARG (n_views outside 1..2^20,
+ *   res outside 1..16384, NULL d_visible); the step cap sets the status word.
+ */
+AG_API ag_status ag_visibility(ag_bvh_t h, int32_t n_views, int32_t res, const ag_opts *opts,
+                               ag_stream_t stream, uint8_t *d_visible, int32_t *d_hit_ids,
+                               uint64_t *d_counters);
+
+/*
+ * ag_exterior_fill - the exterior faces from a visibility mask: faces f and
+ *   g are linked when they share an edge (two vertex indices) and
+ *   n_f . n_g > 0, n = (B - A) x (C - A) evaluated in FP64 in that order
+ *   (x: e1.y e2.z - e1.z e2.y, and so on; the dot product summed x, y, z);
+ *   the exterior is every face linked to a visible face through any chain.
+ *   The result does not depend on the order of the search.
+ *   d_verts [n_verts*3] f32, d_faces [n_faces*3] i32, d_visible [n_faces] u8
+ *   (nonzero = visible), d_exterior [n_faces] u8 out (1 = exterior, kept;
+ *   0 = hidden, to be removed), all device.  Faces with an out-of-range
+ *   vertex index are never exterior and set AG_ERR_INVALID_ARG in the
+ *   status word.  Scratch: about 60 bytes per face + 8 per vertex.
+ */
+AG_API ag_status ag_exterior_fill(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
+                                  int64_t n_faces, const uint8_t *d_visible, ag_stream_t stream,
+                                  uint8_t *d_exterior);
+
 AG_API ag_status ag_sync_status(ag_stream_t stream);
 
 /* Message for the last failing call on this thread ("" if none). */

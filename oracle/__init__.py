@@ -78,7 +78,7 @@ def _load():
         lib.or_loss_grad.restype = _D
         lib.or_view_basis.argtypes = [_I, _I, _P]
         lib.or_view_basis.restype = None
-        lib.or_visibility.argtypes = [_P, _P, _I64, _P, _I, _I, _D, _I, _P, _P, _P, _P, _P, _P]
+        lib.or_visibility.argtypes = [_P, _P, _I64, _P, _I, _I, _D, _I, _P, _P, _P, _P, _P, _P, _P, _I64]
         lib.or_visibility.restype = _I
         lib.or_exterior_fill.argtypes = [_P, _P, _I64, _I64, _P, _P]
         lib.or_exterior_fill.restype = _I
@@ -328,20 +328,23 @@ def view_basis(k: int, n: int):
 
 
 def visibility(V, F, n_views: int, res: int, *, tol_rel: float = 1e-5, candidates: bool = True,
-               bvh: Bvh | None = None, use_bvh: bool = True, nthreads=None):
+               bvh: Bvh | None = None, use_bvh: bool = True, nthreads=None, sample=None):
     """Per-face visibility from n_views orthographic res x res views.
     Returns a dict: visible [nf] u8, hit [n_views, res, res] i32 (-1 miss),
     and with ``candidates`` ncand [n_views, res, res], cand [..., 16] (faces
     within tol_rel*R of the ray, no farther than its first hit + tol_rel*R;
     -1 padded, ncand > 16 means the list is truncated), edge_near (the hit
-    point within tol_rel*R of its triangle's boundary); frame = (c, R)."""
+    point within tol_rel*R of its triangle's boundary); frame = (c, R).
+    With ``sample`` (ray ids view*res*res + j*res + i) only those rays are
+    traced; the per-ray arrays are then flat, in sample order."""
     lib = _load()
     V = _c(V, np.float32)
     F = _c(F, np.int32)
     if use_bvh and bvh is None:
         bvh = Bvh(V, F)
     nf = len(F)
-    nr = n_views * res * res
+    samp = None if sample is None else _c(sample, np.int64)
+    nr = n_views * res * res if samp is None else len(samp)
     visible = np.zeros(nf, np.uint8)
     hit = np.empty(nr, np.int32)
     ncand = np.zeros(nr, np.int32) if candidates else None
@@ -350,13 +353,14 @@ def visibility(V, F, n_views: int, res: int, *, tol_rel: float = 1e-5, candidate
     frame = np.zeros(4, np.float64)
     rc = lib.or_visibility(_p(V), _p(F), nf, bvh.h if use_bvh else None, n_views, res, float(tol_rel),
                            nthreads or default_threads(), _p(visible), _p(hit), _p(ncand), _p(cand), _p(near),
-                           _p(frame))
+                           _p(frame), _p(samp), 0 if samp is None else len(samp))
     if rc != 0:
         raise RuntimeError("oracle visibility: thread start failed")
-    out = dict(visible=visible, hit=hit.reshape(n_views, res, res), frame=(frame[:3].copy(), float(frame[3])))
+    shape = (n_views, res, res) if samp is None else (len(samp),)
+    out = dict(visible=visible, hit=hit.reshape(shape), frame=(frame[:3].copy(), float(frame[3])))
     if candidates:
-        out.update(ncand=ncand.reshape(n_views, res, res), cand=cand.reshape(n_views, res, res, MAX_CAND),
-                   edge_near=near.reshape(n_views, res, res))
+        out.update(ncand=ncand.reshape(shape), cand=cand.reshape(shape + (MAX_CAND,)),
+                   edge_near=near.reshape(shape))
     return out
 
 

@@ -1028,7 +1028,7 @@ typedef struct {
     const float *V; const int32_t *F; int64_t nf; const obvh *bvh;
     double c[3], R; int n_views, res; double delta;
     int32_t *hit; int32_t *ncand; int32_t *cand; uint8_t *edge_near;
-    int64_t nrays; int nthreads, tid;
+    const int64_t *sample; int64_t nrays; int nthreads, tid;
 } vis_job;
 
 #define OR_MAX_CAND 16
@@ -1073,7 +1073,7 @@ static void candidates(const vis_job *j, d3 o, d3 d, const ray_t *r, double tlim
     }
 }
 
-static void vis_one(const vis_job *j, int64_t ray) {
+static void vis_one(const vis_job *j, int64_t slot, int64_t ray) {
     int64_t per = (int64_t)j->res * j->res;
     int k = (int)(ray / per);
     int pix = (int)(ray % per);
@@ -1087,11 +1087,11 @@ static void vis_one(const vis_job *j, int64_t ray) {
     d3 d = scl(u, -1.0);
     hit_t h;
     closest(j->V, j->F, j->nf, j->bvh, o, d, 4.0 * j->R, -1, &h);
-    j->hit[ray] = h.tri;
+    j->hit[slot] = h.tri;
     if (j->ncand) {
         ray_t r = make_ray(o, d);
         double tlim = (h.tri >= 0 ? h.t : 4.0 * j->R) + j->delta;
-        candidates(j, o, d, &r, tlim, j->cand + ray * OR_MAX_CAND, &j->ncand[ray]);
+        candidates(j, o, d, &r, tlim, j->cand + slot * OR_MAX_CAND, &j->ncand[slot]);
         /* the hit point within delta of its own triangle's boundary */
         uint8_t near = 0;
         if (h.tri >= 0) {
@@ -1105,23 +1105,26 @@ static void vis_one(const vis_job *j, int64_t ray) {
                 if (norm(sub(X, add(a, scl(e, s)))) < j->delta) near = 1;
             }
         }
-        j->edge_near[ray] = near;
+        j->edge_near[slot] = near;
     }
 }
 
 static void *vis_worker(void *arg) {
     vis_job *j = (vis_job *)arg;
-    for (int64_t i = j->tid; i < j->nrays; i += j->nthreads) vis_one(j, i);
+    for (int64_t i = j->tid; i < j->nrays; i += j->nthreads) vis_one(j, i, j->sample ? j->sample[i] : i);
     return NULL;
 }
 
 /* hit [n_views*res*res]: first-hit face per ray (-1 = miss); with ncand
  * non-NULL also, per ray, the candidate faces within tol_rel*R (count in
  * ncand, up to 16 ids in cand[ray*16..]) and edge_near (hit point within
- * tol_rel*R of its triangle's boundary); visible [nf] is the union of hits */
+ * tol_rel*R of its triangle's boundary); visible [nf] is the union of hits.
+ * With sample non-NULL only the rays sample[0..n_sample) are traced (ray id
+ * = view*res*res + j*res + i), the outputs indexed by sample position, and
+ * visible is the union over the sample. */
 int or_visibility(const float *V, const int32_t *F, int64_t nf, void *bvh, int n_views, int res, double tol_rel,
                   int nthreads, uint8_t *visible, int32_t *hit, int32_t *ncand, int32_t *cand, uint8_t *edge_near,
-                  double *frame /* out: c[3], R */) {
+                  double *frame /* out: c[3], R */, const int64_t *sample, int64_t n_sample) {
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -1142,7 +1145,8 @@ int or_visibility(const float *V, const int32_t *F, int64_t nf, void *bvh, int n
                         (hi[2] - lo[2]) * (hi[2] - lo[2]));
     base.n_views = n_views; base.res = res; base.delta = tol_rel * base.R;
     base.hit = hit; base.ncand = ncand; base.cand = cand; base.edge_near = edge_near;
-    base.nrays = (int64_t)n_views * res * res;
+    base.sample = sample;
+    base.nrays = sample ? n_sample : (int64_t)n_views * res * res;
     base.nthreads = nthreads;
     if (frame) { frame[0] = base.c[0]; frame[1] = base.c[1]; frame[2] = base.c[2]; frame[3] = base.R; }
     vis_job jobs[256];

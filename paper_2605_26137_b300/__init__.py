@@ -1,4 +1,5 @@
-"""B300-native tangent-space normal baker (AssetGen, Sec. 6.4 "Normal Map Baking").
+"""B300-native tangent-space normal baker (AssetGen, Sec. 6.4 "Normal Map Baking"),
+with the hidden-face removal pass of Sec. 6.2 on the same BVH.
 
 The compute path is the CUDA library ``libagbake.so`` behind the C ABI of
 ``include/ag.h``; this package only marshals torch tensors into it.
@@ -8,7 +9,7 @@ import importlib
 from ._lib import EXPORTS, AgError, load as load_library  # noqa: F401
 
 _TORCH_API = ("Bvh", "BakeOutputs", "Asset", "BatchPlan", "BakeLoss", "bake", "bake_batch", "bake_backward",
-              "bake_loss", "alloc_outputs", "sync_status")
+              "bake_loss", "alloc_outputs", "sync_status", "visibility", "exterior_fill", "hidden_faces")
 
 
 def __getattr__(name):

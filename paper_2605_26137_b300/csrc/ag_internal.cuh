@@ -157,6 +157,10 @@ size_t vertex_normal_scratch_bytes(int64_t nv, int64_t nf);
 cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, int64_t nf,
                                   const float *given, float *acc_out, float4 *nrm, float4 *pos,
                                   void *scratch, cudaStream_t s);
+// vertex -> incident faces (CSR, unsorted lists) in the same scratch layout
+// as the vertex normals; faces with an out-of-range index are left out
+cudaError_t launch_vertex_face_csr(const int32_t *F, int64_t nf, int64_t nv, void *scratch, const unsigned **off,
+                                   const int32_t **list, cudaStream_t s);
 cudaError_t launch_face_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W,
                               int H, const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan,
                               int4 *uvfix, unsigned *status, cudaStream_t s);

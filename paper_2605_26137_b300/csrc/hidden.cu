@@ -1,0 +1,370 @@
+// Hidden-face removal (Sec. 6.2): a visibility pass that casts orthographic
+// rays from viewpoints spread over a sphere around the mesh through its BVH
+// and marks every face that is some ray's first hit, then a flood fill that
+// promotes faces linked to visible ones across edges whose two faces have
+// normals pointing the same way.
+//
+// Visibility (k_visibility): one persistent launch over all views.  A warp
+// takes 32 consecutive rays, an 8x4-pixel tile of one view, so its rays are
+// neighbours and share their node fetches.  View k looks along -u_k, u_k on
+// the Fibonacci (golden-angle) lattice; its res x res pixels tile the square
+// [-R, R]^2 of the plane through the bounding-box centre c spanned by
+// e1 = normalize(a x u) and e2 = u x e1 (a = +z, or +x when |u_z| >= 0.9);
+// pixel (i, j) casts from c + 2R u + x e1 + y e2, x = (2 (i + 1/2) / res - 1) R,
+// along -u.  The traversal and triangle test are those of the texel rays
+// (rays.cuh); origins lie outside the bounding sphere, so the closest |t| is
+// the first hit.  A hit stores 1 into the face's byte of the visibility mask.
+//
+// Exterior fill (k_flood): face normals n = (B - A) x (C - A) in FP64 with the
+// operations in a fixed order, so the gate n_f . n_g > 0 is decided exactly as
+// an FP64 evaluation of that expression; a vertex -> face adjacency gives each
+// face's edge neighbours; one CTA runs a level-synchronous breadth-first search
+// from all visible faces.  The exterior set (everything linked to a visible
+// face) does not depend on the visiting order.
+#include "rays.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+namespace ag {
+namespace {
+
+struct __align__(16) ViewGeom {
+    float4 base;   // c + 2R u
+    float4 e1, e2;
+    float4 dir;    // -u
+};
+
+struct VisArgs {
+    const void *nodes;
+    const float4 *tris;
+    const int32_t *tri_ids;
+    float scene_abs;
+    const ViewGeom *views;
+    int res, tiles_x;
+    long long rays_per_view, n_total;
+    float R, scale, tmax;
+    unsigned long long *counter;
+    unsigned *status;
+    int max_steps;
+    uint8_t *visible;
+    int32_t *hit_ids;
+    unsigned long long *counters;
+};
+
+template <int LAYOUT>
+__device__ __forceinline__ void visit_node(const VisArgs &A, uint32_t idx, const Ray &r, float lim, Next &nx,
+                                           uint2 *stack, int &sp) {
+    if (LAYOUT == AG_BVH_Q8)
+        NodeOps<AG_BVH_Q8>::visit(A.nodes, idx, r, lim, nx, stack, sp, A.status);
+    else
+        NodeOps<AG_BVH_F32>::visit(A.nodes, idx, r, lim, nx, stack, sp, A.status, A.scene_abs);
+}
+
+template <int LAYOUT, bool COUNT>
+__global__ void __launch_bounds__(256) k_visibility(VisArgs A) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long c_nodes = 0, c_tris = 0, c_rays = 0, c_hits = 0;
+    uint2 stack[STACK];
+    for (;;) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(A.counter, 32ull);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if ((long long)base >= A.n_total) break;
+        const long long r = (long long)base + lane;
+        if (r >= A.n_total) continue;
+        const int view = (int)(r / A.rays_per_view);
+        const long long rem = r - (long long)view * A.rays_per_view;
+        const int tile = (int)(rem >> 5), ln = (int)(rem & 31);
+        const int px = (tile % A.tiles_x) * 8 + (ln & 7);
+        const int py = (tile / A.tiles_x) * 4 + (ln >> 3);
+        if (px >= A.res || py >= A.res) continue;
+        const ViewGeom G = A.views[view];
+        const float x = __fmaf_rn((float)px + 0.5f, A.scale, -A.R);
+        const float y = __fmaf_rn((float)py + 0.5f, A.scale, -A.R);
+        const float3 off = f3(G.e1) * x + f3(G.e2) * y;
+        const Ray ray = make_ray(f3(G.base), off, f3(G.dir));
+        Best b;
+        b.t = 0.f; b.babs = A.tmax; b.rec = 0; b.found = false;
+        b.U = b.V = b.W = 0.f; b.det = 1.f;
+        uint32_t cur = 0;
+        int sp = 0, steps = 0;
+        if (COUNT) ++c_rays;
+        for (;;) {
+            Next nx;
+            nx.has = false;
+            nx.ref = 0;
+            nx.dist = 0.f;
+            if (ref_is_leaf(cur)) {
+                const uint32_t first = ref_first(cur);
+                const int cnt = ref_count(cur);
+                for (int k = 0; k < cnt; ++k) test_tri(ray, A.tris, A.tri_ids, first + k, b);
+                if (COUNT) c_tris += cnt;
+            } else {
+                visit_node<LAYOUT>(A, cur, ray, b.babs, nx, stack, sp);
+                if (COUNT) ++c_nodes;
+            }
+            if (nx.has) {
+                cur = nx.ref;
+            } else {
+                bool done = true;
+                while (sp > 0) {
+                    uint2 e = stack[--sp];
+                    if (__uint_as_float(e.y) <= b.babs) { cur = e.x; done = false; break; }
+                }
+                if (done) break;
+            }
+            if (++steps > A.max_steps) {
+                atomicOr(A.status, AGS_STEP_CAP);
+                break;
+            }
+        }
+        const int id = b.found ? A.tri_ids[b.rec] : -1;
+        if (b.found) {
+            A.visible[id] = 1;
+            if (COUNT) ++c_hits;
+        }
+        if (A.hit_ids) A.hit_ids[(long long)view * A.res * A.res + (long long)py * A.res + px] = id;
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) {
+            c_nodes += __shfl_xor_sync(0xffffffffu, c_nodes, o);
+            c_tris += __shfl_xor_sync(0xffffffffu, c_tris, o);
+            c_rays += __shfl_xor_sync(0xffffffffu, c_rays, o);
+            c_hits += __shfl_xor_sync(0xffffffffu, c_hits, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&A.counters[0], c_rays);
+            atomicAdd(&A.counters[1], c_nodes);
+            atomicAdd(&A.counters[2], c_tris);
+            atomicAdd(&A.counters[3], c_hits);
+        }
+    }
+}
+
+// FP64 face normals (fixed operation order) and the flood-fill state:
+// -1 = face with an out-of-range index (never linked), 1 = visible, 0 = not yet
+__global__ void k_face_normals64(const float *__restrict__ V, const int32_t *__restrict__ F, int64_t nf, int64_t nv,
+                                 const uint8_t *__restrict__ vis, double *__restrict__ nrm, int32_t *__restrict__ state,
+                                 unsigned *status) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int32_t i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+    if (i0 < 0 || i0 >= nv || i1 < 0 || i1 >= nv || i2 < 0 || i2 >= nv) {
+        state[f] = -1;
+        nrm[3 * f] = nrm[3 * f + 1] = nrm[3 * f + 2] = 0.0;
+        atomicOr(status, AGS_BAD_FACE);
+        return;
+    }
+    const double ax = V[3 * i0], ay = V[3 * i0 + 1], az = V[3 * i0 + 2];
+    const double e1x = __dsub_rn((double)V[3 * i1], ax), e1y = __dsub_rn((double)V[3 * i1 + 1], ay),
+                 e1z = __dsub_rn((double)V[3 * i1 + 2], az);
+    const double e2x = __dsub_rn((double)V[3 * i2], ax), e2y = __dsub_rn((double)V[3 * i2 + 1], ay),
+                 e2z = __dsub_rn((double)V[3 * i2 + 2], az);
+    nrm[3 * f] = __dsub_rn(__dmul_rn(e1y, e2z), __dmul_rn(e1z, e2y));
+    nrm[3 * f + 1] = __dsub_rn(__dmul_rn(e1z, e2x), __dmul_rn(e1x, e2z));
+    nrm[3 * f + 2] = __dsub_rn(__dmul_rn(e1x, e2y), __dmul_rn(e1y, e2x));
+    state[f] = vis[f] ? 1 : 0;
+}
+
+__device__ __forceinline__ bool same_side(const double *__restrict__ nrm, int64_t f, int64_t g) {
+    const double d = __dadd_rn(__dadd_rn(__dmul_rn(nrm[3 * f], nrm[3 * g]), __dmul_rn(nrm[3 * f + 1], nrm[3 * g + 1])),
+                               __dmul_rn(nrm[3 * f + 2], nrm[3 * g + 2]));
+    return d > 0.0;
+}
+
+constexpr int FLOOD_THREADS = 1024;
+
+// One CTA: level-synchronous BFS from every visible face.
+__global__ void __launch_bounds__(FLOOD_THREADS) k_flood(const int32_t *__restrict__ F, int64_t nf,
+                                                          const unsigned *__restrict__ off,
+                                                          const int32_t *__restrict__ list,
+                                                          const double *__restrict__ nrm, int32_t *state, int32_t *qa,
+                                                          int32_t *qb, uint8_t *__restrict__ ext) {
+    __shared__ int s_count;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+    for (int64_t f = tid; f < nf; f += FLOOD_THREADS)
+        if (state[f] == 1) qa[atomicAdd(&s_count, 1)] = (int32_t)f;
+    __syncthreads();
+    int cur = s_count;
+    __syncthreads();
+    while (cur > 0) {
+        if (tid == 0) s_count = 0;
+        __syncthreads();
+        for (int i = tid; i < cur; i += FLOOD_THREADS) {
+            const int32_t f = qa[i];
+            for (int m = 0; m < 3; ++m) {
+                const int32_t a = F[3 * (int64_t)f + m], b = F[3 * (int64_t)f + (m == 2 ? 0 : m + 1)];
+                if (a == b) continue;
+                for (unsigned j = off[a]; j < off[a + 1]; ++j) {
+                    const int32_t g = list[j];
+                    if (g == f) continue;
+                    const int32_t *G = F + 3 * (int64_t)g;
+                    if (G[0] != b && G[1] != b && G[2] != b) continue;
+                    if (!same_side(nrm, f, g)) continue;
+                    if (atomicCAS(&state[g], 0, 1) == 0) qb[atomicAdd(&s_count, 1)] = g;
+                }
+            }
+        }
+        __syncthreads();
+        cur = s_count;
+        int32_t *t = qa;
+        qa = qb;
+        qb = t;
+        __syncthreads();
+    }
+    for (int64_t f = tid; f < nf; f += FLOOD_THREADS) ext[f] = state[f] == 1 ? 1 : 0;
+}
+
+ag_status check_bvh(ag_bvh_t h) {
+    if (!h || h->magic != AG_BVH_MAGIC) return set_error(AG_ERR_BAD_HANDLE, "invalid BVH handle");
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != h->device) return set_error(AG_ERR_INVALID_ARG, "BVH handle belongs to device %d, current is %d",
+                                           h->device, dev);
+    return AG_OK;
+}
+
+// view k of n on the golden-angle lattice, in double precision, then FP32
+ViewGeom view_geom(int k, int n, const double c[3], double R) {
+    const double golden = 2.39996322972865332223;   // pi (3 - sqrt 5)
+    const double z = 1.0 - (2.0 * k + 1.0) / n;
+    const double rr = std::sqrt(std::fmax(0.0, 1.0 - z * z));
+    const double phi = k * golden;
+    const double u[3] = {rr * std::cos(phi), rr * std::sin(phi), z};
+    const double a[3] = {std::fabs(u[2]) < 0.9 ? 0.0 : 1.0, 0.0, std::fabs(u[2]) < 0.9 ? 1.0 : 0.0};
+    double e1[3] = {a[1] * u[2] - a[2] * u[1], a[2] * u[0] - a[0] * u[2], a[0] * u[1] - a[1] * u[0]};
+    const double l = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+    for (double &v : e1) v /= l;
+    const double e2[3] = {u[1] * e1[2] - u[2] * e1[1], u[2] * e1[0] - u[0] * e1[2], u[0] * e1[1] - u[1] * e1[0]};
+    ViewGeom g;
+    g.base = make_float4((float)(c[0] + 2.0 * R * u[0]), (float)(c[1] + 2.0 * R * u[1]), (float)(c[2] + 2.0 * R * u[2]), 0.f);
+    g.e1 = make_float4((float)e1[0], (float)e1[1], (float)e1[2], 0.f);
+    g.e2 = make_float4((float)e2[0], (float)e2[1], (float)e2[2], 0.f);
+    g.dir = make_float4((float)-u[0], (float)-u[1], (float)-u[2], 0.f);
+    return g;
+}
+
+template <int LAYOUT, bool COUNT>
+cudaError_t launch_vis(const VisArgs &A, int block, int bps, cudaStream_t s) {
+    int dev;
+    cudaGetDevice(&dev);
+    if (bps <= 0) {
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_visibility<LAYOUT, COUNT>, block, 0);
+        bps = occ > 0 ? occ : 1;
+    }
+    k_visibility<LAYOUT, COUNT><<<(unsigned)(device_sm_count(dev) * bps), block, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace ag
+
+using namespace ag;
+
+extern "C" {
+
+AG_API ag_status ag_visibility(ag_bvh_t h, int32_t n_views, int32_t res, const ag_opts *opts, ag_stream_t stream,
+                               uint8_t *d_visible, int32_t *d_hit_ids, uint64_t *d_counters) {
+    ag_status st = check_bvh(h);
+    if (st) return st;
+    if (n_views < 1 || n_views > (1 << 20)) return set_error(AG_ERR_INVALID_ARG, "n_views must be in 1..2^20");
+    if (res < 1 || res > 16384) return set_error(AG_ERR_INVALID_ARG, "res must be in 1..16384");
+    if (!d_visible) return set_error(AG_ERR_INVALID_ARG, "d_visible must be non-NULL");
+    ag_opts o;
+    ag_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.block_size != 0 && (o.block_size < 64 || o.block_size > 256 || o.block_size % 32))
+        return set_error(AG_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in 64..256");
+    if (o.blocks_per_sm < 0 || o.blocks_per_sm > 64) return set_error(AG_ERR_INVALID_ARG, "blocks_per_sm out of range");
+    if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *status = device_status_word(h->device);
+    if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    double c[3], R2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        c[k] = 0.5 * ((double)h->lo[k] + (double)h->hi[k]);
+        const double e = (double)h->hi[k] - (double)h->lo[k];
+        R2 += e * e;
+    }
+    const double R = 0.5 * std::sqrt(R2);
+    std::vector<ViewGeom> views((size_t)n_views);
+    for (int k = 0; k < n_views; ++k) views[(size_t)k] = view_geom(k, n_views, c, R);
+    Scratch sc(s, h->device);
+    ViewGeom *d_views;
+    unsigned long long *counter;
+    AG_CUDA(sc.alloc((void **)&d_views, sizeof(ViewGeom) * views.size()));
+    AG_CUDA(sc.alloc((void **)&counter, sizeof(unsigned long long)));
+    AG_CUDA(cudaMemcpyAsync(d_views, views.data(), sizeof(ViewGeom) * views.size(), cudaMemcpyHostToDevice, s));
+    AG_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
+    AG_CUDA(cudaMemsetAsync(d_visible, 0, (size_t)h->n_tris, s));
+    VisArgs A;
+    memset(&A, 0, sizeof(A));
+    A.nodes = h->nodes;
+    A.tris = h->tris;
+    A.tri_ids = h->tri_ids;
+    A.scene_abs = 0.f;
+    for (int k = 0; k < 3; ++k) A.scene_abs = fmaxf(A.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+    A.views = d_views;
+    A.res = res;
+    A.tiles_x = (res + 7) / 8;
+    A.rays_per_view = (long long)A.tiles_x * ((res + 3) / 4) * 32;
+    A.n_total = A.rays_per_view * n_views;
+    A.R = (float)R;
+    A.scale = (float)(2.0 * R / res);
+    A.tmax = (float)(4.0 * R);
+    A.counter = counter;
+    A.status = status;
+    A.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
+    A.visible = d_visible;
+    A.hit_ids = d_hit_ids;
+    A.counters = reinterpret_cast<unsigned long long *>(d_counters);
+    const int block = o.block_size > 0 ? o.block_size : 128;
+    const bool cnt = d_counters != nullptr;
+    cudaError_t e;
+    if (h->layout == AG_BVH_Q8)
+        e = cnt ? launch_vis<AG_BVH_Q8, true>(A, block, o.blocks_per_sm, s)
+                : launch_vis<AG_BVH_Q8, false>(A, block, o.blocks_per_sm, s);
+    else
+        e = cnt ? launch_vis<AG_BVH_F32, true>(A, block, o.blocks_per_sm, s)
+                : launch_vis<AG_BVH_F32, false>(A, block, o.blocks_per_sm, s);
+    if (e != cudaSuccess) return cuda_error(e, "k_visibility");
+    return AG_OK;
+}
+
+AG_API ag_status ag_exterior_fill(const float *d_verts, int64_t n_verts, const int32_t *d_faces, int64_t n_faces,
+                                  const uint8_t *d_visible, ag_stream_t stream, uint8_t *d_exterior) {
+    if (!d_verts || !d_faces || !d_visible || !d_exterior)
+        return set_error(AG_ERR_INVALID_ARG, "pointers must be non-NULL");
+    if (n_verts < 1 || n_verts >= (1ll << 31)) return set_error(AG_ERR_INVALID_ARG, "n_verts out of range");
+    if (n_faces < 1 || n_faces >= (1ll << 29)) return set_error(AG_ERR_INVALID_ARG, "n_faces out of range");
+    int dev = 0;
+    AG_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *status = device_status_word(dev);
+    if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    Scratch sc(s, dev);
+    void *csr;
+    double *nrm;
+    int32_t *state, *qa, *qb;
+    AG_CUDA(sc.alloc(&csr, vertex_normal_scratch_bytes(n_verts, n_faces)));
+    AG_CUDA(sc.alloc((void **)&nrm, sizeof(double) * 3 * (size_t)n_faces));
+    AG_CUDA(sc.alloc((void **)&state, sizeof(int32_t) * (size_t)n_faces));
+    AG_CUDA(sc.alloc((void **)&qa, sizeof(int32_t) * (size_t)n_faces));
+    AG_CUDA(sc.alloc((void **)&qb, sizeof(int32_t) * (size_t)n_faces));
+    const unsigned *off;
+    const int32_t *list;
+    AG_CUDA(launch_vertex_face_csr(d_faces, n_faces, n_verts, csr, &off, &list, s));
+    k_face_normals64<<<(unsigned)((n_faces + 255) / 256), 256, 0, s>>>(d_verts, d_faces, n_faces, n_verts, d_visible,
+                                                                         nrm, state, status);
+    AG_CUDA_LAUNCH("k_face_normals64");
+    k_flood<<<1, FLOOD_THREADS, 0, s>>>(d_faces, n_faces, off, list, nrm, state, qa, qb, d_exterior);
+    AG_CUDA_LAUNCH("k_flood");
+    return AG_OK;
+}
+
+}  // extern "C"

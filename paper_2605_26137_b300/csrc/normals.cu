@@ -106,6 +106,22 @@ cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, 
     return cudaGetLastError();
 }
 
+cudaError_t launch_vertex_face_csr(const int32_t *F, int64_t nf, int64_t nv, void *scratch, const unsigned **off_out,
+                                   const int32_t **list_out, cudaStream_t s) {
+    unsigned *off = static_cast<unsigned *>(scratch);   // [nv+1]
+    unsigned *fill = off + nv + 1;                      // [nv]
+    int32_t *list = reinterpret_cast<int32_t *>(fill + nv);  // [3nf]
+    unsigned *scan_tmp = reinterpret_cast<unsigned *>(list + 3 * nf);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(off, 0, sizeof(unsigned) * (size_t)(2 * nv + 1), s)) != cudaSuccess) return e;
+    k_degree<<<grid_for(nf, 256), 256, 0, s>>>(F, nf, nv, off);
+    if ((e = launch_scan_exclusive(off, nv, off + nv, scan_tmp, s)) != cudaSuccess) return e;
+    k_fill<<<grid_for(nf, 256), 256, 0, s>>>(F, nf, nv, off, fill, list);
+    *off_out = off;
+    *list_out = list;
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Vertex normals without any allocation, for callers that cannot allocate
 // device memory themselves or through this library (see

@@ -22,179 +22,10 @@
 //     counts as inside;
 //   - ties: equal |t| prefers t >= 0, equal t the lower original id.
 // The backward variant replaces the shading with the adjoint of the loss.
-#include "traverse.cuh"
+#include "rays.cuh"
 
 namespace ag {
 namespace {
-
-struct Ray {
-    // exact-origin triangle test: permuted axes, shear, origin as base + offset
-    int kx, ky, kz;
-    float Sx, Sy, Sz;
-    float bx, by, bz;
-    float ox, oy, oz;
-    // box test: rounded origin, 1/d with zero components made tiny, direction signs
-    float px, py, pz;
-    float ix, iy, iz;
-    bool nx, ny, nz;
-};
-
-__device__ __forceinline__ float pick(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
-
-__device__ __forceinline__ Ray make_ray(float3 base, float3 off, float3 d) {
-    Ray r;
-    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-    r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-    r.kx = r.kz == 2 ? 0 : r.kz + 1;
-    r.ky = r.kx == 2 ? 0 : r.kx + 1;
-    float dz = pick(d, r.kz);
-    if (dz < 0.f) { int t = r.kx; r.kx = r.ky; r.ky = t; }
-    r.Sx = pick(d, r.kx) / dz;
-    r.Sy = pick(d, r.ky) / dz;
-    r.Sz = 1.0f / dz;
-    r.bx = pick(base, r.kx); r.by = pick(base, r.ky); r.bz = pick(base, r.kz);
-    r.ox = pick(off, r.kx); r.oy = pick(off, r.ky); r.oz = pick(off, r.kz);
-    float3 p = base + off;
-    r.px = p.x; r.py = p.y; r.pz = p.z;
-    float3 dd = d;
-    if (fabsf(dd.x) < 1e-30f) dd.x = copysignf(1e-30f, dd.x);
-    if (fabsf(dd.y) < 1e-30f) dd.y = copysignf(1e-30f, dd.y);
-    if (fabsf(dd.z) < 1e-30f) dd.z = copysignf(1e-30f, dd.z);
-    r.ix = 1.0f / dd.x; r.iy = 1.0f / dd.y; r.iz = 1.0f / dd.z;
-    r.nx = r.ix < 0.f; r.ny = r.iy < 0.f; r.nz = r.iz < 0.f;
-    return r;
-}
-
-// vertex in ray space: (v - base) - offset, permuted and sheared
-__device__ __forceinline__ void xform(const Ray &r, float4 v, float &X, float &Y, float &Z) {
-    float3 a = make_float3(v.x, v.y, v.z);
-    float ax = __fsub_rn(__fsub_rn(pick(a, r.kx), r.bx), r.ox);
-    float ay = __fsub_rn(__fsub_rn(pick(a, r.ky), r.by), r.oy);
-    float az = __fsub_rn(__fsub_rn(pick(a, r.kz), r.bz), r.oz);
-    X = __fmaf_rn(-r.Sx, az, ax);
-    Y = __fmaf_rn(-r.Sy, az, ay);
-    Z = __fmul_rn(r.Sz, az);
-}
-
-struct Best {
-    float t, babs;
-    uint32_t rec;
-    float U, V, W, det;
-    bool found;
-};
-
-__device__ __forceinline__ void test_tri(const Ray &r, const float4 *__restrict__ tris,
-                                         const int32_t *__restrict__ tri_ids, uint32_t rec, Best &b) {
-    float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
-    float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
-    xform(r, A, Ax, Ay, Az);
-    xform(r, B, Bx, By, Bz);
-    xform(r, C, Cx, Cy, Cz);
-    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return;
-    float det = U + V + W;
-    if (det == 0.f) return;
-    float T = U * Az + V * Bz + W * Cz;
-    // |T / det| <= babs, tested without the division (with slack; exact below)
-    if (fabsf(T) > b.babs * fabsf(det) * 1.0000010f) return;
-    float t = T / det;
-    float at = fabsf(t);
-    if (!(at <= b.babs)) return;
-    if (b.found && at == b.babs) {
-        if ((t >= 0.f) != (b.t >= 0.f)) {
-            if (t < 0.f) return;
-        } else if (t != b.t || tri_ids[rec] >= tri_ids[b.rec]) {
-            return;
-        }
-    }
-    b.t = t; b.babs = at; b.rec = rec; b.U = U; b.V = V; b.W = W; b.det = det; b.found = true;
-}
-
-template <int LAYOUT>
-struct NodeOps;
-
-// 80-byte quantised node.  Per node and axis the child planes become one FMA
-// each: t(q) = q * a + b with a = 2^e / d and b = (origin - p) / d.  The
-// intervals are widened by eps = 2^-21 (|origin| + |p| + 255 * 2^e) / |d|,
-// which bounds every rounding on the way (decoded plane, a, b, the FMA, the
-// rounded ray origin) by a factor of at least 4, so a box the exact line
-// meets is never rejected.
-template <>
-struct NodeOps<AG_BVH_Q8> {
-    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim, Next &nx,
-                                                 uint2 *stack, int &sp, unsigned *status) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const QNode *>(nodes) + idx);
-        uint4 w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2), w3 = __ldg(p + 3), w4 = __ldg(p + 4);
-        float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
-        float sx = __uint_as_float((w0.w & 0xffu) << 23);
-        float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
-        float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
-        float ax = sx * r.ix, ay = sy * r.iy, az = sz * r.iz;
-        float bx = (ox - r.px) * r.ix, by = (oy - r.py) * r.iy, bz = (oz - r.pz) * r.iz;
-        float ex = EPS_REL * (fabsf(ox) + fabsf(r.px) + 255.f * sx) * fabsf(r.ix);
-        float ey = EPS_REL * (fabsf(oy) + fabsf(r.py) + 255.f * sy) * fabsf(r.iy);
-        float ez = EPS_REL * (fabsf(oz) + fabsf(r.pz) + 255.f * sz) * fabsf(r.iz);
-        float bnx = bx - ex, bfx = bx + ex, bny = by - ey, bfy = by + ey, bnz = bz - ez, bfz = bz + ez;
-        // near-plane bytes: lo for d > 0, hi for d < 0
-        uint32_t nx0 = r.nx ? w3.z : w2.x, nx1 = r.nx ? w3.w : w2.y, fx0 = r.nx ? w2.x : w3.z, fx1 = r.nx ? w2.y : w3.w;
-        uint32_t ny0 = r.ny ? w4.x : w2.z, ny1 = r.ny ? w4.y : w2.w, fy0 = r.ny ? w2.z : w4.x, fy1 = r.ny ? w2.w : w4.y;
-        uint32_t nz0 = r.nz ? w4.z : w3.x, nz1 = r.nz ? w4.w : w3.y, fz0 = r.nz ? w3.x : w4.z, fz1 = r.nz ? w3.y : w4.w;
-        uint32_t child_base = w1.x, tri_base = w1.y;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int k = c & 3;
-            const bool hi = c >= 4;
-            uint32_t m = ((hi ? w1.w : w1.z) >> (8 * k)) & 0xffu;
-            float tnx = __fmaf_rn(byte_f(hi ? nx1 : nx0, k), ax, bnx);
-            float tfx = __fmaf_rn(byte_f(hi ? fx1 : fx0, k), ax, bfx);
-            float tny = __fmaf_rn(byte_f(hi ? ny1 : ny0, k), ay, bny);
-            float tfy = __fmaf_rn(byte_f(hi ? fy1 : fy0, k), ay, bfy);
-            float tnz = __fmaf_rn(byte_f(hi ? nz1 : nz0, k), az, bnz);
-            float tfz = __fmaf_rn(byte_f(hi ? fz1 : fz0, k), az, bfz);
-            float te = fmaxf(fmaxf(tnx, tny), tnz);
-            float tx = fminf(fminf(tfx, tfy), tfz);
-            if (m != 0 && te <= tx && te <= lim && tx >= -lim)
-                offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status);
-        }
-    }
-};
-
-// 208-byte node with exact FP32 child boxes: t = plane / d - p / d, widened by
-// eps = 2^-21 (scene bound + |p|) / |d| per axis.
-template <>
-struct NodeOps<AG_BVH_F32> {
-    static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim, Next &nx,
-                                                 uint2 *stack, int &sp, unsigned *status, float scene_abs) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const FNode *>(nodes) + idx);
-        uint4 h = __ldg(p);
-        uint32_t child_base = h.x, tri_base = h.y;
-        float ex = EPS_REL * (scene_abs + fabsf(r.px)) * fabsf(r.ix);
-        float ey = EPS_REL * (scene_abs + fabsf(r.py)) * fabsf(r.iy);
-        float ez = EPS_REL * (scene_abs + fabsf(r.pz)) * fabsf(r.iz);
-        float cx = -r.px * r.ix, cy = -r.py * r.iy, cz = -r.pz * r.iz;
-        float cnx = cx - ex, cfx = cx + ex, cny = cy - ey, cfy = cy + ey, cnz = cz - ez, cfz = cz + ez;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            uint4 lx = __ldg(p + 1 + half), ly = __ldg(p + 3 + half), lz = __ldg(p + 5 + half);
-            uint4 hx = __ldg(p + 7 + half), hy = __ldg(p + 9 + half), hz = __ldg(p + 11 + half);
-            const uint32_t LX[4] = {lx.x, lx.y, lx.z, lx.w}, LY[4] = {ly.x, ly.y, ly.z, ly.w}, LZ[4] = {lz.x, lz.y, lz.z, lz.w};
-            const uint32_t HX[4] = {hx.x, hx.y, hx.z, hx.w}, HY[4] = {hy.x, hy.y, hy.z, hy.w}, HZ[4] = {hz.x, hz.y, hz.z, hz.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                uint32_t m = ((half ? h.w : h.z) >> (8 * k)) & 0xffu;
-                float plx = __uint_as_float(r.nx ? HX[k] : LX[k]), pfx = __uint_as_float(r.nx ? LX[k] : HX[k]);
-                float ply = __uint_as_float(r.ny ? HY[k] : LY[k]), pfy = __uint_as_float(r.ny ? LY[k] : HY[k]);
-                float plz = __uint_as_float(r.nz ? HZ[k] : LZ[k]), pfz = __uint_as_float(r.nz ? LZ[k] : HZ[k]);
-                float te = fmaxf(fmaxf(__fmaf_rn(plx, r.ix, cnx), __fmaf_rn(ply, r.iy, cny)), __fmaf_rn(plz, r.iz, cnz));
-                float tx = fminf(fminf(__fmaf_rn(pfx, r.ix, cfx), __fmaf_rn(pfy, r.iy, cfy)), __fmaf_rn(pfz, r.iz, cfz));
-                if (m != 0 && te <= tx && te <= lim && tx >= -lim)
-                    offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status);
-            }
-        }
-    }
-};
 
 // Per-lane traversal state of one ray.
 struct RayState {

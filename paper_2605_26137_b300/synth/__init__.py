@@ -263,6 +263,43 @@ def sdf_mesh_target(params: SdfParams, target_faces: int, probe_n: int = 64,
     return V, F
 
 
+def hidden_face_mesh(seed: int, target_faces: int = 22_000, n_inner: int = 8, inner_level: int = 2,
+                     n_prims: int = 16, device=None):
+    """Stand-in for a generated mesh with interior faces (the input of
+    hidden-face removal): the closed marching-grid surface of a seeded SDF
+    union, plus n_inner closed icospheres (20 * 4^inner_level faces each)
+    placed wholly inside the solid: a shell of radius r needs a field value
+    below -(2 r + 2 h + k) at its centre (h the grid spacing, k the smooth-min
+    width), room for the extracted surface's departures from the field's zero
+    set on coarse grids.  Returns (V, F, inner) with inner [F] bool marking
+    the interior shells' faces."""
+    import torch
+    params = sdf_union_params(seed, n_prims=n_prims)
+    ico_v, ico_f = icosphere(inner_level)
+    outer_target = max(1000, target_faces - n_inner * len(ico_f))
+    Vo, Fo = sdf_mesh_target(params, outer_target, device=device)
+    h = 2.5 / (params.meta[f"grid_for_{outer_target}"] - 1)
+    rng = np.random.default_rng(seed + 7919)
+    pts = rng.uniform(-1.0, 1.0, size=(20000, 3))
+    d = sdf_eval(torch.as_tensor(pts, dtype=torch.float64), params).numpy()
+    Vs, Fs, inner = [Vo], [Fo], [np.zeros(len(Fo), bool)]
+    nv = len(Vo)
+    placed = []
+    for i in np.argsort(d):
+        if len(placed) == n_inner or d[i] >= 0:
+            break
+        r = min(0.5 * (-d[i] - 2.0 * h - params.k), 0.12)
+        c = pts[i]
+        if r < 0.01 or any(np.linalg.norm(c - q) < r + rq + 0.01 for q, rq in placed):
+            continue
+        placed.append((c, r))
+        Vs.append((ico_v.astype(np.float64) * r + c).astype(np.float32))
+        Fs.append(ico_f + nv)
+        inner.append(np.ones(len(ico_f), bool))
+        nv += len(ico_v)
+    return np.concatenate(Vs), np.concatenate(Fs).astype(np.int32), np.concatenate(inner)
+
+
 # --------------------------------------------------------------------------
 # UV atlases (per-corner UVs, [F,3,2] float32)
 # --------------------------------------------------------------------------

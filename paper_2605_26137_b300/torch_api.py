@@ -301,6 +301,51 @@ class BatchPlan:
             pass
 
 
+# ----------------------------------------------------------------- hidden-face removal (Sec. 6.2)
+
+def visibility(bvh: Bvh, n_views: int = 512, res: int = 1024, *, hit_ids: bool = False, counters: bool = False,
+               block_size: int = 0, blocks_per_sm: int = 0, max_steps: int = 0, stream=None):
+    """Per-face visibility of the mesh ``bvh`` was built on, from n_views
+    orthographic res x res views on the Fibonacci lattice around it.
+    Returns (visible u8 [n_faces], hit_ids int32 [n_views, res, res] or None,
+    counters u64 [4] (rays, node visits, triangle tests, hits) or None)."""
+    lib = _lib.load()
+    n = bvh.info()["n_tris"]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    vis = torch.empty(n, dtype=torch.uint8, device=dev)
+    hits = torch.empty((n_views, res, res), dtype=torch.int32, device=dev) if hit_ids else None
+    cnt = torch.zeros(4, dtype=torch.int64, device=dev) if counters else None
+    o = _opts(block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps)
+    check(lib.ag_visibility(bvh.handle, n_views, res, ctypes.byref(o), _stream(stream), vis.data_ptr(), _ptr(hits),
+                            _ptr(cnt)))
+    return vis, hits, cnt
+
+
+def exterior_fill(verts, faces, visible, *, stream=None):
+    """Exterior faces (u8 [n_faces], 1 = keep) from a visibility mask by the
+    normal-gated flood fill."""
+    lib = _lib.load()
+    _need(verts, "verts", torch.float32, (3,))
+    _need(faces, "faces", torch.int32, (3,))
+    _need(visible, "visible", torch.uint8)
+    if visible.shape[0] != faces.shape[0]:
+        raise ValueError("visible must have one entry per face")
+    ext = torch.empty(faces.shape[0], dtype=torch.uint8, device=faces.device)
+    check(lib.ag_exterior_fill(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0],
+                               visible.data_ptr(), _stream(stream), ext.data_ptr()))
+    return ext
+
+
+def hidden_faces(verts, faces, n_views: int = 512, res: int = 1024, *, stream=None, **kw):
+    """Hidden-face removal in one call: (exterior u8 [n_faces], visible u8)."""
+    bvh = Bvh(verts, faces, stream=stream)
+    try:
+        vis, _, _ = visibility(bvh, n_views, res, stream=stream, **kw)
+        return exterior_fill(verts, faces, vis, stream=stream), vis
+    finally:
+        bvh.free()
+
+
 def sync_status(stream=None) -> None:
     """Synchronise and raise AgError if a device-side limit was hit."""
     check(_lib.load().ag_sync_status(_stream(stream)))
