@@ -10,9 +10,10 @@ closest-hit traversal with shading, dilation and encoding); the BVH is built
 once per high mesh and timed separately.  The metric is rays per second
 (ray texels baked per second, whole bake) and ms per bake; beside it the
 batched-vs-one-by-one speedup, the backward/forward time ratio, the
-quantised-vs-FP32 BVH comparison and the closest-point correspondence (Sec.
+quantised-vs-FP32 BVH comparison, the closest-point correspondence (Sec.
 6.4 as worded) on the same asset, with its angular difference from the ray
-bake.
+bake, and hidden-face removal (Sec. 6.2: 512 views x 1024^2 rays against a
+~22k-face mesh with interior shells, then the exterior flood fill).
 
 --impl reference times the FP64 CPU oracle (the repository's plain,
 deliberately slow reference) on a bounded sample of the same workload.
@@ -71,10 +72,14 @@ def parse():
     p.add_argument("--profile", action="store_true",
                    help="profiling case for ncu: one BVH build and --steps plain bakes, nothing else")
     p.add_argument("--layout", default="q8", choices=["q8", "f32"])
-    p.add_argument("--query", default="ray", choices=["ray", "closest"], help="--profile: correspondence query")
+    p.add_argument("--query", default="ray", choices=["ray", "closest", "hidden"],
+                   help="--profile: the ray or closest-point bake, or the hidden-face visibility pass")
     p.add_argument("--error-sample", type=float, default=20000,
                    help="ray texels compared with the oracle per layout (a value < 1 is a fraction of them)")
     p.add_argument("--collapse", default="area", choices=["area_count", "area", "count"])
+    p.add_argument("--hidden-views", type=int, default=512, help="hidden-face removal: viewpoints")
+    p.add_argument("--hidden-res", type=int, default=1024, help="hidden-face removal: image resolution")
+    p.add_argument("--hidden-faces", type=int, default=22000, help="hidden-face removal: mesh faces")
     return p.parse_args()
 
 
@@ -93,8 +98,10 @@ def peaks():
     return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh"), "closest": ("closest.cu", "traverse.cuh")}
-PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_2048_2M.md"}
+KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh", "rays.cuh"), "closest": ("closest.cu", "traverse.cuh"),
+                  "visibility": ("hidden.cu", "traverse.cuh", "rays.cuh")}
+PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_2048_2M.md",
+                 "visibility": "visibility_kernel_22k_512x1024.md"}
 
 
 def trace_source_hash(kernel: str = "trace"):
@@ -238,6 +245,23 @@ def run_profile(args):
                       "query": args.query, "bakes": args.steps, "kernel_source_hash": trace_source_hash(kernel)}))
 
 
+def run_profile_hidden(args):
+    """Few launches of the visibility pass on the hidden-face workload."""
+    import torch
+    import paper_2605_26137_b300 as pb
+    from paper_2605_26137_b300 import synth
+    torch.cuda.set_device(0)
+    V, F, _ = synth.hidden_face_mesh(args.seed, target_faces=args.hidden_faces, device="cuda")
+    v, f = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (V, F))
+    bvh = pb.Bvh(v, f)
+    for _ in range(args.steps):
+        vis, _, _ = pb.visibility(bvh, args.hidden_views, args.hidden_res)
+        pb.exterior_fill(v, f, vis)
+    pb.sync_status()
+    print(json.dumps({"profile_case": "hidden-face removal", "faces": int(len(F)), "views": args.hidden_views,
+                      "res": args.hidden_res, "kernel_source_hash": trace_source_hash("visibility")}))
+
+
 def to_dev(a, torch):
     def t(x):
         return torch.from_numpy(np.ascontiguousarray(x)).cuda()
@@ -339,7 +363,10 @@ def main():
         run_reference(args)
         return
     if args.profile:
-        run_profile(args)
+        if args.query == "hidden":
+            run_profile_hidden(args)
+        else:
+            run_profile(args)
         return
     import torch
     import paper_2605_26137_b300 as pb
@@ -535,9 +562,57 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     res["layout_q8_error_vs_oracle"] = layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, args.error_sample)
     bf.free()
     res["closest_point"] = closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush)
+    res["hidden_face_removal"] = hidden_leg(args, pb, torch, dev, flush)
     if args.batch_assets > 0:
         res["batch"] = batch_leg(args, pb, torch, dev, flush)
     return res
+
+
+def hidden_leg(args, pb, torch, dev, flush):
+    """Hidden-face removal (Sec. 6.2) in the paper's configuration: BVH over a
+    ~22k-face generated-mesh stand-in with closed interior shells, visibility
+    from 512 orthographic 1024^2 views, exterior flood fill.  The paper quotes
+    0.179 s per mesh for its kernel (other hardware: context, not a target)."""
+    from paper_2605_26137_b300 import synth
+    V, F, inner = synth.hidden_face_mesh(args.seed, target_faces=args.hidden_faces, device=dev)
+    v, f = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (V, F))
+    nv, nres = args.hidden_views, args.hidden_res
+    bvh = pb.Bvh(v, f)
+    _, _, cnt = pb.visibility(bvh, nv, nres, counters=True)
+    pb.sync_status()
+    c = cnt.cpu().numpy().astype(np.float64)
+    vis = ext = None
+    for _ in range(2):
+        vis, _, _ = pb.visibility(bvh, nv, nres)
+        ext = pb.exterior_fill(v, f, vis)
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record()
+        vis, _, _ = pb.visibility(bvh, nv, nres)
+        ev[i][1].record()
+        ext = pb.exterior_fill(v, f, vis)
+        ev[i][2].record()
+    torch.cuda.synchronize()
+    pb.sync_status()
+    vis_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    fill_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    info = bvh.info()
+    bvh.free()
+    visn, extn = vis.cpu().numpy().astype(bool), ext.cpu().numpy().astype(bool)
+    rays = float(nv) * nres * nres
+    return {"mesh": {"faces": int(len(F)), "interior_shell_faces": int(inner.sum()), "bvh_build_ms": info["build_ms"]},
+            "views": nv, "res": nres, "rays": int(rays),
+            "visibility_ms": vis_ms, "fill_ms": fill_ms, "total_ms": vis_ms + fill_ms,
+            "grays_s": rays / vis_ms / 1e6,
+            "per_ray": {"nodes": c[1] / c[0], "tris": c[2] / c[0], "hit_frac": c[3] / c[0]},
+            "faces_visible": int(visn.sum()), "faces_exterior": int(extn.sum()),
+            "interior_shell_faces_kept": int(extn[inner].sum()),
+            "outer_faces_removed": int((~extn[~inner]).sum()),
+            "traffic": recorded_traffic("q8", nres, int(len(F)), "visibility"),
+            "paper_kernel_s": 0.179}
 
 
 def closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush):

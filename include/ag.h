@@ -319,7 +319,8 @@ AG_API ag_status ag_autotune(ag_bvh_t h, const float *d_lverts, const float *d_l
  *              triangle tests, hits (selects the counting build).
  *   opts: block_size (64..256), blocks_per_sm, max_steps are used.
  *   Errors: AG_ERR_BAD_HANDLE, AG_ERR_INVALID_ARG (n_views outside 1..2^20,
- *   res outside 1..16384, NULL d_visible); the step cap sets the status word.
+ *   res outside 1..16384, n_views * ceil(res/8) * ceil(res/4) >= 2^31, NULL
+ *   d_visible); the step cap sets the status word.
  */
 AG_API ag_status ag_visibility(ag_bvh_t h, int32_t n_views, int32_t res, const ag_opts *opts,
                                ag_stream_t stream, uint8_t *d_visible, int32_t *d_hit_ids,

@@ -41,9 +41,10 @@ struct VisArgs {
     const float4 *tris;
     const int32_t *tri_ids;
     float scene_abs;
+    float3 lo, hi;          // scene bounding box
     const ViewGeom *views;
-    int res, tiles_x;
-    long long rays_per_view, n_total;
+    const Ray *templ;       // per view: the ray of make_ray for its direction, origin = view base
+    int res, tiles_x, tiles_per_view, n_tiles;
     float R, scale, tmax;
     unsigned long long *counter;
     unsigned *status;
@@ -62,36 +63,63 @@ __device__ __forceinline__ void visit_node(const VisArgs &A, uint32_t idx, const
         NodeOps<AG_BVH_F32>::visit(A.nodes, idx, r, lim, nx, stack, sp, A.status, A.scene_abs);
 }
 
+// the direction-dependent part of every ray of a view, once per view
+__global__ void k_view_rays(const ViewGeom *__restrict__ views, int n, Ray *__restrict__ templ) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const ViewGeom G = views[k];
+    templ[k] = make_ray(f3(G.base), make_float3(0.f, 0.f, 0.f), f3(G.dir));
+}
+
+// false only when the ray misses the scene box even widened by the rounding
+// slack of the node tests, so no node of the tree can accept it
+__device__ __forceinline__ bool meets_scene(const VisArgs &A, const Ray &r) {
+    const float ex = EPS_REL * (A.scene_abs + fabsf(r.px)) * fabsf(r.ix);
+    const float ey = EPS_REL * (A.scene_abs + fabsf(r.py)) * fabsf(r.iy);
+    const float ez = EPS_REL * (A.scene_abs + fabsf(r.pz)) * fabsf(r.iz);
+    const float ax = (A.lo.x - r.px) * r.ix, bx = (A.hi.x - r.px) * r.ix;
+    const float ay = (A.lo.y - r.py) * r.iy, by = (A.hi.y - r.py) * r.iy;
+    const float az = (A.lo.z - r.pz) * r.iz, bz = (A.hi.z - r.pz) * r.iz;
+    const float te = fmaxf(fmaxf(fminf(ax, bx) - ex, fminf(ay, by) - ey), fminf(az, bz) - ez);
+    const float tx = fminf(fminf(fmaxf(ax, bx) + ex, fmaxf(ay, by) + ey), fmaxf(az, bz) + ez);
+    return te <= tx && te <= A.tmax && tx >= -A.tmax;
+}
+
 template <int LAYOUT, bool COUNT>
 __global__ void __launch_bounds__(256) k_visibility(VisArgs A) {
     const int lane = threadIdx.x & 31;
     unsigned long long c_nodes = 0, c_tris = 0, c_rays = 0, c_hits = 0;
     uint2 stack[STACK];
     for (;;) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(A.counter, 32ull);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if ((long long)base >= A.n_total) break;
-        const long long r = (long long)base + lane;
-        if (r >= A.n_total) continue;
-        const int view = (int)(r / A.rays_per_view);
-        const long long rem = r - (long long)view * A.rays_per_view;
-        const int tile = (int)(rem >> 5), ln = (int)(rem & 31);
-        const int px = (tile % A.tiles_x) * 8 + (ln & 7);
-        const int py = (tile / A.tiles_x) * 4 + (ln >> 3);
+        // a warp takes one 8x4 tile: view and tile position are warp-uniform
+        int tile = 0;
+        if (lane == 0) tile = (int)atomicAdd(A.counter, 1ull);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= A.n_tiles) break;
+        const int view = tile / A.tiles_per_view;
+        const int t = tile - view * A.tiles_per_view;
+        const int ty = t / A.tiles_x;
+        const int px = (t - ty * A.tiles_x) * 8 + (lane & 7);
+        const int py = ty * 4 + (lane >> 3);
         if (px >= A.res || py >= A.res) continue;
         const ViewGeom G = A.views[view];
         const float x = __fmaf_rn((float)px + 0.5f, A.scale, -A.R);
         const float y = __fmaf_rn((float)py + 0.5f, A.scale, -A.R);
         const float3 off = f3(G.e1) * x + f3(G.e2) * y;
-        const Ray ray = make_ray(f3(G.base), off, f3(G.dir));
+        Ray ray = A.templ[view];
+        {
+            const float3 base = f3(G.base);
+            ray.ox = pick(off, ray.kx); ray.oy = pick(off, ray.ky); ray.oz = pick(off, ray.kz);
+            const float3 p = base + off;
+            ray.px = p.x; ray.py = p.y; ray.pz = p.z;
+        }
         Best b;
         b.t = 0.f; b.babs = A.tmax; b.rec = 0; b.found = false;
         b.U = b.V = b.W = 0.f; b.det = 1.f;
         uint32_t cur = 0;
         int sp = 0, steps = 0;
         if (COUNT) ++c_rays;
-        for (;;) {
+        for (bool live = meets_scene(A, ray); live;) {
             Next nx;
             nx.has = false;
             nx.ref = 0;
@@ -117,7 +145,7 @@ __global__ void __launch_bounds__(256) k_visibility(VisArgs A) {
             }
             if (++steps > A.max_steps) {
                 atomicOr(A.status, AGS_STEP_CAP);
-                break;
+                live = false;
             }
         }
         const int id = b.found ? A.tri_ids[b.rec] : -1;
@@ -296,10 +324,14 @@ AG_API ag_status ag_visibility(ag_bvh_t h, int32_t n_views, int32_t res, const a
     for (int k = 0; k < n_views; ++k) views[(size_t)k] = view_geom(k, n_views, c, R);
     Scratch sc(s, h->device);
     ViewGeom *d_views;
+    Ray *d_templ;
     unsigned long long *counter;
     AG_CUDA(sc.alloc((void **)&d_views, sizeof(ViewGeom) * views.size()));
+    AG_CUDA(sc.alloc((void **)&d_templ, sizeof(Ray) * views.size()));
     AG_CUDA(sc.alloc((void **)&counter, sizeof(unsigned long long)));
     AG_CUDA(cudaMemcpyAsync(d_views, views.data(), sizeof(ViewGeom) * views.size(), cudaMemcpyHostToDevice, s));
+    k_view_rays<<<(unsigned)((n_views + 127) / 128), 128, 0, s>>>(d_views, n_views, d_templ);
+    AG_CUDA_LAUNCH("k_view_rays");
     AG_CUDA(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s));
     AG_CUDA(cudaMemsetAsync(d_visible, 0, (size_t)h->n_tris, s));
     VisArgs A;
@@ -309,11 +341,16 @@ AG_API ag_status ag_visibility(ag_bvh_t h, int32_t n_views, int32_t res, const a
     A.tri_ids = h->tri_ids;
     A.scene_abs = 0.f;
     for (int k = 0; k < 3; ++k) A.scene_abs = fmaxf(A.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+    A.lo = make_float3(h->lo[0], h->lo[1], h->lo[2]);
+    A.hi = make_float3(h->hi[0], h->hi[1], h->hi[2]);
     A.views = d_views;
+    A.templ = d_templ;
     A.res = res;
     A.tiles_x = (res + 7) / 8;
-    A.rays_per_view = (long long)A.tiles_x * ((res + 3) / 4) * 32;
-    A.n_total = A.rays_per_view * n_views;
+    A.tiles_per_view = A.tiles_x * ((res + 3) / 4);
+    if ((long long)A.tiles_per_view * n_views >= (1ll << 31))
+        return set_error(AG_ERR_INVALID_ARG, "n_views * res^2 exceeds 2^36 rays");
+    A.n_tiles = A.tiles_per_view * n_views;
     A.R = (float)R;
     A.scale = (float)(2.0 * R / res);
     A.tmax = (float)(4.0 * R);
