@@ -23,7 +23,8 @@ def declared_symbols():
     names = set()
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
-            src = open(os.path.join(ROOT, "include", fn)).read()
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                src = f.read()
             names |= set(re.findall(r"AG_API\s+[\w\s\*]+?\b(ag_\w+)\s*\(", src))
     return names
 
