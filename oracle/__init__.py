@@ -82,6 +82,14 @@ def _load():
         lib.or_visibility.restype = _I
         lib.or_exterior_fill.argtypes = [_P, _P, _I64, _I64, _P, _P]
         lib.or_exterior_fill.restype = _I
+        lib.or_qem_simplify.argtypes = [_P, _I64, _P, _I64, _I64, _P, _P, _I, _P]
+        lib.or_qem_simplify.restype = _I
+        lib.or_qem_face_quadric.argtypes = [_P, _P]
+        lib.or_qem_face_quadric.restype = None
+        lib.or_qem_eval.argtypes = [_P, _P]
+        lib.or_qem_eval.restype = _D
+        lib.or_qem_place.argtypes = [_P, _P, _P, _P]
+        lib.or_qem_place.restype = _D
         _lib = lib
         return lib
 
@@ -375,3 +383,49 @@ def exterior_fill(V, F, visible, nv=None):
     if lib.or_exterior_fill(_p(V), _p(F), nv if nv is not None else len(V), len(F), _p(vis), _p(ext)) != 0:
         raise MemoryError("oracle exterior fill: allocation failed")
     return ext
+
+
+# ----------------------------------------------------------------- QEM simplification (Sec. 6.1)
+
+def qem_face_quadric(P):
+    """The 10 unique entries (q00 q01 q02 q03 q11 q12 q13 q22 q23 q33) of the
+    plane quadric of triangle P [3,3]."""
+    q = np.zeros(10, np.float64)
+    _load().or_qem_face_quadric(_p(_c(P, np.float64)), _p(q))
+    return q
+
+
+def qem_eval(q, v) -> float:
+    return float(_load().or_qem_eval(_p(_c(q, np.float64)), _p(_c(v, np.float64))))
+
+
+def qem_place(q, v0, v1):
+    """Edge parameter t of the paper's placement and the singular flag."""
+    sing = ctypes.c_int()
+    t = _load().or_qem_place(_p(_c(q, np.float64)), _p(_c(v0, np.float64)), _p(_c(v1, np.float64)),
+                             ctypes.byref(sing))
+    return float(t), bool(sing.value)
+
+
+def qem_simplify(V, F, target: int, max_rounds: int = 100000):
+    """Simplify to at most ``target`` faces.  Returns a dict: V (float64, the
+    surviving vertices in increasing original id), F (renumbered, surviving
+    faces in increasing original id), keep_v / keep_f (original ids),
+    rounds, and per round the alive face count and the number of collapses."""
+    lib = _load()
+    V64 = np.array(V, dtype=np.float64, order="C")
+    F32 = np.array(F, dtype=np.int32, order="C")
+    nv, nf = len(V64), len(F32)
+    va = np.zeros(nv, np.uint8)
+    fa = np.zeros(nf, np.uint8)
+    stats = np.zeros(2 * max_rounds, np.int64)
+    r = lib.or_qem_simplify(_p(V64), nv, _p(F32), nf, int(target), _p(va), _p(fa), max_rounds, _p(stats))
+    if r < 0:
+        raise MemoryError("oracle QEM: allocation failed")
+    keep_v = np.flatnonzero(va)
+    keep_f = np.flatnonzero(fa)
+    new_id = np.full(nv, -1, np.int64)
+    new_id[keep_v] = np.arange(len(keep_v))
+    Fo = new_id[F32[keep_f]].astype(np.int32)
+    return dict(V=V64[keep_v], F=Fo, keep_v=keep_v, keep_f=keep_f, rounds=r,
+                alive=stats[0:2 * r:2].copy(), collapses=stats[1:2 * r:2].copy())

@@ -1200,3 +1200,325 @@ int or_exterior_fill(const float *V, const int32_t *F, int64_t nv, int64_t nf, c
     free(nrm); free(deg); free(list); free(fillp); free(queue);
     return 0;
 }
+
+/* ------------------------------------------------- 9. QEM simplification (Sec. 6.1)
+ * Quadric-error edge collapse with the paper's placement rule, in rounds of
+ * independent collapses.  Everything is double precision with the
+ * operations in the order written (the GPU evaluates the same expressions
+ * in the same order, so every decision below is taken identically).
+ *
+ * Quadrics.  Face f with corners P0, P1, P2: n = (P1 - P0) x (P2 - P0),
+ * unit normal m = n / |n| (no plane for |n| = 0), d = -(m . P0),
+ * p = (m, d), K_f = p p^T.  Q_v = sum of K_f over the faces incident to v,
+ * in increasing face id.  Merging an edge (a, b) gives Q = Q_a + Q_b, and
+ * after the collapse the kept vertex carries that Q.  E(v) = [v 1] Q [v 1]^T.
+ *
+ * Placement (paper): for an interior edge, x = -A^-1 b with A the upper-left
+ * 3x3 of Q and b its upper-right column; t = <x - v0, v1 - v0> / |v1 - v0|^2
+ * clamped to [0, 1]; v = v0 + t (v1 - v0).  Readings: A is singular when
+ * |det A| <= 1e-12 * max_i |A_ii|^3, and then t = 1/2 (the midpoint); the
+ * inverse is the adjugate over the determinant.  Boundary edges (one
+ * incident face) go to the endpoint with the lower E (ties to v0); an
+ * interior edge with one boundary endpoint goes to that endpoint; an
+ * interior edge with two boundary endpoints is not collapsed.  The cost is
+ * E(v), negative rounding clamped to 0.
+ *
+ * Validity (readings): the edge has at most two faces; both endpoints have
+ * at most 64 neighbours; the link condition
+ * |N(a) ∩ N(b)| = number of faces on the edge; the union of the two
+ * neighbourhoods has more than 4 vertices (no tetrahedron collapses); and
+ * no surviving face around a or b turns over: n_old . n_new > 0.
+ *
+ * Rounds (reading of "parallel edge collapse"): the unique edges (a < b) are
+ * ranked in (a, b) order; key = (bits of the cost rounded to float32) << 32
+ * | rank.  m1(v) = min key of the valid edges at v, m2(v) = min of m1 over v
+ * and its neighbours; edge (a, b) collapses when key = m2(a) = m2(b).  Two
+ * such edges never touch adjacent vertices, so their collapses are
+ * independent.  A round that would go below the target keeps only its
+ * smallest keys, just enough to reach it.  Collapsing (a, b) keeps a at v,
+ * removes b, drops the faces holding both and renames b to a in the others.
+ * It stops at the target face count or when no edge collapses. */
+typedef struct { double q[10]; } qem_quad;   /* q00 q01 q02 q03 q11 q12 q13 q22 q23 q33 */
+
+static void face_quadric(d3 P0, d3 P1, d3 P2, qem_quad *K, int *ok) {
+    d3 n = cross(sub(P1, P0), sub(P2, P0));
+    double len = sqrt(dot(n, n));
+    memset(K, 0, sizeof(*K));
+    *ok = len > 0.0;
+    if (!*ok) return;
+    d3 m = mk(n.x / len, n.y / len, n.z / len);
+    double p[4] = {m.x, m.y, m.z, -dot(m, P0)};
+    int k = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = i; j < 4; ++j) K->q[k++] = p[i] * p[j];
+}
+
+static double quad_eval(const qem_quad *Q, d3 v) {
+    const double *q = Q->q;
+    double e = q[0] * v.x * v.x;
+    e = e + 2.0 * q[1] * v.x * v.y;
+    e = e + 2.0 * q[2] * v.x * v.z;
+    e = e + 2.0 * q[3] * v.x;
+    e = e + q[4] * v.y * v.y;
+    e = e + 2.0 * q[5] * v.y * v.z;
+    e = e + 2.0 * q[6] * v.y;
+    e = e + q[7] * v.z * v.z;
+    e = e + 2.0 * q[8] * v.z;
+    e = e + q[9];
+    return e;
+}
+
+/* placement of the interior edge v0 -> v1 under Q; returns t */
+static double qem_place(const qem_quad *Q, d3 v0, d3 v1, int *singular) {
+    const double *q = Q->q;
+    double a00 = q[0], a01 = q[1], a02 = q[2], a11 = q[4], a12 = q[5], a22 = q[7];
+    double b0 = q[3], b1 = q[6], b2 = q[8];
+    double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+    double c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+    double det = a00 * c00 + a01 * c01 + a02 * c02;
+    double s = fmax(fabs(a00), fmax(fabs(a11), fabs(a22)));
+    *singular = !(fabs(det) > 1e-12 * s * s * s);
+    if (*singular) return 0.5;
+    d3 x = mk(-(c00 * b0 + c01 * b1 + c02 * b2) / det, -(c01 * b0 + c11 * b1 + c12 * b2) / det,
+              -(c02 * b0 + c12 * b1 + c22 * b2) / det);
+    d3 e = sub(v1, v0);
+    double ee = dot(e, e);
+    if (!(ee > 0.0)) return 0.0;
+    double t = dot(sub(x, v0), e) / ee;
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return t;
+}
+
+static uint64_t qem_key(double cost, uint32_t rank) {
+    float c = (float)(cost > 0.0 ? cost : 0.0);
+    uint32_t bits;
+    memcpy(&bits, &c, 4);
+    return ((uint64_t)bits << 32) | rank;
+}
+
+typedef struct { int32_t a, b; int nfaces; } qedge_t;
+
+#define QEM_MAX_NBR 64
+
+static int qedge_cmp(const void *x, const void *y) {
+    const qedge_t *p = (const qedge_t *)x, *q = (const qedge_t *)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    return 0;
+}
+
+static int u64_cmp(const void *x, const void *y) {
+    uint64_t p = *(const uint64_t *)x, q = *(const uint64_t *)y;
+    return p < q ? -1 : (p > q ? 1 : 0);
+}
+
+static int face_has(const int32_t *F, int64_t f, int32_t v) { return F[3 * f] == v || F[3 * f + 1] == v || F[3 * f + 2] == v; }
+
+/* V [nv*3] double, F [nf*3] int32 are updated in place; alive flags out;
+ * returns the number of rounds, -1 on allocation failure.  stats (optional,
+ * [max_rounds*2]): alive faces and collapses per round. */
+int or_qem_simplify(double *V, int64_t nv, int32_t *F, int64_t nf, int64_t target, uint8_t *valive, uint8_t *falive,
+                    int max_rounds, int64_t *stats) {
+    qem_quad *Q = (qem_quad *)calloc((size_t)nv, sizeof(qem_quad));
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nv + 1));
+    int32_t *vf = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)nf);
+    int64_t *fillc = (int64_t *)malloc(sizeof(int64_t) * (size_t)nv);
+    qedge_t *E = (qedge_t *)malloc(sizeof(qedge_t) * 3 * (size_t)nf);
+    uint64_t *key = (uint64_t *)malloc(sizeof(uint64_t) * 3 * (size_t)nf);
+    double *tpos = (double *)malloc(sizeof(double) * 3 * 3 * (size_t)nf);
+    uint64_t *m1 = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nv);
+    uint64_t *m2 = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)nv);
+    uint8_t *bnd = (uint8_t *)malloc((size_t)nv);
+    int32_t *remap = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv);
+    int32_t *nbr_a = (int32_t *)malloc(sizeof(int32_t) * (QEM_MAX_NBR + 1)),
+            *nbr_b = (int32_t *)malloc(sizeof(int32_t) * (QEM_MAX_NBR + 1));
+    uint64_t *selk = (uint64_t *)malloc(sizeof(uint64_t) * 3 * (size_t)nf);
+    if (!Q || !off || !vf || !fillc || !E || !key || !tpos || !m1 || !m2 || !bnd || !remap || !nbr_a || !nbr_b || !selk) {
+        free(Q); free(off); free(vf); free(fillc); free(E); free(key); free(tpos); free(m1); free(m2); free(bnd);
+        free(remap); free(nbr_a); free(nbr_b); free(selk);
+        return -1;
+    }
+    for (int64_t v = 0; v < nv; ++v) valive[v] = 0;
+    for (int64_t f = 0; f < nf; ++f) {
+        falive[f] = 1;
+        for (int k = 0; k < 3; ++k) valive[F[3 * f + k]] = 1;
+    }
+    /* initial quadrics: faces in increasing id at every vertex */
+    for (int64_t f = 0; f < nf; ++f) {
+        qem_quad K;
+        int ok;
+        face_quadric(ldd(V, F[3 * f]), ldd(V, F[3 * f + 1]), ldd(V, F[3 * f + 2]), &K, &ok);
+        if (!ok) continue;
+        for (int k = 0; k < 3; ++k) {
+            qem_quad *q = &Q[F[3 * f + k]];
+            for (int i = 0; i < 10; ++i) q->q[i] = q->q[i] + K.q[i];
+        }
+    }
+    int64_t alive = nf;
+    int round = 0;
+    while (alive > target && round < max_rounds) {
+        /* vertex -> alive faces, increasing face id */
+        for (int64_t v = 0; v <= nv; ++v) off[v] = 0;
+        for (int64_t f = 0; f < nf; ++f)
+            if (falive[f]) for (int k = 0; k < 3; ++k) ++off[F[3 * f + k] + 1];
+        for (int64_t v = 0; v < nv; ++v) { off[v + 1] += off[v]; fillc[v] = 0; }
+        for (int64_t f = 0; f < nf; ++f)
+            if (falive[f]) for (int k = 0; k < 3; ++k) { int32_t v = F[3 * f + k]; vf[off[v] + fillc[v]++] = (int32_t)f; }
+        /* unique edges in (a, b) order with their face counts */
+        int64_t ne = 0;
+        for (int64_t f = 0; f < nf; ++f) {
+            if (!falive[f]) continue;
+            for (int k = 0; k < 3; ++k) {
+                int32_t a = F[3 * f + k], b = F[3 * f + (k + 1) % 3];
+                qedge_t e = {a < b ? a : b, a < b ? b : a, 1};
+                E[ne++] = e;
+            }
+        }
+        qsort(E, (size_t)ne, sizeof(qedge_t), qedge_cmp);
+        int64_t nu = 0;
+        for (int64_t i = 0; i < ne; ++i) {
+            if (nu > 0 && E[nu - 1].a == E[i].a && E[nu - 1].b == E[i].b) { E[nu - 1].nfaces++; continue; }
+            E[nu++] = E[i];
+        }
+        for (int64_t v = 0; v < nv; ++v) bnd[v] = 0;
+        for (int64_t i = 0; i < nu; ++i) if (E[i].nfaces == 1) { bnd[E[i].a] = 1; bnd[E[i].b] = 1; }
+        /* cost, placement and validity of every edge */
+        for (int64_t i = 0; i < nu; ++i) {
+            int32_t a = E[i].a, b = E[i].b;
+            key[i] = UINT64_MAX;
+            if (E[i].nfaces > 2) continue;
+            qem_quad Qe;
+            for (int k = 0; k < 10; ++k) Qe.q[k] = Q[a].q[k] + Q[b].q[k];
+            d3 va = ldd(V, a), vb = ldd(V, b), v;
+            if (E[i].nfaces == 1) {
+                v = quad_eval(&Qe, vb) < quad_eval(&Qe, va) ? vb : va;
+            } else if (bnd[a] && bnd[b]) {
+                continue;
+            } else if (bnd[a]) {
+                v = va;
+            } else if (bnd[b]) {
+                v = vb;
+            } else {
+                int sing;
+                double t = qem_place(&Qe, va, vb, &sing);
+                v = add(va, scl(sub(vb, va), t));
+            }
+            /* neighbourhoods */
+            int na = 0, nb = 0;
+            for (int64_t j = off[a]; j < off[a + 1]; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    int32_t u = F[3 * vf[j] + k];
+                    if (u == a) continue;
+                    int seen = 0;
+                    for (int m = 0; m < na; ++m) if (nbr_a[m] == u) seen = 1;
+                    if (!seen && na <= QEM_MAX_NBR) nbr_a[na++] = u;
+                }
+            for (int64_t j = off[b]; j < off[b + 1]; ++j)
+                for (int k = 0; k < 3; ++k) {
+                    int32_t u = F[3 * vf[j] + k];
+                    if (u == b) continue;
+                    int seen = 0;
+                    for (int m = 0; m < nb; ++m) if (nbr_b[m] == u) seen = 1;
+                    if (!seen && nb <= QEM_MAX_NBR) nbr_b[nb++] = u;
+                }
+            if (na > QEM_MAX_NBR || nb > QEM_MAX_NBR) continue;
+            int common = 0;
+            for (int m = 0; m < na; ++m)
+                for (int n = 0; n < nb; ++n) if (nbr_a[m] == nbr_b[n]) ++common;
+            if (common != E[i].nfaces) continue;
+            if (na + nb - common <= 4) continue;   /* |N(a) ∪ N(b)| counting a and b: na + nb - common */
+            /* no surviving face turns over */
+            int flip = 0;
+            for (int side = 0; side < 2 && !flip; ++side) {
+                int32_t w = side ? b : a, o = side ? a : b;
+                for (int64_t j = off[w]; j < off[w + 1] && !flip; ++j) {
+                    int64_t g = vf[j];
+                    if (face_has(F, g, o)) continue;
+                    d3 P[3], R[3];
+                    for (int k = 0; k < 3; ++k) {
+                        P[k] = ldd(V, F[3 * g + k]);
+                        R[k] = F[3 * g + k] == w ? v : P[k];
+                    }
+                    d3 n0 = cross(sub(P[1], P[0]), sub(P[2], P[0]));
+                    d3 n1 = cross(sub(R[1], R[0]), sub(R[2], R[0]));
+                    if (!(dot(n0, n1) > 0.0)) flip = 1;
+                }
+            }
+            if (flip) continue;
+            key[i] = qem_key(quad_eval(&Qe, v), (uint32_t)i);
+            std3(tpos, i, v);
+        }
+        /* two-ring minima */
+        for (int64_t v = 0; v < nv; ++v) m1[v] = UINT64_MAX;
+        for (int64_t i = 0; i < nu; ++i) {
+            if (key[i] < m1[E[i].a]) m1[E[i].a] = key[i];
+            if (key[i] < m1[E[i].b]) m1[E[i].b] = key[i];
+        }
+        for (int64_t v = 0; v < nv; ++v) m2[v] = m1[v];
+        for (int64_t i = 0; i < nu; ++i) {
+            if (m1[E[i].b] < m2[E[i].a]) m2[E[i].a] = m1[E[i].b];
+            if (m1[E[i].a] < m2[E[i].b]) m2[E[i].b] = m1[E[i].a];
+        }
+        int64_t nsel = 0, removable = 0;
+        for (int64_t i = 0; i < nu; ++i)
+            if (key[i] != UINT64_MAX && key[i] == m2[E[i].a] && key[i] == m2[E[i].b]) {
+                selk[nsel++] = key[i];
+                removable += E[i].nfaces;
+            }
+        if (nsel == 0) break;
+        uint64_t limit = UINT64_MAX;
+        if (alive - removable < target) {
+            qsort(selk, (size_t)nsel, sizeof(uint64_t), u64_cmp);
+            int64_t gone = 0;
+            for (int64_t s = 0; s < nsel; ++s) {
+                gone += E[(uint32_t)selk[s]].nfaces;
+                if (alive - gone <= target) { limit = selk[s]; break; }
+            }
+        }
+        /* collapse */
+        for (int64_t v = 0; v < nv; ++v) remap[v] = (int32_t)v;
+        int64_t ncol = 0;
+        for (int64_t i = 0; i < nu; ++i) {
+            if (key[i] == UINT64_MAX || key[i] != m2[E[i].a] || key[i] != m2[E[i].b] || key[i] > limit) continue;
+            int32_t a = E[i].a, b = E[i].b;
+            std3(V, a, ldd(tpos, i));
+            for (int k = 0; k < 10; ++k) Q[a].q[k] = Q[a].q[k] + Q[b].q[k];
+            valive[b] = 0;
+            remap[b] = a;
+            ++ncol;
+        }
+        for (int64_t f = 0; f < nf; ++f) {
+            if (!falive[f]) continue;
+            int32_t r[3];
+            for (int k = 0; k < 3; ++k) r[k] = remap[F[3 * f + k]];
+            if (r[0] == r[1] || r[1] == r[2] || r[0] == r[2]) { falive[f] = 0; --alive; continue; }
+            for (int k = 0; k < 3; ++k) F[3 * f + k] = r[k];
+        }
+        if (stats) { stats[2 * round] = alive; stats[2 * round + 1] = ncol; }
+        ++round;
+    }
+    free(Q); free(off); free(vf); free(fillc); free(E); free(key); free(tpos); free(m1); free(m2); free(bnd);
+    free(remap); free(nbr_a); free(nbr_b); free(selk);
+    return round;
+}
+
+/* pieces exposed for pin tests */
+void or_qem_face_quadric(const double *P, double *q) {
+    qem_quad K;
+    int ok;
+    face_quadric(ldd(P, 0), ldd(P, 1), ldd(P, 2), &K, &ok);
+    memcpy(q, K.q, sizeof(K.q));
+}
+
+double or_qem_eval(const double *q, const double *v) {
+    qem_quad Q;
+    memcpy(Q.q, q, sizeof(Q.q));
+    return quad_eval(&Q, mk(v[0], v[1], v[2]));
+}
+
+double or_qem_place(const double *q, const double *v0, const double *v1, int *singular) {
+    qem_quad Q;
+    memcpy(Q.q, q, sizeof(Q.q));
+    return qem_place(&Q, mk(v0[0], v0[1], v0[2]), mk(v1[0], v1[1], v1[2]), singular);
+}
