@@ -343,6 +343,39 @@ AG_API ag_status ag_exterior_fill(const float *d_verts, int64_t n_verts, const i
                                   int64_t n_faces, const uint8_t *d_visible, ag_stream_t stream,
                                   uint8_t *d_exterior);
 
+/*
+ * ag_qem_simplify - quadric-error edge-collapse simplification (Sec. 6.1 of
+ *   the paper) with its contraction point: the minimiser of the merged
+ *   quadric (A x = -b) projected onto the edge and clamped to it, the
+ *   midpoint when |det A| <= 1e-12 max_i |A_ii|^3; boundary edges go to the
+ *   lower-error endpoint, interior edges with one boundary endpoint to that
+ *   endpoint, interior edges with two are kept.  Quadrics are unweighted
+ *   sums of the incident faces' plane quadrics.
+ *   Collapses run in rounds: an edge (a < b) collapses when its key (its
+ *   cost rounded to float32, then its rank in (a, b) order) is the smallest
+ *   within two edges of both endpoints and the collapse is valid (at most two
+ *   faces on the edge, at most 64 neighbours per endpoint, the link
+ *   condition, no tetrahedron, no surviving face turning over); the round
+ *   that would pass the target keeps only its cheapest collapses.  All
+ *   quadric arithmetic is FP64, rounded to nearest in a fixed order.
+ *   d_verts [n_verts*3] f32 and d_faces [n_faces*3] i32 (device) are read
+ *   only; faces with a repeated index are dropped.
+ *   target: stop at or below this many faces (or when nothing collapses).
+ *   max_rounds: 0 = no limit.
+ *   d_verts_out [n_verts*3] f64, d_faces_out [n_faces*3] i32 (device): the
+ *   surviving vertices in increasing original id (FP64 positions) and the
+ *   surviving faces, renumbered, in increasing original id; only the first
+ *   h_result[0] vertices and h_result[1] faces are written.
+ *   d_keep_verts (optional) [n_verts] i32: original id of each output vertex.
+ *   h_result [3] (host): output vertices, output faces, rounds.
+ *   Synchronises `stream` once per round.  Faces with an out-of-range index
+ *   are dropped and set AG_ERR_INVALID_ARG in the status word.
+ */
+AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
+                                 int64_t n_faces, int64_t target, int32_t max_rounds, ag_stream_t stream,
+                                 double *d_verts_out, int32_t *d_faces_out, int32_t *d_keep_verts,
+                                 int64_t *h_result);
+
 AG_API ag_status ag_sync_status(ag_stream_t stream);
 
 /* Message for the last failing call on this thread ("" if none). */

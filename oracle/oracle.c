@@ -1339,13 +1339,18 @@ int or_qem_simplify(double *V, int64_t nv, int32_t *F, int64_t nf, int64_t targe
         free(remap); free(nbr_a); free(nbr_b); free(selk);
         return -1;
     }
+    /* faces with a repeated vertex index are dropped; vertices of no face are not alive */
+    int64_t alive = 0;
     for (int64_t v = 0; v < nv; ++v) valive[v] = 0;
     for (int64_t f = 0; f < nf; ++f) {
-        falive[f] = 1;
+        falive[f] = !(F[3 * f] == F[3 * f + 1] || F[3 * f + 1] == F[3 * f + 2] || F[3 * f] == F[3 * f + 2]);
+        if (!falive[f]) continue;
+        ++alive;
         for (int k = 0; k < 3; ++k) valive[F[3 * f + k]] = 1;
     }
     /* initial quadrics: faces in increasing id at every vertex */
     for (int64_t f = 0; f < nf; ++f) {
+        if (!falive[f]) continue;
         qem_quad K;
         int ok;
         face_quadric(ldd(V, F[3 * f]), ldd(V, F[3 * f + 1]), ldd(V, F[3 * f + 2]), &K, &ok);
@@ -1355,7 +1360,6 @@ int or_qem_simplify(double *V, int64_t nv, int32_t *F, int64_t nf, int64_t targe
             for (int i = 0; i < 10; ++i) q->q[i] = q->q[i] + K.q[i];
         }
     }
-    int64_t alive = nf;
     int round = 0;
     while (alive > target && round < max_rounds) {
         /* vertex -> alive faces, increasing face id */

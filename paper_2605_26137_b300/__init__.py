@@ -1,5 +1,6 @@
 """B300-native tangent-space normal baker (AssetGen, Sec. 6.4 "Normal Map Baking"),
-with the hidden-face removal pass of Sec. 6.2 on the same BVH.
+with the hidden-face removal pass of Sec. 6.2 on the same BVH and the QEM
+simplification of Sec. 6.1.
 
 The compute path is the CUDA library ``libagbake.so`` behind the C ABI of
 ``include/ag.h``; this package only marshals torch tensors into it.
@@ -9,7 +10,7 @@ import importlib
 from ._lib import EXPORTS, AgError, load as load_library  # noqa: F401
 
 _TORCH_API = ("Bvh", "BakeOutputs", "Asset", "BatchPlan", "BakeLoss", "bake", "bake_batch", "bake_backward",
-              "bake_loss", "alloc_outputs", "sync_status", "visibility", "exterior_fill", "hidden_faces")
+              "bake_loss", "alloc_outputs", "sync_status", "visibility", "exterior_fill", "hidden_faces", "qem_simplify")
 
 
 def __getattr__(name):

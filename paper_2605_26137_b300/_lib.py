@@ -38,7 +38,7 @@ AG_QUERY_CLOSEST = 1
 EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
            "ag_batch_plan_create", "ag_batch_plan_launch", "ag_batch_plan_free", "ag_bake_backward",
            "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc",
-           "ag_autotune", "ag_visibility", "ag_exterior_fill")
+           "ag_autotune", "ag_visibility", "ag_exterior_fill", "ag_qem_simplify")
 
 
 class AgOpts(ctypes.Structure):
@@ -121,6 +121,9 @@ def load():
         lib.ag_visibility.restype = S
         lib.ag_exterior_fill.argtypes = [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
         lib.ag_exterior_fill.restype = S
+        lib.ag_qem_simplify.argtypes = [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int32, c_void_p, c_void_p,
+                                        c_void_p, c_void_p, c_void_p]
+        lib.ag_qem_simplify.restype = S
         lib.ag_sync_status.argtypes = [c_void_p]
         lib.ag_sync_status.restype = S
         lib.ag_last_error.argtypes = []

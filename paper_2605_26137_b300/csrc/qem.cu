@@ -1,0 +1,591 @@
+// QEM mesh simplification (Sec. 6.1): parallel edge collapse ranked by
+// quadric error, with the paper's contraction point: the unconstrained
+// minimiser of the merged quadric projected onto the edge segment and
+// clamped (the midpoint when the quadric is singular); boundary edges go to
+// their lower-error endpoint, interior edges with one boundary endpoint to
+// that endpoint.
+//
+// All quadric arithmetic is FP64 with every operation rounded to nearest in
+// a fixed order (no fused multiply-adds), so cost ranking, validity and
+// positions are decided exactly as the same expressions evaluate on any
+// IEEE machine.
+//
+// A round (all kernels, stream-ordered; the host reads three counters at the
+// end of each round to decide whether to go on):
+//   1. vertex -> alive face adjacency (degree, scan, fill);
+//   2. the unique edges a < b, ranked in (a, b) order: every vertex lists its
+//      distinct higher neighbours, an exclusive scan places them, each
+//      segment is sorted;
+//   3. faces per edge; boundary vertices (on an edge with one face);
+//   4. per edge: placement, cost E(v), validity (at most two faces, at most
+//      64 neighbours per endpoint, link condition, no tetrahedron, no
+//      surviving face turning over), key = float32 cost bits << 32 | rank;
+//   5. m1(v) = min key at v, m2(v) = min of m1 over v and its neighbours; an
+//      edge collapses when its key equals m2 at both ends (such edges never
+//      touch adjacent vertices, so their collapses are independent);
+//   6. if collapsing all of them would pass the target, only the smallest
+//      keys that reach it (a one-block binary search over the selected keys);
+//   7. collapse: keep a at v with Q_a + Q_b, rename b to a, drop the faces
+//      that held both.
+#include "ag_internal.cuh"
+
+#include <cstring>
+
+namespace ag {
+namespace {
+
+constexpr int QEM_MAX_NBR = 64;
+constexpr unsigned long long KEY_NONE = ~0ull;
+
+struct D3 {
+    double x, y, z;
+};
+__device__ __forceinline__ D3 d3v(double x, double y, double z) { D3 r; r.x = x; r.y = y; r.z = z; return r; }
+__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return d3v(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y), __dsub_rn(a.z, b.z)); }
+__device__ __forceinline__ D3 dadd(D3 a, D3 b) { return d3v(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y), __dadd_rn(a.z, b.z)); }
+__device__ __forceinline__ D3 dscl(D3 a, double s) { return d3v(__dmul_rn(a.x, s), __dmul_rn(a.y, s), __dmul_rn(a.z, s)); }
+__device__ __forceinline__ double ddot(D3 a, D3 b) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)), __dmul_rn(a.z, b.z));
+}
+__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
+    return d3v(__dsub_rn(__dmul_rn(a.y, b.z), __dmul_rn(a.z, b.y)), __dsub_rn(__dmul_rn(a.z, b.x), __dmul_rn(a.x, b.z)),
+               __dsub_rn(__dmul_rn(a.x, b.y), __dmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ D3 ldv(const double *V, int64_t i) { return d3v(V[3 * i], V[3 * i + 1], V[3 * i + 2]); }
+
+// plane quadric of a face (10 unique entries, q00 q01 q02 q03 q11 q12 q13 q22 q23 q33); false without a plane
+__device__ __forceinline__ bool face_quadric(D3 P0, D3 P1, D3 P2, double K[10]) {
+    const D3 n = dcross(dsub(P1, P0), dsub(P2, P0));
+    const double len = __dsqrt_rn(ddot(n, n));
+    if (!(len > 0.0)) return false;
+    const D3 m = d3v(__ddiv_rn(n.x, len), __ddiv_rn(n.y, len), __ddiv_rn(n.z, len));
+    const double p[4] = {m.x, m.y, m.z, -ddot(m, P0)};
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j) K[k++] = __dmul_rn(p[i], p[j]);
+    return true;
+}
+
+__device__ __forceinline__ double quad_eval(const double q[10], D3 v) {
+    double e = __dmul_rn(__dmul_rn(q[0], v.x), v.x);
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(__dmul_rn(2.0, q[1]), v.x), v.y));
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(__dmul_rn(2.0, q[2]), v.x), v.z));
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(2.0, q[3]), v.x));
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(q[4], v.y), v.y));
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(__dmul_rn(2.0, q[5]), v.y), v.z));
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(2.0, q[6]), v.y));
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(q[7], v.z), v.z));
+    e = __dadd_rn(e, __dmul_rn(__dmul_rn(2.0, q[8]), v.z));
+    e = __dadd_rn(e, q[9]);
+    return e;
+}
+
+// the paper's placement on the interior edge v0 -> v1: returns t
+__device__ __forceinline__ double qem_place(const double q[10], D3 v0, D3 v1) {
+    const double a00 = q[0], a01 = q[1], a02 = q[2], a11 = q[4], a12 = q[5], a22 = q[7];
+    const double b0 = q[3], b1 = q[6], b2 = q[8];
+    const double c00 = __dsub_rn(__dmul_rn(a11, a22), __dmul_rn(a12, a12));
+    const double c01 = __dsub_rn(__dmul_rn(a02, a12), __dmul_rn(a01, a22));
+    const double c02 = __dsub_rn(__dmul_rn(a01, a12), __dmul_rn(a02, a11));
+    const double c11 = __dsub_rn(__dmul_rn(a00, a22), __dmul_rn(a02, a02));
+    const double c12 = __dsub_rn(__dmul_rn(a01, a02), __dmul_rn(a00, a12));
+    const double c22 = __dsub_rn(__dmul_rn(a00, a11), __dmul_rn(a01, a01));
+    const double det = __dadd_rn(__dadd_rn(__dmul_rn(a00, c00), __dmul_rn(a01, c01)), __dmul_rn(a02, c02));
+    const double s = fmax(fabs(a00), fmax(fabs(a11), fabs(a22)));
+    if (!(fabs(det) > __dmul_rn(__dmul_rn(__dmul_rn(1e-12, s), s), s))) return 0.5;
+    const D3 x = d3v(__ddiv_rn(-__dadd_rn(__dadd_rn(__dmul_rn(c00, b0), __dmul_rn(c01, b1)), __dmul_rn(c02, b2)), det),
+                     __ddiv_rn(-__dadd_rn(__dadd_rn(__dmul_rn(c01, b0), __dmul_rn(c11, b1)), __dmul_rn(c12, b2)), det),
+                     __ddiv_rn(-__dadd_rn(__dadd_rn(__dmul_rn(c02, b0), __dmul_rn(c12, b1)), __dmul_rn(c22, b2)), det));
+    const D3 e = dsub(v1, v0);
+    const double ee = ddot(e, e);
+    if (!(ee > 0.0)) return 0.0;
+    double t = __ddiv_rn(ddot(dsub(x, v0), e), ee);
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long qem_key(double cost, uint32_t rank) {
+    const float c = __double2float_rn(cost > 0.0 ? cost : 0.0);
+    return ((unsigned long long)__float_as_uint(c) << 32) | rank;
+}
+
+__device__ __forceinline__ bool has(const int32_t *F, int64_t f, int32_t v) {
+    return F[3 * f] == v || F[3 * f + 1] == v || F[3 * f + 2] == v;
+}
+
+inline unsigned blocks(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+struct Counters {
+    unsigned long long alive;       // alive faces
+    unsigned long long removable;   // faces the selected collapses would remove
+    int nsel;              // selected collapses
+    int pad;
+};
+
+__global__ void k_init_faces(const int32_t *__restrict__ Fin, int64_t nf, int64_t nv, int32_t *__restrict__ F,
+                             uint8_t *__restrict__ falive, uint8_t *__restrict__ valive, Counters *cnt,
+                             unsigned *status) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int32_t i0 = Fin[3 * f], i1 = Fin[3 * f + 1], i2 = Fin[3 * f + 2];
+    F[3 * f] = i0; F[3 * f + 1] = i1; F[3 * f + 2] = i2;
+    if (i0 < 0 || i0 >= nv || i1 < 0 || i1 >= nv || i2 < 0 || i2 >= nv) {
+        falive[f] = 0;
+        F[3 * f] = F[3 * f + 1] = F[3 * f + 2] = 0;
+        atomicOr(status, AGS_BAD_FACE);
+        return;
+    }
+    const bool ok = !(i0 == i1 || i1 == i2 || i0 == i2);
+    falive[f] = ok;
+    if (!ok) return;
+    atomicAdd(&cnt->alive, 1ull);
+    valive[i0] = 1; valive[i1] = 1; valive[i2] = 1;
+}
+
+__global__ void k_init_verts(const float *__restrict__ Vin, int64_t nv, double *__restrict__ V,
+                             int32_t *__restrict__ remap) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    V[3 * v] = Vin[3 * v]; V[3 * v + 1] = Vin[3 * v + 1]; V[3 * v + 2] = Vin[3 * v + 2];
+    remap[v] = (int32_t)v;
+}
+
+// vertex -> alive faces
+__global__ void k_deg(const int32_t *__restrict__ F, const uint8_t *__restrict__ falive, int64_t nf,
+                      unsigned *__restrict__ deg) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf || !falive[f]) return;
+    for (int k = 0; k < 3; ++k) atomicAdd(&deg[F[3 * f + k]], 1u);
+}
+
+__global__ void k_fill(const int32_t *__restrict__ F, const uint8_t *__restrict__ falive, int64_t nf,
+                       const unsigned *__restrict__ off, unsigned *__restrict__ fill, int32_t *__restrict__ list) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf || !falive[f]) return;
+    for (int k = 0; k < 3; ++k) {
+        const int32_t v = F[3 * f + k];
+        list[off[v] + atomicAdd(&fill[v], 1u)] = (int32_t)f;
+    }
+}
+
+// initial quadrics: each vertex sums its faces' plane quadrics in increasing face id
+__global__ void k_quadric_init(const double *__restrict__ V, const int32_t *__restrict__ F, int64_t nv,
+                               const unsigned *__restrict__ off, int32_t *__restrict__ list, double *__restrict__ Q) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const unsigned b = off[v], e = off[v + 1];
+    for (unsigned i = b + 1; i < e; ++i) {
+        const int32_t x = list[i];
+        unsigned j = i;
+        while (j > b && list[j - 1] > x) { list[j] = list[j - 1]; --j; }
+        list[j] = x;
+    }
+    double q[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) q[k] = 0.0;
+    for (unsigned i = b; i < e; ++i) {
+        const int64_t f = list[i];
+        double K[10];
+        if (!face_quadric(ldv(V, F[3 * f]), ldv(V, F[3 * f + 1]), ldv(V, F[3 * f + 2]), K)) continue;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) q[k] = __dadd_rn(q[k], K[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) Q[10 * v + k] = q[k];
+}
+
+// whether vertex u occurs in a face listed before position i of v's list
+__device__ __forceinline__ bool seen_before(const int32_t *F, const int32_t *list, unsigned b, unsigned i, int32_t u) {
+    for (unsigned j = b; j < i; ++j)
+        if (has(F, list[j], u)) return true;
+    return false;
+}
+
+// number of distinct higher neighbours of every vertex
+__global__ void k_upcount(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
+                          const int32_t *__restrict__ list, unsigned *__restrict__ up) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nv) return;
+    const unsigned b = off[a], e = off[a + 1];
+    unsigned n = 0;
+    for (unsigned i = b; i < e; ++i) {
+        const int64_t f = list[i];
+        for (int k = 0; k < 3; ++k) {
+            const int32_t u = F[3 * f + k];
+            if (u <= a) continue;
+            bool dup = false;
+            for (int m = 0; m < k; ++m) dup = dup || F[3 * f + m] == u;
+            if (!dup && !seen_before(F, list, b, i, u)) ++n;
+        }
+    }
+    up[a] = n;
+}
+
+__global__ void k_edges(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
+                        const int32_t *__restrict__ list, const unsigned *__restrict__ eoff,
+                        int32_t *__restrict__ ea, int32_t *__restrict__ eb) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nv) return;
+    const unsigned b = off[a], e = off[a + 1], o = eoff[a], n_up = eoff[a + 1] - o;
+    unsigned n = 0;
+    for (unsigned i = b; i < e; ++i) {
+        const int64_t f = list[i];
+        for (int k = 0; k < 3; ++k) {
+            const int32_t u = F[3 * f + k];
+            if (u <= a) continue;
+            bool dup = false;
+            for (int m = 0; m < k; ++m) dup = dup || F[3 * f + m] == u;
+            if (!dup && !seen_before(F, list, b, i, u)) { ea[o + n] = (int32_t)a; eb[o + n] = u; ++n; }
+        }
+    }
+    for (unsigned i = 1; i < n_up; ++i) {
+        const int32_t x = eb[o + i];
+        unsigned j = i;
+        while (j > 0 && eb[o + j - 1] > x) { eb[o + j] = eb[o + j - 1]; --j; }
+        eb[o + j] = x;
+    }
+}
+
+__global__ void k_edge_faces(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
+                             const int32_t *__restrict__ list, const int32_t *__restrict__ ea,
+                             const int32_t *__restrict__ eb, int64_t ne, uint8_t *__restrict__ nfaces,
+                             uint8_t *__restrict__ bnd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int32_t a = ea[i], b = eb[i];
+    unsigned n = 0;
+    for (unsigned j = off[a]; j < off[a + 1]; ++j) n += has(F, list[j], b);
+    nfaces[i] = (uint8_t)(n > 255 ? 255 : n);
+    if (n == 1) { bnd[a] = 1; bnd[b] = 1; }
+}
+
+// distinct neighbours of v (not v), up to QEM_MAX_NBR + 1
+__device__ __forceinline__ int neighbours(const int32_t *F, const unsigned *off, const int32_t *list, int32_t v,
+                                          int32_t *out) {
+    int n = 0;
+    for (unsigned j = off[v]; j < off[v + 1]; ++j) {
+        const int64_t f = list[j];
+        for (int k = 0; k < 3; ++k) {
+            const int32_t u = F[3 * f + k];
+            if (u == v) continue;
+            bool seen = false;
+            for (int m = 0; m < n; ++m) seen = seen || out[m] == u;
+            if (!seen && n <= QEM_MAX_NBR) out[n++] = u;
+        }
+    }
+    return n;
+}
+
+__global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V, const int32_t *__restrict__ F,
+                                                    const double *__restrict__ Q, const unsigned *__restrict__ off,
+                                                    const int32_t *__restrict__ list, const int32_t *__restrict__ ea,
+                                                    const int32_t *__restrict__ eb, const uint8_t *__restrict__ nfaces,
+                                                    const uint8_t *__restrict__ bnd, int64_t ne,
+                                                    unsigned long long *__restrict__ key, double *__restrict__ tpos) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    key[i] = KEY_NONE;
+    const int32_t a = ea[i], b = eb[i];
+    const int nfc = nfaces[i];
+    if (nfc > 2) return;
+    double q[10];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) q[k] = __dadd_rn(Q[10 * (int64_t)a + k], Q[10 * (int64_t)b + k]);
+    const D3 va = ldv(V, a), vb = ldv(V, b);
+    D3 v;
+    if (nfc == 1) {
+        v = quad_eval(q, vb) < quad_eval(q, va) ? vb : va;
+    } else if (bnd[a] && bnd[b]) {
+        return;
+    } else if (bnd[a]) {
+        v = va;
+    } else if (bnd[b]) {
+        v = vb;
+    } else {
+        const double t = qem_place(q, va, vb);
+        v = dadd(va, dscl(dsub(vb, va), t));
+    }
+    int32_t na_[QEM_MAX_NBR + 1], nb_[QEM_MAX_NBR + 1];
+    const int na = neighbours(F, off, list, a, na_);
+    const int nb = neighbours(F, off, list, b, nb_);
+    if (na > QEM_MAX_NBR || nb > QEM_MAX_NBR) return;
+    int common = 0;
+    for (int m = 0; m < na; ++m)
+        for (int n = 0; n < nb; ++n) common += na_[m] == nb_[n];
+    if (common != nfc) return;
+    if (na + nb - common <= 4) return;
+    for (int side = 0; side < 2; ++side) {
+        const int32_t w = side ? b : a, o = side ? a : b;
+        for (unsigned j = off[w]; j < off[w + 1]; ++j) {
+            const int64_t g = list[j];
+            if (has(F, g, o)) continue;
+            D3 P[3], R[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                P[k] = ldv(V, F[3 * g + k]);
+                R[k] = F[3 * g + k] == w ? v : P[k];
+            }
+            const D3 n0 = dcross(dsub(P[1], P[0]), dsub(P[2], P[0]));
+            const D3 n1 = dcross(dsub(R[1], R[0]), dsub(R[2], R[0]));
+            if (!(ddot(n0, n1) > 0.0)) return;
+        }
+    }
+    key[i] = qem_key(quad_eval(q, v), (uint32_t)i);
+    tpos[3 * i] = v.x; tpos[3 * i + 1] = v.y; tpos[3 * i + 2] = v.z;
+}
+
+__global__ void k_m1(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
+                     const unsigned long long *__restrict__ key, int64_t ne, unsigned long long *__restrict__ m1) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne || key[i] == KEY_NONE) return;
+    atomicMin(&m1[ea[i]], key[i]);
+    atomicMin(&m1[eb[i]], key[i]);
+}
+
+__global__ void k_m2(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
+                     const unsigned long long *__restrict__ m1, int64_t ne, unsigned long long *__restrict__ m2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const int32_t a = ea[i], b = eb[i];
+    atomicMin(&m2[a], m1[b]);
+    atomicMin(&m2[b], m1[a]);
+}
+
+__global__ void k_select(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
+                         const unsigned long long *__restrict__ key, const uint8_t *__restrict__ nfaces,
+                         const unsigned long long *__restrict__ m2, int64_t ne, uint8_t *__restrict__ sel,
+                         unsigned long long *__restrict__ selk, uint8_t *__restrict__ selnf, Counters *cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    const unsigned long long k = key[i];
+    const bool s = k != KEY_NONE && k == m2[ea[i]] && k == m2[eb[i]];
+    sel[i] = s;
+    if (!s) return;
+    const int slot = atomicAdd(&cnt->nsel, 1);
+    selk[slot] = k;
+    selnf[slot] = nfaces[i];
+    atomicAdd(&cnt->removable, (unsigned long long)nfaces[i]);
+}
+
+// smallest selected key L with sum(nfaces of selected keys <= L) >= need
+__global__ void __launch_bounds__(1024) k_limit(const unsigned long long *__restrict__ selk,
+                                                 const uint8_t *__restrict__ selnf, const Counters *cnt,
+                                                 long long target, unsigned long long *limit) {
+    __shared__ long long part[32];
+    __shared__ unsigned long long s_lo, s_hi;
+    const int n = cnt->nsel;
+    const long long need = (long long)cnt->alive - target;
+    if (threadIdx.x == 0) { s_lo = 0ull; s_hi = KEY_NONE; }
+    __syncthreads();
+    for (int it = 0; it < 70; ++it) {
+        const unsigned long long lo = s_lo, hi = s_hi;
+        if (lo >= hi) break;
+        const unsigned long long mid = lo + (hi - lo) / 2;
+        long long sum = 0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x)
+            if (selk[j] <= mid) sum += selnf[j];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long t = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+            if (t >= need) s_hi = mid; else s_lo = mid + 1;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *limit = s_lo;
+}
+
+__global__ void k_apply(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
+                        const unsigned long long *__restrict__ key, const uint8_t *__restrict__ sel,
+                        const double *__restrict__ tpos, const unsigned long long *__restrict__ limit, int64_t ne,
+                        double *__restrict__ V, double *__restrict__ Q, uint8_t *__restrict__ valive,
+                        int32_t *__restrict__ remap) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne || !sel[i] || key[i] > *limit) return;
+    const int64_t a = ea[i], b = eb[i];
+    V[3 * a] = tpos[3 * i]; V[3 * a + 1] = tpos[3 * i + 1]; V[3 * a + 2] = tpos[3 * i + 2];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) Q[10 * a + k] = __dadd_rn(Q[10 * a + k], Q[10 * b + k]);
+    valive[b] = 0;
+    remap[b] = (int32_t)a;
+}
+
+__global__ void k_faces(int32_t *__restrict__ F, uint8_t *__restrict__ falive, int64_t nf,
+                        const int32_t *__restrict__ remap, Counters *cnt) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf || !falive[f]) return;
+    const int32_t r0 = remap[F[3 * f]], r1 = remap[F[3 * f + 1]], r2 = remap[F[3 * f + 2]];
+    if (r0 == r1 || r1 == r2 || r0 == r2) {
+        falive[f] = 0;
+        atomicAdd(&cnt->alive, ~0ull);   // -1
+        return;
+    }
+    F[3 * f] = r0; F[3 * f + 1] = r1; F[3 * f + 2] = r2;
+}
+
+__global__ void k_flag_u32(const uint8_t *__restrict__ flag, int64_t n, unsigned *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = flag[i] ? 1u : 0u;
+}
+
+__global__ void k_compact_v(const double *__restrict__ V, const uint8_t *__restrict__ valive,
+                            const unsigned *__restrict__ vid, int64_t nv, double *__restrict__ Vout,
+                            int32_t *__restrict__ keep_v) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv || !valive[v]) return;
+    const unsigned o = vid[v];
+    Vout[3 * (int64_t)o] = V[3 * v]; Vout[3 * (int64_t)o + 1] = V[3 * v + 1]; Vout[3 * (int64_t)o + 2] = V[3 * v + 2];
+    if (keep_v) keep_v[o] = (int32_t)v;
+}
+
+__global__ void k_compact_f(const int32_t *__restrict__ F, const uint8_t *__restrict__ falive,
+                            const unsigned *__restrict__ fid, const unsigned *__restrict__ vid, int64_t nf,
+                            int32_t *__restrict__ Fout) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf || !falive[f]) return;
+    const int64_t o = fid[f];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Fout[3 * o + k] = (int32_t)vid[F[3 * f + k]];
+}
+
+}  // namespace
+}  // namespace ag
+
+using namespace ag;
+
+extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
+                                            int64_t n_faces, int64_t target, int32_t max_rounds, ag_stream_t stream,
+                                            double *d_verts_out, int32_t *d_faces_out, int32_t *d_keep_verts,
+                                            int64_t *h_result) {
+    if (!d_verts || !d_faces || !d_verts_out || !d_faces_out || !h_result)
+        return set_error(AG_ERR_INVALID_ARG, "pointers must be non-NULL (d_keep_verts may be NULL)");
+    if (n_verts < 3 || n_verts >= (1ll << 31)) return set_error(AG_ERR_INVALID_ARG, "n_verts out of range");
+    if (n_faces < 1 || n_faces >= (1ll << 29)) return set_error(AG_ERR_INVALID_ARG, "n_faces out of range");
+    if (target < 0) return set_error(AG_ERR_INVALID_ARG, "target must be >= 0");
+    if (max_rounds < 0) return set_error(AG_ERR_INVALID_ARG, "max_rounds must be >= 0");
+    const int rounds_cap = max_rounds > 0 ? max_rounds : 100000;
+    int dev = 0;
+    AG_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *status = device_status_word(dev);
+    if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    const int64_t nv = n_verts, nf = n_faces, emax = 3 * nf;
+    Scratch sc(s, dev);
+    double *V, *Q, *tpos;
+    int32_t *F, *remap, *list, *ea, *eb;
+    uint8_t *falive, *valive, *bnd, *nfaces, *sel, *selnf;
+    unsigned *off, *fill, *eoff, *scan_tmp, *vid, *fid;
+    unsigned long long *key, *m1, *m2, *selk, *limit;
+    Counters *cnt;
+    AG_CUDA(sc.alloc((void **)&V, sizeof(double) * 3 * nv));
+    AG_CUDA(sc.alloc((void **)&Q, sizeof(double) * 10 * nv));
+    AG_CUDA(sc.alloc((void **)&tpos, sizeof(double) * 3 * emax));
+    AG_CUDA(sc.alloc((void **)&F, sizeof(int32_t) * 3 * nf));
+    AG_CUDA(sc.alloc((void **)&remap, sizeof(int32_t) * nv));
+    AG_CUDA(sc.alloc((void **)&list, sizeof(int32_t) * 3 * nf));
+    AG_CUDA(sc.alloc((void **)&ea, sizeof(int32_t) * emax));
+    AG_CUDA(sc.alloc((void **)&eb, sizeof(int32_t) * emax));
+    AG_CUDA(sc.alloc((void **)&falive, nf));
+    AG_CUDA(sc.alloc((void **)&valive, nv));
+    AG_CUDA(sc.alloc((void **)&bnd, nv));
+    AG_CUDA(sc.alloc((void **)&nfaces, emax));
+    AG_CUDA(sc.alloc((void **)&sel, emax));
+    AG_CUDA(sc.alloc((void **)&selnf, emax));
+    AG_CUDA(sc.alloc((void **)&off, sizeof(unsigned) * (nv + 1)));
+    AG_CUDA(sc.alloc((void **)&fill, sizeof(unsigned) * nv));
+    AG_CUDA(sc.alloc((void **)&eoff, sizeof(unsigned) * (nv + 1)));
+    AG_CUDA(sc.alloc((void **)&scan_tmp, scan_scratch_bytes(nv > nf ? nv : nf)));
+    AG_CUDA(sc.alloc((void **)&vid, sizeof(unsigned) * (nv + 1)));
+    AG_CUDA(sc.alloc((void **)&fid, sizeof(unsigned) * (nf + 1)));
+    AG_CUDA(sc.alloc((void **)&key, sizeof(unsigned long long) * emax));
+    AG_CUDA(sc.alloc((void **)&m1, sizeof(unsigned long long) * nv));
+    AG_CUDA(sc.alloc((void **)&m2, sizeof(unsigned long long) * nv));
+    AG_CUDA(sc.alloc((void **)&selk, sizeof(unsigned long long) * emax));
+    AG_CUDA(sc.alloc((void **)&limit, sizeof(unsigned long long)));
+    AG_CUDA(sc.alloc((void **)&cnt, sizeof(Counters)));
+    Counters *h_cnt = nullptr;
+    AG_CUDA(cudaMallocHost((void **)&h_cnt, sizeof(Counters)));
+    struct HostFree {
+        Counters *p;
+        ~HostFree() { if (p) cudaFreeHost(p); }
+    } hf{h_cnt};
+
+    const int B = 256;
+    AG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), s));
+    AG_CUDA(cudaMemsetAsync(valive, 0, nv, s));
+    k_init_faces<<<blocks(nf, B), B, 0, s>>>(d_faces, nf, nv, F, falive, valive, cnt, status);
+    k_init_verts<<<blocks(nv, B), B, 0, s>>>(d_verts, nv, V, remap);
+    AG_CUDA_LAUNCH("qem init");
+
+    auto build_csr = [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(off, 0, sizeof(unsigned) * (nv + 1), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(fill, 0, sizeof(unsigned) * nv, s)) != cudaSuccess) return e;
+        k_deg<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, off);
+        if ((e = launch_scan_exclusive(off, nv, off + nv, scan_tmp, s)) != cudaSuccess) return e;
+        k_fill<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, off, fill, list);
+        return cudaGetLastError();
+    };
+    AG_CUDA(build_csr());
+    k_quadric_init<<<blocks(nv, 128), 128, 0, s>>>(V, F, nv, off, list, Q);
+    AG_CUDA_LAUNCH("k_quadric_init");
+
+    int64_t rounds = 0;
+    for (;;) {
+        AG_CUDA(cudaMemcpyAsync(h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaStreamSynchronize(s));
+        if ((long long)h_cnt->alive <= target || rounds >= rounds_cap) break;
+        AG_CUDA(build_csr());
+        k_upcount<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff);
+        AG_CUDA(launch_scan_exclusive(eoff, nv, eoff + nv, scan_tmp, s));
+        unsigned ne32 = 0;
+        AG_CUDA(cudaMemcpyAsync(&ne32, eoff + nv, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaStreamSynchronize(s));
+        const int64_t ne = ne32;
+        if (ne == 0) break;
+        k_edges<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff, ea, eb);
+        AG_CUDA(cudaMemsetAsync(bnd, 0, nv, s));
+        k_edge_faces<<<blocks(ne, B), B, 0, s>>>(F, off, list, ea, eb, ne, nfaces, bnd);
+        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, F, Q, off, list, ea, eb, nfaces, bnd, ne, key, tpos);
+        AG_CUDA(cudaMemsetAsync(m1, 0xff, sizeof(unsigned long long) * nv, s));
+        k_m1<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, ne, m1);
+        AG_CUDA(cudaMemcpyAsync(m2, m1, sizeof(unsigned long long) * nv, cudaMemcpyDeviceToDevice, s));
+        k_m2<<<blocks(ne, B), B, 0, s>>>(ea, eb, m1, ne, m2);
+        AG_CUDA(cudaMemsetAsync(&cnt->removable, 0, sizeof(unsigned long long) + 2 * sizeof(int), s));
+        k_select<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, nfaces, m2, ne, sel, selk, selnf, cnt);
+        AG_CUDA_LAUNCH("qem round");
+        AG_CUDA(cudaMemcpyAsync(h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaStreamSynchronize(s));
+        if (h_cnt->nsel == 0) break;
+        if ((long long)h_cnt->alive - (long long)h_cnt->removable < target) {
+            k_limit<<<1, 1024, 0, s>>>(selk, selnf, cnt, (long long)target, limit);
+        } else {
+            AG_CUDA(cudaMemsetAsync(limit, 0xff, sizeof(unsigned long long), s));
+        }
+        k_apply<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, tpos, limit, ne, V, Q, valive, remap);
+        k_faces<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, remap, cnt);
+        AG_CUDA_LAUNCH("qem collapse");
+        ++rounds;
+    }
+    // compaction: surviving vertices and faces in increasing original id
+    k_flag_u32<<<blocks(nv, B), B, 0, s>>>(valive, nv, vid);
+    AG_CUDA(launch_scan_exclusive(vid, nv, vid + nv, scan_tmp, s));
+    k_flag_u32<<<blocks(nf, B), B, 0, s>>>(falive, nf, fid);
+    AG_CUDA(launch_scan_exclusive(fid, nf, fid + nf, scan_tmp, s));
+    k_compact_v<<<blocks(nv, B), B, 0, s>>>(V, valive, vid, nv, d_verts_out, d_keep_verts);
+    k_compact_f<<<blocks(nf, B), B, 0, s>>>(F, falive, fid, vid, nf, d_faces_out);
+    AG_CUDA_LAUNCH("qem compact");
+    unsigned nvo = 0, nfo = 0;
+    AG_CUDA(cudaMemcpyAsync(&nvo, vid + nv, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    AG_CUDA(cudaMemcpyAsync(&nfo, fid + nf, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    AG_CUDA(cudaStreamSynchronize(s));
+    h_result[0] = nvo;
+    h_result[1] = nfo;
+    h_result[2] = rounds;
+    return AG_OK;
+}

@@ -346,6 +346,24 @@ def hidden_faces(verts, faces, n_views: int = 512, res: int = 1024, *, stream=No
         bvh.free()
 
 
+# ----------------------------------------------------------------- QEM simplification (Sec. 6.1)
+
+def qem_simplify(verts, faces, target: int, *, max_rounds: int = 0, stream=None):
+    """Simplify to at most ``target`` faces.  Returns (verts f64 [n,3],
+    faces i32 [m,3], keep_verts i32 [n] original ids, rounds)."""
+    lib = _lib.load()
+    _need(verts, "verts", torch.float32, (3,))
+    _need(faces, "faces", torch.int32, (3,))
+    vo = torch.empty((verts.shape[0], 3), dtype=torch.float64, device=verts.device)
+    fo = torch.empty((faces.shape[0], 3), dtype=torch.int32, device=faces.device)
+    keep = torch.empty(verts.shape[0], dtype=torch.int32, device=verts.device)
+    res = (ctypes.c_int64 * 3)()
+    check(lib.ag_qem_simplify(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0], int(target),
+                              int(max_rounds), _stream(stream), vo.data_ptr(), fo.data_ptr(), keep.data_ptr(), res))
+    n, m = int(res[0]), int(res[1])
+    return vo[:n], fo[:m], keep[:n], int(res[2])
+
+
 def sync_status(stream=None) -> None:
     """Synchronise and raise AgError if a device-side limit was hit."""
     check(_lib.load().ag_sync_status(_stream(stream)))
