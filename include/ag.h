@@ -362,6 +362,9 @@ AG_API ag_status ag_exterior_fill(const float *d_verts, int64_t n_verts, const i
  *   only; faces with a repeated index are dropped.
  *   target: stop at or below this many faces (or when nothing collapses).
  *   max_rounds: 0 = no limit.
+ *   placement: AG_QEM_OPTIMAL (0, the paper's projected optimum) or
+ *   AG_QEM_MIDPOINT (1, every interior edge at its midpoint: the baseline
+ *   the paper improves on; boundary rules unchanged).
  *   d_verts_out [n_verts*3] f64, d_faces_out [n_faces*3] i32 (device): the
  *   surviving vertices in increasing original id (FP64 positions) and the
  *   surviving faces, renumbered, in increasing original id; only the first
@@ -371,10 +374,24 @@ AG_API ag_status ag_exterior_fill(const float *d_verts, int64_t n_verts, const i
  *   Synchronises `stream` once per round.  Faces with an out-of-range index
  *   are dropped and set AG_ERR_INVALID_ARG in the status word.
  */
+enum { AG_QEM_OPTIMAL = 0, AG_QEM_MIDPOINT = 1 };
 AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
-                                 int64_t n_faces, int64_t target, int32_t max_rounds, ag_stream_t stream,
+                                 int64_t n_faces, int64_t target, int32_t max_rounds, int32_t placement,
+                                 ag_stream_t stream,
                                  double *d_verts_out, int32_t *d_faces_out, int32_t *d_keep_verts,
                                  int64_t *h_result);
+
+/*
+ * ag_point_distance - distance from each of n points to the mesh of the
+ *   handle (the closed triangles; a measurement tool, e.g. for Chamfer and
+ *   Hausdorff distances between meshes).  d_points [n*3] f32 device;
+ *   d_dist [n] f32 out: the distance, or -1 when no triangle lies within
+ *   max_dist; d_tri (optional) [n] i32 out: the nearest triangle (lowest id
+ *   among equal distances), -1 when none.  The query and its FP32
+ *   arithmetic are those of AG_QUERY_CLOSEST.
+ */
+AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_points, float max_dist,
+                                   const ag_opts *opts, ag_stream_t stream, float *d_dist, int32_t *d_tri);
 
 AG_API ag_status ag_sync_status(ag_stream_t stream);
 

@@ -82,7 +82,7 @@ def _load():
         lib.or_visibility.restype = _I
         lib.or_exterior_fill.argtypes = [_P, _P, _I64, _I64, _P, _P]
         lib.or_exterior_fill.restype = _I
-        lib.or_qem_simplify.argtypes = [_P, _I64, _P, _I64, _I64, _P, _P, _I, _P]
+        lib.or_qem_simplify.argtypes = [_P, _I64, _P, _I64, _I64, _P, _P, _I, _P, _I]
         lib.or_qem_simplify.restype = _I
         lib.or_qem_face_quadric.argtypes = [_P, _P]
         lib.or_qem_face_quadric.restype = None
@@ -407,7 +407,7 @@ def qem_place(q, v0, v1):
     return float(t), bool(sing.value)
 
 
-def qem_simplify(V, F, target: int, max_rounds: int = 100000):
+def qem_simplify(V, F, target: int, max_rounds: int = 100000, midpoint: bool = False):
     """Simplify to at most ``target`` faces.  Returns a dict: V (float64, the
     surviving vertices in increasing original id), F (renumbered, surviving
     faces in increasing original id), keep_v / keep_f (original ids),
@@ -419,7 +419,8 @@ def qem_simplify(V, F, target: int, max_rounds: int = 100000):
     va = np.zeros(nv, np.uint8)
     fa = np.zeros(nf, np.uint8)
     stats = np.zeros(2 * max_rounds, np.int64)
-    r = lib.or_qem_simplify(_p(V64), nv, _p(F32), nf, int(target), _p(va), _p(fa), max_rounds, _p(stats))
+    r = lib.or_qem_simplify(_p(V64), nv, _p(F32), nf, int(target), _p(va), _p(fa), max_rounds, _p(stats),
+                            int(bool(midpoint)))
     if r < 0:
         raise MemoryError("oracle QEM: allocation failed")
     keep_v = np.flatnonzero(va)

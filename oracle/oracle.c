@@ -1221,7 +1221,8 @@ int or_exterior_fill(const float *V, const int32_t *F, int64_t nv, int64_t nf, c
  * incident face) go to the endpoint with the lower E (ties to v0); an
  * interior edge with one boundary endpoint goes to that endpoint; an
  * interior edge with two boundary endpoints is not collapsed.  The cost is
- * E(v), negative rounding clamped to 0.
+ * E(v), negative rounding clamped to 0.  With `midpoint` set, interior edges
+ * go to their midpoint instead (the baseline the paper improves on).
  *
  * Validity (readings): the edge has at most two faces; both endpoints have
  * at most 64 neighbours; the link condition
@@ -1319,7 +1320,7 @@ static int face_has(const int32_t *F, int64_t f, int32_t v) { return F[3 * f] ==
  * returns the number of rounds, -1 on allocation failure.  stats (optional,
  * [max_rounds*2]): alive faces and collapses per round. */
 int or_qem_simplify(double *V, int64_t nv, int32_t *F, int64_t nf, int64_t target, uint8_t *valive, uint8_t *falive,
-                    int max_rounds, int64_t *stats) {
+                    int max_rounds, int64_t *stats, int midpoint) {
     qem_quad *Q = (qem_quad *)calloc((size_t)nv, sizeof(qem_quad));
     int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nv + 1));
     int32_t *vf = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)nf);
@@ -1405,7 +1406,7 @@ int or_qem_simplify(double *V, int64_t nv, int32_t *F, int64_t nf, int64_t targe
                 v = vb;
             } else {
                 int sing;
-                double t = qem_place(&Qe, va, vb, &sing);
+                double t = midpoint ? 0.5 : qem_place(&Qe, va, vb, &sing);
                 v = add(va, scl(sub(vb, va), t));
             }
             /* neighbourhoods */

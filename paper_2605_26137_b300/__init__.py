@@ -10,7 +10,8 @@ import importlib
 from ._lib import EXPORTS, AgError, load as load_library  # noqa: F401
 
 _TORCH_API = ("Bvh", "BakeOutputs", "Asset", "BatchPlan", "BakeLoss", "bake", "bake_batch", "bake_backward",
-              "bake_loss", "alloc_outputs", "sync_status", "visibility", "exterior_fill", "hidden_faces", "qem_simplify")
+              "bake_loss", "alloc_outputs", "sync_status", "visibility", "exterior_fill", "hidden_faces", "qem_simplify",
+              "point_distance")
 
 
 def __getattr__(name):

@@ -33,12 +33,15 @@ AG_SCHED_BATCH = 0
 AG_SCHED_REFILL = 1
 AG_QUERY_RAY = 0
 AG_QUERY_CLOSEST = 1
+AG_QEM_OPTIMAL = 0
+AG_QEM_MIDPOINT = 1
 
 # every symbol include/ag.h declares
 EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
            "ag_batch_plan_create", "ag_batch_plan_launch", "ag_batch_plan_free", "ag_bake_backward",
            "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc",
-           "ag_autotune", "ag_visibility", "ag_exterior_fill", "ag_qem_simplify")
+           "ag_autotune", "ag_visibility", "ag_exterior_fill", "ag_qem_simplify",
+           "ag_point_distance")
 
 
 class AgOpts(ctypes.Structure):
@@ -121,8 +124,11 @@ def load():
         lib.ag_visibility.restype = S
         lib.ag_exterior_fill.argtypes = [c_void_p, c_int64, c_void_p, c_int64, c_void_p, c_void_p, c_void_p]
         lib.ag_exterior_fill.restype = S
-        lib.ag_qem_simplify.argtypes = [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int32, c_void_p, c_void_p,
-                                        c_void_p, c_void_p, c_void_p]
+        lib.ag_qem_simplify.argtypes = [c_void_p, c_int64, c_void_p, c_int64, c_int64, c_int32, c_int32, c_void_p,
+                                        c_void_p, c_void_p, c_void_p, c_void_p]
+        lib.ag_point_distance.argtypes = [c_void_p, c_void_p, c_int64, c_float, POINTER(AgOpts), c_void_p, c_void_p,
+                                          c_void_p]
+        lib.ag_point_distance.restype = S
         lib.ag_qem_simplify.restype = S
         lib.ag_sync_status.argtypes = [c_void_p]
         lib.ag_sync_status.restype = S

@@ -190,6 +190,9 @@ struct TraceLaunch {
 cudaError_t launch_trace(const TraceLaunch &L, cudaStream_t s);
 // closest-point query, forward only (closest.cu)
 cudaError_t launch_closest(const TraceLaunch &L, cudaStream_t s);
+// distance from n points to the mesh of L.job0 (nodes, tris, tri_ids, scene_abs), -1 beyond max_dist
+cudaError_t launch_point_distance(const TraceLaunch &L, const float *pts, long long n, float max_dist, float *dist,
+                                  int32_t *tri, cudaStream_t s);
 
 cudaError_t launch_finalize(const float4 *ntsd, const int32_t *face_map, int W, int H, int gutter,
                             int disp_fp16, uint8_t *rgba, uint8_t *mask, void *disp,

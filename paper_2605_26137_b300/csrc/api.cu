@@ -454,6 +454,33 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
     return AG_OK;
 }
 
+AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_points, float max_dist,
+                                   const ag_opts *opts, ag_stream_t stream, float *d_dist, int32_t *d_tri) {
+    g_err.clear();
+    ag_status st = check_handle(h);
+    if (st) return st;
+    if (n_points < 0) return set_error(AG_ERR_INVALID_ARG, "n_points must be >= 0");
+    if (n_points == 0) return AG_OK;
+    if (!d_points || !d_dist) return set_error(AG_ERR_INVALID_ARG, "d_points and d_dist must be non-NULL");
+    if (!(max_dist > 0.f) || !(max_dist < 3.0e38f)) return set_error(AG_ERR_INVALID_ARG, "max_dist must be finite and > 0");
+    ag_opts o = resolve_opts(opts);
+    if ((st = check_opts(o))) return st;
+    unsigned *status = device_status_word(h->device);
+    if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    TraceLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.job0.nodes = h->nodes;
+    L.job0.tris = h->tris;
+    L.job0.tri_ids = h->tri_ids;
+    L.job0.scene_abs = 0.f;
+    for (int k = 0; k < 3; ++k) L.job0.scene_abs = fmaxf(L.job0.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+    L.status = status;
+    L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
+    L.layout = h->layout;
+    AG_CUDA(launch_point_distance(L, d_points, n_points, max_dist, d_dist, d_tri, (cudaStream_t)stream));
+    return AG_OK;
+}
+
 AG_API ag_status ag_sync_status(ag_stream_t stream) {
     g_err.clear();
     cudaStream_t s = (cudaStream_t)stream;

@@ -24,6 +24,8 @@
 //     zero counts as +).
 #include "traverse.cuh"
 
+#include <cstring>
+
 namespace ag {
 namespace {
 
@@ -357,7 +359,53 @@ cudaError_t launch_one(const TraceLaunch &L, const TraceArgs &A, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Point-to-mesh distance (measurement tool): the same branch-and-bound query
+// from arbitrary points, the radius starting at max_dist.
+template <int LAYOUT>
+__global__ void __launch_bounds__(256) k_point_dist(TraceArgs A, const float *__restrict__ pts, long long n,
+                                                    float max_dist, float *__restrict__ dist,
+                                                    int32_t *__restrict__ tri) {
+    uint2 stack[STACK];
+    PointState S;
+    unsigned long long c0 = 0, c1 = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        S.job = 0;
+        S.base = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        S.off = make_float3(0.f, 0.f, 0.f);
+        S.p = S.base;
+        S.d = make_float3(0.f, 0.f, 1.f);
+        S.best.d2 = max_dist * max_dist;
+        S.best.rec = 0;
+        S.best.found = false;
+        S.cur = 0;
+        S.sp = 0;
+        S.steps = 0;
+        while (step_point<LAYOUT, false>(A, A.job0, S, stack, c0, c1)) {
+        }
+        dist[i] = S.best.found ? sqrtf(S.best.d2) : -1.f;
+        if (tri) tri[i] = S.best.found ? A.job0.tri_ids[S.best.rec] : -1;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_point_distance(const TraceLaunch &L, const float *pts, long long n, float max_dist, float *dist,
+                                  int32_t *tri, cudaStream_t s) {
+    TraceArgs A;
+    memset(&A, 0, sizeof(A));
+    A.job0 = L.job0;
+    A.n_jobs = 1;
+    A.status = L.status;
+    A.max_steps = L.max_steps;
+    int dev;
+    cudaGetDevice(&dev);
+    const unsigned grid = (unsigned)(device_sm_count(dev) * 8);
+    if (L.layout == AG_BVH_Q8)
+        k_point_dist<AG_BVH_Q8><<<grid, 128, 0, s>>>(A, pts, n, max_dist, dist, tri);
+    else
+        k_point_dist<AG_BVH_F32><<<grid, 128, 0, s>>>(A, pts, n, max_dist, dist, tri);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_closest(const TraceLaunch &L, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(L.ray_counter, 0, sizeof(unsigned long long), s);

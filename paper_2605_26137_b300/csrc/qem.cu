@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V,
                                                     const double *__restrict__ Q, const unsigned *__restrict__ off,
                                                     const int32_t *__restrict__ list, const int32_t *__restrict__ ea,
                                                     const int32_t *__restrict__ eb, const uint8_t *__restrict__ nfaces,
-                                                    const uint8_t *__restrict__ bnd, int64_t ne,
+                                                    const uint8_t *__restrict__ bnd, int64_t ne, int placement,
                                                     unsigned long long *__restrict__ key, double *__restrict__ tpos) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V,
     } else if (bnd[b]) {
         v = vb;
     } else {
-        const double t = qem_place(q, va, vb);
+        const double t = placement == AG_QEM_MIDPOINT ? 0.5 : qem_place(q, va, vb);
         v = dadd(va, dscl(dsub(vb, va), t));
     }
     int32_t na_[QEM_MAX_NBR + 1], nb_[QEM_MAX_NBR + 1];
@@ -459,7 +459,8 @@ __global__ void k_compact_f(const int32_t *__restrict__ F, const uint8_t *__rest
 using namespace ag;
 
 extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
-                                            int64_t n_faces, int64_t target, int32_t max_rounds, ag_stream_t stream,
+                                            int64_t n_faces, int64_t target, int32_t max_rounds, int32_t placement,
+                                            ag_stream_t stream,
                                             double *d_verts_out, int32_t *d_faces_out, int32_t *d_keep_verts,
                                             int64_t *h_result) {
     if (!d_verts || !d_faces || !d_verts_out || !d_faces_out || !h_result)
@@ -468,6 +469,8 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     if (n_faces < 1 || n_faces >= (1ll << 29)) return set_error(AG_ERR_INVALID_ARG, "n_faces out of range");
     if (target < 0) return set_error(AG_ERR_INVALID_ARG, "target must be >= 0");
     if (max_rounds < 0) return set_error(AG_ERR_INVALID_ARG, "max_rounds must be >= 0");
+    if (placement != AG_QEM_OPTIMAL && placement != AG_QEM_MIDPOINT)
+        return set_error(AG_ERR_INVALID_ARG, "placement must be AG_QEM_OPTIMAL or AG_QEM_MIDPOINT");
     const int rounds_cap = max_rounds > 0 ? max_rounds : 100000;
     int dev = 0;
     AG_CUDA(cudaGetDevice(&dev));
@@ -551,7 +554,7 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
         k_edges<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff, ea, eb);
         AG_CUDA(cudaMemsetAsync(bnd, 0, nv, s));
         k_edge_faces<<<blocks(ne, B), B, 0, s>>>(F, off, list, ea, eb, ne, nfaces, bnd);
-        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, F, Q, off, list, ea, eb, nfaces, bnd, ne, key, tpos);
+        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, F, Q, off, list, ea, eb, nfaces, bnd, ne, placement, key, tpos);
         AG_CUDA(cudaMemsetAsync(m1, 0xff, sizeof(unsigned long long) * nv, s));
         k_m1<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, ne, m1);
         AG_CUDA(cudaMemcpyAsync(m2, m1, sizeof(unsigned long long) * nv, cudaMemcpyDeviceToDevice, s));

@@ -348,9 +348,11 @@ def hidden_faces(verts, faces, n_views: int = 512, res: int = 1024, *, stream=No
 
 # ----------------------------------------------------------------- QEM simplification (Sec. 6.1)
 
-def qem_simplify(verts, faces, target: int, *, max_rounds: int = 0, stream=None):
-    """Simplify to at most ``target`` faces.  Returns (verts f64 [n,3],
-    faces i32 [m,3], keep_verts i32 [n] original ids, rounds)."""
+def qem_simplify(verts, faces, target: int, *, max_rounds: int = 0, placement: str = "optimal", stream=None):
+    """Simplify to at most ``target`` faces.  ``placement`` is "optimal" (the
+    paper's projected optimum) or "midpoint" (the baseline it improves on).
+    Returns (verts f64 [n,3], faces i32 [m,3], keep_verts i32 [n] original
+    ids, rounds)."""
     lib = _lib.load()
     _need(verts, "verts", torch.float32, (3,))
     _need(faces, "faces", torch.int32, (3,))
@@ -358,10 +360,25 @@ def qem_simplify(verts, faces, target: int, *, max_rounds: int = 0, stream=None)
     fo = torch.empty((faces.shape[0], 3), dtype=torch.int32, device=faces.device)
     keep = torch.empty(verts.shape[0], dtype=torch.int32, device=verts.device)
     res = (ctypes.c_int64 * 3)()
+    mode = {"optimal": _lib.AG_QEM_OPTIMAL, "midpoint": _lib.AG_QEM_MIDPOINT}[placement]
     check(lib.ag_qem_simplify(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0], int(target),
-                              int(max_rounds), _stream(stream), vo.data_ptr(), fo.data_ptr(), keep.data_ptr(), res))
+                              int(max_rounds), mode, _stream(stream), vo.data_ptr(), fo.data_ptr(), keep.data_ptr(),
+                              res))
     n, m = int(res[0]), int(res[1])
     return vo[:n], fo[:m], keep[:n], int(res[2])
+
+
+def point_distance(bvh: Bvh, points, max_dist: float, *, tri: bool = False, stream=None):
+    """Distance from each point [n,3] f32 to the mesh ``bvh`` was built on
+    (-1 where nothing lies within max_dist); with ``tri`` also the nearest
+    triangle ids."""
+    lib = _lib.load()
+    _need(points, "points", torch.float32, (3,))
+    d = torch.empty(points.shape[0], dtype=torch.float32, device=points.device)
+    t = torch.empty(points.shape[0], dtype=torch.int32, device=points.device) if tri else None
+    check(lib.ag_point_distance(bvh.handle, points.data_ptr(), points.shape[0], float(max_dist), None,
+                                _stream(stream), d.data_ptr(), _ptr(t)))
+    return (d, t) if tri else d
 
 
 def sync_status(stream=None) -> None:

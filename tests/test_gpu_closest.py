@@ -177,3 +177,30 @@ def test_closest_full_size_sampled_parity():
     filled = g["normal_rgba8"][..., 3] == 255
     assert np.abs(np.linalg.norm(n[filled], axis=-1) - 1).max() < 1e-5
     bvh.free()
+
+
+def test_point_distance_matches_oracle():
+    """ag_point_distance: distances from random points near and far from a
+    marching-grid surface against the oracle's closest point."""
+    import paper_2605_26137_b300 as pb
+    V, F = synth.sdf_mesh(synth.sdf_union_params(4, 12), 40, device="cpu")
+    diam = float(np.linalg.norm(V.max(0) - V.min(0)))
+    rng = np.random.default_rng(3)
+    pts = np.concatenate([V[rng.integers(0, len(V), 3000)] + rng.normal(scale=0.02, size=(3000, 3)),
+                          rng.uniform(-1.5, 1.5, size=(1000, 3))]).astype(np.float32)
+    bvh = pb.Bvh(_t(V), _t(F))
+    max_dist = 0.1
+    d, tri = pb.point_distance(bvh, _t(pts), max_dist, tri=True)
+    pb.sync_status()
+    d, tri = d.cpu().numpy().astype(np.float64), tri.cpu().numpy()
+    ob = oracle.Bvh(V, F)
+    for k, p in enumerate(pts):
+        t, d2, _, _ = oracle.closest_point(V, F, p.astype(np.float64), max_dist, bvh=ob)
+        if t < 0:
+            assert d[k] == -1.0 or abs(d[k] - max_dist) < 1e-6 * diam
+            continue
+        assert abs(d[k] - np.sqrt(d2)) <= 1e-6 * diam, k
+        # the kernel's triangle is at the same distance (ties may pick another)
+        _, d2k, _, _ = oracle.closest_point(V[F[tri[k]]], np.array([[0, 1, 2]], np.int32), p.astype(np.float64), 10.0)
+        assert abs(np.sqrt(d2k) - np.sqrt(d2)) <= 1e-6 * diam
+    bvh.free()

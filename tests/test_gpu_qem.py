@@ -94,3 +94,21 @@ def test_identical_to_oracle_250k():
     V, F = synth.sdf_mesh(synth.sdf_union_params(5, 24), 128, device="cpu")
     assert len(F) > 150_000
     assert_identical(V, F, 10_000)
+
+
+def test_midpoint_placement_identical_and_worse_than_optimal():
+    """The baseline placement (every interior edge at its midpoint) through the
+    same rounds: identical to the oracle's baseline; on a curved surface the
+    paper's projected optimum keeps the vertices closer to the original."""
+    V, F = synth.sdf_mesh(synth.sdf_union_params(3, 12), 48, device="cpu")
+    o = oracle.qem_simplify(V, F, 4000, midpoint=True)
+    vo, fo, keep, rounds = gpu_simplify(V, F, 4000, placement="midpoint")
+    assert rounds == o["rounds"] and np.array_equal(fo, o["F"]) and np.array_equal(keep, o["keep_v"])
+    assert np.array_equal(vo.view(np.uint64), o["V"].view(np.uint64))
+    opt = oracle.qem_simplify(V, F, 4000)
+    bvh = oracle.Bvh(V, F)
+    diam = float(np.linalg.norm(V.max(0) - V.min(0)))
+
+    def mean_dist(Vs):
+        return np.mean([np.sqrt(oracle.closest_point(V, F, v, diam, bvh=bvh)[1]) for v in Vs])
+    assert mean_dist(opt["V"]) < mean_dist(o["V"])
