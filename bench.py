@@ -12,8 +12,10 @@ once per high mesh and timed separately.  The metric is rays per second
 batched-vs-one-by-one speedup, the backward/forward time ratio, the
 quantised-vs-FP32 BVH comparison, the closest-point correspondence (Sec.
 6.4 as worded) on the same asset, with its angular difference from the ray
-bake, and hidden-face removal (Sec. 6.2: 512 views x 1024^2 rays against a
-~22k-face mesh with interior shells, then the exterior flood fill).
+bake, hidden-face removal (Sec. 6.2: 512 views x 1024^2 rays against a
+~22k-face mesh with interior shells, then the exterior flood fill) and QEM
+simplification (Sec. 6.1: ~1M faces to 10k and 5k, the paper's placement
+against the midpoint baseline, Chamfer and Hausdorff distances).
 
 --impl reference times the FP64 CPU oracle (the repository's plain,
 deliberately slow reference) on a bounded sample of the same workload.
@@ -72,14 +74,15 @@ def parse():
     p.add_argument("--profile", action="store_true",
                    help="profiling case for ncu: one BVH build and --steps plain bakes, nothing else")
     p.add_argument("--layout", default="q8", choices=["q8", "f32"])
-    p.add_argument("--query", default="ray", choices=["ray", "closest", "hidden"],
-                   help="--profile: the ray or closest-point bake, or the hidden-face visibility pass")
+    p.add_argument("--query", default="ray", choices=["ray", "closest", "hidden", "qem"],
+                   help="--profile: the ray or closest-point bake, the hidden-face visibility pass or QEM")
     p.add_argument("--error-sample", type=float, default=20000,
                    help="ray texels compared with the oracle per layout (a value < 1 is a fraction of them)")
     p.add_argument("--collapse", default="area", choices=["area_count", "area", "count"])
     p.add_argument("--hidden-views", type=int, default=512, help="hidden-face removal: viewpoints")
     p.add_argument("--hidden-res", type=int, default=1024, help="hidden-face removal: image resolution")
     p.add_argument("--hidden-faces", type=int, default=22000, help="hidden-face removal: mesh faces")
+    p.add_argument("--qem-faces", type=int, default=1_000_000, help="QEM simplification: input faces")
     return p.parse_args()
 
 
@@ -245,6 +248,21 @@ def run_profile(args):
                       "query": args.query, "bakes": args.steps, "kernel_source_hash": trace_source_hash(kernel)}))
 
 
+def run_profile_qem(args):
+    """One QEM simplification of the ~1M-face surface to 10k faces."""
+    import torch
+    import paper_2605_26137_b300 as pb
+    from paper_2605_26137_b300 import synth
+    torch.cuda.set_device(0)
+    V, F = synth.sdf_mesh_target(synth.sdf_union_params(args.seed, 32), args.qem_faces, device="cuda")
+    v, f = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (V, F))
+    for _ in range(args.steps):
+        _, fo, _, rounds = pb.qem_simplify(v, f, 10000)
+    pb.sync_status()
+    print(json.dumps({"profile_case": "QEM simplification", "faces": int(len(F)), "out_faces": int(fo.shape[0]),
+                      "rounds": rounds}))
+
+
 def run_profile_hidden(args):
     """Few launches of the visibility pass on the hidden-face workload."""
     import torch
@@ -365,6 +383,8 @@ def main():
     if args.profile:
         if args.query == "hidden":
             run_profile_hidden(args)
+        elif args.query == "qem":
+            run_profile_qem(args)
         else:
             run_profile(args)
         return
@@ -563,9 +583,62 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     bf.free()
     res["closest_point"] = closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush)
     res["hidden_face_removal"] = hidden_leg(args, pb, torch, dev, flush)
+    res["qem_simplification"] = qem_leg(args, pb, torch, dev)
     if args.batch_assets > 0:
         res["batch"] = batch_leg(args, pb, torch, dev, flush)
     return res
+
+
+def sample_surface(torch, V, F, n, seed):
+    """n points uniformly by area on the triangle mesh (V f32 [.,3], F i32 [.,3], device tensors)."""
+    g = torch.Generator(device=V.device)
+    g.manual_seed(seed)
+    A, B, C = V[F[:, 0].long()], V[F[:, 1].long()], V[F[:, 2].long()]
+    area = torch.linalg.vector_norm(torch.cross(B - A, C - A, dim=1), dim=1).double()
+    idx = torch.multinomial(area / area.sum(), n, replacement=True, generator=g)
+    u = torch.rand(n, device=V.device, generator=g)
+    v = torch.rand(n, device=V.device, generator=g)
+    flip = u + v > 1
+    u, v = torch.where(flip, 1 - u, u), torch.where(flip, 1 - v, v)
+    return (A[idx] + (B - A)[idx] * u[:, None] + (C - A)[idx] * v[:, None]).contiguous()
+
+
+def qem_leg(args, pb, torch, dev):
+    """QEM simplification (Sec. 6.1) of a ~1M-face marching-grid SDF surface
+    (the paper's input size) to 10k and 5k faces, with the paper's projected
+    optimum and with the midpoint baseline it improves on: time, rounds, and
+    the paper's geometric metrics against the input (Chamfer: mean
+    point-to-surface distance both ways; Hausdorff: the maximum), on 256k
+    area-sampled points per side, as fractions of the bounding-box diagonal."""
+    from paper_2605_26137_b300 import synth
+    V, F = synth.sdf_mesh_target(synth.sdf_union_params(args.seed, 32), args.qem_faces, device=dev)
+    v, f = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (V, F))
+    diam = float(np.linalg.norm(V.max(0) - V.min(0)))
+    orig = pb.Bvh(v, f)
+    p_orig = sample_surface(torch, v, f, 1 << 18, args.seed)
+    pb.qem_simplify(v, f, 10000)   # warm-up
+    torch.cuda.synchronize()
+    out = {"input_faces": int(len(F)), "input_verts": int(len(V)), "diam": diam, "runs": []}
+    for target in (10000, 5000):
+        for placement in ("optimal", "midpoint"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            vo, fo, keep, rounds = pb.qem_simplify(v, f, target, placement=placement)
+            torch.cuda.synchronize()
+            ms = 1e3 * (time.perf_counter() - t0)
+            vs = vo.float().contiguous()
+            simp = pb.Bvh(vs, fo)
+            p_simp = sample_surface(torch, vs, fo, 1 << 18, args.seed + 1)
+            d_os = pb.point_distance(simp, p_orig, diam)
+            d_so = pb.point_distance(orig, p_simp, diam)
+            pb.sync_status()
+            simp.free()
+            out["runs"].append({"target": target, "placement": placement, "faces": int(fo.shape[0]),
+                                "rounds": rounds, "ms": ms,
+                                "chamfer": float((d_os.mean() + d_so.mean()) / 2 / diam),
+                                "hausdorff": float(torch.maximum(d_os.max(), d_so.max()) / diam)})
+    orig.free()
+    return out
 
 
 def hidden_leg(args, pb, torch, dev, flush):
