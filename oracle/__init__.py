@@ -84,6 +84,11 @@ def _load():
         lib.or_exterior_fill.restype = _I
         lib.or_qem_simplify.argtypes = [_P, _I64, _P, _I64, _I64, _P, _P, _I, _P, _I]
         lib.or_qem_simplify.restype = _I
+        lib.or_render_view.argtypes = [_P, _P, _I64, _P, _P, _I, _I, _D, _P, _P, _P]
+        lib.or_render_view.restype = _I
+        lib.or_backproject.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P,
+                                       _D, _D, _D, _D, _D, _P, _P, _P, _P]
+        lib.or_backproject.restype = _I
         lib.or_qem_face_quadric.argtypes = [_P, _P]
         lib.or_qem_face_quadric.restype = None
         lib.or_qem_eval.argtypes = [_P, _P]
@@ -430,3 +435,59 @@ def qem_simplify(V, F, target: int, max_rounds: int = 100000, midpoint: bool = F
     Fo = new_id[F32[keep_f]].astype(np.int32)
     return dict(V=V64[keep_v], F=Fo, keep_v=keep_v, keep_f=keep_f, rounds=r,
                 alive=stats[0:2 * r:2].copy(), collapses=stats[1:2 * r:2].copy())
+
+
+# ----------------------------------------------------------------- UV-space backprojection (Sec. 7.4)
+
+def render_views(V, F, cams, w: int, h: int, *, tol_rel: float = 1e-5, bvh: Bvh | None = None):
+    """Depth [K,h,w] (camera z of the first hit, +inf on a miss), world points
+    [K,h,w,3] (NaN on a miss) and near-edge flags [K,h,w] of K pinhole
+    views (cams [K,16] f32: R row-major, t, fx, fy, cx, cy)."""
+    lib = _load()
+    V = _c(V, np.float32)
+    F = _c(F, np.int32)
+    if bvh is None:
+        bvh = Bvh(V, F)
+    Vd = V.astype(np.float64)
+    scale = float(np.linalg.norm(Vd.max(0) - Vd.min(0)))
+    cams = _c(cams, np.float32).reshape(-1, 16)
+    K = len(cams)
+    depth = np.empty((K, h, w), np.float64)
+    point = np.empty((K, h, w, 3), np.float64)
+    near = np.empty((K, h, w), np.uint8)
+    for k in range(K):
+        lib.or_render_view(_p(V), _p(F), len(F), bvh.h, _p(cams[k]), w, h, tol_rel * scale,
+                           _p(depth[k]), _p(point[k]), _p(near[k]))
+    return depth, point, near
+
+
+def backproject(lv, lf, luv, W: int, H: int, cams, images, weights, *, alpha: float, eps: float,
+                depth_tol: float, edge_tol: float, views=None, tol_rel: float = 1e-5):
+    """Texture [H,W,3] (FP64), filled [H,W], flags [H,W] and incidence
+    [K,H,W] of the blended backprojection of K views onto the low mesh's
+    atlas.  ``views`` = (depth, point, near) from render_views, rendered here
+    when None."""
+    lib = _load()
+    lv = _c(lv, np.float32)
+    lf = _c(lf, np.int32)
+    luv = _c(luv, np.float32)
+    cams = _c(cams, np.float32).reshape(-1, 16)
+    images = _c(images, np.uint8)
+    K, ih, iw = images.shape[0], images.shape[1], images.shape[2]
+    weights = _c(weights, np.float32)
+    if views is None:
+        views = render_views(lv, lf, cams, iw, ih, tol_rel=tol_rel)
+    depth, point, near = (_c(views[0], np.float64), _c(views[1], np.float64), _c(views[2], np.uint8))
+    face, bary, _ = raster(luv, W, H)
+    ln = vertex_normals(lv, lf)
+    Vd = lv.astype(np.float64)
+    scale = float(np.linalg.norm(Vd.max(0) - Vd.min(0)))
+    tex = np.zeros((H, W, 3), np.float64)
+    filled = np.zeros((H, W), np.uint8)
+    flags = np.zeros((H, W), np.uint8)
+    incid = np.zeros((K, H, W), np.float64)
+    lib.or_backproject(_p(lv), len(lv), _p(lf), len(lf), _p(ln), _p(face), _p(bary), W, H, K, _p(cams), _p(images),
+                       iw, ih, _p(depth), _p(point), _p(near), _p(weights), float(alpha), float(eps),
+                       float(depth_tol), float(edge_tol), scale, _p(tex), _p(filled), _p(flags), _p(incid))
+    return dict(texture=tex, filled=filled, flags=flags, incidence=incid, face=face, bary=bary,
+                depth=depth, point=point, near=near)

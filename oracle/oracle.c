@@ -1527,3 +1527,209 @@ double or_qem_place(const double *q, const double *v0, const double *v1, int *si
     memcpy(Q.q, q, sizeof(Q.q));
     return qem_place(&Q, mk(v0[0], v0[1], v0[2]), mk(v1[0], v1[1], v1[2]), singular);
 }
+
+/* ------------------------------------------------- 10. UV-space backprojection (Sec. 7.4)
+ * Readings.  A view is a pinhole camera with world -> camera rotation R (rows
+ * right, down, forward), translation t and intrinsics fx, fy, cx, cy in
+ * pixels: a point p has camera coordinates c = R p + t, depth z = c.z, and
+ * image position u = fx c.x / z + cx, v = fy c.y / z + cy; pixel (i, j)
+ * covers [i, i+1) x [j, j+1).
+ *  - Depth buffer: for every pixel, the first hit of the ray through its
+ *    centre against the mesh (section 4's closest-hit rules), its depth z and
+ *    world point; +inf / NaN where the ray misses.  A pixel is an edge pixel
+ *    when it is a hit and one of its 4-neighbours is a miss or has a world
+ *    point farther than edge_tol from its own (the paper's large
+ *    neighbour differences of the point map).
+ *  - Per ray texel (the raster of section 2, surface point p = sum b_i v_i,
+ *    normal n = normalize(sum b_i n_i) of the smooth vertex normals): for
+ *    every view with z > 0 and (u, v) inside the image, the pixel (floor u,
+ *    floor v) must be a hit, not an edge pixel, with z <= its depth +
+ *    depth_tol; then I = max(0, n . normalize(C - p)) (C the camera centre)
+ *    and the colour A is the bilinear sample of the view's RGB at
+ *    (u - 1/2, v - 1/2), clamped to the image, 8-bit codes / 255.
+ *  - Blend: T = sum_k w_k I_k^alpha A_k / (sum_k w_k I_k^alpha + eps) over the
+ *    views with I_k > 0, evaluated through the log-sum-exp form
+ *    m = max_k (log w_k + alpha log I_k),
+ *    T = sum_k e^(L_k - m) A_k / (sum_k e^(L_k - m) + eps e^(-m)).
+ *    A texel with no such view stays unfilled (T = 0).
+ *  - Exception flags: a texel is flagged when, for some view, u or v lies
+ *    within 1e-3 pixel of a pixel boundary or of the image border, z lies
+ *    within 1e-5 * scale of the depth limit, or the pixel's ray or one of its
+ *    4-neighbours' passes within 1e-5 * scale of a triangle edge (hit, edge
+ *    mask and depth there depend on rounding). */
+typedef struct { double R[9], t[3], fx, fy, cx, cy; } cam_t;
+
+static cam_t load_cam(const float *c) {
+    cam_t k;
+    for (int i = 0; i < 9; ++i) k.R[i] = c[i];
+    for (int i = 0; i < 3; ++i) k.t[i] = c[9 + i];
+    k.fx = c[12]; k.fy = c[13]; k.cx = c[14]; k.cy = c[15];
+    return k;
+}
+
+static d3 cam_apply(const cam_t *k, d3 p) {
+    return mk(k->R[0] * p.x + k->R[1] * p.y + k->R[2] * p.z + k->t[0],
+              k->R[3] * p.x + k->R[4] * p.y + k->R[5] * p.z + k->t[1],
+              k->R[6] * p.x + k->R[7] * p.y + k->R[8] * p.z + k->t[2]);
+}
+
+static d3 cam_centre(const cam_t *k) {   /* C = -R^T t */
+    return mk(-(k->R[0] * k->t[0] + k->R[3] * k->t[1] + k->R[6] * k->t[2]),
+              -(k->R[1] * k->t[0] + k->R[4] * k->t[1] + k->R[7] * k->t[2]),
+              -(k->R[2] * k->t[0] + k->R[5] * k->t[1] + k->R[8] * k->t[2]));
+}
+
+/* depth [h*w] (camera z of the first hit, +inf on a miss), point [h*w*3]
+ * (NaN on a miss), near [h*w] (the pixel's ray passes within tol of a
+ * triangle edge), per view */
+int or_render_view(const float *V, const int32_t *F, int64_t nf, void *bvh, const float *camf, int w, int h,
+                   double tol, double *depth, double *point, uint8_t *near) {
+    cam_t k = load_cam(camf);
+    d3 C = cam_centre(&k);
+    const obvh *b = (const obvh *)bvh;
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            int64_t px = (int64_t)j * w + i;
+            d3 dc = mk((i + 0.5 - k.cx) / k.fx, (j + 0.5 - k.cy) / k.fy, 1.0);
+            /* world direction R^T dc */
+            d3 d = normalize(mk(k.R[0] * dc.x + k.R[3] * dc.y + k.R[6] * dc.z,
+                                k.R[1] * dc.x + k.R[4] * dc.y + k.R[7] * dc.z,
+                                k.R[2] * dc.x + k.R[5] * dc.y + k.R[8] * dc.z));
+            hit_t hh;
+            closest(V, F, nf, b, C, d, 1e30, -1, &hh);
+            uint8_t nr = 0;
+            if (hh.tri >= 0 && hh.t > 0.0) {
+                d3 X = add(C, scl(d, hh.t));
+                depth[px] = cam_apply(&k, X).z;
+                std3(point, px, X);
+                const int32_t *f = F + 3 * hh.tri;
+                for (int m = 0; m < 3; ++m) {
+                    d3 a = ldf(V, f[m]), e = sub(ldf(V, f[(m + 1) % 3]), a);
+                    double ee = dot(e, e), s = ee > 0 ? dot(sub(X, a), e) / ee : 0.0;
+                    if (s < 0) s = 0;
+                    if (s > 1) s = 1;
+                    if (norm(sub(X, add(a, scl(e, s)))) < tol) nr = 1;
+                }
+            } else {
+                depth[px] = INFINITY;
+                std3(point, px, mk(NAN, NAN, NAN));
+                /* a miss near the silhouette */
+                vis_job vj;
+                memset(&vj, 0, sizeof(vj));
+                vj.V = V; vj.F = F; vj.nf = nf; vj.bvh = b; vj.delta = tol;
+                int32_t cl[OR_MAX_CAND], nc = 0;
+                ray_t r = make_ray(C, d);
+                candidates(&vj, C, d, &r, 1e30, cl, &nc);
+                if (nc > 0) nr = 1;
+            }
+            near[px] = nr;
+        }
+    return 0;
+}
+
+static double bilinear(const uint8_t *img, int w, int h, int ch, double x, double y) {
+    double fx = floor(x), fy = floor(y);
+    double ax = x - fx, ay = y - fy;
+    int x0 = (int)fx, y0 = (int)fy;
+    double acc = 0.0;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+            int xx = x0 + dx, yy = y0 + dy;
+            if (xx < 0) xx = 0;
+            if (yy < 0) yy = 0;
+            if (xx > w - 1) xx = w - 1;
+            if (yy > h - 1) yy = h - 1;
+            double wgt = (dx ? ax : 1.0 - ax) * (dy ? ay : 1.0 - ay);
+            acc += wgt * (img[((int64_t)yy * w + xx) * 4 + ch] / 255.0);
+        }
+    return acc;
+}
+
+static int is_edge(const double *depth, const double *point, int w, int h, int i, int j, double edge_tol) {
+    int64_t px = (int64_t)j * w + i;
+    if (!(depth[px] < INFINITY)) return 0;
+    const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+    for (int n = 0; n < 4; ++n) {
+        int ii = i + di[n], jj = j + dj[n];
+        if (ii < 0 || jj < 0 || ii >= w || jj >= h) continue;
+        int64_t q = (int64_t)jj * w + ii;
+        if (!(depth[q] < INFINITY)) return 1;
+        if (norm(sub(ldd(point, q), ldd(point, px))) > edge_tol) return 1;
+    }
+    return 0;
+}
+
+/* texture [H*W*3], filled [H*W], flags [H*W], incid (optional) [K*H*W] */
+int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf, const double *ln, const int32_t *face,
+                   const double *bary, int W, int H, int K, const float *cams, const uint8_t *images, int iw, int ih,
+                   const double *depth, const double *point, const uint8_t *near, const float *weights, double alpha,
+                   double eps, double depth_tol, double edge_tol, double scale, double *texture, uint8_t *filled,
+                   uint8_t *flags, double *incid) {
+    (void)nlv; (void)nlf;
+    int64_t npix = (int64_t)iw * ih;
+    for (int64_t tex = 0; tex < (int64_t)W * H; ++tex) {
+        texture[3 * tex] = texture[3 * tex + 1] = texture[3 * tex + 2] = 0.0;
+        filled[tex] = 0;
+        flags[tex] = 0;
+        if (incid) for (int k = 0; k < K; ++k) incid[(int64_t)k * W * H + tex] = 0.0;
+        int32_t f = face[tex];
+        if (f < 0) continue;
+        const double *b = bary + 3 * tex;
+        d3 p = mk(0, 0, 0), s = mk(0, 0, 0);
+        for (int m = 0; m < 3; ++m) {
+            p = add(p, scl(ldf(lv, lf[3 * f + m]), b[m]));
+            s = add(s, scl(ldd(ln, lf[3 * f + m]), b[m]));
+        }
+        d3 n = normalize(s);
+        double L[64], A[64][3];
+        int nk = 0;
+        uint8_t fl = 0;
+        for (int k = 0; k < K && k < 64; ++k) {
+            cam_t c = load_cam(cams + 16 * k);
+            d3 q = cam_apply(&c, p);
+            if (!(q.z > 0.0)) continue;
+            double u = c.fx * q.x / q.z + c.cx, v = c.fy * q.y / q.z + c.cy;
+            double fu = u - floor(u), fv = v - floor(v);
+            if (fu < 1e-3 || fu > 1.0 - 1e-3 || fv < 1e-3 || fv > 1.0 - 1e-3) fl = 1;
+            if (!(u >= 0.0 && u < iw && v >= 0.0 && v < ih)) continue;
+            int i = (int)floor(u), j = (int)floor(v);
+            const double *dk = depth + (int64_t)k * npix;
+            const double *pk = point + (int64_t)k * npix * 3;
+            const uint8_t *nk_ = near + (int64_t)k * npix;
+            int64_t px = (int64_t)j * iw + i;
+            if (nk_[px]) fl = 1;
+            {
+                const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+                for (int nn = 0; nn < 4; ++nn) {
+                    int ii = i + di[nn], jj = j + dj[nn];
+                    if (ii >= 0 && jj >= 0 && ii < iw && jj < ih && nk_[(int64_t)jj * iw + ii]) fl = 1;
+                }
+            }
+            if (!(dk[px] < INFINITY)) continue;
+            if (is_edge(dk, pk, iw, ih, i, j, edge_tol)) continue;
+            if (fabs(q.z - (dk[px] + depth_tol)) < 1e-5 * scale) fl = 1;
+            if (q.z > dk[px] + depth_tol) continue;
+            d3 C = cam_centre(&c);
+            double I = dot(n, normalize(sub(C, p)));
+            if (!(I > 0.0)) continue;
+            if (incid) incid[(int64_t)k * W * H + tex] = I;
+            L[nk] = log((double)weights[k]) + alpha * log(I);
+            for (int ch = 0; ch < 3; ++ch) A[nk][ch] = bilinear(images + (int64_t)k * npix * 4, iw, ih, ch, u - 0.5, v - 0.5);
+            ++nk;
+        }
+        flags[tex] = fl;
+        if (nk == 0) continue;
+        double m = L[0];
+        for (int k = 1; k < nk; ++k) if (L[k] > m) m = L[k];
+        double num[3] = {0, 0, 0}, den = 0.0;
+        for (int k = 0; k < nk; ++k) {
+            double e = exp(L[k] - m);
+            den += e;
+            for (int ch = 0; ch < 3; ++ch) num[ch] += e * A[k][ch];
+        }
+        den += eps * exp(-m);
+        for (int ch = 0; ch < 3; ++ch) texture[3 * tex + ch] = num[ch] / den;
+        filled[tex] = 1;
+    }
+    return 0;
+}

@@ -414,3 +414,76 @@ def sdf_asset(seed: int, high_faces: int, low_faces: int, W: int, H: int,
               f"sdf{n_prims}-s{seed}-high{len(hf)}-low{len(lf)}-{W}x{H}", {"seed": seed, "grids": dict(p.meta)})
     a.max_dist = max_dist_frac * a.diam
     return a
+
+
+# --------------------------------------------------------------------------
+# Cameras and generated-view stand-ins (UV-space backprojection)
+# --------------------------------------------------------------------------
+
+# the paper's view set (Sec. 7.4): azimuth / elevation in degrees and prior weight
+PAPER_VIEWS = (("front", 0, 0, 1.0), ("rear", 180, 0, 1.0), ("top", 0, 90, 0.3), ("bottom", 0, -90, 0.3),
+               ("front_left45", -45, 0, 0.1), ("front_right45", 45, 0, 0.1), ("left", -90, 0, 0.01),
+               ("right", 90, 0, 0.01), ("rear_left45", -135, 0, 0.001), ("rear_right45", 135, 0, 0.001))
+
+
+def look_at_camera(eye, target, up, fov_deg: float, w: int, h: int):
+    """Pinhole camera [16] f32: R (rows right, down, forward) row-major, t,
+    fx, fy, cx, cy, looking from ``eye`` at ``target``."""
+    eye, target, up = (np.asarray(x, np.float64) for x in (eye, target, up))
+    f = target - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(f, up)
+    if np.linalg.norm(r) < 1e-9:
+        r = np.cross(f, [1.0, 0.0, 0.0])
+    r /= np.linalg.norm(r)
+    d = np.cross(f, r)
+    R = np.stack([r, d, f])
+    t = -R @ eye
+    fy = 0.5 * h / math.tan(math.radians(fov_deg) / 2)
+    return np.concatenate([R.ravel(), t, [fy, fy, 0.5 * w, 0.5 * h]]).astype(np.float32)
+
+
+def paper_cameras(center, radius: float, w: int, h: int, fov_deg: float = 40.0):
+    """The ten views of PAPER_VIEWS around a bounding sphere (centre, radius),
+    framed so that the sphere fits the image; front looks along -z, up is +y.
+    Returns (cams [10,16] f32, weights [10] f32, names)."""
+    dist = radius / math.sin(math.radians(fov_deg) / 2) * 1.05
+    cams, weights, names = [], [], []
+    for name, az, el, wgt in PAPER_VIEWS:
+        a, e = math.radians(az), math.radians(el)
+        direction = np.array([math.sin(a) * math.cos(e), math.sin(e), math.cos(a) * math.cos(e)])
+        up = [0.0, 1.0, 0.0] if abs(el) < 80 else [0.0, 0.0, -1.0 if el > 0 else 1.0]
+        cams.append(look_at_camera(np.asarray(center) + dist * direction, center, up, fov_deg, w, h))
+        weights.append(wgt)
+        names.append(name)
+    return np.stack(cams), np.asarray(weights, np.float32), names
+
+
+def color_field(points):
+    """Smooth seeded colour of world points [...,3] (numpy or torch), values in
+    [0.05, 0.95] per channel: the stand-in for a generated texture."""
+    mod = np
+    try:
+        import torch
+        if isinstance(points, torch.Tensor):
+            mod = torch
+    except ImportError:
+        pass
+    x, y, z = points[..., 0], points[..., 1], points[..., 2]
+    r = 0.5 + 0.45 * mod.sin(2.1 * x + 0.7 * y + 0.3)
+    g = 0.5 + 0.45 * mod.sin(1.3 * y - 1.7 * z + 1.1)
+    b = 0.5 + 0.45 * mod.cos(1.9 * z + 0.9 * x - 0.4)
+    return mod.stack([r, g, b], -1)
+
+
+def view_images(points, colors=color_field):
+    """RGBA8 images [K,h,w,4] of world point maps [K,h,w,3] (NaN = background,
+    coloured black, alpha 0)."""
+    pts = np.asarray(points, np.float64)
+    hit = np.isfinite(pts[..., 0])
+    c = np.zeros(pts.shape[:-1] + (3,), np.float64)
+    c[hit] = colors(pts[hit])
+    img = np.zeros(pts.shape[:-1] + (4,), np.uint8)
+    img[..., :3] = np.clip(np.round(c * 255), 0, 255).astype(np.uint8)
+    img[..., 3] = np.where(hit, 255, 0)
+    return img

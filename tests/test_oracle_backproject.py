@@ -1,0 +1,197 @@
+"""Pins for the oracle's UV-space backprojection and incidence blending
+(Sec. 7.4).
+
+* a plane seen face-on through an image whose codes are affine in the pixel
+  index: bilinear sampling reproduces the affine map, so the texture equals
+  the closed form of the projection;
+* occlusion: a plane behind another receives nothing where it is covered;
+* blending: two constant-colour views of a tilted plane mix with weights
+  w_k cos^alpha(theta_k) (closed form); a large alpha, where the powers
+  underflow, still picks the better view (the log-space reduction);
+* back-facing surfaces, points behind a camera and edge pixels (depth
+  discontinuities) contribute nothing;
+* the rendered depth of a plane is its distance along the view axis.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_26137_b300 import synth
+
+
+def _plane(n, z=0.0, size=1.0, flip=False):
+    xs = np.linspace(-size, size, n + 1)
+    X, Y = np.meshgrid(xs, xs)
+    V = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], -1).astype(np.float32)
+    F = []
+    for j in range(n):
+        for i in range(n):
+            a = j * (n + 1) + i
+            F += [(a, a + 1, a + n + 2), (a, a + n + 2, a + n + 1)]
+    F = np.asarray(F, np.int32)
+    if flip:
+        F = F[:, ::-1].copy()
+    return V, F
+
+
+def _front_camera(D, w, h, f=60.0):
+    # at (0, 0, D) looking down -z: right = +x, down = -y, forward = -z
+    R = np.array([[1, 0, 0], [0, -1, 0], [0, 0, -1]], np.float64)
+    t = -R @ np.array([0.0, 0.0, D])
+    return np.concatenate([R.ravel(), t, [f, f, w / 2, h / 2]]).astype(np.float32)
+
+
+def _texel_points(o, V, F):
+    m = o["face"] >= 0
+    p = (o["bary"][m][:, :, None] * V.astype(np.float64)[F[o["face"][m]]]).sum(1)
+    return m, p
+
+
+def test_render_depth_is_view_distance():
+    V, F = _plane(4, z=0.25)
+    cam = _front_camera(3.0, 32, 32)
+    depth, point, near = oracle.render_views(V, F, cam[None], 32, 32)
+    hit = np.isfinite(depth[0])
+    assert hit.sum() > 100
+    assert np.abs(depth[0][hit] - 2.75).max() < 1e-12
+    assert np.abs(point[0][hit][:, 2] - 0.25).max() < 1e-12
+
+
+def test_face_on_affine_image_closed_form():
+    V, F = _plane(4)
+    w = h = 64
+    D, fx = 3.0, 60.0
+    cam = _front_camera(D, w, h, fx)
+    ii, jj = np.meshgrid(np.arange(w), np.arange(h))
+    img = np.zeros((1, h, w, 4), np.uint8)
+    img[0, ..., 0] = 2 * ii + 40
+    img[0, ..., 1] = 3 * jj + 20
+    img[0, ..., 2] = 128
+    img[0, ..., 3] = 255
+    W = H = 64
+    uv = synth.grid_atlas(len(F), W, H, 2)
+    o = oracle.backproject(V, F, uv, W, H, cam[None], img, np.ones(1, np.float32), alpha=1.0, eps=0.0,
+                           depth_tol=1e-3, edge_tol=1.0)
+    m, p = _texel_points(o, V, F)
+    u = fx * p[:, 0] / D + w / 2
+    v = -fx * p[:, 1] / D + h / 2
+    # away from the plane's projected rim (edge pixels, two pixels wide with the bilinear footprint)
+    margin = 1.0 - 2.5 * D / fx
+    interior = (np.abs(p[:, 0]) < margin) & (np.abs(p[:, 1]) < margin) & (o["flags"][m] == 0)
+    assert interior.sum() > 1000
+    tex = o["texture"][m]
+    assert o["filled"][m][interior].all()
+    assert np.abs(tex[interior, 0] - (2 * (u[interior] - 0.5) + 40) / 255).max() < 1e-9
+    assert np.abs(tex[interior, 1] - (3 * (v[interior] - 0.5) + 20) / 255).max() < 1e-9
+    assert np.abs(tex[interior, 2] - 128 / 255).max() < 1e-12
+    # incidence: cos of the angle between the plane normal (+z) and the direction to the camera
+    I = o["incidence"][0][m]
+    cos = D / np.sqrt(p[:, 0] ** 2 + p[:, 1] ** 2 + D ** 2)
+    assert np.abs(I[interior] - cos[interior]).max() < 1e-12
+
+
+def test_occluded_plane_receives_nothing():
+    Vb, Fb = _plane(4, z=0.0)
+    Vf, Ff = _plane(2, z=0.5, size=0.4)
+    V = np.concatenate([Vb, Vf])
+    F = np.concatenate([Fb, Ff + len(Vb)]).astype(np.int32)
+    w = h = 64
+    cam = _front_camera(3.0, w, h)
+    img = np.full((1, h, w, 4), 200, np.uint8)
+    W = H = 96
+    uv = synth.grid_atlas(len(F), W, H, 2)
+    # the pixel footprint is 0.05 world units here: edge_tol must exceed it (the planes are 0.5 apart)
+    o = oracle.backproject(V, F, uv, W, H, cam[None], img, np.ones(1, np.float32), alpha=1.0, eps=1e-6,
+                           depth_tol=1e-3, edge_tol=0.2)
+    m, p = _texel_points(o, V, F)
+    back = o["face"][m] < len(Fb)
+    # behind the front plane's footprint, seen from the camera (with a margin of a few pixels)
+    proj = p[:, :2] * 3.0 / (3.0 - p[:, 2:3])
+    covered = back & (np.abs(proj).max(1) < 0.4 * 3.0 / 2.5 - 0.05)
+    clear = (back & (np.abs(proj).max(1) > 0.4 * 3.0 / 2.5 + 0.15) & (np.abs(p[:, :2]).max(1) < 1 - 2.5 * 3.0 / 60)
+             & (o["flags"][m] == 0))
+    assert covered.sum() > 50 and clear.sum() > 200
+    assert not o["filled"][m][covered].any()
+    assert o["filled"][m][clear].all()
+
+
+@pytest.mark.parametrize("alpha", [1.0, 4.0, 400.0])
+def test_two_view_blend_closed_form(alpha):
+    # the plane z = 0 seen from cameras at angles a1, a2 in the xz-plane; it
+    # extends past both images (no silhouette, no edge pixels in view)
+    V, F = _plane(8, size=1.5)
+    w = h = 48
+    cams, I_exp = [], []
+    for ang in (10.0, 50.0):
+        a = math.radians(ang)
+        eye = np.array([4 * math.sin(a), 0.0, 4 * math.cos(a)])
+        cams.append(synth.look_at_camera(eye, [0, 0, 0], [0, 1, 0], 30.0, w, h))
+    img = np.zeros((2, h, w, 4), np.uint8)
+    img[0, ..., 0] = 255
+    img[1, ..., 2] = 255
+    img[..., 3] = 255
+    wts = np.array([0.3, 1.0], np.float32)
+    W = H = 128
+    uv = synth.grid_atlas(len(F), W, H, 2)
+    # eps is absolute in the linear domain: at alpha = 400 the weights w I^alpha
+    # are ~1e-60 and any eps > 0 would dominate, so that case takes eps = 0
+    eps = 1e-6 if alpha < 100 else 0.0
+    # depth_tol above the change of depth across one pixel of the oblique view
+    # (the depth test reads the nearest pixel)
+    o = oracle.backproject(V, F, uv, W, H, np.stack(cams), img, wts, alpha=alpha, eps=eps, depth_tol=0.1,
+                           edge_tol=10.0)
+    m, p = _texel_points(o, V, F)
+    ok = (o["flags"][m] == 0) & (np.abs(p[:, :2]).max(1) < 0.5)      # inside both frusta
+    assert ok.sum() > 100
+    C = [np.array([4 * math.sin(math.radians(a)), 0.0, 4 * math.cos(math.radians(a))]) for a in (10.0, 50.0)]
+    cos = np.stack([(c[None] - p)[:, 2] / np.linalg.norm(c[None] - p, axis=1) for c in C])   # normal +z
+    L = np.log(wts.astype(np.float64))[:, None] + alpha * np.log(cos)
+    mx = L.max(0)
+    e = np.exp(L - mx)
+    red = e[0] / (e.sum(0) + eps * np.exp(-mx))
+    blue = e[1] / (e.sum(0) + eps * np.exp(-mx))
+    tex = o["texture"][m]
+    # 1e-6: the cameras are FP32 values, the closed form uses the exact positions
+    assert np.abs(tex[ok, 0] - red[ok]).max() < 1e-6
+    assert np.abs(tex[ok, 2] - blue[ok]).max() < 1e-6
+    if alpha > 100:
+        # the powers underflow; the log-space form still gives the better view's colour
+        clear = ok & (np.abs(cos[0] - cos[1]) > 0.01)
+        assert clear.sum() > 100
+        assert (np.maximum(tex[clear, 0], tex[clear, 2]) > 0.999).all()
+        assert np.array_equal(tex[clear, 0] > 0.5, (np.log(wts[0]) + alpha * np.log(cos[0]))[clear] >
+                              (np.log(wts[1]) + alpha * np.log(cos[1]))[clear])
+
+
+def test_backfacing_behind_camera_and_edges():
+    # the plane's back side faces the camera: incidence 0, nothing filled
+    V, F = _plane(4, flip=True)
+    w = h = 48
+    cam = _front_camera(3.0, w, h)
+    img = np.full((1, h, w, 4), 90, np.uint8)
+    W = H = 64
+    uv = synth.grid_atlas(len(F), W, H, 2)
+    o = oracle.backproject(V, F, uv, W, H, cam[None], img, np.ones(1, np.float32), alpha=1.0, eps=1e-6,
+                           depth_tol=1e-3, edge_tol=0.2)
+    assert not o["filled"].any()
+    # a camera between the plane and ... looking away: every texel behind it
+    Vp, Fp = _plane(4)
+    R = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float64)     # forward = +z, away from the plane
+    t = -R @ np.array([0.0, 0.0, 1.0])
+    cam2 = np.concatenate([R.ravel(), t, [40, 40, w / 2, h / 2]]).astype(np.float32)
+    o = oracle.backproject(Vp, Fp, uv, W, H, cam2[None], img, np.ones(1, np.float32), alpha=1.0, eps=1e-6,
+                           depth_tol=1e-3, edge_tol=0.2)
+    assert not o["filled"].any()
+    # edge pixels: the silhouette of a small plane in front of the camera
+    depth, point, near = oracle.render_views(Vp, Fp, _front_camera(3.0, w, h)[None], w, h)
+    hit = np.isfinite(depth[0])
+    rim = hit & ~(np.roll(hit, 1, 0) & np.roll(hit, -1, 0) & np.roll(hit, 1, 1) & np.roll(hit, -1, 1))
+    o = oracle.backproject(Vp, Fp, uv, W, H, _front_camera(3.0, w, h)[None], img, np.ones(1, np.float32),
+                           alpha=1.0, eps=1e-6, depth_tol=1e-3, edge_tol=0.2, views=(depth, point, near))
+    m, p = _texel_points(o, Vp, Fp)
+    u = np.floor(60 * p[:, 0] / 3.0 + w / 2).astype(int)
+    v = np.floor(-60 * p[:, 1] / 3.0 + h / 2).astype(int)
+    on_rim = rim[v.clip(0, h - 1), u.clip(0, w - 1)]
+    assert on_rim.sum() > 20 and not o["filled"][m][on_rim].any()
