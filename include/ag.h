@@ -393,6 +393,46 @@ AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_verts, const in
 AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_points, float max_dist,
                                    const ag_opts *opts, ag_stream_t stream, float *d_dist, int32_t *d_tri);
 
+/*
+ * UV-space backprojection and incidence blending (Sec. 7.4 of the paper).
+ *
+ * Cameras (host float [16] per view): R (3x3, row-major, world -> camera,
+ * rows = right, down, forward), t (3), fx, fy, cx, cy in pixels.  A point p
+ * has camera coordinates c = R p + t, depth c.z and image position
+ * (fx c.x / c.z + cx, fy c.y / c.z + cy); pixel (i, j) covers
+ * [i, i+1) x [j, j+1).  Cameras are meant to lie outside the mesh's bounding
+ * sphere (a surface behind a camera nearer than the first one in front makes
+ * the pixel a miss).
+ *
+ * ag_render_views - per view and pixel: the camera depth of the first hit of
+ *   the ray through the pixel centre (d_depth [K*h*w] f32, +inf on a miss),
+ *   its world point (d_points, optional [K*h*w*3] f32, NaN on a miss) and
+ *   the edge mask (d_edge, optional [K*h*w] u8: a hit whose 4-neighbour
+ *   misses or lies farther than edge_tol from it).
+ *
+ * ag_backproject - the texture of the low mesh's atlas (the bake's raster)
+ *   from K views: for every ray texel and view, its surface point p and
+ *   smooth normal n; the view counts when c.z > 0, the pixel is inside the
+ *   image, a hit, not an edge pixel, and c.z <= its depth + depth_tol; its
+ *   incidence is I = max(0, n . normalize(C - p)) (C the camera centre) and
+ *   its colour the bilinear sample of the RGBA8 image at (u - 1/2, v - 1/2)
+ *   (clamped, codes / 255).  T = sum_k w_k I^alpha A_k / (sum_k w_k I^alpha
+ *   + eps) over the counting views, evaluated in log space.
+ *   d_images [K*h*w*4] u8, d_depth, d_edge from ag_render_views (device);
+ *   h_weights [K] host, > 0 (the view prior);
+ *   d_texture [H*W*4] f32 out: RGB and 1 where at least one view counts
+ *   (else all 0); d_incidence optional [K*H*W] f32 out.
+ */
+AG_API ag_status ag_render_views(ag_bvh_t h, int32_t n_views, const float *h_cams, int32_t w, int32_t hgt,
+                                 float edge_tol, const ag_opts *opts, ag_stream_t stream, float *d_depth,
+                                 float *d_points, uint8_t *d_edge);
+AG_API ag_status ag_backproject(const float *d_lverts, const float *d_lnormals, const float *d_luv,
+                                const int32_t *d_lfaces, int64_t n_lverts, int64_t n_lfaces, int32_t W, int32_t H,
+                                int32_t n_views, const float *h_cams, const float *h_weights,
+                                const uint8_t *d_images, const float *d_depth, const uint8_t *d_edge, int32_t w,
+                                int32_t hgt, float alpha, float eps, float depth_tol, const ag_opts *opts,
+                                ag_stream_t stream, float *d_texture, float *d_incidence);
+
 AG_API ag_status ag_sync_status(ag_stream_t stream);
 
 /* Message for the last failing call on this thread ("" if none). */

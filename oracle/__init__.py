@@ -86,6 +86,8 @@ def _load():
         lib.or_qem_simplify.restype = _I
         lib.or_render_view.argtypes = [_P, _P, _I64, _P, _P, _I, _I, _D, _P, _P, _P]
         lib.or_render_view.restype = _I
+        lib.or_edge_mask.argtypes = [_P, _P, _I, _I, _D, _P]
+        lib.or_edge_mask.restype = _I
         lib.or_backproject.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P,
                                        _D, _D, _D, _D, _D, _P, _P, _P, _P]
         lib.or_backproject.restype = _I
@@ -459,6 +461,20 @@ def render_views(V, F, cams, w: int, h: int, *, tol_rel: float = 1e-5, bvh: Bvh 
         lib.or_render_view(_p(V), _p(F), len(F), bvh.h, _p(cams[k]), w, h, tol_rel * scale,
                            _p(depth[k]), _p(point[k]), _p(near[k]))
     return depth, point, near
+
+
+def edge_mask(depth, point, edge_tol: float):
+    """Edge pixels [K,h,w] u8 of rendered views (depth [K,h,w], point
+    [K,h,w,3]): a hit with a 4-neighbour that misses or whose world point
+    lies farther than edge_tol from its own."""
+    lib = _load()
+    depth = _c(depth, np.float64)
+    point = _c(point, np.float64)
+    K, h, w = depth.shape
+    edge = np.empty((K, h, w), np.uint8)
+    for k in range(K):
+        lib.or_edge_mask(_p(depth[k]), _p(point[k]), w, h, float(edge_tol), _p(edge[k]))
+    return edge
 
 
 def backproject(lv, lf, luv, W: int, H: int, cams, images, weights, *, alpha: float, eps: float,

@@ -1554,9 +1554,9 @@ double or_qem_place(const double *q, const double *v0, const double *v1, int *si
  *    A texel with no such view stays unfilled (T = 0).
  *  - Exception flags: a texel is flagged when, for some view, u or v lies
  *    within 1e-3 pixel of a pixel boundary or of the image border, z lies
- *    within 1e-5 * scale of the depth limit, or the pixel's ray or one of its
- *    4-neighbours' passes within 1e-5 * scale of a triangle edge (hit, edge
- *    mask and depth there depend on rounding). */
+ *    within 1e-5 * scale of the depth limit, a neighbour distance of the
+ *    pixel lies within 1e-5 * scale of edge_tol, or the pixel or one of its
+ *    4-neighbours is a rounding-dependent render (or_render_view's near). */
 typedef struct { double R[9], t[3], fx, fy, cx, cy; } cam_t;
 
 static cam_t load_cam(const float *c) {
@@ -1580,8 +1580,10 @@ static d3 cam_centre(const cam_t *k) {   /* C = -R^T t */
 }
 
 /* depth [h*w] (camera z of the first hit, +inf on a miss), point [h*w*3]
- * (NaN on a miss), near [h*w] (the pixel's ray passes within tol of a
- * triangle edge), per view */
+ * (NaN on a miss), near [h*w] per view: the pixel's value depends on
+ * rounding: its ray misses but passes within tol of a triangle, or passes
+ * within tol of a triangle 100 tol or more in front of its hit, or (where
+ * the ray can leave the hit's sheet within tol of the hit) behind it */
 int or_render_view(const float *V, const int32_t *F, int64_t nf, void *bvh, const float *camf, int w, int h,
                    double tol, double *depth, double *point, uint8_t *near) {
     cam_t k = load_cam(camf);
@@ -1597,30 +1599,73 @@ int or_render_view(const float *V, const int32_t *F, int64_t nf, void *bvh, cons
                                 k.R[2] * dc.x + k.R[5] * dc.y + k.R[8] * dc.z));
             hit_t hh;
             closest(V, F, nf, b, C, d, 1e30, -1, &hh);
+            /* triangles within tol of the ray, up to the hit */
+            vis_job vj;
+            memset(&vj, 0, sizeof(vj));
+            vj.V = V; vj.F = F; vj.nf = nf; vj.bvh = b; vj.delta = tol;
+            int32_t cl[OR_MAX_CAND], nc = 0;
+            ray_t r = make_ray(C, d);
+            int hit = hh.tri >= 0 && hh.t > 0.0;
+            candidates(&vj, C, d, &r, 1e30, cl, &nc);
             uint8_t nr = 0;
-            if (hh.tri >= 0 && hh.t > 0.0) {
+            if (hit) {
                 d3 X = add(C, scl(d, hh.t));
                 depth[px] = cam_apply(&k, X).z;
                 std3(point, px, X);
+                /* a silhouette: a triangle within tol of the ray clearly in front
+                 * of the hit, or clearly behind it while the ray can leave the
+                 * hit's sheet within tol of the hit: the hit lies within tol of
+                 * an edge of its triangle that no same-facing triangle continues,
+                 * or a triangle near the hit faces the other way.  Across an edge
+                 * that a same-facing triangle continues, rounding only moves the
+                 * hit to that neighbour: depth and point stay. */
                 const int32_t *f = F + 3 * hh.tri;
-                for (int m = 0; m < 3; ++m) {
+                const double sep = 100.0 * tol;
+                d3 nh = cross(sub(ldf(V, f[1]), ldf(V, f[0])), sub(ldf(V, f[2]), ldf(V, f[0])));
+                double sh = dot(d, nh);
+                int leave = 0;
+                for (int m = 0; m < 3 && !leave; ++m) {
                     d3 a = ldf(V, f[m]), e = sub(ldf(V, f[(m + 1) % 3]), a);
-                    double ee = dot(e, e), s = ee > 0 ? dot(sub(X, a), e) / ee : 0.0;
-                    if (s < 0) s = 0;
-                    if (s > 1) s = 1;
-                    if (norm(sub(X, add(a, scl(e, s)))) < tol) nr = 1;
+                    double ee = dot(e, e), sp = ee > 0 ? dot(sub(X, a), e) / ee : 0.0;
+                    if (sp < 0) sp = 0;
+                    if (sp > 1) sp = 1;
+                    if (!(norm(sub(X, add(a, scl(e, sp)))) < tol)) continue;
+                    int cont = 0;
+                    for (int q = 0; q < nc && q < OR_MAX_CAND; ++q) {
+                        const int32_t *g = F + 3 * cl[q];
+                        if (cl[q] == hh.tri) continue;
+                        int ha = 0, hb = 0;
+                        for (int z = 0; z < 3; ++z) {
+                            ha |= g[z] == f[m];
+                            hb |= g[z] == f[(m + 1) % 3];
+                        }
+                        if (!(ha && hb)) continue;
+                        d3 ng = cross(sub(ldf(V, g[1]), ldf(V, g[0])), sub(ldf(V, g[2]), ldf(V, g[0])));
+                        if (dot(d, ng) * sh > 0) cont = 1;
+                    }
+                    if (!cont) leave = 1;
                 }
+                for (int m = 0; m < nc && m < OR_MAX_CAND; ++m) {
+                    double tc;
+                    line_tri_dist(V, F, cl[m], C, d, &r, &tc);
+                    if (tc < hh.t - sep) nr = 1;
+                    if (fabs(tc - hh.t) <= sep) {
+                        const int32_t *g = F + 3 * cl[m];
+                        d3 ng = cross(sub(ldf(V, g[1]), ldf(V, g[0])), sub(ldf(V, g[2]), ldf(V, g[0])));
+                        if (!(dot(d, ng) * sh > 0)) leave = 1;
+                    }
+                }
+                if (leave)
+                    for (int m = 0; m < nc && m < OR_MAX_CAND; ++m) {
+                        double tc;
+                        line_tri_dist(V, F, cl[m], C, d, &r, &tc);
+                        if (tc > hh.t + sep) nr = 1;
+                    }
+                if (nc > OR_MAX_CAND) nr = 1;
             } else {
                 depth[px] = INFINITY;
                 std3(point, px, mk(NAN, NAN, NAN));
-                /* a miss near the silhouette */
-                vis_job vj;
-                memset(&vj, 0, sizeof(vj));
-                vj.V = V; vj.F = F; vj.nf = nf; vj.bvh = b; vj.delta = tol;
-                int32_t cl[OR_MAX_CAND], nc = 0;
-                ray_t r = make_ray(C, d);
-                candidates(&vj, C, d, &r, 1e30, cl, &nc);
-                if (nc > 0) nr = 1;
+                if (nc > 0) nr = 1;   /* a miss near the silhouette */
             }
             near[px] = nr;
         }
@@ -1645,17 +1690,33 @@ static double bilinear(const uint8_t *img, int w, int h, int ch, double x, doubl
     return acc;
 }
 
-static int is_edge(const double *depth, const double *point, int w, int h, int i, int j, double edge_tol) {
+/* edge pixel test; *amb is set when a neighbour distance lies within
+ * amb_tol of edge_tol (the decision is a rounding decision there) */
+static int is_edge(const double *depth, const double *point, int w, int h, int i, int j, double edge_tol,
+                   double amb_tol, int *amb) {
     int64_t px = (int64_t)j * w + i;
     if (!(depth[px] < INFINITY)) return 0;
     const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+    int e = 0;
     for (int n = 0; n < 4; ++n) {
         int ii = i + di[n], jj = j + dj[n];
         if (ii < 0 || jj < 0 || ii >= w || jj >= h) continue;
         int64_t q = (int64_t)jj * w + ii;
-        if (!(depth[q] < INFINITY)) return 1;
-        if (norm(sub(ldd(point, q), ldd(point, px))) > edge_tol) return 1;
+        if (!(depth[q] < INFINITY)) { e = 1; continue; }
+        double dist = norm(sub(ldd(point, q), ldd(point, px)));
+        if (fabs(dist - edge_tol) < amb_tol) *amb = 1;
+        if (dist > edge_tol) e = 1;
     }
+    return e;
+}
+
+/* edge [h*w]: the edge pixel rule above applied to one rendered view */
+int or_edge_mask(const double *depth, const double *point, int w, int h, double edge_tol, uint8_t *edge) {
+    for (int j = 0; j < h; ++j)
+        for (int i = 0; i < w; ++i) {
+            int amb = 0;
+            edge[(int64_t)j * w + i] = (uint8_t)is_edge(depth, point, w, h, i, j, edge_tol, 0.0, &amb);
+        }
     return 0;
 }
 
@@ -1706,7 +1767,10 @@ int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf,
                 }
             }
             if (!(dk[px] < INFINITY)) continue;
-            if (is_edge(dk, pk, iw, ih, i, j, edge_tol)) continue;
+            int amb = 0;
+            int edge = is_edge(dk, pk, iw, ih, i, j, edge_tol, 1e-5 * scale, &amb);
+            if (amb) fl = 1;
+            if (edge) continue;
             if (fabs(q.z - (dk[px] + depth_tol)) < 1e-5 * scale) fl = 1;
             if (q.z > dk[px] + depth_tol) continue;
             d3 C = cam_centre(&c);

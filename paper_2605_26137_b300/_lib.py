@@ -41,7 +41,7 @@ EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_
            "ag_batch_plan_create", "ag_batch_plan_launch", "ag_batch_plan_free", "ag_bake_backward",
            "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc",
            "ag_autotune", "ag_visibility", "ag_exterior_fill", "ag_qem_simplify",
-           "ag_point_distance")
+           "ag_point_distance", "ag_render_views", "ag_backproject")
 
 
 class AgOpts(ctypes.Structure):
@@ -129,6 +129,13 @@ def load():
         lib.ag_point_distance.argtypes = [c_void_p, c_void_p, c_int64, c_float, POINTER(AgOpts), c_void_p, c_void_p,
                                           c_void_p]
         lib.ag_point_distance.restype = S
+        lib.ag_render_views.argtypes = [c_void_p, c_int32, c_void_p, c_int32, c_int32, c_float, POINTER(AgOpts),
+                                        c_void_p, c_void_p, c_void_p, c_void_p]
+        lib.ag_render_views.restype = S
+        lib.ag_backproject.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
+                                       c_int32, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                       c_float, c_float, c_float, POINTER(AgOpts), c_void_p, c_void_p, c_void_p]
+        lib.ag_backproject.restype = S
         lib.ag_qem_simplify.restype = S
         lib.ag_sync_status.argtypes = [c_void_p]
         lib.ag_sync_status.restype = S

@@ -481,6 +481,83 @@ AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_
     return AG_OK;
 }
 
+AG_API ag_status ag_render_views(ag_bvh_t h, int32_t n_views, const float *h_cams, int32_t w, int32_t hgt,
+                                 float edge_tol, const ag_opts *opts, ag_stream_t stream, float *d_depth,
+                                 float *d_points, uint8_t *d_edge) {
+    g_err.clear();
+    ag_status st = check_handle(h);
+    if (st) return st;
+    if (n_views < 1 || n_views > 4096) return set_error(AG_ERR_INVALID_ARG, "n_views must be in 1..4096");
+    if (w < 1 || hgt < 1 || w > 16384 || hgt > 16384) return set_error(AG_ERR_INVALID_ARG, "w and h must be in 1..16384");
+    if (!h_cams || !d_depth) return set_error(AG_ERR_INVALID_ARG, "h_cams and d_depth must be non-NULL");
+    if (!(edge_tol > 0.f) || !(edge_tol < 3.0e38f)) return set_error(AG_ERR_INVALID_ARG, "edge_tol must be finite and > 0");
+    ag_opts o = resolve_opts(opts);
+    if ((st = check_opts(o))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *status = device_status_word(h->device);
+    if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    Scratch sc(s, h->device);
+    void *cams;
+    AG_CUDA(sc.alloc(&cams, render_scratch_bytes(n_views)));
+    float *points = d_points;
+    if (!points && d_edge) AG_CUDA(sc.alloc((void **)&points, sizeof(float) * 3 * (size_t)n_views * w * hgt));
+    TraceLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.job0.nodes = h->nodes;
+    L.job0.tris = h->tris;
+    L.job0.tri_ids = h->tri_ids;
+    for (int k = 0; k < 3; ++k) L.job0.scene_abs = fmaxf(L.job0.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+    L.status = status;
+    L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
+    L.layout = h->layout;
+    AG_CUDA(launch_render_views(L, h_cams, n_views, w, hgt, edge_tol, d_depth, points, d_edge, cams, s));
+    return AG_OK;
+}
+
+AG_API ag_status ag_backproject(const float *d_lverts, const float *d_lnormals, const float *d_luv,
+                                const int32_t *d_lfaces, int64_t n_lverts, int64_t n_lfaces, int32_t W, int32_t H,
+                                int32_t n_views, const float *h_cams, const float *h_weights, const uint8_t *d_images,
+                                const float *d_depth, const uint8_t *d_edge, int32_t w, int32_t hgt, float alpha,
+                                float eps, float depth_tol, const ag_opts *opts, ag_stream_t stream, float *d_texture,
+                                float *d_incidence) {
+    g_err.clear();
+    ag_status st;
+    if ((st = check_low(d_lverts, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, 1.0f))) return st;
+    if (n_views < 1 || n_views > 4096) return set_error(AG_ERR_INVALID_ARG, "n_views must be in 1..4096");
+    if (w < 1 || hgt < 1 || w > 16384 || hgt > 16384) return set_error(AG_ERR_INVALID_ARG, "w and h must be in 1..16384");
+    if (!h_cams || !h_weights || !d_images || !d_depth || !d_edge || !d_texture)
+        return set_error(AG_ERR_INVALID_ARG, "cameras, weights, images, depth, edge and texture must be non-NULL");
+    if (!(alpha >= 0.f) || !(alpha < 3.0e38f) || !(eps >= 0.f) || !(eps < 3.0e38f) || !(depth_tol >= 0.f) ||
+        !(depth_tol < 3.0e38f))
+        return set_error(AG_ERR_INVALID_ARG, "alpha, eps and depth_tol must be finite and >= 0");
+    std::vector<float> logw((size_t)n_views);
+    for (int k = 0; k < n_views; ++k) {
+        if (!(h_weights[k] > 0.f) || !(h_weights[k] < 3.0e38f))
+            return set_error(AG_ERR_INVALID_ARG, "view weights must be finite and > 0");
+        logw[(size_t)k] = logf(h_weights[k]);
+    }
+    ag_opts o = resolve_opts(opts);
+    if ((st = check_opts(o))) return st;
+    int dev = 0;
+    AG_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *status = device_status_word(dev);
+    if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    Scratch sc(s, dev);
+    AssetScratch a;
+    memset(&a, 0, sizeof(a));
+    if ((st = alloc_asset(sc, n_lverts, n_lfaces, W, H, true, a))) return st;
+    void *scr;
+    AG_CUDA(sc.alloc(&scr, backproject_scratch_bytes(n_views)));
+    if ((st = run_prep(d_lverts, d_lnormals, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, o.ray_tile, nullptr, status, a,
+                       s)))
+        return st;
+    AG_CUDA(launch_backproject(a.lpos, a.lnrm, a.lface, a.rays, a.n_rays, W, H, h_cams, logw.data(), n_views,
+                               d_images, d_depth, d_edge, w, hgt, alpha, eps, depth_tol,
+                               reinterpret_cast<float4 *>(d_texture), d_incidence, scr, s));
+    return AG_OK;   // the pageable copies of the cameras and log-weights were staged before returning
+}
+
 AG_API ag_status ag_sync_status(ag_stream_t stream) {
     g_err.clear();
     cudaStream_t s = (cudaStream_t)stream;

@@ -381,6 +381,52 @@ def point_distance(bvh: Bvh, points, max_dist: float, *, tri: bool = False, stre
     return (d, t) if tri else d
 
 
+# ----------------------------------------------------------------- UV-space backprojection (Sec. 7.4)
+
+def render_views(bvh: Bvh, cams, w: int, h: int, *, edge_tol: float, points: bool = True, stream=None):
+    """Depth [K,h,w] f32 (+inf on a miss), world points [K,h,w,3] (NaN on a
+    miss) and edge mask [K,h,w] u8 of K pinhole views (cams: host numpy
+    [K,16] f32) of the mesh ``bvh`` was built on."""
+    import numpy as np
+    lib = _lib.load()
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    K = cams.shape[0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    depth = torch.empty((K, h, w), dtype=torch.float32, device=dev)
+    pts = torch.empty((K, h, w, 3), dtype=torch.float32, device=dev) if points else None
+    edge = torch.empty((K, h, w), dtype=torch.uint8, device=dev)
+    check(lib.ag_render_views(bvh.handle, K, cams.ctypes.data, w, h, float(edge_tol), None, _stream(stream),
+                              depth.data_ptr(), _ptr(pts), edge.data_ptr()))
+    return depth, pts, edge
+
+
+def backproject(low_verts, low_faces, low_uv, W: int, H: int, cams, weights, images, depth, edge, *,
+                alpha: float, eps: float, depth_tol: float, low_normals=None, incidence: bool = False,
+                ray_tile="8x8", stream=None):
+    """Blended texture [H,W,4] f32 (RGB, 1 where filled) of K views (images
+    [K,h,w,4] u8, depth / edge from render_views, cams [K,16] and weights [K]
+    host numpy) on the low mesh's atlas; with ``incidence`` also [K,H,W]."""
+    import numpy as np
+    lib = _lib.load()
+    _check_low(low_verts, low_faces, low_uv, low_normals)
+    _need(images, "images", torch.uint8, (4,))
+    _need(depth, "depth", torch.float32)
+    _need(edge, "edge", torch.uint8)
+    cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
+    weights = np.ascontiguousarray(weights, dtype=np.float32)
+    K, h, w = images.shape[0], images.shape[1], images.shape[2]
+    if cams.shape[0] != K or weights.shape[0] != K or tuple(depth.shape) != (K, h, w) or tuple(edge.shape) != (K, h, w):
+        raise ValueError("cams, weights, images, depth and edge must describe the same K views")
+    tex = torch.empty((H, W, 4), dtype=torch.float32, device=low_verts.device)
+    inc = torch.empty((K, H, W), dtype=torch.float32, device=low_verts.device) if incidence else None
+    o = _opts(ray_tile=ray_tile)
+    check(lib.ag_backproject(low_verts.data_ptr(), _ptr(low_normals), low_uv.data_ptr(), low_faces.data_ptr(),
+                             low_verts.shape[0], low_faces.shape[0], W, H, K, cams.ctypes.data, weights.ctypes.data,
+                             images.data_ptr(), depth.data_ptr(), edge.data_ptr(), w, h, float(alpha), float(eps),
+                             float(depth_tol), ctypes.byref(o), _stream(stream), tex.data_ptr(), _ptr(inc)))
+    return (tex, inc) if incidence else tex
+
+
 def sync_status(stream=None) -> None:
     """Synchronise and raise AgError if a device-side limit was hit."""
     check(_lib.load().ag_sync_status(_stream(stream)))

@@ -1,0 +1,190 @@
+"""GPU parity of UV-space backprojection and incidence blending (Sec. 7.4)
+against the FP64 oracle through the C ABI (ag_render_views, ag_backproject).
+
+The generated views are stand-ins made from the oracle's own renders (a smooth
+colour field at each pixel's surface point), so no input comes from the CUDA
+path.  The kernel renders its own depth buffers and edge masks.  Where the
+oracle flags a texel (a pixel boundary, the depth limit, an edge decision or a
+silhouette within rounding of the decision), the texel is not compared."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_26137_b300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL_TEX = 1e-4
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_both(lv, lf, uv, W, H, cams, weights, w, h, *, alpha, eps, depth_tol, edge_tol):
+    import paper_2605_26137_b300 as pb
+    depth_o, point_o, near_o = oracle.render_views(lv, lf, cams, w, h)
+    images = synth.view_images(point_o)
+    o = oracle.backproject(lv, lf, uv, W, H, cams, images, weights, alpha=alpha, eps=eps, depth_tol=depth_tol,
+                           edge_tol=edge_tol, views=(depth_o, point_o, near_o))
+    bvh = pb.Bvh(_t(lv), _t(lf))
+    depth, pts, edge = pb.render_views(bvh, cams, w, h, edge_tol=edge_tol)
+    tex, inc = pb.backproject(_t(lv), _t(lf), _t(uv), W, H, cams, weights, _t(images), depth, edge, alpha=alpha,
+                              eps=eps, depth_tol=depth_tol, incidence=True)
+    pb.sync_status()
+    bvh.free()
+    g = dict(depth=depth.cpu().numpy(), points=pts.cpu().numpy(), edge=edge.cpu().numpy(),
+             texture=tex.cpu().numpy(), incidence=inc.cpu().numpy())
+    return g, o
+
+
+def check_render(g, o, scale):
+    near = o["near"].astype(bool)
+    hit_o = np.isfinite(o["depth"])
+    hit_g = np.isfinite(g["depth"])
+    assert np.array_equal(hit_g[~near], hit_o[~near])
+    both = hit_o & hit_g & ~near
+    assert np.abs(g["depth"][both] - o["depth"][both]).max() <= 1e-5 * scale
+    assert np.abs(g["points"][both] - o["point"][both]).max() <= 1e-5 * scale
+
+
+def check_texture(g, o):
+    ray = o["face"] >= 0
+    ok = ray & (o["flags"] == 0)
+    filled_g = g["texture"][..., 3] > 0.5
+    assert np.array_equal(filled_g[ok], o["filled"][ok].astype(bool))
+    both = ok & filled_g
+    err = np.abs(g["texture"][..., :3][both] - o["texture"][both])
+    assert err.max() <= TOL_TEX, err.max()
+    inc = np.abs(g["incidence"][:, ok] - o["incidence"][:, ok])
+    assert inc.max() <= 1e-5
+    # outside the ray texels nothing is written
+    assert not g["texture"][~ray].any()
+    return float(ok.sum() / ray.sum())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_paper_views_tiny_asset(seed):
+    a = synth.tiny_asset(seed)
+    lv, lf = a.low_v, a.low_f
+    c = (lv.max(0) + lv.min(0)) / 2
+    r = float(np.linalg.norm(lv.max(0) - lv.min(0)) / 2)
+    cams, weights, _ = synth.paper_cameras(c, r, 96, 80)
+    scale = 2 * r
+    g, o = run_both(lv, lf, a.low_uv, a.W, a.H, cams, weights, 96, 80, alpha=6.0, eps=1e-6, depth_tol=0.02 * scale,
+                    edge_tol=0.05 * scale)
+    check_render(g, o, scale)
+    frac = check_texture(g, o)
+    assert frac > 0.85
+    assert o["filled"][o["face"] >= 0].mean() > 0.6
+
+
+def test_sdf_asset_large_alpha_and_ragged_sizes():
+    """A marching-grid low mesh (~6k faces), a 512 x 384 atlas, views of
+    ragged sizes, alpha = 40 (the log-space blend)."""
+    a = synth.sdf_asset(7, 60_000, 6_000, 512, 384, n_prims=16)
+    lv, lf = a.low_v, a.low_f
+    c = (lv.max(0) + lv.min(0)) / 2
+    r = float(np.linalg.norm(lv.max(0) - lv.min(0)) / 2)
+    # views dense enough that a pixel covers few texels (a flagged pixel flags them all)
+    cams, weights, _ = synth.paper_cameras(c, r, 509, 383)
+    scale = 2 * r
+    g, o = run_both(lv, lf, a.low_uv, a.W, a.H, cams, weights, 509, 383, alpha=40.0, eps=1e-30,
+                    depth_tol=0.01 * scale, edge_tol=0.03 * scale)
+    check_render(g, o, scale)
+    # a pixel whose render depends on rounding flags every texel that lands on
+    # it or beside it in any view; on this marching-grid mesh (slivers whose
+    # texel cells are as large as any other face's) that is about a fifth
+    assert check_texture(g, o) > 0.7
+
+
+@pytest.mark.parametrize("alpha,eps", [(6.0, 1e-6), (40.0, 1e-30)])
+def test_backproject_on_oracle_views(alpha, eps):
+    """The blend step alone: the kernel reads the oracle's depth buffers (as
+    FP32) and edge masks, so a pixel whose render depends on rounding cannot
+    change the comparison; only texels within rounding of a pixel boundary,
+    the depth limit or the image border are skipped."""
+    import paper_2605_26137_b300 as pb
+    a = synth.sdf_asset(3, 40_000, 4_000, 384, 256, n_prims=12)
+    lv, lf = a.low_v, a.low_f
+    c = (lv.max(0) + lv.min(0)) / 2
+    r = float(np.linalg.norm(lv.max(0) - lv.min(0)) / 2)
+    w, h = 333, 250
+    cams, weights, _ = synth.paper_cameras(c, r, w, h)
+    scale, edge_tol = 2 * r, 0.03 * 2 * r
+    depth_o, point_o, near_o = oracle.render_views(lv, lf, cams, w, h)
+    edge_o = oracle.edge_mask(depth_o, point_o, edge_tol)
+    images = synth.view_images(point_o)
+    o = oracle.backproject(lv, lf, a.low_uv, a.W, a.H, cams, images, weights, alpha=alpha, eps=eps,
+                           depth_tol=0.01 * scale, edge_tol=edge_tol, views=(depth_o, point_o, np.zeros_like(near_o)))
+    tex, inc = pb.backproject(_t(lv), _t(lf), _t(a.low_uv), a.W, a.H, cams, weights, _t(images),
+                              _t(depth_o.astype(np.float32)), _t(edge_o), alpha=alpha, eps=eps,
+                              depth_tol=0.01 * scale, incidence=True)
+    pb.sync_status()
+    g = dict(texture=tex.cpu().numpy(), incidence=inc.cpu().numpy())
+    assert check_texture(g, o) > 0.93
+    assert o["filled"][o["face"] >= 0].mean() > 0.8
+
+
+def test_face_on_affine_image_closed_form():
+    """The oracle's closed form, through the kernel: a plane seen face-on
+    through an image whose codes are affine in the pixel index."""
+    import paper_2605_26137_b300 as pb
+    n = 4
+    xs = np.linspace(-1, 1, n + 1)
+    X, Y = np.meshgrid(xs, xs)
+    V = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], -1).astype(np.float32)
+    F = np.asarray([(j * (n + 1) + i, j * (n + 1) + i + 1, j * (n + 1) + i + n + 2) for j in range(n) for i in range(n)] +
+                   [(j * (n + 1) + i, j * (n + 1) + i + n + 2, j * (n + 1) + i + n + 1) for j in range(n) for i in range(n)],
+                   np.int32)
+    w = h = 64
+    D, f = 3.0, 60.0
+    R = np.array([[1, 0, 0], [0, -1, 0], [0, 0, -1]], np.float64)
+    cam = np.concatenate([R.ravel(), -R @ [0, 0, D], [f, f, w / 2, h / 2]]).astype(np.float32)[None]
+    ii, jj = np.meshgrid(np.arange(w), np.arange(h))
+    img = np.zeros((1, h, w, 4), np.uint8)
+    img[0, ..., 0] = 2 * ii + 40
+    img[0, ..., 1] = 3 * jj + 20
+    img[0, ..., 3] = 255
+    W = H = 64
+    uv = synth.grid_atlas(len(F), W, H, 2)
+    bvh = pb.Bvh(_t(V), _t(F))
+    depth, _, edge = pb.render_views(bvh, cam, w, h, edge_tol=1.0)
+    tex = pb.backproject(_t(V), _t(F), _t(uv), W, H, cam, np.ones(1, np.float32), _t(img), depth, edge, alpha=1.0,
+                         eps=0.0, depth_tol=1e-3)
+    pb.sync_status()
+    tex = tex.cpu().numpy()
+    face, bary, _ = oracle.raster(uv, W, H)
+    m = face >= 0
+    p = (bary[m][:, :, None] * V.astype(np.float64)[F[face[m]]]).sum(1)
+    u = f * p[:, 0] / D + w / 2
+    v = -f * p[:, 1] / D + h / 2
+    margin = 1.0 - 2.5 * D / f
+    inner = (np.abs(p[:, 0]) < margin) & (np.abs(p[:, 1]) < margin) & (np.abs(u - np.round(u)) > 1e-3) & \
+        (np.abs(v - np.round(v)) > 1e-3)
+    t = tex[m]
+    assert inner.sum() > 1000 and (t[inner, 3] == 1).all()
+    assert np.abs(t[inner, 0] - (2 * (u[inner] - 0.5) + 40) / 255).max() < 2e-5
+    assert np.abs(t[inner, 1] - (3 * (v[inner] - 0.5) + 20) / 255).max() < 2e-5
+    bvh.free()
+
+
+def test_argument_errors():
+    import paper_2605_26137_b300 as pb
+    a = synth.tiny_asset(0)
+    bvh = pb.Bvh(_t(a.low_v), _t(a.low_f))
+    cams, weights, _ = synth.paper_cameras(np.zeros(3), 1.0, 32, 32)
+    depth, _, edge = pb.render_views(bvh, cams, 32, 32, edge_tol=0.1)
+    imgs = torch.zeros((10, 32, 32, 4), dtype=torch.uint8, device="cuda")
+    bad = weights.copy()
+    bad[3] = 0.0
+    with pytest.raises(pb.AgError):
+        pb.backproject(_t(a.low_v), _t(a.low_f), _t(a.low_uv), a.W, a.H, cams, bad, imgs, depth, edge, alpha=2.0,
+                       eps=1e-6, depth_tol=0.01)
+    with pytest.raises(pb.AgError):
+        pb.render_views(bvh, cams, 0, 32, edge_tol=0.1)
+    with pytest.raises(ValueError):
+        pb.backproject(_t(a.low_v), _t(a.low_f), _t(a.low_uv), a.W, a.H, cams[:5], weights, imgs, depth, edge,
+                       alpha=2.0, eps=1e-6, depth_tol=0.01)
+    bvh.free()

@@ -188,6 +188,8 @@ def test_backfacing_behind_camera_and_edges():
     depth, point, near = oracle.render_views(Vp, Fp, _front_camera(3.0, w, h)[None], w, h)
     hit = np.isfinite(depth[0])
     rim = hit & ~(np.roll(hit, 1, 0) & np.roll(hit, -1, 0) & np.roll(hit, 1, 1) & np.roll(hit, -1, 1))
+    # one flat sheet well inside the image: the edge pixels are exactly the hits beside a miss
+    assert np.array_equal(oracle.edge_mask(depth, point, 0.2)[0].astype(bool), rim)
     o = oracle.backproject(Vp, Fp, uv, W, H, _front_camera(3.0, w, h)[None], img, np.ones(1, np.float32),
                            alpha=1.0, eps=1e-6, depth_tol=1e-3, edge_tol=0.2, views=(depth, point, near))
     m, p = _texel_points(o, Vp, Fp)
