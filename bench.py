@@ -74,7 +74,7 @@ def parse():
     p.add_argument("--profile", action="store_true",
                    help="profiling case for ncu: one BVH build and --steps plain bakes, nothing else")
     p.add_argument("--layout", default="q8", choices=["q8", "f32"])
-    p.add_argument("--query", default="ray", choices=["ray", "closest", "hidden", "qem"],
+    p.add_argument("--query", default="ray", choices=["ray", "closest", "hidden", "qem", "backproject"],
                    help="--profile: the ray or closest-point bake, the hidden-face visibility pass or QEM")
     p.add_argument("--error-sample", type=float, default=20000,
                    help="ray texels compared with the oracle per layout (a value < 1 is a fraction of them)")
@@ -83,6 +83,7 @@ def parse():
     p.add_argument("--hidden-res", type=int, default=1024, help="hidden-face removal: image resolution")
     p.add_argument("--hidden-faces", type=int, default=22000, help="hidden-face removal: mesh faces")
     p.add_argument("--qem-faces", type=int, default=1_000_000, help="QEM simplification: input faces")
+    p.add_argument("--bp-res", type=int, default=1024, help="backprojection: view resolution (ten views)")
     return p.parse_args()
 
 
@@ -102,9 +103,11 @@ def peaks():
 
 
 KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh", "rays.cuh"), "closest": ("closest.cu", "traverse.cuh"),
-                  "visibility": ("hidden.cu", "traverse.cuh", "rays.cuh")}
+                  "visibility": ("hidden.cu", "traverse.cuh", "rays.cuh"),
+                  "backproject": ("backproject.cu", "rays.cuh", "traverse.cuh")}
 PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_2048_2M.md",
-                 "visibility": "visibility_kernel_22k_512x1024.md"}
+                 "visibility": "visibility_kernel_22k_512x1024.md",
+                 "backproject": "backproject_kernels_10x1024_2048.md"}
 
 
 def trace_source_hash(kernel: str = "trace"):
@@ -263,6 +266,27 @@ def run_profile_qem(args):
                       "rounds": rounds}))
 
 
+def run_profile_backproject(args):
+    """Few launches of view rendering and backprojection onto the asset's
+    low mesh and atlas."""
+    import torch
+    import paper_2605_26137_b300 as pb
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    a = make_asset(args, dev)
+    _, _, lv, lf, uv = to_dev(a, torch)
+    W = H = args.res
+    lbvh, cams, weights, images, w, h, tol = backproject_setup(args, pb, torch, a, lv, lf, dev)
+    for _ in range(args.steps):
+        d, _, e = pb.render_views(lbvh, cams, w, h, edge_tol=tol["edge_tol"], points=False)
+        pb.backproject(lv, lf, uv, W, H, cams, weights, images, d, e, alpha=6.0, eps=1e-6,
+                       depth_tol=tol["depth_tol"])
+    pb.sync_status()
+    lbvh.free()
+    print(json.dumps({"profile_case": "backprojection", "low_faces": int(len(a.low_f)), "atlas": W,
+                      "views": len(cams), "view_res": w, "kernel_source_hash": trace_source_hash("backproject")}))
+
+
 def run_profile_hidden(args):
     """Few launches of the visibility pass on the hidden-face workload."""
     import torch
@@ -385,6 +409,8 @@ def main():
             run_profile_hidden(args)
         elif args.query == "qem":
             run_profile_qem(args)
+        elif args.query == "backproject":
+            run_profile_backproject(args)
         else:
             run_profile(args)
         return
@@ -584,6 +610,7 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     res["closest_point"] = closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush)
     res["hidden_face_removal"] = hidden_leg(args, pb, torch, dev, flush)
     res["qem_simplification"] = qem_leg(args, pb, torch, dev)
+    res["backprojection"] = backproject_leg(args, pb, torch, a, lv, lf, uv, W, H, dev, flush)
     if args.batch_assets > 0:
         res["batch"] = batch_leg(args, pb, torch, dev, flush)
     return res
@@ -686,6 +713,72 @@ def hidden_leg(args, pb, torch, dev, flush):
             "outer_faces_removed": int((~extn[~inner]).sum()),
             "traffic": recorded_traffic("q8", nres, int(len(F)), "visibility"),
             "paper_kernel_s": 0.179}
+
+
+def backproject_setup(args, pb, torch, a, lv, lf, dev):
+    """The paper's ten views (Sec. 7.4) of the low mesh at bp_res^2, and
+    their RGBA8 images: a smooth colour field at each rendered surface point
+    (the stand-in for the generated views)."""
+    from paper_2605_26137_b300 import synth
+    V = a.low_v.astype(np.float64)
+    c = (V.max(0) + V.min(0)) / 2
+    r = float(np.linalg.norm(V.max(0) - V.min(0)) / 2)
+    w = h = args.bp_res
+    cams, weights, _ = synth.paper_cameras(c, r, w, h)
+    diam = 2 * r
+    tol = {"edge_tol": 0.01 * diam, "depth_tol": 0.005 * diam}
+    lbvh = pb.Bvh(lv, lf)
+    _, pts, _ = pb.render_views(lbvh, cams, w, h, edge_tol=tol["edge_tol"])
+    pb.sync_status()
+    images = torch.from_numpy(synth.view_images(pts.cpu().numpy())).to(dev)
+    return lbvh, cams, weights, images, w, h, tol
+
+
+def backproject_leg(args, pb, torch, a, lv, lf, uv, W, H, dev, flush):
+    """UV-space backprojection and incidence blending (Sec. 7.4) of the
+    paper's ten views at bp_res^2 onto the baked asset's low mesh and atlas:
+    depth/point/edge rendering of the views, then per-texel projection, depth
+    test, incidence and the log-space blend (alpha = 6)."""
+    lbvh, cams, weights, images, w, h, tol = backproject_setup(args, pb, torch, a, lv, lf, dev)
+    K = len(cams)
+    depth = torch.empty((K, h, w), dtype=torch.float32, device=dev)
+    edge = torch.empty((K, h, w), dtype=torch.uint8, device=dev)
+    steps = max(3, args.steps // 2)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record()
+        d, _, e = pb.render_views(lbvh, cams, w, h, edge_tol=tol["edge_tol"], points=False)
+        if ev is not None:
+            ev[1].record()
+        tex = pb.backproject(lv, lf, uv, W, H, cams, weights, images, d, e, alpha=6.0, eps=1e-6,
+                             depth_tol=tol["depth_tol"])
+        if ev is not None:
+            ev[2].record()
+        return tex
+
+    for _ in range(3):
+        tex = step()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        tex = step(ev[i])
+    torch.cuda.synchronize()
+    pb.sync_status()
+    render_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    blend_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    t = tex.cpu().numpy()
+    info = lbvh.info()
+    lbvh.free()
+    filled = int((t[..., 3] > 0.5).sum())
+    return {"views": K, "view_res": [w, h], "atlas": [W, H], "low_faces": int(len(a.low_f)),
+            "alpha": 6.0, "tolerances": tol, "low_bvh_build_ms": info["build_ms"],
+            "render_ms": render_ms, "blend_ms": blend_ms, "total_ms": render_ms + blend_ms,
+            "texels_filled": filled, "mtexels_s_blend": W * H / blend_ms / 1e3,
+            "view_rays_s_render": K * w * h / render_ms / 1e3 / 1e3,
+            "note": "blend_ms is the whole ag_backproject call (raster, vertex normals, blend); render_ms the "
+                    "ag_render_views call (depth + edge buffers, points not written)"}
 
 
 def closest_leg(args, pb, torch, a, bvh, lv, lf, uv, W, H, dev, flush):
