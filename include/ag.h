@@ -84,6 +84,16 @@ enum { AG_SCHED_AUTO = -1, AG_SCHED_BATCH = 0, AG_SCHED_REFILL = 1 };
  *                     ag_bake_backward supports the ray query only. */
 enum { AG_QUERY_RAY = 0, AG_QUERY_CLOSEST = 1 };
 
+/* View rendering (ag_opts.render).  Both give every pixel the first hit of
+ * the ray through its centre under the watertight ray-triangle test:
+ *  AG_RENDER_RASTER - a z-buffer pass proposes each pixel's triangle, the ray
+ *                     test confirms it, and only a pixel whose proposal the
+ *                     test rejects (a centre within rounding of an edge) is
+ *                     traced through the BVH; a view in which a triangle
+ *                     reaches the camera plane is traced whole.
+ *  AG_RENDER_TRACE  - every pixel traced through the BVH. */
+enum { AG_RENDER_RASTER = 0, AG_RENDER_TRACE = 1 };
+
 /* Options.  Zero-initialise then call ag_opts_default, or pass NULL for the
  * defaults. */
 typedef struct {
@@ -102,7 +112,8 @@ typedef struct {
     int32_t ray_tile;    /* ag_bake*: atlas tile shape that orders the ray list, AG_TILE_*
                             (a warp's 32 rays come from one tile; default AG_TILE_8x8) */
     int32_t query;       /* ag_bake*, ag_autotune: AG_QUERY_RAY (0, default) or AG_QUERY_CLOSEST */
-    int32_t reserved[6];
+    int32_t render;      /* ag_render_views: AG_RENDER_RASTER (0, default) or AG_RENDER_TRACE */
+    int32_t reserved[5];
 } ag_opts;
 
 /* Optional extra outputs of ag_bake (any member may be NULL). */

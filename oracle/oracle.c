@@ -1535,7 +1535,8 @@ double or_qem_place(const double *q, const double *v0, const double *v1, int *si
  * image position u = fx c.x / z + cx, v = fy c.y / z + cy; pixel (i, j)
  * covers [i, i+1) x [j, j+1).
  *  - Depth buffer: for every pixel, the first hit of the ray through its
- *    centre against the mesh (section 4's closest-hit rules), its depth z and
+ *    centre in front of the camera (the smallest t > 0 under section 4's
+ *    intersection test, equal t: the lower triangle id), its depth z and
  *    world point; +inf / NaN where the ray misses.  A pixel is an edge pixel
  *    when it is a hit and one of its 4-neighbours is a miss or has a world
  *    point farther than edge_tol from its own (the paper's large
@@ -1579,6 +1580,36 @@ static d3 cam_centre(const cam_t *k) {   /* C = -R^T t */
               -(k->R[2] * k->t[0] + k->R[5] * k->t[1] + k->R[8] * k->t[2]));
 }
 
+/* the first hit in front of the origin: the smallest t > 0 over the
+ * triangles the line meets (equal t: the lower triangle id) */
+static void first_hit(const float *V, const int32_t *F, const obvh *b, d3 o, d3 d, hit_t *best) {
+    ray_t r = make_ray(o, d);
+    best->tri = -1; best->t = INFINITY; best->b[0] = best->b[1] = best->b[2] = 0.0;
+    if (b->nf == 0) return;
+    int stack[256], sp = 0;
+    stack[sp++] = 0;
+    while (sp) {
+        const bnode *n = &b->nodes[stack[--sp]];
+        double t0, t1;
+        if (!box_interval(n, o, d, &t0, &t1)) continue;
+        if (t1 < 0.0 || t0 > best->t) continue;
+        if (n->left < 0) {
+            for (int i = n->first; i < n->first + n->count; ++i) {
+                int tri = b->idx[i];
+                double t, bb[3];
+                if (!isect(&r, ldf(V, F[3 * tri]), ldf(V, F[3 * tri + 1]), ldf(V, F[3 * tri + 2]), &t, bb)) continue;
+                if (!(t > 0.0)) continue;
+                if (t < best->t || (t == best->t && tri < best->tri)) {
+                    best->tri = tri; best->t = t; best->b[0] = bb[0]; best->b[1] = bb[1]; best->b[2] = bb[2];
+                }
+            }
+        } else {
+            stack[sp++] = n->left;
+            stack[sp++] = n->right;
+        }
+    }
+}
+
 /* depth [h*w] (camera z of the first hit, +inf on a miss), point [h*w*3]
  * (NaN on a miss), near [h*w] per view: the pixel's value depends on
  * rounding: its ray misses but passes within tol of a triangle, or passes
@@ -1598,15 +1629,26 @@ int or_render_view(const float *V, const int32_t *F, int64_t nf, void *bvh, cons
                                 k.R[1] * dc.x + k.R[4] * dc.y + k.R[7] * dc.z,
                                 k.R[2] * dc.x + k.R[5] * dc.y + k.R[8] * dc.z));
             hit_t hh;
-            closest(V, F, nf, b, C, d, 1e30, -1, &hh);
-            /* triangles within tol of the ray, up to the hit */
+            first_hit(V, F, b, C, d, &hh);
+            /* triangles within tol of the ray (those behind the camera plane
+             * by more than 100 tol play no part) */
             vis_job vj;
             memset(&vj, 0, sizeof(vj));
             vj.V = V; vj.F = F; vj.nf = nf; vj.bvh = b; vj.delta = tol;
             int32_t cl[OR_MAX_CAND], nc = 0;
             ray_t r = make_ray(C, d);
-            int hit = hh.tri >= 0 && hh.t > 0.0;
+            int hit = hh.tri >= 0;
             candidates(&vj, C, d, &r, 1e30, cl, &nc);
+            const double sep = 100.0 * tol;
+            {
+                int kept = 0;
+                for (int m = 0; m < nc && m < OR_MAX_CAND; ++m) {
+                    double tc;
+                    line_tri_dist(V, F, cl[m], C, d, &r, &tc);
+                    if (tc >= -sep) cl[kept++] = cl[m];
+                }
+                if (nc <= OR_MAX_CAND) nc = kept;
+            }
             uint8_t nr = 0;
             if (hit) {
                 d3 X = add(C, scl(d, hh.t));
@@ -1620,7 +1662,6 @@ int or_render_view(const float *V, const int32_t *F, int64_t nf, void *bvh, cons
                  * that a same-facing triangle continues, rounding only moves the
                  * hit to that neighbour: depth and point stay. */
                 const int32_t *f = F + 3 * hh.tri;
-                const double sep = 100.0 * tol;
                 d3 nh = cross(sub(ldf(V, f[1]), ldf(V, f[0])), sub(ldf(V, f[2]), ldf(V, f[0])));
                 double sh = dot(d, nh);
                 int leave = 0;

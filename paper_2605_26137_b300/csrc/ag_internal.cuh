@@ -192,9 +192,12 @@ cudaError_t launch_trace(const TraceLaunch &L, cudaStream_t s);
 cudaError_t launch_closest(const TraceLaunch &L, cudaStream_t s);
 // UV-space backprojection (backproject.cu): per-view depth / point / edge
 // maps of the mesh of L.job0, and the blended texture of the ray texels
-size_t render_scratch_bytes(int n_views);
-cudaError_t launch_render_views(const TraceLaunch &L, const float *h_cams, int n_views, int w, int h, float edge_tol,
-                                float *depth, float *points, uint8_t *edge, void *scratch, cudaStream_t s);
+int render_chunk_views(int n_views, int w, int h);
+size_t render_head_bytes(int n_views);
+size_t render_scratch_bytes(int n_views, int w, int h, bool raster);
+cudaError_t launch_render_views(const TraceLaunch &L, int n_tris, const float *h_cams, int n_views, int w, int h,
+                                float edge_tol, bool raster, float *depth, float *points, uint8_t *edge, void *scratch,
+                                cudaStream_t s);
 size_t backproject_scratch_bytes(int n_views);
 cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const int4 *rays,
                                const long long *n_rays, int W, int H, const float *h_cams, const float *h_logw,

@@ -123,6 +123,8 @@ ag_status check_opts(const ag_opts &o) {
     if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
     if (o.query != AG_QUERY_RAY && o.query != AG_QUERY_CLOSEST)
         return set_error(AG_ERR_INVALID_ARG, "query must be AG_QUERY_RAY or AG_QUERY_CLOSEST");
+    if (o.render != AG_RENDER_RASTER && o.render != AG_RENDER_TRACE)
+        return set_error(AG_ERR_INVALID_ARG, "render must be AG_RENDER_RASTER or AG_RENDER_TRACE");
     return AG_OK;
 }
 
@@ -498,9 +500,9 @@ AG_API ag_status ag_render_views(ag_bvh_t h, int32_t n_views, const float *h_cam
     if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
     Scratch sc(s, h->device);
     void *cams;
-    AG_CUDA(sc.alloc(&cams, render_scratch_bytes(n_views)));
+    const bool raster = o.render == AG_RENDER_RASTER;
+    AG_CUDA(sc.alloc(&cams, render_scratch_bytes(n_views, w, hgt, raster)));
     float *points = d_points;
-    if (!points && d_edge) AG_CUDA(sc.alloc((void **)&points, sizeof(float) * 3 * (size_t)n_views * w * hgt));
     TraceLaunch L;
     memset(&L, 0, sizeof(L));
     L.job0.nodes = h->nodes;
@@ -510,7 +512,8 @@ AG_API ag_status ag_render_views(ag_bvh_t h, int32_t n_views, const float *h_cam
     L.status = status;
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = h->layout;
-    AG_CUDA(launch_render_views(L, h_cams, n_views, w, hgt, edge_tol, d_depth, points, d_edge, cams, s));
+    AG_CUDA(launch_render_views(L, (int)h->n_tris, h_cams, n_views, w, hgt, edge_tol, raster, d_depth, points, d_edge,
+                                cams, s));
     return AG_OK;
 }
 

@@ -3,9 +3,22 @@
 // texels' surface points, weighted by how squarely and how visibly each view
 // sees them.
 //
+// k_zbuffer: a z-buffer pass that proposes each pixel's first triangle: one
+// lane per (view, triangle) sets up the projected triangle (edge functions
+// evaluated with the lexicographically smaller endpoint first, so that two
+// triangles sharing an edge get exactly opposite values and no pixel centre
+// falls between them), the warp then walks the 32 triangles' pixel boxes
+// together (a prefix sum over the box sizes spreads the pixels evenly over
+// the lanes), and every covered pixel centre takes a 64-bit atomicMin of
+// (camera depth bits, triangle record).  A view in which some triangle
+// reaches the camera plane is traced whole instead.
 // k_render_views: the depth buffer, world-point map of every view (pinhole
-// camera, one thread per pixel, the ray through the pixel centre traced with
-// the closest-hit machinery of rays.cuh; camera depth of the first hit).
+// camera, one thread per pixel, the ray through the pixel centre).  With a
+// raster proposal the pixel's proposed triangle is tested with the
+// watertight ray-triangle test of rays.cuh; when the test confirms it the
+// hit is that of the full traversal, otherwise (a pixel centre within
+// rounding of an edge) the ray is traced through the BVH with the
+// closest-hit machinery of rays.cuh (camera depth of the first hit).
 // k_edge_mask: pixels whose 4-neighbours miss or lie farther than edge_tol in
 // world space (depth discontinuities and silhouettes).
 // k_backproject: per ray texel (the bake's UV raster and ray list), for every
@@ -16,6 +29,8 @@
 // + eps) is accumulated in one pass in log space (running maximum of
 // log w_k + alpha log I_k, rescaled sums), so large alpha neither under- nor
 // overflows.
+#include <algorithm>
+
 #include "rays.cuh"
 
 namespace ag {
@@ -36,25 +51,257 @@ struct RenderArgs {
     int max_steps;
     float *depth;
     float *points;
+    const unsigned long long *keys;   // raster proposals of views [v0, v0 + nv)
+    const int *whole;                 // per view: 1 = a triangle reaches the camera plane, trace every pixel
+    uint32_t *list;                   // pixels (within the launch's views) left to trace, or null: all
+    unsigned *count;                  // entries of list
+    int v0, nv;                       // the views of this launch
 };
 
+constexpr unsigned long long NO_KEY = ~0ull;
+
+struct RasterArgs {
+    const float4 *tris;
+    int n_tris;
+    const Cam *cams;
+    int w, h, v0, nv;
+    unsigned long long *keys;   // [nv*w*h], NO_KEY before the pass
+    int *whole;                 // [n_views]
+};
+
+// one lane's triangle: three canonical edges (a, b - a) with the orientation
+// that makes the inside non-negative, the camera-space plane n . X = d0, the
+// pixel box
+struct TriSetup {
+    float ax[3], ay[3], dx[3], dy[3];
+    float nx, ny, nz, d0;
+    int x0, y0, bw;
+    float rbw;        // 1 / bw, for the pixel offset -> (x, y) split
+    unsigned flip, rec, cnt;
+};
+
+__device__ __forceinline__ float edge_fn(float ax, float ay, float dx, float dy, float px, float py) {
+    return __fsub_rn(__fmul_rn(dx, __fsub_rn(py, ay)), __fmul_rn(dy, __fsub_rn(px, ax)));
+}
+
+__global__ void __launch_bounds__(256) k_zbuffer(RasterArgs A) {
+    __shared__ TriSetup ts[256];
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    const int per_view = (A.n_tris + 255) / 256;
+    const int kv = blockIdx.x / per_view;            // view within the launch
+    const int tri = (blockIdx.x - kv * per_view) * 256 + threadIdx.x;
+    const int k = A.v0 + kv;
+    const Cam &c = A.cams[k];
+    unsigned cnt = 0;
+    TriSetup T;
+    if (tri < A.n_tris) {
+        float X[3], Y[3], Z[3], u[3], v[3];
+        bool ok = true;
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float4 p = __ldg(&A.tris[3 * (size_t)tri + m]);
+            X[m] = c.R[0] * p.x + c.R[1] * p.y + c.R[2] * p.z + c.t[0];
+            Y[m] = c.R[3] * p.x + c.R[4] * p.y + c.R[5] * p.z + c.t[1];
+            Z[m] = c.R[6] * p.x + c.R[7] * p.y + c.R[8] * p.z + c.t[2];
+            u[m] = c.fx * X[m] / Z[m] + c.cx;
+            v[m] = c.fy * Y[m] / Z[m] + c.cy;
+            ok = ok && Z[m] > 0.f && fabsf(u[m]) < 1.0e30f && fabsf(v[m]) < 1.0e30f;
+        }
+        if (!ok) {
+            A.whole[k] = 1;
+        } else {
+            const float area = (u[1] - u[0]) * (v[2] - v[0]) - (v[1] - v[0]) * (u[2] - u[0]);
+            T.flip = 0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const int q = m == 2 ? 0 : m + 1;
+                const bool sw = u[q] < u[m] || (u[q] == u[m] && v[q] < v[m]);
+                const int a = sw ? q : m, b = sw ? m : q;
+                T.ax[m] = u[a];
+                T.ay[m] = v[a];
+                T.dx[m] = u[b] - u[a];
+                T.dy[m] = v[b] - v[a];
+                T.flip |= (unsigned)(sw != (area < 0.f)) << m;
+            }
+            const float e1x = X[1] - X[0], e1y = Y[1] - Y[0], e1z = Z[1] - Z[0];
+            const float e2x = X[2] - X[0], e2y = Y[2] - Y[0], e2z = Z[2] - Z[0];
+            T.nx = e1y * e2z - e1z * e2y;
+            T.ny = e1z * e2x - e1x * e2z;
+            T.nz = e1x * e2y - e1y * e2x;
+            T.d0 = T.nx * X[0] + T.ny * Y[0] + T.nz * Z[0];
+            T.rec = (unsigned)tri;
+            // pixel centres i + 1/2 inside [min u, max u] (and v), clamped to the image
+            const float lo_u = fminf(u[0], fminf(u[1], u[2])), hi_u = fmaxf(u[0], fmaxf(u[1], u[2]));
+            const float lo_v = fminf(v[0], fminf(v[1], v[2])), hi_v = fmaxf(v[0], fmaxf(v[1], v[2]));
+            const int x0 = (int)fmaxf(ceilf(lo_u - 0.5f), 0.f), x1 = (int)fminf(floorf(hi_u - 0.5f), (float)(A.w - 1));
+            const int y0 = (int)fmaxf(ceilf(lo_v - 0.5f), 0.f), y1 = (int)fminf(floorf(hi_v - 0.5f), (float)(A.h - 1));
+            T.x0 = x0;
+            T.y0 = y0;
+            T.bw = x1 - x0 + 1;
+            T.rbw = 1.0f / (float)T.bw;
+            // at most 16384^2 = 2^28 pixels
+            if (area != 0.f && x1 >= x0 && y1 >= y0) cnt = (unsigned)(x1 - x0 + 1) * (unsigned)(y1 - y0 + 1);
+        }
+    }
+    T.cnt = cnt;
+    ts[threadIdx.x] = T;
+    __syncwarp();
+    const long long npix = (long long)A.w * A.h;
+    unsigned long long *keys = A.keys + (long long)kv * npix;
+    const float icx = c.cx, icy = c.cy, rfx = 1.0f / c.fx, rfy = 1.0f / c.fy;
+    // the warp walks its 32 triangles one after the other, the lanes over
+    // the pixels of the current triangle's box (setup loads are broadcasts)
+    for (int q = 0; q < 32; ++q) {
+        const TriSetup &S = ts[wbase + q];
+        const unsigned n = S.cnt;
+        if (n == 0) continue;
+        const int bw = S.bw;
+        for (unsigned o = lane; o < n; o += 32) {
+            // o = y * bw + x: below 2^24 (o exact in FP32) the float
+            // estimate of y is within one of the quotient and one correction
+            // makes it exact; larger boxes divide in integers
+            int yy, xx;
+            if (n <= (1u << 24)) {
+                yy = (int)((float)o * S.rbw);
+                xx = (int)o - yy * bw;
+                if (xx < 0) { --yy; xx += bw; } else if (xx >= bw) { ++yy; xx -= bw; }
+            } else {
+                yy = (int)(o / (unsigned)bw);
+                xx = (int)o - yy * bw;
+            }
+            const int i = S.x0 + xx, j = S.y0 + yy;
+            const float px = (float)i + 0.5f, py = (float)j + 0.5f;
+            bool in = true;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float e = edge_fn(S.ax[m], S.ay[m], S.dx[m], S.dy[m], px, py);
+                in = in && (((S.flip >> m) & 1u) ? -e : e) >= 0.f;
+            }
+            if (!in) continue;
+            const float xh = (px - icx) * rfx, yh = (py - icy) * rfy;
+            const float z = __fdividef(S.d0, S.nx * xh + S.ny * yh + S.nz);
+            if (!(z > 0.f) || !(z < 3.0e38f)) continue;
+            const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | S.rec;
+            atomicMin(&keys[(long long)j * A.w + i], key);
+        }
+    }
+}
+
+// the watertight ray-triangle test of rays.cuh, keeping only hits in front
+// of the camera: the smallest t > 0 (b.babs holds it), equal t: lower id
+__device__ __forceinline__ void test_tri_front(const Ray &r, const float4 *__restrict__ tris,
+                                               const int32_t *__restrict__ tri_ids, uint32_t rec, Best &b) {
+    float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
+    float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+    xform(r, A, Ax, Ay, Az);
+    xform(r, B, Bx, By, Bz);
+    xform(r, C, Cx, Cy, Cz);
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return;
+    float det = U + V + W;
+    if (det == 0.f) return;
+    float T = U * Az + V * Bz + W * Cz;
+    float t = T / det;
+    if (!(t > 0.f) || !(t <= b.babs)) return;
+    if (b.found && t == b.babs && tri_ids[rec] >= tri_ids[b.rec]) return;
+    b.t = t; b.babs = t; b.rec = rec; b.U = U; b.V = V; b.W = W; b.det = det; b.found = true;
+}
+
+// the ray through pixel (i, j): camera centre C = -R^T t and unit direction
+// normalize(R^T ((i + 1/2 - cx) / fx, (j + 1/2 - cy) / fy, 1))
+__device__ __forceinline__ void pixel_ray(const Cam &c, int i, int j, float3 &C, float3 &d) {
+    const float dcx = ((float)i + 0.5f - c.cx) / c.fx, dcy = ((float)j + 0.5f - c.cy) / c.fy;
+    d = normalize3(make_float3(c.R[0] * dcx + c.R[3] * dcy + c.R[6], c.R[1] * dcx + c.R[4] * dcy + c.R[7],
+                               c.R[2] * dcx + c.R[5] * dcy + c.R[8]));
+    C = make_float3(-(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]),
+                    -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]),
+                    -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]));
+}
+
+// depth = t (d . forward), point = C + t d; +inf / NaN on a miss
+__device__ __forceinline__ void store_pixel(const RenderArgs &A, long long r, const Cam &c, float3 C, float3 d, bool hit,
+                                            float t) {
+    A.depth[r] = hit ? t * dot3(d, make_float3(c.R[6], c.R[7], c.R[8])) : __int_as_float(0x7f800000);
+    if (A.points) {
+        const float3 X = C + d * t;
+        const float nanv = __int_as_float(0x7fc00000);
+        A.points[3 * r] = hit ? X.x : nanv;
+        A.points[3 * r + 1] = hit ? X.y : nanv;
+        A.points[3 * r + 2] = hit ? X.z : nanv;
+    }
+}
+
+// the light pass over the raster proposals: a miss where nothing covers the
+// pixel centre, the proposed triangle's hit where the ray test confirms it;
+// every other pixel (a rejected proposal, or a view traced whole) is
+// appended to the trace list (warp-aggregated append)
+__global__ void __launch_bounds__(256) k_resolve_views(RenderArgs A) {
+    const long long npix = (long long)A.w * A.h;
+    const long long n = (long long)A.nv * npix;
+    const int lane = threadIdx.x & 31;
+    for (long long rr = (long long)blockIdx.x * blockDim.x + threadIdx.x; rr < n; rr += (long long)gridDim.x * blockDim.x) {
+        const int kv = (int)(rr / npix);
+        const int k = A.v0 + kv;
+        const int pix = (int)(rr - (long long)kv * npix);
+        const long long r = (long long)k * npix + pix;
+        bool queue = false;
+        if (A.whole[k]) {
+            queue = true;
+        } else {
+            const unsigned long long key = A.keys[rr];
+            const Cam &c = A.cams[k];
+            float3 C, d;
+            if (key == NO_KEY) {
+                A.depth[r] = __int_as_float(0x7f800000);
+                if (A.points) {
+                    const float nanv = __int_as_float(0x7fc00000);
+                    A.points[3 * r] = nanv;
+                    A.points[3 * r + 1] = nanv;
+                    A.points[3 * r + 2] = nanv;
+                }
+            } else {
+                pixel_ray(c, pix % A.w, pix / A.w, C, d);
+                const Ray ray = make_ray(C, make_float3(0.f, 0.f, 0.f), d);
+                Best b;
+                b.t = 0.f; b.babs = 3.0e38f; b.rec = 0; b.found = false;
+                b.U = b.V = b.W = 0.f; b.det = 1.f;
+                test_tri_front(ray, A.tris, A.tri_ids, (uint32_t)(key & 0xffffffffu), b);
+                if (b.found)
+                    store_pixel(A, r, c, C, d, true, b.t);
+                else
+                    queue = true;
+            }
+        }
+        const unsigned act = __activemask();
+        const unsigned want = __ballot_sync(act, queue);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            unsigned base = 0;
+            if (lane == leader) base = atomicAdd(A.count, (unsigned)__popc(want));
+            base = __shfl_sync(act, base, leader);
+            if (queue) A.list[base + __popc(want & ((1u << lane) - 1u))] = (uint32_t)rr;
+        }
+    }
+}
+
+// the full closest-hit traversal for the pixels of the trace list (or for
+// every pixel of the launch's views when there is no list)
 template <int LAYOUT>
-__global__ void __launch_bounds__(128) k_render_views(RenderArgs A) {
+__global__ void __launch_bounds__(128) k_trace_views(RenderArgs A) {
     uint2 stack[STACK];
-    const long long n = (long long)A.n_views * A.w * A.h;
-    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(r / ((long long)A.w * A.h));
-        const int pix = (int)(r - (long long)k * A.w * A.h);
-        const int i = pix % A.w, j = pix / A.w;
+    const long long npix = (long long)A.w * A.h;
+    const long long n = A.list ? (long long)*A.count : (long long)A.nv * npix;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long rr = A.list ? (long long)A.list[e] : e;
+        const int kv = (int)(rr / npix);
+        const int k = A.v0 + kv;
+        const int pix = (int)(rr - (long long)kv * npix);
+        const long long r = (long long)k * npix + pix;
         const Cam &c = A.cams[k];
-        const float dcx = ((float)i + 0.5f - c.cx) / c.fx, dcy = ((float)j + 0.5f - c.cy) / c.fy;
-        // world direction R^T (dcx, dcy, 1) and camera centre -R^T t
-        float3 d = make_float3(c.R[0] * dcx + c.R[3] * dcy + c.R[6], c.R[1] * dcx + c.R[4] * dcy + c.R[7],
-                               c.R[2] * dcx + c.R[5] * dcy + c.R[8]);
-        d = normalize3(d);
-        const float3 C = make_float3(-(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]),
-                                     -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]),
-                                     -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]));
+        float3 C, d;
+        pixel_ray(c, pix % A.w, pix / A.w, C, d);
         const Ray ray = make_ray(C, make_float3(0.f, 0.f, 0.f), d);
         Best b;
         b.t = 0.f; b.babs = 3.0e38f; b.rec = 0; b.found = false;
@@ -69,7 +316,7 @@ __global__ void __launch_bounds__(128) k_render_views(RenderArgs A) {
             if (ref_is_leaf(cur)) {
                 const uint32_t first = ref_first(cur);
                 const int cnt = ref_count(cur);
-                for (int q = 0; q < cnt; ++q) test_tri(ray, A.tris, A.tri_ids, first + q, b);
+                for (int q = 0; q < cnt; ++q) test_tri_front(ray, A.tris, A.tri_ids, first + q, b);
             } else if (LAYOUT == AG_BVH_Q8) {
                 NodeOps<AG_BVH_Q8>::visit(A.nodes, cur, ray, b.babs, nx, stack, sp, A.status);
             } else {
@@ -80,8 +327,8 @@ __global__ void __launch_bounds__(128) k_render_views(RenderArgs A) {
             } else {
                 bool done = true;
                 while (sp > 0) {
-                    uint2 e = stack[--sp];
-                    if (__uint_as_float(e.y) <= b.babs) { cur = e.x; done = false; break; }
+                    uint2 en = stack[--sp];
+                    if (__uint_as_float(en.y) <= b.babs) { cur = en.x; done = false; break; }
                 }
                 if (done) break;
             }
@@ -90,21 +337,14 @@ __global__ void __launch_bounds__(128) k_render_views(RenderArgs A) {
                 break;
             }
         }
-        const bool hit = b.found && b.t > 0.f;
-        const float3 fwd = make_float3(c.R[6], c.R[7], c.R[8]);
-        A.depth[r] = hit ? b.t * dot3(d, fwd) : __int_as_float(0x7f800000);
-        if (A.points) {
-            const float3 X = C + d * b.t;
-            const float nanv = __int_as_float(0x7fc00000);
-            A.points[3 * r] = hit ? X.x : nanv;
-            A.points[3 * r + 1] = hit ? X.y : nanv;
-            A.points[3 * r + 2] = hit ? X.z : nanv;
-        }
+        store_pixel(A, r, c, C, d, b.found, b.t);
     }
 }
 
-__global__ void k_edge_mask(const float *__restrict__ depth, const float *__restrict__ points, int w, int h,
-                            int n_views, float edge_tol, uint8_t *__restrict__ edge) {
+// edge pixels from the depth buffer alone: the world point of pixel (i, j)
+// at camera depth z is C + z R^T ((i + 1/2 - cx) / fx, (j + 1/2 - cy) / fy, 1)
+__global__ void k_edge_mask(const float *__restrict__ depth, const Cam *__restrict__ cams, int w, int h, int n_views,
+                            float edge_tol, uint8_t *__restrict__ edge) {
     const long long n = (long long)n_views * w * h;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -112,17 +352,30 @@ __global__ void k_edge_mask(const float *__restrict__ depth, const float *__rest
     const int pix = (int)(r - (long long)k * w * h);
     const int i = pix % w, j = pix / w;
     uint8_t e = 0;
-    if (depth[r] < 3.0e38f) {
-        const float3 P = make_float3(points[3 * r], points[3 * r + 1], points[3 * r + 2]);
+    const float z = depth[r];
+    if (z < 3.0e38f) {
+        const Cam &c = cams[k];
+        const float rfx = 1.0f / c.fx, rfy = 1.0f / c.fy;
+        const float3 C = make_float3(-(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]),
+                                     -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]),
+                                     -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]));
+        const float3 ex = make_float3(c.R[0], c.R[1], c.R[2]), ey = make_float3(c.R[3], c.R[4], c.R[5]);
+        const float3 ez = make_float3(c.R[6], c.R[7], c.R[8]);
+        auto point = [&](int ii, int jj, float zz) {
+            const float x = ((float)ii + 0.5f - c.cx) * rfx, y = ((float)jj + 0.5f - c.cy) * rfy;
+            return C + (ex * x + ey * y + ez) * zz;
+        };
+        const float3 P = point(i, j, z);
+        const float tol2 = edge_tol * edge_tol;
         const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
-        for (int m = 0; m < 4 && !e; ++m) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
             const int ii = i + di[m], jj = j + dj[m];
             if (ii < 0 || jj < 0 || ii >= w || jj >= h) continue;
-            const long long q = (long long)k * w * h + (long long)jj * w + ii;
-            if (!(depth[q] < 3.0e38f)) { e = 1; break; }
-            const float3 Q = make_float3(points[3 * q], points[3 * q + 1], points[3 * q + 2]);
-            const float3 D = Q - P;
-            if (dot3(D, D) > edge_tol * edge_tol) e = 1;
+            const float zq = depth[(long long)k * w * h + (long long)jj * w + ii];
+            if (!(zq < 3.0e38f)) { e = 1; continue; }
+            const float3 D = point(ii, jj, zq) - P;
+            if (dot3(D, D) > tol2) e = 1;
         }
     }
     edge[r] = e;
@@ -216,13 +469,32 @@ __global__ void __launch_bounds__(128) k_backproject(BlendArgs A) {
     }
 }
 
+// blocks of one wave: SMs x resident blocks per SM at this block size
+template <typename Kernel>
+unsigned resident_grid(Kernel kernel, int block, int dev) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (unsigned)(device_sm_count(dev) * per_sm);
+}
+
 }  // namespace
 
-cudaError_t launch_render_views(const TraceLaunch &L, const float *h_cams, int n_views, int w, int h, float edge_tol,
-                                float *depth, float *points, uint8_t *edge, void *scratch, cudaStream_t s) {
+cudaError_t launch_render_views(const TraceLaunch &L, int n_tris, const float *h_cams, int n_views, int w, int h,
+                                float edge_tol, bool raster, float *depth, float *points, uint8_t *edge, void *scratch,
+                                cudaStream_t s) {
+    // scratch: cameras, per-view flags, list count | keys | list
     Cam *d_cams = static_cast<Cam *>(scratch);
+    int *whole = reinterpret_cast<int *>(d_cams + n_views);
+    unsigned *count = reinterpret_cast<unsigned *>(whole + n_views);
+    const size_t head = render_head_bytes(n_views);
+    const int chunk = render_chunk_views(n_views, w, h);
+    const long long npix = (long long)w * h;
+    unsigned long long *keys = reinterpret_cast<unsigned long long *>(static_cast<char *>(scratch) + head);
+    uint32_t *list = reinterpret_cast<uint32_t *>(keys + (size_t)chunk * npix);
     cudaError_t e = cudaMemcpyAsync(d_cams, h_cams, sizeof(Cam) * n_views, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
+    if (raster && (e = cudaMemsetAsync(whole, 0, sizeof(int) * n_views, s)) != cudaSuccess) return e;
     RenderArgs A;
     A.nodes = L.job0.nodes;
     A.tris = L.job0.tris;
@@ -236,23 +508,71 @@ cudaError_t launch_render_views(const TraceLaunch &L, const float *h_cams, int n
     A.max_steps = L.max_steps;
     A.depth = depth;
     A.points = points;
+    A.whole = whole;
+    A.count = count;
     int dev;
     cudaGetDevice(&dev);
-    const unsigned grid = (unsigned)(device_sm_count(dev) * 8);
-    if (L.layout == AG_BVH_Q8)
-        k_render_views<AG_BVH_Q8><<<grid, 128, 0, s>>>(A);
-    else
-        k_render_views<AG_BVH_F32><<<grid, 128, 0, s>>>(A);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // one full wave of resident blocks (a partial second wave would double
+    // the time of the grid-stride loops)
+    const unsigned tgrid = L.layout == AG_BVH_Q8 ? resident_grid(k_trace_views<AG_BVH_Q8>, 128, dev)
+                                                 : resident_grid(k_trace_views<AG_BVH_F32>, 128, dev);
+    const unsigned rgrid = resident_grid(k_resolve_views, 256, dev);
+    for (int v0 = 0; v0 < n_views; v0 += chunk) {
+        const int nv = std::min(chunk, n_views - v0);
+        A.v0 = v0;
+        A.nv = nv;
+        A.keys = nullptr;
+        A.list = nullptr;
+        if (raster && n_tris > 0) {
+            if ((e = cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)(nv * npix), s)) != cudaSuccess)
+                return e;
+            if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+            RasterArgs R;
+            R.tris = L.job0.tris;
+            R.n_tris = n_tris;
+            R.cams = d_cams;
+            R.w = w;
+            R.h = h;
+            R.v0 = v0;
+            R.nv = nv;
+            R.keys = keys;
+            R.whole = whole;
+            k_zbuffer<<<(unsigned)(nv * ((n_tris + 255) / 256)), 256, 0, s>>>(R);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            A.keys = keys;
+            A.list = list;
+            k_resolve_views<<<rgrid, 256, 0, s>>>(A);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (L.layout == AG_BVH_Q8)
+            k_trace_views<AG_BVH_Q8><<<tgrid, 128, 0, s>>>(A);
+        else
+            k_trace_views<AG_BVH_F32><<<tgrid, 128, 0, s>>>(A);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (edge) {
         const long long n = (long long)n_views * w * h;
-        k_edge_mask<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(depth, points, w, h, n_views, edge_tol, edge);
+        k_edge_mask<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(depth, d_cams, w, h, n_views, edge_tol, edge);
         e = cudaGetLastError();
     }
     return e;
 }
 
-size_t render_scratch_bytes(int n_views) { return sizeof(Cam) * (size_t)n_views; }
+// cameras, per-view flags and the list count, rounded to 256 bytes
+size_t render_head_bytes(int n_views) {
+    return ((sizeof(Cam) + sizeof(int)) * (size_t)n_views + sizeof(unsigned) + 255) / 256 * 256;
+}
+
+// views per raster chunk: the chunk's proposal keys and trace list stay
+// within 1.5 GiB
+int render_chunk_views(int n_views, int w, int h) {
+    const long long per_view = 12ll * w * h;
+    return (int)std::max(1ll, std::min<long long>(n_views, (3ll << 29) / per_view));
+}
+
+size_t render_scratch_bytes(int n_views, int w, int h, bool raster) {
+    return render_head_bytes(n_views) + (raster ? 12ull * (size_t)w * h * render_chunk_views(n_views, w, h) : 0);
+}
 
 cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const int4 *rays,
                                const long long *n_rays, int W, int H, const float *h_cams, const float *h_logw,
@@ -291,7 +611,7 @@ cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int
     A.incidence = incidence;
     int dev;
     cudaGetDevice(&dev);
-    k_backproject<<<(unsigned)(device_sm_count(dev) * 8), 128, 0, s>>>(A);
+    k_backproject<<<resident_grid(k_backproject, 128, dev), 128, 0, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -383,10 +383,13 @@ def point_distance(bvh: Bvh, points, max_dist: float, *, tri: bool = False, stre
 
 # ----------------------------------------------------------------- UV-space backprojection (Sec. 7.4)
 
-def render_views(bvh: Bvh, cams, w: int, h: int, *, edge_tol: float, points: bool = True, stream=None):
+def render_views(bvh: Bvh, cams, w: int, h: int, *, edge_tol: float, points: bool = True, render: str = "raster",
+                 stream=None):
     """Depth [K,h,w] f32 (+inf on a miss), world points [K,h,w,3] (NaN on a
     miss) and edge mask [K,h,w] u8 of K pinhole views (cams: host numpy
-    [K,16] f32) of the mesh ``bvh`` was built on."""
+    [K,16] f32) of the mesh ``bvh`` was built on.  render: "raster"
+    (z-buffer proposals confirmed by the ray test) or "trace" (every pixel
+    traced)."""
     import numpy as np
     lib = _lib.load()
     cams = np.ascontiguousarray(cams, dtype=np.float32).reshape(-1, 16)
@@ -395,7 +398,8 @@ def render_views(bvh: Bvh, cams, w: int, h: int, *, edge_tol: float, points: boo
     depth = torch.empty((K, h, w), dtype=torch.float32, device=dev)
     pts = torch.empty((K, h, w, 3), dtype=torch.float32, device=dev) if points else None
     edge = torch.empty((K, h, w), dtype=torch.uint8, device=dev)
-    check(lib.ag_render_views(bvh.handle, K, cams.ctypes.data, w, h, float(edge_tol), None, _stream(stream),
+    o = default_opts(render={"raster": _lib.AG_RENDER_RASTER, "trace": _lib.AG_RENDER_TRACE}[render])
+    check(lib.ag_render_views(bvh.handle, K, cams.ctypes.data, w, h, float(edge_tol), ctypes.byref(o), _stream(stream),
                               depth.data_ptr(), _ptr(pts), edge.data_ptr()))
     return depth, pts, edge
 

@@ -57,6 +57,15 @@ def test_render_depth_is_view_distance():
     assert hit.sum() > 100
     assert np.abs(depth[0][hit] - 2.75).max() < 1e-12
     assert np.abs(point[0][hit][:, 2] - 0.25).max() < 1e-12
+    # a larger plane just behind the camera (nearer along the line than the
+    # one in front) plays no part: the first hit is the smallest t > 0
+    Vb, Fb = _plane(8, z=3.5, size=4.0)
+    V2 = np.concatenate([V, Vb])
+    F2 = np.concatenate([F, Fb + len(V)]).astype(np.int32)
+    depth2, _, near2 = oracle.render_views(V2, F2, cam[None], 32, 32)
+    assert np.array_equal(np.isfinite(depth2[0]), hit)
+    assert np.abs(depth2[0][hit] - 2.75).max() < 1e-12
+    assert not near2[0][hit].any()
 
 
 def test_face_on_affine_image_closed_form():
