@@ -94,6 +94,20 @@ enum { AG_QUERY_RAY = 0, AG_QUERY_CLOSEST = 1 };
  *  AG_RENDER_TRACE  - every pixel traced through the BVH. */
 enum { AG_RENDER_RASTER = 0, AG_RENDER_TRACE = 1 };
 
+/* View sampling of ag_backproject (ag_opts.filter):
+ *  AG_FILTER_ANISO    - per texel and view, the image footprint of one texel
+ *                       (central differences of the owning face's UV -> position
+ *                       map through the projection), its SVD, up to AG_MAX_TAPS
+ *                       taps along the major axis (N = ceil(s1 / s2 - 0.05)), each
+ *                       a trilinear sample of the view's Lanczos-2 pyramid at
+ *                       log2(max(s2, s1 / AG_MAX_TAPS)) + AG_LOD_BIAS, levels >= 1
+ *                       sharpened by P + AG_SHARPEN (P - blur P) (Sec. 7.4).
+ *  AG_FILTER_BILINEAR - one bilinear sample at the projected position. */
+enum { AG_FILTER_ANISO = 0, AG_FILTER_BILINEAR = 1 };
+#define AG_MAX_TAPS 8
+#define AG_LOD_BIAS (-0.5f)
+#define AG_SHARPEN 0.25f
+
 /* Options.  Zero-initialise then call ag_opts_default, or pass NULL for the
  * defaults. */
 typedef struct {
@@ -113,7 +127,8 @@ typedef struct {
                             (a warp's 32 rays come from one tile; default AG_TILE_8x8) */
     int32_t query;       /* ag_bake*, ag_autotune: AG_QUERY_RAY (0, default) or AG_QUERY_CLOSEST */
     int32_t render;      /* ag_render_views: AG_RENDER_RASTER (0, default) or AG_RENDER_TRACE */
-    int32_t reserved[5];
+    int32_t filter;      /* ag_backproject: AG_FILTER_ANISO (0, default) or AG_FILTER_BILINEAR */
+    int32_t reserved[4];
 } ag_opts;
 
 /* Optional extra outputs of ag_bake (any member may be NULL). */

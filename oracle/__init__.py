@@ -88,8 +88,10 @@ def _load():
         lib.or_render_view.restype = _I
         lib.or_edge_mask.argtypes = [_P, _P, _I, _I, _D, _P]
         lib.or_edge_mask.restype = _I
-        lib.or_backproject.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P, _P,
-                                       _D, _D, _D, _D, _D, _P, _P, _P, _P]
+        lib.or_backproject.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P,
+                                       _P, _D, _D, _D, _D, _D, _I, _D, _I, _D, _P, _P, _P, _P]
+        lib.or_mip_levels.argtypes = [_P, _I, _I, _D, _P, _P, _P]
+        lib.or_mip_levels.restype = _I
         lib.or_backproject.restype = _I
         lib.or_qem_face_quadric.argtypes = [_P, _P]
         lib.or_qem_face_quadric.restype = None
@@ -477,12 +479,36 @@ def edge_mask(depth, point, edge_tol: float):
     return edge
 
 
+def mip_levels(img, sharpen: float = 0.25):
+    """Levels 1.. of one RGBA8 image's Lanczos-2 pyramid (the anisotropic
+    filter's), each as ([h,w,3] unsharpened, [h,w,3] sharpened)."""
+    lib = _load()
+    img = _c(img, np.uint8)
+    h, w = img.shape[:2]
+    tot = 3 * sum(max(1, w >> l) * max(1, h >> l) for l in range(1, 17))
+    plain = np.zeros(tot, np.float64)
+    sharp = np.zeros(tot, np.float64)
+    dims = np.zeros(32, np.int32)
+    n = lib.or_mip_levels(_p(img), w, h, float(sharpen), _p(plain), _p(sharp), _p(dims))
+    if n < 0:
+        raise MemoryError("or_mip_levels failed")
+    out, off = [], 0
+    for l in range(n - 1):
+        lw, lh = int(dims[2 * l]), int(dims[2 * l + 1])
+        k = 3 * lw * lh
+        out.append((plain[off:off + k].reshape(lh, lw, 3), sharp[off:off + k].reshape(lh, lw, 3)))
+        off += k
+    return out
+
+
 def backproject(lv, lf, luv, W: int, H: int, cams, images, weights, *, alpha: float, eps: float,
-                depth_tol: float, edge_tol: float, views=None, tol_rel: float = 1e-5):
+                depth_tol: float, edge_tol: float, views=None, tol_rel: float = 1e-5, filter: str = "aniso",
+                lod_bias: float = -0.5, max_taps: int = 8, sharpen: float = 0.25):
     """Texture [H,W,3] (FP64), filled [H,W], flags [H,W] and incidence
     [K,H,W] of the blended backprojection of K views onto the low mesh's
     atlas.  ``views`` = (depth, point, near) from render_views, rendered here
-    when None."""
+    when None.  filter: "aniso" (footprint taps over a Lanczos-2 pyramid) or
+    "bilinear" (one sample)."""
     lib = _load()
     lv = _c(lv, np.float32)
     lf = _c(lf, np.int32)
@@ -502,8 +528,12 @@ def backproject(lv, lf, luv, W: int, H: int, cams, images, weights, *, alpha: fl
     filled = np.zeros((H, W), np.uint8)
     flags = np.zeros((H, W), np.uint8)
     incid = np.zeros((K, H, W), np.float64)
-    lib.or_backproject(_p(lv), len(lv), _p(lf), len(lf), _p(ln), _p(face), _p(bary), W, H, K, _p(cams), _p(images),
-                       iw, ih, _p(depth), _p(point), _p(near), _p(weights), float(alpha), float(eps),
-                       float(depth_tol), float(edge_tol), scale, _p(tex), _p(filled), _p(flags), _p(incid))
+    rc = lib.or_backproject(_p(lv), len(lv), _p(lf), len(lf), _p(ln), _p(luv), _p(face), _p(bary), W, H, K,
+                            _p(cams), _p(images), iw, ih, _p(depth), _p(point), _p(near), _p(weights), float(alpha),
+                            float(eps), float(depth_tol), float(edge_tol), scale,
+                            {"bilinear": 0, "aniso": 1}[filter], float(lod_bias), int(max_taps), float(sharpen),
+                            _p(tex), _p(filled), _p(flags), _p(incid))
+    if rc != 0:
+        raise MemoryError("or_backproject failed")
     return dict(texture=tex, filled=filled, flags=flags, incidence=incid, face=face, bary=bary,
                 depth=depth, point=point, near=near)

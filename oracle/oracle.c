@@ -1731,6 +1731,144 @@ static double bilinear(const uint8_t *img, int w, int h, int ch, double x, doubl
     return acc;
 }
 
+/* --- anisotropic filtering (Sec. 7.4), readings:
+ *  - Mip chain of each view's RGB (codes / 255): level l+1 has max(1, w_l / 2) x max(1, h_l / 2)
+ *    pixels; its pixel j is centred at level-l coordinate 2j + 1, and takes the 8 level-l pixels
+ *    i = 2j - 3 .. 2j + 4 (clamped to the image) with weights L((i + 1/2 - (2j + 1)) / 2),
+ *    L(x) = sinc(x) sinc(x / 2) for |x| < 2 (Lanczos-2 stretched for a 2x reduction),
+ *    normalised; rows first, then columns; the level is clamped to [0, 1].
+ *  - Per-level sharpening: level l >= 1 is sampled as clamp(P + s (P - B P), 0, 1), B the
+ *    separable [1, 2, 1] / 4 blur with clamped borders; P is the unsharpened level, from which
+ *    the next level is built.
+ *  - Footprint: the texel's surface point moves by dp/dx, dp/dy per texel (the owning face's
+ *    affine UV -> position map); the Jacobian J of texel -> image is the central difference of
+ *    the projections of p -+ dp/dx / 2 and p -+ dp/dy / 2.  A face whose UV area is below
+ *    1e-4 texel^2, or a difference point behind the camera, falls back to the centre sample.
+ *  - SVD of J: singular values s1 >= s2 and the major image direction e1 (from J J^T).
+ *    Taps N = clamp(ceil(s1 / s2 - 0.05), 1, max_taps) (ratios within 5 % above an integer add
+ *    no tap, so an isotropic footprint keeps one tap under rounding), spread over the major axis:
+ *    (u, v) + e1 s1 ((i + 1/2) / N - 1/2), equally weighted.
+ *  - Level lambda = log2(max(s2, s1 / max_taps)) + lod_bias (the minor axis, raised when the taps
+ *    cannot cover the major axis), clamped to [0, levels - 1]; trilinear: the bilinear samples of
+ *    levels floor(lambda) and floor(lambda) + 1 at (u / 2^l - 1/2, v / 2^l - 1/2), blended by the
+ *    fraction; level 0 is the 8-bit image itself. */
+#define OR_MAX_LEV 16
+typedef struct { int n; int w[OR_MAX_LEV], h[OR_MAX_LEV]; double *p[OR_MAX_LEV], *s[OR_MAX_LEV]; } mips_t;
+
+static double lanczos2(double x) {
+    if (x == 0.0) return 1.0;
+    if (fabs(x) >= 2.0) return 0.0;
+    const double px = M_PI * x;
+    return 2.0 * sin(px) * sin(0.5 * px) / (px * px);
+}
+
+/* level 0 of pyramid m is the image (never stored); levels 1.. are built here */
+static int build_mips(const uint8_t *img, int w, int h, double sharpen, mips_t *m) {
+    memset(m, 0, sizeof(*m));
+    m->n = 1;
+    m->w[0] = w; m->h[0] = h;
+    double wt[8], sw = 0.0;
+    for (int t = 0; t < 8; ++t) { wt[t] = lanczos2((t - 3.5) / 2.0); sw += wt[t]; }
+    for (int t = 0; t < 8; ++t) wt[t] /= sw;
+    const double *prev = NULL;
+    int pw = w, ph = h;
+    while ((pw > 1 || ph > 1) && m->n < OR_MAX_LEV) {
+        int nw = pw / 2 > 1 ? pw / 2 : 1, nh = ph / 2 > 1 ? ph / 2 : 1;
+        double *tmp = (double *)malloc(sizeof(double) * 3 * (size_t)nw * ph);
+        double *out = (double *)malloc(sizeof(double) * 3 * (size_t)nw * nh);
+        double *shp = (double *)malloc(sizeof(double) * 3 * (size_t)nw * nh);
+        double *blr = (double *)malloc(sizeof(double) * 3 * (size_t)nw * nh);
+        if (!tmp || !out || !shp || !blr) { free(tmp); free(out); free(shp); free(blr); return -1; }
+        for (int y = 0; y < ph; ++y)
+            for (int x = 0; x < nw; ++x)
+                for (int c = 0; c < 3; ++c) {
+                    double acc = 0.0;
+                    for (int t = 0; t < 8; ++t) {
+                        int i = 2 * x - 3 + t;
+                        if (i < 0) i = 0;
+                        if (i > pw - 1) i = pw - 1;
+                        double v = prev ? prev[((size_t)y * pw + i) * 3 + c] : img[((size_t)y * pw + i) * 4 + c] / 255.0;
+                        acc += wt[t] * v;
+                    }
+                    tmp[((size_t)y * nw + x) * 3 + c] = acc;
+                }
+        for (int y = 0; y < nh; ++y)
+            for (int x = 0; x < nw; ++x)
+                for (int c = 0; c < 3; ++c) {
+                    double acc = 0.0;
+                    for (int t = 0; t < 8; ++t) {
+                        int j = 2 * y - 3 + t;
+                        if (j < 0) j = 0;
+                        if (j > ph - 1) j = ph - 1;
+                        acc += wt[t] * tmp[((size_t)j * nw + x) * 3 + c];
+                    }
+                    out[((size_t)y * nw + x) * 3 + c] = acc < 0.0 ? 0.0 : (acc > 1.0 ? 1.0 : acc);
+                }
+        /* sharpened copy: P + s (P - B P) */
+        for (int y = 0; y < nh; ++y)
+            for (int x = 0; x < nw; ++x)
+                for (int c = 0; c < 3; ++c) {
+                    int xl = x > 0 ? x - 1 : 0, xr = x < nw - 1 ? x + 1 : nw - 1;
+                    blr[((size_t)y * nw + x) * 3 + c] = 0.25 * out[((size_t)y * nw + xl) * 3 + c] +
+                                                        0.5 * out[((size_t)y * nw + x) * 3 + c] +
+                                                        0.25 * out[((size_t)y * nw + xr) * 3 + c];
+                }
+        for (int y = 0; y < nh; ++y)
+            for (int x = 0; x < nw; ++x)
+                for (int c = 0; c < 3; ++c) {
+                    int yu = y > 0 ? y - 1 : 0, yd = y < nh - 1 ? y + 1 : nh - 1;
+                    double b = 0.25 * blr[((size_t)yu * nw + x) * 3 + c] + 0.5 * blr[((size_t)y * nw + x) * 3 + c] +
+                               0.25 * blr[((size_t)yd * nw + x) * 3 + c];
+                    double P = out[((size_t)y * nw + x) * 3 + c];
+                    double v = P + sharpen * (P - b);
+                    shp[((size_t)y * nw + x) * 3 + c] = v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+                }
+        free(tmp);
+        free(blr);
+        m->p[m->n] = out; m->s[m->n] = shp; m->w[m->n] = nw; m->h[m->n] = nh;
+        ++m->n;
+        prev = out; pw = nw; ph = nh;
+    }
+    return 0;
+}
+
+static void free_mips(mips_t *m) {
+    for (int l = 1; l < m->n; ++l) { free(m->p[l]); free(m->s[l]); }
+}
+
+static double bilinear_d(const double *lev, int w, int h, int ch, double x, double y) {
+    double fx = floor(x), fy = floor(y);
+    double ax = x - fx, ay = y - fy;
+    int x0 = (int)fx, y0 = (int)fy;
+    double acc = 0.0;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx) {
+            int xx = x0 + dx, yy = y0 + dy;
+            if (xx < 0) xx = 0;
+            if (yy < 0) yy = 0;
+            if (xx > w - 1) xx = w - 1;
+            if (yy > h - 1) yy = h - 1;
+            acc += (dx ? ax : 1.0 - ax) * (dy ? ay : 1.0 - ay) * lev[((int64_t)yy * w + xx) * 3 + ch];
+        }
+    return acc;
+}
+
+/* the bilinear sample of level l at level-0 image position (u, v) */
+static double level_sample(const uint8_t *img, const mips_t *m, int l, int ch, double u, double v) {
+    if (l == 0) return bilinear(img, m->w[0], m->h[0], ch, u - 0.5, v - 0.5);
+    const double sc = ldexp(1.0, -l);
+    return bilinear_d(m->s[l], m->w[l], m->h[l], ch, u * sc - 0.5, v * sc - 0.5);
+}
+
+static double trilinear(const uint8_t *img, const mips_t *m, double lam, int ch, double u, double v) {
+    int l0 = (int)floor(lam);
+    double f = lam - l0;
+    if (l0 >= m->n - 1) return level_sample(img, m, m->n - 1, ch, u, v);
+    double a = level_sample(img, m, l0, ch, u, v);
+    if (f == 0.0) return a;
+    return (1.0 - f) * a + f * level_sample(img, m, l0 + 1, ch, u, v);
+}
+
 /* edge pixel test; *amb is set when a neighbour distance lies within
  * amb_tol of edge_tol (the decision is a rounding decision there) */
 static int is_edge(const double *depth, const double *point, int w, int h, int i, int j, double edge_tol,
@@ -1761,14 +1899,94 @@ int or_edge_mask(const double *depth, const double *point, int w, int h, double 
     return 0;
 }
 
-/* texture [H*W*3], filled [H*W], flags [H*W], incid (optional) [K*H*W] */
-int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf, const double *ln, const int32_t *face,
-                   const double *bary, int W, int H, int K, const float *cams, const uint8_t *images, int iw, int ih,
-                   const double *depth, const double *point, const uint8_t *near, const float *weights, double alpha,
-                   double eps, double depth_tol, double edge_tol, double scale, double *texture, uint8_t *filled,
+/* the anisotropic colour of one view at image position (u, v) for the texel
+ * of face f at surface point p (the readings above); *fl is set when the tap
+ * count or the fallback decision lies within rounding of its threshold */
+static void aniso_color(const float *lv, const int32_t *lf, const float *luv, int W, int H, int32_t f, d3 p,
+                        const cam_t *c, const uint8_t *img, const mips_t *m, double u, double v, double lod_bias,
+                        int max_taps, double out[3], uint8_t *fl) {
+    double x[3], y[3];
+    for (int q = 0; q < 3; ++q) {
+        x[q] = (double)luv[6 * (int64_t)f + 2 * q] * W;
+        y[q] = (double)luv[6 * (int64_t)f + 2 * q + 1] * H;
+    }
+    double det = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
+    if (fabs(fabs(det) * 0.5 - 1e-4) < 1e-6) *fl = 1;
+    int ok = fabs(det) * 0.5 >= 1e-4;
+    d3 dpx = mk(0, 0, 0), dpy = mk(0, 0, 0);
+    if (ok) {
+        double b1x = (y[2] - y[0]) / det, b1y = -(x[2] - x[0]) / det;
+        double b2x = -(y[1] - y[0]) / det, b2y = (x[1] - x[0]) / det;
+        d3 P0 = ldf(lv, lf[3 * f]), e1 = sub(ldf(lv, lf[3 * f + 1]), P0), e2 = sub(ldf(lv, lf[3 * f + 2]), P0);
+        dpx = add(scl(e1, b1x), scl(e2, b2x));
+        dpy = add(scl(e1, b1y), scl(e2, b2y));
+    }
+    double J[2][2];
+    for (int a = 0; a < 2 && ok; ++a) {
+        d3 dp = a ? dpy : dpx;
+        d3 q1 = cam_apply(c, add(p, scl(dp, 0.5))), q0 = cam_apply(c, sub(p, scl(dp, 0.5)));
+        if (!(q1.z > 0.0) || !(q0.z > 0.0)) { ok = 0; break; }
+        J[0][a] = (c->fx * q1.x / q1.z + c->cx) - (c->fx * q0.x / q0.z + c->cx);
+        J[1][a] = (c->fy * q1.y / q1.z + c->cy) - (c->fy * q0.y / q0.z + c->cy);
+    }
+    if (!ok) {
+        for (int ch = 0; ch < 3; ++ch) out[ch] = bilinear(img, m->w[0], m->h[0], ch, u - 0.5, v - 0.5);
+        return;
+    }
+    /* J J^T = [[a, b], [b, d]] */
+    double a = J[0][0] * J[0][0] + J[0][1] * J[0][1], b = J[0][0] * J[1][0] + J[0][1] * J[1][1];
+    double dd = J[1][0] * J[1][0] + J[1][1] * J[1][1];
+    double half = 0.5 * (a + dd), disc = sqrt(0.25 * (a - dd) * (a - dd) + b * b);
+    double l1 = half + disc, l2 = half - disc;
+    if (l2 < 0.0) l2 = 0.0;
+    double s1 = sqrt(l1), s2 = sqrt(l2);
+    double ex, ey;
+    if (b != 0.0) { ex = l1 - dd; ey = b; }
+    else if (a >= dd) { ex = 1.0; ey = 0.0; }
+    else { ex = 0.0; ey = 1.0; }
+    double en = sqrt(ex * ex + ey * ey);
+    ex /= en; ey /= en;
+    int N = max_taps;
+    if (s2 > 0.0) {
+        double ratio = s1 / s2;
+        for (int k = 1; k < max_taps; ++k)
+            if (fabs(ratio - 0.05 - k) < 1e-4 * ratio) *fl = 1;
+        double nf = ceil(ratio - 0.05);
+        N = nf < 1.0 ? 1 : (nf > max_taps ? max_taps : (int)nf);
+    }
+    double mm = s2 > s1 / max_taps ? s2 : s1 / max_taps;
+    double lam = mm > 0.0 ? log2(mm) + lod_bias : 0.0;
+    if (lam < 0.0) lam = 0.0;
+    if (lam > m->n - 1) lam = m->n - 1;
+    for (int ch = 0; ch < 3; ++ch) out[ch] = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double o = s1 * ((i + 0.5) / N - 0.5);
+        for (int ch = 0; ch < 3; ++ch) out[ch] += trilinear(img, m, lam, ch, u + ex * o, v + ey * o);
+    }
+    for (int ch = 0; ch < 3; ++ch) out[ch] /= N;
+}
+
+/* texture [H*W*3], filled [H*W], flags [H*W], incid (optional) [K*H*W];
+ * filter 0: one bilinear sample, 1: anisotropic (the readings above) */
+int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf, const double *ln, const float *luv,
+                   const int32_t *face, const double *bary, int W, int H, int K, const float *cams,
+                   const uint8_t *images, int iw, int ih, const double *depth, const double *point, const uint8_t *near,
+                   const float *weights, double alpha, double eps, double depth_tol, double edge_tol, double scale,
+                   int filter, double lod_bias, int max_taps, double sharpen, double *texture, uint8_t *filled,
                    uint8_t *flags, double *incid) {
     (void)nlv; (void)nlf;
     int64_t npix = (int64_t)iw * ih;
+    mips_t *mips = NULL;
+    if (filter) {
+        mips = (mips_t *)calloc((size_t)(K > 0 ? K : 1), sizeof(mips_t));
+        if (!mips) return -1;
+        for (int k = 0; k < K; ++k)
+            if (build_mips(images + (int64_t)k * npix * 4, iw, ih, sharpen, &mips[k])) {
+                for (int q = 0; q <= k; ++q) free_mips(&mips[q]);
+                free(mips);
+                return -1;
+            }
+    }
     for (int64_t tex = 0; tex < (int64_t)W * H; ++tex) {
         texture[3 * tex] = texture[3 * tex + 1] = texture[3 * tex + 2] = 0.0;
         filled[tex] = 0;
@@ -1819,7 +2037,12 @@ int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf,
             if (!(I > 0.0)) continue;
             if (incid) incid[(int64_t)k * W * H + tex] = I;
             L[nk] = log((double)weights[k]) + alpha * log(I);
-            for (int ch = 0; ch < 3; ++ch) A[nk][ch] = bilinear(images + (int64_t)k * npix * 4, iw, ih, ch, u - 0.5, v - 0.5);
+            if (filter)
+                aniso_color(lv, lf, luv, W, H, f, p, &c, images + (int64_t)k * npix * 4, &mips[k], u, v, lod_bias,
+                            max_taps, A[nk], &fl);
+            else
+                for (int ch = 0; ch < 3; ++ch)
+                    A[nk][ch] = bilinear(images + (int64_t)k * npix * 4, iw, ih, ch, u - 0.5, v - 0.5);
             ++nk;
         }
         flags[tex] = fl;
@@ -1836,5 +2059,28 @@ int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf,
         for (int ch = 0; ch < 3; ++ch) texture[3 * tex + ch] = num[ch] / den;
         filled[tex] = 1;
     }
+    if (mips) {
+        for (int k = 0; k < K; ++k) free_mips(&mips[k]);
+        free(mips);
+    }
     return 0;
+}
+
+/* levels >= 1 of one view's pyramid, unsharpened and sharpened, for pin
+ * tests: out [sum of level sizes * 3] per kind; returns the level count */
+int or_mip_levels(const uint8_t *img, int w, int h, double sharpen, double *plain, double *sharp, int32_t *dims) {
+    mips_t m;
+    if (build_mips(img, w, h, sharpen, &m)) return -1;
+    size_t off = 0;
+    for (int l = 1; l < m.n; ++l) {
+        size_t n3 = 3 * (size_t)m.w[l] * m.h[l];
+        memcpy(plain + off, m.p[l], n3 * sizeof(double));
+        memcpy(sharp + off, m.s[l], n3 * sizeof(double));
+        off += n3;
+        dims[2 * (l - 1)] = m.w[l];
+        dims[2 * (l - 1) + 1] = m.h[l];
+    }
+    int n = m.n;
+    free_mips(&m);
+    return n;
 }

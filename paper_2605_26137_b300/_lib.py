@@ -35,6 +35,8 @@ AG_QUERY_RAY = 0
 AG_QUERY_CLOSEST = 1
 AG_RENDER_RASTER = 0
 AG_RENDER_TRACE = 1
+AG_FILTER_ANISO = 0
+AG_FILTER_BILINEAR = 1
 AG_QEM_OPTIMAL = 0
 AG_QEM_MIDPOINT = 1
 
@@ -50,7 +52,7 @@ class AgOpts(ctypes.Structure):
     _fields_ = [("bvh_layout", c_int32), ("gutter", c_int32), ("disp_fp16", c_int32), ("schedule", c_int32),
                 ("block_size", c_int32), ("blocks_per_sm", c_int32), ("max_steps", c_int32),
                 ("collapse", c_int32), ("ray_tile", c_int32), ("query", c_int32), ("render", c_int32),
-                ("reserved", c_int32 * 5)]
+                ("filter", c_int32), ("reserved", c_int32 * 4)]
 
 
 class AgBakeAux(ctypes.Structure):

@@ -198,11 +198,12 @@ size_t render_scratch_bytes(int n_views, int w, int h, bool raster);
 cudaError_t launch_render_views(const TraceLaunch &L, int n_tris, const float *h_cams, int n_views, int w, int h,
                                 float edge_tol, bool raster, float *depth, float *points, uint8_t *edge, void *scratch,
                                 cudaStream_t s);
-size_t backproject_scratch_bytes(int n_views);
-cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const int4 *rays,
-                               const long long *n_rays, int W, int H, const float *h_cams, const float *h_logw,
-                               int n_views, const uint8_t *images, const float *depth, const uint8_t *edge, int w,
-                               int h, float alpha, float eps, float depth_tol, float4 *texture, float *incidence,
+size_t backproject_scratch_bytes(int n_views, int w, int h, int filter);
+cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const float *luv,
+                               const int4 *rays, const long long *n_rays, int W, int H, const float *h_cams,
+                               const float *h_logw, int n_views, const uint8_t *images, const float *depth,
+                               const uint8_t *edge, int w, int h, float alpha, float eps, float depth_tol, int filter,
+                               float lod_bias, int max_taps, float sharpen, float4 *texture, float *incidence,
                                void *scratch, cudaStream_t s);
 // distance from n points to the mesh of L.job0 (nodes, tris, tri_ids, scene_abs), -1 beyond max_dist
 cudaError_t launch_point_distance(const TraceLaunch &L, const float *pts, long long n, float max_dist, float *dist,

@@ -125,6 +125,8 @@ ag_status check_opts(const ag_opts &o) {
         return set_error(AG_ERR_INVALID_ARG, "query must be AG_QUERY_RAY or AG_QUERY_CLOSEST");
     if (o.render != AG_RENDER_RASTER && o.render != AG_RENDER_TRACE)
         return set_error(AG_ERR_INVALID_ARG, "render must be AG_RENDER_RASTER or AG_RENDER_TRACE");
+    if (o.filter != AG_FILTER_ANISO && o.filter != AG_FILTER_BILINEAR)
+        return set_error(AG_ERR_INVALID_ARG, "filter must be AG_FILTER_ANISO or AG_FILTER_BILINEAR");
     return AG_OK;
 }
 
@@ -551,13 +553,13 @@ AG_API ag_status ag_backproject(const float *d_lverts, const float *d_lnormals, 
     memset(&a, 0, sizeof(a));
     if ((st = alloc_asset(sc, n_lverts, n_lfaces, W, H, true, a))) return st;
     void *scr;
-    AG_CUDA(sc.alloc(&scr, backproject_scratch_bytes(n_views)));
+    AG_CUDA(sc.alloc(&scr, backproject_scratch_bytes(n_views, w, hgt, o.filter)));
     if ((st = run_prep(d_lverts, d_lnormals, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, o.ray_tile, nullptr, status, a,
                        s)))
         return st;
-    AG_CUDA(launch_backproject(a.lpos, a.lnrm, a.lface, a.rays, a.n_rays, W, H, h_cams, logw.data(), n_views,
-                               d_images, d_depth, d_edge, w, hgt, alpha, eps, depth_tol,
-                               reinterpret_cast<float4 *>(d_texture), d_incidence, scr, s));
+    AG_CUDA(launch_backproject(a.lpos, a.lnrm, a.lface, d_luv, a.rays, a.n_rays, W, H, h_cams, logw.data(), n_views,
+                               d_images, d_depth, d_edge, w, hgt, alpha, eps, depth_tol, o.filter, AG_LOD_BIAS,
+                               AG_MAX_TAPS, AG_SHARPEN, reinterpret_cast<float4 *>(d_texture), d_incidence, scr, s));
     return AG_OK;   // the pageable copies of the cameras and log-weights were staged before returning
 }
 

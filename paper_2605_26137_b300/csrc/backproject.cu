@@ -30,6 +30,8 @@
 // log w_k + alpha log I_k, rescaled sums), so large alpha neither under- nor
 // overflows.
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 
 #include "rays.cuh"
 
@@ -381,9 +383,22 @@ __global__ void k_edge_mask(const float *__restrict__ depth, const Cam *__restri
     edge[r] = e;
 }
 
+// The views' Lanczos-2 pyramids: level 0 is the RGBA8 image itself, levels
+// 1.. (sharpened, RGB in float4) are stored per view at off[l] within a
+// block of `stride` pixels.
+constexpr int MAX_LEV = 16;
+struct Pyramid {
+    int n;                       // levels, level 0 included
+    int w[MAX_LEV], h[MAX_LEV];
+    long long off[MAX_LEV];
+    long long stride;
+    const float4 *S;             // [n_views * stride]
+};
+
 struct BlendArgs {
     const float4 *lpos, *lnrm;
     const int4 *lface;
+    const float *luv;            // per corner [F*3*2] (anisotropic footprint)
     const int4 *rays;
     const long long *n_rays;
     const Cam *cams;
@@ -393,6 +408,10 @@ struct BlendArgs {
     const uint8_t *edge;         // [K*h*w]
     int w, h, n_views, W, H;
     float alpha, eps, depth_tol;
+    int filter;                  // AG_FILTER_*
+    float lod_bias;
+    int max_taps;
+    Pyramid pyr;
     float4 *texture;             // [H*W]: rgb, filled
     float *incidence;            // optional [K*H*W]
 };
@@ -401,6 +420,111 @@ __device__ __forceinline__ float texel_rgb(const uint8_t *img, int w, int h, int
     x = min(max(x, 0), w - 1);
     y = min(max(y, 0), h - 1);
     return (float)img[((long long)y * w + x) * 4 + ch] * (1.0f / 255.0f);
+}
+
+// bilinear RGB of the 8-bit image at image position (u, v): sample point
+// (u - 1/2, v - 1/2) on the pixel-centre grid, clamped to the image
+__device__ __forceinline__ float3 sample_image(const uint8_t *img, int w, int h, float u, float v) {
+    const float x = u - 0.5f, y = v - 0.5f;
+    const float fx0 = floorf(x), fy0 = floorf(y);
+    const float ax = x - fx0, ay = y - fy0;
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    float col[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch)
+        col[ch] = (1.f - ax) * (1.f - ay) * texel_rgb(img, w, h, x0, y0, ch) +
+                  ax * (1.f - ay) * texel_rgb(img, w, h, x0 + 1, y0, ch) +
+                  (1.f - ax) * ay * texel_rgb(img, w, h, x0, y0 + 1, ch) +
+                  ax * ay * texel_rgb(img, w, h, x0 + 1, y0 + 1, ch);
+    return make_float3(col[0], col[1], col[2]);
+}
+
+// bilinear RGB of pyramid level l >= 1 at level-0 image position (u, v)
+__device__ __forceinline__ float3 sample_level(const float4 *lev, int w, int h, int l, float u, float v) {
+    const float sc = __int_as_float((127 - l) << 23);     // 2^-l
+    const float x = u * sc - 0.5f, y = v * sc - 0.5f;
+    const float fx0 = floorf(x), fy0 = floorf(y);
+    const float ax = x - fx0, ay = y - fy0;
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    const int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
+    const int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+    const float4 p00 = lev[(long long)ya * w + xa], p10 = lev[(long long)ya * w + xb];
+    const float4 p01 = lev[(long long)yb * w + xa], p11 = lev[(long long)yb * w + xb];
+    const float w00 = (1.f - ax) * (1.f - ay), w10 = ax * (1.f - ay), w01 = (1.f - ax) * ay, w11 = ax * ay;
+    return make_float3(w00 * p00.x + w10 * p10.x + w01 * p01.x + w11 * p11.x,
+                       w00 * p00.y + w10 * p10.y + w01 * p01.y + w11 * p11.y,
+                       w00 * p00.z + w10 * p10.z + w01 * p01.z + w11 * p11.z);
+}
+
+__device__ __forceinline__ float3 sample_lod(const BlendArgs &A, int k, int l, float u, float v) {
+    if (l == 0) return sample_image(A.images + (long long)k * A.w * A.h * 4, A.w, A.h, u, v);
+    const Pyramid &P = A.pyr;
+    return sample_level(P.S + (long long)k * P.stride + P.off[l], P.w[l], P.h[l], l, u, v);
+}
+
+// anisotropic colour of view k at image position (u, v) for a texel of
+// `face` at surface point p: central-difference footprint of the face's UV
+// -> position map through the projection, its SVD, N taps along the major
+// axis, each a trilinear sample at the level of the (compensated) minor axis
+__device__ float3 aniso_color(const BlendArgs &A, int k, const Cam &c, int face, const int4 &fi, float3 p, float u,
+                              float v) {
+    const float *q = A.luv + 6 * (long long)face;
+    const float x0 = q[0] * A.W, y0 = q[1] * A.H, x1 = q[2] * A.W, y1 = q[3] * A.H, x2 = q[4] * A.W, y2 = q[5] * A.H;
+    const float det = (x1 - x0) * (y2 - y0) - (x2 - x0) * (y1 - y0);
+    bool ok = fabsf(det) * 0.5f >= 1e-4f;
+    float J00 = 0.f, J01 = 0.f, J10 = 0.f, J11 = 0.f;
+    if (ok) {
+        const float b1x = (y2 - y0) / det, b1y = -(x2 - x0) / det;
+        const float b2x = -(y1 - y0) / det, b2y = (x1 - x0) / det;
+        const float3 P0 = f3(A.lpos[fi.x]);
+        const float3 e1 = f3(A.lpos[fi.y]) - P0, e2 = f3(A.lpos[fi.z]) - P0;
+        const float3 dpx = e1 * b1x + e2 * b2x, dpy = e1 * b1y + e2 * b2y;
+        float Ju[2], Jv[2];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            const float3 d = (a ? dpy : dpx) * 0.5f;
+            const float3 pa = p + d, pb = p - d;
+            const float ax_ = c.R[0] * pa.x + c.R[1] * pa.y + c.R[2] * pa.z + c.t[0];
+            const float ay_ = c.R[3] * pa.x + c.R[4] * pa.y + c.R[5] * pa.z + c.t[1];
+            const float az_ = c.R[6] * pa.x + c.R[7] * pa.y + c.R[8] * pa.z + c.t[2];
+            const float bx_ = c.R[0] * pb.x + c.R[1] * pb.y + c.R[2] * pb.z + c.t[0];
+            const float by_ = c.R[3] * pb.x + c.R[4] * pb.y + c.R[5] * pb.z + c.t[1];
+            const float bz_ = c.R[6] * pb.x + c.R[7] * pb.y + c.R[8] * pb.z + c.t[2];
+            ok = ok && az_ > 0.f && bz_ > 0.f;
+            Ju[a] = c.fx * ax_ / az_ - c.fx * bx_ / bz_;
+            Jv[a] = c.fy * ay_ / az_ - c.fy * by_ / bz_;
+        }
+        J00 = Ju[0]; J01 = Ju[1]; J10 = Jv[0]; J11 = Jv[1];
+    }
+    if (!ok) return sample_image(A.images + (long long)k * A.w * A.h * 4, A.w, A.h, u, v);
+    // J J^T = [[a, b], [b, d]]: singular values and the major image direction
+    const float a = J00 * J00 + J01 * J01, b = J00 * J10 + J01 * J11, d = J10 * J10 + J11 * J11;
+    const float half = 0.5f * (a + d), disc = sqrtf(0.25f * (a - d) * (a - d) + b * b);
+    const float l1 = half + disc, l2 = fmaxf(half - disc, 0.f);
+    const float s1 = sqrtf(l1), s2 = sqrtf(l2);
+    float ex, ey;
+    if (b != 0.f) { ex = l1 - d; ey = b; }
+    else if (a >= d) { ex = 1.f; ey = 0.f; }
+    else { ex = 0.f; ey = 1.f; }
+    const float en = rsqrtf(ex * ex + ey * ey);
+    ex *= en; ey *= en;
+    int N = A.max_taps;
+    if (s2 > 0.f) N = (int)fminf(fmaxf(ceilf(s1 / s2 - 0.05f), 1.f), (float)A.max_taps);
+    const float mm = fmaxf(s2, s1 / (float)A.max_taps);
+    float lam = mm > 0.f ? log2f(mm) + A.lod_bias : 0.f;
+    lam = fminf(fmaxf(lam, 0.f), (float)(A.pyr.n - 1));
+    const int l0 = (int)floorf(lam);
+    const float fr = lam - (float)l0;
+    const bool two = l0 < A.pyr.n - 1 && fr > 0.f;
+    float3 acc = make_float3(0.f, 0.f, 0.f);
+    for (int i = 0; i < N; ++i) {
+        const float o = s1 * (((float)i + 0.5f) / (float)N - 0.5f);
+        const float tu = u + ex * o, tv = v + ey * o;
+        float3 sm = sample_lod(A, k, l0, tu, tv);
+        if (two) sm = sm * (1.f - fr) + sample_lod(A, k, l0 + 1, tu, tv) * fr;
+        acc = acc + sm;
+    }
+    return acc * (1.f / (float)N);
 }
 
 __global__ void __launch_bounds__(128) k_backproject(BlendArgs A) {
@@ -435,19 +559,11 @@ __global__ void __launch_bounds__(128) k_backproject(BlendArgs A) {
             const float I = dot3(nrm, normalize3(C - p));
             if (!(I > 0.f)) continue;
             if (A.incidence) A.incidence[(long long)k * A.W * A.H + texel] = I;
-            // bilinear colour at (u - 1/2, v - 1/2), clamped to the image
-            const float x = u - 0.5f, y = v - 0.5f;
-            const float fx0 = floorf(x), fy0 = floorf(y);
-            const float ax = x - fx0, ay = y - fy0;
-            const int x0 = (int)fx0, y0 = (int)fy0;
-            const uint8_t *img = A.images + (long long)k * npix * 4;
-            float col[3];
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch)
-                col[ch] = (1.f - ax) * (1.f - ay) * texel_rgb(img, A.w, A.h, x0, y0, ch) +
-                          ax * (1.f - ay) * texel_rgb(img, A.w, A.h, x0 + 1, y0, ch) +
-                          (1.f - ax) * ay * texel_rgb(img, A.w, A.h, x0, y0 + 1, ch) +
-                          ax * ay * texel_rgb(img, A.w, A.h, x0 + 1, y0 + 1, ch);
+            // colour: anisotropic footprint taps, or one bilinear sample at (u - 1/2, v - 1/2)
+            const float3 cc = A.filter == AG_FILTER_ANISO ? aniso_color(A, k, c, face, fi, p, u, v)
+                                                           : sample_image(A.images + (long long)k * npix * 4, A.w,
+                                                                          A.h, u, v);
+            const float col[3] = {cc.x, cc.y, cc.z};
             // online log-sum-exp: keep den, num as sums of e^(L_k - m)
             const float L = A.logw[k] + A.alpha * logf(I);
             if (L > m) {
@@ -467,6 +583,99 @@ __global__ void __launch_bounds__(128) k_backproject(BlendArgs A) {
         }
         A.texture[texel] = out;
     }
+}
+
+// one 2x Lanczos-2 reduction for every view: level-l pixels 2x-3 .. 2x+4
+// (clamped) with the normalised weights wt, rows first, clamped to [0, 1];
+// the source is the RGBA8 image (level 0) or an unsharpened float level
+struct MipArgs {
+    const uint8_t *img0;
+    const float4 *src;
+    int sw, sh;
+    float4 *dst;
+    int dw, dh, n_views;
+    float wt[8];
+};
+
+__global__ void k_mip_down(MipArgs M) {
+    const long long per = (long long)M.dw * M.dh;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (long long)M.n_views * per) return;
+    const int k = (int)(r / per);
+    const int pix = (int)(r - (long long)k * per);
+    const int x = pix % M.dw, y = pix / M.dw;
+    const long long sper = (long long)M.sw * M.sh;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+    for (int ty = 0; ty < 8; ++ty) {
+        const int j = min(max(2 * y - 3 + ty, 0), M.sh - 1);
+        float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+#pragma unroll
+        for (int tx = 0; tx < 8; ++tx) {
+            const int i = min(max(2 * x - 3 + tx, 0), M.sw - 1);
+            const long long q = (long long)k * sper + (long long)j * M.sw + i;
+            float v0, v1, v2;
+            if (M.img0) {
+                const uint8_t *c = M.img0 + 4 * q;
+                v0 = c[0] * (1.0f / 255.0f); v1 = c[1] * (1.0f / 255.0f); v2 = c[2] * (1.0f / 255.0f);
+            } else {
+                const float4 c = M.src[q];
+                v0 = c.x; v1 = c.y; v2 = c.z;
+            }
+            r0 += M.wt[tx] * v0; r1 += M.wt[tx] * v1; r2 += M.wt[tx] * v2;
+        }
+        a0 += M.wt[ty] * r0; a1 += M.wt[ty] * r1; a2 += M.wt[ty] * r2;
+    }
+    M.dst[r] = make_float4(fminf(fmaxf(a0, 0.f), 1.f), fminf(fmaxf(a1, 0.f), 1.f), fminf(fmaxf(a2, 0.f), 1.f), 0.f);
+}
+
+// the sampled copy of a level: clamp(P + amt (P - B P), 0, 1), B the
+// separable [1, 2, 1] / 4 blur with clamped borders (rows first)
+__global__ void k_mip_sharpen(const float4 *__restrict__ P, int w, int h, int n_views, float amt, float4 *S,
+                              long long s_stride, long long s_off) {
+    const long long per = (long long)w * h;
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (long long)n_views * per) return;
+    const int k = (int)(r / per);
+    const int pix = (int)(r - (long long)k * per);
+    const int x = pix % w, y = pix / w;
+    const int xl = max(x - 1, 0), xr = min(x + 1, w - 1);
+    const float4 *Pk = P + (long long)k * per;
+    float3 bl[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const int yy = min(max(y - 1 + m, 0), h - 1);
+        const float4 l = Pk[(long long)yy * w + xl], c = Pk[(long long)yy * w + x], rr = Pk[(long long)yy * w + xr];
+        bl[m] = make_float3(0.25f * l.x + 0.5f * c.x + 0.25f * rr.x, 0.25f * l.y + 0.5f * c.y + 0.25f * rr.y,
+                            0.25f * l.z + 0.5f * c.z + 0.25f * rr.z);
+    }
+    const float3 b = bl[0] * 0.25f + bl[1] * 0.5f + bl[2] * 0.25f;
+    const float4 c = Pk[pix];
+    const float v0 = c.x + amt * (c.x - b.x), v1 = c.y + amt * (c.y - b.y), v2 = c.z + amt * (c.z - b.z);
+    S[(long long)k * s_stride + s_off + pix] =
+        make_float4(fminf(fmaxf(v0, 0.f), 1.f), fminf(fmaxf(v1, 0.f), 1.f), fminf(fmaxf(v2, 0.f), 1.f), 0.f);
+}
+
+// pyramid sizes for w x h views: level l + 1 has max(1, w_l / 2) x max(1, h_l / 2)
+// pixels, down to 1 x 1 (at most MAX_LEV levels)
+Pyramid pyramid_dims(int w, int h) {
+    Pyramid P;
+    memset(&P, 0, sizeof(P));
+    P.n = 1;
+    P.w[0] = w;
+    P.h[0] = h;
+    P.stride = 0;
+    int pw = w, ph = h;
+    while ((pw > 1 || ph > 1) && P.n < MAX_LEV) {
+        pw = std::max(1, pw / 2);
+        ph = std::max(1, ph / 2);
+        P.w[P.n] = pw;
+        P.h[P.n] = ph;
+        P.off[P.n] = P.stride;
+        P.stride += (long long)pw * ph;
+        ++P.n;
+    }
+    return P;
 }
 
 // blocks of one wave: SMs x resident blocks per SM at this block size
@@ -574,10 +783,32 @@ size_t render_scratch_bytes(int n_views, int w, int h, bool raster) {
     return render_head_bytes(n_views) + (raster ? 12ull * (size_t)w * h * render_chunk_views(n_views, w, h) : 0);
 }
 
-cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const int4 *rays,
-                               const long long *n_rays, int W, int H, const float *h_cams, const float *h_logw,
-                               int n_views, const uint8_t *images, const float *depth, const uint8_t *edge, int w,
-                               int h, float alpha, float eps, float depth_tol, float4 *texture, float *incidence,
+static double lanczos2_host(double x) {
+    if (x == 0.0) return 1.0;
+    if (std::fabs(x) >= 2.0) return 0.0;
+    const double px = 3.14159265358979323846 * x;
+    return 2.0 * std::sin(px) * std::sin(0.5 * px) / (px * px);
+}
+
+// scratch: cameras | log-weights | (anisotropic) pyramid levels | two
+// unsharpened level buffers
+static size_t bp_head_bytes(int n_views) { return ((sizeof(Cam) + sizeof(float)) * (size_t)n_views + 255) / 256 * 256; }
+
+size_t backproject_scratch_bytes(int n_views, int w, int h, int filter) {
+    size_t b = bp_head_bytes(n_views);
+    if (filter == AG_FILTER_ANISO) {
+        const Pyramid P = pyramid_dims(w, h);
+        b += sizeof(float4) * (size_t)n_views * (size_t)P.stride;
+        if (P.n > 1) b += 2 * sizeof(float4) * (size_t)n_views * (size_t)P.w[1] * P.h[1];
+    }
+    return b;
+}
+
+cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const float *luv,
+                               const int4 *rays, const long long *n_rays, int W, int H, const float *h_cams,
+                               const float *h_logw, int n_views, const uint8_t *images, const float *depth,
+                               const uint8_t *edge, int w, int h, float alpha, float eps, float depth_tol, int filter,
+                               float lod_bias, int max_taps, float sharpen, float4 *texture, float *incidence,
                                void *scratch, cudaStream_t s) {
     Cam *d_cams = static_cast<Cam *>(scratch);
     float *d_logw = reinterpret_cast<float *>(d_cams + n_views);
@@ -589,9 +820,38 @@ cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int
     if (incidence && (e = cudaMemsetAsync(incidence, 0, sizeof(float) * (size_t)n_views * W * H, s)) != cudaSuccess)
         return e;
     BlendArgs A;
+    memset(&A, 0, sizeof(A));
+    A.pyr = pyramid_dims(w, h);
+    if (filter == AG_FILTER_ANISO && A.pyr.n > 1) {
+        float4 *S = reinterpret_cast<float4 *>(static_cast<char *>(scratch) + bp_head_bytes(n_views));
+        float4 *ping = S + (size_t)n_views * (size_t)A.pyr.stride;
+        float4 *pong = ping + (size_t)n_views * (size_t)A.pyr.w[1] * A.pyr.h[1];
+        MipArgs M;
+        double wt[8], sw = 0.0;
+        for (int t = 0; t < 8; ++t) { wt[t] = lanczos2_host((t - 3.5) / 2.0); sw += wt[t]; }
+        for (int t = 0; t < 8; ++t) M.wt[t] = (float)(wt[t] / sw);
+        M.n_views = n_views;
+        for (int l = 1; l < A.pyr.n; ++l) {
+            M.img0 = l == 1 ? images : nullptr;
+            M.src = l == 1 ? nullptr : (l % 2 == 0 ? ping : pong);
+            M.sw = A.pyr.w[l - 1];
+            M.sh = A.pyr.h[l - 1];
+            M.dst = l % 2 == 1 ? ping : pong;
+            M.dw = A.pyr.w[l];
+            M.dh = A.pyr.h[l];
+            const long long n = (long long)n_views * M.dw * M.dh;
+            k_mip_down<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            k_mip_sharpen<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M.dst, M.dw, M.dh, n_views, sharpen, S,
+                                                                     A.pyr.stride, A.pyr.off[l]);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        A.pyr.S = S;
+    }
     A.lpos = lpos;
     A.lnrm = lnrm;
     A.lface = lface;
+    A.luv = luv;
     A.rays = rays;
     A.n_rays = n_rays;
     A.cams = d_cams;
@@ -607,6 +867,9 @@ cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int
     A.alpha = alpha;
     A.eps = eps;
     A.depth_tol = depth_tol;
+    A.filter = filter;
+    A.lod_bias = lod_bias;
+    A.max_taps = max_taps;
     A.texture = texture;
     A.incidence = incidence;
     int dev;
@@ -614,7 +877,5 @@ cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int
     k_backproject<<<resident_grid(k_backproject, 128, dev), 128, 0, s>>>(A);
     return cudaGetLastError();
 }
-
-size_t backproject_scratch_bytes(int n_views) { return (sizeof(Cam) + sizeof(float)) * (size_t)n_views + 16; }
 
 }  // namespace ag

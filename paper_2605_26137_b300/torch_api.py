@@ -406,10 +406,12 @@ def render_views(bvh: Bvh, cams, w: int, h: int, *, edge_tol: float, points: boo
 
 def backproject(low_verts, low_faces, low_uv, W: int, H: int, cams, weights, images, depth, edge, *,
                 alpha: float, eps: float, depth_tol: float, low_normals=None, incidence: bool = False,
-                ray_tile="8x8", stream=None):
+                filter: str = "aniso", ray_tile="8x8", stream=None):
     """Blended texture [H,W,4] f32 (RGB, 1 where filled) of K views (images
     [K,h,w,4] u8, depth / edge from render_views, cams [K,16] and weights [K]
-    host numpy) on the low mesh's atlas; with ``incidence`` also [K,H,W]."""
+    host numpy) on the low mesh's atlas; with ``incidence`` also [K,H,W].
+    filter: "aniso" (footprint taps over each view's Lanczos-2 pyramid) or
+    "bilinear" (one sample)."""
     import numpy as np
     lib = _lib.load()
     _check_low(low_verts, low_faces, low_uv, low_normals)
@@ -424,6 +426,7 @@ def backproject(low_verts, low_faces, low_uv, W: int, H: int, cams, weights, ima
     tex = torch.empty((H, W, 4), dtype=torch.float32, device=low_verts.device)
     inc = torch.empty((K, H, W), dtype=torch.float32, device=low_verts.device) if incidence else None
     o = _opts(ray_tile=ray_tile)
+    o.filter = {"aniso": _lib.AG_FILTER_ANISO, "bilinear": _lib.AG_FILTER_BILINEAR}[filter]
     check(lib.ag_backproject(low_verts.data_ptr(), _ptr(low_normals), low_uv.data_ptr(), low_faces.data_ptr(),
                              low_verts.shape[0], low_faces.shape[0], W, H, K, cams.ctypes.data, weights.ctypes.data,
                              images.data_ptr(), depth.data_ptr(), edge.data_ptr(), w, h, float(alpha), float(eps),

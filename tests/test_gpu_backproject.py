@@ -132,8 +132,8 @@ def test_render_modes_against_oracle():
     bvh.free()
 
 
-@pytest.mark.parametrize("alpha,eps", [(6.0, 1e-6), (40.0, 1e-30)])
-def test_backproject_on_oracle_views(alpha, eps):
+@pytest.mark.parametrize("alpha,eps,filt", [(6.0, 1e-6, "aniso"), (40.0, 1e-30, "aniso"), (6.0, 1e-6, "bilinear")])
+def test_backproject_on_oracle_views(alpha, eps, filt):
     """The blend step alone: the kernel reads the oracle's depth buffers (as
     FP32) and edge masks, so a pixel whose render depends on rounding cannot
     change the comparison; only texels within rounding of a pixel boundary,
@@ -150,10 +150,11 @@ def test_backproject_on_oracle_views(alpha, eps):
     edge_o = oracle.edge_mask(depth_o, point_o, edge_tol)
     images = synth.view_images(point_o)
     o = oracle.backproject(lv, lf, a.low_uv, a.W, a.H, cams, images, weights, alpha=alpha, eps=eps,
-                           depth_tol=0.01 * scale, edge_tol=edge_tol, views=(depth_o, point_o, np.zeros_like(near_o)))
+                           depth_tol=0.01 * scale, edge_tol=edge_tol, views=(depth_o, point_o, np.zeros_like(near_o)),
+                           filter=filt)
     tex, inc = pb.backproject(_t(lv), _t(lf), _t(a.low_uv), a.W, a.H, cams, weights, _t(images),
                               _t(depth_o.astype(np.float32)), _t(edge_o), alpha=alpha, eps=eps,
-                              depth_tol=0.01 * scale, incidence=True)
+                              depth_tol=0.01 * scale, incidence=True, filter=filt)
     pb.sync_status()
     g = dict(texture=tex.cpu().numpy(), incidence=inc.cpu().numpy())
     assert check_texture(g, o) > 0.93
@@ -221,3 +222,52 @@ def test_argument_errors():
         pb.backproject(_t(a.low_v), _t(a.low_f), _t(a.low_uv), a.W, a.H, cams[:5], weights, imgs, depth, edge,
                        alpha=2.0, eps=1e-6, depth_tol=0.01)
     bvh.free()
+
+
+def _planar(n, size, s):
+    xs = np.linspace(-size, size, n + 1)
+    X, Y = np.meshgrid(xs, xs)
+    V = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], -1).astype(np.float32)
+    F = np.asarray([(j * (n + 1) + i, j * (n + 1) + i + 1, j * (n + 1) + i + n + 2) for j in range(n) for i in range(n)] +
+                   [(j * (n + 1) + i, j * (n + 1) + i + n + 2, j * (n + 1) + i + n + 1) for j in range(n) for i in range(n)],
+                   np.int32)
+    uv = (V[F][:, :, :2].astype(np.float64) * s + 0.5).astype(np.float32)
+    return V, F, uv
+
+
+@pytest.mark.parametrize("case", ["oblique", "far"])
+def test_aniso_footprints(case):
+    """The anisotropic filter against the oracle where it does most: a plane
+    65 degrees off the view axis (two or three taps along the major axis) and
+    a plane far away (footprints of several pixels: trilinear between pyramid
+    levels), each filling a ragged-size view with a seeded random image."""
+    import paper_2605_26137_b300 as pb
+    import math
+    rng = np.random.default_rng(9)
+    if case == "oblique":
+        size, n, W, w, h = 10.0, 8, 512, 61, 47
+        a = math.radians(65.0)
+        cam = synth.look_at_camera([0.0, -4 * math.sin(a), 4 * math.cos(a)], [0, 0, 0], [0, 1, 0], 30.0, w, h)
+    else:
+        size, n, W, w, h = 1.0, 4, 256, 70, 52
+        D, f = 3.0, 4.5 * 0.45 * 256 * 3.0
+        R = np.array([[1, 0, 0], [0, -1, 0], [0, 0, -1]], np.float64)
+        cam = np.concatenate([R.ravel(), -R @ [0, 0, D], [f, f, w / 2, h / 2]]).astype(np.float32)
+    V, F, uv = _planar(n, size, 0.45 / size)
+    img = np.zeros((1, h, w, 4), np.uint8)
+    img[0, ..., :3] = rng.integers(0, 256, (h, w, 3))
+    img[0, ..., 3] = 255
+    depth_o, point_o, near_o = oracle.render_views(V, F, cam[None], w, h)
+    edge_o = oracle.edge_mask(depth_o, point_o, 10.0)
+    kw = dict(alpha=1.0, eps=0.0, depth_tol=0.05)
+    o = oracle.backproject(V, F, uv, W, W, cam[None], img, np.ones(1, np.float32), edge_tol=10.0,
+                           views=(depth_o, point_o, near_o), **kw)
+    tex = pb.backproject(_t(V), _t(F), _t(uv), W, W, cam[None], np.ones(1, np.float32), _t(img),
+                         _t(depth_o.astype(np.float32)), _t(edge_o), **kw)
+    pb.sync_status()
+    g = tex.cpu().numpy()
+    ok = (o["face"] >= 0) & (o["flags"] == 0) & o["filled"].astype(bool)
+    assert ok.sum() > (2000 if case == "oblique" else 100)
+    assert np.array_equal(g[..., 3][ok] > 0.5, np.ones(ok.sum(), bool))
+    err = np.abs(g[..., :3][ok] - o["texture"][ok])
+    assert err.max() <= TOL_TEX, err.max()

@@ -10,7 +10,11 @@
   underflow, still picks the better view (the log-space reduction);
 * back-facing surfaces, points behind a camera and edge pixels (depth
   discontinuities) contribute nothing;
-* the rendered depth of a plane is its distance along the view axis.
+* the rendered depth of a plane is its distance along the view axis;
+* anisotropic filtering: the Lanczos-2 pyramid against numpy's sinc (a ramp,
+  a constant, one bright pixel), the taps of an oblique footprint against the
+  exact derivative of the projection and numpy's SVD, and the trilinear level
+  of a far face-on footprint against numpy bilinear samples of the pyramid.
 """
 import math
 
@@ -206,3 +210,141 @@ def test_backfacing_behind_camera_and_edges():
     v = np.floor(-60 * p[:, 1] / 3.0 + h / 2).astype(int)
     on_rim = rim[v.clip(0, h - 1), u.clip(0, w - 1)]
     assert on_rim.sum() > 20 and not o["filled"][m][on_rim].any()
+
+
+# ---------------------------------------------------------------- anisotropic filtering
+
+def _planar(n, size, s):
+    """A flat grid in z = 0 with a planar atlas: uv = (x, y) * s + 1/2 per
+    corner (one chart, similar to the surface, so texels are square on it)."""
+    V, F = _plane(n, size=size)
+    uv = (V[F][:, :, :2].astype(np.float64) * s + 0.5).astype(np.float32)
+    return V, F, uv
+
+
+def _bilinear(level, x, y):
+    """Plain bilinear sample of an [h,w,3] array at continuous (x, y), pixel
+    centres on the integer grid, clamped to the edge."""
+    h, w = level.shape[:2]
+    x0, y0 = np.floor(x).astype(int), np.floor(y).astype(int)
+    ax, ay = x - x0, y - y0
+    out = 0.0
+    for dy in (0, 1):
+        for dx in (0, 1):
+            xx = np.clip(x0 + dx, 0, w - 1)
+            yy = np.clip(y0 + dy, 0, h - 1)
+            out = out + ((ax if dx else 1 - ax) * (ay if dy else 1 - ay))[..., None] * level[yy, xx]
+    return out
+
+
+def test_mip_pyramid_lanczos2():
+    w, h = 100, 60
+    img = np.zeros((h, w, 4), np.uint8)
+    img[..., :3] = 77
+    img[..., 3] = 255
+    levels = oracle.mip_levels(img)
+    assert [(P.shape[1], P.shape[0]) for P, _ in levels] == [(50, 30), (25, 15), (12, 7), (6, 3), (3, 1), (1, 1)]
+    for P, S in levels:     # a constant stays constant, sharpened or not
+        assert np.abs(P - 77 / 255).max() < 1e-12 and np.abs(S - 77 / 255).max() < 1e-12
+    # a ramp in x: away from the border, level 1 is the ramp at the new pixel centres (X = 2j + 1)
+    x = np.arange(w)
+    img[..., 0] = 2 * x + 10
+    P1, S1 = oracle.mip_levels(img)[0]
+    j = np.arange(50)
+    interior = (2 * j - 3 >= 0) & (2 * j + 4 <= w - 1)
+    assert np.abs(P1[:, interior, 0] - (4 * j[interior] + 11) / 255).max() < 1e-12
+    # the [1,2,1] unsharp mask leaves a ramp alone one pixel farther in
+    inner = interior & np.roll(interior, 1) & np.roll(interior, -1)
+    assert np.abs(S1[:, inner, 0] - P1[:, inner, 0]).max() < 1e-12
+    # one brighter pixel on grey: level 1 holds the separable, normalised Lanczos-2 weights
+    img[..., :3] = 128
+    i0, j0 = 41, 27
+    img[j0, i0, 0] = 228
+    P1 = oracle.mip_levels(img)[0][0]
+    t = np.arange(8)
+    wt = np.sinc((t - 3.5) / 2) * np.sinc((t - 3.5) / 4)
+    wt /= wt.sum()
+    tx = i0 - 2 * np.arange(50) + 3
+    ty = j0 - 2 * np.arange(30) + 3
+    wx = np.where((tx >= 0) & (tx < 8), wt[np.clip(tx, 0, 7)], 0.0)
+    wy = np.where((ty >= 0) & (ty < 8), wt[np.clip(ty, 0, 7)], 0.0)
+    assert np.abs(P1[..., 0] - (128 + 100 * wy[:, None] * wx[None, :]) / 255).max() < 1e-12
+    assert np.abs(P1[..., 1] - 128 / 255).max() < 1e-12
+
+
+def test_aniso_taps_follow_the_footprint():
+    """A plane seen 65 degrees off its normal through an image whose codes
+    vary along u only: the colour is the mean of N equally spaced samples
+    along the major axis of the texel's image footprint.  The expectation uses
+    the exact derivative of the projection and numpy's SVD."""
+    size, n, W = 10.0, 8, 512
+    s = 0.45 / size
+    V, F, uv = _planar(n, size, s)
+    w = h = 48
+    a = math.radians(65.0)
+    eye = np.array([0.0, -4 * math.sin(a), 4 * math.cos(a)])
+    cam = synth.look_at_camera(eye, [0, 0, 0], [0, 1, 0], 30.0, w, h)
+    codes = (37 * np.arange(w) + 11) % 256
+    img = np.zeros((1, h, w, 4), np.uint8)
+    img[0, ..., 0] = codes[None, :]
+    img[0, ..., 3] = 255
+    kw = dict(alpha=1.0, eps=0.0, depth_tol=0.05, edge_tol=10.0)
+    o = oracle.backproject(V, F, uv, W, W, cam[None], img, np.ones(1, np.float32), **kw)
+    ob = oracle.backproject(V, F, uv, W, W, cam[None], img, np.ones(1, np.float32), filter="bilinear", **kw)
+    m, p = _texel_points(o, V, F)
+    R = cam[:9].astype(np.float64).reshape(3, 3)
+    t = cam[9:12].astype(np.float64)
+    fx, fy, cx, cy = (float(q) for q in cam[12:])
+    c = p @ R.T + t
+    u = fx * c[:, 0] / c[:, 2] + cx
+    du = fx * (R[0][None] * c[:, 2:3] - c[:, 0:1] * R[2][None]) / c[:, 2:3] ** 2
+    dv = fy * (R[1][None] * c[:, 2:3] - c[:, 1:2] * R[2][None]) / c[:, 2:3] ** 2
+    dp = np.array([[1 / (s * W), 0.0], [0.0, 1 / (s * W)], [0.0, 0.0]])     # world per texel (x, y)
+    J = np.stack([du @ dp, dv @ dp], 1)                                     # [n, 2 (u, v), 2 (x, y)]
+    U, S, _ = np.linalg.svd(J)
+    ratio = S[:, 0] / S[:, 1]
+    N = np.clip(np.ceil(ratio - 0.05), 1, 8).astype(int)
+    lam = np.log2(np.maximum(S[:, 1], S[:, 0] / 8)) - 0.5
+    expect = np.zeros(len(p))
+    for k in range(len(p)):
+        taps = u[k] + U[k, 0, 0] * S[k, 0] * ((np.arange(N[k]) + 0.5) / N[k] - 0.5)
+        expect[k] = np.mean(np.interp(taps - 0.5, np.arange(w), codes / 255))
+    near = np.abs(ratio - 0.05 - np.round(ratio - 0.05)) < 1e-3
+    ok = o["filled"][m].astype(bool) & (o["flags"][m] == 0) & ~near & (lam <= 0)
+    assert ok.sum() > 2000 and (N[ok] >= 2).mean() > 0.9     # mostly two or three taps along u
+    tex = o["texture"][m]
+    assert np.abs(tex[ok, 0] - expect[ok]).max() < 1e-6
+    # the single bilinear sample is a different (unfiltered) value
+    assert np.abs(ob["texture"][m][ok, 0] - expect[ok]).max() > 0.05
+
+
+def test_aniso_level_of_detail_trilinear():
+    """A plane seen face-on from far away (an affine, isotropic footprint of
+    4.5 pixels per texel): one tap, level log2(4.5) - 1/2 between pyramid
+    levels 1 and 2, blended linearly."""
+    size, n, W = 1.0, 4, 256
+    s = 0.45 / size
+    V, F, uv = _planar(n, size, s)
+    w = h = 64
+    D = 3.0
+    sigma = 4.5
+    f = sigma * s * W * D                 # pixels per texel = f / D * (1 / (s W))
+    cam = _front_camera(D, w, h, f)
+    rng = np.random.default_rng(5)
+    img = np.zeros((1, h, w, 4), np.uint8)
+    img[0, ..., :3] = rng.integers(0, 256, (h, w, 3))
+    img[0, ..., 3] = 255
+    o = oracle.backproject(V, F, uv, W, W, cam[None], img, np.ones(1, np.float32), alpha=1.0, eps=0.0,
+                           depth_tol=0.05, edge_tol=10.0)
+    m, p = _texel_points(o, V, F)
+    u = f * p[:, 0] / D + w / 2
+    v = -f * p[:, 1] / D + h / 2
+    lam = math.log2(sigma) - 0.5
+    fr = lam - 1
+    S1 = oracle.mip_levels(img[0])[0][1]
+    S2 = oracle.mip_levels(img[0])[1][1]
+    expect = (1 - fr) * _bilinear(S1, u / 2 - 0.5, v / 2 - 0.5) + fr * _bilinear(S2, u / 4 - 0.5, v / 4 - 0.5)
+    inside = (u > 0) & (u < w) & (v > 0) & (v < h)
+    ok = o["filled"][m].astype(bool) & (o["flags"][m] == 0) & inside
+    assert ok.sum() > 50
+    assert np.abs(o["texture"][m][ok] - expect[ok]).max() < 1e-6
