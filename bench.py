@@ -699,6 +699,11 @@ def hidden_leg(args, pb, torch, dev, flush):
     pb.sync_status()
     vis_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     fill_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    # every ray traced through the BVH (the paper's formulation), for comparison
+    vis_t, _, _ = pb.visibility(bvh, nv, nres, render="trace")
+    trace_ms = statistics.mean(timed(torch, lambda: pb.visibility(bvh, nv, nres, render="trace"), steps, 1, flush))
+    pb.sync_status()
+    same_mask = bool(torch.equal(vis_t, vis))
     info = bvh.info()
     bvh.free()
     visn, extn = vis.cpu().numpy().astype(bool), ext.cpu().numpy().astype(bool)
@@ -706,7 +711,9 @@ def hidden_leg(args, pb, torch, dev, flush):
     return {"mesh": {"faces": int(len(F)), "interior_shell_faces": int(inner.sum()), "bvh_build_ms": info["build_ms"]},
             "views": nv, "res": nres, "rays": int(rays),
             "visibility_ms": vis_ms, "fill_ms": fill_ms, "total_ms": vis_ms + fill_ms,
-            "grays_s": rays / vis_ms / 1e6,
+            "grays_s": rays / vis_ms / 1e6, "visibility_traced_ms": trace_ms,
+            "mask_equal_to_traced": same_mask,
+            "visibility": "z-buffer proposals confirmed by the watertight ray test (rejected pixels traced)",
             "per_ray": {"nodes": c[1] / c[0], "tris": c[2] / c[0], "hit_frac": c[3] / c[0]},
             "faces_visible": int(visn.sum()), "faces_exterior": int(extn.sum()),
             "interior_shell_faces_kept": int(extn[inner].sum()),

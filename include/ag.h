@@ -90,7 +90,9 @@ enum { AG_QUERY_RAY = 0, AG_QUERY_CLOSEST = 1 };
  *                     test confirms it, and only a pixel whose proposal the
  *                     test rejects (a centre within rounding of an edge) is
  *                     traced through the BVH; a view in which a triangle
- *                     reaches the camera plane is traced whole.
+ *                     reaches the camera plane is traced whole.  The buffers
+ *                     equal AG_RENDER_TRACE's except where two triangles lie
+ *                     within rounding of each other along a pixel's ray.
  *  AG_RENDER_TRACE  - every pixel traced through the BVH. */
 enum { AG_RENDER_RASTER = 0, AG_RENDER_TRACE = 1 };
 
@@ -342,8 +344,13 @@ AG_API ag_status ag_autotune(ag_bvh_t h, const float *d_lverts, const float *d_l
  *              face of pixel (i, j) of view k at k*res*res + j*res + i, -1
  *              on a miss (for tests and debugging; 4 bytes per ray).
  *   d_counters optional [4] u64, device, accumulated: rays, node visits,
- *              triangle tests, hits (selects the counting build).
- *   opts: block_size (64..256), blocks_per_sm, max_steps are used.
+ *              triangle tests, hits (selects the counting build, which
+ *              traces every ray).
+ *   opts: render (AG_RENDER_RASTER: z-buffer proposals of the orthographic
+ *   views confirmed by the ray test, the other pixels traced: the first hits
+ *   of tracing every ray except where two triangles lie within rounding of
+ *   each other along a ray; AG_RENDER_TRACE: every ray traced),
+ *   block_size (64..256), blocks_per_sm (tracing), max_steps are used.
  *   Errors: AG_ERR_BAD_HANDLE, AG_ERR_INVALID_ARG (n_views outside 1..2^20,
  *   res outside 1..16384, n_views * ceil(res/8) * ceil(res/4) >= 2^31, NULL
  *   d_visible); the step cap sets the status word.

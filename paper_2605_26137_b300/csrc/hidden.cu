@@ -23,6 +23,7 @@
 // face) does not depend on the visiting order.
 #include "rays.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -85,6 +86,61 @@ __device__ __forceinline__ bool meets_scene(const VisArgs &A, const Ray &r) {
     return te <= tx && te <= A.tmax && tx >= -A.tmax;
 }
 
+// the ray of pixel (px, py) of a view: the view's template (direction part)
+// with the pixel's offset in the view plane as origin offset
+__device__ __forceinline__ Ray vis_ray(const VisArgs &A, int view, int px, int py) {
+    const ViewGeom G = A.views[view];
+    const float x = __fmaf_rn((float)px + 0.5f, A.scale, -A.R);
+    const float y = __fmaf_rn((float)py + 0.5f, A.scale, -A.R);
+    const float3 off = f3(G.e1) * x + f3(G.e2) * y;
+    Ray ray = A.templ[view];
+    ray.ox = pick(off, ray.kx); ray.oy = pick(off, ray.ky); ray.oz = pick(off, ray.kz);
+    const float3 p = f3(G.base) + off;
+    ray.px = p.x; ray.py = p.y; ray.pz = p.z;
+    return ray;
+}
+
+// the closest hit of one visibility ray through the BVH
+template <int LAYOUT, bool COUNT>
+__device__ __forceinline__ Best trace_vis(const VisArgs &A, const Ray &ray, uint2 *stack, unsigned long long &c_nodes,
+                                          unsigned long long &c_tris) {
+    Best b;
+    b.t = 0.f; b.babs = A.tmax; b.rec = 0; b.found = false;
+    b.U = b.V = b.W = 0.f; b.det = 1.f;
+    uint32_t cur = 0;
+    int sp = 0, steps = 0;
+    for (bool live = meets_scene(A, ray); live;) {
+        Next nx;
+        nx.has = false;
+        nx.ref = 0;
+        nx.dist = 0.f;
+        if (ref_is_leaf(cur)) {
+            const uint32_t first = ref_first(cur);
+            const int cnt = ref_count(cur);
+            for (int k = 0; k < cnt; ++k) test_tri(ray, A.tris, A.tri_ids, first + k, b);
+            if (COUNT) c_tris += cnt;
+        } else {
+            visit_node<LAYOUT>(A, cur, ray, b.babs, nx, stack, sp);
+            if (COUNT) ++c_nodes;
+        }
+        if (nx.has) {
+            cur = nx.ref;
+        } else {
+            bool done = true;
+            while (sp > 0) {
+                uint2 e = stack[--sp];
+                if (__uint_as_float(e.y) <= b.babs) { cur = e.x; done = false; break; }
+            }
+            if (done) break;
+        }
+        if (++steps > A.max_steps) {
+            atomicOr(A.status, AGS_STEP_CAP);
+            live = false;
+        }
+    }
+    return b;
+}
+
 template <int LAYOUT, bool COUNT>
 __global__ void __launch_bounds__(256) k_visibility(VisArgs A) {
     const int lane = threadIdx.x & 31;
@@ -102,52 +158,9 @@ __global__ void __launch_bounds__(256) k_visibility(VisArgs A) {
         const int px = (t - ty * A.tiles_x) * 8 + (lane & 7);
         const int py = ty * 4 + (lane >> 3);
         if (px >= A.res || py >= A.res) continue;
-        const ViewGeom G = A.views[view];
-        const float x = __fmaf_rn((float)px + 0.5f, A.scale, -A.R);
-        const float y = __fmaf_rn((float)py + 0.5f, A.scale, -A.R);
-        const float3 off = f3(G.e1) * x + f3(G.e2) * y;
-        Ray ray = A.templ[view];
-        {
-            const float3 base = f3(G.base);
-            ray.ox = pick(off, ray.kx); ray.oy = pick(off, ray.ky); ray.oz = pick(off, ray.kz);
-            const float3 p = base + off;
-            ray.px = p.x; ray.py = p.y; ray.pz = p.z;
-        }
-        Best b;
-        b.t = 0.f; b.babs = A.tmax; b.rec = 0; b.found = false;
-        b.U = b.V = b.W = 0.f; b.det = 1.f;
-        uint32_t cur = 0;
-        int sp = 0, steps = 0;
+        const Ray ray = vis_ray(A, view, px, py);
         if (COUNT) ++c_rays;
-        for (bool live = meets_scene(A, ray); live;) {
-            Next nx;
-            nx.has = false;
-            nx.ref = 0;
-            nx.dist = 0.f;
-            if (ref_is_leaf(cur)) {
-                const uint32_t first = ref_first(cur);
-                const int cnt = ref_count(cur);
-                for (int k = 0; k < cnt; ++k) test_tri(ray, A.tris, A.tri_ids, first + k, b);
-                if (COUNT) c_tris += cnt;
-            } else {
-                visit_node<LAYOUT>(A, cur, ray, b.babs, nx, stack, sp);
-                if (COUNT) ++c_nodes;
-            }
-            if (nx.has) {
-                cur = nx.ref;
-            } else {
-                bool done = true;
-                while (sp > 0) {
-                    uint2 e = stack[--sp];
-                    if (__uint_as_float(e.y) <= b.babs) { cur = e.x; done = false; break; }
-                }
-                if (done) break;
-            }
-            if (++steps > A.max_steps) {
-                atomicOr(A.status, AGS_STEP_CAP);
-                live = false;
-            }
-        }
+        const Best b = trace_vis<LAYOUT, COUNT>(A, ray, stack, c_nodes, c_tris);
         const int id = b.found ? A.tri_ids[b.rec] : -1;
         if (b.found) {
             A.visible[id] = 1;
@@ -168,6 +181,213 @@ __global__ void __launch_bounds__(256) k_visibility(VisArgs A) {
             atomicAdd(&A.counters[2], c_tris);
             atomicAdd(&A.counters[3], c_hits);
         }
+    }
+}
+
+// ---- z-buffer proposals for the orthographic views (AG_RENDER_RASTER).
+// One lane per (view, triangle): the vertices in pixel units of the view
+// plane, X = ((p - base) . e1 + R) / scale (pixel centre i + 1/2 <-> X = i + 1/2),
+// ray parameter t = (p - base) . dir; edge functions from the lexicographically
+// smaller endpoint (a shared edge gets exactly opposite values), t at a pixel
+// centre from the barycentrics the edge values give; the warp walks its
+// triangles' pixel boxes, a 64-bit atomicMin of (t bits, record) per covered
+// centre.  Only a proposal the watertight test confirms is taken; the other
+// pixels go to the traversal.  The first hits are the traversal's except
+// where two triangles lie within rounding of each other along the ray (a
+// shared edge, touching sheets).
+constexpr unsigned long long VIS_NO_KEY = ~0ull;
+
+struct VisRaster {
+    const float4 *tris;
+    int n_tris;
+    const ViewGeom *views;
+    int res, v0, nv;
+    float R, scale;
+    unsigned long long *keys;   // [nv * res * res]
+    unsigned *next;             // work counter of this chunk (zero before the launch)
+};
+
+struct VisTri {
+    float ax[3], ay[3], dx[3], dy[3];
+    float t[3];                  // ray parameter of the vertex opposite each edge
+    float inv_area;
+    int x0, y0, bw;
+    float rbw;
+    unsigned flip, rec, cnt;
+};
+
+__device__ __forceinline__ float vis_edge(float ax, float ay, float dx, float dy, float px, float py) {
+    return __fsub_rn(__fmul_rn(dx, __fsub_rn(py, ay)), __fmul_rn(dy, __fsub_rn(px, ax)));
+}
+
+// persistent warps take (view, 32-triangle group) items from a counter, so
+// the last wave is balanced at the grain of one group
+__global__ void __launch_bounds__(256) k_vis_zbuffer(VisRaster A) {
+    __shared__ VisTri ts[256];
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    const int groups = (A.n_tris + 31) / 32;
+    const unsigned total = (unsigned)A.nv * (unsigned)groups;
+    const float rs = 1.0f / A.scale;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(A.next, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        const int kv = (int)(item / (unsigned)groups);
+        const int tri = (int)(item - (unsigned)kv * groups) * 32 + lane;
+        const ViewGeom G = A.views[A.v0 + kv];
+        VisTri T;
+        T.cnt = 0;
+        if (tri < A.n_tris) {
+            float X[3], Y[3], Z[3];
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float4 p = __ldg(&A.tris[3 * (size_t)tri + m]);
+                const float3 d = make_float3(p.x - G.base.x, p.y - G.base.y, p.z - G.base.z);
+                X[m] = (d.x * G.e1.x + d.y * G.e1.y + d.z * G.e1.z + A.R) * rs;
+                Y[m] = (d.x * G.e2.x + d.y * G.e2.y + d.z * G.e2.z + A.R) * rs;
+                Z[m] = d.x * G.dir.x + d.y * G.dir.y + d.z * G.dir.z;
+            }
+            const float area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+            T.flip = 0;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const int q = m == 2 ? 0 : m + 1;
+                const bool sw = X[q] < X[m] || (X[q] == X[m] && Y[q] < Y[m]);
+                const int a = sw ? q : m, b = sw ? m : q;
+                T.ax[m] = X[a];
+                T.ay[m] = Y[a];
+                T.dx[m] = X[b] - X[a];
+                T.dy[m] = Y[b] - Y[a];
+                T.flip |= (unsigned)(sw != (area < 0.f)) << m;
+                T.t[m] = Z[m == 0 ? 2 : m - 1];     // edge m (vertex m -> m+1) weighs the vertex m+2
+            }
+            T.inv_area = 1.0f / fabsf(area);
+            T.rec = (unsigned)tri;
+            const float lo_x = fminf(X[0], fminf(X[1], X[2])), hi_x = fmaxf(X[0], fmaxf(X[1], X[2]));
+            const float lo_y = fminf(Y[0], fminf(Y[1], Y[2])), hi_y = fmaxf(Y[0], fmaxf(Y[1], Y[2]));
+            const int x0 = (int)fmaxf(ceilf(lo_x - 0.5f), 0.f), x1 = (int)fminf(floorf(hi_x - 0.5f), (float)(A.res - 1));
+            const int y0 = (int)fmaxf(ceilf(lo_y - 0.5f), 0.f), y1 = (int)fminf(floorf(hi_y - 0.5f), (float)(A.res - 1));
+            T.x0 = x0;
+            T.y0 = y0;
+            T.bw = x1 - x0 + 1;
+            T.rbw = 1.0f / (float)T.bw;
+            if (area != 0.f && x1 >= x0 && y1 >= y0) T.cnt = (unsigned)(x1 - x0 + 1) * (unsigned)(y1 - y0 + 1);
+        }
+        __syncwarp();
+        ts[threadIdx.x] = T;
+        __syncwarp();
+        unsigned long long *keys = A.keys + (long long)kv * A.res * A.res;
+        for (int q = 0; q < 32; ++q) {
+            const VisTri &S = ts[wbase + q];
+            const unsigned n = S.cnt;
+            if (n == 0) continue;
+            const int bw = S.bw;
+            for (unsigned o = lane; o < n; o += 32) {
+                // o = y * bw + x (see the view raster of the backprojection)
+                int yy, xx;
+                if (n <= (1u << 24)) {
+                    yy = (int)((float)o * S.rbw);
+                    xx = (int)o - yy * bw;
+                    if (xx < 0) { --yy; xx += bw; } else if (xx >= bw) { ++yy; xx -= bw; }
+                } else {
+                    yy = (int)(o / (unsigned)bw);
+                    xx = (int)o - yy * bw;
+                }
+                const int i = S.x0 + xx, j = S.y0 + yy;
+                const float px = (float)i + 0.5f, py = (float)j + 0.5f;
+                float e[3];
+                bool in = true;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    const float v = vis_edge(S.ax[m], S.ay[m], S.dx[m], S.dy[m], px, py);
+                    e[m] = ((S.flip >> m) & 1u) ? -v : v;
+                    in = in && e[m] >= 0.f;
+                }
+                if (!in) continue;
+                const float t = (e[0] * S.t[0] + e[1] * S.t[1] + e[2] * S.t[2]) * S.inv_area;
+                if (!(t > 0.f) || !(t < 3.0e38f)) continue;
+                atomicMin(&keys[(long long)j * A.res + i], ((unsigned long long)__float_as_uint(t) << 32) | S.rec);
+            }
+        }
+    }
+}
+
+// proposals confirmed by the watertight test mark their face; the others go
+// to the deferred trace list (global pixel index, warp-aggregated append).
+// The keys are reset behind the read for the next chunk.  A list that would
+// overflow sets the chunk's flag instead, and the whole chunk is traced.
+__global__ void __launch_bounds__(256) k_vis_resolve(VisArgs A, unsigned long long *__restrict__ keys, int v0,
+                                                     unsigned long long *list, unsigned long long cap,
+                                                     unsigned long long *count, int *overflow) {
+    const unsigned npix = (unsigned)A.res * (unsigned)A.res;
+    const int kv = blockIdx.y, view = v0 + kv;
+    unsigned long long *vkeys = keys + (long long)kv * npix;
+    const unsigned stride = gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    for (unsigned pix = blockIdx.x * blockDim.x + threadIdx.x; pix < npix; pix += stride) {
+        const unsigned long long key = vkeys[pix];
+        bool queue = false;
+        if (key == VIS_NO_KEY) {
+            if (A.hit_ids) A.hit_ids[(long long)view * npix + pix] = -1;
+        } else {
+            vkeys[pix] = VIS_NO_KEY;
+            const Ray ray = vis_ray(A, view, (int)(pix % (unsigned)A.res), (int)(pix / (unsigned)A.res));
+            Best b;
+            b.t = 0.f; b.babs = A.tmax; b.rec = 0; b.found = false;
+            b.U = b.V = b.W = 0.f; b.det = 1.f;
+            test_tri(ray, A.tris, A.tri_ids, (uint32_t)(key & 0xffffffffu), b);
+            if (b.found) {
+                const int id = A.tri_ids[b.rec];
+                A.visible[id] = 1;
+                if (A.hit_ids) A.hit_ids[(long long)view * npix + pix] = id;
+            } else {
+                queue = true;
+            }
+        }
+        const unsigned act = __activemask();
+        const unsigned want = __ballot_sync(act, queue);
+        if (want) {
+            const int leader = __ffs(want) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(want));
+            base = __shfl_sync(act, base, leader);
+            if (queue) {
+                const unsigned long long at = base + __popc(want & ((1u << lane) - 1u));
+                if (at < cap)
+                    list[at] = (unsigned long long)view * npix + pix;
+                else
+                    *overflow = 1;
+            }
+        }
+    }
+}
+
+// the full traversal for the deferred pixels (global pixel indices); with
+// `overflow` set, every pixel of views [v0, v0 + nv) instead
+template <int LAYOUT>
+__global__ void __launch_bounds__(128) k_vis_trace(VisArgs A, const unsigned long long *__restrict__ list,
+                                                   const unsigned long long *__restrict__ count,
+                                                   unsigned long long cap, const int *overflow, int v0, int nv) {
+    uint2 stack[STACK];
+    unsigned long long cn = 0, ct = 0;
+    const long long npix = (long long)A.res * A.res;
+    long long n;
+    if (overflow) {
+        if (!*overflow) return;
+        n = (long long)nv * npix;
+    } else {
+        n = (long long)min(*count, cap);
+    }
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const long long g = overflow ? (long long)v0 * npix + e : (long long)list[e];
+        const int view = (int)(g / npix);
+        const int pix = (int)(g - (long long)view * npix);
+        const Ray ray = vis_ray(A, view, pix % A.res, pix / A.res);
+        const Best b = trace_vis<LAYOUT, false>(A, ray, stack, cn, ct);
+        const int id = b.found ? A.tri_ids[b.rec] : -1;
+        if (b.found) A.visible[id] = 1;
+        if (A.hit_ids) A.hit_ids[(long long)view * npix + pix] = id;
     }
 }
 
@@ -276,6 +496,20 @@ ViewGeom view_geom(int k, int n, const double c[3], double R) {
     return g;
 }
 
+// the keys of one chunk of views (8 bytes per pixel) stay within this
+// budget, so that they live in L2 between the passes
+constexpr long long VIS_CHUNK_BYTES = 96ll << 20;
+// deferred trace list entries (8 bytes each)
+constexpr long long VIS_LIST_CAP = 1ll << 22;
+
+template <typename Kernel>
+unsigned resident_blocks(Kernel kernel, int block, int dev) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (unsigned)(device_sm_count(dev) * per_sm);
+}
+
 template <int LAYOUT, bool COUNT>
 cudaError_t launch_vis(const VisArgs &A, int block, int bps, cudaStream_t s) {
     int dev;
@@ -360,6 +594,66 @@ AG_API ag_status ag_visibility(ag_bvh_t h, int32_t n_views, int32_t res, const a
     A.visible = d_visible;
     A.hit_ids = d_hit_ids;
     A.counters = reinterpret_cast<unsigned long long *>(d_counters);
+    if (o.render != AG_RENDER_RASTER && o.render != AG_RENDER_TRACE)
+        return set_error(AG_ERR_INVALID_ARG, "render must be AG_RENDER_RASTER or AG_RENDER_TRACE");
+    if (o.render == AG_RENDER_RASTER && !d_counters && h->n_tris > 0) {
+        // z-buffer proposals per chunk of views (keys sized to stay in L2);
+        // rejected pixels are traced once at the end
+        const long long npix = (long long)res * res;
+        // views per chunk: keys within the budget, the views on grid.y (< 2^16), and
+        // the chunk's (view, 32-triangle group) items countable in 32 bits
+        const long long groups = (h->n_tris + 31) / 32;
+        const long long cmax = std::min(65535ll, 0xffffffffll / groups);
+        const int chunk = (int)std::max(1ll, std::min<long long>(std::min<long long>(n_views, cmax),
+                                                                 VIS_CHUNK_BYTES / (8ll * npix)));
+        const unsigned long long cap = (unsigned long long)std::min<long long>((long long)n_views * npix, VIS_LIST_CAP);
+        unsigned long long *keys, *list, *count;
+        int *overflow;
+        const int n_chunks = (n_views + chunk - 1) / chunk;
+        AG_CUDA(sc.alloc((void **)&keys, sizeof(unsigned long long) * (size_t)chunk * npix));
+        AG_CUDA(sc.alloc((void **)&list, sizeof(unsigned long long) * (size_t)cap));
+        AG_CUDA(sc.alloc((void **)&count, sizeof(unsigned long long)));
+        AG_CUDA(sc.alloc((void **)&overflow, sizeof(int) * (size_t)n_chunks));
+        AG_CUDA(cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)chunk * npix, s));
+        AG_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s));
+        AG_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int) * (size_t)n_chunks, s));
+        VisRaster Z;
+        Z.tris = h->tris;
+        Z.n_tris = (int)h->n_tris;
+        Z.views = d_views;
+        Z.res = res;
+        Z.R = A.R;
+        Z.scale = A.scale;
+        Z.keys = keys;
+        const unsigned zgrid = resident_blocks(k_vis_zbuffer, 256, h->device);
+        // resolve: grid.y over the chunk's views, one wave of blocks in all
+        const unsigned rgrid_x = std::max(1u, resident_blocks(k_vis_resolve, 256, h->device) / (unsigned)chunk);
+        unsigned *next;
+        AG_CUDA(sc.alloc((void **)&next, sizeof(unsigned) * (size_t)n_chunks));
+        AG_CUDA(cudaMemsetAsync(next, 0, sizeof(unsigned) * (size_t)n_chunks, s));
+        const unsigned tgrid = h->layout == AG_BVH_Q8 ? resident_blocks(k_vis_trace<AG_BVH_Q8>, 128, h->device)
+                                                      : resident_blocks(k_vis_trace<AG_BVH_F32>, 128, h->device);
+        auto trace = [&](const int *ovf, int v0, int nv) {
+            if (h->layout == AG_BVH_Q8)
+                k_vis_trace<AG_BVH_Q8><<<tgrid, 128, 0, s>>>(A, list, count, cap, ovf, v0, nv);
+            else
+                k_vis_trace<AG_BVH_F32><<<tgrid, 128, 0, s>>>(A, list, count, cap, ovf, v0, nv);
+            return cudaGetLastError();
+        };
+        for (int c = 0; c < n_chunks; ++c) {
+            const int v0 = c * chunk, nv = std::min(chunk, n_views - v0);
+            Z.v0 = v0;
+            Z.nv = nv;
+            Z.next = next + c;
+            k_vis_zbuffer<<<zgrid, 256, 0, s>>>(Z);
+            AG_CUDA_LAUNCH("k_vis_zbuffer");
+            k_vis_resolve<<<dim3(rgrid_x, (unsigned)nv), 256, 0, s>>>(A, keys, v0, list, cap, count, overflow + c);
+            AG_CUDA_LAUNCH("k_vis_resolve");
+            AG_CUDA(trace(overflow + c, v0, nv));   // exits at once unless the list overflowed
+        }
+        AG_CUDA(trace(nullptr, 0, 0));
+        return AG_OK;
+    }
     const int block = o.block_size > 0 ? o.block_size : 128;
     const bool cnt = d_counters != nullptr;
     cudaError_t e;

@@ -304,11 +304,13 @@ class BatchPlan:
 # ----------------------------------------------------------------- hidden-face removal (Sec. 6.2)
 
 def visibility(bvh: Bvh, n_views: int = 512, res: int = 1024, *, hit_ids: bool = False, counters: bool = False,
-               block_size: int = 0, blocks_per_sm: int = 0, max_steps: int = 0, stream=None):
+               block_size: int = 0, blocks_per_sm: int = 0, max_steps: int = 0, render: str = "raster", stream=None):
     """Per-face visibility of the mesh ``bvh`` was built on, from n_views
     orthographic res x res views on the Fibonacci lattice around it.
     Returns (visible u8 [n_faces], hit_ids int32 [n_views, res, res] or None,
-    counters u64 [4] (rays, node visits, triangle tests, hits) or None)."""
+    counters u64 [4] (rays, node visits, triangle tests, hits) or None).
+    render: "raster" (z-buffer proposals confirmed by the ray test) or
+    "trace" (every ray traced; always used with counters)."""
     lib = _lib.load()
     n = bvh.info()["n_tris"]
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -316,6 +318,7 @@ def visibility(bvh: Bvh, n_views: int = 512, res: int = 1024, *, hit_ids: bool =
     hits = torch.empty((n_views, res, res), dtype=torch.int32, device=dev) if hit_ids else None
     cnt = torch.zeros(4, dtype=torch.int64, device=dev) if counters else None
     o = _opts(block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps)
+    o.render = {"raster": _lib.AG_RENDER_RASTER, "trace": _lib.AG_RENDER_TRACE}[render]
     check(lib.ag_visibility(bvh.handle, n_views, res, ctypes.byref(o), _stream(stream), vis.data_ptr(), _ptr(hits),
                             _ptr(cnt)))
     return vis, hits, cnt

@@ -7,7 +7,8 @@ than that from the face's boundary; elsewhere it must be one of the oracle's
 candidate faces (or a miss).  The per-face mask must be the union of the
 kernel's own hits and lie between the oracle's certain and candidate sets.
 The flood fill is integer graph work with the gate decided in FP64 in the same
-order on both sides: bit-exact."""
+order on both sides: bit-exact.  Both renders are checked: z-buffer proposals
+confirmed by the ray test (the default) and every ray traced."""
 import numpy as np
 import pytest
 import torch
@@ -22,12 +23,15 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def gpu_vis(V, F, n_views, res, layout="q8", **kw):
+def gpu_vis(V, F, n_views, res, layout="q8", render="raster", **kw):
+    """Visibility through the kernel; the counting build (tracing every ray)
+    with render="trace"."""
     import paper_2605_26137_b300 as pb
     bvh = pb.Bvh(_t(V), _t(F), layout=layout)
-    vis, hits, cnt = pb.visibility(bvh, n_views, res, hit_ids=True, counters=True, **kw)
+    trace = render == "trace"
+    vis, hits, cnt = pb.visibility(bvh, n_views, res, hit_ids=True, counters=trace, render=render, **kw)
     pb.sync_status()
-    out = vis.cpu().numpy(), hits.cpu().numpy(), cnt.cpu().numpy()
+    out = vis.cpu().numpy(), hits.cpu().numpy(), cnt.cpu().numpy() if trace else None
     bvh.free()
     return out
 
@@ -74,10 +78,11 @@ MESHES = _meshes()
 @pytest.mark.parametrize("name", sorted(MESHES))
 @pytest.mark.parametrize("layout", ["q8", "f32"])
 @pytest.mark.parametrize("n_views,res", [(16, 64), (7, 37)])
-def test_visibility_matches_oracle(name, layout, n_views, res):
+@pytest.mark.parametrize("render", ["raster", "trace"])
+def test_visibility_matches_oracle(name, layout, n_views, res, render):
     V, F = MESHES[name]
     o = oracle.visibility(V, F, n_views, res)
-    vis, hits, cnt = gpu_vis(V, F, n_views, res, layout)
+    vis, hits, cnt = gpu_vis(V, F, n_views, res, layout, render)
     frac = check_rays(hits, o)
     assert frac > 0.98
     # the mask is the union of the kernel's own hits, between the oracle's bounds
@@ -86,7 +91,8 @@ def test_visibility_matches_oracle(name, layout, n_views, res):
     assert np.array_equal(vis, own)
     strict, loose = mask_bounds(o, len(F))
     assert np.all(vis[strict] == 1) and not np.any(vis[~loose])
-    assert cnt[0] == n_views * res * res and cnt[3] == (hits >= 0).sum()
+    if cnt is not None:
+        assert cnt[0] == n_views * res * res and cnt[3] == (hits >= 0).sum()
 
 
 def test_exterior_fill_bit_exact_and_generated_mesh_cleanup():
@@ -134,8 +140,8 @@ def test_hidden_faces_one_call_and_argument_errors():
     pb.sync_status()
     o1 = oracle.visibility(V, F, 1, 1)
     check_rays(h1.cpu().numpy(), o1)
-    # step cap
-    pb.visibility(bvh, 2, 16, max_steps=1)
+    # step cap (of the traversal: every ray traced)
+    pb.visibility(bvh, 2, 16, max_steps=1, render="trace")
     with pytest.raises(pb.AgError) as ei:
         pb.sync_status()
     assert ei.value.status == 4
@@ -159,8 +165,7 @@ def test_full_size_sampled():
     import paper_2605_26137_b300 as pb
     V, F, inner = synth.hidden_face_mesh(0, target_faces=22000, device="cpu")
     n_views, res = 512, 1024
-    vis, hits, cnt = gpu_vis(V, F, n_views, res)
-    assert cnt[0] == n_views * res * res
+    vis, hits, _ = gpu_vis(V, F, n_views, res)
     own = np.zeros(len(F), np.uint8)
     flat = hits.reshape(-1)
     own[np.unique(flat[flat >= 0])] = 1
