@@ -75,11 +75,11 @@ struct RasterArgs {
 // that makes the inside non-negative, the camera-space plane n . X = d0, the
 // pixel box
 struct TriSetup {
-    float ax[3], ay[3], dx[3], dy[3];
+    float ax[3], ay[3], dx[3], dy[3];   // canonical edges, (dx, dy) negated where the inside is negative
     float nx, ny, nz, d0;
     int x0, y0, bw;
-    float rbw;        // 1 / bw, for the pixel offset -> (x, y) split
-    unsigned flip, rec, cnt;
+    float rbw;        // 1 / bw, for the first pixel offset -> (x, y) split
+    unsigned rec, cnt;
 };
 
 __device__ __forceinline__ float edge_fn(float ax, float ay, float dx, float dy, float px, float py) {
@@ -113,17 +113,17 @@ __global__ void __launch_bounds__(256) k_zbuffer(RasterArgs A) {
             A.whole[k] = 1;
         } else {
             const float area = (u[1] - u[0]) * (v[2] - v[0]) - (v[1] - v[0]) * (u[2] - u[0]);
-            T.flip = 0;
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 const int q = m == 2 ? 0 : m + 1;
                 const bool sw = u[q] < u[m] || (u[q] == u[m] && v[q] < v[m]);
                 const int a = sw ? q : m, b = sw ? m : q;
+                // negating both differences negates the rounded edge value exactly
+                const float sg = (sw != (area < 0.f)) ? -1.f : 1.f;
                 T.ax[m] = u[a];
                 T.ay[m] = v[a];
-                T.dx[m] = u[b] - u[a];
-                T.dy[m] = v[b] - v[a];
-                T.flip |= (unsigned)(sw != (area < 0.f)) << m;
+                T.dx[m] = sg * (u[b] - u[a]);
+                T.dy[m] = sg * (v[b] - v[a]);
             }
             const float e1x = X[1] - X[0], e1y = Y[1] - Y[0], e1z = Z[1] - Z[0];
             const float e2x = X[2] - X[0], e2y = Y[2] - Y[0], e2z = Z[2] - Z[0];
@@ -158,33 +158,37 @@ __global__ void __launch_bounds__(256) k_zbuffer(RasterArgs A) {
         const unsigned n = S.cnt;
         if (n == 0) continue;
         const int bw = S.bw;
+        // the lane's pixels o = lane, lane + 32, ... of the box, o = y bw + x,
+        // stepped by (32 mod bw, 32 div bw) with one wrap: exact integers and
+        // exact small floats for the centre coordinates (the first split: a
+        // float estimate of lane / bw is within one, one correction)
+        int yy = (int)((float)lane * S.rbw);
+        int xx = lane - yy * bw;
+        if (xx < 0) { --yy; xx += bw; } else if (xx >= bw) { ++yy; xx -= bw; }
+        const int sx = bw > 32 ? 32 : 32 % bw, sy = bw > 32 ? 0 : 32 / bw;
+        float px = (float)(S.x0 + xx) + 0.5f, py = (float)(S.y0 + yy) + 0.5f;
+        long long at = (long long)(S.y0 + yy) * A.w + S.x0 + xx;
+        const long long astep = (long long)sy * A.w + sx, awrap = (long long)A.w - bw;
         for (unsigned o = lane; o < n; o += 32) {
-            // o = y * bw + x: below 2^24 (o exact in FP32) the float
-            // estimate of y is within one of the quotient and one correction
-            // makes it exact; larger boxes divide in integers
-            int yy, xx;
-            if (n <= (1u << 24)) {
-                yy = (int)((float)o * S.rbw);
-                xx = (int)o - yy * bw;
-                if (xx < 0) { --yy; xx += bw; } else if (xx >= bw) { ++yy; xx -= bw; }
-            } else {
-                yy = (int)(o / (unsigned)bw);
-                xx = (int)o - yy * bw;
-            }
-            const int i = S.x0 + xx, j = S.y0 + yy;
-            const float px = (float)i + 0.5f, py = (float)j + 0.5f;
             bool in = true;
 #pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const float e = edge_fn(S.ax[m], S.ay[m], S.dx[m], S.dy[m], px, py);
-                in = in && (((S.flip >> m) & 1u) ? -e : e) >= 0.f;
+            for (int m = 0; m < 3; ++m) in = in && edge_fn(S.ax[m], S.ay[m], S.dx[m], S.dy[m], px, py) >= 0.f;
+            if (in) {
+                const float xh = (px - icx) * rfx, yh = (py - icy) * rfy;
+                const float z = __fdividef(S.d0, S.nx * xh + S.ny * yh + S.nz);
+                if (z > 0.f && z < 3.0e38f)
+                    atomicMin(&keys[at], ((unsigned long long)__float_as_uint(z) << 32) | S.rec);
             }
-            if (!in) continue;
-            const float xh = (px - icx) * rfx, yh = (py - icy) * rfy;
-            const float z = __fdividef(S.d0, S.nx * xh + S.ny * yh + S.nz);
-            if (!(z > 0.f) || !(z < 3.0e38f)) continue;
-            const unsigned long long key = ((unsigned long long)__float_as_uint(z) << 32) | S.rec;
-            atomicMin(&keys[(long long)j * A.w + i], key);
+            xx += sx;
+            px += (float)sx;
+            py += (float)sy;
+            at += astep;
+            if (xx >= bw) {
+                xx -= bw;
+                px -= (float)bw;
+                py += 1.f;
+                at += awrap;
+            }
         }
     }
 }

@@ -208,12 +208,12 @@ struct VisRaster {
 };
 
 struct VisTri {
-    float ax[3], ay[3], dx[3], dy[3];
+    float ax[3], ay[3], dx[3], dy[3];   // canonical edges, (dx, dy) negated where the inside is negative
     float t[3];                  // ray parameter of the vertex opposite each edge
     float inv_area;
     int x0, y0, bw;
     float rbw;
-    unsigned flip, rec, cnt;
+    unsigned rec, cnt;
 };
 
 __device__ __forceinline__ float vis_edge(float ax, float ay, float dx, float dy, float px, float py) {
@@ -249,17 +249,17 @@ __global__ void __launch_bounds__(256) k_vis_zbuffer(VisRaster A) {
                 Z[m] = d.x * G.dir.x + d.y * G.dir.y + d.z * G.dir.z;
             }
             const float area = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
-            T.flip = 0;
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 const int q = m == 2 ? 0 : m + 1;
                 const bool sw = X[q] < X[m] || (X[q] == X[m] && Y[q] < Y[m]);
                 const int a = sw ? q : m, b = sw ? m : q;
+                // negating both factors' differences negates the rounded edge value exactly
+                const float sg = (sw != (area < 0.f)) ? -1.f : 1.f;
                 T.ax[m] = X[a];
                 T.ay[m] = Y[a];
-                T.dx[m] = X[b] - X[a];
-                T.dy[m] = Y[b] - Y[a];
-                T.flip |= (unsigned)(sw != (area < 0.f)) << m;
+                T.dx[m] = sg * (X[b] - X[a]);
+                T.dy[m] = sg * (Y[b] - Y[a]);
                 T.t[m] = Z[m == 0 ? 2 : m - 1];     // edge m (vertex m -> m+1) weighs the vertex m+2
             }
             T.inv_area = 1.0f / fabsf(area);
@@ -283,31 +283,39 @@ __global__ void __launch_bounds__(256) k_vis_zbuffer(VisRaster A) {
             const unsigned n = S.cnt;
             if (n == 0) continue;
             const int bw = S.bw;
+            // the lane's pixels o = lane, lane + 32, ... of the box, o = y bw + x,
+            // stepped by (32 mod bw, 32 div bw) with one wrap: exact integers
+            // (and exact small floats for the centre coordinates)
+            int yy = (int)((float)lane * S.rbw);
+            int xx = lane - yy * bw;
+            if (xx < 0) { --yy; xx += bw; } else if (xx >= bw) { ++yy; xx -= bw; }
+            const int sx = bw > 32 ? 32 : 32 % bw, sy = bw > 32 ? 0 : 32 / bw;
+            float px = (float)(S.x0 + xx) + 0.5f, py = (float)(S.y0 + yy) + 0.5f;
+            int at = (S.y0 + yy) * A.res + S.x0 + xx;
+            const int astep = sy * A.res + sx, awrap = A.res - bw;
             for (unsigned o = lane; o < n; o += 32) {
-                // o = y * bw + x (see the view raster of the backprojection)
-                int yy, xx;
-                if (n <= (1u << 24)) {
-                    yy = (int)((float)o * S.rbw);
-                    xx = (int)o - yy * bw;
-                    if (xx < 0) { --yy; xx += bw; } else if (xx >= bw) { ++yy; xx -= bw; }
-                } else {
-                    yy = (int)(o / (unsigned)bw);
-                    xx = (int)o - yy * bw;
-                }
-                const int i = S.x0 + xx, j = S.y0 + yy;
-                const float px = (float)i + 0.5f, py = (float)j + 0.5f;
                 float e[3];
                 bool in = true;
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
-                    const float v = vis_edge(S.ax[m], S.ay[m], S.dx[m], S.dy[m], px, py);
-                    e[m] = ((S.flip >> m) & 1u) ? -v : v;
+                    e[m] = vis_edge(S.ax[m], S.ay[m], S.dx[m], S.dy[m], px, py);
                     in = in && e[m] >= 0.f;
                 }
-                if (!in) continue;
-                const float t = (e[0] * S.t[0] + e[1] * S.t[1] + e[2] * S.t[2]) * S.inv_area;
-                if (!(t > 0.f) || !(t < 3.0e38f)) continue;
-                atomicMin(&keys[(long long)j * A.res + i], ((unsigned long long)__float_as_uint(t) << 32) | S.rec);
+                if (in) {
+                    const float t = (e[0] * S.t[0] + e[1] * S.t[1] + e[2] * S.t[2]) * S.inv_area;
+                    if (t > 0.f && t < 3.0e38f)
+                        atomicMin(&keys[at], ((unsigned long long)__float_as_uint(t) << 32) | S.rec);
+                }
+                xx += sx;
+                px += (float)sx;
+                py += (float)sy;
+                at += astep;
+                if (xx >= bw) {
+                    xx -= bw;
+                    px -= (float)bw;
+                    py += 1.f;
+                    at += awrap;
+                }
             }
         }
     }
