@@ -18,9 +18,10 @@
 // Exterior fill (k_flood): face normals n = (B - A) x (C - A) in FP64 with the
 // operations in a fixed order, so the gate n_f . n_g > 0 is decided exactly as
 // an FP64 evaluation of that expression; a vertex -> face adjacency gives each
-// face's edge neighbours; one CTA runs a level-synchronous breadth-first search
-// from all visible faces.  The exterior set (everything linked to a visible
-// face) does not depend on the visiting order.
+// face's edge neighbours; a level-synchronous breadth-first search from all
+// visible faces runs its first levels over the whole GPU, one launch per
+// level, and one CTA finishes any deeper levels.  The exterior set
+// (everything linked to a visible face) does not depend on the visiting order.
 #include "rays.cuh"
 
 #include <algorithm>
@@ -431,40 +432,59 @@ __device__ __forceinline__ bool same_side(const double *__restrict__ nrm, int64_
 }
 
 constexpr int FLOOD_THREADS = 1024;
+// breadth-first levels run over the whole GPU before one CTA finishes the
+// (rare) deeper levels
+constexpr int FLOOD_GRID_LEVELS = 16;
 
-// One CTA: level-synchronous BFS from every visible face.
+// claims every same-side edge neighbour of f that is not yet reached and
+// appends it to q
+__device__ __forceinline__ void flood_expand(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
+                                             const int32_t *__restrict__ list, const double *__restrict__ nrm,
+                                             int32_t *state, int32_t f, int32_t *q, unsigned *cnt) {
+    for (int m = 0; m < 3; ++m) {
+        const int32_t a = F[3 * (int64_t)f + m], b = F[3 * (int64_t)f + (m == 2 ? 0 : m + 1)];
+        if (a == b) continue;
+        for (unsigned j = off[a]; j < off[a + 1]; ++j) {
+            const int32_t g = list[j];
+            if (g == f) continue;
+            const int32_t *G = F + 3 * (int64_t)g;
+            if (G[0] != b && G[1] != b && G[2] != b) continue;
+            if (!same_side(nrm, f, g)) continue;
+            if (atomicCAS(&state[g], 0, 1) == 0) q[atomicAdd(cnt, 1u)] = g;
+        }
+    }
+}
+
+// the first queue: every visible face
+__global__ void k_flood_seed(const int32_t *__restrict__ state, int64_t nf, int32_t *q, unsigned *cnt) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < nf && state[f] == 1) q[atomicAdd(cnt, 1u)] = (int32_t)f;
+}
+
+// one breadth-first level over the whole GPU
+__global__ void k_flood_level(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
+                              const int32_t *__restrict__ list, const double *__restrict__ nrm, int32_t *state,
+                              const int32_t *__restrict__ qin, const unsigned *__restrict__ cin, int32_t *qout,
+                              unsigned *cout) {
+    const unsigned n = *cin;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        flood_expand(F, off, list, nrm, state, qin[i], qout, cout);
+}
+
+// One CTA: the remaining levels from queue qa (count *cin), then the mask.
 __global__ void __launch_bounds__(FLOOD_THREADS) k_flood(const int32_t *__restrict__ F, int64_t nf,
                                                           const unsigned *__restrict__ off,
                                                           const int32_t *__restrict__ list,
                                                           const double *__restrict__ nrm, int32_t *state, int32_t *qa,
-                                                          int32_t *qb, uint8_t *__restrict__ ext) {
-    __shared__ int s_count;
+                                                          const unsigned *__restrict__ cin, int32_t *qb,
+                                                          uint8_t *__restrict__ ext) {
+    __shared__ unsigned s_count;
     const int tid = threadIdx.x;
-    if (tid == 0) s_count = 0;
-    __syncthreads();
-    for (int64_t f = tid; f < nf; f += FLOOD_THREADS)
-        if (state[f] == 1) qa[atomicAdd(&s_count, 1)] = (int32_t)f;
-    __syncthreads();
-    int cur = s_count;
-    __syncthreads();
+    unsigned cur = *cin;
     while (cur > 0) {
         if (tid == 0) s_count = 0;
         __syncthreads();
-        for (int i = tid; i < cur; i += FLOOD_THREADS) {
-            const int32_t f = qa[i];
-            for (int m = 0; m < 3; ++m) {
-                const int32_t a = F[3 * (int64_t)f + m], b = F[3 * (int64_t)f + (m == 2 ? 0 : m + 1)];
-                if (a == b) continue;
-                for (unsigned j = off[a]; j < off[a + 1]; ++j) {
-                    const int32_t g = list[j];
-                    if (g == f) continue;
-                    const int32_t *G = F + 3 * (int64_t)g;
-                    if (G[0] != b && G[1] != b && G[2] != b) continue;
-                    if (!same_side(nrm, f, g)) continue;
-                    if (atomicCAS(&state[g], 0, 1) == 0) qb[atomicAdd(&s_count, 1)] = g;
-                }
-            }
-        }
+        for (unsigned i = tid; i < cur; i += FLOOD_THREADS) flood_expand(F, off, list, nrm, state, qa[i], qb, &s_count);
         __syncthreads();
         cur = s_count;
         int32_t *t = qa;
@@ -701,7 +721,19 @@ AG_API ag_status ag_exterior_fill(const float *d_verts, int64_t n_verts, const i
     k_face_normals64<<<(unsigned)((n_faces + 255) / 256), 256, 0, s>>>(d_verts, d_faces, n_faces, n_verts, d_visible,
                                                                          nrm, state, status);
     AG_CUDA_LAUNCH("k_face_normals64");
-    k_flood<<<1, FLOOD_THREADS, 0, s>>>(d_faces, n_faces, off, list, nrm, state, qa, qb, d_exterior);
+    unsigned *counts;
+    AG_CUDA(sc.alloc((void **)&counts, sizeof(unsigned) * (FLOOD_GRID_LEVELS + 1)));
+    AG_CUDA(cudaMemsetAsync(counts, 0, sizeof(unsigned) * (FLOOD_GRID_LEVELS + 1), s));
+    k_flood_seed<<<(unsigned)((n_faces + 255) / 256), 256, 0, s>>>(state, n_faces, qa, counts);
+    AG_CUDA_LAUNCH("k_flood_seed");
+    const unsigned lgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(device_sm_count(dev) * 4, (n_faces + 255) / 256));
+    for (int l = 0; l < FLOOD_GRID_LEVELS; ++l) {
+        k_flood_level<<<lgrid, 256, 0, s>>>(d_faces, off, list, nrm, state, qa, counts + l, qb, counts + l + 1);
+        AG_CUDA_LAUNCH("k_flood_level");
+        std::swap(qa, qb);
+    }
+    k_flood<<<1, FLOOD_THREADS, 0, s>>>(d_faces, n_faces, off, list, nrm, state, qa, counts + FLOOD_GRID_LEVELS, qb,
+                                        d_exterior);
     AG_CUDA_LAUNCH("k_flood");
     return AG_OK;
 }
