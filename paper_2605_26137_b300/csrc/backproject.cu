@@ -601,36 +601,57 @@ struct MipArgs {
     float wt[8];
 };
 
-__global__ void k_mip_down(MipArgs M) {
-    const long long per = (long long)M.dw * M.dh;
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= (long long)M.n_views * per) return;
-    const int k = (int)(r / per);
-    const int pix = (int)(r - (long long)k * per);
-    const int x = pix % M.dw, y = pix / M.dw;
-    const long long sper = (long long)M.sw * M.sh;
+// a tile of 32 x 8 outputs per block: the 22 source rows it needs are first
+// reduced horizontally into shared memory (8 taps each), then each output
+// takes its 8 vertical taps from there
+constexpr int MIP_TX = 32, MIP_TY = 8, MIP_ROWS = 2 * MIP_TY + 6;
+
+__device__ __forceinline__ float3 mip_src(const MipArgs &M, long long q) {
+    if (M.img0) {
+        const uint8_t *c = M.img0 + 4 * q;
+        return make_float3(c[0] * (1.0f / 255.0f), c[1] * (1.0f / 255.0f), c[2] * (1.0f / 255.0f));
+    }
+    const float4 c = M.src[q];
+    return make_float3(c.x, c.y, c.z);
+}
+
+__global__ void __launch_bounds__(MIP_TX * MIP_TY) k_mip_down(MipArgs M) {
+    __shared__ float3 hs[MIP_ROWS][MIP_TX];
+    const int k = blockIdx.z;
+    const int x = blockIdx.x * MIP_TX + threadIdx.x;
+    const int y0 = blockIdx.y * MIP_TY;
+    const long long sbase = (long long)k * M.sw * M.sh;
+    // horizontal: source rows 2 y0 - 3 + r (clamped), output column x
+    for (int r = threadIdx.y; r < MIP_ROWS; r += MIP_TY) {
+        const int j = min(max(2 * y0 - 3 + r, 0), M.sh - 1);
+        float3 acc = make_float3(0.f, 0.f, 0.f);
+        if (x < M.dw) {
+#pragma unroll
+            for (int tx = 0; tx < 8; ++tx) {
+                const int i = min(max(2 * x - 3 + tx, 0), M.sw - 1);
+                const float3 v = mip_src(M, sbase + (long long)j * M.sw + i);
+                acc.x += M.wt[tx] * v.x;
+                acc.y += M.wt[tx] * v.y;
+                acc.z += M.wt[tx] * v.z;
+            }
+        }
+        hs[r][threadIdx.x] = acc;
+    }
+    __syncthreads();
+    const int y = y0 + threadIdx.y;
+    if (x >= M.dw || y >= M.dh) return;
+    // vertical: output row y takes source rows 2y - 3 .. 2y + 4, local 2 (y - y0) + ty;
+    // near the bottom edge the clamped rows repeat, which the local copy already holds
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
 #pragma unroll
     for (int ty = 0; ty < 8; ++ty) {
-        const int j = min(max(2 * y - 3 + ty, 0), M.sh - 1);
-        float r0 = 0.f, r1 = 0.f, r2 = 0.f;
-#pragma unroll
-        for (int tx = 0; tx < 8; ++tx) {
-            const int i = min(max(2 * x - 3 + tx, 0), M.sw - 1);
-            const long long q = (long long)k * sper + (long long)j * M.sw + i;
-            float v0, v1, v2;
-            if (M.img0) {
-                const uint8_t *c = M.img0 + 4 * q;
-                v0 = c[0] * (1.0f / 255.0f); v1 = c[1] * (1.0f / 255.0f); v2 = c[2] * (1.0f / 255.0f);
-            } else {
-                const float4 c = M.src[q];
-                v0 = c.x; v1 = c.y; v2 = c.z;
-            }
-            r0 += M.wt[tx] * v0; r1 += M.wt[tx] * v1; r2 += M.wt[tx] * v2;
-        }
-        a0 += M.wt[ty] * r0; a1 += M.wt[ty] * r1; a2 += M.wt[ty] * r2;
+        const float3 v = hs[2 * threadIdx.y + ty][threadIdx.x];
+        a0 += M.wt[ty] * v.x;
+        a1 += M.wt[ty] * v.y;
+        a2 += M.wt[ty] * v.z;
     }
-    M.dst[r] = make_float4(fminf(fmaxf(a0, 0.f), 1.f), fminf(fmaxf(a1, 0.f), 1.f), fminf(fmaxf(a2, 0.f), 1.f), 0.f);
+    M.dst[(long long)k * M.dw * M.dh + (long long)y * M.dw + x] =
+        make_float4(fminf(fmaxf(a0, 0.f), 1.f), fminf(fmaxf(a1, 0.f), 1.f), fminf(fmaxf(a2, 0.f), 1.f), 0.f);
 }
 
 // the sampled copy of a level: clamp(P + amt (P - B P), 0, 1), B the
@@ -844,7 +865,9 @@ cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int
             M.dw = A.pyr.w[l];
             M.dh = A.pyr.h[l];
             const long long n = (long long)n_views * M.dw * M.dh;
-            k_mip_down<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M);
+            const dim3 mgrid((unsigned)((M.dw + MIP_TX - 1) / MIP_TX), (unsigned)((M.dh + MIP_TY - 1) / MIP_TY),
+                             (unsigned)n_views);
+            k_mip_down<<<mgrid, dim3(MIP_TX, MIP_TY), 0, s>>>(M);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             k_mip_sharpen<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M.dst, M.dw, M.dh, n_views, sharpen, S,
                                                                      A.pyr.stride, A.pyr.off[l]);
