@@ -451,7 +451,8 @@ AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_
  *   its colour the bilinear sample of the RGBA8 image at (u - 1/2, v - 1/2)
  *   (clamped, codes / 255).  T = sum_k w_k I^alpha A_k / (sum_k w_k I^alpha
  *   + eps) over the counting views, evaluated in log space.
- *   d_images [K*h*w*4] u8, d_depth, d_edge from ag_render_views (device);
+ *   d_images [K*h*w*4] u8 (4-byte aligned), d_depth, d_edge from
+ *   ag_render_views (device);
  *   h_weights [K] host, > 0 (the view prior);
  *   d_texture [H*W*4] f32 out: RGB and 1 where at least one view counts
  *   (else all 0); d_incidence optional [K*H*W] f32 out.

@@ -201,7 +201,7 @@ cudaError_t launch_render_views(const TraceLaunch &L, int n_tris, const float *h
 size_t backproject_scratch_bytes(int n_views, int w, int h, int filter);
 cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const float *luv,
                                const int4 *rays, const long long *n_rays, int W, int H, const float *h_cams,
-                               const float *h_logw, int n_views, const uint8_t *images, const float *depth,
+                               const float *h_centres, const float *h_logw, int n_views, const uint8_t *images, const float *depth,
                                const uint8_t *edge, int w, int h, float alpha, float eps, float depth_tol, int filter,
                                float lod_bias, int max_taps, float sharpen, float4 *texture, float *incidence,
                                void *scratch, cudaStream_t s);

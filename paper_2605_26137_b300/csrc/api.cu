@@ -532,6 +532,8 @@ AG_API ag_status ag_backproject(const float *d_lverts, const float *d_lnormals, 
     if (w < 1 || hgt < 1 || w > 16384 || hgt > 16384) return set_error(AG_ERR_INVALID_ARG, "w and h must be in 1..16384");
     if (!h_cams || !h_weights || !d_images || !d_depth || !d_edge || !d_texture)
         return set_error(AG_ERR_INVALID_ARG, "cameras, weights, images, depth, edge and texture must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(d_images) % 4)
+        return set_error(AG_ERR_INVALID_ARG, "d_images must be 4-byte aligned (RGBA8 pixels)");
     if (!(alpha >= 0.f) || !(alpha < 3.0e38f) || !(eps >= 0.f) || !(eps < 3.0e38f) || !(depth_tol >= 0.f) ||
         !(depth_tol < 3.0e38f))
         return set_error(AG_ERR_INVALID_ARG, "alpha, eps and depth_tol must be finite and >= 0");
@@ -540,6 +542,14 @@ AG_API ag_status ag_backproject(const float *d_lverts, const float *d_lnormals, 
         if (!(h_weights[k] > 0.f) || !(h_weights[k] < 3.0e38f))
             return set_error(AG_ERR_INVALID_ARG, "view weights must be finite and > 0");
         logw[(size_t)k] = logf(h_weights[k]);
+    }
+    // camera centres C = -R^T t (float, 4 per view)
+    std::vector<float> centres((size_t)n_views * 4);
+    for (int k = 0; k < n_views; ++k) {
+        const float *c = h_cams + 16 * (size_t)k;
+        for (int a = 0; a < 3; ++a)
+            centres[4 * (size_t)k + a] = -(c[a] * c[9] + c[3 + a] * c[10] + c[6 + a] * c[11]);
+        centres[4 * (size_t)k + 3] = 0.f;
     }
     ag_opts o = resolve_opts(opts);
     if ((st = check_opts(o))) return st;
@@ -557,7 +567,8 @@ AG_API ag_status ag_backproject(const float *d_lverts, const float *d_lnormals, 
     if ((st = run_prep(d_lverts, d_lnormals, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, o.ray_tile, nullptr, status, a,
                        s)))
         return st;
-    AG_CUDA(launch_backproject(a.lpos, a.lnrm, a.lface, d_luv, a.rays, a.n_rays, W, H, h_cams, logw.data(), n_views,
+    AG_CUDA(launch_backproject(a.lpos, a.lnrm, a.lface, d_luv, a.rays, a.n_rays, W, H, h_cams, centres.data(),
+                               logw.data(), n_views,
                                d_images, d_depth, d_edge, w, hgt, alpha, eps, depth_tol, o.filter, AG_LOD_BIAS,
                                AG_MAX_TAPS, AG_SHARPEN, reinterpret_cast<float4 *>(d_texture), d_incidence, scr, s));
     return AG_OK;   // the pageable copies of the cameras and log-weights were staged before returning

@@ -406,6 +406,7 @@ struct BlendArgs {
     const int4 *rays;
     const long long *n_rays;
     const Cam *cams;
+    const float4 *centres;       // camera centres -R^T t
     const float *logw;           // log of the view prior weights
     const uint8_t *images;       // [K*h*w*4]
     const float *depth;          // [K*h*w]
@@ -420,10 +421,13 @@ struct BlendArgs {
     float *incidence;            // optional [K*H*W]
 };
 
-__device__ __forceinline__ float texel_rgb(const uint8_t *img, int w, int h, int x, int y, int ch) {
+// RGB of pixel (x, y) clamped to the image, one 32-bit load (the images are
+// 4-byte aligned RGBA8)
+__device__ __forceinline__ float3 texel_rgb(const uint8_t *img, int w, int h, int x, int y) {
     x = min(max(x, 0), w - 1);
     y = min(max(y, 0), h - 1);
-    return (float)img[((long long)y * w + x) * 4 + ch] * (1.0f / 255.0f);
+    const uchar4 c = reinterpret_cast<const uchar4 *>(img)[(long long)y * w + x];
+    return make_float3(c.x * (1.0f / 255.0f), c.y * (1.0f / 255.0f), c.z * (1.0f / 255.0f));
 }
 
 // bilinear RGB of the 8-bit image at image position (u, v): sample point
@@ -433,14 +437,12 @@ __device__ __forceinline__ float3 sample_image(const uint8_t *img, int w, int h,
     const float fx0 = floorf(x), fy0 = floorf(y);
     const float ax = x - fx0, ay = y - fy0;
     const int x0 = (int)fx0, y0 = (int)fy0;
-    float col[3];
-#pragma unroll
-    for (int ch = 0; ch < 3; ++ch)
-        col[ch] = (1.f - ax) * (1.f - ay) * texel_rgb(img, w, h, x0, y0, ch) +
-                  ax * (1.f - ay) * texel_rgb(img, w, h, x0 + 1, y0, ch) +
-                  (1.f - ax) * ay * texel_rgb(img, w, h, x0, y0 + 1, ch) +
-                  ax * ay * texel_rgb(img, w, h, x0 + 1, y0 + 1, ch);
-    return make_float3(col[0], col[1], col[2]);
+    const float3 p00 = texel_rgb(img, w, h, x0, y0), p10 = texel_rgb(img, w, h, x0 + 1, y0);
+    const float3 p01 = texel_rgb(img, w, h, x0, y0 + 1), p11 = texel_rgb(img, w, h, x0 + 1, y0 + 1);
+    const float w00 = (1.f - ax) * (1.f - ay), w10 = ax * (1.f - ay), w01 = (1.f - ax) * ay, w11 = ax * ay;
+    return make_float3(w00 * p00.x + w10 * p10.x + w01 * p01.x + w11 * p11.x,
+                       w00 * p00.y + w10 * p10.y + w01 * p01.y + w11 * p11.y,
+                       w00 * p00.z + w10 * p10.z + w01 * p01.z + w11 * p11.z);
 }
 
 // bilinear RGB of pyramid level l >= 1 at level-0 image position (u, v)
@@ -547,6 +549,9 @@ __global__ void __launch_bounds__(128) k_backproject(BlendArgs A) {
         const long long npix = (long long)A.w * A.h;
         for (int k = 0; k < A.n_views; ++k) {
             const Cam &c = A.cams[k];
+            // incidence first (the cheapest test): a view that sees the back of the texel is skipped
+            const float I = dot3(nrm, normalize3(f3(A.centres[k]) - p));
+            if (!(I > 0.f)) continue;
             const float qx = c.R[0] * p.x + c.R[1] * p.y + c.R[2] * p.z + c.t[0];
             const float qy = c.R[3] * p.x + c.R[4] * p.y + c.R[5] * p.z + c.t[1];
             const float qz = c.R[6] * p.x + c.R[7] * p.y + c.R[8] * p.z + c.t[2];
@@ -557,11 +562,6 @@ __global__ void __launch_bounds__(128) k_backproject(BlendArgs A) {
             const long long px = (long long)k * npix + (long long)j * A.w + i;
             const float dz = A.depth[px];
             if (!(dz < 3.0e38f) || A.edge[px] || qz > dz + A.depth_tol) continue;
-            const float3 C = make_float3(-(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]),
-                                         -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]),
-                                         -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]));
-            const float I = dot3(nrm, normalize3(C - p));
-            if (!(I > 0.f)) continue;
             if (A.incidence) A.incidence[(long long)k * A.W * A.H + texel] = I;
             // colour: anisotropic footprint taps, or one bilinear sample at (u - 1/2, v - 1/2)
             const float3 cc = A.filter == AG_FILTER_ANISO ? aniso_color(A, k, c, face, fi, p, u, v)
@@ -817,7 +817,9 @@ static double lanczos2_host(double x) {
 
 // scratch: cameras | log-weights | (anisotropic) pyramid levels | two
 // unsharpened level buffers
-static size_t bp_head_bytes(int n_views) { return ((sizeof(Cam) + sizeof(float)) * (size_t)n_views + 255) / 256 * 256; }
+static size_t bp_head_bytes(int n_views) {
+    return ((sizeof(Cam) + sizeof(float4) + sizeof(float)) * (size_t)n_views + 255) / 256 * 256;
+}
 
 size_t backproject_scratch_bytes(int n_views, int w, int h, int filter) {
     size_t b = bp_head_bytes(n_views);
@@ -831,15 +833,18 @@ size_t backproject_scratch_bytes(int n_views, int w, int h, int filter) {
 
 cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int4 *lface, const float *luv,
                                const int4 *rays, const long long *n_rays, int W, int H, const float *h_cams,
-                               const float *h_logw, int n_views, const uint8_t *images, const float *depth,
+                               const float *h_centres, const float *h_logw, int n_views, const uint8_t *images, const float *depth,
                                const uint8_t *edge, int w, int h, float alpha, float eps, float depth_tol, int filter,
                                float lod_bias, int max_taps, float sharpen, float4 *texture, float *incidence,
                                void *scratch, cudaStream_t s) {
     Cam *d_cams = static_cast<Cam *>(scratch);
-    float *d_logw = reinterpret_cast<float *>(d_cams + n_views);
+    float4 *d_centres = reinterpret_cast<float4 *>(d_cams + n_views);
+    float *d_logw = reinterpret_cast<float *>(d_centres + n_views);
     cudaError_t e = cudaMemcpyAsync(d_cams, h_cams, sizeof(Cam) * n_views, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(d_logw, h_logw, sizeof(float) * n_views, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(d_centres, h_centres, sizeof(float4) * n_views, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return e;
     if ((e = cudaMemsetAsync(texture, 0, sizeof(float4) * (size_t)W * H, s)) != cudaSuccess) return e;
     if (incidence && (e = cudaMemsetAsync(incidence, 0, sizeof(float) * (size_t)n_views * W * H, s)) != cudaSuccess)
@@ -882,6 +887,7 @@ cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int
     A.rays = rays;
     A.n_rays = n_rays;
     A.cams = d_cams;
+    A.centres = d_centres;
     A.logw = d_logw;
     A.images = images;
     A.depth = depth;
