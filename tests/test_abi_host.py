@@ -49,7 +49,9 @@ def test_opts_default(lib):
     assert o.bvh_layout == _lib.AG_BVH_Q8 and o.gutter == 2 and o.disp_fp16 == 1
     assert o.schedule == _lib.AG_SCHED_AUTO and o.max_steps == 0
     assert o.query == _lib.AG_QUERY_RAY
-    assert ctypes.sizeof(_lib.AgOpts) == 64   # 16 int32: the query took one reserved slot
+    assert o.render == _lib.AG_RENDER_RASTER and o.filter == _lib.AG_FILTER_ANISO
+    assert ctypes.sizeof(_lib.AgOpts) == 64   # 16 int32: query, render and filter took reserved slots
+    assert _lib.AgOpts.render.offset == 40 and _lib.AgOpts.filter.offset == 44
 
 
 def test_host_argument_checks(lib):
@@ -67,6 +69,17 @@ def test_host_argument_checks(lib):
     bad = _lib.default_opts(query=7)
     assert lib.ag_bvh_build(1, 3, 1, 1, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.AG_ERR_INVALID_ARG
     assert b"query" in lib.ag_last_error()
+    for field in ("render", "filter"):
+        bad = _lib.default_opts(**{field: 7})
+        assert lib.ag_bvh_build(1, 3, 1, 1, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.AG_ERR_INVALID_ARG
+        assert field.encode() in lib.ag_last_error()
+    # backprojection: RGBA8 images must be 4-byte aligned (checked before any device call)
+    cams = (ctypes.c_float * 16)(*([1.0] * 16))
+    wts = (ctypes.c_float * 1)(1.0)
+    tex = ctypes.c_void_p(256)
+    st = lib.ag_backproject(256, None, 256, 256, 3, 1, 8, 8, 1, cams, wts, 258, 256, 256, 4, 4, 1.0, 0.0, 0.01,
+                            None, None, tex, None)
+    assert st == _lib.AG_ERR_INVALID_ARG and b"aligned" in lib.ag_last_error()
     # bad handles
     assert lib.ag_bvh_free(None) == _lib.AG_OK
     info = _lib.AgBvhInfo()

@@ -271,3 +271,41 @@ def test_aniso_footprints(case):
     assert np.array_equal(g[..., 3][ok] > 0.5, np.ones(ok.sum(), bool))
     err = np.abs(g[..., :3][ok] - o["texture"][ok])
     assert err.max() <= TOL_TEX, err.max()
+
+
+def test_aniso_jittered_atlas_and_degenerate_uv():
+    """Random off-lattice UV triangles (strongly anisotropic and varied
+    footprints, some faces with zero or tiny UV area: the centre-sample
+    fallback) on the paper's views of the tiny asset, on the oracle's views."""
+    import paper_2605_26137_b300 as pb
+    a = synth.tiny_asset(3)
+    lv, lf = a.low_v, a.low_f
+    W = H = 256
+    uv = synth.jittered_atlas(len(lf), W, H, seed=4)
+    # a few faces shrunk to 0.02 x 0.006 texel (UV area 6e-5 texel^2, below the
+    # footprint's 1e-4 limit): each still owns the texel it sits in
+    tiny = np.arange(0, len(lf), 7)
+    for f in tiny:
+        p = uv[f].astype(np.float64) * [W, H]
+        x0, y0 = np.floor(p[:, 0].mean()) + 0.4, np.floor(p[:, 1].mean()) + 0.4
+        uv[f] = (np.array([[x0, y0], [x0 + 0.02, y0], [x0 + 0.02, y0 + 0.006]]) / [W, H]).astype(np.float32)
+    c = (lv.max(0) + lv.min(0)) / 2
+    r = float(np.linalg.norm(lv.max(0) - lv.min(0)) / 2)
+    w, h = 161, 119
+    cams, weights, _ = synth.paper_cameras(c, r, w, h)
+    depth_o, point_o, near_o = oracle.render_views(lv, lf, cams, w, h)
+    edge_o = oracle.edge_mask(depth_o, point_o, 0.05 * 2 * r)
+    images = synth.view_images(point_o)
+    kw = dict(alpha=6.0, eps=1e-6, depth_tol=0.02 * 2 * r)
+    o = oracle.backproject(lv, lf, uv, W, H, cams, images, weights, edge_tol=0.05 * 2 * r,
+                           views=(depth_o, point_o, np.zeros_like(near_o)), **kw)
+    tex = pb.backproject(_t(lv), _t(lf), _t(uv), W, H, cams, weights, _t(images), _t(depth_o.astype(np.float32)),
+                         _t(edge_o), **kw)
+    pb.sync_status()
+    g = dict(texture=tex.cpu().numpy(), incidence=np.zeros((len(cams), H, W), np.float32))
+    o2 = dict(o)
+    o2["incidence"] = np.zeros_like(g["incidence"])
+    assert check_texture(g, o2) > 0.9
+    # the centre-sample fallback was compared on filled texels of the shrunk faces
+    on_tiny = np.isin(o["face"], tiny) & (o["flags"] == 0) & o["filled"].astype(bool)
+    assert on_tiny.sum() >= 5
