@@ -130,6 +130,17 @@ ag_status check_opts(const ag_opts &o) {
     return AG_OK;
 }
 
+// the handle's arrays come from the device's memory pool (stream-ordered)
+void free_handle_arrays(ag_bvh *h, cudaStream_t s) {
+    void *arrays[4] = {h->nodes, h->tris, h->tri_ids, h->vnormals};
+    for (void *p : arrays)
+        if (p) cudaFreeAsync(p, s);
+    h->nodes = nullptr;
+    h->tris = nullptr;
+    h->tri_ids = nullptr;
+    h->vnormals = nullptr;
+}
+
 ag_status check_handle(ag_bvh_t h) {
     if (!h || h->magic != AG_BVH_MAGIC) return set_error(AG_ERR_BAD_HANDLE, "invalid BVH handle");
     int dev = -1;
@@ -283,10 +294,8 @@ AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32
     }
     if (st != AG_OK) {
         cudaStreamSynchronize(s);
-        cudaFree(h->nodes);
-        cudaFree(h->tris);
-        cudaFree(h->tri_ids);
-        cudaFree(h->vnormals);
+        free_handle_arrays(h, s);
+        cudaStreamSynchronize(s);
         h->magic = 0;
         delete h;
         return st;
@@ -302,10 +311,8 @@ AG_API ag_status ag_bvh_free(ag_bvh_t h) {
     cudaGetDevice(&prev);
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    cudaFree(h->nodes);
-    cudaFree(h->tris);
-    cudaFree(h->tri_ids);
-    cudaFree(h->vnormals);
+    free_handle_arrays(h, nullptr);
+    cudaStreamSynchronize(nullptr);
     cudaSetDevice(prev);
     h->magic = 0;
     delete h;

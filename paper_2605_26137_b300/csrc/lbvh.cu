@@ -17,6 +17,9 @@ namespace ag {
 namespace {
 
 constexpr int RS_BLOCK = 256;
+// collapse levels launched before the host checks the queue (a 30-bit Morton
+// tree collapses to about 12 levels of 8-wide nodes)
+constexpr int COLLAPSE_LEVELS = 24;
 constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_BLOCK * RS_ROUNDS;
 
@@ -246,6 +249,7 @@ struct CollapseArgs {
     int32_t *tri_ids;
     unsigned *node_count, *tri_count;
     int *q_count_out;
+    uint32_t *rec_pos;            // leaf-order record -> sorted position (records written by k_tri_records)
 };
 
 __device__ __forceinline__ int subtree_count(const CollapseArgs &A, int b) {
@@ -295,10 +299,7 @@ __device__ int choose_exp(float o, float hi_node, const float *clo, const float 
     }
 }
 
-__global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, int nq, int2 *__restrict__ q_out) {
-    int qi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= nq) return;
-    int2 item = q_in[qi];
+__device__ void collapse_node(const CollapseArgs &A, int2 item, int2 *__restrict__ q_out) {
     int b = item.x;
     unsigned wslot = (unsigned)item.y;
     int ch[8];
@@ -344,19 +345,8 @@ __global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, int nq
             ++rank;
         } else {
             meta[k] = (unsigned char)((cnt << 5) | toff);
-            int first = subtree_first(A, ch[k]);
-            for (int j = 0; j < cnt; ++j) {
-                unsigned orig = A.vals[first + j];
-                int32_t id[3] = {A.F[3 * (int64_t)orig], A.F[3 * (int64_t)orig + 1], A.F[3 * (int64_t)orig + 2]};
-                if (id[0] < 0 || id[0] >= A.nv || id[1] < 0 || id[1] >= A.nv || id[2] < 0 || id[2] >= A.nv)
-                    id[0] = id[1] = id[2] = 0;   // reported through the status word by k_tri_prep
-                unsigned rec = tri_base + toff + j;
-                for (int v = 0; v < 3; ++v) {
-                    const float *p = A.V + 3 * (int64_t)id[v];
-                    A.tris[3 * (int64_t)rec + v] = make_float4(p[0], p[1], p[2], __int_as_float(id[v]));
-                }
-                A.tri_ids[rec] = (int32_t)orig;
-            }
+            const int first = subtree_first(A, ch[k]);
+            for (int j = 0; j < cnt; ++j) A.rec_pos[tri_base + toff + j] = (uint32_t)(first + j);
             toff += cnt;
         }
     }
@@ -402,6 +392,47 @@ __global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, int nq
     }
 }
 
+// one level of the top-down collapse: the level's queue length is read on the
+// device, so the levels run back to back without a host round trip
+__global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, const int *__restrict__ nq_in,
+                           int2 *__restrict__ q_out) {
+    const int nq = *nq_in;
+    for (int qi = blockIdx.x * blockDim.x + threadIdx.x; qi < nq; qi += gridDim.x * blockDim.x)
+        collapse_node(A, q_in[qi], q_out);
+}
+
+// the 48-byte leaf-order triangle records, one thread per record
+__global__ void k_tri_records(const uint32_t *__restrict__ rec_pos, const unsigned *__restrict__ vals,
+                              const float *__restrict__ V, const int32_t *__restrict__ F, int64_t nv, int64_t n,
+                              float4 *__restrict__ tris, int32_t *__restrict__ tri_ids) {
+    const int64_t rec = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (rec >= n) return;
+    const unsigned orig = vals[rec_pos[rec]];
+    int32_t id[3] = {F[3 * (int64_t)orig], F[3 * (int64_t)orig + 1], F[3 * (int64_t)orig + 2]};
+    if (id[0] < 0 || id[0] >= nv || id[1] < 0 || id[1] >= nv || id[2] < 0 || id[2] >= nv)
+        id[0] = id[1] = id[2] = 0;   // reported through the status word by k_tri_prep
+    for (int v = 0; v < 3; ++v) {
+        const float *p = V + 3 * (int64_t)id[v];
+        tris[3 * rec + v] = make_float4(p[0], p[1], p[2], __int_as_float(id[v]));
+    }
+    tri_ids[rec] = (int32_t)orig;
+}
+
+// level 0 of the collapse queue: the binary root (internal node 0, or leaf 0
+// for a one-triangle mesh), node counter 1, triangle counter 0
+__global__ void k_collapse_init(int2 *q0, int *counts, unsigned *counters) {
+    q0[0] = make_int2(0, 0);
+    counts[0] = 1;
+    counters[0] = 1u;
+    counters[1] = 0u;
+}
+
+// bound keys: min keys start at all ones, max keys at zero
+__global__ void k_bounds_init(unsigned *bounds) {
+    const int q = threadIdx.x;
+    if (q < 16) bounds[q] = (q < 3 || (q >= 6 && q < 9)) ? 0xffffffffu : 0u;
+}
+
 inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 }  // namespace
@@ -443,27 +474,29 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     AG_CUDA(sc.alloc((void **)&counters, sizeof(unsigned) * 2));
     AG_CUDA(sc.alloc(&nscr, vertex_normal_scratch_bytes(nv, n)));
 
-    // persistent arrays owned by the handle (worst-case node count, compacted later)
+    // persistent arrays owned by the handle (worst-case node count, compacted
+    // later), from the device's memory pool so that rebuilds reuse them
     const int64_t max_nodes = std::max<int64_t>(1, n - 1);
     const size_t node_size = layout == AG_BVH_Q8 ? sizeof(QNode) : sizeof(FNode);
     void *nodes_tmp = nullptr;
+    uint32_t *rec_pos;
+    int *lcounts;
     AG_CUDA(sc.alloc(&nodes_tmp, node_size * max_nodes));
-    AG_CUDA(cudaMalloc((void **)&h->tris, sizeof(float4) * 3 * n));
-    AG_CUDA(cudaMalloc((void **)&h->tri_ids, sizeof(int32_t) * n));
-    AG_CUDA(cudaMalloc((void **)&h->vnormals, sizeof(float4) * nv));
+    AG_CUDA(sc.alloc((void **)&rec_pos, sizeof(uint32_t) * n));
+    AG_CUDA(sc.alloc((void **)&lcounts, sizeof(int) * (COLLAPSE_LEVELS + 1)));
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return set_error(AG_ERR_OOM, "memory pool unavailable");
+    AG_CUDA(cudaMallocFromPoolAsync((void **)&h->tris, sizeof(float4) * 3 * n, pool, s));
+    AG_CUDA(cudaMallocFromPoolAsync((void **)&h->tri_ids, sizeof(int32_t) * n, pool, s));
+    AG_CUDA(cudaMallocFromPoolAsync((void **)&h->vnormals, sizeof(float4) * nv, pool, s));
 
     cudaEvent_t e0, e1;
     AG_CUDA(cudaEventCreate(&e0));
     AG_CUDA(cudaEventCreate(&e1));
     AG_CUDA(cudaEventRecord(e0, s));
 
-    // bounds init: min keys 0xff.., max keys 0
-    {
-        unsigned init[16];
-        for (int q = 0; q < 16; ++q) init[q] = (q < 3 || (q >= 6 && q < 9)) ? 0xffffffffu : 0u;
-        AG_CUDA(cudaMemcpyAsync(bounds, init, sizeof(init), cudaMemcpyHostToDevice, s));
-        AG_CUDA(cudaStreamSynchronize(s));  // init is a stack array
-    }
+    k_bounds_init<<<1, 32, 0, s>>>(bounds);
+    AG_CUDA_LAUNCH("k_bounds_init");
     k_tri_prep<<<grid_for(n, 256), 256, 0, s>>>(d_verts, d_faces, nv, n, tlo, thi, cent, bounds, status);
     AG_CUDA_LAUNCH("k_tri_prep");
     k_morton<<<grid_for(n, 256), 256, 0, s>>>(cent, n, bounds, k0, v0);
@@ -487,37 +520,43 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     k_bounds<<<grid_for(n, 256), 256, 0, s>>>(va, n, tlo, thi, child, parent, box_lo, box_hi, flags);
     AG_CUDA_LAUNCH("k_bounds");
 
-    // top-down collapse, one launch per level
+    // top-down collapse, one launch per level; the queue lengths stay on the
+    // device, and the host looks at them once after COLLAPSE_LEVELS levels
     CollapseArgs A;
     A.n = n; A.child = child; A.range = range; A.box_lo = box_lo; A.box_hi = box_hi; A.vals = va;
     A.V = d_verts; A.F = d_faces; A.nv = nv; A.layout = layout; A.rule = rule; A.nodes = nodes_tmp; A.tris = h->tris;
-    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1;
-    {
-        unsigned init[2] = {1u, 0u};
-        int2 root = make_int2(n > 1 ? 0 : 0, 0);   // binary root: internal 0, or leaf 0 when n == 1
-        if (n == 1) root.x = 0;                      // leaf index n-1+0 == 0
-        AG_CUDA(cudaMemcpyAsync(counters, init, sizeof(init), cudaMemcpyHostToDevice, s));
-        AG_CUDA(cudaMemcpyAsync(q0, &root, sizeof(root), cudaMemcpyHostToDevice, s));
-        AG_CUDA(cudaStreamSynchronize(s));
-    }
-    int nq = 1, depth = 0;
+    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1; A.rec_pos = rec_pos;
+    AG_CUDA(cudaMemsetAsync(lcounts, 0, sizeof(int) * (COLLAPSE_LEVELS + 1), s));
+    k_collapse_init<<<1, 1, 0, s>>>(q0, lcounts, counters);
+    AG_CUDA_LAUNCH("k_collapse_init");
+    const unsigned cgrid = (unsigned)std::min<int64_t>(grid_for(n, 128), (int64_t)device_sm_count(dev) * 16);
     int2 *qin = q0, *qout = q1;
-    int *hcount = nullptr;
-    AG_CUDA(cudaMallocHost((void **)&hcount, sizeof(int)));
+    for (int l = 0; l < COLLAPSE_LEVELS; ++l) {
+        A.q_count_out = lcounts + l + 1;
+        k_collapse<<<cgrid, 128, 0, s>>>(A, qin, lcounts + l, qout);
+        AG_CUDA_LAUNCH("k_collapse");
+        std::swap(qin, qout);
+    }
+    int hl[COLLAPSE_LEVELS + 1];
+    AG_CUDA(cudaMemcpyAsync(hl, lcounts, sizeof(hl), cudaMemcpyDeviceToHost, s));
+    AG_CUDA(cudaStreamSynchronize(s));
+    int depth = 0;
+    while (depth <= COLLAPSE_LEVELS && hl[depth] > 0) ++depth;
+    // a deeper tree than that (many equal Morton codes) continues level by level
+    int nq = hl[COLLAPSE_LEVELS];
     while (nq > 0) {
-        AG_CUDA(cudaMemsetAsync(qcount, 0, sizeof(int), s));
-        A.q_count_out = qcount;
-        k_collapse<<<grid_for(nq, 128), 128, 0, s>>>(A, qin, nq, qout);
-        cudaError_t le = cudaGetLastError();
-        if (le != cudaSuccess) { cudaFreeHost(hcount); return cuda_error(le, "k_collapse"); }
-        cudaMemcpyAsync(hcount, qcount, sizeof(int), cudaMemcpyDeviceToHost, s);
-        cudaError_t se = cudaStreamSynchronize(s);
-        if (se != cudaSuccess) { cudaFreeHost(hcount); return cuda_error(se, "collapse level"); }
-        nq = *hcount;
+        AG_CUDA(cudaMemsetAsync(lcounts + 1, 0, sizeof(int), s));
+        AG_CUDA(cudaMemcpyAsync(lcounts, &nq, sizeof(int), cudaMemcpyHostToDevice, s));
+        A.q_count_out = lcounts + 1;
+        k_collapse<<<cgrid, 128, 0, s>>>(A, qin, lcounts, qout);
+        AG_CUDA_LAUNCH("k_collapse");
+        AG_CUDA(cudaMemcpyAsync(&nq, lcounts + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaStreamSynchronize(s));
         std::swap(qin, qout);
         ++depth;
     }
-    cudaFreeHost(hcount);
+    k_tri_records<<<grid_for(n, 256), 256, 0, s>>>(rec_pos, va, d_verts, d_faces, nv, n, h->tris, h->tri_ids);
+    AG_CUDA_LAUNCH("k_tri_records");
     unsigned hc[2];
     AG_CUDA(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
     AG_CUDA(cudaStreamSynchronize(s));
@@ -525,7 +564,7 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
         return set_error(AG_ERR_CUDA, "BVH collapse wrote %u of %lld triangle records", hc[1], (long long)n);
     h->n_nodes = hc[0];
     h->max_depth = depth;
-    AG_CUDA(cudaMalloc(&h->nodes, node_size * h->n_nodes));
+    AG_CUDA(cudaMallocFromPoolAsync(&h->nodes, node_size * h->n_nodes, pool, s));
     AG_CUDA(cudaMemcpyAsync(h->nodes, nodes_tmp, node_size * h->n_nodes, cudaMemcpyDeviceToDevice, s));
 
     AG_CUDA(launch_vertex_normals(d_verts, d_faces, nv, n, nullptr, nullptr, h->vnormals, nullptr, nscr, s));
