@@ -282,12 +282,13 @@ __device__ int choose_exp(float o, float hi_node, const float *clo, const float 
     }
     for (;; ++e) {
         float s = __uint_as_float((unsigned)e << 23);
+        const float inv = 1.0f / s;   // a power of two: x * inv is exactly x / s
         bool ok = true;
         for (int c = 0; c < nc && ok; ++c) {
-            int ql = (int)floorf((clo[c] - o) / s);
+            int ql = (int)floorf((clo[c] - o) * inv);
             ql = max(0, min(255, ql));
             while (ql > 0 && fmaf((float)ql, s, o) > clo[c]) --ql;
-            int qh = (int)ceilf((chi[c] - o) / s);
+            int qh = (int)ceilf((chi[c] - o) * inv);
             qh = max(0, qh);
             while (qh <= 255 && fmaf((float)qh, s, o) < chi[c]) ++qh;
             while (qh > 0 && qh - 1 >= ql && fmaf((float)(qh - 1), s, o) >= chi[c]) --qh;
@@ -307,24 +308,28 @@ __device__ void collapse_node(const CollapseArgs &A, int2 item, int2 *__restrict
     if (b >= A.n - 1 || subtree_count(A, b) <= LEAF_MAX) {
         ch[nc++] = b;   // only the root of a tiny mesh gets here
     } else {
+        // greedy expansion; each child's priority (-1: a leaf-sized subtree) is
+        // computed once when the child enters the list
+        auto prio = [&](int node) {
+            const int cnt = subtree_count(A, node);
+            if (cnt <= LEAF_MAX) return -1.f;
+            return A.rule == AG_COLLAPSE_COUNT ? (float)cnt
+                 : A.rule == AG_COLLAPSE_AREA ? half_area(A, node)
+                                              : half_area(A, node) * (float)cnt;
+        };
+        float pr[8];
         int2 c = A.child[b];
-        ch[nc++] = c.x;
-        ch[nc++] = c.y;
+        ch[nc] = c.x; pr[nc++] = prio(c.x);
+        ch[nc] = c.y; pr[nc++] = prio(c.y);
         while (nc < 8) {
             int best = -1;
             float ba = -1.f;
-            for (int k = 0; k < nc; ++k) {
-                int cnt = subtree_count(A, ch[k]);
-                if (cnt <= LEAF_MAX) continue;
-                float a = A.rule == AG_COLLAPSE_COUNT ? (float)cnt
-                        : A.rule == AG_COLLAPSE_AREA ? half_area(A, ch[k])
-                                                     : half_area(A, ch[k]) * (float)cnt;
-                if (a > ba) { ba = a; best = k; }
-            }
+            for (int k = 0; k < nc; ++k)
+                if (pr[k] >= 0.f && pr[k] > ba) { ba = pr[k]; best = k; }
             if (best < 0) break;
             int2 cc = A.child[ch[best]];
-            ch[best] = cc.x;
-            ch[nc++] = cc.y;
+            ch[best] = cc.x; pr[best] = prio(cc.x);
+            ch[nc] = cc.y; pr[nc++] = prio(cc.y);
         }
     }
     int n_int = 0, n_tri = 0;
