@@ -197,6 +197,13 @@ AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32
 /* Free a handle (synchronises the device first).  NULL is a no-op. */
 AG_API ag_status ag_bvh_free(ag_bvh_t h);
 
+/* Free a handle in stream order: its device arrays return to the library's
+ * memory pool once the work already queued on `stream` has run, without
+ * synchronising.  Work that uses the handle on other streams must be ordered
+ * before `stream` by the caller.  The handle is invalid on return.  NULL is a
+ * no-op. */
+AG_API ag_status ag_bvh_free_async(ag_bvh_t h, ag_stream_t stream);
+
 /* Query sizes of a built BVH. */
 AG_API ag_status ag_bvh_info(ag_bvh_t h, ag_bvh_info_t *out);
 

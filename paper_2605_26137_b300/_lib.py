@@ -41,7 +41,7 @@ AG_QEM_OPTIMAL = 0
 AG_QEM_MIDPOINT = 1
 
 # every symbol include/ag.h declares
-EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
+EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_free_async", "ag_bvh_info", "ag_bvh_copy_out", "ag_bake", "ag_bake_batch",
            "ag_batch_plan_create", "ag_batch_plan_launch", "ag_batch_plan_free", "ag_bake_backward",
            "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc",
            "ag_autotune", "ag_visibility", "ag_exterior_fill", "ag_qem_simplify",
@@ -102,6 +102,8 @@ def load():
         lib.ag_bvh_build.restype = S
         lib.ag_bvh_free.argtypes = [c_void_p]
         lib.ag_bvh_free.restype = S
+        lib.ag_bvh_free_async.argtypes = [c_void_p, c_void_p]
+        lib.ag_bvh_free_async.restype = S
         lib.ag_bvh_info.argtypes = [c_void_p, POINTER(AgBvhInfo)]
         lib.ag_bvh_info.restype = S
         lib.ag_bvh_copy_out.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]

@@ -304,6 +304,19 @@ AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32
     return AG_OK;
 }
 
+AG_API ag_status ag_bvh_free_async(ag_bvh_t h, ag_stream_t stream) {
+    if (!h) return AG_OK;
+    if (h->magic != AG_BVH_MAGIC) return set_error(AG_ERR_BAD_HANDLE, "invalid BVH handle");
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    free_handle_arrays(h, (cudaStream_t)stream);
+    cudaSetDevice(prev);
+    h->magic = 0;
+    delete h;
+    return AG_OK;
+}
+
 AG_API ag_status ag_bvh_free(ag_bvh_t h) {
     if (!h) return AG_OK;
     if (h->magic != AG_BVH_MAGIC) return set_error(AG_ERR_BAD_HANDLE, "invalid BVH handle");

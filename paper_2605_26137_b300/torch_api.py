@@ -99,9 +99,14 @@ class Bvh:
                                         vn.ctypes.data))
         return nodes, tris, ids, vn
 
-    def free(self) -> None:
+    def free(self, stream=None) -> None:
+        """Release the handle: synchronously, or in the order of ``stream``
+        (after the work already queued on it) when one is given."""
         if self._h:
-            check(self._lib.ag_bvh_free(self._h))
+            if stream is None:
+                check(self._lib.ag_bvh_free(self._h))
+            else:
+                check(self._lib.ag_bvh_free_async(self._h, _stream(stream)))
             self._h = ctypes.c_void_p()
 
     def __del__(self):

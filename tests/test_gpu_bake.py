@@ -354,3 +354,27 @@ def test_tiny_high_meshes(n_high):
     _, g, _ = gpu_bake(a)
     st = parity.compare(g, o, a.diam, a.gutter)
     parity.check(st)
+
+
+def test_stream_pipeline_with_stream_ordered_free():
+    """Two bakes in flight on two streams, each handle freed in its stream's
+    order (ag_bvh_free_async): the maps equal a plain synchronous bake."""
+    import paper_2605_26137_b300 as pb
+    a = synth.tiny_asset(2)
+    _, ref, _ = gpu_bake(a)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = []
+    for i in range(4):
+        st = streams[i % 2]
+        with torch.cuda.stream(st):
+            bvh = pb.Bvh(_t(a.high_v), _t(a.high_f))
+            out = pb.bake(bvh, _t(a.low_v), _t(a.low_f), _t(a.low_uv), a.W, a.H, a.max_dist, gutter=a.gutter)
+            host = torch.empty_like(out.normal_rgba8, device="cpu").pin_memory()
+            host.copy_(out.normal_rgba8, non_blocking=True)
+            bvh.free(stream=st)
+            outs.append((host, out))
+    for st in streams:
+        st.synchronize()
+    pb.sync_status()
+    for host, _ in outs:
+        assert np.array_equal(host.numpy(), ref["normal_rgba8"])
