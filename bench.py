@@ -502,7 +502,7 @@ def main():
             "per_ray": {"nodes": nodes_pr, "tris": tris_pr, "hit_frac": hit_frac, "bytes": bpr},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": recorded_traffic("q8", W, int(len(a.high_f))),
-                         "kernel": "k_trace (closest-hit traversal + shading)", "peak_kind": peak_kind},
+                         "kernel": "k_trace_fwd_q8 (closest-hit traversal + shading)", "peak_kind": peak_kind},
             "clocks": clocks,
             "gpu_launches": 7 * args.steps}
 
