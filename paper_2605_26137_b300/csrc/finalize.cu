@@ -35,17 +35,31 @@ __global__ void __launch_bounds__(256) k_finalize(const float4 *__restrict__ nts
     __shared__ float4 sv[NB][BH][BW];
     __shared__ uint8_t sf[NB][BH][BW];   // 0 empty, 1 ray texel, 2 dilated, 3 outside the image
     const int x0 = blockIdx.x * TW - G, y0 = blockIdx.y * TH - G;
-    for (int i = threadIdx.x; i < CELLS; i += blockDim.x) {
-        int lx = i % BW, ly = i / BW;
-        int x = x0 + lx, y = y0 + ly;
-        float4 v = make_float4(0.f, 0.f, 1.f, 0.f);
-        uint8_t f = 3;
-        if (x >= 0 && y >= 0 && x < W && y < H) {
-            size_t t = (size_t)y * W + x;
-            f = face_map[t] >= 0 ? 1 : 0;
-            if (f) v = ntsd[t];
+    // staging: every cell's face entry and value are loaded without waiting on
+    // each other (the value of an empty texel is read and dropped), all
+    // iterations' loads in flight together
+    constexpr int PER = (CELLS + 255) / 256;
+    int32_t fm[PER];
+    float4 vv[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + 256 * k;
+        const int lx = i % BW, ly = i / BW;
+        const int x = x0 + lx, y = y0 + ly;
+        fm[k] = -2;
+        if (i < CELLS && x >= 0 && y >= 0 && x < W && y < H) {
+            const size_t t = (size_t)y * W + x;
+            fm[k] = __ldg(&face_map[t]);
+            vv[k] = __ldg(&ntsd[t]);
         }
-        sv[0][ly][lx] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = threadIdx.x + 256 * k;
+        if (i >= CELLS) break;
+        const int lx = i % BW, ly = i / BW;
+        const uint8_t f = fm[k] == -2 ? 3 : (fm[k] >= 0 ? 1 : 0);
+        sv[0][ly][lx] = f == 1 ? vv[k] : make_float4(0.f, 0.f, 1.f, 0.f);
         sf[0][ly][lx] = f;
     }
     __syncthreads();
