@@ -440,24 +440,28 @@ AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_
  * rows = right, down, forward), t (3), fx, fy, cx, cy in pixels.  A point p
  * has camera coordinates c = R p + t, depth c.z and image position
  * (fx c.x / c.z + cx, fy c.y / c.z + cy); pixel (i, j) covers
- * [i, i+1) x [j, j+1).  Cameras are meant to lie outside the mesh's bounding
- * sphere (a surface behind a camera nearer than the first one in front makes
- * the pixel a miss).
+ * [i, i+1) x [j, j+1).
  *
- * ag_render_views - per view and pixel: the camera depth of the first hit of
- *   the ray through the pixel centre (d_depth [K*h*w] f32, +inf on a miss),
- *   its world point (d_points, optional [K*h*w*3] f32, NaN on a miss) and
- *   the edge mask (d_edge, optional [K*h*w] u8: a hit whose 4-neighbour
- *   misses or lies farther than edge_tol from it).
+ * ag_render_views - per view and pixel: the camera depth of the first hit in
+ *   front of the camera of the ray through the pixel centre (smallest t > 0
+ *   under the watertight test, equal t: lower id; d_depth [K*h*w] f32, +inf
+ *   on a miss), its world point (d_points, optional [K*h*w*3] f32, NaN on a
+ *   miss) and the edge mask (d_edge, optional [K*h*w] u8: a hit whose
+ *   4-neighbour misses or lies farther than edge_tol from it, world points
+ *   rebuilt from depth).  opts: render (AG_RENDER_*), max_steps.  Errors:
+ *   AG_ERR_BAD_HANDLE, AG_ERR_INVALID_ARG (n_views outside 1..4096, w or h
+ *   outside 1..16384, NULL h_cams or d_depth, edge_tol not finite and > 0).
  *
  * ag_backproject - the texture of the low mesh's atlas (the bake's raster)
  *   from K views: for every ray texel and view, its surface point p and
  *   smooth normal n; the view counts when c.z > 0, the pixel is inside the
  *   image, a hit, not an edge pixel, and c.z <= its depth + depth_tol; its
  *   incidence is I = max(0, n . normalize(C - p)) (C the camera centre) and
- *   its colour the bilinear sample of the RGBA8 image at (u - 1/2, v - 1/2)
- *   (clamped, codes / 255).  T = sum_k w_k I^alpha A_k / (sum_k w_k I^alpha
- *   + eps) over the counting views, evaluated in log space.
+ *   its colour A_k the anisotropic footprint sample (opts->filter ==
+ *   AG_FILTER_ANISO, the default) or the bilinear sample of the RGBA8 image
+ *   at (u - 1/2, v - 1/2) (AG_FILTER_BILINEAR; clamped, codes / 255).
+ *   T = sum_k w_k I^alpha A_k / (sum_k w_k I^alpha + eps) over the counting
+ *   views, evaluated in log space.  opts: filter, ray_tile.
  *   d_images [K*h*w*4] u8 (4-byte aligned), d_depth, d_edge from
  *   ag_render_views (device);
  *   h_weights [K] host, > 0 (the view prior);
