@@ -89,9 +89,8 @@ __device__ __forceinline__ float edge_fn(float ax, float ay, float dx, float dy,
 __global__ void __launch_bounds__(256) k_zbuffer(RasterArgs A) {
     __shared__ TriSetup ts[256];
     const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
-    const int per_view = (A.n_tris + 255) / 256;
-    const int kv = blockIdx.x / per_view;            // view within the launch
-    const int tri = (blockIdx.x - kv * per_view) * 256 + threadIdx.x;
+    const int kv = blockIdx.y;                       // view within the launch
+    const int tri = blockIdx.x * 256 + threadIdx.x;
     const int k = A.v0 + kv;
     const Cam &c = A.cams[k];
     unsigned cnt = 0;
@@ -771,7 +770,7 @@ cudaError_t launch_render_views(const TraceLaunch &L, int n_tris, const float *h
             R.nv = nv;
             R.keys = keys;
             R.whole = whole;
-            k_zbuffer<<<(unsigned)(nv * ((n_tris + 255) / 256)), 256, 0, s>>>(R);
+            k_zbuffer<<<dim3((unsigned)((n_tris + 255) / 256), (unsigned)nv), 256, 0, s>>>(R);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             A.keys = keys;
             A.list = list;
