@@ -102,7 +102,8 @@ def peaks():
     return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh", "rays.cuh"), "closest": ("closest.cu", "traverse.cuh"),
+KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh", "rays.cuh", "ag_internal.cuh"),
+                  "closest": ("closest.cu", "traverse.cuh", "ag_internal.cuh"),
                   "visibility": ("hidden.cu", "traverse.cuh", "rays.cuh"),
                   "backproject": ("backproject.cu", "rays.cuh", "traverse.cuh")}
 PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_2048_2M.md",
@@ -111,9 +112,10 @@ PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_
 
 
 def trace_source_hash(kernel: str = "trace"):
-    """Hash of a traversal kernel's code (the profiled kernel's file and the
-    traversal header it includes), comments and blank lines removed, so that
-    only a change of the code itself retires a recorded capture."""
+    """Hash of a traversal kernel's code (the profiled kernel's file, the
+    traversal headers it includes and the node and leaf layout), comments and
+    blank lines removed, so that only a change of the code itself retires a
+    recorded capture."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", name)) as f:

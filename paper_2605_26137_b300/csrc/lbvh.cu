@@ -3,7 +3,7 @@
 //   triangle bounds + centroid bounds -> 30-bit Morton codes -> LSD radix
 //   sort (8-bit digits, stable warp-ranked scatter) -> Karras (2012) binary
 //   hierarchy -> bottom-up FP32 boxes -> top-down collapse to 8-wide nodes
-//   (greedy largest-area expansion, leaves of <= 3 triangles) with child boxes
+//   (greedy largest-area expansion, leaves of <= 2 triangles) with child boxes
 //   quantised to 8 bits and rounded outward (or kept in FP32) -> triangles
 //   reordered into 48-byte leaf-order records -> area-weighted vertex normals.
 #include "ag_internal.cuh"
