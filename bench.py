@@ -78,7 +78,7 @@ def parse():
                    help="--profile: the ray or closest-point bake, the hidden-face visibility pass or QEM")
     p.add_argument("--error-sample", type=float, default=20000,
                    help="ray texels compared with the oracle per layout (a value < 1 is a fraction of them)")
-    p.add_argument("--collapse", default="area", choices=["area_count", "area", "count"])
+    p.add_argument("--collapse", default="sah", choices=["area_count", "area", "count", "sah"])
     p.add_argument("--hidden-views", type=int, default=512, help="hidden-face removal: viewpoints")
     p.add_argument("--hidden-res", type=int, default=1024, help="hidden-face removal: image resolution")
     p.add_argument("--hidden-faces", type=int, default=22000, help="hidden-face removal: mesh faces")
@@ -102,8 +102,8 @@ def peaks():
     return 6400.0, "fallback"
 
 
-KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh", "rays.cuh", "ag_internal.cuh"),
-                  "closest": ("closest.cu", "traverse.cuh", "ag_internal.cuh"),
+KERNEL_SOURCES = {"trace": ("trace.cu", "traverse.cuh", "rays.cuh", "ag_internal.cuh", "lbvh.cu"),
+                  "closest": ("closest.cu", "traverse.cuh", "ag_internal.cuh", "lbvh.cu"),
                   "visibility": ("hidden.cu", "traverse.cuh", "rays.cuh"),
                   "backproject": ("backproject.cu", "rays.cuh", "traverse.cuh")}
 PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_2048_2M.md",
@@ -113,9 +113,9 @@ PROFILE_FILES = {"trace": "trace_kernel_2048_2M.md", "closest": "closest_kernel_
 
 def trace_source_hash(kernel: str = "trace"):
     """Hash of a traversal kernel's code (the profiled kernel's file, the
-    traversal headers it includes and the node and leaf layout), comments and
-    blank lines removed, so that only a change of the code itself retires a
-    recorded capture."""
+    traversal headers it includes, the node and leaf layout and the tree
+    builder), comments and blank lines removed, so that only a change of the
+    code itself retires a recorded capture."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2605_26137_b300", "csrc", name)) as f:

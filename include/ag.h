@@ -61,7 +61,7 @@ typedef enum {
 enum { AG_BVH_Q8 = 0, AG_BVH_F32 = 1 };
 /* Collapse rules: expand the child with the largest surface area, the largest
  * surface area x triangle count, or the most triangles. */
-enum { AG_COLLAPSE_AREA = 0, AG_COLLAPSE_AREA_COUNT = 1, AG_COLLAPSE_COUNT = 2 };
+enum { AG_COLLAPSE_AREA = 0, AG_COLLAPSE_AREA_COUNT = 1, AG_COLLAPSE_COUNT = 2, AG_COLLAPSE_SAH = 3 };
 
 /* Ray-list tile shapes (texels), see ag_opts.ray_tile. */
 enum { AG_TILE_8x8 = 0, AG_TILE_16x16 = 1, AG_TILE_32x8 = 2, AG_TILE_4x4 = 3 };
@@ -122,9 +122,11 @@ typedef struct {
     int32_t blocks_per_sm; /* persistent trace CTAs per SM (0 = schedule default) */
     int32_t max_steps;   /* per-ray traversal step cap (0 = 1<<20); exceeding it sets
                             AG_ERR_TRAVERSAL_LIMIT */
-    int32_t collapse;    /* ag_bvh_build: child chosen for expansion while collapsing the binary
-                            tree into 8-wide nodes: AG_COLLAPSE_AREA (0, default),
-                            AG_COLLAPSE_AREA_COUNT or AG_COLLAPSE_COUNT */
+    int32_t collapse;    /* ag_bvh_build: how the binary tree collapses into 8-wide nodes:
+                            AG_COLLAPSE_SAH (ag_opts_default: the children that minimise the
+                            tree's surface-area cost, a bottom-up dynamic program over the
+                            binary tree), or greedy expansion of the largest child by area
+                            (AG_COLLAPSE_AREA, 0), area x count or count */
     int32_t ray_tile;    /* ag_bake*: atlas tile shape that orders the ray list, AG_TILE_*
                             (a warp's 32 rays come from one tile; default AG_TILE_8x8) */
     int32_t query;       /* ag_bake*, ag_autotune: AG_QUERY_RAY (0, default) or AG_QUERY_CLOSEST */

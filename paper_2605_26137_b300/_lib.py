@@ -24,6 +24,7 @@ AG_BVH_F32 = 1
 AG_COLLAPSE_AREA = 0
 AG_COLLAPSE_AREA_COUNT = 1
 AG_COLLAPSE_COUNT = 2
+AG_COLLAPSE_SAH = 3
 AG_TILE_8x8 = 0
 AG_TILE_16x16 = 1
 AG_TILE_32x8 = 2

@@ -118,7 +118,7 @@ ag_status check_opts(const ag_opts &o) {
     if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
     if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_REFILL)
         return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
-    if (o.collapse < AG_COLLAPSE_AREA || o.collapse > AG_COLLAPSE_COUNT)
+    if (o.collapse < AG_COLLAPSE_AREA || o.collapse > AG_COLLAPSE_SAH)
         return set_error(AG_ERR_INVALID_ARG, "unknown collapse rule");
     if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
     if (o.query != AG_QUERY_RAY && o.query != AG_QUERY_CLOSEST)
@@ -237,6 +237,7 @@ AG_API void ag_opts_default(ag_opts *o) {
     o->gutter = 2;
     o->disp_fp16 = 1;
     o->schedule = AG_SCHED_AUTO;
+    o->collapse = AG_COLLAPSE_SAH;
 }
 
 AG_API int32_t ag_version(void) { return 100; }

@@ -208,16 +208,70 @@ __global__ void k_karras(const unsigned *__restrict__ k, int64_t n, int2 *__rest
     parent[right] = (int)i;
 }
 
-// bottom-up boxes: box_lo/hi [2n-1]; flags [n-1] zeroed
+// ---- SAH-optimal collapse (AG_COLLAPSE_SAH) ---------------------------------------------
+// cost[8 * node + i - 1] = C(node, i): the least surface-area cost of the
+// node's subtree when it may take up to i child slots of its wide parent.
+//   leaf (a subtree of <= LEAF_MAX triangles): A(n) * SAH_TRI * count;
+//   C(n, 1) = leaf cost, or A(n) * SAH_NODE + D(n, 8) for a wide node;
+//   D(n, j) = min over k of C(left, k) + C(right, j - k);
+//   C(n, i) = min(C(n, i - 1), D(n, i)) for i >= 2 (a leaf-sized subtree may
+//   still spread over several slots as smaller leaves).
+// Computed in the bottom-up box pass (the second child to arrive computes the
+// parent's box, then its costs).
+constexpr float SAH_NODE = 1.0f;
+constexpr float SAH_TRI = 0.3f;
+
+__device__ __forceinline__ float box_half_area(float4 lo, float4 hi) {
+    const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__device__ __forceinline__ void sah_node_cost(const int2 *__restrict__ range, const int2 *__restrict__ child,
+                                              int64_t n, int64_t node, float a, float *cost) {
+    float c[8];
+    if (node >= n - 1) {   // one triangle
+#pragma unroll
+        for (int i = 0; i < 8; ++i) c[i] = a * SAH_TRI;
+    } else {
+        const int2 ch = child[node];
+        const int2 rg = range[node];
+        const int cnt = rg.y - rg.x + 1;
+        float cl[8], cr[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            cl[i] = __ldcg(&cost[8 * (int64_t)ch.x + i]);
+            cr[i] = __ldcg(&cost[8 * (int64_t)ch.y + i]);
+        }
+        float d[8];
+#pragma unroll
+        for (int j = 2; j <= 8; ++j) {
+            float best = 3.0e38f;
+#pragma unroll
+            for (int k = 1; k < j; ++k) best = fminf(best, cl[k - 1] + cr[j - k - 1]);
+            d[j - 1] = best;
+        }
+        c[0] = cnt <= LEAF_MAX ? a * SAH_TRI * (float)cnt : a * SAH_NODE + d[7];
+#pragma unroll
+        for (int i = 1; i < 8; ++i) c[i] = fminf(c[i - 1], d[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) __stcg(&cost[8 * node + i], c[i]);
+}
+
+// bottom-up boxes: box_lo/hi [2n-1]; flags [n-1] zeroed; with `cost`, the
+// SAH collapse costs of every node in the same pass
 __global__ void k_bounds(const unsigned *__restrict__ vals, int64_t n, const float4 *__restrict__ tlo,
                          const float4 *__restrict__ thi, const int2 *__restrict__ child,
-                         const int *__restrict__ parent, float4 *box_lo, float4 *box_hi, int *flags) {
+                         const int2 *__restrict__ range, const int *__restrict__ parent, float4 *box_lo,
+                         float4 *box_hi, int *flags, float *cost) {
     int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (kk >= n) return;
     int64_t node = n - 1 + kk;
     unsigned t = vals[kk];
-    box_lo[node] = tlo[t];
-    box_hi[node] = thi[t];
+    const float4 lo0 = tlo[t], hi0 = thi[t];
+    box_lo[node] = lo0;
+    box_hi[node] = hi0;
+    if (cost) sah_node_cost(range, child, n, node, box_half_area(lo0, hi0), cost);
     if (n == 1) return;
     while (true) {
         __threadfence();
@@ -226,8 +280,11 @@ __global__ void k_bounds(const unsigned *__restrict__ vals, int64_t n, const flo
         int2 c = child[p];
         float4 a0 = __ldcg(&box_lo[c.x]), a1 = __ldcg(&box_hi[c.x]);
         float4 b0 = __ldcg(&box_lo[c.y]), b1 = __ldcg(&box_hi[c.y]);
-        __stcg(&box_lo[p], make_float4(fminf(a0.x, b0.x), fminf(a0.y, b0.y), fminf(a0.z, b0.z), 0.f));
-        __stcg(&box_hi[p], make_float4(fmaxf(a1.x, b1.x), fmaxf(a1.y, b1.y), fmaxf(a1.z, b1.z), 0.f));
+        const float4 lo = make_float4(fminf(a0.x, b0.x), fminf(a0.y, b0.y), fminf(a0.z, b0.z), 0.f);
+        const float4 hi = make_float4(fmaxf(a1.x, b1.x), fmaxf(a1.y, b1.y), fmaxf(a1.z, b1.z), 0.f);
+        __stcg(&box_lo[p], lo);
+        __stcg(&box_hi[p], hi);
+        if (cost) sah_node_cost(range, child, n, p, box_half_area(lo, hi), cost);
         node = p;
         if (p == 0) return;
     }
@@ -250,6 +307,7 @@ struct CollapseArgs {
     unsigned *node_count, *tri_count;
     int *q_count_out;
     uint32_t *rec_pos;            // leaf-order record -> sorted position (records written by k_tri_records)
+    const float *sah;             // C(node, 1..8) of the SAH collapse, or null (greedy rules)
 };
 
 __device__ __forceinline__ int subtree_count(const CollapseArgs &A, int b) {
@@ -307,6 +365,38 @@ __device__ void collapse_node(const CollapseArgs &A, int2 item, int2 *__restrict
     int nc = 0;
     if (b >= A.n - 1 || subtree_count(A, b) <= LEAF_MAX) {
         ch[nc++] = b;   // only the root of a tiny mesh gets here
+    } else if (A.sah) {
+        // the slots of the SAH decision: (node, slots) pairs, split while a
+        // node takes more than one slot and splitting is what its cost used
+        int sn[8], sk[8], top = 0;
+        auto split = [&](int node, int j, int &kl) {
+            const int2 c = A.child[node];
+            float best = 3.0e38f;
+            kl = 1;
+            for (int k = 1; k < j; ++k) {
+                const float v = A.sah[8 * (int64_t)c.x + k - 1] + A.sah[8 * (int64_t)c.y + j - k - 1];
+                if (v < best) { best = v; kl = k; }
+            }
+            return c;
+        };
+        int kl;
+        int2 c = split(b, 8, kl);
+        sn[top] = c.y; sk[top++] = 8 - kl;
+        sn[top] = c.x; sk[top++] = kl;
+        while (top > 0) {
+            const int node = sn[--top];
+            int j = sk[top];
+            // fewer slots do as well: use the fewest that reach the cost
+            while (j > 1 && A.sah[8 * (int64_t)node + j - 2] <= A.sah[8 * (int64_t)node + j - 1]) --j;
+            if (j == 1 || node >= A.n - 1) {
+                ch[nc++] = node;
+                continue;
+            }
+            int k2;
+            const int2 cc = split(node, j, k2);
+            sn[top] = cc.y; sk[top++] = j - k2;
+            sn[top] = cc.x; sk[top++] = k2;
+        }
     } else {
         // greedy expansion; each child's priority (-1: a leaf-sized subtree) is
         // computed once when the child enters the list
@@ -522,7 +612,9 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
         AG_CUDA_LAUNCH("k_karras");
         AG_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * (n - 1), s));
     }
-    k_bounds<<<grid_for(n, 256), 256, 0, s>>>(va, n, tlo, thi, child, parent, box_lo, box_hi, flags);
+    float *sah = nullptr;
+    if (rule == AG_COLLAPSE_SAH) AG_CUDA(sc.alloc((void **)&sah, sizeof(float) * 8 * (size_t)nbin));
+    k_bounds<<<grid_for(n, 256), 256, 0, s>>>(va, n, tlo, thi, child, range, parent, box_lo, box_hi, flags, sah);
     AG_CUDA_LAUNCH("k_bounds");
 
     // top-down collapse, one launch per level; the queue lengths stay on the
@@ -530,7 +622,7 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     CollapseArgs A;
     A.n = n; A.child = child; A.range = range; A.box_lo = box_lo; A.box_hi = box_hi; A.vals = va;
     A.V = d_verts; A.F = d_faces; A.nv = nv; A.layout = layout; A.rule = rule; A.nodes = nodes_tmp; A.tris = h->tris;
-    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1; A.rec_pos = rec_pos;
+    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1; A.rec_pos = rec_pos; A.sah = sah;
     AG_CUDA(cudaMemsetAsync(lcounts, 0, sizeof(int) * (COLLAPSE_LEVELS + 1), s));
     k_collapse_init<<<1, 1, 0, s>>>(q0, lcounts, counters);
     AG_CUDA_LAUNCH("k_collapse_init");

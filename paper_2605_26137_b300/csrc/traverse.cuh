@@ -10,7 +10,10 @@
 namespace ag {
 namespace {
 
-constexpr int STACK = 64;
+// Per-thread traversal stack entries.  A visit pushes at most 7 children, so
+// a query whose radius still covers every box (a point-to-mesh distance with a
+// large limit) needs up to 7 x the tree depth; 128 covers depths up to 18.
+constexpr int STACK = 128;
 constexpr float EPS_REL = 4.76837158203125e-07f;  // 2^-21: widening per unit of coordinate magnitude
 
 struct TraceArgs {

@@ -36,7 +36,8 @@ def _need(t: torch.Tensor, name: str, dtype, shape_tail=None):
     return t
 
 
-_COLLAPSE = {"area_count": _lib.AG_COLLAPSE_AREA_COUNT, "area": _lib.AG_COLLAPSE_AREA, "count": _lib.AG_COLLAPSE_COUNT}
+_COLLAPSE = {"area_count": _lib.AG_COLLAPSE_AREA_COUNT, "area": _lib.AG_COLLAPSE_AREA, "count": _lib.AG_COLLAPSE_COUNT,
+             "sah": _lib.AG_COLLAPSE_SAH}
 
 
 _TILES = {"8x8": _lib.AG_TILE_8x8, "16x16": _lib.AG_TILE_16x16, "32x8": _lib.AG_TILE_32x8, "4x4": _lib.AG_TILE_4x4}
@@ -46,7 +47,7 @@ _QUERY = {"ray": _lib.AG_QUERY_RAY, "closest": _lib.AG_QUERY_CLOSEST}
 
 
 def _opts(layout="q8", gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
-          collapse="area", ray_tile="8x8", query="ray"):
+          collapse="sah", ray_tile="8x8", query="ray"):
     return default_opts(bvh_layout=_LAYOUTS[layout], gutter=gutter, disp_fp16=int(bool(disp_fp16)),
                         schedule=_SCHED[schedule] if isinstance(schedule, str) else schedule,
                         block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps,
@@ -59,7 +60,7 @@ class Bvh:
     """8-wide BVH over a high-poly mesh (owns its device memory)."""
 
     def __init__(self, verts: torch.Tensor, faces: torch.Tensor, layout: str = "q8", stream=None,
-                 collapse: str = "area"):
+                 collapse: str = "sah"):
         lib = _lib.load()
         _need(verts, "verts", torch.float32, (3,))
         _need(faces, "faces", torch.int32, (3,))

@@ -50,6 +50,7 @@ def test_opts_default(lib):
     assert o.schedule == _lib.AG_SCHED_AUTO and o.max_steps == 0
     assert o.query == _lib.AG_QUERY_RAY
     assert o.render == _lib.AG_RENDER_RASTER and o.filter == _lib.AG_FILTER_ANISO
+    assert o.collapse == _lib.AG_COLLAPSE_SAH
     assert ctypes.sizeof(_lib.AgOpts) == 64   # 16 int32: query, render and filter took reserved slots
     assert _lib.AgOpts.render.offset == 40 and _lib.AgOpts.filter.offset == 44
 

@@ -64,13 +64,14 @@ def test_sdf_asset_matches_oracle():
     parity.check(st)
 
 
-def test_bvh_structure_invariants():
+@pytest.mark.parametrize("collapse", ["area", "sah"])
+def test_bvh_structure_invariants(collapse):
     import struct
     a = synth.sdf_asset(3, 60_000, 2_000, 256, 256, n_prims=12)
     hv, hf = _t(a.high_v), _t(a.high_f)
     import paper_2605_26137_b300 as pb
     for layout in ("q8", "f32"):
-        bvh = pb.Bvh(hv, hf, layout=layout)
+        bvh = pb.Bvh(hv, hf, layout=layout, collapse=collapse)
         info = bvh.info()
         nodes, tris, ids, vn = bvh.copy_out()
         n = len(a.high_f)
@@ -378,3 +379,22 @@ def test_stream_pipeline_with_stream_ordered_free():
     pb.sync_status()
     for host, _ in outs:
         assert np.array_equal(host.numpy(), ref["normal_rgba8"])
+
+
+@pytest.mark.parametrize("collapse", ["area_count", "count", "sah"])
+def test_collapse_rules_give_identical_bakes(collapse):
+    """Every collapse rule builds a different tree over the same triangles; the
+    closest hit does not depend on the tree, so the maps are byte-identical."""
+    import paper_2605_26137_b300 as pb
+    a = synth.sdf_asset(5, 120_000, 6_000, 512, 384, n_prims=16)
+    hv, hf = _t(a.high_v), _t(a.high_f)
+    lv, lf, uv = _t(a.low_v), _t(a.low_f), _t(a.low_uv)
+    outs = []
+    for rule in ("area", collapse):
+        bvh = pb.Bvh(hv, hf, collapse=rule)
+        o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, aux=True)
+        pb.sync_status()
+        outs.append(parity.to_numpy(o))
+        bvh.free()
+    for k in ("normal_rgba8", "mask", "disp", "hit_tri"):
+        assert np.array_equal(outs[0][k], outs[1][k]), k

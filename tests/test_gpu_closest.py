@@ -204,3 +204,28 @@ def test_point_distance_matches_oracle():
         _, d2k, _, _ = oracle.closest_point(V[F[tri[k]]], np.array([[0, 1, 2]], np.int32), p.astype(np.float64), 10.0)
         assert abs(np.sqrt(d2k) - np.sqrt(d2)) <= 1e-6 * diam
     bvh.free()
+
+
+@pytest.mark.parametrize("collapse", ["sah", "area"])
+def test_point_distance_unbounded_radius_deep_tree(collapse):
+    """A radius as large as the mesh (the Chamfer and Hausdorff measurements)
+    keeps every box in range while the first descent runs: the stack must hold
+    7 entries per level of a deep tree without overflowing.  The ~1M-face
+    surface of the QEM workload; a sample of the distances against the
+    oracle."""
+    import paper_2605_26137_b300 as pb
+    V, F = synth.sdf_mesh_target(synth.sdf_union_params(1, 32), 1_000_000)
+    diam = float(np.linalg.norm(V.max(0) - V.min(0)))
+    rng = np.random.default_rng(8)
+    pts = np.concatenate([V[rng.integers(0, len(V), 20000)] + rng.normal(scale=0.01, size=(20000, 3)),
+                          rng.uniform(-2.0, 2.0, size=(4000, 3))]).astype(np.float32)
+    bvh = pb.Bvh(_t(V), _t(F), collapse=collapse)
+    assert bvh.info()["max_depth"] >= 9
+    d = pb.point_distance(bvh, _t(pts), diam)
+    pb.sync_status()    # raises on a stack overflow
+    d = d.cpu().numpy().astype(np.float64)
+    ob = oracle.Bvh(V, F)
+    for k in rng.choice(len(pts), 300, replace=False):
+        t, d2, _, _ = oracle.closest_point(V, F, pts[k].astype(np.float64), diam, bvh=ob)
+        assert t >= 0 and abs(d[k] - np.sqrt(d2)) <= 1e-6 * diam, k
+    bvh.free()
