@@ -19,7 +19,7 @@ namespace {
 constexpr int RS_BLOCK = 256;
 // collapse levels launched before the host checks the queue (a 30-bit Morton
 // tree collapses to about 12 levels of 8-wide nodes)
-constexpr int COLLAPSE_LEVELS = 24;
+constexpr int COLLAPSE_LEVELS = 16;
 constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_BLOCK * RS_ROUNDS;
 
@@ -209,13 +209,20 @@ __global__ void k_karras(const unsigned *__restrict__ k, int64_t n, int2 *__rest
 }
 
 // ---- SAH-optimal collapse (AG_COLLAPSE_SAH) ---------------------------------------------
-// cost[8 * node + i - 1] = C(node, i): the least surface-area cost of the
-// node's subtree when it may take up to i child slots of its wide parent.
+// cost[8 * node + i - 1] = C(node, i) for the internal nodes: the least
+// surface-area cost of the node's subtree when it may take up to i child
+// slots of its wide parent.
 //   leaf (a subtree of <= LEAF_MAX triangles): A(n) * SAH_TRI * count;
 //   C(n, 1) = leaf cost, or A(n) * SAH_NODE + D(n, 8) for a wide node;
 //   D(n, j) = min over k of C(left, k) + C(right, j - k);
 //   C(n, i) = min(C(n, i - 1), D(n, i)) for i >= 2 (a leaf-sized subtree may
 //   still spread over several slots as smaller leaves).
+// A one-triangle binary leaf costs A * SAH_TRI for every i; it is not stored,
+// the parent takes it from the leaf's box.
+// dec[node] records the decisions the top-down collapse follows, 3 bits each
+// for j = 2..8: bits 3(j-2).. hold k(j) - 1, the first k reaching D(n, j);
+// bits 21 + 3(j-2).. hold f(j) - 1, the fewest slots f <= j with C(n, f) =
+// C(n, j) (the node takes f slots when offered j).
 // Computed in the bottom-up box pass (the second child to arrive computes the
 // parent's box, then its costs).
 constexpr float SAH_NODE = 1.0f;
@@ -226,67 +233,124 @@ __device__ __forceinline__ float box_half_area(float4 lo, float4 hi) {
     return dx * dy + dy * dz + dz * dx;
 }
 
-__device__ __forceinline__ void sah_node_cost(const int2 *__restrict__ range, const int2 *__restrict__ child,
-                                              int64_t n, int64_t node, float a, float *cost) {
-    float c[8];
-    if (node >= n - 1) {   // one triangle
+// costs and decisions of internal node `node` from its children's costs cl
+// (left) and cr (right) and its own half area a; c receives C(node, 1..8)
+__device__ __forceinline__ void sah_node_cost(const float (&cl)[8], const float (&cr)[8], int cnt, float a,
+                                              int64_t node, float (&c)[8], float *cost, uint64_t *dec) {
+    float d[8];
+    uint64_t code = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) c[i] = a * SAH_TRI;
-    } else {
-        const int2 ch = child[node];
-        const int2 rg = range[node];
-        const int cnt = rg.y - rg.x + 1;
-        float cl[8], cr[8];
+    for (int j = 2; j <= 8; ++j) {
+        float best = 3.0e38f;
+        int kb = 1;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            cl[i] = __ldcg(&cost[8 * (int64_t)ch.x + i]);
-            cr[i] = __ldcg(&cost[8 * (int64_t)ch.y + i]);
+        for (int k = 1; k < j; ++k) {
+            const float v = cl[k - 1] + cr[j - k - 1];
+            if (v < best) { best = v; kb = k; }
         }
-        float d[8];
-#pragma unroll
-        for (int j = 2; j <= 8; ++j) {
-            float best = 3.0e38f;
-#pragma unroll
-            for (int k = 1; k < j; ++k) best = fminf(best, cl[k - 1] + cr[j - k - 1]);
-            d[j - 1] = best;
-        }
-        c[0] = cnt <= LEAF_MAX ? a * SAH_TRI * (float)cnt : a * SAH_NODE + d[7];
-#pragma unroll
-        for (int i = 1; i < 8; ++i) c[i] = fminf(c[i - 1], d[i]);
+        d[j - 1] = best;
+        code |= (uint64_t)(kb - 1) << (3 * (j - 2));
     }
+    c[0] = cnt <= LEAF_MAX ? a * SAH_TRI * (float)cnt : a * SAH_NODE + d[7];
+    int f = 1;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) __stcg(&cost[8 * node + i], c[i]);
+    for (int i = 1; i < 8; ++i) {
+        c[i] = fminf(c[i - 1], d[i]);
+        if (!(c[i - 1] <= c[i])) f = i + 1;   // C(n, i + 1) < C(n, i): the fewest is i + 1
+        code |= (uint64_t)(f - 1) << (21 + 3 * (i - 1));
+    }
+    float4 *q = reinterpret_cast<float4 *>(cost + 8 * node);
+    __stcg(q, make_float4(c[0], c[1], c[2], c[3]));
+    __stcg(q + 1, make_float4(c[4], c[5], c[6], c[7]));
+    __stcg(&dec[node], code);
 }
 
-// bottom-up boxes: box_lo/hi [2n-1]; flags [n-1] zeroed; with `cost`, the
-// SAH collapse costs of every node in the same pass
+// arrival count of a binary node: adds 1 and returns the old count. With
+// `rel` the caller's earlier stores are visible to whoever sees the new count;
+// with `acq` the caller sees the stores of the thread that counted before it.
+__device__ __forceinline__ int arrive(int *p, bool rel, bool acq) {
+    int old;
+    if (rel && acq) asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    else if (rel) asm volatile("atom.release.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    else if (acq) asm volatile("atom.acquire.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
+    else old = atomicAdd(p, 1);
+    return old;
+}
+
+// bottom-up boxes: box_lo/hi [2n-1]; flags [n-1] zeroed; with `cost` and
+// `dec`, the SAH collapse costs and decisions of every internal node in the
+// same pass. A thread climbs from its leaf while it is the second child to
+// arrive; it keeps its own node's box and costs in registers and reads only
+// the sibling's. A leaf's box and cost follow from the triangle boxes, which
+// earlier kernels wrote, so only internal nodes publish (release) and only a
+// thread whose sibling is internal needs to see that (acquire). The parent's
+// links and a leaf sibling's box are read before the arrival count comes back.
 __global__ void k_bounds(const unsigned *__restrict__ vals, int64_t n, const float4 *__restrict__ tlo,
                          const float4 *__restrict__ thi, const int2 *__restrict__ child,
                          const int2 *__restrict__ range, const int *__restrict__ parent, float4 *box_lo,
-                         float4 *box_hi, int *flags, float *cost) {
+                         float4 *box_hi, int *flags, float *cost, uint64_t *dec) {
     int64_t kk = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (kk >= n) return;
     int64_t node = n - 1 + kk;
     unsigned t = vals[kk];
-    const float4 lo0 = tlo[t], hi0 = thi[t];
-    box_lo[node] = lo0;
-    box_hi[node] = hi0;
-    if (cost) sah_node_cost(range, child, n, node, box_half_area(lo0, hi0), cost);
+    float4 lo = tlo[t], hi = thi[t];
+    __stcg(&box_lo[node], lo);
+    __stcg(&box_hi[node], hi);
     if (n == 1) return;
+    float own[8];
+    {
+        const float la = box_half_area(lo, hi) * SAH_TRI;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) own[i] = la;
+    }
+    bool own_leaf = true;
+    int p = parent[node];
     while (true) {
-        __threadfence();
-        int p = parent[node];
-        if (atomicAdd(&flags[p], 1) == 0) return;
-        int2 c = child[p];
-        float4 a0 = __ldcg(&box_lo[c.x]), a1 = __ldcg(&box_hi[c.x]);
-        float4 b0 = __ldcg(&box_lo[c.y]), b1 = __ldcg(&box_hi[c.y]);
-        const float4 lo = make_float4(fminf(a0.x, b0.x), fminf(a0.y, b0.y), fminf(a0.z, b0.z), 0.f);
-        const float4 hi = make_float4(fmaxf(a1.x, b1.x), fmaxf(a1.y, b1.y), fmaxf(a1.z, b1.z), 0.f);
+        const int2 c = child[p];
+        const int2 rg = cost ? range[p] : make_int2(0, 0);
+        const int pp = p ? parent[p] : 0;
+        const bool left = c.x == node;
+        const int sib = left ? c.y : c.x;
+        const bool sib_leaf = sib >= n - 1;
+        float4 s0, s1;
+        if (sib_leaf) {
+            const unsigned st = vals[sib - (n - 1)];
+            s0 = tlo[st];
+            s1 = thi[st];
+        }
+        if (arrive(&flags[p], !own_leaf, !sib_leaf) == 0) return;
+        float sc[8];
+        if (sib_leaf) {
+            const float sa = box_half_area(s0, s1) * SAH_TRI;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sc[i] = sa;
+        } else {
+            s0 = __ldcg(&box_lo[sib]);
+            s1 = __ldcg(&box_hi[sib]);
+            if (cost) {
+                const float4 *q = reinterpret_cast<const float4 *>(cost + 8 * (int64_t)sib);
+                const float4 u = __ldcg(q), v = __ldcg(q + 1);
+                sc[0] = u.x; sc[1] = u.y; sc[2] = u.z; sc[3] = u.w;
+                sc[4] = v.x; sc[5] = v.y; sc[6] = v.z; sc[7] = v.w;
+            }
+        }
+        lo = make_float4(fminf(lo.x, s0.x), fminf(lo.y, s0.y), fminf(lo.z, s0.z), 0.f);
+        hi = make_float4(fmaxf(hi.x, s1.x), fmaxf(hi.y, s1.y), fmaxf(hi.z, s1.z), 0.f);
         __stcg(&box_lo[p], lo);
         __stcg(&box_hi[p], hi);
-        if (cost) sah_node_cost(range, child, n, p, box_half_area(lo, hi), cost);
+        if (cost) {
+            float cl[8], cr[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                cl[i] = left ? own[i] : sc[i];
+                cr[i] = left ? sc[i] : own[i];
+            }
+            sah_node_cost(cl, cr, rg.y - rg.x + 1, box_half_area(lo, hi), p, own, cost, dec);
+        }
         node = p;
+        own_leaf = false;
         if (p == 0) return;
+        p = pp;
     }
 }
 
@@ -307,17 +371,13 @@ struct CollapseArgs {
     unsigned *node_count, *tri_count;
     int *q_count_out;
     uint32_t *rec_pos;            // leaf-order record -> sorted position (records written by k_tri_records)
-    const float *sah;             // C(node, 1..8) of the SAH collapse, or null (greedy rules)
+    const uint64_t *sah_dec;      // decisions of the SAH collapse (internal nodes), or null (greedy rules)
 };
 
 __device__ __forceinline__ int subtree_count(const CollapseArgs &A, int b) {
     if (b >= A.n - 1) return 1;
     int2 r = A.range[b];
     return r.y - r.x + 1;
-}
-__device__ __forceinline__ int subtree_first(const CollapseArgs &A, int b) {
-    if (b >= A.n - 1) return (int)(b - (A.n - 1));
-    return A.range[b].x;
 }
 __device__ __forceinline__ float half_area(const CollapseArgs &A, int b) {
     float4 lo = A.box_lo[b], hi = A.box_hi[b];
@@ -327,9 +387,10 @@ __device__ __forceinline__ float half_area(const CollapseArgs &A, int b) {
 
 // smallest power-of-two exponent (biased, as float exponent bits) such that
 // every child box quantises into 0..255 with outward rounding verified in the
-// exact decode arithmetic of the traversal: fmaf(q, 2^e, origin).
-__device__ int choose_exp(float o, float hi_node, const float *clo, const float *chi, int nc,
-                          unsigned char *qlo, unsigned char *qhi) {
+// exact decode arithmetic of the traversal: fmaf(q, 2^e, origin). Slots from
+// nc on get the empty box (lo 255, hi 0).
+__device__ __forceinline__ int choose_exp(float o, float hi_node, const float (&clo)[8], const float (&chi)[8],
+                                          int nc, int (&qlo)[8], int (&qhi)[8]) {
     float ext = hi_node - o;
     int e;
     if (!(ext > 0.f)) e = 1;
@@ -342,7 +403,11 @@ __device__ int choose_exp(float o, float hi_node, const float *clo, const float 
         float s = __uint_as_float((unsigned)e << 23);
         const float inv = 1.0f / s;   // a power of two: x * inv is exactly x / s
         bool ok = true;
-        for (int c = 0; c < nc && ok; ++c) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            qlo[c] = 255;
+            qhi[c] = 0;
+            if (c >= nc) continue;
             int ql = (int)floorf((clo[c] - o) * inv);
             ql = max(0, min(255, ql));
             while (ql > 0 && fmaf((float)ql, s, o) > clo[c]) --ql;
@@ -350,53 +415,87 @@ __device__ int choose_exp(float o, float hi_node, const float *clo, const float 
             qh = max(0, qh);
             while (qh <= 255 && fmaf((float)qh, s, o) < chi[c]) ++qh;
             while (qh > 0 && qh - 1 >= ql && fmaf((float)(qh - 1), s, o) >= chi[c]) --qh;
-            if (qh > 255 || fmaf((float)ql, s, o) > clo[c]) { ok = false; break; }
-            qlo[c] = (unsigned char)ql;
-            qhi[c] = (unsigned char)qh;
+            if (qh > 255 || fmaf((float)ql, s, o) > clo[c]) ok = false;
+            qlo[c] = ql;
+            qhi[c] = min(qh, 255);
         }
         if (ok || e >= 254) return e;
     }
 }
 
-__device__ void collapse_node(const CollapseArgs &A, int2 item, int2 *__restrict__ q_out) {
+// all 32 lanes of the warp call this together: each lane gets `v` entries of
+// the counter, with one atomic per warp
+__device__ __forceinline__ unsigned warp_alloc(unsigned *ctr, unsigned v) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += t;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31u && total) base = atomicAdd(ctr, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + incl - v;
+}
+
+// the children of the wide node made from binary node item.x, written to wide
+// slot item.y; `live` is false for the lanes past the end of the queue, which
+// only take part in the warp's counter allocations
+__device__ void collapse_node(const CollapseArgs &A, int2 item, bool live, int2 *__restrict__ q_out) {
     int b = item.x;
     unsigned wslot = (unsigned)item.y;
     int ch[8];
     int nc = 0;
-    if (b >= A.n - 1 || subtree_count(A, b) <= LEAF_MAX) {
+    if (!live) {
+    } else if (b >= A.n - 1 || subtree_count(A, b) <= LEAF_MAX) {
         ch[nc++] = b;   // only the root of a tiny mesh gets here
-    } else if (A.sah) {
-        // the slots of the SAH decision: (node, slots) pairs, split while a
-        // node takes more than one slot and splitting is what its cost used
-        int sn[8], sk[8], top = 0;
-        auto split = [&](int node, int j, int &kl) {
-            const int2 c = A.child[node];
-            float best = 3.0e38f;
-            kl = 1;
-            for (int k = 1; k < j; ++k) {
-                const float v = A.sah[8 * (int64_t)c.x + k - 1] + A.sah[8 * (int64_t)c.y + j - k - 1];
-                if (v < best) { best = v; kl = k; }
-            }
-            return c;
-        };
-        int kl;
-        int2 c = split(b, 8, kl);
-        sn[top] = c.y; sk[top++] = 8 - kl;
-        sn[top] = c.x; sk[top++] = kl;
-        while (top > 0) {
-            const int node = sn[--top];
-            int j = sk[top];
-            // fewer slots do as well: use the fewest that reach the cost
-            while (j > 1 && A.sah[8 * (int64_t)node + j - 2] <= A.sah[8 * (int64_t)node + j - 1]) --j;
-            if (j == 1 || node >= A.n - 1) {
-                ch[nc++] = node;
-                continue;
-            }
-            int k2;
-            const int2 cc = split(node, j, k2);
-            sn[top] = cc.y; sk[top++] = j - k2;
-            sn[top] = cc.x; sk[top++] = k2;
+    } else if (A.sah_dec) {
+        // the SAH decisions, breadth first: every round splits each entry
+        // (node, slots) that still takes several slots, in place, so that the
+        // children keep the binary tree's left-to-right order; the loads of
+        // one round are independent of each other
+        int sn[8], sk[8];
+        bool fin[8];
+        {
+            const int2 c = A.child[b];
+            const int kl = (int)((A.sah_dec[b] >> 18) & 7u) + 1;   // k(8) of the root
+            sn[0] = c.x; sk[0] = kl; fin[0] = false;
+            sn[1] = c.y; sk[1] = 8 - kl; fin[1] = false;
+            nc = 2;
         }
+        for (int round = 0; round < 8; ++round) {
+            uint64_t dd[8];
+            int2 cc[8];
+            bool any = false;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i < nc && !fin[i]) {
+                    if (sn[i] >= A.n - 1 || sk[i] == 1) fin[i] = true;
+                    else { dd[i] = A.sah_dec[sn[i]]; cc[i] = A.child[sn[i]]; any = true; }
+                }
+            }
+            if (!any) break;
+            int tn[8], tk[8];
+            bool tf[8];
+            int m = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i >= nc) continue;
+                if (fin[i]) { tn[m] = sn[i]; tk[m] = sk[i]; tf[m++] = true; continue; }
+                // f(slots) <= slots and 1 <= k(f) < f by construction; the
+                // clamps keep the list within 8 entries whatever the word holds
+                const int j = min(sk[i], (int)((dd[i] >> (21 + 3 * (sk[i] - 2))) & 7u) + 1);
+                if (j == 1) { tn[m] = sn[i]; tk[m] = 1; tf[m++] = true; continue; }
+                const int kl = min(j - 1, (int)((dd[i] >> (3 * (j - 2))) & 7u) + 1);
+                tn[m] = cc[i].x; tk[m] = kl; tf[m++] = false;
+                tn[m] = cc[i].y; tk[m] = j - kl; tf[m++] = false;
+            }
+            nc = m;
+            for (int i = 0; i < m; ++i) { sn[i] = tn[i]; sk[i] = tk[i]; fin[i] = tf[i]; }
+        }
+        for (int i = 0; i < nc; ++i) ch[i] = sn[i];
     } else {
         // greedy expansion; each child's priority (-1: a leaf-sized subtree) is
         // computed once when the child enters the list
@@ -422,68 +521,89 @@ __device__ void collapse_node(const CollapseArgs &A, int2 item, int2 *__restrict
             ch[nc] = cc.y; pr[nc++] = prio(cc.y);
         }
     }
-    int n_int = 0, n_tri = 0;
-    for (int k = 0; k < nc; ++k) {
-        int cnt = subtree_count(A, ch[k]);
-        if (cnt <= LEAF_MAX) n_tri += cnt; else ++n_int;
+    // per child: triangle count, first sorted position and box, the loads of
+    // all children issued together
+    const float4 nlo = A.box_lo[live ? b : 0], nhi = A.box_hi[live ? b : 0];
+    int cnt[8], first[8];
+    float clo[3][8], chi[3][8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        cnt[k] = 0;
+        first[k] = 0;
+        clo[0][k] = clo[1][k] = clo[2][k] = 1.f;
+        chi[0][k] = chi[1][k] = chi[2][k] = -1.f;
+        if (k < nc) {
+            const int c = ch[k];
+            const int2 r = c >= A.n - 1 ? make_int2(c - (int)(A.n - 1), c - (int)(A.n - 1)) : A.range[c];
+            cnt[k] = r.y - r.x + 1;
+            first[k] = r.x;
+            const float4 lo = A.box_lo[c], hi = A.box_hi[c];
+            clo[0][k] = lo.x; clo[1][k] = lo.y; clo[2][k] = lo.z;
+            chi[0][k] = hi.x; chi[1][k] = hi.y; chi[2][k] = hi.z;
+        }
     }
-    unsigned child_base = n_int ? atomicAdd(A.node_count, (unsigned)n_int) : 0u;
-    unsigned tri_base = n_tri ? atomicAdd(A.tri_count, (unsigned)n_tri) : 0u;
-    unsigned char meta[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int n_int = 0, n_tri = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (cnt[k] > LEAF_MAX) ++n_int;
+        else n_tri += cnt[k];
+    }
+    const unsigned child_base = warp_alloc(A.node_count, (unsigned)n_int);
+    const unsigned tri_base = warp_alloc(A.tri_count, (unsigned)n_tri);
+    const unsigned q_base = warp_alloc(reinterpret_cast<unsigned *>(A.q_count_out), (unsigned)n_int);
+    if (!live) return;
+    uint32_t meta[2] = {0u, 0u};
     int rank = 0, toff = 0;
-    for (int k = 0; k < nc; ++k) {
-        int cnt = subtree_count(A, ch[k]);
-        if (cnt > LEAF_MAX) {
-            meta[k] = (unsigned char)(0x80 | rank);
-            int slot = atomicAdd(A.q_count_out, 1);
-            q_out[slot] = make_int2(ch[k], (int)(child_base + rank));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k >= nc) continue;
+        uint32_t m;
+        if (cnt[k] > LEAF_MAX) {
+            m = 0x80u | (uint32_t)rank;
+            q_out[q_base + rank] = make_int2(ch[k], (int)(child_base + rank));
             ++rank;
         } else {
-            meta[k] = (unsigned char)((cnt << 5) | toff);
-            const int first = subtree_first(A, ch[k]);
-            for (int j = 0; j < cnt; ++j) A.rec_pos[tri_base + toff + j] = (uint32_t)(first + j);
-            toff += cnt;
+            m = (uint32_t)((cnt[k] << 5) | toff);
+            for (int j = 0; j < cnt[k]; ++j) A.rec_pos[tri_base + toff + j] = (uint32_t)(first[k] + j);
+            toff += cnt[k];
         }
-    }
-    // node box = box of binary node b; child boxes
-    float clo[3][8], chi[3][8];
-    for (int k = 0; k < nc; ++k) {
-        float4 lo = A.box_lo[ch[k]], hi = A.box_hi[ch[k]];
-        clo[0][k] = lo.x; clo[1][k] = lo.y; clo[2][k] = lo.z;
-        chi[0][k] = hi.x; chi[1][k] = hi.y; chi[2][k] = hi.z;
+        meta[k >> 2] |= m << (8 * (k & 3));
     }
     if (A.layout == AG_BVH_Q8) {
-        QNode nd;
-        float4 blo = A.box_lo[b], bhi = A.box_hi[b];
-        float o[3] = {blo.x, blo.y, blo.z}, h[3] = {bhi.x, bhi.y, bhi.z};
-        unsigned char qlo[3][8], qhi[3][8];
+        // the 80-byte node as 20 words (the QNode field order), five 16-byte stores
+        const float o[3] = {nlo.x, nlo.y, nlo.z}, h[3] = {nhi.x, nhi.y, nhi.z};
+        uint32_t qw[12];
         int e[3];
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            e[a] = choose_exp(o[a], h[a], clo[a], chi[a], nc, qlo[a], qhi[a]);
-            for (int k = nc; k < 8; ++k) { qlo[a][k] = 255; qhi[a][k] = 0; }
+            int ql[8], qh[8];
+            e[a] = choose_exp(o[a], h[a], clo[a], chi[a], nc, ql, qh);
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                qw[2 * a + w] = (uint32_t)ql[4 * w] | ((uint32_t)ql[4 * w + 1] << 8) |
+                                ((uint32_t)ql[4 * w + 2] << 16) | ((uint32_t)ql[4 * w + 3] << 24);
+                qw[6 + 2 * a + w] = (uint32_t)qh[4 * w] | ((uint32_t)qh[4 * w + 1] << 8) |
+                                    ((uint32_t)qh[4 * w + 2] << 16) | ((uint32_t)qh[4 * w + 3] << 24);
+            }
         }
-        nd.ox = o[0]; nd.oy = o[1]; nd.oz = o[2];
-        nd.ex = (uint8_t)e[0]; nd.ey = (uint8_t)e[1]; nd.ez = (uint8_t)e[2];
-        nd.nchild = (uint8_t)nc;
-        nd.child_base = child_base;
-        nd.tri_base = tri_base;
-        for (int k = 0; k < 8; ++k) {
-            nd.meta[k] = meta[k];
-            nd.qlox[k] = qlo[0][k]; nd.qloy[k] = qlo[1][k]; nd.qloz[k] = qlo[2][k];
-            nd.qhix[k] = qhi[0][k]; nd.qhiy[k] = qhi[1][k]; nd.qhiz[k] = qhi[2][k];
-        }
-        ((QNode *)A.nodes)[wslot] = nd;
+        const uint32_t hdr = (uint32_t)e[0] | ((uint32_t)e[1] << 8) | ((uint32_t)e[2] << 16) | ((uint32_t)nc << 24);
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<QNode *>(A.nodes) + wslot);
+        dst[0] = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]), hdr);
+        dst[1] = make_uint4(child_base, tri_base, meta[0], meta[1]);
+        dst[2] = make_uint4(qw[0], qw[1], qw[2], qw[3]);
+        dst[3] = make_uint4(qw[4], qw[5], qw[6], qw[7]);
+        dst[4] = make_uint4(qw[8], qw[9], qw[10], qw[11]);
     } else {
         FNode nd;
         nd.child_base = child_base;
         nd.tri_base = tri_base;
+#pragma unroll
         for (int k = 0; k < 8; ++k) {
-            nd.meta[k] = meta[k];
-            bool v = k < nc;
-            nd.lox[k] = v ? clo[0][k] : 1.f; nd.loy[k] = v ? clo[1][k] : 1.f; nd.loz[k] = v ? clo[2][k] : 1.f;
-            nd.hix[k] = v ? chi[0][k] : -1.f; nd.hiy[k] = v ? chi[1][k] : -1.f; nd.hiz[k] = v ? chi[2][k] : -1.f;
+            nd.meta[k] = (uint8_t)(meta[k >> 2] >> (8 * (k & 3)));
+            nd.lox[k] = clo[0][k]; nd.loy[k] = clo[1][k]; nd.loz[k] = clo[2][k];
+            nd.hix[k] = chi[0][k]; nd.hiy[k] = chi[1][k]; nd.hiz[k] = chi[2][k];
         }
-        ((FNode *)A.nodes)[wslot] = nd;
+        static_cast<FNode *>(A.nodes)[wslot] = nd;
     }
 }
 
@@ -492,8 +612,13 @@ __device__ void collapse_node(const CollapseArgs &A, int2 item, int2 *__restrict
 __global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, const int *__restrict__ nq_in,
                            int2 *__restrict__ q_out) {
     const int nq = *nq_in;
-    for (int qi = blockIdx.x * blockDim.x + threadIdx.x; qi < nq; qi += gridDim.x * blockDim.x)
-        collapse_node(A, q_in[qi], q_out);
+    // the loop bound is uniform over the block, so that whole warps call the
+    // counter allocations together
+    for (int q0 = blockIdx.x * blockDim.x; q0 < nq; q0 += gridDim.x * blockDim.x) {
+        const int qi = q0 + threadIdx.x;
+        const bool live = qi < nq;
+        collapse_node(A, live ? q_in[qi] : make_int2(0, 0), live, q_out);
+    }
 }
 
 // the 48-byte leaf-order triangle records, one thread per record
@@ -613,8 +738,14 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
         AG_CUDA(cudaMemsetAsync(flags, 0, sizeof(int) * (n - 1), s));
     }
     float *sah = nullptr;
-    if (rule == AG_COLLAPSE_SAH) AG_CUDA(sc.alloc((void **)&sah, sizeof(float) * 8 * (size_t)nbin));
-    k_bounds<<<grid_for(n, 256), 256, 0, s>>>(va, n, tlo, thi, child, range, parent, box_lo, box_hi, flags, sah);
+    uint64_t *sah_dec = nullptr;
+    if (rule == AG_COLLAPSE_SAH) {
+        const size_t n_int = (size_t)std::max<int64_t>(1, n - 1);
+        AG_CUDA(sc.alloc((void **)&sah, sizeof(float) * 8 * n_int));
+        AG_CUDA(sc.alloc((void **)&sah_dec, sizeof(uint64_t) * n_int));
+    }
+    k_bounds<<<grid_for(n, 256), 256, 0, s>>>(va, n, tlo, thi, child, range, parent, box_lo, box_hi, flags, sah,
+                                              sah_dec);
     AG_CUDA_LAUNCH("k_bounds");
 
     // top-down collapse, one launch per level; the queue lengths stay on the
@@ -622,7 +753,7 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     CollapseArgs A;
     A.n = n; A.child = child; A.range = range; A.box_lo = box_lo; A.box_hi = box_hi; A.vals = va;
     A.V = d_verts; A.F = d_faces; A.nv = nv; A.layout = layout; A.rule = rule; A.nodes = nodes_tmp; A.tris = h->tris;
-    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1; A.rec_pos = rec_pos; A.sah = sah;
+    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1; A.rec_pos = rec_pos; A.sah_dec = sah_dec;
     AG_CUDA(cudaMemsetAsync(lcounts, 0, sizeof(int) * (COLLAPSE_LEVELS + 1), s));
     k_collapse_init<<<1, 1, 0, s>>>(q0, lcounts, counters);
     AG_CUDA_LAUNCH("k_collapse_init");

@@ -398,3 +398,40 @@ def test_collapse_rules_give_identical_bakes(collapse):
         bvh.free()
     for k in ("normal_rgba8", "mask", "disp", "hit_tri"):
         assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def _wide_tree_cost(nodes, node_size):
+    """Surface-area cost of an FP32-layout wide tree, the root excluded: every
+    wide child costs its box's half area, every leaf 0.3 x half area x count."""
+    import struct
+    raw = nodes.reshape(-1, node_size)
+    total = 0.0
+    for r in raw:
+        meta = r[8:16]
+        f = np.frombuffer(r[16:208].tobytes(), np.float32).reshape(6, 8).astype(np.float64)
+        d = f[3:] - f[:3]
+        ha = d[0] * d[1] + d[1] * d[2] + d[2] * d[0]
+        for c in range(8):
+            m = int(meta[c])
+            if m == 0:
+                continue
+            total += ha[c] if m & 0x80 else 0.3 * ha[c] * ((m >> 5) & 3)
+    return total
+
+
+def test_sah_collapse_costs_no_more_than_greedy_rules():
+    """The SAH collapse minimises the surface-area cost over every way of
+    cutting the same binary tree into 8-wide nodes, and each greedy rule makes
+    one such cut: its tree costs at least as much (to float rounding)."""
+    import paper_2605_26137_b300 as pb
+    a = synth.sdf_asset(6, 40_000, 2_000, 256, 256, n_prims=10)
+    hv, hf = _t(a.high_v), _t(a.high_f)
+    cost = {}
+    for rule in ("sah", "area", "area_count", "count"):
+        bvh = pb.Bvh(hv, hf, layout="f32", collapse=rule)
+        nodes, _, _, _ = bvh.copy_out()
+        cost[rule] = _wide_tree_cost(nodes, bvh.info()["node_size"])
+        bvh.free()
+    print(cost)
+    for rule in ("area", "area_count", "count"):
+        assert cost["sah"] <= cost[rule] * (1 + 1e-5), rule
