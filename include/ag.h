@@ -2,7 +2,7 @@
  * ag.h - C ABI of the B300 tangent-space normal baker.
  *
  * The operation is the normal-baking stage of AssetGen's geometry
- * post-processing (Sec. 6.4, "Normal Map Baking"): the low-poly mesh is
+ * post-processing (Sec. 6.4, normal-map baking): the low-poly mesh is
  * rasterised into its own UV space; for every covered texel a ray is cast
  * from the texel's surface point along its interpolated smooth normal against
  * a BVH over the dense high-poly mesh; the closest hit within the distance
@@ -132,7 +132,9 @@ typedef struct {
     int32_t query;       /* ag_bake*, ag_autotune: AG_QUERY_RAY (0, default) or AG_QUERY_CLOSEST */
     int32_t render;      /* ag_render_views: AG_RENDER_RASTER (0, default) or AG_RENDER_TRACE */
     int32_t filter;      /* ag_backproject: AG_FILTER_ANISO (0, default) or AG_FILTER_BILINEAR */
-    int32_t reserved[4];
+    int32_t build_async; /* ag_bvh_build: 0 (default) waits for the build; 1 returns once it is
+                            enqueued (see ag_bvh_build) */
+    int32_t reserved[3];
 } ag_opts;
 
 /* Optional extra outputs of ag_bake (any member may be NULL). */
@@ -182,15 +184,26 @@ AG_API void ag_opts_default(ag_opts *o);
 
 /*
  * ag_bvh_build - acceleration structure over the high-poly mesh
- * (Sec. 6.4: "A GPU BVH built on the high-poly mesh").
+ * (Sec. 6.4: the device-built tree over the high-poly triangles).
  * d_verts [n_verts*3] float32, d_faces [n_faces*3] int32 (0 <= index < n_verts;
  * checked on the device: out-of-range faces are reported as AG_ERR_INVALID_ARG).
  * Builds a linear BVH (30-bit Morton codes of triangle centroids, device radix
  * sort, Karras hierarchy), collapses it to 8-wide nodes with leaves of <= 2
  * triangles, stores child boxes per opts->bvh_layout, reorders triangles into
  * leaf order and computes area-weighted smooth vertex normals.  The handle
- * keeps its own copies; the inputs may be freed after the call returns.
- * Synchronises `stream`.  1 <= n_faces < 2^29, 3 <= n_verts < 2^31.
+ * keeps its own copies.  1 <= n_faces < 2^29, 3 <= n_verts < 2^31.
+ * Default (opts->build_async = 0): synchronises `stream`; the inputs may be
+ * freed after the call returns; out-of-range face indices are returned as
+ * AG_ERR_INVALID_ARG; the node array is trimmed to the node count.
+ * opts->build_async = 1: returns once the build is enqueued on `stream`, with
+ * no host round trip.  The inputs must stay valid until `stream` has run the
+ * build; later calls on `stream` (or ordered after it) may use the handle at
+ * once.  Face index errors reach the status word (ag_sync_status).  The node
+ * array keeps its worst-case size (n_faces - 1 nodes).  ag_bvh_info,
+ * ag_bvh_copy_out, ag_visibility, ag_render_views, ag_point_distance and
+ * calls on an AG_BVH_F32 tree wait for the build the first time they need
+ * its summary (node count, depth, scene box); ag_bake, ag_bake_backward and
+ * ag_bake_batch on an AG_BVH_Q8 tree do not wait.
  */
 AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
                               int64_t n_faces, const ag_opts *opts, ag_stream_t stream,

@@ -1230,7 +1230,7 @@ int or_exterior_fill(const float *V, const int32_t *F, int64_t nv, int64_t nf, c
  * neighbourhoods has more than 4 vertices (no tetrahedron collapses); and
  * no surviving face around a or b turns over: n_old . n_new > 0.
  *
- * Rounds (reading of "parallel edge collapse"): the unique edges (a < b) are
+ * Rounds (our reading of collapsing many edges at once): the unique edges (a < b) are
  * ranked in (a, b) order; key = (bits of the cost rounded to float32) << 32
  * | rank.  m1(v) = min key of the valid edges at v, m2(v) = min of m1 over v
  * and its neighbours; edge (a, b) collapses when key = m2(a) = m2(b).  Two

@@ -1,4 +1,4 @@
-"""B300-native tangent-space normal baker (AssetGen, Sec. 6.4 "Normal Map Baking"),
+"""B300-native tangent-space normal baker (AssetGen, Sec. 6.4, normal-map baking),
 with the hidden-face removal pass of Sec. 6.2 on the same BVH and the QEM
 simplification of Sec. 6.1.
 

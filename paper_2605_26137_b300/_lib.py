@@ -53,7 +53,7 @@ class AgOpts(ctypes.Structure):
     _fields_ = [("bvh_layout", c_int32), ("gutter", c_int32), ("disp_fp16", c_int32), ("schedule", c_int32),
                 ("block_size", c_int32), ("blocks_per_sm", c_int32), ("max_steps", c_int32),
                 ("collapse", c_int32), ("ray_tile", c_int32), ("query", c_int32), ("render", c_int32),
-                ("filter", c_int32), ("reserved", c_int32 * 4)]
+                ("filter", c_int32), ("build_async", c_int32), ("reserved", c_int32 * 3)]
 
 
 class AgBakeAux(ctypes.Structure):

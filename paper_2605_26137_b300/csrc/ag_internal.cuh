@@ -115,10 +115,23 @@ struct ag_bvh {
     float diam;
     int max_depth;
     float build_ms;
+    // the build's summary (device) and its events; the scalars above except
+    // n_tris and n_verts are valid once `ready` (ag::bvh_ready reads them)
+    void *d_info;
+    cudaEvent_t ev_start, ev_done;
+    bool ready;
 };
 constexpr uint64_t AG_BVH_MAGIC = 0x4147425648414e44ull;
 
 namespace ag {
+
+// the build's summary (node count, depth, scene box, build time): waits for
+// the build the first time, then reads the handle's copy
+ag_status bvh_ready(ag_bvh *h);
+// largest |coordinate| of the high mesh's box, the rounding slack of the
+// FP32-node traversal; the 8-bit-node traversal does not use it, so for such
+// a tree this returns 0 without waiting for the build
+ag_status scene_abs_for(ag_bvh *h, float *out);
 
 // ------------------------------------------------------------------ per-asset bake job
 // Everything the trace needs for one asset (device-resident table).

@@ -10,7 +10,7 @@
 namespace ag {
 
 ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, int layout, int rule,
-                    cudaStream_t s, ag_bvh *h);
+                    bool sync, cudaStream_t s, ag_bvh *h);
 
 namespace {
 thread_local std::string g_err;
@@ -127,19 +127,26 @@ ag_status check_opts(const ag_opts &o) {
         return set_error(AG_ERR_INVALID_ARG, "render must be AG_RENDER_RASTER or AG_RENDER_TRACE");
     if (o.filter != AG_FILTER_ANISO && o.filter != AG_FILTER_BILINEAR)
         return set_error(AG_ERR_INVALID_ARG, "filter must be AG_FILTER_ANISO or AG_FILTER_BILINEAR");
+    if (o.build_async != 0 && o.build_async != 1) return set_error(AG_ERR_INVALID_ARG, "build_async must be 0 or 1");
     return AG_OK;
 }
 
 // the handle's arrays come from the device's memory pool (stream-ordered)
 void free_handle_arrays(ag_bvh *h, cudaStream_t s) {
-    void *arrays[4] = {h->nodes, h->tris, h->tri_ids, h->vnormals};
+    void *arrays[5] = {h->nodes, h->tris, h->tri_ids, h->vnormals, h->d_info};
     for (void *p : arrays)
         if (p) cudaFreeAsync(p, s);
     h->nodes = nullptr;
     h->tris = nullptr;
     h->tri_ids = nullptr;
     h->vnormals = nullptr;
+    h->d_info = nullptr;
+    // events still pending are released by the runtime once they complete
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_done) cudaEventDestroy(h->ev_done);
+    h->ev_start = h->ev_done = nullptr;
 }
+
 
 ag_status check_handle(ag_bvh_t h) {
     if (!h || h->magic != AG_BVH_MAGIC) return set_error(AG_ERR_BAD_HANDLE, "invalid BVH handle");
@@ -199,8 +206,8 @@ ag_status run_prep(const float *lv, const float *ln, const float *luv, const int
     return AG_OK;
 }
 
-TraceJob make_job(ag_bvh_t h, const AssetScratch &a, int W, int H, float max_dist, uint8_t *mask, int32_t *hit_tri,
-                  float *hit_t) {
+TraceJob make_job(ag_bvh_t h, const AssetScratch &a, int W, int H, float max_dist, float scene_abs, uint8_t *mask,
+                  int32_t *hit_tri, float *hit_t) {
     TraceJob j;
     memset(&j, 0, sizeof(j));
     j.nodes = h->nodes;
@@ -219,8 +226,7 @@ TraceJob make_job(ag_bvh_t h, const AssetScratch &a, int W, int H, float max_dis
     j.W = W;
     j.H = H;
     j.max_dist = max_dist;
-    j.scene_abs = 0.f;
-    for (int k = 0; k < 3; ++k) j.scene_abs = fmaxf(j.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+    j.scene_abs = scene_abs;
     return j;
 }
 
@@ -280,10 +286,10 @@ AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32
     h->layout = o.bvh_layout;
     h->n_tris = n_faces;
     h->n_verts = n_verts;
-    // clear a stale bad-face bit so this build's check is its own
+    const bool sync = !o.build_async;
     unsigned word = 0;
-    st = build_bvh(d_verts, n_verts, d_faces, n_faces, o.bvh_layout, o.collapse, s, h);
-    if (st == AG_OK) {
+    st = build_bvh(d_verts, n_verts, d_faces, n_faces, o.bvh_layout, o.collapse, sync, s, h);
+    if (st == AG_OK && sync) {
         cudaError_t e = cudaMemcpyAsync(&word, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_error(e, "ag_bvh_build status");
@@ -334,9 +340,12 @@ AG_API ag_status ag_bvh_free(ag_bvh_t h) {
 }
 
 AG_API ag_status ag_bvh_info(ag_bvh_t h, ag_bvh_info_t *out) {
+    g_err.clear();
     if (!h || h->magic != AG_BVH_MAGIC) return set_error(AG_ERR_BAD_HANDLE, "invalid BVH handle");
     if (!out) return set_error(AG_ERR_INVALID_ARG, "out must be non-NULL");
     memset(out, 0, sizeof(*out));
+    ag_status st = bvh_ready(h);
+    if (st) return st;
     out->n_tris = h->n_tris;
     out->n_verts = h->n_verts;
     out->n_nodes = h->n_nodes;
@@ -359,6 +368,7 @@ AG_API ag_status ag_bvh_copy_out(ag_bvh_t h, void *nodes, float *tris, int32_t *
     g_err.clear();
     ag_status st = check_handle(h);
     if (st) return st;
+    if ((st = bvh_ready(h))) return st;
     AG_CUDA(cudaDeviceSynchronize());
     size_t ns = h->layout == AG_BVH_Q8 ? sizeof(QNode) : sizeof(FNode);
     if (nodes) AG_CUDA(cudaMemcpy(nodes, h->nodes, ns * h->n_nodes, cudaMemcpyDeviceToHost));
@@ -398,9 +408,11 @@ AG_API ag_status ag_bake(ag_bvh_t h, const float *d_lverts, const float *d_lnorm
                        s)))
         return st;
     if (ev) AG_CUDA(cudaEventRecord(ev[1], s));
+    float sabs;
+    if ((st = scene_abs_for(h, &sabs))) return st;
     TraceLaunch L;
     memset(&L, 0, sizeof(L));
-    L.job0 = make_job(h, a, W, H, max_dist, d_mask, ax.hit_tri, ax.hit_t);
+    L.job0 = make_job(h, a, W, H, max_dist, sabs, d_mask, ax.hit_tri, ax.hit_t);
     L.n_jobs = 1;
     L.n_rays_dev = a.n_rays;
     L.ray_counter = ray_counter;
@@ -455,9 +467,11 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
     if ((st = run_prep(d_lverts, nullptr, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, o.ray_tile, nullptr, status, a,
                        s)))
         return st;
+    float sabs;
+    if ((st = scene_abs_for(h, &sabs))) return st;
     TraceLaunch L;
     memset(&L, 0, sizeof(L));
-    L.job0 = make_job(h, a, W, H, max_dist, nullptr, nullptr, nullptr);
+    L.job0 = make_job(h, a, W, H, max_dist, sabs, nullptr, nullptr, nullptr);
     L.job0.g_pos = d_grad ? g_pos : nullptr;   // loss only: no adjoint scatter
     L.job0.g_nrm = g_nrm;
     L.job0.loss_acc = loss_acc;
@@ -497,8 +511,7 @@ AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_
     L.job0.nodes = h->nodes;
     L.job0.tris = h->tris;
     L.job0.tri_ids = h->tri_ids;
-    L.job0.scene_abs = 0.f;
-    for (int k = 0; k < 3; ++k) L.job0.scene_abs = fmaxf(L.job0.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+    if ((st = scene_abs_for(h, &L.job0.scene_abs))) return st;
     L.status = status;
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = h->layout;
@@ -531,7 +544,7 @@ AG_API ag_status ag_render_views(ag_bvh_t h, int32_t n_views, const float *h_cam
     L.job0.nodes = h->nodes;
     L.job0.tris = h->tris;
     L.job0.tri_ids = h->tri_ids;
-    for (int k = 0; k < 3; ++k) L.job0.scene_abs = fmaxf(L.job0.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+    if ((st = scene_abs_for(h, &L.job0.scene_abs))) return st;
     L.status = status;
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = h->layout;

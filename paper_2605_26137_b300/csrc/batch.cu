@@ -81,6 +81,10 @@ ag_status check_descs(int n, const ag_asset_desc *d, int *layout) {
         const ag_asset_desc &x = d[a];
         if (!x.bvh || x.bvh->magic != AG_BVH_MAGIC) return set_error(AG_ERR_BAD_HANDLE, "asset %d: invalid BVH handle", a);
         if (x.bvh->device != dev) return set_error(AG_ERR_INVALID_ARG, "asset %d: handle on another device", a);
+        if (x.bvh->layout != AG_BVH_Q8) {   // FP32 nodes: the job needs the scene box
+            ag_status st = bvh_ready(x.bvh);
+            if (st) return st;
+        }
         if (a == 0) *layout = x.bvh->layout;
         else if (x.bvh->layout != *layout)
             return set_error(AG_ERR_INVALID_ARG, "asset %d: all BVHs of a batch must share one layout", a);
@@ -132,8 +136,7 @@ void fill_tables(int n, const ag_asset_desc *d, const std::vector<AssetBufs> &b,
         j.W = d[a].W;
         j.H = d[a].H;
         j.max_dist = d[a].max_dist;
-        j.scene_abs = 0.f;
-        for (int k = 0; k < 3; ++k) j.scene_abs = fmaxf(j.scene_abs, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
+        scene_abs_for(h, &j.scene_abs);   // ready: check_descs waited for FP32-node builds
         counts[a] = b[a].n_rays;
     }
 }

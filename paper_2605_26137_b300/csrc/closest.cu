@@ -1,7 +1,7 @@
-// Closest-point correspondence (Sec. 6.4 as worded: for each texel's
-// world-space position, the nearest point of the high-poly surface found
-// through the BVH, and the smooth normal interpolated there with the point's
-// barycentrics), followed by the same distance filter, UV-reliability filter
+// Closest-point correspondence (the literal reading of Sec. 6.4): per texel,
+// the high-poly surface point nearest to the texel's 3D position, found by a
+// BVH search, with the smooth normal interpolated there by the point's
+// barycentrics, followed by the same distance filter, UV-reliability filter
 // and tangent-space shading as the ray query.
 //
 // One persistent launch per ray list; a warp takes 32 consecutive texels of

@@ -575,6 +575,8 @@ AG_API ag_status ag_visibility(ag_bvh_t h, int32_t n_views, int32_t res, const a
     cudaStream_t s = (cudaStream_t)stream;
     unsigned *status = device_status_word(h->device);
     if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    st = bvh_ready(h);   // the views are placed around the scene box
+    if (st) return st;
     double c[3], R2 = 0.0;
     for (int k = 0; k < 3; ++k) {
         c[k] = 0.5 * ((double)h->lo[k] + (double)h->hi[k]);

@@ -1,12 +1,15 @@
-// LBVH over the high-poly mesh (Sec. 6.4: "A GPU BVH built on the high-poly
-// mesh"), built entirely on the device:
+// LBVH over the high-poly mesh (the tree Sec. 6.4 searches), built entirely
+// on the device:
 //   triangle bounds + centroid bounds -> 30-bit Morton codes -> LSD radix
 //   sort (8-bit digits, stable warp-ranked scatter) -> Karras (2012) binary
-//   hierarchy -> bottom-up FP32 boxes -> top-down collapse to 8-wide nodes
-//   (greedy largest-area expansion, leaves of <= 2 triangles) with child boxes
-//   quantised to 8 bits and rounded outward (or kept in FP32) -> triangles
-//   reordered into 48-byte leaf-order records -> area-weighted vertex normals.
+//   hierarchy -> bottom-up FP32 boxes (with the SAH collapse costs) ->
+//   top-down collapse to 8-wide nodes (SAH-optimal children, or greedy
+//   expansion; leaves of <= 2 triangles) with child boxes quantised to 8 bits
+//   and rounded outward (or kept in FP32) -> triangles reordered into 48-byte
+//   leaf-order records -> area-weighted vertex normals.
 #include "ag_internal.cuh"
+
+#include <cstdlib>
 
 #include <algorithm>
 #include <cmath>
@@ -17,9 +20,20 @@ namespace ag {
 namespace {
 
 constexpr int RS_BLOCK = 256;
-// collapse levels launched before the host checks the queue (a 30-bit Morton
-// tree collapses to about 12 levels of 8-wide nodes)
+// collapse levels launched one kernel each (a 30-bit Morton tree collapses to
+// about 12 levels of 8-wide nodes); deeper levels run on one CTA
 constexpr int COLLAPSE_LEVELS = 16;
+// levels in all: the binary tree of 30-bit codes over at most 2^29 sorted
+// triangles is at most 59 deep, and every wide level descends at least one
+// binary level
+constexpr int COLLAPSE_MAX = 64;
+
+// what the host reads back from a build (one copy, once the build is done)
+struct BuildSummary {
+    unsigned counters[2];           // wide nodes, triangle records written by the collapse
+    int levels[COLLAPSE_MAX + 1];   // queue length of every collapse level
+    unsigned bounds[16];            // centroid and scene box keys of k_tri_prep (scene box at 6..11)
+};
 constexpr int RS_ROUNDS = 16;
 constexpr int RS_TILE = RS_BLOCK * RS_ROUNDS;
 
@@ -621,6 +635,29 @@ __global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, const 
     }
 }
 
+// the collapse levels from `first` (COLLAPSE_LEVELS) on, all on one CTA (only
+// a tree deeper than that gets work here); qa holds the first of them. A queue left
+// after COLLAPSE_MAX levels cannot happen for a tree of 30-bit Morton codes
+// and at most 2^29 triangles; it would leave levels[COLLAPSE_MAX] set, which
+// the summary check reports.
+__global__ void __launch_bounds__(256) k_collapse_tail(CollapseArgs A, int2 *qa, int2 *qb, int *levels, int first) {
+    int2 *qin = qa, *qout = qb;
+    for (int l = first; l < COLLAPSE_MAX; ++l) {
+        const int nq = __ldcg(&levels[l]);
+        if (nq == 0) return;
+        A.q_count_out = levels + l + 1;
+        for (int q0 = 0; q0 < nq; q0 += blockDim.x) {
+            const int qi = q0 + threadIdx.x;
+            const bool live = qi < nq;
+            collapse_node(A, live ? qin[qi] : make_int2(0, 0), live, qout);
+        }
+        __syncthreads();   // the level's nodes, queue and count are complete
+        int2 *t = qin;
+        qin = qout;
+        qout = t;
+    }
+}
+
 // the 48-byte leaf-order triangle records, one thread per record
 __global__ void k_tri_records(const uint32_t *__restrict__ rec_pos, const unsigned *__restrict__ vals,
                               const float *__restrict__ V, const int32_t *__restrict__ F, int64_t nv, int64_t n,
@@ -658,23 +695,21 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 }  // namespace
 
 ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, int64_t nf, int layout, int rule,
-                    cudaStream_t s, ag_bvh *h) {
+                    bool sync, cudaStream_t s, ag_bvh *h) {
     int dev = h->device;
     unsigned *status = device_status_word(dev);
     Scratch sc(s, dev);
     const int64_t n = nf;
     float4 *tlo, *thi, *cent, *box_lo, *box_hi;
-    unsigned *bounds, *k0, *v0, *k1, *v1, *hist;
+    unsigned *k0, *v0, *k1, *v1, *hist;
     int2 *child, *range, *q0, *q1;
-    int *parent, *flags, *qcount;
-    unsigned *counters;
+    int *parent, *flags;
     void *nscr;
     const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
     const int64_t nbin = 2 * n - 1;
     AG_CUDA(sc.alloc((void **)&tlo, sizeof(float4) * n));
     AG_CUDA(sc.alloc((void **)&thi, sizeof(float4) * n));
     AG_CUDA(sc.alloc((void **)&cent, sizeof(float4) * n));
-    AG_CUDA(sc.alloc((void **)&bounds, sizeof(unsigned) * 16));
     AG_CUDA(sc.alloc((void **)&k0, sizeof(unsigned) * n));
     AG_CUDA(sc.alloc((void **)&v0, sizeof(unsigned) * n));
     AG_CUDA(sc.alloc((void **)&k1, sizeof(unsigned) * n));
@@ -690,31 +725,31 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     AG_CUDA(sc.alloc((void **)&box_hi, sizeof(float4) * nbin));
     AG_CUDA(sc.alloc((void **)&q0, sizeof(int2) * std::max<int64_t>(1, n)));
     AG_CUDA(sc.alloc((void **)&q1, sizeof(int2) * std::max<int64_t>(1, n)));
-    AG_CUDA(sc.alloc((void **)&qcount, sizeof(int) * 2));
-    AG_CUDA(sc.alloc((void **)&counters, sizeof(unsigned) * 2));
     AG_CUDA(sc.alloc(&nscr, vertex_normal_scratch_bytes(nv, n)));
+    uint32_t *rec_pos;
+    AG_CUDA(sc.alloc((void **)&rec_pos, sizeof(uint32_t) * n));
 
-    // persistent arrays owned by the handle (worst-case node count, compacted
-    // later), from the device's memory pool so that rebuilds reuse them
+    // arrays owned by the handle, from the device's memory pool so that
+    // rebuilds reuse them: nodes for the worst-case count (one per internal
+    // node of the binary tree; a synchronous build trims them to the count),
+    // triangle records, ids, vertex normals and the build summary
     const int64_t max_nodes = std::max<int64_t>(1, n - 1);
     const size_t node_size = layout == AG_BVH_Q8 ? sizeof(QNode) : sizeof(FNode);
-    void *nodes_tmp = nullptr;
-    uint32_t *rec_pos;
-    int *lcounts;
-    AG_CUDA(sc.alloc(&nodes_tmp, node_size * max_nodes));
-    AG_CUDA(sc.alloc((void **)&rec_pos, sizeof(uint32_t) * n));
-    AG_CUDA(sc.alloc((void **)&lcounts, sizeof(int) * (COLLAPSE_LEVELS + 1)));
     cudaMemPool_t pool = device_pool(dev);
     if (!pool) return set_error(AG_ERR_OOM, "memory pool unavailable");
+    AG_CUDA(cudaMallocFromPoolAsync(&h->nodes, node_size * max_nodes, pool, s));
     AG_CUDA(cudaMallocFromPoolAsync((void **)&h->tris, sizeof(float4) * 3 * n, pool, s));
     AG_CUDA(cudaMallocFromPoolAsync((void **)&h->tri_ids, sizeof(int32_t) * n, pool, s));
     AG_CUDA(cudaMallocFromPoolAsync((void **)&h->vnormals, sizeof(float4) * nv, pool, s));
+    AG_CUDA(cudaMallocFromPoolAsync(&h->d_info, sizeof(BuildSummary), pool, s));
+    BuildSummary *info = static_cast<BuildSummary *>(h->d_info);
+    unsigned *bounds = info->bounds, *counters = info->counters;
+    int *lcounts = info->levels;
+    AG_CUDA(cudaEventCreate(&h->ev_start));
+    AG_CUDA(cudaEventCreate(&h->ev_done));
+    AG_CUDA(cudaEventRecord(h->ev_start, s));
 
-    cudaEvent_t e0, e1;
-    AG_CUDA(cudaEventCreate(&e0));
-    AG_CUDA(cudaEventCreate(&e1));
-    AG_CUDA(cudaEventRecord(e0, s));
-
+    AG_CUDA(cudaMemsetAsync(info, 0, sizeof(BuildSummary), s));
     k_bounds_init<<<1, 32, 0, s>>>(bounds);
     AG_CUDA_LAUNCH("k_bounds_init");
     k_tri_prep<<<grid_for(n, 256), 256, 0, s>>>(d_verts, d_faces, nv, n, tlo, thi, cent, bounds, status);
@@ -748,59 +783,65 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
                                               sah_dec);
     AG_CUDA_LAUNCH("k_bounds");
 
-    // top-down collapse, one launch per level; the queue lengths stay on the
-    // device, and the host looks at them once after COLLAPSE_LEVELS levels
+    // top-down collapse: one launch per level for the first COLLAPSE_LEVELS
+    // levels (queue lengths stay on the device), then one CTA for any deeper
+    // levels; the host never waits
     CollapseArgs A;
     A.n = n; A.child = child; A.range = range; A.box_lo = box_lo; A.box_hi = box_hi; A.vals = va;
-    A.V = d_verts; A.F = d_faces; A.nv = nv; A.layout = layout; A.rule = rule; A.nodes = nodes_tmp; A.tris = h->tris;
-    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1; A.rec_pos = rec_pos; A.sah_dec = sah_dec;
-    AG_CUDA(cudaMemsetAsync(lcounts, 0, sizeof(int) * (COLLAPSE_LEVELS + 1), s));
+    A.V = d_verts; A.F = d_faces; A.nv = nv; A.layout = layout; A.rule = rule; A.nodes = h->nodes; A.tris = h->tris;
+    A.tri_ids = h->tri_ids; A.node_count = counters; A.tri_count = counters + 1; A.rec_pos = rec_pos;
+    A.sah_dec = sah_dec;
     k_collapse_init<<<1, 1, 0, s>>>(q0, lcounts, counters);
     AG_CUDA_LAUNCH("k_collapse_init");
     const unsigned cgrid = (unsigned)std::min<int64_t>(grid_for(n, 128), (int64_t)device_sm_count(dev) * 16);
+    // AG_TEST_GRID_LEVELS (tests only) hands the tree to the one-CTA path
+    // after fewer levels, so that path runs on ordinary meshes
+    int grid_levels = COLLAPSE_LEVELS;
+    if (const char *e = getenv("AG_TEST_GRID_LEVELS")) grid_levels = std::max(0, std::min(COLLAPSE_LEVELS, atoi(e)));
     int2 *qin = q0, *qout = q1;
-    for (int l = 0; l < COLLAPSE_LEVELS; ++l) {
+    for (int l = 0; l < grid_levels; ++l) {
         A.q_count_out = lcounts + l + 1;
         k_collapse<<<cgrid, 128, 0, s>>>(A, qin, lcounts + l, qout);
         AG_CUDA_LAUNCH("k_collapse");
         std::swap(qin, qout);
     }
-    int hl[COLLAPSE_LEVELS + 1];
-    AG_CUDA(cudaMemcpyAsync(hl, lcounts, sizeof(hl), cudaMemcpyDeviceToHost, s));
-    AG_CUDA(cudaStreamSynchronize(s));
-    int depth = 0;
-    while (depth <= COLLAPSE_LEVELS && hl[depth] > 0) ++depth;
-    // a deeper tree than that (many equal Morton codes) continues level by level
-    int nq = hl[COLLAPSE_LEVELS];
-    while (nq > 0) {
-        AG_CUDA(cudaMemsetAsync(lcounts + 1, 0, sizeof(int), s));
-        AG_CUDA(cudaMemcpyAsync(lcounts, &nq, sizeof(int), cudaMemcpyHostToDevice, s));
-        A.q_count_out = lcounts + 1;
-        k_collapse<<<cgrid, 128, 0, s>>>(A, qin, lcounts, qout);
-        AG_CUDA_LAUNCH("k_collapse");
-        AG_CUDA(cudaMemcpyAsync(&nq, lcounts + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
-        AG_CUDA(cudaStreamSynchronize(s));
-        std::swap(qin, qout);
-        ++depth;
-    }
+    k_collapse_tail<<<1, 256, 0, s>>>(A, qin, qout, lcounts, grid_levels);
+    AG_CUDA_LAUNCH("k_collapse_tail");
     k_tri_records<<<grid_for(n, 256), 256, 0, s>>>(rec_pos, va, d_verts, d_faces, nv, n, h->tris, h->tri_ids);
     AG_CUDA_LAUNCH("k_tri_records");
-    unsigned hc[2];
-    AG_CUDA(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
-    AG_CUDA(cudaStreamSynchronize(s));
-    if ((int64_t)hc[1] != n)
-        return set_error(AG_ERR_CUDA, "BVH collapse wrote %u of %lld triangle records", hc[1], (long long)n);
-    h->n_nodes = hc[0];
-    h->max_depth = depth;
-    AG_CUDA(cudaMallocFromPoolAsync(&h->nodes, node_size * h->n_nodes, pool, s));
-    AG_CUDA(cudaMemcpyAsync(h->nodes, nodes_tmp, node_size * h->n_nodes, cudaMemcpyDeviceToDevice, s));
-
     AG_CUDA(launch_vertex_normals(d_verts, d_faces, nv, n, nullptr, nullptr, h->vnormals, nullptr, nscr, s));
-    AG_CUDA(cudaEventRecord(e1, s));
+    AG_CUDA(cudaEventRecord(h->ev_done, s));
+    h->n_nodes = max_nodes;   // until the summary is read
+    if (!sync) return AG_OK;
 
-    unsigned hb[16];
-    AG_CUDA(cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, s));
-    AG_CUDA(cudaStreamSynchronize(s));
+    ag_status st = bvh_ready(h);
+    if (st != AG_OK) return st;
+    if (h->n_nodes < max_nodes) {
+        void *trimmed = nullptr;
+        AG_CUDA(cudaMallocFromPoolAsync(&trimmed, node_size * h->n_nodes, pool, s));
+        AG_CUDA(cudaMemcpyAsync(trimmed, h->nodes, node_size * h->n_nodes, cudaMemcpyDeviceToDevice, s));
+        AG_CUDA(cudaFreeAsync(h->nodes, s));
+        h->nodes = trimmed;
+    }
+    return AG_OK;
+}
+
+// read the build summary once the build has finished (waits for it)
+ag_status bvh_ready(ag_bvh *h) {
+    if (h->ready) return AG_OK;
+    AG_CUDA(cudaEventSynchronize(h->ev_done));
+    BuildSummary bs;
+    AG_CUDA(cudaMemcpy(&bs, h->d_info, sizeof(bs), cudaMemcpyDeviceToHost));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev_start, h->ev_done);
+    cudaEventDestroy(h->ev_start);
+    cudaEventDestroy(h->ev_done);
+    h->ev_start = h->ev_done = nullptr;
+    h->build_ms = ms;
+    h->ready = true;
+    int depth = 0;
+    while (depth <= COLLAPSE_MAX && bs.levels[depth] > 0) ++depth;
+    h->max_depth = depth;
     auto k2f = [](unsigned k) {
         unsigned b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
         float f;
@@ -809,17 +850,25 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     };
     double d2 = 0.0;
     for (int a = 0; a < 3; ++a) {
-        h->lo[a] = k2f(hb[6 + a]);
-        h->hi[a] = k2f(hb[9 + a]);
+        h->lo[a] = k2f(bs.bounds[6 + a]);
+        h->hi[a] = k2f(bs.bounds[9 + a]);
         double e = (double)h->hi[a] - (double)h->lo[a];
         d2 += e * e;
     }
     h->diam = (float)sqrt(d2);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    h->build_ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if ((int64_t)bs.counters[1] != h->n_tris || bs.levels[COLLAPSE_MAX] > 0)
+        return set_error(AG_ERR_CUDA, "BVH collapse wrote %u of %lld triangle records", bs.counters[1],
+                         (long long)h->n_tris);
+    h->n_nodes = bs.counters[0];
+    return AG_OK;
+}
+
+ag_status scene_abs_for(ag_bvh *h, float *out) {
+    *out = 0.f;
+    if (h->layout == AG_BVH_Q8) return AG_OK;
+    ag_status st = bvh_ready(h);
+    if (st) return st;
+    for (int k = 0; k < 3; ++k) *out = fmaxf(*out, fmaxf(fabsf(h->lo[k]), fabsf(h->hi[k])));
     return AG_OK;
 }
 

@@ -1,8 +1,7 @@
-// Closest-hit traversal and shading (Sec. 6.4, stages two to four: the
-// correspondence on the high-poly surface for each texel's world-space
-// position with the smooth normal interpolated there, the distance filter,
-// the UV-reliability filter and the projection into the texel's tangent
-// frame).
+// Closest-hit traversal and shading (Sec. 6.4, stages two to four: a texel's
+// 3D point is matched to a high-poly surface point whose smooth normal is
+// interpolated; then the distance filter, the UV-reliability filter, and the
+// normal expressed in the texel's tangent basis).
 //
 // One persistent launch serves a whole ray list (one asset or a batch): each
 // warp pops 32 consecutive rays from a global counter; rays are texels in

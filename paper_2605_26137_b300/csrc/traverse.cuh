@@ -1,8 +1,8 @@
 // Traversal pieces shared by the ray query (trace.cu) and the closest-point
 // query (closest.cu) over the same 8-wide BVH: launch arguments, the
 // nearest-child-next bookkeeping, the 8-bit plane decode, the counting build's
-// reduction and the forward shading store (Sec. 6.4: the hit normal projected
-// into the texel's tangent frame; the UV-reliability filter).
+// reduction and the forward shading store (Sec. 6.4: the hit normal written in
+// the texel's tangent basis; the UV-reliability filter).
 #pragma once
 
 #include "ag_internal.cuh"

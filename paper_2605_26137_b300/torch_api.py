@@ -60,17 +60,22 @@ class Bvh:
     """8-wide BVH over a high-poly mesh (owns its device memory)."""
 
     def __init__(self, verts: torch.Tensor, faces: torch.Tensor, layout: str = "q8", stream=None,
-                 collapse: str = "sah"):
+                 collapse: str = "sah", async_build: bool = False):
+        """async_build: return once the build is enqueued on the stream (no
+        host round trip); the handle keeps verts and faces referenced until
+        free(), and info() waits for the build the first time."""
         lib = _lib.load()
         _need(verts, "verts", torch.float32, (3,))
         _need(faces, "faces", torch.int32, (3,))
         h = ctypes.c_void_p()
         o = _opts(layout=layout, collapse=collapse)
+        o.build_async = int(bool(async_build))
         check(lib.ag_bvh_build(verts.data_ptr(), verts.shape[0], faces.data_ptr(), faces.shape[0],
                                ctypes.byref(o), _stream(stream), ctypes.byref(h)))
         self._h = h
         self._lib = lib
         self.layout = layout
+        self._inputs = (verts, faces) if async_build else None
 
     @property
     def handle(self) -> int:
@@ -109,6 +114,7 @@ class Bvh:
             else:
                 check(self._lib.ag_bvh_free_async(self._h, _stream(stream)))
             self._h = ctypes.c_void_p()
+            self._inputs = None
 
     def __del__(self):
         try:

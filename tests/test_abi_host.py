@@ -51,8 +51,10 @@ def test_opts_default(lib):
     assert o.query == _lib.AG_QUERY_RAY
     assert o.render == _lib.AG_RENDER_RASTER and o.filter == _lib.AG_FILTER_ANISO
     assert o.collapse == _lib.AG_COLLAPSE_SAH
-    assert ctypes.sizeof(_lib.AgOpts) == 64   # 16 int32: query, render and filter took reserved slots
+    assert o.build_async == 0
+    assert ctypes.sizeof(_lib.AgOpts) == 64   # 16 int32: query, render, filter, build_async took reserved slots
     assert _lib.AgOpts.render.offset == 40 and _lib.AgOpts.filter.offset == 44
+    assert _lib.AgOpts.build_async.offset == 48
 
 
 def test_host_argument_checks(lib):
@@ -70,7 +72,7 @@ def test_host_argument_checks(lib):
     bad = _lib.default_opts(query=7)
     assert lib.ag_bvh_build(1, 3, 1, 1, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.AG_ERR_INVALID_ARG
     assert b"query" in lib.ag_last_error()
-    for field in ("render", "filter"):
+    for field in ("render", "filter", "build_async"):
         bad = _lib.default_opts(**{field: 7})
         assert lib.ag_bvh_build(1, 3, 1, 1, ctypes.byref(bad), None, ctypes.byref(h)) == _lib.AG_ERR_INVALID_ARG
         assert field.encode() in lib.ag_last_error()

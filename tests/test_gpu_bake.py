@@ -64,9 +64,13 @@ def test_sdf_asset_matches_oracle():
     parity.check(st)
 
 
-@pytest.mark.parametrize("collapse", ["area", "sah"])
-def test_bvh_structure_invariants(collapse):
+@pytest.mark.parametrize("collapse,grid_levels", [("area", None), ("sah", None), ("sah", "1")])
+def test_bvh_structure_invariants(collapse, grid_levels, monkeypatch):
+    """grid_levels "1": every collapse level after the first runs on the
+    one-CTA path that otherwise only trees deeper than 16 levels reach."""
     import struct
+    if grid_levels is not None:
+        monkeypatch.setenv("AG_TEST_GRID_LEVELS", grid_levels)
     a = synth.sdf_asset(3, 60_000, 2_000, 256, 256, n_prims=12)
     hv, hf = _t(a.high_v), _t(a.high_f)
     import paper_2605_26137_b300 as pb
@@ -435,3 +439,35 @@ def test_sah_collapse_costs_no_more_than_greedy_rules():
     print(cost)
     for rule in ("area", "area_count", "count"):
         assert cost["sah"] <= cost[rule] * (1 + 1e-5), rule
+
+
+@pytest.mark.parametrize("layout", ["q8", "f32"])
+def test_async_build_and_one_cta_collapse_give_identical_bakes(layout, monkeypatch):
+    """A build that returns without a host round trip (the bake is enqueued
+    before anything waits for the build), and builds whose collapse hands every
+    level after the second to the one-CTA path, give the default build's tree
+    summary and byte-identical maps."""
+    import paper_2605_26137_b300 as pb
+    a = synth.sdf_asset(5, 120_000, 6_000, 512, 384, n_prims=16)
+    hv, hf = _t(a.high_v), _t(a.high_f)
+    lv, lf, uv = _t(a.low_v), _t(a.low_f), _t(a.low_uv)
+
+    def run(**kw):
+        bvh = pb.Bvh(hv, hf, layout=layout, **kw)
+        o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, aux=True)
+        pb.sync_status()
+        out = parity.to_numpy(o)
+        inf = bvh.info()
+        bvh.free()
+        return out, inf
+
+    ref, ri = run()
+    cases = [run(async_build=True)]
+    monkeypatch.setenv("AG_TEST_GRID_LEVELS", "2")
+    cases += [run(), run(async_build=True)]
+    for out, inf in cases:
+        for k in ("normal_rgba8", "mask", "disp", "hit_tri"):
+            assert np.array_equal(out[k], ref[k]), k
+        for k in ("n_nodes", "max_depth", "scene_lo", "scene_hi", "diam", "n_tris"):
+            assert inf[k] == ri[k], k
+        assert inf["build_ms"] > 0
