@@ -247,10 +247,25 @@ __device__ __forceinline__ float box_half_area(float4 lo, float4 hi) {
     return dx * dy + dy * dz + dz * dx;
 }
 
-// costs and decisions of internal node `node` from its children's costs cl
-// (left) and cr (right) and its own half area a; c receives C(node, 1..8)
-__device__ __forceinline__ void sah_node_cost(const float (&cl)[8], const float (&cr)[8], int cnt, float a,
-                                              int64_t node, float (&c)[8], float *cost, uint64_t *dec) {
+__device__ __forceinline__ void sah_child_cost(int c, int64_t n, float area, const float *cost, float *out) {
+    if (c >= n - 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) out[i] = area * SAH_TRI;
+    } else {
+        const float4 *q = reinterpret_cast<const float4 *>(cost + 8 * (int64_t)c);
+        const float4 u = __ldcg(q), v = __ldcg(q + 1);
+        out[0] = u.x; out[1] = u.y; out[2] = u.z; out[3] = u.w;
+        out[4] = v.x; out[5] = v.y; out[6] = v.z; out[7] = v.w;
+    }
+}
+
+// costs and decisions of internal node `node` with children `ch`, the child
+// boxes' half areas al, ar and its own half area a
+__device__ __forceinline__ void sah_node_cost(int2 ch, int cnt, float a, float al, float ar, int64_t n,
+                                              int64_t node, float *cost, uint64_t *dec) {
+    float cl[8], cr[8];
+    sah_child_cost(ch.x, n, al, cost, cl);
+    sah_child_cost(ch.y, n, ar, cost, cr);
     float d[8];
     uint64_t code = 0;
 #pragma unroll
@@ -265,6 +280,7 @@ __device__ __forceinline__ void sah_node_cost(const float (&cl)[8], const float 
         d[j - 1] = best;
         code |= (uint64_t)(kb - 1) << (3 * (j - 2));
     }
+    float c[8];
     c[0] = cnt <= LEAF_MAX ? a * SAH_TRI * (float)cnt : a * SAH_NODE + d[7];
     int f = 1;
 #pragma unroll
@@ -279,26 +295,9 @@ __device__ __forceinline__ void sah_node_cost(const float (&cl)[8], const float 
     __stcg(&dec[node], code);
 }
 
-// arrival count of a binary node: adds 1 and returns the old count. With
-// `rel` the caller's earlier stores are visible to whoever sees the new count;
-// with `acq` the caller sees the stores of the thread that counted before it.
-__device__ __forceinline__ int arrive(int *p, bool rel, bool acq) {
-    int old;
-    if (rel && acq) asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
-    else if (rel) asm volatile("atom.release.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
-    else if (acq) asm volatile("atom.acquire.gpu.global.add.s32 %0, [%1], 1;" : "=r"(old) : "l"(p) : "memory");
-    else old = atomicAdd(p, 1);
-    return old;
-}
-
 // bottom-up boxes: box_lo/hi [2n-1]; flags [n-1] zeroed; with `cost` and
 // `dec`, the SAH collapse costs and decisions of every internal node in the
-// same pass. A thread climbs from its leaf while it is the second child to
-// arrive; it keeps its own node's box and costs in registers and reads only
-// the sibling's. A leaf's box and cost follow from the triangle boxes, which
-// earlier kernels wrote, so only internal nodes publish (release) and only a
-// thread whose sibling is internal needs to see that (acquire). The parent's
-// links and a leaf sibling's box are read before the arrival count comes back.
+// same pass
 __global__ void k_bounds(const unsigned *__restrict__ vals, int64_t n, const float4 *__restrict__ tlo,
                          const float4 *__restrict__ thi, const int2 *__restrict__ child,
                          const int2 *__restrict__ range, const int *__restrict__ parent, float4 *box_lo,
@@ -307,64 +306,28 @@ __global__ void k_bounds(const unsigned *__restrict__ vals, int64_t n, const flo
     if (kk >= n) return;
     int64_t node = n - 1 + kk;
     unsigned t = vals[kk];
-    float4 lo = tlo[t], hi = thi[t];
-    __stcg(&box_lo[node], lo);
-    __stcg(&box_hi[node], hi);
+    const float4 lo0 = tlo[t], hi0 = thi[t];
+    box_lo[node] = lo0;
+    box_hi[node] = hi0;
     if (n == 1) return;
-    float own[8];
-    {
-        const float la = box_half_area(lo, hi) * SAH_TRI;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) own[i] = la;
-    }
-    bool own_leaf = true;
-    int p = parent[node];
     while (true) {
-        const int2 c = child[p];
-        const int2 rg = cost ? range[p] : make_int2(0, 0);
-        const int pp = p ? parent[p] : 0;
-        const bool left = c.x == node;
-        const int sib = left ? c.y : c.x;
-        const bool sib_leaf = sib >= n - 1;
-        float4 s0, s1;
-        if (sib_leaf) {
-            const unsigned st = vals[sib - (n - 1)];
-            s0 = tlo[st];
-            s1 = thi[st];
-        }
-        if (arrive(&flags[p], !own_leaf, !sib_leaf) == 0) return;
-        float sc[8];
-        if (sib_leaf) {
-            const float sa = box_half_area(s0, s1) * SAH_TRI;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) sc[i] = sa;
-        } else {
-            s0 = __ldcg(&box_lo[sib]);
-            s1 = __ldcg(&box_hi[sib]);
-            if (cost) {
-                const float4 *q = reinterpret_cast<const float4 *>(cost + 8 * (int64_t)sib);
-                const float4 u = __ldcg(q), v = __ldcg(q + 1);
-                sc[0] = u.x; sc[1] = u.y; sc[2] = u.z; sc[3] = u.w;
-                sc[4] = v.x; sc[5] = v.y; sc[6] = v.z; sc[7] = v.w;
-            }
-        }
-        lo = make_float4(fminf(lo.x, s0.x), fminf(lo.y, s0.y), fminf(lo.z, s0.z), 0.f);
-        hi = make_float4(fmaxf(hi.x, s1.x), fmaxf(hi.y, s1.y), fmaxf(hi.z, s1.z), 0.f);
+        __threadfence();
+        int p = parent[node];
+        if (atomicAdd(&flags[p], 1) == 0) return;
+        int2 c = child[p];
+        float4 a0 = __ldcg(&box_lo[c.x]), a1 = __ldcg(&box_hi[c.x]);
+        float4 b0 = __ldcg(&box_lo[c.y]), b1 = __ldcg(&box_hi[c.y]);
+        const float4 lo = make_float4(fminf(a0.x, b0.x), fminf(a0.y, b0.y), fminf(a0.z, b0.z), 0.f);
+        const float4 hi = make_float4(fmaxf(a1.x, b1.x), fmaxf(a1.y, b1.y), fmaxf(a1.z, b1.z), 0.f);
         __stcg(&box_lo[p], lo);
         __stcg(&box_hi[p], hi);
         if (cost) {
-            float cl[8], cr[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                cl[i] = left ? own[i] : sc[i];
-                cr[i] = left ? sc[i] : own[i];
-            }
-            sah_node_cost(cl, cr, rg.y - rg.x + 1, box_half_area(lo, hi), p, own, cost, dec);
+            const int2 rg = range[p];
+            sah_node_cost(c, rg.y - rg.x + 1, box_half_area(lo, hi), box_half_area(a0, a1),
+                          box_half_area(b0, b1), n, p, cost, dec);
         }
         node = p;
-        own_leaf = false;
         if (p == 0) return;
-        p = pp;
     }
 }
 
