@@ -282,6 +282,24 @@ def test_full_size_asset_sampled_parity():
     bvh.free()
 
 
+def test_large_asset_sampled_parity_both_layouts():
+    """The 8M-triangle, 4096^2 precision-study workload: the whole raster map
+    bit-exact, and a seeded sample of ray texels against the oracle for the
+    8-bit and the FP32 node layouts."""
+    a = synth.sdf_asset(1, 8_000_000, 30_000, 4096, 4096, n_prims=32)
+    face, _, _ = oracle.raster(a.low_uv, a.W, a.H)
+    rays = np.flatnonzero(face.reshape(-1) >= 0)
+    sample = np.sort(np.random.default_rng(2).choice(rays, size=1500, replace=False))
+    o = oracle.bake_asset(a, sample=sample)
+    for layout in ("q8", "f32"):
+        bvh, g, _ = gpu_bake(a, layout=layout)
+        assert np.array_equal(g["face"], face)
+        st = parity.compare(g, o, a.diam, a.gutter, sample=sample)
+        print(layout, len(a.high_f), st)
+        parity.check(st, small=0)
+        bvh.free()
+
+
 def test_launch_configurations_give_identical_bakes_and_autotune(tmp_path, monkeypatch):
     """Schedules, block sizes and ray tiles change only the speed: every
     configuration produces the same bytes; the autotuner picks one of them
