@@ -204,6 +204,9 @@ AG_API void ag_opts_default(ag_opts *o);
  * calls on an AG_BVH_F32 tree wait for the build the first time they need
  * its summary (node count, depth, scene box); ag_bake, ag_bake_backward and
  * ag_bake_batch on an AG_BVH_Q8 tree do not wait.
+ * Test hook: the environment variable AG_TEST_GRID_LEVELS=k (0..16) runs the
+ * collapse levels from k on in the single-CTA kernel that otherwise serves
+ * only trees deeper than 16 levels; the tree is the same.
  */
 AG_API ag_status ag_bvh_build(const float *d_verts, int64_t n_verts, const int32_t *d_faces,
                               int64_t n_faces, const ag_opts *opts, ag_stream_t stream,
