@@ -146,10 +146,11 @@ __global__ void k_init_faces(const int32_t *__restrict__ Fin, int64_t nf, int64_
 }
 
 __global__ void k_init_verts(const float *__restrict__ Vin, int64_t nv, double *__restrict__ V,
-                             int32_t *__restrict__ remap) {
+                             float *__restrict__ V32, int32_t *__restrict__ remap) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     V[3 * v] = Vin[3 * v]; V[3 * v + 1] = Vin[3 * v + 1]; V[3 * v + 2] = Vin[3 * v + 2];
+    V32[3 * v] = Vin[3 * v]; V32[3 * v + 1] = Vin[3 * v + 1]; V32[3 * v + 2] = Vin[3 * v + 2];
     remap[v] = (int32_t)v;
 }
 
@@ -279,7 +280,47 @@ __device__ __forceinline__ int neighbours(const int32_t *F, const unsigned *off,
     return n;
 }
 
-__global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V, const int32_t *__restrict__ F,
+// Sign of the turn-over product n_old . n_new of one face, decided in FP32
+// when that is certain: +1 (> 0), -1 (< 0), 0 (undecided: the caller takes the
+// FP64 test). The FP32 inputs are the FP64 positions rounded to FP32 (V32);
+// the bound B covers, with a factor of two to spare, the rounding of the
+// inputs (u |coordinate|), of the edge differences, the cross products and the
+// dot product against exact arithmetic on the FP64 positions, which is also
+// where the FP64 test lands to within far less than B/2. So whenever
+// |s| > B the FP64 test takes the same decision, and the collapses stay
+// identical. Near the bottom of the FP32 range the FP64 test decides.
+__device__ __forceinline__ int turn_sign32(const float *__restrict__ V32, const int32_t *id, int32_t w, float3 v) {
+    float3 P[3], R[3];
+    float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fabsf(v.z));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int64_t i = id[k];
+        P[k] = make_float3(V32[3 * i], V32[3 * i + 1], V32[3 * i + 2]);
+        R[k] = id[k] == w ? v : P[k];
+        m = fmaxf(m, fmaxf(fmaxf(fabsf(P[k].x), fabsf(P[k].y)), fabsf(P[k].z)));
+    }
+    const float3 e1 = P[1] - P[0], e2 = P[2] - P[0], f1 = R[1] - R[0], f2 = R[2] - R[0];
+    const float3 c0 = cross3(e1, e2), c1 = cross3(f1, f2);
+    const float sgn = dot3(c0, c1);
+    auto amax = [](float3 a, float3 b) {
+        return fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(b.x))),
+                     fmaxf(fabsf(b.y), fabsf(b.z)));
+    };
+    const float E0 = amax(e1, e2), E1 = amax(f1, f2);
+    const float u = 5.9604645e-8f;   // 2^-24
+    const float d = 4.f * u * (m + fmaxf(E0, E1));
+    const float dc0 = 4.f * E0 * d + 2.f * d * d + 6.f * u * E0 * E0;
+    const float dc1 = 4.f * E1 * d + 2.f * d * d + 6.f * u * E1 * E1;
+    const float C0 = 2.f * E0 * E0 + dc0, C1 = 2.f * E1 * E1 + dc1;
+    const float B = 2.f * (3.f * (C0 * dc1 + C1 * dc0 + dc0 * dc1) + 15.f * u * C0 * C1);
+    if (!(B >= 1e-30f) || !(B < 1e30f)) return 0;
+    if (sgn > B) return 1;
+    if (sgn < -B) return -1;
+    return 0;
+}
+
+__global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V, const float *__restrict__ V32,
+                                                    const int32_t *__restrict__ F,
                                                     const double *__restrict__ Q, const unsigned *__restrict__ off,
                                                     const int32_t *__restrict__ list, const int32_t *__restrict__ ea,
                                                     const int32_t *__restrict__ eb, const uint8_t *__restrict__ nfaces,
@@ -317,11 +358,16 @@ __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V,
         for (int n = 0; n < nb; ++n) common += na_[m] == nb_[n];
     if (common != nfc) return;
     if (na + nb - common <= 4) return;
+    const float3 v32 = make_float3(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z));
     for (int side = 0; side < 2; ++side) {
         const int32_t w = side ? b : a, o = side ? a : b;
         for (unsigned j = off[w]; j < off[w + 1]; ++j) {
             const int64_t g = list[j];
             if (has(F, g, o)) continue;
+            const int32_t id[3] = {F[3 * g], F[3 * g + 1], F[3 * g + 2]};
+            const int sg = turn_sign32(V32, id, w, v32);
+            if (sg > 0) continue;
+            if (sg < 0) return;
             D3 P[3], R[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -403,12 +449,14 @@ __global__ void __launch_bounds__(1024) k_limit(const unsigned long long *__rest
 __global__ void k_apply(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
                         const unsigned long long *__restrict__ key, const uint8_t *__restrict__ sel,
                         const double *__restrict__ tpos, const unsigned long long *__restrict__ limit, int64_t ne,
-                        double *__restrict__ V, double *__restrict__ Q, uint8_t *__restrict__ valive,
-                        int32_t *__restrict__ remap) {
+                        double *__restrict__ V, float *__restrict__ V32, double *__restrict__ Q,
+                        uint8_t *__restrict__ valive, int32_t *__restrict__ remap) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne || !sel[i] || key[i] > *limit) return;
     const int64_t a = ea[i], b = eb[i];
     V[3 * a] = tpos[3 * i]; V[3 * a + 1] = tpos[3 * i + 1]; V[3 * a + 2] = tpos[3 * i + 2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) V32[3 * a + k] = __double2float_rn(tpos[3 * i + k]);
 #pragma unroll
     for (int k = 0; k < 10; ++k) Q[10 * a + k] = __dadd_rn(Q[10 * a + k], Q[10 * b + k]);
     valive[b] = 0;
@@ -486,6 +534,8 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     unsigned long long *key, *m1, *m2, *selk, *limit;
     Counters *cnt;
     AG_CUDA(sc.alloc((void **)&V, sizeof(double) * 3 * nv));
+    float *V32;   // V rounded to FP32 (the turn-over filter's input)
+    AG_CUDA(sc.alloc((void **)&V32, sizeof(float) * 3 * nv));
     AG_CUDA(sc.alloc((void **)&Q, sizeof(double) * 10 * nv));
     AG_CUDA(sc.alloc((void **)&tpos, sizeof(double) * 3 * emax));
     AG_CUDA(sc.alloc((void **)&F, sizeof(int32_t) * 3 * nf));
@@ -522,7 +572,7 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     AG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), s));
     AG_CUDA(cudaMemsetAsync(valive, 0, nv, s));
     k_init_faces<<<blocks(nf, B), B, 0, s>>>(d_faces, nf, nv, F, falive, valive, cnt, status);
-    k_init_verts<<<blocks(nv, B), B, 0, s>>>(d_verts, nv, V, remap);
+    k_init_verts<<<blocks(nv, B), B, 0, s>>>(d_verts, nv, V, V32, remap);
     AG_CUDA_LAUNCH("qem init");
 
     auto build_csr = [&]() -> cudaError_t {
@@ -554,7 +604,8 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
         k_edges<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff, ea, eb);
         AG_CUDA(cudaMemsetAsync(bnd, 0, nv, s));
         k_edge_faces<<<blocks(ne, B), B, 0, s>>>(F, off, list, ea, eb, ne, nfaces, bnd);
-        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, F, Q, off, list, ea, eb, nfaces, bnd, ne, placement, key, tpos);
+        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, V32, F, Q, off, list, ea, eb, nfaces, bnd, ne, placement, key,
+                                                    tpos);
         AG_CUDA(cudaMemsetAsync(m1, 0xff, sizeof(unsigned long long) * nv, s));
         k_m1<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, ne, m1);
         AG_CUDA(cudaMemcpyAsync(m2, m1, sizeof(unsigned long long) * nv, cudaMemcpyDeviceToDevice, s));
@@ -570,7 +621,7 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
         } else {
             AG_CUDA(cudaMemsetAsync(limit, 0xff, sizeof(unsigned long long), s));
         }
-        k_apply<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, tpos, limit, ne, V, Q, valive, remap);
+        k_apply<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, tpos, limit, ne, V, V32, Q, valive, remap);
         k_faces<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, remap, cnt);
         AG_CUDA_LAUNCH("qem collapse");
         ++rounds;

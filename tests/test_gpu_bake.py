@@ -182,6 +182,16 @@ def test_device_argument_errors():
     with pytest.raises(pb.AgError) as ei:
         pb.Bvh(hv, bad)
     assert ei.value.status == 1
+    # an asynchronous build returns before the check: the bad index reaches
+    # the status word, and the handle stays safe to use and free
+    pb.sync_status()
+    abvh = pb.Bvh(hv, bad, async_build=True)
+    with pytest.raises(pb.AgError) as ei:
+        pb.sync_status()
+    assert ei.value.status == 1
+    assert abvh.info()["n_tris"] == len(a.high_f)
+    abvh.free()
+    pb.sync_status()
     bvh = pb.Bvh(hv, hf)
     lv, lf, uv = _t(a.low_v), _t(a.low_f), _t(a.low_uv)
     with pytest.raises(pb.AgError):
