@@ -205,11 +205,42 @@ __device__ __forceinline__ bool seen_before(const int32_t *F, const int32_t *lis
     return false;
 }
 
+// the distinct higher neighbours (u > a) of vertex a in ascending order, into
+// nb; -1 when there are more than UP_CAP (the callers then take the general
+// scan below)
+constexpr int UP_CAP = 48;
+__device__ __forceinline__ int higher_neighbours(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
+                                                 const int32_t *__restrict__ list, int64_t a, int32_t *nb) {
+    int n = 0;
+    for (unsigned i = off[a]; i < off[a + 1]; ++i) {
+        const int64_t f = list[i];
+        const int32_t tri[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+        for (int k = 0; k < 3; ++k) {
+            const int32_t u = tri[k];
+            if (u <= a) continue;
+            int j = n;
+            while (j > 0 && nb[j - 1] > u) --j;
+            if (j > 0 && nb[j - 1] == u) continue;
+            if (n == UP_CAP) return -1;
+            for (int m = n; m > j; --m) nb[m] = nb[m - 1];
+            nb[j] = u;
+            ++n;
+        }
+    }
+    return n;
+}
+
 // number of distinct higher neighbours of every vertex
 __global__ void k_upcount(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
                           const int32_t *__restrict__ list, unsigned *__restrict__ up) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nv) return;
+    int32_t nb[UP_CAP];
+    const int c = higher_neighbours(F, off, list, a, nb);
+    if (c >= 0) {
+        up[a] = (unsigned)c;
+        return;
+    }
     const unsigned b = off[a], e = off[a + 1];
     unsigned n = 0;
     for (unsigned i = b; i < e; ++i) {
@@ -225,12 +256,19 @@ __global__ void k_upcount(const int32_t *__restrict__ F, int64_t nv, const unsig
     up[a] = n;
 }
 
+// the ranked edge list: the edges (a, u > a) of vertex a at eoff[a], u ascending
 __global__ void k_edges(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
                         const int32_t *__restrict__ list, const unsigned *__restrict__ eoff,
                         int32_t *__restrict__ ea, int32_t *__restrict__ eb) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nv) return;
     const unsigned b = off[a], e = off[a + 1], o = eoff[a], n_up = eoff[a + 1] - o;
+    int32_t nb[UP_CAP];
+    const int c = higher_neighbours(F, off, list, a, nb);
+    if (c >= 0) {
+        for (int m = 0; m < c; ++m) { ea[o + m] = (int32_t)a; eb[o + m] = nb[m]; }
+        return;
+    }
     unsigned n = 0;
     for (unsigned i = b; i < e; ++i) {
         const int64_t f = list[i];
