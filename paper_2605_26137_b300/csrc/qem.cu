@@ -363,11 +363,33 @@ __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V,
                                                     const int32_t *__restrict__ list, const int32_t *__restrict__ ea,
                                                     const int32_t *__restrict__ eb, const uint8_t *__restrict__ nfaces,
                                                     const uint8_t *__restrict__ bnd, int64_t ne, int placement,
-                                                    unsigned long long *__restrict__ key, double *__restrict__ tpos) {
+                                                    unsigned long long *__restrict__ key, double *__restrict__ tpos,
+                                                    const uint8_t *__restrict__ dirty, const unsigned *__restrict__ eoff_prev,
+                                                    const int32_t *__restrict__ eb_prev,
+                                                    const unsigned long long *__restrict__ key_prev,
+                                                    const double *__restrict__ tpos_prev) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ne) return;
     key[i] = KEY_NONE;
     const int32_t a = ea[i], b = eb[i];
+    if (key_prev && !dirty[a] && !dirty[b]) {
+        // neither end nor any vertex of their faces changed in the last
+        // round: the edge's cost, validity and placement are as they were
+        unsigned lo = eoff_prev[a], hi = eoff_prev[a + 1];
+        while (lo < hi) {
+            const unsigned mid = (lo + hi) >> 1;
+            if (eb_prev[mid] < b) lo = mid + 1; else hi = mid;
+        }
+        if (lo < eoff_prev[a + 1] && eb_prev[lo] == b) {
+            const unsigned long long k = key_prev[lo];
+            if (k != KEY_NONE) {
+                key[i] = (k & 0xffffffff00000000ull) | (uint32_t)i;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) tpos[3 * i + c] = tpos_prev[3 * (int64_t)lo + c];
+            }
+            return;
+        }
+    }
     const int nfc = nfaces[i];
     if (nfc > 2) return;
     double q[10];
@@ -501,6 +523,27 @@ __global__ void k_apply(const int32_t *__restrict__ ea, const int32_t *__restric
     remap[b] = (int32_t)a;
 }
 
+// the vertices whose edges must be re-evaluated next round: both ends of
+// every collapse and every vertex of their faces (read before k_faces
+// rewrites the faces)
+__global__ void k_mark(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
+                       const unsigned long long *__restrict__ key, const uint8_t *__restrict__ sel,
+                       const unsigned long long *__restrict__ limit, int64_t ne, const int32_t *__restrict__ F,
+                       const unsigned *__restrict__ off, const int32_t *__restrict__ list, uint8_t *__restrict__ dirty) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne || !sel[i] || key[i] > *limit) return;
+    for (int side = 0; side < 2; ++side) {
+        const int32_t w = side ? eb[i] : ea[i];
+        dirty[w] = 1;
+        for (unsigned j = off[w]; j < off[w + 1]; ++j) {
+            const int64_t f = list[j];
+            dirty[F[3 * f]] = 1;
+            dirty[F[3 * f + 1]] = 1;
+            dirty[F[3 * f + 2]] = 1;
+        }
+    }
+}
+
 __global__ void k_faces(int32_t *__restrict__ F, uint8_t *__restrict__ falive, int64_t nf,
                         const int32_t *__restrict__ remap, Counters *cnt) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -599,6 +642,19 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     AG_CUDA(sc.alloc((void **)&selk, sizeof(unsigned long long) * emax));
     AG_CUDA(sc.alloc((void **)&limit, sizeof(unsigned long long)));
     AG_CUDA(sc.alloc((void **)&cnt, sizeof(Counters)));
+    // the previous round's edge list (ends b by segment of a), keys and
+    // placements, reused for edges whose neighbourhood did not change
+    int32_t *eb_prev;
+    unsigned *eoff_prev;
+    unsigned long long *key_prev;
+    double *tpos_prev;
+    uint8_t *dirty;
+    AG_CUDA(sc.alloc((void **)&eb_prev, sizeof(int32_t) * emax));
+    AG_CUDA(sc.alloc((void **)&eoff_prev, sizeof(unsigned) * (nv + 1)));
+    AG_CUDA(sc.alloc((void **)&key_prev, sizeof(unsigned long long) * emax));
+    AG_CUDA(sc.alloc((void **)&tpos_prev, sizeof(double) * 3 * emax));
+    AG_CUDA(sc.alloc((void **)&dirty, nv));
+    bool have_prev = false;
     Counters *h_cnt = nullptr;
     AG_CUDA(cudaMallocHost((void **)&h_cnt, sizeof(Counters)));
     struct HostFree {
@@ -643,7 +699,9 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
         AG_CUDA(cudaMemsetAsync(bnd, 0, nv, s));
         k_edge_faces<<<blocks(ne, B), B, 0, s>>>(F, off, list, ea, eb, ne, nfaces, bnd);
         k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, V32, F, Q, off, list, ea, eb, nfaces, bnd, ne, placement, key,
-                                                    tpos);
+                                                    tpos, dirty, eoff_prev, eb_prev, have_prev ? key_prev : nullptr,
+                                                    tpos_prev);
+        AG_CUDA(cudaMemsetAsync(dirty, 0, nv, s));
         AG_CUDA(cudaMemsetAsync(m1, 0xff, sizeof(unsigned long long) * nv, s));
         k_m1<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, ne, m1);
         AG_CUDA(cudaMemcpyAsync(m2, m1, sizeof(unsigned long long) * nv, cudaMemcpyDeviceToDevice, s));
@@ -660,8 +718,14 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
             AG_CUDA(cudaMemsetAsync(limit, 0xff, sizeof(unsigned long long), s));
         }
         k_apply<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, tpos, limit, ne, V, V32, Q, valive, remap);
+        k_mark<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, limit, ne, F, off, list, dirty);
         k_faces<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, remap, cnt);
         AG_CUDA_LAUNCH("qem collapse");
+        std::swap(eb, eb_prev);
+        std::swap(eoff, eoff_prev);
+        std::swap(key, key_prev);
+        std::swap(tpos, tpos_prev);
+        have_prev = true;
         ++rounds;
     }
     // compaction: surviving vertices and faces in increasing original id
