@@ -52,18 +52,38 @@ __global__ void k_gather(const float *__restrict__ V, const int32_t *__restrict_
     if (v >= nv) return;
     float3 s = make_float3(0.f, 0.f, 0.f);
     if (!given) {
-        unsigned b = off[v], e = off[v + 1];
-        // insertion sort of this vertex's faces by id (degrees are small)
-        for (unsigned i = b + 1; i < e; ++i) {
-            int32_t x = list[i];
-            unsigned j = i;
-            while (j > b && list[j - 1] > x) { list[j] = list[j - 1]; --j; }
-            list[j] = x;
-        }
-        for (unsigned i = b; i < e; ++i) {
-            int64_t f = list[i];
-            float3 c = face_cross(ldv(V, F[3 * f]), ldv(V, F[3 * f + 1]), ldv(V, F[3 * f + 2]));
-            s = make_float3(__fadd_rn(s.x, c.x), __fadd_rn(s.y, c.y), __fadd_rn(s.z, c.z));
+        const unsigned b = off[v], e = off[v + 1];
+        constexpr unsigned CAP = 32;
+        if (e - b <= CAP) {
+            // this vertex's faces sorted by id in a local list (written back:
+            // the list leaves this kernel sorted either way)
+            int32_t fl[CAP];
+            unsigned n = 0;
+            for (unsigned i = b; i < e; ++i) {
+                const int32_t x = list[i];
+                unsigned j = n++;
+                while (j > 0 && fl[j - 1] > x) { fl[j] = fl[j - 1]; --j; }
+                fl[j] = x;
+            }
+            for (unsigned i = 0; i < n; ++i) {
+                list[b + i] = fl[i];
+                const int64_t f = fl[i];
+                const float3 c = face_cross(ldv(V, F[3 * f]), ldv(V, F[3 * f + 1]), ldv(V, F[3 * f + 2]));
+                s = make_float3(__fadd_rn(s.x, c.x), __fadd_rn(s.y, c.y), __fadd_rn(s.z, c.z));
+            }
+        } else {
+            // insertion sort of the faces by id in place
+            for (unsigned i = b + 1; i < e; ++i) {
+                int32_t x = list[i];
+                unsigned j = i;
+                while (j > b && list[j - 1] > x) { list[j] = list[j - 1]; --j; }
+                list[j] = x;
+            }
+            for (unsigned i = b; i < e; ++i) {
+                int64_t f = list[i];
+                float3 c = face_cross(ldv(V, F[3 * f]), ldv(V, F[3 * f + 1]), ldv(V, F[3 * f + 2]));
+                s = make_float3(__fadd_rn(s.x, c.x), __fadd_rn(s.y, c.y), __fadd_rn(s.z, c.z));
+            }
         }
     } else {
         s = ldv(given, v);
