@@ -482,6 +482,10 @@ __global__ void __launch_bounds__(1024) k_limit(const unsigned long long *__rest
                                                  long long target, unsigned long long *limit) {
     __shared__ long long part[32];
     __shared__ unsigned long long s_lo, s_hi;
+    if ((long long)cnt->alive - (long long)cnt->removable >= target) {   // no cut needed this round
+        if (threadIdx.x == 0) *limit = ~0ull;
+        return;
+    }
     const int n = cnt->nsel;
     const long long need = (long long)cnt->alive - target;
     if (threadIdx.x == 0) { s_lo = 0ull; s_hi = KEY_NONE; }
@@ -682,17 +686,27 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     k_quadric_init<<<blocks(nv, 128), 128, 0, s>>>(V, F, nv, off, list, Q);
     AG_CUDA_LAUNCH("k_quadric_init");
 
-    int64_t rounds = 0;
-    for (;;) {
-        AG_CUDA(cudaMemcpyAsync(h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-        AG_CUDA(cudaStreamSynchronize(s));
-        if ((long long)h_cnt->alive <= target || rounds >= rounds_cap) break;
-        AG_CUDA(build_csr());
+    // One host read per round: the counters (alive faces, last round's
+    // selections) and the next edge count come back together; the cut to the
+    // target is decided on the device (k_limit).
+    auto edge_offsets = [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = build_csr()) != cudaSuccess) return e;
         k_upcount<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff);
-        AG_CUDA(launch_scan_exclusive(eoff, nv, eoff + nv, scan_tmp, s));
+        return launch_scan_exclusive(eoff, nv, eoff + nv, scan_tmp, s);
+    };
+    int64_t rounds = 0;
+    AG_CUDA(edge_offsets());
+    for (;;) {
         unsigned ne32 = 0;
+        AG_CUDA(cudaMemcpyAsync(h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
         AG_CUDA(cudaMemcpyAsync(&ne32, eoff + nv, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         AG_CUDA(cudaStreamSynchronize(s));
+        if (rounds > 0 && h_cnt->nsel == 0) {   // the last round selected nothing: it changed nothing
+            --rounds;
+            break;
+        }
+        if ((long long)h_cnt->alive <= target || rounds >= rounds_cap) break;
         const int64_t ne = ne32;
         if (ne == 0) break;
         k_edges<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff, ea, eb);
@@ -708,15 +722,8 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
         k_m2<<<blocks(ne, B), B, 0, s>>>(ea, eb, m1, ne, m2);
         AG_CUDA(cudaMemsetAsync(&cnt->removable, 0, sizeof(unsigned long long) + 2 * sizeof(int), s));
         k_select<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, nfaces, m2, ne, sel, selk, selnf, cnt);
+        k_limit<<<1, 1024, 0, s>>>(selk, selnf, cnt, (long long)target, limit);
         AG_CUDA_LAUNCH("qem round");
-        AG_CUDA(cudaMemcpyAsync(h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-        AG_CUDA(cudaStreamSynchronize(s));
-        if (h_cnt->nsel == 0) break;
-        if ((long long)h_cnt->alive - (long long)h_cnt->removable < target) {
-            k_limit<<<1, 1024, 0, s>>>(selk, selnf, cnt, (long long)target, limit);
-        } else {
-            AG_CUDA(cudaMemsetAsync(limit, 0xff, sizeof(unsigned long long), s));
-        }
         k_apply<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, tpos, limit, ne, V, V32, Q, valive, remap);
         k_mark<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, limit, ne, F, off, list, dirty);
         k_faces<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, remap, cnt);
@@ -727,6 +734,7 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
         std::swap(tpos, tpos_prev);
         have_prev = true;
         ++rounds;
+        AG_CUDA(edge_offsets());
     }
     // compaction: surviving vertices and faces in increasing original id
     k_flag_u32<<<blocks(nv, B), B, 0, s>>>(valive, nv, vid);
