@@ -49,8 +49,10 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        build()
-        lib = ctypes.CDLL(_LIB)
+        # AG_ORACLE_LIB (tests only): load another build of oracle.c, e.g. one
+        # with a planted mistake, to show that the pins catch it
+        path = os.environ.get("AG_ORACLE_LIB") or build()
+        lib = ctypes.CDLL(path)
         lib.or_vertex_normals.argtypes = [_P, _I64, _P, _I64, _P]
         lib.or_vertex_normals.restype = None
         lib.or_snap.argtypes = [ctypes.c_float, _I]

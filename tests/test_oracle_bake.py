@@ -199,3 +199,28 @@ def test_dilation_hand_checked():
     assert np.allclose(n2[3, 1], exp / np.linalg.norm(exp))
     assert np.isclose(d2[3, 1], (d1[2, 0] + d1[2, 1] + d1[2, 2]) / 3)
     assert f2[3, 4] == 0 or f2[3, 4] == 2
+
+
+@pytest.mark.parametrize("mirror", [False, True])
+def test_bitangent_follows_dp_dv(mirror):
+    """A tilted high plane z = h - s y over the flat low quad, with UVs an
+    affine function of position (v increasing or, mirrored, decreasing with
+    y): the texel frame is T = dp/du = +x, B along +dp/dv (so -y when
+    mirrored), N = +z, and the hit normal (0, s, 1) / sqrt(1 + s^2) has
+    tangent-space components (0, +-s, 1) / sqrt(1 + s^2)."""
+    h, s = 0.05, 0.02
+    lv = np.array([[-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0]], np.float32)
+    lf = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    sgn = -1.0 if mirror else 1.0
+
+    def uvmap(p):
+        return (0.1 + 0.4 * (p[0] + 1), 0.5 + sgn * 0.4 * p[1])
+    uv = np.array([[uvmap(lv[i]) for i in f] for f in lf], np.float32)
+    hv, hf = _grid_plane(24, 0.0, 1.5)
+    hv[:, 2] = (h - s * hv[:, 1].astype(np.float64)).astype(np.float32)
+    r = oracle.bake(hv, hf, lv, lf, uv, 64, 64, 0.1)
+    m = r["face"] >= 0
+    assert m.sum() > 1000 and r["mask"][m].all()
+    k = 1.0 / np.sqrt(1 + s * s)
+    exp = np.array([0.0, sgn * s * k, k])
+    assert np.abs(r["nts"][m] - exp).max() < 2e-4

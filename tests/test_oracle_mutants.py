@@ -1,0 +1,56 @@
+"""The pins catch plausible mistakes in the oracle. Each case plants one
+mistake in a copy of oracle.c (a flipped operand order, a dropped factor, a
+transposed index, a wrong constant), builds it, and runs the closed-form,
+invariant and brute-force pins against it in a child process: at least one
+must fail. The stored regression fixture of the oracle's own output is left
+out, so that only pins fixed by the paper and the mathematics count."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = {
+    "vertex normal operands swapped":
+        ("d3 n = cross(sub(vb, va), sub(vc, va));", "d3 n = cross(sub(vc, va), sub(vb, va));"),
+    "tie prefers the negative side":
+        ("if ((t >= 0.0) != (best->t >= 0.0)) return t >= 0.0;", "if ((t >= 0.0) != (best->t >= 0.0)) return t < 0.0;"),
+    "hit normal weights transposed":
+        ("m = add(m, scl(ldd(j->hn, j->hf[3 * tri + k]), b[k]));",
+         "m = add(m, scl(ldd(j->hn, j->hf[3 * tri + k]), b[(k + 1) % 3]));"),
+    "bitangent handedness dropped":
+        ("d3 B = scl(cross(N, Tt), j->wsign[f]);", "d3 B = cross(N, Tt);"),
+    "ray direction not normalised":
+        ("    d3 d = normalize(s);\n    double tol = 1e-5 * j->diam;", "    d3 d = s;\n    double tol = 1e-5 * j->diam;"),
+    "displacement sign flipped":
+        ("disp = h.tri >= 0 ? h.t : 0.0;", "disp = h.tri >= 0 ? -h.t : 0.0;"),
+    "RGB8 scale 128":
+        ("float r = v * 127.0f;", "float r = v * 128.0f;"),
+    "dilated normal not renormalised":
+        ("std3(nts, i, norm(mm) > 0 ? normalize(mm) : mk(0, 0, 1));", "std3(nts, i, mm);"),
+    "tangent not made orthogonal to the normal":
+        ("d3 Tt = normalize(sub(ts, scl(N, dot(ts, N))));", "d3 Tt = normalize(ts);"),
+}
+
+PINS = ["tests/test_oracle_bake.py", "tests/test_oracle_hit.py", "tests/test_oracle_raster.py",
+        "tests/test_golden.py::test_encode_fixture", "tests/test_golden.py::test_dilation_fixture",
+        "tests/test_golden.py::test_flat_plane_fixture"]
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "the mutation site moved"
+    mutant = tmp_path / "oracle_mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-o", str(lib), str(mutant), "-lm", "-lpthread"])
+    env = dict(os.environ, AG_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider",
+                        *PINS], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"no pin caught '{name}':\n{r.stdout[-2000:]}"
