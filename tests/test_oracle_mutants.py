@@ -35,9 +35,52 @@ MUTANTS = {
         ("d3 Tt = normalize(sub(ts, scl(N, dot(ts, N))));", "d3 Tt = normalize(ts);"),
 }
 
+# the next rows' functions, each with the pins of its own row
+ROW_MUTANTS = {
+    "closest point: edge parameter not clamped above":
+        ("        if (s > 1.0) s = 1.0;\n        d3 y = add(a, scl(e, s));", "        d3 y = add(a, scl(e, s));",
+         ["tests/test_oracle_closest.py"]),
+    "closest point: edge barycentrics swapped":
+        ("b[k] = 1.0 - s; b[(k + 1) % 3] = s; b[(k + 2) % 3] = 0.0;",
+         "b[k] = s; b[(k + 1) % 3] = 1.0 - s; b[(k + 2) % 3] = 0.0;", ["tests/test_oracle_closest.py"]),
+    "QEM placement parameter measured from the far end":
+        ("double t = dot(sub(x, v0), e) / ee;", "double t = dot(sub(x, v1), e) / ee;", ["tests/test_oracle_qem.py"]),
+    "exterior fill gate dropped":
+        ("if (dot(nf_, ldd(nrm, g)) > 0.0) { exterior[g] = 1; queue[qt++] = g; }",
+         "{ exterior[g] = 1; queue[qt++] = g; }", ["tests/test_oracle_hidden.py"]),
+    "backprojection incidence exponent dropped":
+        ("L[nk] = log((double)weights[k]) + alpha * log(I);", "L[nk] = log((double)weights[k]) + log(I);",
+         ["tests/test_oracle_backproject.py"]),
+}
+
 PINS = ["tests/test_oracle_bake.py", "tests/test_oracle_hit.py", "tests/test_oracle_raster.py",
         "tests/test_golden.py::test_encode_fixture", "tests/test_golden.py::test_dilation_fixture",
         "tests/test_golden.py::test_flat_plane_fixture"]
+
+
+def _build_mutant(old, new, tmp_path):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "the mutation site moved"
+    mutant = tmp_path / "oracle_mutant.c"
+    mutant.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-o", str(lib), str(mutant), "-lm", "-lpthread"])
+    return lib
+
+
+def _pins_fail(lib, pins):
+    env = dict(os.environ, AG_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider",
+                        *pins], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode == 1, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(ROW_MUTANTS))
+def test_row_pins_catch_planted_mistake(name, tmp_path):
+    old, new, pins = ROW_MUTANTS[name]
+    failed, out = _pins_fail(_build_mutant(old, new, tmp_path), pins)
+    assert failed, f"no pin caught '{name}':\n{out}"
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
