@@ -208,7 +208,7 @@ __device__ __forceinline__ bool seen_before(const int32_t *F, const int32_t *lis
 // the distinct higher neighbours (u > a) of vertex a in ascending order, into
 // nb; -1 when there are more than UP_CAP (the callers then take the general
 // scan below)
-constexpr int UP_CAP = 48;
+constexpr int UP_CAP = 160;
 __device__ __forceinline__ int higher_neighbours(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
                                                  const int32_t *__restrict__ list, int64_t a, int32_t *nb) {
     int n = 0;
