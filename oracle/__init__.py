@@ -70,8 +70,11 @@ def _load():
         lib.or_closest_point.argtypes = [_P, _P, _I64, _P, _P, _D, _P]
         lib.or_closest_point.restype = _I
         lib.or_trace.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
-                                 _I, _I, _D, _D, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _I]
+                                 _I, _I, _D, _D, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _I, _P]
         lib.or_trace.restype = _I
+        lib.or_normal_map_error.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P,
+                                            _P, _P, _I64, _D, _D, _I, _P, _P]
+        lib.or_normal_map_error.restype = _I
         lib.or_encode.argtypes = [_P, _P, _I64, _P]
         lib.or_encode.restype = None
         lib.or_dilate.argtypes = [_I, _I, _I, _P, _P, _P]
@@ -235,11 +238,14 @@ def default_threads() -> int:
 
 
 def bake(high_v, high_f, low_v, low_f, low_uv, W, H, max_dist, gutter=2, *,
-         diam=None, use_bvh=True, sample=None, nthreads=None, bvh: Bvh | None = None, query="ray"):
+         diam=None, use_bvh=True, sample=None, nthreads=None, bvh: Bvh | None = None, query="ray",
+         force=None):
     """The whole bake in FP64.  With ``sample`` (texel ids), only those texels
     are traced and dilation is skipped.  ``query`` is "ray" (the line along
     the texel normal) or "closest" (the nearest point of the high surface);
     ``hit_t`` is then the signed ray parameter or the signed distance.
+    ``force`` ([H*W] int32, with ``sample``) evaluates the given triangle at
+    each sampled texel instead of searching (see ``shade_given``).
     Returns a dict of numpy arrays."""
     lib = _load()
     hv = _c(high_v, np.float32)
@@ -274,7 +280,7 @@ def bake(high_v, high_f, low_v, low_f, low_uv, W, H, max_dist, gutter=2, *,
                       _p(face), _p(bary), W, H, float(max_dist), float(diam),
                       _p(texels), len(texels), nth,
                       _p(mask), _p(nts), _p(disp), _p(hit_tri), _p(hit_t), _p(hit_b), _p(flags),
-                      QUERIES[query])
+                      QUERIES[query], _p(force) if force is not None else None)
     if rc != 0:
         raise RuntimeError("oracle trace: thread start failed")
     filled = (face.reshape(-1) >= 0).astype(np.uint8)
@@ -287,9 +293,66 @@ def bake(high_v, high_f, low_v, low_f, low_uv, W, H, max_dist, gutter=2, *,
     out["nts"] = nts.reshape(H, W, 3)
     out["disp"] = disp.reshape(H, W)
     out["rgba8"] = encode(nts, filled).reshape(H, W, 4)
-    # binary16 is decided in the kernel's precision: FP64 -> FP32 -> FP16 (RNE)
-    out["disp16"] = disp.astype(np.float32).astype(np.float16).reshape(H, W)
+    # binary16 straight from the FP64 value (IEEE round to nearest even)
+    out["disp16"] = disp.astype(np.float16).reshape(H, W)
     return out
+
+
+def shade_given(asset, texels, tris, query="ray"):
+    """FP64 evaluation of one given high triangle per texel, for checking an
+    answer where several are equally correct (two triangles within rounding
+    of the closest hit).  Ray query: the line's crossing of the triangle's
+    plane, with signed barycentrics (a triangle missed by a hair shows a
+    slightly negative one); closest-point query: the triangle's nearest point.
+    Returns (n_ts [n,3], t [n], barycentrics [n,3], valid [n])."""
+    texels = np.asarray(texels, np.int64)
+    force = np.full(asset.W * asset.H, -1, np.int32)
+    force[texels] = np.asarray(tris, np.int32)
+    r = bake_asset(asset, sample=texels, force=force, query=query, use_bvh=False)
+    tri = r["hit_tri"].reshape(-1)[texels]
+    return (r["nts"].reshape(-1, 3)[texels], r["hit_t"].reshape(-1)[texels], r["hit_b"].reshape(-1, 3)[texels],
+            tri >= 0)
+
+
+def normal_map_error(high_v, high_f, low_v, low_f, low_uv, W, H, rgba8, sample_face, sample_bary, max_dist, *,
+                     diam=None, bvh: Bvh | None = None, use_bvh=True, nthreads=None):
+    """The "baked mean" measure of Sec. 6.1 in FP64, per sample point of the
+    low mesh (face id and barycentrics b1, b2 of corners 1 and 2): the angle
+    in degrees between the normal the RGBA8 map gives there (decoded and
+    taken to world space through the bake's tangent frame at the point) and
+    the raw mesh's smooth normal at its surface point nearest to the sample
+    (-1 with none within max_dist).  Returns (angle [n], flags [n]); flag 1:
+    two raw triangles within rounding of the nearest distance give different
+    normals."""
+    lib = _load()
+    hv = _c(high_v, np.float32)
+    hf = _c(high_f, np.int32)
+    lv = _c(low_v, np.float32)
+    lf = _c(low_f, np.int32)
+    luv = _c(low_uv, np.float32)
+    rgba = _c(rgba8, np.uint8)
+    sf = _c(sample_face, np.int32)
+    sb = _c(sample_bary, np.float64).reshape(-1, 2)
+    if rgba.size != W * H * 4 or len(sb) != len(sf):
+        raise ValueError("map or sample sizes do not match")
+    if len(sf) and (sf.min() < 0 or sf.max() >= len(lf)):
+        raise ValueError("sample face out of range")
+    if diam is None:
+        diam = float(np.linalg.norm(hv.astype(np.float64).max(0) - hv.astype(np.float64).min(0)))
+    hn = vertex_normals(hv, hf)
+    ln = vertex_normals(lv, lf)
+    T, w, _ = face_frames(lv, lf, luv, W, H, ln)
+    if use_bvh and bvh is None:
+        bvh = Bvh(hv, hf)
+    angle = np.zeros(len(sf), np.float64)
+    flags = np.zeros(len(sf), np.uint8)
+    rc = lib.or_normal_map_error(_p(hv), len(hv), _p(hf), len(hf), _p(hn), bvh.h if use_bvh else None,
+                                 _p(lv), _p(lf), _p(ln), _p(luv), _p(_c(T, np.float64)), _p(_c(w, np.float64)),
+                                 W, H, _p(rgba), _p(sf), _p(sb), len(sf), float(max_dist), float(diam),
+                                 nthreads or default_threads(), _p(angle), _p(flags))
+    if rc != 0:
+        raise RuntimeError("oracle normal_map_error: thread start failed")
+    return angle, flags
 
 
 def bake_asset(asset, **kw):

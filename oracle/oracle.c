@@ -338,6 +338,22 @@ static int isect(const ray_t *r, d3 A, d3 B, d3 C, double *t, double b[3]) {
     return 1;
 }
 
+/* the same edge functions without the inside test: the line's parameter and
+ * signed barycentrics on the plane of (A, B, C); 0 when the line is parallel */
+static int plane_hit(const ray_t *r, d3 A, d3 B, d3 C, double *t, double b[3]) {
+    d3 a = sub(A, r->o), bb = sub(B, r->o), c = sub(C, r->o);
+    double Ax = comp(a, r->kx) - r->Sx * comp(a, r->kz), Ay = comp(a, r->ky) - r->Sy * comp(a, r->kz);
+    double Bx = comp(bb, r->kx) - r->Sx * comp(bb, r->kz), By = comp(bb, r->ky) - r->Sy * comp(bb, r->kz);
+    double Cx = comp(c, r->kx) - r->Sx * comp(c, r->kz), Cy = comp(c, r->ky) - r->Sy * comp(c, r->kz);
+    double U = Cx * By - Cy * Bx, Vv = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+    double det = U + Vv + W;
+    if (det == 0.0) return 0;
+    double T = U * r->Sz * comp(a, r->kz) + Vv * r->Sz * comp(bb, r->kz) + W * r->Sz * comp(c, r->kz);
+    *t = T / det;
+    b[0] = U / det; b[1] = Vv / det; b[2] = W / det;
+    return 1;
+}
+
 static int better(double t, int id, const hit_t *best) {
     if (best->tri < 0) return 1;
     double at = fabs(t), ab = fabs(best->t);
@@ -652,6 +668,7 @@ typedef struct {
     const int64_t *texels; int64_t ntex;
     uint8_t *mask; double *nts; double *disp; int32_t *hit_tri; double *hit_t; double *hit_b; uint8_t *flags;
     int query;
+    const int32_t *force;   /* optional [W*H]: evaluate this triangle instead of searching */
     int nthreads, tid;
 } trace_job;
 
@@ -700,7 +717,26 @@ static void trace_one(const trace_job *j, int64_t tex) {
     uint8_t fl = 0;
     int hit = 0, tri = -1;
     double disp = 0.0, hb[3] = {0.0, 0.0, 0.0};
-    if (j->query == 0) {
+    if (j->force) {
+        /* The given triangle alone, for checking an answer of another
+         * implementation where several are equally correct: the ray query
+         * takes the line's crossing of its plane (signed barycentrics, so a
+         * triangle missed by a hair shows a slightly negative one), the
+         * closest-point query its nearest point.  No filter, no flags. */
+        tri = j->force[tex];
+        if (tri < 0) return;
+        d3 A = ldf(j->hv, j->hf[3 * tri]), B = ldf(j->hv, j->hf[3 * tri + 1]), C = ldf(j->hv, j->hf[3 * tri + 2]);
+        if (j->query == 0) {
+            ray_t r = make_ray(p, d);
+            hit = plane_hit(&r, A, B, C, &disp, hb);
+        } else {
+            d3 x;
+            double dist = sqrt(tri_closest(p, A, B, C, &x, hb));
+            disp = dot(sub(x, p), d) >= 0.0 ? dist : -dist;
+            hit = 1;
+        }
+        if (!hit) { tri = -1; disp = 0.0; }
+    } else if (j->query == 0) {
         hit_t h;
         closest(j->hv, j->hf, j->nhf, j->bvh, p, d, j->max_dist + tol, -1, &h);
         hit = h.tri >= 0 && fabs(h.t) <= j->max_dist;
@@ -774,19 +810,112 @@ int or_trace(const float *hv, int64_t nhv, const int32_t *hf, int64_t nhf, const
              const int32_t *face, const double *bary, int W, int H, double max_dist, double diam,
              const int64_t *texels, int64_t ntex, int nthreads,
              uint8_t *mask, double *nts, double *disp, int32_t *hit_tri, double *hit_t, double *hit_b, uint8_t *flags,
-             int query) {
+             int query, const int32_t *force) {
     (void)nhv;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 256) nthreads = 256;
     trace_job base = {hv, hf, nhf, hn, (const obvh *)bvh, lv, lf, ln, luv, T, wsign, degen, face, bary,
                       W, H, max_dist, diam, texels, texels ? ntex : (int64_t)W * H,
-                      mask, nts, disp, hit_tri, hit_t, hit_b, flags, query, nthreads, 0};
+                      mask, nts, disp, hit_tri, hit_t, hit_b, flags, query, force, nthreads, 0};
     trace_job jobs[256];
     pthread_t th[256];
     for (int i = 0; i < nthreads; ++i) { jobs[i] = base; jobs[i].tid = i; }
     for (int i = 1; i < nthreads; ++i)
         if (pthread_create(&th[i], NULL, trace_worker, &jobs[i])) return -1;
     trace_worker(&jobs[0]);
+    for (int i = 1; i < nthreads; ++i) pthread_join(th[i], NULL);
+    return 0;
+}
+
+/* ------------------------------------------------- "baked mean" (Sec. 6.1)
+ * The quality measure of a baked normal map that the simplification benchmark
+ * reports: at points spread uniformly by area over the simplified (low) mesh,
+ * the angle between the normal the map gives there and the true normal of
+ * the raw (high) mesh, averaged over the points.  Readings of what the paper
+ * leaves open:
+ *  - sample k is given by the caller: face f_k and barycentrics
+ *    (1 - b1 - b2, b1, b2);
+ *  - the map is read at the texel holding the sample's UV point,
+ *    x = floor(u W), y = floor(v H) (clamped to the atlas), unfiltered; the
+ *    RGB codes decode as c = (q - 128) / 127 (the inverse of the encoding of
+ *    section 6) and the vector is renormalised;
+ *  - it is taken to world space through the tangent frame of the bake at the
+ *    sample point: N = normalize(sum b_i n_i), T = the interpolated corner
+ *    tangents made orthogonal to N, B = w (N x T);
+ *  - the raw mesh's true normal is its area-weighted smooth normal,
+ *    interpolated at the point of the raw surface nearest to the sample
+ *    (within max_dist; with none, the angle is -1);
+ *  - angle = atan2(|a x b|, a . b), in degrees.
+ * flags bit0: another raw triangle within 1e-7 * diam of the nearest distance
+ * gives a smooth normal more than 1e-5 away (two correct answers). */
+typedef struct {
+    trace_job j;
+    const int32_t *sface; const double *sbary; int64_t n;
+    const uint8_t *rgba; double *angle; uint8_t *sflags;
+} map_err_job;
+
+static void map_error_one(const map_err_job *m, int64_t k) {
+    const trace_job *j = &m->j;
+    int32_t f = m->sface[k];
+    double b[3] = {1.0 - m->sbary[2 * k] - m->sbary[2 * k + 1], m->sbary[2 * k], m->sbary[2 * k + 1]};
+    int32_t ids[3] = {j->lf[3 * f], j->lf[3 * f + 1], j->lf[3 * f + 2]};
+    d3 p = mk(0, 0, 0), s = mk(0, 0, 0), ts = mk(0, 0, 0);
+    double u = 0.0, v = 0.0;
+    for (int q = 0; q < 3; ++q) {
+        p = add(p, scl(ldf(j->lv, ids[q]), b[q]));
+        s = add(s, scl(ldd(j->ln, ids[q]), b[q]));
+        ts = add(ts, scl(ldd(j->T, 3 * f + q), b[q]));
+        u += b[q] * j->luv[6 * f + 2 * q];
+        v += b[q] * j->luv[6 * f + 2 * q + 1];
+    }
+    d3 N = normalize(s);
+    d3 Tt = normalize(sub(ts, scl(N, dot(ts, N))));
+    d3 B = scl(cross(N, Tt), j->wsign[f]);
+    int x = (int)floor(u * j->W), y = (int)floor(v * j->H);
+    if (x < 0) x = 0;
+    if (x > j->W - 1) x = j->W - 1;
+    if (y < 0) y = 0;
+    if (y > j->H - 1) y = j->H - 1;
+    const uint8_t *q8 = m->rgba + 4 * ((int64_t)y * j->W + x);
+    d3 c = normalize(mk((q8[0] - 128.0) / 127.0, (q8[1] - 128.0) / 127.0, (q8[2] - 128.0) / 127.0));
+    d3 nm = normalize(add(add(scl(Tt, c.x), scl(B, c.y)), scl(N, c.z)));
+    cpt_t cp;
+    closest_point(j->hv, j->hf, j->nhf, j->bvh, p, j->max_dist, &cp);
+    m->sflags[k] = 0;
+    if (cp.tri < 0) { m->angle[k] = -1.0; return; }
+    d3 nr = hit_normal(j, cp.tri, cp.b);
+    m->angle[k] = atan2(norm(cross(nm, nr)), dot(nm, nr)) * (180.0 / 3.14159265358979323846);
+    cp_amb_t a = {j, cp.tri, nr, p, N, 1, 0, 0};
+    cp_range(j->hv, j->hf, j->nhf, j->bvh, p, sqrt(cp.d2) + 1e-7 * j->diam, cp_amb_visit, &a);
+    if (a.ambiguous) m->sflags[k] |= 1;
+}
+
+static void *map_error_worker(void *arg) {
+    map_err_job *m = (map_err_job *)arg;
+    for (int64_t k = m->j.tid; k < m->n; k += m->j.nthreads) map_error_one(m, k);
+    return NULL;
+}
+
+int or_normal_map_error(const float *hv, int64_t nhf_unused, const int32_t *hf, int64_t nhf, const double *hn,
+                        void *bvh, const float *lv, const int32_t *lf, const double *ln, const float *luv,
+                        const double *T, const double *wsign, int W, int H, const uint8_t *rgba,
+                        const int32_t *sface, const double *sbary, int64_t n, double max_dist, double diam,
+                        int nthreads, double *angle, uint8_t *sflags) {
+    (void)nhf_unused;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    map_err_job base;
+    memset(&base, 0, sizeof(base));
+    base.j.hv = hv; base.j.hf = hf; base.j.nhf = nhf; base.j.hn = hn; base.j.bvh = (const obvh *)bvh;
+    base.j.lv = lv; base.j.lf = lf; base.j.ln = ln; base.j.luv = luv; base.j.T = T; base.j.wsign = wsign;
+    base.j.W = W; base.j.H = H; base.j.max_dist = max_dist; base.j.diam = diam; base.j.nthreads = nthreads;
+    base.sface = sface; base.sbary = sbary; base.n = n; base.rgba = rgba; base.angle = angle; base.sflags = sflags;
+    map_err_job jobs[256];
+    pthread_t th[256];
+    for (int i = 0; i < nthreads; ++i) { jobs[i] = base; jobs[i].j.tid = i; }
+    for (int i = 1; i < nthreads; ++i)
+        if (pthread_create(&th[i], NULL, map_error_worker, &jobs[i])) return -1;
+    map_error_worker(&jobs[0]);
     for (int i = 1; i < nthreads; ++i) pthread_join(th[i], NULL);
     return 0;
 }
@@ -803,15 +932,15 @@ int or_trace(const float *hv, int64_t nhv, const int32_t *hf, int64_t nhf, const
  * pass gives every unfilled texel with at least one filled 8-neighbour (as of
  * the previous pass) the renormalised mean of those neighbours' tangent-space
  * normals and the mean of their displacements.  The hit mask is not dilated. */
-/* The 8-bit code is an integer decided by floating point, so it is taken in
- * the precision of the GPU kernel it is compared with: the FP64 value is
- * rounded to FP32 and every step below is one FP32 rounding. */
+/* The code is taken from the FP64 component itself; a kernel working in a
+ * narrower precision may land one code away where 127*c lies within its
+ * rounding of a half-integer, which the comparison's 1-LSB allowance covers. */
 static uint8_t enc(double c) {
-    float v = (float)c;
-    if (v < -1.0f) v = -1.0f;
-    if (v > 1.0f) v = 1.0f;
-    float r = v * 127.0f;
-    float q = r >= 0.0f ? floorf(r + 0.5f) : -floorf(-r + 0.5f);
+    double v = c;
+    if (v < -1.0) v = -1.0;
+    if (v > 1.0) v = 1.0;
+    double r = v * 127.0;
+    double q = r >= 0.0 ? floor(r + 0.5) : -floor(-r + 0.5);
     return (uint8_t)(128 + (int)q);
 }
 

@@ -364,6 +364,22 @@ def jittered_atlas(n_faces: int, W: int, H: int, seed: int, gutter: int = 2):
 # assembled assets
 # --------------------------------------------------------------------------
 
+def surface_samples(V, F, n: int, seed: int):
+    """n seeded points spread uniformly by area over a triangle mesh, as
+    (face id int32 [n], barycentrics (b1, b2) of corners 1 and 2 float32 [n, 2]):
+    a face drawn with probability proportional to its area, then a uniform
+    point of it (the square's two halves folded onto one triangle)."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F, np.int64)
+    area = np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)
+    rng = np.random.default_rng(seed)
+    face = rng.choice(len(F), size=n, p=area / area.sum()).astype(np.int32)
+    u, v = rng.random(n), rng.random(n)
+    flip = u + v > 1.0
+    u, v = np.where(flip, 1.0 - u, u), np.where(flip, 1.0 - v, v)
+    return face, np.stack([u, v], -1).astype(np.float32)
+
+
 @dataclass
 class Asset:
     high_v: np.ndarray

@@ -33,7 +33,7 @@ def test_tiny_closest_matches_brute_force_oracle(seed, layout):
     a = synth.tiny_asset(seed)
     o = oracle.bake_asset(a, use_bvh=False, query="closest")
     _, g, _ = gpu_bake(a, layout)
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a, query="closest")
     print(st)
     parity.check(st)
     assert st["n_ray"] == 4000
@@ -47,7 +47,7 @@ def test_closest_jittered_atlas_ragged_sizes(W, H, seed):
     a = synth.Asset(hv, hf, lv, lf, uv, W, H, 0.15, 2)
     o = oracle.bake_asset(a, query="closest")
     _, g, _ = gpu_bake(a)
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a, query="closest")
     print(st)
     parity.check(st)
 
@@ -59,7 +59,7 @@ def test_closest_sdf_asset_and_layouts_identical():
     a = synth.sdf_asset(7, 120_000, 6_000, 512, 384, n_prims=16)
     o = oracle.bake_asset(a, query="closest")
     _, g, _ = gpu_bake(a, "q8")
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a, query="closest")
     print(st)
     parity.check(st)
     _, g2, _ = gpu_bake(a, "f32")
@@ -170,7 +170,7 @@ def test_closest_full_size_sampled_parity():
     sample = np.sort(rng.choice(rays, size=3000, replace=False))
     o = oracle.bake_asset(a, sample=sample, query="closest")
     assert np.array_equal(o["face"], face)
-    st = parity.compare(g, o, a.diam, a.gutter, sample=sample)
+    st = parity.compare(g, o, a.diam, a.gutter, sample=sample, asset=a, query="closest")
     print(st)
     parity.check(st, small=0)
     n = g["normal_ts"]

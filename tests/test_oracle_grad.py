@@ -64,3 +64,36 @@ def test_gradient_coordinate_subset_sign():
     L1, _ = oracle.loss_grad(*args, lv + step, a.low_f, r["face"], r["bary"], r["hit_tri"], 0.1, False)
     L2, _ = oracle.loss_grad(*args, lv - step, a.low_f, r["face"], r["bary"], r["hit_tri"], 0.1, False)
     assert L1 > L0 > L2
+
+
+def test_normal_term_closed_form_on_tilted_plane():
+    """The lambda term in closed form.  A flat low quad (normal +z) under a
+    high plane z = h - s y that covers only part of it: every hit texel sees
+    the plane's normal (0, s, 1)/sqrt(1 + s^2), so n_hit . d = 1/sqrt(1 + s^2)
+    and L(lambda) - L(0) = lambda (1 - 1/sqrt(1 + s^2)), with the mean taken
+    over the hit texels only.  Texels the plane does not cover miss, so a
+    mean over all ray texels would scale the term by the hit fraction."""
+    h, s = 0.05, 0.3
+    lv = np.array([[-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0]], np.float32)
+    lf = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    uv = np.array([[(0.1 + 0.4 * (lv[i, 0] + 1), 0.1 + 0.4 * (lv[i, 1] + 1)) for i in f] for f in lf], np.float32)
+    n = 24
+    xs, ys = np.linspace(-1.5, 0.2, n + 1), np.linspace(-1.5, 1.5, n + 1)
+    X, Y = np.meshgrid(xs, ys)
+    hv = np.stack([X.ravel(), Y.ravel(), h - s * Y.ravel()], -1).astype(np.float32)
+    hf = []
+    for j in range(n):
+        for i in range(n):
+            a = j * (n + 1) + i
+            hf += [(a, a + 1, a + n + 2), (a, a + n + 2, a + n + 1)]
+    hf = np.asarray(hf, np.int32)
+    r = oracle.bake(hv, hf, lv, lf, uv, 64, 64, 0.5)
+    ray = r["face"] >= 0
+    hit = ray & (r["mask"] == 1)
+    frac = hit.sum() / ray.sum()
+    assert 0.4 < frac < 0.8, frac
+    args = (hv, hf, r["high_normals"], lv.astype(np.float64), lf, r["face"], r["bary"], r["hit_tri"])
+    L0, _ = oracle.loss_grad(*args, 0.0, False)
+    for lam in (0.1, 0.7):
+        L, _ = oracle.loss_grad(*args, lam, False)
+        assert (L - L0) / lam == pytest.approx(1.0 - 1.0 / np.sqrt(1.0 + s * s), abs=1e-6)

@@ -118,3 +118,42 @@ def test_tie_rules():
     assert tri >= 0 and t == pytest.approx(0.02)
     tri, _, _ = oracle.closest_hit(Vp, Fp, o, d, np.nextafter(np.float32(0.02), 0) * 0.999)
     assert tri == -1
+
+
+@pytest.mark.parametrize("query", ["ray", "closest"])
+def test_shade_given_triangle(query):
+    """The evaluation of one given triangle per texel (used to check answers
+    where two triangles are within rounding of the closest one): with the
+    oracle's own closest triangle it reproduces the search's normal,
+    displacement and barycentrics; on a flat plane z = c any triangle gives
+    t = c (the plane's crossing) and the normal (0, 0, 1); a triangle beside
+    the texel's ray shows a negative barycentric (ray) or lies farther than
+    the plane's distance (closest point)."""
+    a = synth.tiny_asset(4)
+    r = oracle.bake_asset(a, query=query)
+    tex = np.flatnonzero((r["mask"] == 1).reshape(-1))[::7]
+    tris = r["hit_tri"].reshape(-1)[tex]
+    nts, t, b, valid = oracle.shade_given(a, tex, tris, query)
+    assert valid.all()
+    assert np.abs(nts - r["nts"].reshape(-1, 3)[tex]).max() < 1e-12
+    assert np.abs(t - r["hit_t"].reshape(-1)[tex]).max() < 1e-12
+    assert np.abs(b - r["hit_b"].reshape(-1, 3)[tex]).max() < 1e-9 and b.min() >= 0.0
+
+    lv = np.array([[-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0]], np.float32)
+    lf = np.array([[0, 1, 2], [0, 2, 3]], np.int32)
+    uv = synth.grid_atlas(2, 32, 32, 2)
+    c = 0.0625
+    hv, hf = _plane(8, c, 1.5)
+    p = synth.Asset(hv, hf, lv, lf, uv, 32, 32, 0.5, 2)
+    rp = oracle.bake_asset(p, query=query)
+    tex = np.flatnonzero((rp["mask"] == 1).reshape(-1))
+    own = rp["hit_tri"].reshape(-1)[tex]
+    other = (own + 37) % len(hf)
+    nts, t, b, valid = oracle.shade_given(p, tex, other, query)
+    assert valid.all()
+    assert np.abs(nts - [0.0, 0.0, 1.0]).max() < 1e-12
+    if query == "ray":
+        assert np.abs(t - c).max() < 1e-12
+        assert (b.min(1) < -1e-3).all()
+    else:
+        assert (np.abs(t) > c + 1e-3).all()

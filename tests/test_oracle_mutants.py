@@ -28,7 +28,7 @@ MUTANTS = {
     "displacement sign flipped":
         ("disp = h.tri >= 0 ? h.t : 0.0;", "disp = h.tri >= 0 ? -h.t : 0.0;"),
     "RGB8 scale 128":
-        ("float r = v * 127.0f;", "float r = v * 128.0f;"),
+        ("double r = v * 127.0;", "double r = v * 128.0;"),
     "dilated normal not renormalised":
         ("std3(nts, i, norm(mm) > 0 ? normalize(mm) : mk(0, 0, 1));", "std3(nts, i, mm);"),
     "tangent not made orthogonal to the normal":
@@ -48,6 +48,20 @@ ROW_MUTANTS = {
     "exterior fill gate dropped":
         ("if (dot(nf_, ldd(nrm, g)) > 0.0) { exterior[g] = 1; queue[qt++] = g; }",
          "{ exterior[g] = 1; queue[qt++] = g; }", ["tests/test_oracle_hidden.py"]),
+    "loss: normal term averaged over every ray texel instead of the hit texels":
+        ("    return (sum_t + lambda * sum_n) * inv;",
+         "    int64_t nray = 0;\n    for (int64_t k = 0; k < ntex; ++k) nray += face[k] >= 0;\n"
+         "    return sum_t * inv + lambda * sum_n / (double)nray;", ["tests/test_oracle_grad.py"]),
+    "baked mean: map codes decoded about 127":
+        ("d3 c = normalize(mk((q8[0] - 128.0) / 127.0, (q8[1] - 128.0) / 127.0, (q8[2] - 128.0) / 127.0));",
+         "d3 c = normalize(mk((q8[0] - 127.0) / 127.0, (q8[1] - 127.0) / 127.0, (q8[2] - 127.0) / 127.0));",
+         ["tests/test_oracle_map_error.py"]),
+    "baked mean: texel row read from the far side":
+        ("const uint8_t *q8 = m->rgba + 4 * ((int64_t)y * j->W + x);",
+         "const uint8_t *q8 = m->rgba + 4 * ((int64_t)(j->H - 1 - y) * j->W + x);", ["tests/test_oracle_map_error.py"]),
+    "baked mean: bitangent handedness dropped":
+        ("    d3 B = scl(cross(N, Tt), j->wsign[f]);\n    int x = (int)floor(u * j->W)",
+         "    d3 B = cross(N, Tt);\n    int x = (int)floor(u * j->W)", ["tests/test_oracle_map_error.py"]),
     "backprojection incidence exponent dropped":
         ("L[nk] = log((double)weights[k]) + alpha * log(I);", "L[nk] = log((double)weights[k]) + log(I);",
          ["tests/test_oracle_backproject.py"]),
