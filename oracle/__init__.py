@@ -72,7 +72,7 @@ def _load():
         lib.or_trace.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P,
                                  _I, _I, _D, _D, _P, _I64, _I, _P, _P, _P, _P, _P, _P, _P, _I, _P]
         lib.or_trace.restype = _I
-        lib.or_normal_map_error.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P,
+        lib.or_normal_map_error.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _I, _P,
                                             _P, _P, _I64, _D, _D, _I, _P, _P]
         lib.or_normal_map_error.restype = _I
         lib.or_encode.argtypes = [_P, _P, _I64, _P]
@@ -94,7 +94,8 @@ def _load():
         lib.or_edge_mask.argtypes = [_P, _P, _I, _I, _D, _P]
         lib.or_edge_mask.restype = _I
         lib.or_backproject.argtypes = [_P, _I64, _P, _I64, _P, _P, _P, _P, _I, _I, _I, _P, _P, _I, _I, _P, _P, _P,
-                                       _P, _D, _D, _D, _D, _D, _I, _D, _I, _D, _P, _P, _P, _P]
+                                       _P, _D, _D, _D, _D, _D, _I, _D, _I, _D, _P, _P, _P, _P, _P, _I64, _I64,
+                                       _P, _P, _P, _P]
         lib.or_mip_levels.argtypes = [_P, _I, _I, _D, _P, _P, _P]
         lib.or_mip_levels.restype = _I
         lib.or_backproject.restype = _I
@@ -319,7 +320,8 @@ def normal_map_error(high_v, high_f, low_v, low_f, low_uv, W, H, rgba8, sample_f
     """The "baked mean" measure of Sec. 6.1 in FP64, per sample point of the
     low mesh (face id and barycentrics b1, b2 of corners 1 and 2): the angle
     in degrees between the normal the RGBA8 map gives there (decoded and
-    taken to world space through the bake's tangent frame at the point) and
+    taken to world space through the bake's tangent frame at the point; on a
+    degenerate-UV face the interpolated low normal) and
     the raw mesh's smooth normal at its surface point nearest to the sample
     (-1 with none within max_dist).  Returns (angle [n], flags [n]); flag 1:
     two raw triangles within rounding of the nearest distance give different
@@ -341,14 +343,14 @@ def normal_map_error(high_v, high_f, low_v, low_f, low_uv, W, H, rgba8, sample_f
         diam = float(np.linalg.norm(hv.astype(np.float64).max(0) - hv.astype(np.float64).min(0)))
     hn = vertex_normals(hv, hf)
     ln = vertex_normals(lv, lf)
-    T, w, _ = face_frames(lv, lf, luv, W, H, ln)
+    T, w, dg = face_frames(lv, lf, luv, W, H, ln)
     if use_bvh and bvh is None:
         bvh = Bvh(hv, hf)
     angle = np.zeros(len(sf), np.float64)
     flags = np.zeros(len(sf), np.uint8)
     rc = lib.or_normal_map_error(_p(hv), len(hv), _p(hf), len(hf), _p(hn), bvh.h if use_bvh else None,
                                  _p(lv), _p(lf), _p(ln), _p(luv), _p(_c(T, np.float64)), _p(_c(w, np.float64)),
-                                 W, H, _p(rgba), _p(sf), _p(sb), len(sf), float(max_dist), float(diam),
+                                 _p(_c(dg, np.uint8)), W, H, _p(rgba), _p(sf), _p(sb), len(sf), float(max_dist), float(diam),
                                  nthreads or default_threads(), _p(angle), _p(flags))
     if rc != 0:
         raise RuntimeError("oracle normal_map_error: thread start failed")
@@ -568,12 +570,16 @@ def mip_levels(img, sharpen: float = 0.25):
 
 def backproject(lv, lf, luv, W: int, H: int, cams, images, weights, *, alpha: float, eps: float,
                 depth_tol: float, edge_tol: float, views=None, tol_rel: float = 1e-5, filter: str = "aniso",
-                lod_bias: float = -0.5, max_taps: int = 8, sharpen: float = 0.25):
+                lod_bias: float = -0.5, max_taps: int = 8, sharpen: float = 0.25, sample=None,
+                variants: bool = False):
     """Texture [H,W,3] (FP64), filled [H,W], flags [H,W] and incidence
     [K,H,W] of the blended backprojection of K views onto the low mesh's
     atlas.  ``views`` = (depth, point, near) from render_views, rendered here
     when None.  filter: "aniso" (footprint taps over a Lanczos-2 pyramid) or
-    "bilinear" (one sample)."""
+    "bilinear" (one sample).  ``sample`` (texel ids): only those texels.
+    ``variants``: for every flagged texel, the set of correct results
+    ("variants": {texel: array [n, 4] of rgb + filled}, an empty array when
+    there are too many to list)."""
     lib = _load()
     lv = _c(lv, np.float32)
     lf = _c(lf, np.int32)
@@ -593,12 +599,25 @@ def backproject(lv, lf, luv, W: int, H: int, cams, images, weights, *, alpha: fl
     filled = np.zeros((H, W), np.uint8)
     flags = np.zeros((H, W), np.uint8)
     incid = np.zeros((K, H, W), np.float64)
+    texels = None if sample is None else _c(sample, np.int64)
+    max_var = 0
+    if variants:
+        max_var = len(texels) if texels is not None else int((face >= 0).sum())
+    var_tex = np.zeros(max(max_var, 1), np.int64)
+    var_n = np.zeros(max(max_var, 1), np.uint8)
+    var_rgbf = np.zeros((max(max_var, 1), 64, 4), np.float64)
+    n_var = np.zeros(1, np.int64)
     rc = lib.or_backproject(_p(lv), len(lv), _p(lf), len(lf), _p(ln), _p(luv), _p(face), _p(bary), W, H, K,
                             _p(cams), _p(images), iw, ih, _p(depth), _p(point), _p(near), _p(weights), float(alpha),
                             float(eps), float(depth_tol), float(edge_tol), scale,
                             {"bilinear": 0, "aniso": 1}[filter], float(lod_bias), int(max_taps), float(sharpen),
-                            _p(tex), _p(filled), _p(flags), _p(incid))
+                            _p(tex), _p(filled), _p(flags), _p(incid), _p(texels),
+                            0 if texels is None else len(texels), max_var,
+                            _p(var_tex) if variants else None, _p(var_n), _p(var_rgbf), _p(n_var))
     if rc != 0:
         raise MemoryError("or_backproject failed")
-    return dict(texture=tex, filled=filled, flags=flags, incidence=incid, face=face, bary=bary,
-                depth=depth, point=point, near=near)
+    out = dict(texture=tex, filled=filled, flags=flags, incidence=incid, face=face, bary=bary,
+               depth=depth, point=point, near=near)
+    if variants:
+        out["variants"] = {int(var_tex[j]): var_rgbf[j, :var_n[j]].copy() for j in range(int(n_var[0]))}
+    return out

@@ -841,7 +841,9 @@ int or_trace(const float *hv, int64_t nhv, const int32_t *hf, int64_t nhf, const
  *    section 6) and the vector is renormalised;
  *  - it is taken to world space through the tangent frame of the bake at the
  *    sample point: N = normalize(sum b_i n_i), T = the interpolated corner
- *    tangents made orthogonal to N, B = w (N x T);
+ *    tangents made orthogonal to N, B = w (N x T); on a face the
+ *    UV-reliability filter marks (degenerate UVs, whose frame is bookkeeping
+ *    only) the map is not used and the normal is N, as a neutral texel gives;
  *  - the raw mesh's true normal is its area-weighted smooth normal,
  *    interpolated at the point of the raw surface nearest to the sample
  *    (within max_dist; with none, the angle is -1);
@@ -878,7 +880,7 @@ static void map_error_one(const map_err_job *m, int64_t k) {
     if (y > j->H - 1) y = j->H - 1;
     const uint8_t *q8 = m->rgba + 4 * ((int64_t)y * j->W + x);
     d3 c = normalize(mk((q8[0] - 128.0) / 127.0, (q8[1] - 128.0) / 127.0, (q8[2] - 128.0) / 127.0));
-    d3 nm = normalize(add(add(scl(Tt, c.x), scl(B, c.y)), scl(N, c.z)));
+    d3 nm = j->degen[f] ? N : normalize(add(add(scl(Tt, c.x), scl(B, c.y)), scl(N, c.z)));
     cpt_t cp;
     closest_point(j->hv, j->hf, j->nhf, j->bvh, p, j->max_dist, &cp);
     m->sflags[k] = 0;
@@ -898,7 +900,8 @@ static void *map_error_worker(void *arg) {
 
 int or_normal_map_error(const float *hv, int64_t nhf_unused, const int32_t *hf, int64_t nhf, const double *hn,
                         void *bvh, const float *lv, const int32_t *lf, const double *ln, const float *luv,
-                        const double *T, const double *wsign, int W, int H, const uint8_t *rgba,
+                        const double *T, const double *wsign, const uint8_t *degen, int W, int H,
+                        const uint8_t *rgba,
                         const int32_t *sface, const double *sbary, int64_t n, double max_dist, double diam,
                         int nthreads, double *angle, uint8_t *sflags) {
     (void)nhf_unused;
@@ -908,6 +911,7 @@ int or_normal_map_error(const float *hv, int64_t nhf_unused, const int32_t *hf, 
     memset(&base, 0, sizeof(base));
     base.j.hv = hv; base.j.hf = hf; base.j.nhf = nhf; base.j.hn = hn; base.j.bvh = (const obvh *)bvh;
     base.j.lv = lv; base.j.lf = lf; base.j.ln = ln; base.j.luv = luv; base.j.T = T; base.j.wsign = wsign;
+    base.j.degen = degen;
     base.j.W = W; base.j.H = H; base.j.max_dist = max_dist; base.j.diam = diam; base.j.nthreads = nthreads;
     base.sface = sface; base.sbary = sbary; base.n = n; base.rgba = rgba; base.angle = angle; base.sflags = sflags;
     map_err_job jobs[256];
@@ -2029,19 +2033,24 @@ int or_edge_mask(const double *depth, const double *point, int w, int h, double 
 }
 
 /* the anisotropic colour of one view at image position (u, v) for the texel
- * of face f at surface point p (the readings above); *fl is set when the tap
- * count or the fallback decision lies within rounding of its threshold */
-static void aniso_color(const float *lv, const int32_t *lf, const float *luv, int W, int H, int32_t f, d3 p,
-                        const cam_t *c, const uint8_t *img, const mips_t *m, double u, double v, double lod_bias,
-                        int max_taps, double out[3], uint8_t *fl) {
+ * of face f at surface point p (the readings above).  Two of its decisions
+ * are thresholds: the footprint or the centre-sample fallback (UV area at
+ * least 1e-4 texel^2), and the tap count N = ceil(s1 / s2 - 0.05).
+ * force_centre (-1: decide, 0: footprint, 1: centre sample) and force_taps
+ * (0: decide, else that N) fix them.  *amb gets bit0 when the area, bit1 when
+ * the ratio lies within rounding of its threshold; *taps the N used. */
+static void aniso_core(const float *lv, const int32_t *lf, const float *luv, int W, int H, int32_t f, d3 p,
+                       const cam_t *c, const uint8_t *img, const mips_t *m, double u, double v, double lod_bias,
+                       int max_taps, int force_centre, int force_taps, double out[3], int *amb, int *taps) {
     double x[3], y[3];
     for (int q = 0; q < 3; ++q) {
         x[q] = (double)luv[6 * (int64_t)f + 2 * q] * W;
         y[q] = (double)luv[6 * (int64_t)f + 2 * q + 1] * H;
     }
     double det = (x[1] - x[0]) * (y[2] - y[0]) - (x[2] - x[0]) * (y[1] - y[0]);
-    if (fabs(fabs(det) * 0.5 - 1e-4) < 1e-6) *fl = 1;
-    int ok = fabs(det) * 0.5 >= 1e-4;
+    if (fabs(fabs(det) * 0.5 - 1e-4) < 1e-6) *amb |= 1;
+    int ok = force_centre < 0 ? fabs(det) * 0.5 >= 1e-4 : !force_centre;
+    *taps = 0;
     d3 dpx = mk(0, 0, 0), dpy = mk(0, 0, 0);
     if (ok) {
         double b1x = (y[2] - y[0]) / det, b1y = -(x[2] - x[0]) / det;
@@ -2079,10 +2088,12 @@ static void aniso_color(const float *lv, const int32_t *lf, const float *luv, in
     if (s2 > 0.0) {
         double ratio = s1 / s2;
         for (int k = 1; k < max_taps; ++k)
-            if (fabs(ratio - 0.05 - k) < 1e-4 * ratio) *fl = 1;
+            if (fabs(ratio - 0.05 - k) < 1e-4 * ratio) *amb |= 2;
         double nf = ceil(ratio - 0.05);
         N = nf < 1.0 ? 1 : (nf > max_taps ? max_taps : (int)nf);
     }
+    if (force_taps > 0) N = force_taps;
+    *taps = N;
     double mm = s2 > s1 / max_taps ? s2 : s1 / max_taps;
     double lam = mm > 0.0 ? log2(mm) + lod_bias : 0.0;
     if (lam < 0.0) lam = 0.0;
@@ -2095,17 +2106,107 @@ static void aniso_color(const float *lv, const int32_t *lf, const float *luv, in
     for (int ch = 0; ch < 3; ++ch) out[ch] /= N;
 }
 
+/* the colour, and where one threshold decision lies within rounding the
+ * colour of its other branch: *ncol = 1, 2, or 0 when both decisions are
+ * within rounding at once (not enumerated); *fl is set on any of them */
+static void aniso_color(const float *lv, const int32_t *lf, const float *luv, int W, int H, int32_t f, d3 p,
+                        const cam_t *c, const uint8_t *img, const mips_t *m, double u, double v, double lod_bias,
+                        int max_taps, double out[3], double alt[3], int *ncol, uint8_t *fl) {
+    int amb = 0, taps = 0;
+    aniso_core(lv, lf, luv, W, H, f, p, c, img, m, u, v, lod_bias, max_taps, -1, 0, out, &amb, &taps);
+    *ncol = 1;
+    if (!amb) return;
+    *fl = 1;
+    int a2 = 0, t2 = 0;
+    if (amb == 1) {
+        /* the other side of the area threshold */
+        int centre = taps == 0;
+        aniso_core(lv, lf, luv, W, H, f, p, c, img, m, u, v, lod_bias, max_taps, !centre, 0, alt, &a2, &t2);
+        *ncol = 2;
+    } else if (amb == 2 && taps > 0) {
+        /* the other side of the tap-count threshold the ratio sits on */
+        int lo = taps, hi = taps + 1, other = 0;
+        for (int k = 1; k < max_taps; ++k)
+            if (k == taps || k + 1 == taps) { lo = k; hi = k + 1; }
+        other = taps == hi ? lo : hi;
+        if (other < 1) other = 1;
+        if (other > max_taps) other = max_taps;
+        aniso_core(lv, lf, luv, W, H, f, p, c, img, m, u, v, lod_bias, max_taps, 0, other, alt, &a2, &t2);
+        *ncol = other == taps ? 1 : 2;
+    } else {
+        *ncol = 0;
+    }
+}
+
+/* the blend of n counted views: sum e^(L_k - m) A_k / (sum e^(L_k - m) + eps e^(-m)), m = max L_k */
+static void blend_views(int n, const double *L, double (*A)[3], double eps, double out[3]) {
+    double m = L[0];
+    for (int k = 1; k < n; ++k) if (L[k] > m) m = L[k];
+    double num[3] = {0, 0, 0}, den = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double e = exp(L[k] - m);
+        den += e;
+        for (int ch = 0; ch < 3; ++ch) num[ch] += e * A[k][ch];
+    }
+    den += eps * exp(-m);
+    for (int ch = 0; ch < 3; ++ch) out[ch] = num[ch] / den;
+}
+
+/* The set of correct results of a flagged texel.  A view is flagged when its
+ * inclusion depends on rounding (a pixel or image boundary, a render within
+ * rounding, an edge or depth decision within rounding), or, with the
+ * anisotropic filter, when its tap count or fallback does; an implementation
+ * in another precision may then count the view or not, or take the other
+ * branch of the threshold.  Every combination of those choices is a correct
+ * result: each view contributes a list of options (absent, and/or present
+ * with one of its colours); the blends of all combinations are written,
+ * with a filled flag, up to OR_MAX_VARIANTS of them (0 = too many). */
+#define OR_MAX_VARIANTS 64
+typedef struct { int absent_ok, ncol; double L; double A[2][3]; } view_opt;
+
+static int enumerate_variants(int nv, const view_opt *vo, double eps, double *out /*[OR_MAX_VARIANTS*4]*/) {
+    int total = 1;
+    for (int k = 0; k < nv; ++k) {
+        total *= vo[k].absent_ok + vo[k].ncol;
+        if (total > OR_MAX_VARIANTS) return 0;
+    }
+    for (int c = 0; c < total; ++c) {
+        double L[64], A[64][3];
+        int n = 0, r = c;
+        for (int k = 0; k < nv; ++k) {
+            int no = vo[k].absent_ok + vo[k].ncol, o = r % no;
+            r /= no;
+            if (vo[k].absent_ok && o == 0) continue;
+            int col = o - vo[k].absent_ok;
+            L[n] = vo[k].L;
+            for (int ch = 0; ch < 3; ++ch) A[n][ch] = vo[k].A[col][ch];
+            ++n;
+        }
+        double *dst = out + 4 * (int64_t)c;
+        if (n == 0) { dst[0] = dst[1] = dst[2] = 0.0; dst[3] = 0.0; continue; }
+        blend_views(n, L, A, eps, dst);
+        dst[3] = 1.0;
+    }
+    return total;
+}
+
 /* texture [H*W*3], filled [H*W], flags [H*W], incid (optional) [K*H*W];
- * filter 0: one bilinear sample, 1: anisotropic (the readings above) */
+ * filter 0: one bilinear sample, 1: anisotropic (the readings above).
+ * texels (optional, ntex of them): only these texels (the others are left
+ * as they are).  var_* (optional): for up to max_var flagged texels, in
+ * order, the texel id, the number of correct results (0: too many to list)
+ * and the results [OR_MAX_VARIANTS][rgb, filled]; *n_var the count. */
 int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf, const double *ln, const float *luv,
                    const int32_t *face, const double *bary, int W, int H, int K, const float *cams,
                    const uint8_t *images, int iw, int ih, const double *depth, const double *point, const uint8_t *near,
                    const float *weights, double alpha, double eps, double depth_tol, double edge_tol, double scale,
                    int filter, double lod_bias, int max_taps, double sharpen, double *texture, uint8_t *filled,
-                   uint8_t *flags, double *incid) {
+                   uint8_t *flags, double *incid, const int64_t *texels, int64_t ntex, int64_t max_var,
+                   int64_t *var_tex, uint8_t *var_n, double *var_rgbf, int64_t *n_var) {
     (void)nlv; (void)nlf;
     int64_t npix = (int64_t)iw * ih;
     mips_t *mips = NULL;
+    if (n_var) *n_var = 0;
     if (filter) {
         mips = (mips_t *)calloc((size_t)(K > 0 ? K : 1), sizeof(mips_t));
         if (!mips) return -1;
@@ -2116,7 +2217,9 @@ int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf,
                 return -1;
             }
     }
-    for (int64_t tex = 0; tex < (int64_t)W * H; ++tex) {
+    int64_t count = texels ? ntex : (int64_t)W * H;
+    for (int64_t it = 0; it < count; ++it) {
+        int64_t tex = texels ? texels[it] : it;
         texture[3 * tex] = texture[3 * tex + 1] = texture[3 * tex + 2] = 0.0;
         filled[tex] = 0;
         flags[tex] = 0;
@@ -2131,7 +2234,8 @@ int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf,
         }
         d3 n = normalize(s);
         double L[64], A[64][3];
-        int nk = 0;
+        view_opt vo[64];
+        int nk = 0, nvo = 0;
         uint8_t fl = 0;
         for (int k = 0; k < K && k < 64; ++k) {
             cam_t c = load_cam(cams + 16 * k);
@@ -2139,53 +2243,73 @@ int or_backproject(const float *lv, int64_t nlv, const int32_t *lf, int64_t nlf,
             if (!(q.z > 0.0)) continue;
             double u = c.fx * q.x / q.z + c.cx, v = c.fy * q.y / q.z + c.cy;
             double fu = u - floor(u), fv = v - floor(v);
-            if (fu < 1e-3 || fu > 1.0 - 1e-3 || fv < 1e-3 || fv > 1.0 - 1e-3) fl = 1;
-            if (!(u >= 0.0 && u < iw && v >= 0.0 && v < ih)) continue;
-            int i = (int)floor(u), j = (int)floor(v);
-            const double *dk = depth + (int64_t)k * npix;
-            const double *pk = point + (int64_t)k * npix * 3;
-            const uint8_t *nk_ = near + (int64_t)k * npix;
-            int64_t px = (int64_t)j * iw + i;
-            if (nk_[px]) fl = 1;
-            {
-                const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
-                for (int nn = 0; nn < 4; ++nn) {
-                    int ii = i + di[nn], jj = j + dj[nn];
-                    if (ii >= 0 && jj >= 0 && ii < iw && jj < ih && nk_[(int64_t)jj * iw + ii]) fl = 1;
+            /* ak: whether this view counts depends on rounding */
+            int ak = fu < 1e-3 || fu > 1.0 - 1e-3 || fv < 1e-3 || fv > 1.0 - 1e-3;
+            int counted = 1;
+            if (!(u >= 0.0 && u < iw && v >= 0.0 && v < ih)) {
+                counted = 0;
+            } else {
+                int i = (int)floor(u), j = (int)floor(v);
+                const double *dk = depth + (int64_t)k * npix;
+                const double *pk = point + (int64_t)k * npix * 3;
+                const uint8_t *nk_ = near + (int64_t)k * npix;
+                int64_t px = (int64_t)j * iw + i;
+                if (nk_[px]) ak = 1;
+                {
+                    const int di[4] = {1, -1, 0, 0}, dj[4] = {0, 0, 1, -1};
+                    for (int nn = 0; nn < 4; ++nn) {
+                        int ii = i + di[nn], jj = j + dj[nn];
+                        if (ii >= 0 && jj >= 0 && ii < iw && jj < ih && nk_[(int64_t)jj * iw + ii]) ak = 1;
+                    }
+                }
+                if (!(dk[px] < INFINITY)) {
+                    counted = 0;
+                } else {
+                    int amb = 0;
+                    int edge = is_edge(dk, pk, iw, ih, i, j, edge_tol, 1e-5 * scale, &amb);
+                    if (amb) ak = 1;
+                    if (edge) {
+                        counted = 0;
+                    } else {
+                        if (fabs(q.z - (dk[px] + depth_tol)) < 1e-5 * scale) ak = 1;
+                        if (q.z > dk[px] + depth_tol) counted = 0;
+                    }
                 }
             }
-            if (!(dk[px] < INFINITY)) continue;
-            int amb = 0;
-            int edge = is_edge(dk, pk, iw, ih, i, j, edge_tol, 1e-5 * scale, &amb);
-            if (amb) fl = 1;
-            if (edge) continue;
-            if (fabs(q.z - (dk[px] + depth_tol)) < 1e-5 * scale) fl = 1;
-            if (q.z > dk[px] + depth_tol) continue;
+            if (ak) fl = 1;
+            if (!counted && !ak) continue;
             d3 C = cam_centre(&c);
             double I = dot(n, normalize(sub(C, p)));
             if (!(I > 0.0)) continue;
-            if (incid) incid[(int64_t)k * W * H + tex] = I;
-            L[nk] = log((double)weights[k]) + alpha * log(I);
+            double Lk = log((double)weights[k]) + alpha * log(I);
+            double col[3], alt[3];
+            int ncol = 1;
             if (filter)
                 aniso_color(lv, lf, luv, W, H, f, p, &c, images + (int64_t)k * npix * 4, &mips[k], u, v, lod_bias,
-                            max_taps, A[nk], &fl);
+                            max_taps, col, alt, &ncol, &fl);
             else
                 for (int ch = 0; ch < 3; ++ch)
-                    A[nk][ch] = bilinear(images + (int64_t)k * npix * 4, iw, ih, ch, u - 0.5, v - 0.5);
+                    col[ch] = bilinear(images + (int64_t)k * npix * 4, iw, ih, ch, u - 0.5, v - 0.5);
+            vo[nvo].absent_ok = ak || !counted;
+            vo[nvo].ncol = ncol > 0 ? ncol : 1;
+            vo[nvo].L = Lk;
+            for (int ch = 0; ch < 3; ++ch) { vo[nvo].A[0][ch] = col[ch]; vo[nvo].A[1][ch] = ncol == 2 ? alt[ch] : col[ch]; }
+            if (ncol == 0) vo[nvo].ncol = 99;   /* not enumerable */
+            ++nvo;
+            if (!counted) continue;
+            if (incid) incid[(int64_t)k * W * H + tex] = I;
+            L[nk] = log((double)weights[k]) + alpha * log(I);
+            for (int ch = 0; ch < 3; ++ch) A[nk][ch] = col[ch];
             ++nk;
         }
         flags[tex] = fl;
-        if (nk == 0) continue;
-        double m = L[0];
-        for (int k = 1; k < nk; ++k) if (L[k] > m) m = L[k];
-        double num[3] = {0, 0, 0}, den = 0.0;
-        for (int k = 0; k < nk; ++k) {
-            double e = exp(L[k] - m);
-            den += e;
-            for (int ch = 0; ch < 3; ++ch) num[ch] += e * A[k][ch];
+        if (fl && var_tex && *n_var < max_var) {
+            int64_t j = (*n_var)++;
+            var_tex[j] = tex;
+            var_n[j] = (uint8_t)enumerate_variants(nvo, vo, eps, var_rgbf + (int64_t)j * OR_MAX_VARIANTS * 4);
         }
-        den += eps * exp(-m);
-        for (int ch = 0; ch < 3; ++ch) texture[3 * tex + ch] = num[ch] / den;
+        if (nk == 0) continue;
+        blend_views(nk, L, A, eps, texture + 3 * tex);
         filled[tex] = 1;
     }
     if (mips) {

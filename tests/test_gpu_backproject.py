@@ -5,7 +5,10 @@ The generated views are stand-ins made from the oracle's own renders (a smooth
 colour field at each pixel's surface point), so no input comes from the CUDA
 path.  The kernel renders its own depth buffers and edge masks.  Where the
 oracle flags a texel (a pixel boundary, the depth limit, an edge decision or a
-silhouette within rounding of the decision), the texel is not compared."""
+silhouette within rounding of the decision, or an anisotropic tap count or
+fallback at its threshold), the oracle lists every correct result (each
+rounding-dependent view counted or not, each threshold taken either way) and
+the kernel's texel must be one of them."""
 import numpy as np
 import pytest
 import torch
@@ -27,7 +30,7 @@ def run_both(lv, lf, uv, W, H, cams, weights, w, h, *, alpha, eps, depth_tol, ed
     depth_o, point_o, near_o = oracle.render_views(lv, lf, cams, w, h)
     images = synth.view_images(point_o)
     o = oracle.backproject(lv, lf, uv, W, H, cams, images, weights, alpha=alpha, eps=eps, depth_tol=depth_tol,
-                           edge_tol=edge_tol, views=(depth_o, point_o, near_o))
+                           edge_tol=edge_tol, views=(depth_o, point_o, near_o), variants=True)
     bvh = pb.Bvh(_t(lv), _t(lf))
     depth, pts, edge = pb.render_views(bvh, cams, w, h, edge_tol=edge_tol)
     tex, inc = pb.backproject(_t(lv), _t(lf), _t(uv), W, H, cams, weights, _t(images), depth, edge, alpha=alpha,
@@ -49,19 +52,43 @@ def check_render(g, o, scale):
     assert np.abs(g["points"][both] - o["point"][both]).max() <= 1e-5 * scale
 
 
-def check_texture(g, o):
+def check_texture(g, o, sample=None):
+    """Texels the oracle does not flag by value; flagged ones against the
+    oracle's list of correct results.  Returns the fraction of compared
+    texels checked either way (texels whose list was too long to write are
+    the rest, at most 1 %)."""
     ray = o["face"] >= 0
-    ok = ray & (o["flags"] == 0)
+    if sample is not None:
+        sel = np.zeros(ray.size, bool)
+        sel[np.asarray(sample)] = True
+        sel = sel.reshape(ray.shape) & ray
+    else:
+        sel = ray
+    ok = sel & (o["flags"] == 0)
     filled_g = g["texture"][..., 3] > 0.5
     assert np.array_equal(filled_g[ok], o["filled"][ok].astype(bool))
     both = ok & filled_g
     err = np.abs(g["texture"][..., :3][both] - o["texture"][both])
     assert err.max() <= TOL_TEX, err.max()
-    inc = np.abs(g["incidence"][:, ok] - o["incidence"][:, ok])
-    assert inc.max() <= 1e-5
+    if "incidence" in g:
+        inc = np.abs(g["incidence"][:, ok] - o["incidence"][:, ok])
+        assert inc.max() <= 1e-5
     # outside the ray texels nothing is written
-    assert not g["texture"][~ray].any()
-    return float(ok.sum() / ray.sum())
+    if sample is None:
+        assert not g["texture"][~ray].any()
+    gt = g["texture"].reshape(-1, 4)
+    n_set = n_unlisted = 0
+    for tex in np.flatnonzero((sel & (o["flags"] != 0)).reshape(-1)):
+        var = o["variants"][int(tex)]
+        if len(var) == 0:
+            n_unlisted += 1
+            continue
+        fill = 1.0 if gt[tex, 3] > 0.5 else 0.0
+        d = np.abs(var[:, :3] - gt[tex, :3]).max(1)
+        assert ((var[:, 3] == fill) & (d <= TOL_TEX)).any(), (int(tex), gt[tex], var)
+        n_set += 1
+    assert n_unlisted <= 0.01 * sel.sum(), n_unlisted
+    return float((ok.sum() + n_set) / sel.sum())
 
 
 @pytest.mark.parametrize("seed", [0, 1])
@@ -76,7 +103,7 @@ def test_paper_views_tiny_asset(seed):
                     edge_tol=0.05 * scale)
     check_render(g, o, scale)
     frac = check_texture(g, o)
-    assert frac > 0.85
+    assert frac > 0.99
     assert o["filled"][o["face"] >= 0].mean() > 0.6
 
 
@@ -94,9 +121,9 @@ def test_sdf_asset_large_alpha_and_ragged_sizes():
                     depth_tol=0.01 * scale, edge_tol=0.03 * scale)
     check_render(g, o, scale)
     # a pixel whose render depends on rounding flags every texel that lands on
-    # it or beside it in any view; on this marching-grid mesh (slivers whose
-    # texel cells are as large as any other face's) that is about a fifth
-    assert check_texture(g, o) > 0.7
+    # it or beside it in any view (on this marching-grid mesh about a fifth);
+    # those are checked against the oracle's list of correct results
+    assert check_texture(g, o) > 0.99
 
 
 def test_render_modes_against_oracle():
@@ -151,13 +178,13 @@ def test_backproject_on_oracle_views(alpha, eps, filt):
     images = synth.view_images(point_o)
     o = oracle.backproject(lv, lf, a.low_uv, a.W, a.H, cams, images, weights, alpha=alpha, eps=eps,
                            depth_tol=0.01 * scale, edge_tol=edge_tol, views=(depth_o, point_o, np.zeros_like(near_o)),
-                           filter=filt)
+                           filter=filt, variants=True)
     tex, inc = pb.backproject(_t(lv), _t(lf), _t(a.low_uv), a.W, a.H, cams, weights, _t(images),
                               _t(depth_o.astype(np.float32)), _t(edge_o), alpha=alpha, eps=eps,
                               depth_tol=0.01 * scale, incidence=True, filter=filt)
     pb.sync_status()
     g = dict(texture=tex.cpu().numpy(), incidence=inc.cpu().numpy())
-    assert check_texture(g, o) > 0.93
+    assert check_texture(g, o) > 0.99
     assert o["filled"][o["face"] >= 0].mean() > 0.8
 
 
@@ -261,7 +288,7 @@ def test_aniso_footprints(case):
     edge_o = oracle.edge_mask(depth_o, point_o, 10.0)
     kw = dict(alpha=1.0, eps=0.0, depth_tol=0.05)
     o = oracle.backproject(V, F, uv, W, W, cam[None], img, np.ones(1, np.float32), edge_tol=10.0,
-                           views=(depth_o, point_o, near_o), **kw)
+                           views=(depth_o, point_o, near_o), variants=True, **kw)
     tex = pb.backproject(_t(V), _t(F), _t(uv), W, W, cam[None], np.ones(1, np.float32), _t(img),
                          _t(depth_o.astype(np.float32)), _t(edge_o), **kw)
     pb.sync_status()
@@ -271,6 +298,44 @@ def test_aniso_footprints(case):
     assert np.array_equal(g[..., 3][ok] > 0.5, np.ones(ok.sum(), bool))
     err = np.abs(g[..., :3][ok] - o["texture"][ok])
     assert err.max() <= TOL_TEX, err.max()
+    assert check_texture(dict(texture=g), o) > 0.99
+
+
+def test_bench_configuration_sampled():
+    """The benchmark's backprojection workload: the paper's ten views at
+    1024^2 of the headline asset's ~31.7k-face low mesh onto its 2048^2 grid
+    atlas, alpha = 6, the bench's depth and edge tolerances.  The kernel
+    renders its views and blends; 20k seeded ray texels are compared with the
+    oracle (its own renders, its own colour images for both sides)."""
+    import paper_2605_26137_b300 as pb
+    a = synth.sdf_asset(1, 2_000_000, 30_000, 2048, 2048, n_prims=32, device="cuda")
+    lv, lf = a.low_v, a.low_f
+    V = lv.astype(np.float64)
+    c = (V.max(0) + V.min(0)) / 2
+    r = float(np.linalg.norm(V.max(0) - V.min(0)) / 2)
+    w = h = 1024
+    cams, weights, _ = synth.paper_cameras(c, r, w, h)
+    diam = 2 * r
+    edge_tol, depth_tol = 0.01 * diam, 0.005 * diam
+    depth_o, point_o, near_o = oracle.render_views(lv, lf, cams, w, h)
+    images = synth.view_images(point_o)
+    face, _, _ = oracle.raster(a.low_uv, a.W, a.H)
+    rays = np.flatnonzero(face.reshape(-1) >= 0)
+    sample = np.sort(np.random.default_rng(4).choice(rays, 20000, replace=False))
+    o = oracle.backproject(lv, lf, a.low_uv, a.W, a.H, cams, images, weights, alpha=6.0, eps=1e-6,
+                           depth_tol=depth_tol, edge_tol=edge_tol, views=(depth_o, point_o, near_o), sample=sample,
+                           variants=True)
+    bvh = pb.Bvh(_t(lv), _t(lf))
+    depth, pts, edge = pb.render_views(bvh, cams, w, h, edge_tol=edge_tol)
+    tex = pb.backproject(_t(lv), _t(lf), _t(a.low_uv), a.W, a.H, cams, weights, _t(images), depth, edge, alpha=6.0,
+                         eps=1e-6, depth_tol=depth_tol)
+    pb.sync_status()
+    bvh.free()
+    check_render(dict(depth=depth.cpu().numpy(), points=pts.cpu().numpy()),
+                 dict(depth=depth_o, point=point_o, near=near_o), diam)
+    frac = check_texture(dict(texture=tex.cpu().numpy()), o, sample=sample)
+    print("compared by value or set:", frac, "flagged:", float((o["flags"].reshape(-1)[sample] != 0).mean()))
+    assert frac > 0.99
 
 
 def test_aniso_jittered_atlas_and_degenerate_uv():
@@ -298,14 +363,14 @@ def test_aniso_jittered_atlas_and_degenerate_uv():
     images = synth.view_images(point_o)
     kw = dict(alpha=6.0, eps=1e-6, depth_tol=0.02 * 2 * r)
     o = oracle.backproject(lv, lf, uv, W, H, cams, images, weights, edge_tol=0.05 * 2 * r,
-                           views=(depth_o, point_o, np.zeros_like(near_o)), **kw)
+                           views=(depth_o, point_o, np.zeros_like(near_o)), variants=True, **kw)
     tex = pb.backproject(_t(lv), _t(lf), _t(uv), W, H, cams, weights, _t(images), _t(depth_o.astype(np.float32)),
                          _t(edge_o), **kw)
     pb.sync_status()
     g = dict(texture=tex.cpu().numpy(), incidence=np.zeros((len(cams), H, W), np.float32))
     o2 = dict(o)
     o2["incidence"] = np.zeros_like(g["incidence"])
-    assert check_texture(g, o2) > 0.9
+    assert check_texture(g, o2) > 0.99
     # the centre-sample fallback was compared on filled texels of the shrunk faces
     on_tiny = np.isin(o["face"], tiny) & (o["flags"] == 0) & o["filled"].astype(bool)
     assert on_tiny.sum() >= 5

@@ -348,3 +348,70 @@ def test_aniso_level_of_detail_trilinear():
     ok = o["filled"][m].astype(bool) & (o["flags"][m] == 0) & inside
     assert ok.sum() > 50
     assert np.abs(o["texture"][m][ok] - expect[ok]).max() < 1e-6
+
+
+def test_variants_list_the_results_of_every_rounding_choice():
+    """The set of correct results of a flagged texel (the set-valued check of
+    the GPU parity tests).  Two constant-colour views (red, blue) of a plane
+    with eps = 0: a blend of both is the closed form, of one view alone that
+    view's colour exactly, of none an unfilled texel.  A texel whose
+    projection lies within 1e-3 pixel of a pixel boundary in one view only
+    has exactly two correct results, with that view and without it; in both
+    views, four.  The texel's own result is always one of them."""
+    V, F = _plane(8, size=1.5)
+    w = h = 48
+    cams = []
+    for ang in (10.0, 50.0):
+        a = math.radians(ang)
+        cams.append(synth.look_at_camera([4 * math.sin(a), 0.0, 4 * math.cos(a)], [0, 0, 0], [0, 1, 0], 30.0, w, h))
+    cams = np.stack(cams)
+    img = np.zeros((2, h, w, 4), np.uint8)
+    img[0, ..., 0] = 255
+    img[1, ..., 2] = 255
+    img[..., 3] = 255
+    wts = np.array([0.3, 1.0], np.float32)
+    W = H = 512
+    uv = synth.grid_atlas(len(F), W, H, 2)
+    for filt in ("bilinear", "aniso"):
+        o = oracle.backproject(V, F, uv, W, H, cams, img, wts, alpha=6.0, eps=0.0, depth_tol=0.1, edge_tol=10.0,
+                               filter=filt, variants=True)
+        m, p = _texel_points(o, V, F)
+        inner = np.abs(p[:, :2]).max(1) < 0.5                      # inside both frusta, away from the rims
+        ids = np.flatnonzero(m.reshape(-1))
+        # each view's pixel coordinates of the texel point, in FP64 from the FP32 cameras
+        near_bd = []
+        for k in range(2):
+            c = cams[k].astype(np.float64)
+            R, t, (fx, fy, cx, cy) = c[:9].reshape(3, 3), c[9:12], c[12:16]
+            q = p @ R.T + t
+            u, v = fx * q[:, 0] / q[:, 2] + cx, fy * q[:, 1] / q[:, 2] + cy
+            fr = np.minimum(np.abs(u - np.round(u)), np.abs(v - np.round(v)))
+            near_bd.append(fr < 1e-3)
+        near_bd = np.stack(near_bd)
+        C = [cams[k][:9].astype(np.float64).reshape(3, 3).T @ -cams[k][9:12].astype(np.float64) for k in range(2)]
+        cos = np.stack([(c[None] - p)[:, 2] / np.linalg.norm(c[None] - p, axis=1) for c in C])
+        L = np.log(wts.astype(np.float64))[:, None] + 6.0 * np.log(cos)
+        e = np.exp(L - L.max(0))
+        both = np.stack([e[0] / e.sum(0), np.zeros(len(p)), e[1] / e.sum(0)], -1)
+        one = [np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0])]
+        n_single = n_double = 0
+        for r, tex in enumerate(ids):
+            if not inner[r]:
+                continue
+            fl = o["flags"].reshape(-1)[tex]
+            assert fl == bool(near_bd[:, r].any()), (filt, tex)
+            if not fl:
+                continue
+            var = o["variants"][int(tex)]
+            own = np.concatenate([o["texture"].reshape(-1, 3)[tex], [o["filled"].reshape(-1)[tex]]])
+            assert np.abs(var - own).max(1).min() < 1e-12
+            def has(x, filled=1.0):
+                return np.abs(var - np.concatenate([x, [filled]])).max(1).min() < 1e-9
+            if near_bd[:, r].sum() == 1:
+                k = int(np.flatnonzero(near_bd[:, r])[0])
+                assert len(var) == 2 and has(both[r]) and has(one[1 - k])
+                n_single += 1
+            else:
+                assert len(var) == 4 and has(both[r]) and has(one[0]) and has(one[1]) and has(np.zeros(3), 0.0)
+                n_double += 1
+        assert n_single > 50, (filt, n_single)

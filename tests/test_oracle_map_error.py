@@ -129,3 +129,26 @@ def test_bvh_equals_brute_force():
                                      a.max_dist, use_bvh=False)
     assert np.array_equal(g1, g2) and np.array_equal(f1, f2)
     assert (g1 >= 0).mean() > 0.9
+
+
+def test_degenerate_uv_face_uses_the_low_normal():
+    """A face whose UVs are degenerate (the UV-reliability filter) does not
+    read the map: its samples give the angle between the low normal and the
+    raw normal (the tilt), while the other face's samples read the
+    non-neutral map value."""
+    s = 0.25
+    hv, hf = _plane(8, -1.5, 1.5, -1.5, 1.5, 0.05, s)
+    W = H = 64
+    uv = _quad_uv()
+    uv[1] = uv[1][0]                                   # face 1: all three corners at one UV point
+    rgba = np.zeros((H, W, 4), np.uint8)
+    rgba[...] = (128, 128 + 40, 128 + 119, 255)        # tilted away from +z in tangent space
+    sf, sb = synth.surface_samples(QUAD_V, QUAD_F, 2000, 3)
+    ang, _ = oracle.normal_map_error(hv, hf, QUAD_V, QUAD_F, uv, W, H, rgba, sf, sb, 1.0)
+    tilt = np.degrees(np.arctan(s))
+    assert np.abs(ang[sf == 1] - tilt).max() < 1e-4
+    c = np.array([0.0, 40.0, 119.0]) / 127
+    c /= np.linalg.norm(c)
+    raw = np.array([0.0, s, 1.0]) / np.sqrt(1 + s * s)
+    exp = np.degrees(np.arccos(c @ raw))
+    assert np.abs(ang[sf == 0] - exp).max() < 1e-4

@@ -22,7 +22,8 @@ MUTANTS = {
         ("m = add(m, scl(ldd(j->hn, j->hf[3 * tri + k]), b[k]));",
          "m = add(m, scl(ldd(j->hn, j->hf[3 * tri + k]), b[(k + 1) % 3]));"),
     "bitangent handedness dropped":
-        ("d3 B = scl(cross(N, Tt), j->wsign[f]);", "d3 B = cross(N, Tt);"),
+        ("        d3 B = scl(cross(N, Tt), j->wsign[f]);\n        d3 nh = hit_normal(j, tri, hb);",
+         "        d3 B = cross(N, Tt);\n        d3 nh = hit_normal(j, tri, hb);"),
     "ray direction not normalised":
         ("    d3 d = normalize(s);\n    double tol = 1e-5 * j->diam;", "    d3 d = s;\n    double tol = 1e-5 * j->diam;"),
     "displacement sign flipped":
@@ -32,7 +33,8 @@ MUTANTS = {
     "dilated normal not renormalised":
         ("std3(nts, i, norm(mm) > 0 ? normalize(mm) : mk(0, 0, 1));", "std3(nts, i, mm);"),
     "tangent not made orthogonal to the normal":
-        ("d3 Tt = normalize(sub(ts, scl(N, dot(ts, N))));", "d3 Tt = normalize(ts);"),
+        ("        d3 Tt = normalize(sub(ts, scl(N, dot(ts, N))));\n        d3 B = scl(cross(N, Tt), j->wsign[f]);\n        d3 nh",
+         "        d3 Tt = normalize(ts);\n        d3 B = scl(cross(N, Tt), j->wsign[f]);\n        d3 nh"),
 }
 
 # the next rows' functions, each with the pins of its own row
@@ -62,6 +64,8 @@ ROW_MUTANTS = {
     "baked mean: bitangent handedness dropped":
         ("    d3 B = scl(cross(N, Tt), j->wsign[f]);\n    int x = (int)floor(u * j->W)",
          "    d3 B = cross(N, Tt);\n    int x = (int)floor(u * j->W)", ["tests/test_oracle_map_error.py"]),
+    "backprojection: a counted view within rounding of its decision never left out":
+        ("vo[nvo].absent_ok = ak || !counted;", "vo[nvo].absent_ok = !counted;", ["tests/test_oracle_backproject.py"]),
     "backprojection incidence exponent dropped":
         ("L[nk] = log((double)weights[k]) + alpha * log(I);", "L[nk] = log((double)weights[k]) + log(I);",
          ["tests/test_oracle_backproject.py"]),
