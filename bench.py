@@ -84,6 +84,10 @@ def parse():
     p.add_argument("--hidden-faces", type=int, default=22000, help="hidden-face removal: mesh faces")
     p.add_argument("--qem-faces", type=int, default=1_000_000, help="QEM simplification: input faces")
     p.add_argument("--bp-res", type=int, default=1024, help="backprojection: view resolution (ten views)")
+    p.add_argument("--c2-faces", type=int, default=8_000_000,
+                   help="precision study: high-mesh triangles (0 = skip the leg)")
+    p.add_argument("--c2-res", type=int, default=4096, help="precision study: atlas size")
+    p.add_argument("--c2-sample", type=float, default=0.01, help="precision study: fraction of ray texels checked")
     return p.parse_args()
 
 
@@ -313,11 +317,21 @@ def to_dev(a, torch):
 
 
 def bytes_per_ray(node_size, nodes_per_ray, tris_per_ray, hit_frac):
-    """Algorithmic bytes one ray requests from memory in the trace kernel:
+    """Algorithmic bytes of one ray, counted from what the method itself
+    reads and writes: node_size per node visit (80 for an 8-bit node), 48 per
+    triangle test, the raster record 12 (face id + two barycentrics), the
+    three corners' position, normal and tangent 3 x 28, on a hit the hit
+    triangle's three smooth normals 3 x 12, and the outputs 7 (RGBA8 4, fp16
+    displacement 2, mask 1)."""
+    return node_size * nodes_per_ray + 48 * tris_per_ray + 12 + 3 * 28 + hit_frac * 3 * 12 + 7
+
+
+def layout_bytes_per_ray(node_size, nodes_per_ray, tris_per_ray, hit_frac):
+    """Bytes the trace kernel requests in its own layout, padding included:
     ray record 16, low face 16, 3 low positions + 3 low normals + 3 corner
     tangents 144 (float4 each), node_size per node visit, 48 per triangle
-    test, on a hit the hit record 48 + 3 smooth normals 48, outputs 17
-    (float4 normal/displacement + mask byte)."""
+    test, on a hit the hit record 48 + 3 smooth normals 48, and the 17-byte
+    intermediate (float4 normal/displacement + mask byte)."""
     return 16 + 16 + 144 + node_size * nodes_per_ray + 48 * tris_per_ray + hit_frac * (48 + 48) + 17
 
 
@@ -394,9 +408,17 @@ def cpu_baseline(a, seconds):
         passes += 1
         if spent >= 0.8 * seconds or n < len(rays) or passes >= 50:
             break
+    # the same oracle on one thread, over a smaller sample (about a third of the time)
+    n1 = int(min(len(rays), max(1000, (seconds / 3 - fixed) / (per_ray * cores))))
+    samp1 = rng.choice(rays, size=n1, replace=False)
+    t0 = time.perf_counter()
+    oracle.bake_asset(a, sample=samp1, bvh=bvh, nthreads=1)
+    s1 = time.perf_counter() - t0
     return {"value": done / spent / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{passes} x {len(samp)} ray texels of the {len(rays)} ({spent:.1f} s; FP64 oracle: raster, "
-                      f"frames, median-split BVH traversal, shading; all host cores; oracle BVH build untimed)"}
+                      f"frames, median-split BVH traversal, shading; all host cores; oracle BVH build untimed)",
+            "single_thread": {"value": n1 / s1 / 1e6, "unit": UNIT, "cores": 1,
+                              "sample": f"{n1} random ray texels ({s1:.1f} s; same oracle, one thread)"}}
 
 
 # --------------------------------------------------------------------------- our arm
@@ -461,6 +483,7 @@ def main():
     n_rays = int(cnt.n_rays.item())
     nodes_pr, tris_pr, hit_frac = c[1] / c[0], c[2] / c[0], c[3] / c[0]
     bpr = bytes_per_ray(info["node_size"], nodes_pr, tris_pr, hit_frac)
+    bpl = layout_bytes_per_ray(info["node_size"], nodes_pr, tris_pr, hit_frac)
 
     out = pb.alloc_outputs(W, H, dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
@@ -490,6 +513,7 @@ def main():
     trace_avg = statistics.mean(trace_ms)
     hbm, peak_kind = peaks()
     achieved = bpr * n_rays / (trace_avg * 1e-3) / 1e9
+    achieved_layout = bpl * n_rays / (trace_avg * 1e-3) / 1e9
     clocks = clk.summary(wall0, wall1)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -510,10 +534,14 @@ def main():
             "bvh": {"build_ms": statistics.median(build_ms[1:]), "build_wall_ms": build_wall_ms,
                     "build_first_ms": build_ms[0], "collapse": args.collapse, "nodes": info["n_nodes"],
                     "node_bytes": info["node_bytes"], "tri_bytes": info["tri_bytes"], "depth": info["max_depth"]},
-            "per_ray": {"nodes": nodes_pr, "tris": tris_pr, "hit_frac": hit_frac, "bytes": bpr},
+            "per_ray": {"nodes": nodes_pr, "tris": tris_pr, "hit_frac": hit_frac, "bytes": bpr,
+                        "bytes_layout": bpl},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": recorded_traffic("q8", W, int(len(a.high_f))),
-                         "kernel": "k_trace_fwd_q8 (closest-hit traversal + shading)", "peak_kind": peak_kind},
+                         "kernel": "k_trace_fwd_q8 (closest-hit traversal + shading)", "peak_kind": peak_kind,
+                         "bytes_per_ray": bpr, "rays_per_launch": n_rays,
+                         "layout": {"bytes_per_ray": bpl, "achieved": achieved_layout,
+                                    "frac": achieved_layout / hbm}},
             "clocks": clocks,
             "gpu_launches": 7 * args.steps}
 
@@ -614,6 +642,8 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     n_rays = int(cnt.n_rays.item())
     res["layout_f32"] = {"ms_per_bake": statistics.mean(f32), "mrays_s": n_rays / statistics.mean(f32) / 1e3,
                          "bytes_per_ray": bytes_per_ray(bf.info()["node_size"], c[1] / c[0], c[2] / c[0], c[3] / c[0]),
+                         "bytes_per_ray_layout": layout_bytes_per_ray(bf.info()["node_size"], c[1] / c[0], c[2] / c[0],
+                                                                      c[3] / c[0]),
                          "node_bytes": bf.info()["node_bytes"], "nodes_per_ray": c[1] / c[0],
                          "error_vs_oracle": layout_errors(pb, torch, a, bf, lv, lf, uv, W, H, args.error_sample)}
     res["layout_q8_error_vs_oracle"] = layout_errors(pb, torch, a, bvh, lv, lf, uv, W, H, args.error_sample)
@@ -624,6 +654,68 @@ def extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, fwd_ms
     res["backprojection"] = backproject_leg(args, pb, torch, a, lv, lf, uv, W, H, dev, flush)
     if args.batch_assets > 0:
         res["batch"] = batch_leg(args, pb, torch, dev, flush)
+    if args.c2_faces > 0:
+        res["precision_study"] = c2_leg(args, pb, torch, dev, flush)
+    return res
+
+
+def c2_leg(args, pb, torch, dev, flush):
+    """The precision study: the headline generator at ~8M high-poly
+    triangles and a 4096^2 atlas, baked over 8-bit quantised and over FP32
+    BVH nodes.  Per layout: ms per bake, Mrays/s, algorithmic bytes per ray
+    and the node and triangle counts behind them, and the error of the
+    tangent-space normals against the FP64 oracle on one seeded sample of
+    the ray texels (c2_sample of them; ambiguous-closest texels excluded, as
+    in the parity tests)."""
+    import oracle
+    from paper_2605_26137_b300 import synth
+    t0 = time.perf_counter()
+    a = synth.sdf_asset(args.seed, args.c2_faces, args.low_faces, args.c2_res, args.c2_res, n_prims=32, device=dev)
+    gen_s = time.perf_counter() - t0
+    hv, hf, lv, lf, uv = to_dev(a, torch)
+    W = H = args.c2_res
+    out = pb.alloc_outputs(W, H, dev)
+    res = {"workload": f"SDF union of 32 primitives, {len(a.high_f)}-tri high mesh, {len(a.low_f)}-tri low mesh, "
+                       f"{W}x{H} grid atlas", "high_tris": int(len(a.high_f)), "low_tris": int(len(a.low_f)),
+           "atlas": W, "fixture_s": gen_s, "layouts": {}}
+    steps = max(3, args.steps // 2)
+    maps = {}
+    for layout in ("q8", "f32"):
+        bvh = pb.Bvh(hv, hf, layout=layout, collapse=args.collapse)
+        cnt = pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, counters=True, aux=True)
+        pb.sync_status()
+        c = cnt.counters.cpu().numpy().astype(np.float64)
+        n = int(cnt.n_rays.item())
+        maps[layout] = (cnt.normal_ts.cpu().numpy().reshape(-1, 3), cnt.mask.cpu().numpy().reshape(-1))
+        ms = timed(torch, lambda: pb.bake(bvh, lv, lf, uv, W, H, a.max_dist, out=out), steps, 2, flush)
+        pb.sync_status()
+        info = bvh.info()
+        res["layouts"][layout] = {
+            "ms_per_bake": statistics.mean(ms), "mrays_s": n / statistics.mean(ms) / 1e3,
+            "bytes_per_ray": bytes_per_ray(info["node_size"], c[1] / c[0], c[2] / c[0], c[3] / c[0]),
+            "nodes_per_ray": c[1] / c[0], "tris_per_ray": c[2] / c[0], "node_size": info["node_size"],
+            "node_bytes": info["node_bytes"], "nodes": info["n_nodes"], "build_ms": info["build_ms"]}
+        res["ray_texels"] = n
+        bvh.free()
+    face = cnt.face.cpu().numpy().reshape(-1)
+    rays = np.flatnonzero(face >= 0)
+    rng = np.random.default_rng(11)
+    samp = np.sort(rng.choice(rays, size=max(1, int(args.c2_sample * len(rays))), replace=False))
+    t0 = time.perf_counter()
+    o = oracle.bake_asset(a, sample=samp)
+    res["oracle_sample"] = {"texels": int(len(samp)), "fraction": args.c2_sample, "s": time.perf_counter() - t0}
+    on = o["nts"].reshape(-1, 3)[samp]
+    om = o["mask"].reshape(-1)[samp]
+    amb = (o["flags"].reshape(-1)[samp] & 8) != 0
+    for layout, (g, gm) in maps.items():
+        ok = (om == gm[samp]) & ~amb
+        err = np.abs(g[samp] - on).max(-1)[ok]
+        res["layouts"][layout]["error_vs_oracle"] = {"max": float(err.max()), "mean": float(err.mean()),
+                                                     "compared": int(ok.sum()),
+                                                     "mask_mismatch": int((om != gm[samp]).sum())}
+    res["q8_over_f32_speed"] = res["layouts"]["f32"]["ms_per_bake"] / res["layouts"]["q8"]["ms_per_bake"]
+    res["identical_maps"] = bool(np.array_equal(maps["q8"][0], maps["f32"][0]) and
+                                 np.array_equal(maps["q8"][1], maps["f32"][1]))
     return res
 
 
@@ -647,7 +739,12 @@ def qem_leg(args, pb, torch, dev):
     optimum and with the midpoint baseline it improves on: time, rounds, and
     the paper's geometric metrics against the input (Chamfer: mean
     point-to-surface distance both ways; Hausdorff: the maximum), on 256k
-    area-sampled points per side, as fractions of the bounding-box diagonal."""
+    area-sampled points per side, as fractions of the bounding-box diagonal;
+    and the "baked mean" (the footnote's measure): the simplified mesh gets
+    the grid atlas at 1024^2 and a normal map baked from the input mesh (the
+    paper's 1 % distance filter), then at 256k area-sampled points of the
+    simplified mesh the angle between the map's normal and the input mesh's
+    smooth normal at its nearest point (ag_normal_map_error), in degrees."""
     from paper_2605_26137_b300 import synth
     V, F = synth.sdf_mesh_target(synth.sdf_union_params(args.seed, 32), args.qem_faces, device=dev)
     v, f = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (V, F))
@@ -671,12 +768,33 @@ def qem_leg(args, pb, torch, dev):
             d_so = pb.point_distance(orig, p_simp, diam)
             pb.sync_status()
             simp.free()
+            baked = baked_mean(pb, torch, orig, vs, fo, diam, args.seed)
             out["runs"].append({"target": target, "placement": placement, "faces": int(fo.shape[0]),
                                 "rounds": rounds, "ms": ms,
                                 "chamfer": float((d_os.mean() + d_so.mean()) / 2 / diam),
-                                "hausdorff": float(torch.maximum(d_os.max(), d_so.max()) / diam)})
+                                "hausdorff": float(torch.maximum(d_os.max(), d_so.max()) / diam),
+                                "baked_mean_deg": baked})
     orig.free()
     return out
+
+
+def baked_mean(pb, torch, raw_bvh, vs, fo, diam, seed, res=1024, n=1 << 18):
+    """The baked-mean measure of one simplified mesh against the raw mesh of
+    raw_bvh (mean, median and max angle in degrees, the bake's time)."""
+    from paper_2605_26137_b300 import synth
+    uv = torch.from_numpy(synth.grid_atlas(int(fo.shape[0]), res, res, 2)).to(vs.device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = pb.bake(raw_bvh, vs, fo, uv, res, res, 0.01 * diam)
+    torch.cuda.synchronize()
+    bake_ms = 1e3 * (time.perf_counter() - t0)
+    sf, sb = synth.surface_samples(vs.cpu().numpy(), fo.cpu().numpy(), n, seed + 7)
+    ang = pb.normal_map_error(raw_bvh, vs, fo, uv, res, res, out.normal_rgba8, torch.from_numpy(sf).to(vs.device),
+                              torch.from_numpy(sb).to(vs.device), 0.1 * diam)
+    pb.sync_status()
+    a = ang[ang >= 0]
+    return {"mean": float(a.mean()), "median": float(a.median()), "max": float(a.max()),
+            "samples": n, "found": float((ang >= 0).float().mean()), "atlas": res, "bake_ms": bake_ms}
 
 
 def hidden_leg(args, pb, torch, dev, flush):
@@ -905,6 +1023,17 @@ def batch_leg(args, pb, torch, dev, flush):
     for x in assets:
         o = pb.bake(x.bvh, x.low_verts, x.low_faces, x.low_uv, x.W, x.H, x.max_dist, aux=True)
         rays += int(o.n_rays.item())
+    # where the one-by-one time goes: each asset's single bake with stage
+    # events (L2 flushed before each), traversal against the rest
+    trace_sum, bake_sum = 0.0, 0.0
+    for x, o in zip(assets, seq_out):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        flush.zero_()
+        pb.bake(x.bvh, x.low_verts, x.low_faces, x.low_uv, x.W, x.H, x.max_dist, out=o, events=ev, **lk)
+        torch.cuda.synchronize()
+        trace_sum += ev[1].elapsed_time(ev[2])
+        bake_sum += ev[0].elapsed_time(ev[3])
+    pb.sync_status()
     plan.free()
     for h in handles:
         h.free()
@@ -913,6 +1042,10 @@ def batch_leg(args, pb, torch, dev, flush):
             "ms_batched": ms_bat, "speedup": ms_seq / ms_bat, "mrays_s_batched": rays / ms_bat / 1e3,
             "mrays_s_sequential": rays / ms_seq / 1e3,
             "ms_sequential_with_readback": ms_seq_rb, "speedup_vs_readback_loop": ms_seq_rb / ms_bat,
+            "attribution": {"sum_single_bake_ms": bake_sum, "sum_single_trace_ms": trace_sum,
+                            "trace_share": trace_sum / bake_sum,
+                            "ceiling_speedup_if_only_traversal_remained": ms_seq / trace_sum,
+                            "batched_over_sum_trace": ms_bat / trace_sum},
             "launch": lk,
             "note": "sequential = 64 ag_bake calls back to back on one stream; batched = one captured plan launch"}
 

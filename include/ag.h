@@ -66,12 +66,23 @@ enum { AG_COLLAPSE_AREA = 0, AG_COLLAPSE_AREA_COUNT = 1, AG_COLLAPSE_COUNT = 2, 
 /* Ray-list tile shapes (texels), see ag_opts.ray_tile. */
 enum { AG_TILE_8x8 = 0, AG_TILE_16x16 = 1, AG_TILE_32x8 = 2, AG_TILE_4x4 = 3 };
 
-/* Traversal schedules (one ray per thread in both):
- *  AG_SCHED_BATCH  - a warp takes 32 consecutive rays and finishes all of them
- *                    before taking more;
- *  AG_SCHED_REFILL - lanes take new rays as they finish (in groups of at
- *                    least 8 idle lanes), shading deferred to the refill. */
-enum { AG_SCHED_AUTO = -1, AG_SCHED_BATCH = 0, AG_SCHED_REFILL = 1 };
+/* Traversal schedules:
+ *  AG_SCHED_BATCH  - one ray per thread: a warp takes 32 consecutive rays and
+ *                    finishes all of them before taking more;
+ *  AG_SCHED_REFILL - one ray per thread: lanes take new rays as they finish
+ *                    (in groups of at least 8 idle lanes), shading deferred
+ *                    to the refill;
+ *  AG_SCHED_COOP2, AG_SCHED_COOP4, AG_SCHED_COOP8 - warp-cooperative: 2, 4
+ *                    or 8 lanes share one ray (16, 8 or 4 rays per warp)
+ *                    and split each node's eight children among them; hit
+ *                    leaves are tested at once by the lanes that own them;
+ *                    128-thread blocks (block_size is ignored).  These apply to the forward
+ *                    ray bake over 8-bit nodes (AG_BVH_Q8); other launches
+ *                    (FP32 nodes, the backward pass, the closest-point
+ *                    query) run AG_SCHED_BATCH in their place.
+ * Every schedule produces the same bytes; only the speed differs. */
+enum { AG_SCHED_AUTO = -1, AG_SCHED_BATCH = 0, AG_SCHED_REFILL = 1, AG_SCHED_COOP4 = 2, AG_SCHED_COOP8 = 3,
+       AG_SCHED_COOP2 = 4 };
 
 /* Correspondence queries (ag_opts.query):
  *  AG_QUERY_RAY     - the line from the texel's surface point p along its
@@ -134,7 +145,11 @@ typedef struct {
     int32_t filter;      /* ag_backproject: AG_FILTER_ANISO (0, default) or AG_FILTER_BILINEAR */
     int32_t build_async; /* ag_bvh_build: 0 (default) waits for the build; 1 returns once it is
                             enqueued (see ag_bvh_build) */
-    int32_t reserved[3];
+    int32_t stack_limit; /* test hook, ag_bake with aux counters only (the counting build): use at
+                            most this many traversal stack entries per ray (0 = all of them), so
+                            that an overflow, reported as AG_ERR_TRAVERSAL_LIMIT, can be provoked
+                            on purpose; the other builds ignore it */
+    int32_t reserved[2];
 } ag_opts;
 
 /* Optional extra outputs of ag_bake (any member may be NULL). */
@@ -317,10 +332,10 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
  * are rejected with AG_ERR_INVALID_ARG (use ag_bvh_build instead).
  * Scratch: one static device array of about 4.2 MB inside this library,
  * present on every device that loads the library until the process exits.
- * No cudaMalloc, cudaFree or pool allocation is made.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), which
- * may initialise the library's device code; make that first call before
- * capturing a stream into a CUDA graph.  All calls share the one array and
+ * No cudaMalloc, cudaFree or pool allocation is made.  Every call looks up
+ * that array's device address on the current device (cudaGetSymbolAddress);
+ * the first call on a device may initialise the library's device code there,
+ * so make that first call before capturing a stream into a CUDA graph.  All calls share the one array and
  * each call clears the parts that must start at zero, so calls that overlap
  * on the GPU (other streams or other host threads) race and must be
  * serialised by the caller.  Ordered on `stream`; does not synchronise.
@@ -438,6 +453,41 @@ AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_verts, const in
                                  ag_stream_t stream,
                                  double *d_verts_out, int32_t *d_faces_out, int32_t *d_keep_verts,
                                  int64_t *h_result);
+
+/*
+ * ag_normal_map_error - the "baked mean" quality measure of Sec. 6.1 (the
+ *   simplification benchmark's baked-normal error, a footnote there: points
+ *   spread uniformly over the simplified mesh, the angle between the baked
+ *   normal and the raw mesh's true normal, averaged).  Per sample point of
+ *   the low mesh, the angle in degrees between
+ *   - the normal the RGBA8 map gives there: the texel holding the point's UV
+ *     (x = floor(u W), y = floor(v H), clamped), RGB codes decoded as
+ *     (q - 128) / 127 and renormalised, taken to world space through the
+ *     bake's tangent frame at the point (N the interpolated area-weighted
+ *     vertex normal, T the interpolated corner tangent made orthogonal to N,
+ *     B = w (N x T)); on a face whose UVs are degenerate (the bake's
+ *     UV-reliability filter) the map is not used and the normal is N, and
+ *   - the smooth normal of the handle's mesh (the raw mesh) at its surface
+ *     point nearest to the sample (the AG_QUERY_CLOSEST search, radius
+ *     max_dist),
+ *   as atan2(|a x b|, a . b).
+ *   h: BVH of the raw mesh.  Low mesh, d_luv, W, H: as in ag_bake.
+ *   d_normal_rgba8 [H*W*4] (device, 4-byte aligned): a map baked for this
+ *   low mesh and atlas (any map: it is only read).
+ *   d_sample_face [n] i32, d_sample_bary [n*2] f32 (device): each sample's
+ *   low face and its barycentrics (b1, b2) of corners 1 and 2; the caller
+ *   draws them (uniform by area for the paper's measure).
+ *   d_angle_deg [n] f32 (device, out): the angle, or -1 where no raw point
+ *   lies within max_dist, or the sample's face was dropped (bad UVs); a face
+ *   id out of range gives -1 and sets AG_ERR_INVALID_ARG in the status word.
+ *   Ordered on `stream`; does not synchronise.
+ */
+AG_API ag_status ag_normal_map_error(ag_bvh_t h, const float *d_lverts, const float *d_luv,
+                                     const int32_t *d_lfaces, int64_t n_lverts, int64_t n_lfaces,
+                                     int32_t W, int32_t H, const uint8_t *d_normal_rgba8,
+                                     const int32_t *d_sample_face, const float *d_sample_bary,
+                                     int64_t n_samples, float max_dist, const ag_opts *opts,
+                                     ag_stream_t stream, float *d_angle_deg);
 
 /*
  * ag_point_distance - distance from each of n points to the mesh of the

@@ -11,7 +11,7 @@ from ._lib import EXPORTS, AgError, load as load_library  # noqa: F401
 
 _TORCH_API = ("Bvh", "BakeOutputs", "Asset", "BatchPlan", "BakeLoss", "bake", "bake_batch", "bake_backward",
               "bake_loss", "alloc_outputs", "sync_status", "visibility", "exterior_fill", "hidden_faces", "qem_simplify",
-              "point_distance", "render_views", "backproject")
+              "point_distance", "render_views", "backproject", "normal_map_error")
 
 
 def __getattr__(name):

@@ -32,6 +32,9 @@ AG_TILE_4x4 = 3
 AG_SCHED_AUTO = -1
 AG_SCHED_BATCH = 0
 AG_SCHED_REFILL = 1
+AG_SCHED_COOP4 = 2
+AG_SCHED_COOP8 = 3
+AG_SCHED_COOP2 = 4
 AG_QUERY_RAY = 0
 AG_QUERY_CLOSEST = 1
 AG_RENDER_RASTER = 0
@@ -46,14 +49,14 @@ EXPORTS = ("ag_opts_default", "ag_bvh_build", "ag_bvh_free", "ag_bvh_free_async"
            "ag_batch_plan_create", "ag_batch_plan_launch", "ag_batch_plan_free", "ag_bake_backward",
            "ag_sync_status", "ag_last_error", "ag_status_string", "ag_version", "ag_vertex_normals_noalloc",
            "ag_autotune", "ag_visibility", "ag_exterior_fill", "ag_qem_simplify",
-           "ag_point_distance", "ag_render_views", "ag_backproject")
+           "ag_point_distance", "ag_render_views", "ag_backproject", "ag_normal_map_error")
 
 
 class AgOpts(ctypes.Structure):
     _fields_ = [("bvh_layout", c_int32), ("gutter", c_int32), ("disp_fp16", c_int32), ("schedule", c_int32),
                 ("block_size", c_int32), ("blocks_per_sm", c_int32), ("max_steps", c_int32),
                 ("collapse", c_int32), ("ray_tile", c_int32), ("query", c_int32), ("render", c_int32),
-                ("filter", c_int32), ("build_async", c_int32), ("reserved", c_int32 * 3)]
+                ("filter", c_int32), ("build_async", c_int32), ("stack_limit", c_int32), ("reserved", c_int32 * 2)]
 
 
 class AgBakeAux(ctypes.Structure):
@@ -137,6 +140,10 @@ def load():
         lib.ag_point_distance.argtypes = [c_void_p, c_void_p, c_int64, c_float, POINTER(AgOpts), c_void_p, c_void_p,
                                           c_void_p]
         lib.ag_point_distance.restype = S
+        lib.ag_normal_map_error.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
+                                            c_void_p, c_void_p, c_void_p, c_int64, c_float, POINTER(AgOpts), c_void_p,
+                                            c_void_p]
+        lib.ag_normal_map_error.restype = S
         lib.ag_render_views.argtypes = [c_void_p, c_int32, c_void_p, c_int32, c_int32, c_float, POINTER(AgOpts),
                                         c_void_p, c_void_p, c_void_p, c_void_p]
         lib.ag_render_views.restype = S

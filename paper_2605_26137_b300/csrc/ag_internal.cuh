@@ -197,6 +197,7 @@ struct TraceLaunch {
     unsigned *status;
     int max_steps;
     unsigned long long *counters;  // non-NULL -> counting build
+    int stack_cap;              // counting build: usable traversal stack entries (0 = all)
     int layout;
     int schedule;
     int query;                  // AG_QUERY_RAY / AG_QUERY_CLOSEST
@@ -225,6 +226,9 @@ cudaError_t launch_backproject(const float4 *lpos, const float4 *lnrm, const int
 // distance from n points to the mesh of L.job0 (nodes, tris, tri_ids, scene_abs), -1 beyond max_dist
 cudaError_t launch_point_distance(const TraceLaunch &L, const float *pts, long long n, float max_dist, float *dist,
                                   int32_t *tri, cudaStream_t s);
+// "baked mean" angle per sample point of the low mesh of L.job0 (closest.cu)
+cudaError_t launch_map_error(const TraceLaunch &L, const uint8_t *rgba, const float *luv, int64_t n_lfaces,
+                             const int32_t *sface, const float *sbary, long long n, float *angle, cudaStream_t s);
 
 cudaError_t launch_finalize(const float4 *ntsd, const int32_t *face_map, int W, int H, int gutter,
                             int disp_fp16, uint8_t *rgba, uint8_t *mask, void *disp,

@@ -116,8 +116,9 @@ ag_status check_opts(const ag_opts &o) {
         return set_error(AG_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in 64..1024");
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 64) return set_error(AG_ERR_INVALID_ARG, "blocks_per_sm out of range");
     if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
-    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_REFILL)
+    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_COOP2)
         return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
+    if (o.stack_limit < 0) return set_error(AG_ERR_INVALID_ARG, "stack_limit must be >= 0");
     if (o.collapse < AG_COLLAPSE_AREA || o.collapse > AG_COLLAPSE_SAH)
         return set_error(AG_ERR_INVALID_ARG, "unknown collapse rule");
     if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
@@ -419,6 +420,7 @@ AG_API ag_status ag_bake(ag_bvh_t h, const float *d_lverts, const float *d_lnorm
     L.status = status;
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.counters = reinterpret_cast<unsigned long long *>(ax.counters);
+    L.stack_cap = o.stack_limit;
     L.layout = h->layout;
     L.schedule = pick_schedule(o);
     L.query = o.query;
@@ -490,6 +492,54 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
     AG_CUDA(launch_trace(L, s));
     AG_CUDA(launch_backward_finish(a.lpos, a.lface, n_lverts, n_lfaces, a.acc, g_pos, g_nrm, g_a, loss_acc, lambda,
                                    d_loss, d_grad, s));
+    return AG_OK;
+}
+
+AG_API ag_status ag_normal_map_error(ag_bvh_t h, const float *d_lverts, const float *d_luv, const int32_t *d_lfaces,
+                                     int64_t n_lverts, int64_t n_lfaces, int32_t W, int32_t H,
+                                     const uint8_t *d_normal_rgba8, const int32_t *d_sample_face,
+                                     const float *d_sample_bary, int64_t n_samples, float max_dist,
+                                     const ag_opts *opts, ag_stream_t stream, float *d_angle_deg) {
+    g_err.clear();
+    ag_status st = check_handle(h);
+    if (st) return st;
+    if ((st = check_low(d_lverts, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, max_dist))) return st;
+    if (n_samples < 0 || n_samples >= (1ll << 40)) return set_error(AG_ERR_INVALID_ARG, "n_samples out of range");
+    if (n_samples == 0) return AG_OK;
+    if (!d_normal_rgba8 || !d_sample_face || !d_sample_bary || !d_angle_deg)
+        return set_error(AG_ERR_INVALID_ARG, "map, sample and output pointers must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(d_normal_rgba8) % 4)
+        return set_error(AG_ERR_INVALID_ARG, "d_normal_rgba8 must be 4-byte aligned");
+    ag_opts o = resolve_opts(opts);
+    if ((st = check_opts(o))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *status = device_status_word(h->device);
+    if (!status) return set_error(AG_ERR_OOM, "status word allocation failed");
+    Scratch sc(s, h->device);
+    AssetScratch a;
+    memset(&a, 0, sizeof(a));
+    AG_CUDA(sc.alloc((void **)&a.acc, sizeof(float) * 3 * n_lverts));
+    AG_CUDA(sc.alloc((void **)&a.lpos, sizeof(float4) * n_lverts));
+    AG_CUDA(sc.alloc((void **)&a.lnrm, sizeof(float4) * n_lverts));
+    AG_CUDA(sc.alloc((void **)&a.ltan, sizeof(float4) * 3 * n_lfaces));
+    AG_CUDA(sc.alloc((void **)&a.lface, sizeof(int4) * n_lfaces));
+    AG_CUDA(sc.alloc((void **)&a.uvfix, sizeof(int4) * 2 * n_lfaces));
+    AG_CUDA(sc.alloc(&a.nscr, vertex_normal_scratch_bytes(n_lverts, n_lfaces)));
+    // the bake's low-mesh set-up: vertex normals, corner tangents, face flags
+    AG_CUDA(launch_vertex_normals(d_lverts, d_lfaces, n_lverts, n_lfaces, nullptr, a.acc, a.lnrm, a.lpos, a.nscr, s));
+    AG_CUDA(launch_face_setup(d_luv, d_lfaces, n_lfaces, n_lverts, W, H, a.lpos, a.lnrm, a.lface, a.ltan, a.uvfix,
+                              status, s));
+    float sabs;
+    if ((st = scene_abs_for(h, &sabs))) return st;
+    TraceLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.job0 = make_job(h, a, W, H, max_dist, sabs, nullptr, nullptr, nullptr);
+    L.n_jobs = 1;
+    L.status = status;
+    L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
+    L.layout = h->layout;
+    AG_CUDA(launch_map_error(L, d_normal_rgba8, d_luv, n_lfaces, d_sample_face, d_sample_bary, n_samples, d_angle_deg,
+                             s));
     return AG_OK;
 }
 

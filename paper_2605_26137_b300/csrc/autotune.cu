@@ -27,40 +27,51 @@ extern "C" AG_API ag_status ag_autotune(ag_bvh_t h, const float *d_lverts, const
     cudaEvent_t e0, e1;
     AG_CUDA(cudaEventCreate(&e0));
     AG_CUDA(cudaEventCreate(&e1));
-    const int scheds[2] = {AG_SCHED_BATCH, AG_SCHED_REFILL};
+    // candidates: the one-ray-per-thread schedules at three block sizes, and
+    // the warp-cooperative ones (fixed 128-thread blocks; forward ray bake
+    // over 8-bit nodes only), each with every ray tile
+    struct Cand { int schedule, block; };
+    Cand cands[8];
+    int n_cand = 0;
     const int blocks[3] = {64, 128, 256};
+    for (int bi = 0; bi < 3; ++bi) cands[n_cand++] = {AG_SCHED_BATCH, blocks[bi]};
+    if (inout->query != AG_QUERY_CLOSEST) {   // the closest-point query has one schedule
+        for (int bi = 0; bi < 3; ++bi) cands[n_cand++] = {AG_SCHED_REFILL, blocks[bi]};
+        if (h->layout == AG_BVH_Q8) {
+            cands[n_cand++] = {AG_SCHED_COOP2, 0};
+            cands[n_cand++] = {AG_SCHED_COOP4, 0};
+        }
+    }
     const int tiles[4] = {AG_TILE_8x8, AG_TILE_16x16, AG_TILE_32x8, AG_TILE_4x4};
     ag_opts best = *inout;
     float best_t = 3.0e38f;
     ag_status st = AG_OK;
-    const int n_sched = inout->query == AG_QUERY_CLOSEST ? 1 : 2;   // the closest-point query has one schedule
-    for (int si = 0; si < n_sched && st == AG_OK; ++si)
-        for (int bi = 0; bi < 3 && st == AG_OK; ++bi)
-            for (int ti = 0; ti < 4 && st == AG_OK; ++ti) {
-                ag_opts o = *inout;
-                o.schedule = scheds[si];
-                o.block_size = blocks[bi];
-                o.blocks_per_sm = 0;
-                o.ray_tile = tiles[ti];
-                o.disp_fp16 = 1;
-                float ts[3];
-                for (int rep = 0; rep < 4 && st == AG_OK; ++rep) {
-                    if (rep) cudaEventRecord(e0, s);
-                    st = ag_bake(h, d_lverts, d_lnormals, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, max_dist, &o,
-                                 stream, rgba, mask, disp, nullptr);
-                    if (rep && st == AG_OK) {
-                        cudaEventRecord(e1, s);
-                        cudaEventSynchronize(e1);
-                        cudaEventElapsedTime(&ts[rep - 1], e0, e1);
-                    }
-                }
-                if (st != AG_OK) break;
-                std::sort(ts, ts + 3);
-                if (ts[1] < best_t) {
-                    best_t = ts[1];
-                    best = o;
+    for (int ci = 0; ci < n_cand && st == AG_OK; ++ci)
+        for (int ti = 0; ti < 4 && st == AG_OK; ++ti) {
+            ag_opts o = *inout;
+            o.schedule = cands[ci].schedule;
+            o.block_size = cands[ci].block;
+            o.blocks_per_sm = 0;
+            o.ray_tile = tiles[ti];
+            o.disp_fp16 = 1;
+            float ts[3];
+            for (int rep = 0; rep < 4 && st == AG_OK; ++rep) {
+                if (rep) cudaEventRecord(e0, s);
+                st = ag_bake(h, d_lverts, d_lnormals, d_luv, d_lfaces, n_lverts, n_lfaces, W, H, max_dist, &o,
+                             stream, rgba, mask, disp, nullptr);
+                if (rep && st == AG_OK) {
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&ts[rep - 1], e0, e1);
                 }
             }
+            if (st != AG_OK) break;
+            std::sort(ts, ts + 3);
+            if (ts[1] < best_t) {
+                best_t = ts[1];
+                best = o;
+            }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != AG_OK) return st;

@@ -106,7 +106,7 @@ ag_status check_opts_batch(const ag_opts &o) {
         return set_error(AG_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in 64..1024");
     if (o.blocks_per_sm < 0 || o.blocks_per_sm > 64) return set_error(AG_ERR_INVALID_ARG, "blocks_per_sm out of range");
     if (o.max_steps < 0) return set_error(AG_ERR_INVALID_ARG, "max_steps must be >= 0");
-    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_REFILL) return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
+    if (o.schedule < AG_SCHED_AUTO || o.schedule > AG_SCHED_COOP2) return set_error(AG_ERR_INVALID_ARG, "unknown schedule");
     if (o.ray_tile < AG_TILE_8x8 || o.ray_tile > AG_TILE_4x4) return set_error(AG_ERR_INVALID_ARG, "unknown ray tile");
     if (o.query != AG_QUERY_RAY && o.query != AG_QUERY_CLOSEST)
         return set_error(AG_ERR_INVALID_ARG, "query must be AG_QUERY_RAY or AG_QUERY_CLOSEST");

@@ -158,10 +158,14 @@ struct PointNode;
 // (p, origin - p, the slack subtraction, the FMA, and the half ulp by which
 // the build's rounded decode may exceed the exact plane) sum to at most
 // 2^-24 (4 |origin| + 4 |p| + 510 * 2^e), half of that slack.
+// With LEAVES, leaf children within the bound are recorded in *ls (to be
+// tested by the caller right away) instead of being offered.
 template <>
 struct PointNode<AG_BVH_Q8> {
+    template <bool LEAVES = false>
     static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, float3 p, float lim, Next &nx,
-                                                 uint2 *stack, int &sp, unsigned *status, float) {
+                                                 uint2 *stack, int &sp, unsigned *status, float,
+                                                 LeafSet *ls = nullptr) {
         const uint4 *q = reinterpret_cast<const uint4 *>(static_cast<const QNode *>(nodes) + idx);
         uint4 w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + 2), w3 = __ldg(q + 3), w4 = __ldg(q + 4);
         float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
@@ -176,6 +180,7 @@ struct PointNode<AG_BVH_Q8> {
         float blx = rx - ex, bly = ry - ey, blz = rz - ez;
         float bhx = -rx - ex, bhy = -ry - ey, bhz = -rz - ez;
         uint32_t child_base = w1.x, tri_base = w1.y;
+        if (LEAVES) *ls = LeafSet{0u, w1.z, w1.w, tri_base};
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int k = c & 3;
@@ -188,7 +193,12 @@ struct PointNode<AG_BVH_Q8> {
             float gz = fmaxf(fmaxf(__fmaf_rn(byte_f(hi ? w3.y : w3.x, k), sz, blz),
                                    __fmaf_rn(byte_f(hi ? w4.w : w4.z, k), -sz, bhz)), 0.f);
             float g2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, gz * gz));
-            if (m != 0 && g2 <= lim) offer(child_ref(m, child_base, tri_base), g2, nx, stack, sp, status);
+            if (m != 0 && g2 <= lim) {
+                if (LEAVES && !(m & 0x80u))
+                    ls->mask |= 1u << c;
+                else
+                    offer(child_ref(m, child_base, tri_base), g2, nx, stack, sp, status);
+            }
         }
     }
 };
@@ -197,11 +207,14 @@ struct PointNode<AG_BVH_Q8> {
 // 2^-21 (scene bound + |p|).
 template <>
 struct PointNode<AG_BVH_F32> {
+    template <bool LEAVES = false>
     static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, float3 p, float lim, Next &nx,
-                                                 uint2 *stack, int &sp, unsigned *status, float scene_abs) {
+                                                 uint2 *stack, int &sp, unsigned *status, float scene_abs,
+                                                 LeafSet *ls = nullptr) {
         const uint4 *q = reinterpret_cast<const uint4 *>(static_cast<const FNode *>(nodes) + idx);
         uint4 h = __ldg(q);
         uint32_t child_base = h.x, tri_base = h.y;
+        if (LEAVES) *ls = LeafSet{0u, h.z, h.w, tri_base};
         float ex = EPS_REL * (scene_abs + fabsf(p.x));
         float ey = EPS_REL * (scene_abs + fabsf(p.y));
         float ez = EPS_REL * (scene_abs + fabsf(p.z));
@@ -218,7 +231,12 @@ struct PointNode<AG_BVH_F32> {
                 float gy = fmaxf(fmaxf(__uint_as_float(LY[k]) - p.y, p.y - __uint_as_float(HY[k])) - ey, 0.f);
                 float gz = fmaxf(fmaxf(__uint_as_float(LZ[k]) - p.z, p.z - __uint_as_float(HZ[k])) - ez, 0.f);
                 float g2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, gz * gz));
-                if (m != 0 && g2 <= lim) offer(child_ref(m, child_base, tri_base), g2, nx, stack, sp, status);
+                if (m != 0 && g2 <= lim) {
+                    if (LEAVES && !(m & 0x80u))
+                        ls->mask |= 1u << (4 * half + k);
+                    else
+                        offer(child_ref(m, child_base, tri_base), g2, nx, stack, sp, status);
+                }
             }
         }
     }
@@ -293,6 +311,49 @@ __device__ __forceinline__ bool step_point(const TraceArgs &A, const TraceJob &J
     return true;
 }
 
+// A node visit that tests the node's leaf children within the bound right
+// away (slot order); only inner children are offered and stacked.  Every step
+// of a lane is a node visit (3.32 -> 2.72 ms on the 2.1M-triangle bake over
+// 8-bit nodes, for 62 % more triangle tests: sibling leaves are no longer
+// taken nearest first, so fewer are culled by a shrinking bound).
+template <int LAYOUT, bool COUNT>
+__device__ __forceinline__ bool step_point_leaves(const TraceArgs &A, const TraceJob &J, PointState &S, uint2 *stack,
+                                                  unsigned long long &c_nodes, unsigned long long &c_tris) {
+    Next nx;
+    nx.has = false;
+    nx.ref = 0;
+    nx.dist = 0.f;
+    LeafSet ls;
+    PointNode<LAYOUT>::template visit<true>(J.nodes, S.cur, S.p, S.best.d2 * LIM_REL, nx, stack, S.sp, A.status,
+                                            J.scene_abs, &ls);
+    if (COUNT) ++c_nodes;
+    while (ls.mask) {
+        const int c = __ffs(ls.mask) - 1;
+        ls.mask &= ls.mask - 1;
+        uint32_t first;
+        int cnt;
+        leaf_range(ls, c, first, cnt);
+        for (int t = 0; t < cnt; ++t) test_tri(S, J.tris, J.tri_ids, first + t);
+        if (COUNT) c_tris += cnt;
+    }
+    if (nx.has) {
+        S.cur = nx.ref;
+    } else {
+        bool done = true;
+        const float lim = S.best.d2 * LIM_REL;
+        while (S.sp > 0) {
+            uint2 e = stack[--S.sp];
+            if (__uint_as_float(e.y) <= lim) { S.cur = e.x; done = false; break; }
+        }
+        if (done) return false;
+    }
+    if (++S.steps > A.max_steps) {
+        atomicOr(A.status, AGS_STEP_CAP);
+        return false;
+    }
+    return true;
+}
+
 __device__ __forceinline__ void finish_point(const TraceArgs &A, const PointState &S) {
     const TraceJob &J = job_of(A, S.job);
     const bool hit = S.best.found;
@@ -335,7 +396,7 @@ __global__ void __launch_bounds__(256) k_closest(TraceArgs A) {
         setup_point(A, r, S);
         if (COUNT) ++c_rays;
         const TraceJob &J = job_of(A, S.job);
-        while (step_point<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+        while (step_point_leaves<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
         }
         if (COUNT && S.best.found) ++c_hits;
         finish_point(A, S);
@@ -387,7 +448,107 @@ __global__ void __launch_bounds__(256) k_point_dist(TraceArgs A, const float *__
     }
 }
 
+// The "baked mean" measure of Sec. 6.1, one thread per sample point of the low
+// mesh: the normal the RGBA8 map gives at the point (the texel holding its UV
+// point, codes decoded as (q - 128) / 127 and renormalised, taken to world
+// space through the bake's tangent frame at the point; on a face with
+// degenerate UVs the interpolated low normal) against the raw mesh's
+// smooth normal at its surface point nearest to the sample (the same
+// branch-and-bound query as the closest-point bake, radius max_dist), as the
+// angle atan2(|a x b|, a . b) in degrees; -1 where no raw point lies within
+// max_dist or the sample's face was dropped.
+template <int LAYOUT>
+__global__ void __launch_bounds__(128) k_map_error(TraceArgs A, const uchar4 *__restrict__ rgba,
+                                                   const float *__restrict__ luv, int64_t n_lfaces,
+                                                   const int32_t *__restrict__ sface, const float *__restrict__ sbary,
+                                                   long long n, float *__restrict__ angle) {
+    uint2 stack[STACK];
+    PointState S;
+    const TraceJob &J = A.job0;
+    unsigned long long c0 = 0, c1 = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int f = sface[i];
+        if (f < 0 || f >= n_lfaces) {
+            atomicOr(A.status, AGS_BAD_FACE);
+            angle[i] = -1.f;
+            continue;
+        }
+        const int4 fi = J.lface[f];
+        if (fi.w & FACE_INVALID) {
+            angle[i] = -1.f;
+            continue;
+        }
+        const float b1 = sbary[2 * i], b2 = sbary[2 * i + 1];
+        const float3 P0 = f3(J.lpos[fi.x]), P1 = f3(J.lpos[fi.y]), P2 = f3(J.lpos[fi.z]);
+        const float3 N0 = f3(J.lnrm[fi.x]), N1 = f3(J.lnrm[fi.y]), N2 = f3(J.lnrm[fi.z]);
+        S.job = 0;
+        S.base = P0;
+        S.off = (P1 - P0) * b1 + (P2 - P0) * b2;
+        S.p = P0 + S.off;
+        const float3 sv = N0 + (N1 - N0) * b1 + (N2 - N0) * b2;
+        const float3 d = sv * (1.0f / sqrtf(dot3(sv, sv)));
+        S.d = d;
+        S.best.d2 = J.max_dist * J.max_dist;
+        S.best.rec = 0;
+        S.best.found = false;
+        S.cur = 0;
+        S.sp = 0;
+        S.steps = 0;
+        while (step_point<LAYOUT, false>(A, J, S, stack, c0, c1)) {
+        }
+        if (!S.best.found) {
+            angle[i] = -1.f;
+            continue;
+        }
+        const size_t r3 = 3 * (size_t)S.best.rec;
+        const float4 TA = __ldg(&J.tris[r3]), TB = __ldg(&J.tris[r3 + 1]), TC = __ldg(&J.tris[r3 + 2]);
+        TriQ q;
+        tri_query(rel(S, TA), rel(S, TB), rel(S, TC), q);
+        const float3 bw = tri_bary(q);
+        const float3 nr = normalize3(f3(__ldg(&J.hnormals[__float_as_int(TA.w)])) * bw.x +
+                                     f3(__ldg(&J.hnormals[__float_as_int(TB.w)])) * bw.y +
+                                     f3(__ldg(&J.hnormals[__float_as_int(TC.w)])) * bw.z);
+        // the bake's frame at the point
+        const float4 T0 = J.ltan[3 * f], T1 = J.ltan[3 * f + 1], T2 = J.ltan[3 * f + 2];
+        float3 tt = f3(T0) + (f3(T1) - f3(T0)) * b1 + (f3(T2) - f3(T0)) * b2;
+        tt = normalize3(tt - d * dot3(tt, d));
+        const float3 bb = cross3(d, tt) * T0.w;
+        // the texel holding the point's UV
+        const float *uv = luv + 6 * (size_t)f;
+        const float u = uv[0] + (uv[2] - uv[0]) * b1 + (uv[4] - uv[0]) * b2;
+        const float v = uv[1] + (uv[3] - uv[1]) * b1 + (uv[5] - uv[1]) * b2;
+        const int x = min(max((int)floorf(u * (float)J.W), 0), J.W - 1);
+        const int y = min(max((int)floorf(v * (float)J.H), 0), J.H - 1);
+        const uchar4 c8 = rgba[(size_t)y * J.W + x];
+        const float3 c = normalize3(make_float3(((float)c8.x - 128.f) * (1.f / 127.f), ((float)c8.y - 128.f) * (1.f / 127.f),
+                                                ((float)c8.z - 128.f) * (1.f / 127.f)));
+        // a face the UV-reliability filter marks has no usable frame: its normal is d
+        const float3 nm = (fi.w & FACE_DEGEN) ? d : normalize3(tt * c.x + bb * c.y + d * c.z);
+        const float3 cr = cross3(nm, nr);
+        angle[i] = atan2f(sqrtf(dot3(cr, cr)), dot3(nm, nr)) * 57.29577951308232f;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_map_error(const TraceLaunch &L, const uint8_t *rgba, const float *luv, int64_t n_lfaces,
+                             const int32_t *sface, const float *sbary, long long n, float *angle, cudaStream_t s) {
+    TraceArgs A;
+    memset(&A, 0, sizeof(A));
+    A.job0 = L.job0;
+    A.n_jobs = 1;
+    A.status = L.status;
+    A.max_steps = L.max_steps;
+    int dev;
+    cudaGetDevice(&dev);
+    const unsigned grid = (unsigned)(device_sm_count(dev) * 8);
+    const uchar4 *q = reinterpret_cast<const uchar4 *>(rgba);
+    if (L.layout == AG_BVH_Q8)
+        k_map_error<AG_BVH_Q8><<<grid, 128, 0, s>>>(A, q, luv, n_lfaces, sface, sbary, n, angle);
+    else
+        k_map_error<AG_BVH_F32><<<grid, 128, 0, s>>>(A, q, luv, n_lfaces, sface, sbary, n, angle);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_point_distance(const TraceLaunch &L, const float *pts, long long n, float max_dist, float *dist,
                                   int32_t *tri, cudaStream_t s) {

@@ -10,7 +10,6 @@
 #include "ag_internal.cuh"
 #include "exact.cuh"
 
-#include <mutex>
 
 namespace ag {
 
@@ -163,27 +162,16 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = sizeof(unsigned) * (size_t)(2 * NOALLOC
 // host threads) race on it
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-constexpr int NOALLOC_MAXDEV = 64;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[NOALLOC_MAXDEV] = {nullptr};
-
 // Device address of the array on the current device.  In host code the
 // symbol g_noalloc_scratch is only a host-side stand-in, so the address is
-// looked up once per device with that device current, and cached.
+// looked up with the device current, on every call: nothing is cached, so a
+// new context on the device (after cudaDeviceReset, say) gets its own
+// address rather than a stale one.
 ag_status noalloc_scratch_on_current_device(void **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_error(e, "ag_vertex_normals_noalloc: cudaGetDevice");
-    if (dev < 0 || dev >= NOALLOC_MAXDEV)
-        return set_error(AG_ERR_INVALID_ARG, "ag_vertex_normals_noalloc: device %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_error(e, "ag_vertex_normals_noalloc: cudaGetSymbolAddress");
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_error(e, "ag_vertex_normals_noalloc: cudaGetSymbolAddress");
+    *out = p;
     return AG_OK;
 }
 

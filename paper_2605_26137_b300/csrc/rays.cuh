@@ -98,6 +98,41 @@ __device__ __forceinline__ void test_tri(const Ray &r, const float4 *__restrict_
     b.t = t; b.babs = at; b.rec = rec; b.U = U; b.V = V; b.W = W; b.det = det; b.found = true;
 }
 
+// The same test for a lane that shares its ray with other lanes: `lim` is the
+// closest |t| any lane of the ray has found (max_dist at the start), the
+// lane's own best decides ties only among its own candidates, and an accepted
+// hit lowers `lim`.  Candidates at an equal |t| held by different lanes are
+// ordered when the lanes' bests are merged (t >= 0 first, then the lower id).
+__device__ __forceinline__ void test_tri_shared(const Ray &r, const float4 *__restrict__ tris,
+                                                const int32_t *__restrict__ tri_ids, uint32_t rec, Best &b,
+                                                float &lim) {
+    float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
+    float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+    xform(r, A, Ax, Ay, Az);
+    xform(r, B, Bx, By, Bz);
+    xform(r, C, Cx, Cy, Cz);
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return;
+    float det = U + V + W;
+    if (det == 0.f) return;
+    float T = U * Az + V * Bz + W * Cz;
+    if (fabsf(T) > lim * fabsf(det) * 1.0000010f) return;
+    float t = T / det;
+    float at = fabsf(t);
+    if (!(at <= lim)) return;
+    if (b.found && at == b.babs) {
+        if ((t >= 0.f) != (b.t >= 0.f)) {
+            if (t < 0.f) return;
+        } else if (t != b.t || tri_ids[rec] >= tri_ids[b.rec]) {
+            return;
+        }
+    }
+    b.t = t; b.babs = at; b.rec = rec; b.U = U; b.V = V; b.W = W; b.det = det; b.found = true;
+    lim = at;
+}
+
 template <int LAYOUT>
 struct NodeOps;
 
@@ -107,10 +142,14 @@ struct NodeOps;
 // which bounds every rounding on the way (decoded plane, a, b, the FMA, the
 // rounded ray origin) by a factor of at least 4, so a box the exact line
 // meets is never rejected.
+// With LEAVES, hit leaf children are recorded in *ls (to be tested by the
+// caller right away) instead of being offered.
 template <>
 struct NodeOps<AG_BVH_Q8> {
+    template <bool LEAVES = false>
     static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim, Next &nx,
-                                                 uint2 *stack, int &sp, unsigned *status) {
+                                                 uint2 *stack, int &sp, unsigned *status, int cap = STACK,
+                                                 LeafSet *ls = nullptr) {
         const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const QNode *>(nodes) + idx);
         uint4 w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2), w3 = __ldg(p + 3), w4 = __ldg(p + 4);
         float ox = __uint_as_float(w0.x), oy = __uint_as_float(w0.y), oz = __uint_as_float(w0.z);
@@ -128,6 +167,7 @@ struct NodeOps<AG_BVH_Q8> {
         uint32_t ny0 = r.ny ? w4.x : w2.z, ny1 = r.ny ? w4.y : w2.w, fy0 = r.ny ? w2.z : w4.x, fy1 = r.ny ? w2.w : w4.y;
         uint32_t nz0 = r.nz ? w4.z : w3.x, nz1 = r.nz ? w4.w : w3.y, fz0 = r.nz ? w3.x : w4.z, fz1 = r.nz ? w3.y : w4.w;
         uint32_t child_base = w1.x, tri_base = w1.y;
+        if (LEAVES) *ls = LeafSet{0u, w1.z, w1.w, tri_base};
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
             const int k = c & 3;
@@ -141,8 +181,12 @@ struct NodeOps<AG_BVH_Q8> {
             float tfz = __fmaf_rn(byte_f(hi ? fz1 : fz0, k), az, bfz);
             float te = fmaxf(fmaxf(tnx, tny), tnz);
             float tx = fminf(fminf(tfx, tfy), tfz);
-            if (m != 0 && te <= tx && te <= lim && tx >= -lim)
-                offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status);
+            if (m != 0 && te <= tx && te <= lim && tx >= -lim) {
+                if (LEAVES && !(m & 0x80u))
+                    ls->mask |= 1u << c;
+                else
+                    offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status, cap);
+            }
         }
     }
 };
@@ -151,11 +195,14 @@ struct NodeOps<AG_BVH_Q8> {
 // eps = 2^-21 (scene bound + |p|) / |d| per axis.
 template <>
 struct NodeOps<AG_BVH_F32> {
+    template <bool LEAVES = false>
     static __device__ __forceinline__ void visit(const void *nodes, uint32_t idx, const Ray &r, float lim, Next &nx,
-                                                 uint2 *stack, int &sp, unsigned *status, float scene_abs) {
+                                                 uint2 *stack, int &sp, unsigned *status, float scene_abs,
+                                                 int cap = STACK, LeafSet *ls = nullptr) {
         const uint4 *p = reinterpret_cast<const uint4 *>(static_cast<const FNode *>(nodes) + idx);
         uint4 h = __ldg(p);
         uint32_t child_base = h.x, tri_base = h.y;
+        if (LEAVES) *ls = LeafSet{0u, h.z, h.w, tri_base};
         float ex = EPS_REL * (scene_abs + fabsf(r.px)) * fabsf(r.ix);
         float ey = EPS_REL * (scene_abs + fabsf(r.py)) * fabsf(r.iy);
         float ez = EPS_REL * (scene_abs + fabsf(r.pz)) * fabsf(r.iz);
@@ -175,8 +222,13 @@ struct NodeOps<AG_BVH_F32> {
                 float plz = __uint_as_float(r.nz ? HZ[k] : LZ[k]), pfz = __uint_as_float(r.nz ? LZ[k] : HZ[k]);
                 float te = fmaxf(fmaxf(__fmaf_rn(plx, r.ix, cnx), __fmaf_rn(ply, r.iy, cny)), __fmaf_rn(plz, r.iz, cnz));
                 float tx = fminf(fminf(__fmaf_rn(pfx, r.ix, cfx), __fmaf_rn(pfy, r.iy, cfy)), __fmaf_rn(pfz, r.iz, cfz));
-                if (m != 0 && te <= tx && te <= lim && tx >= -lim)
-                    offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status);
+                if (m != 0 && te <= tx && te <= lim && tx >= -lim) {
+                    if (LEAVES && !(m & 0x80u))
+                        ls->mask |= 1u << (4 * half + k);
+                    else
+                        offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status,
+                              cap);
+                }
             }
         }
     }

@@ -26,6 +26,7 @@ struct TraceArgs {
     unsigned *status;
     int max_steps;
     unsigned long long *counters;
+    int stack_cap;   // counting build only: usable stack entries (test hook)
 };
 
 __device__ __forceinline__ const TraceJob &job_of(const TraceArgs &A, int j) {
@@ -45,7 +46,10 @@ struct Next {
     bool has;
 };
 
-__device__ __forceinline__ void offer(uint32_t ref, float d, Next &nx, uint2 *stack, int &sp, unsigned *status) {
+// cap: the stack's usable entries (STACK; less only in the counting build
+// under the ag_opts.stack_limit test hook)
+__device__ __forceinline__ void offer(uint32_t ref, float d, Next &nx, uint2 *stack, int &sp, unsigned *status,
+                                      int cap = STACK) {
     uint32_t pr = ref;
     float pd = d;
     if (!nx.has || d < nx.dist) {
@@ -55,12 +59,26 @@ __device__ __forceinline__ void offer(uint32_t ref, float d, Next &nx, uint2 *st
         nx.dist = d;
         if (!nx.has) { nx.has = true; return; }
     }
-    if (sp < STACK) stack[sp++] = make_uint2(pr, __float_as_uint(pd));
+    if (sp < cap) stack[sp++] = make_uint2(pr, __float_as_uint(pd));
     else atomicOr(status, AGS_STACK);
 }
 
 __device__ __forceinline__ uint32_t child_ref(uint32_t m, uint32_t child_base, uint32_t tri_base) {
     return (m & 0x80u) ? child_base + (m & 0x7fu) : ref_leaf(tri_base + (m & 31u), (int)((m >> 5) & 3u));
+}
+
+// The leaf children of one node visit that are to be tested right away
+// instead of going through the nearest-next bookkeeping: a mask of child
+// slots, and the node's meta words (one byte per slot: bit 7 inner child,
+// bits 5-6 triangle count, bits 0-4 first triangle after tri_base).
+struct LeafSet {
+    uint32_t mask, meta_lo, meta_hi, tri_base;
+};
+
+__device__ __forceinline__ void leaf_range(const LeafSet &ls, int c, uint32_t &first, int &count) {
+    const uint32_t m = ((c >= 4 ? ls.meta_hi : ls.meta_lo) >> (8 * (c & 3))) & 0xffu;
+    first = ls.tri_base + (m & 31u);
+    count = (int)((m >> 5) & 3u);
 }
 
 template <bool COUNT>

@@ -16,7 +16,8 @@ from . import _lib
 from ._lib import AgAssetDesc, AgBakeAux, AgBvhInfo, check, default_opts
 
 _LAYOUTS = {"q8": _lib.AG_BVH_Q8, "f32": _lib.AG_BVH_F32}
-_SCHED = {"auto": _lib.AG_SCHED_AUTO, "batch": _lib.AG_SCHED_BATCH, "refill": _lib.AG_SCHED_REFILL}
+_SCHED = {"auto": _lib.AG_SCHED_AUTO, "batch": _lib.AG_SCHED_BATCH, "refill": _lib.AG_SCHED_REFILL,
+          "coop4": _lib.AG_SCHED_COOP4, "coop8": _lib.AG_SCHED_COOP8, "coop2": _lib.AG_SCHED_COOP2}
 
 
 def _stream(stream=None) -> int:
@@ -47,13 +48,13 @@ _QUERY = {"ray": _lib.AG_QUERY_RAY, "closest": _lib.AG_QUERY_CLOSEST}
 
 
 def _opts(layout="q8", gutter=2, disp_fp16=True, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
-          collapse="sah", ray_tile="8x8", query="ray"):
+          collapse="sah", ray_tile="8x8", query="ray", stack_limit=0):
     return default_opts(bvh_layout=_LAYOUTS[layout], gutter=gutter, disp_fp16=int(bool(disp_fp16)),
                         schedule=_SCHED[schedule] if isinstance(schedule, str) else schedule,
                         block_size=block_size, blocks_per_sm=blocks_per_sm, max_steps=max_steps,
                         collapse=_COLLAPSE[collapse],
                         ray_tile=_TILES[ray_tile] if isinstance(ray_tile, str) else ray_tile,
-                        query=_QUERY[query] if isinstance(query, str) else query)
+                        query=_QUERY[query] if isinstance(query, str) else query, stack_limit=stack_limit)
 
 
 class Bvh:
@@ -175,20 +176,22 @@ def _ptr(t):
 def bake(bvh: Bvh, low_verts, low_faces, low_uv, W: int, H: int, max_dist: float, *, low_normals=None,
          gutter: int = 2, disp_fp16: bool = True, aux: bool = False, counters: bool = False,
          out: BakeOutputs | None = None, schedule="auto", block_size=0, blocks_per_sm=0, max_steps=0,
-         stream=None, events=None, ray_tile="8x8", query="ray") -> BakeOutputs:
+         stream=None, events=None, ray_tile="8x8", query="ray", stack_limit=0) -> BakeOutputs:
     """One bake.  ``query`` is "ray" (the line along the texel normal) or
     "closest" (the nearest point of the high surface, Sec. 6.4 as worded).
     ``aux`` adds float tangent-space normals, raster and hit outputs (hit_t is
     the signed ray parameter or signed distance); ``counters`` selects the
     counting traversal build; ``events`` (4 torch.cuda.Event) are recorded
     before the raster, before and after the traversal and after the
-    encoding."""
+    encoding.  ``stack_limit`` (with ``counters``; a test hook) caps the
+    traversal stack so that an overflow can be provoked."""
     lib = _lib.load()
     _check_low(low_verts, low_faces, low_uv, low_normals)
     if out is None:
         out = alloc_outputs(W, H, low_verts.device, disp_fp16, aux, counters)
     o = _opts(gutter=gutter, disp_fp16=disp_fp16, schedule=schedule, block_size=block_size,
-              blocks_per_sm=blocks_per_sm, max_steps=max_steps, ray_tile=ray_tile, query=query)
+              blocks_per_sm=blocks_per_sm, max_steps=max_steps, ray_tile=ray_tile, query=query,
+              stack_limit=stack_limit)
     ev = None
     if events is not None:
         if len(events) != 4:
@@ -394,6 +397,28 @@ def point_distance(bvh: Bvh, points, max_dist: float, *, tri: bool = False, stre
     check(lib.ag_point_distance(bvh.handle, points.data_ptr(), points.shape[0], float(max_dist), None,
                                 _stream(stream), d.data_ptr(), _ptr(t)))
     return (d, t) if tri else d
+
+
+def normal_map_error(bvh: Bvh, low_verts, low_faces, low_uv, W: int, H: int, normal_rgba8, sample_face, sample_bary,
+                     max_dist: float, *, stream=None):
+    """The "baked mean" measure (Sec. 6.1) per sample point of the low mesh:
+    the angle in degrees between the normal the RGBA8 map [H,W,4] gives at
+    the point and the smooth normal of the mesh ``bvh`` was built on (the raw
+    mesh) at its nearest point (-1 where none lies within max_dist).
+    sample_face [n] i32 and sample_bary [n,2] f32 (b1, b2) place the samples."""
+    lib = _lib.load()
+    _check_low(low_verts, low_faces, low_uv, None)
+    _need(normal_rgba8, "normal_rgba8", torch.uint8, (W, 4))
+    _need(sample_face, "sample_face", torch.int32)
+    _need(sample_bary, "sample_bary", torch.float32, (2,))
+    if normal_rgba8.shape[0] != H or sample_bary.shape[0] != sample_face.shape[0]:
+        raise ValueError("map or sample shapes do not match")
+    ang = torch.empty(sample_face.shape[0], dtype=torch.float32, device=low_verts.device)
+    check(lib.ag_normal_map_error(bvh.handle, low_verts.data_ptr(), low_uv.data_ptr(), low_faces.data_ptr(),
+                                  low_verts.shape[0], low_faces.shape[0], W, H, normal_rgba8.data_ptr(),
+                                  sample_face.data_ptr(), sample_bary.data_ptr(), sample_face.shape[0],
+                                  float(max_dist), None, _stream(stream), ang.data_ptr()))
+    return ang
 
 
 # ----------------------------------------------------------------- UV-space backprojection (Sec. 7.4)

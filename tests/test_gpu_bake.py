@@ -31,7 +31,7 @@ def test_tiny_bake_matches_oracle(seed, layout):
     a = synth.tiny_asset(seed)
     o = oracle.bake_asset(a, use_bvh=False)  # brute-force oracle
     _, g, _ = gpu_bake(a, layout)
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a)
     print(st)
     parity.check(st)
     assert st["n_ray"] == 4000
@@ -47,7 +47,7 @@ def test_jittered_atlas_ragged_sizes(W, H, seed):
     a = synth.Asset(hv, hf, lv, lf, uv, W, H, 0.15, 2)
     o = oracle.bake_asset(a)
     _, g, _ = gpu_bake(a)
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a)
     print(st)
     parity.check(st)
     assert o["degen"].sum() > 0
@@ -59,7 +59,7 @@ def test_sdf_asset_matches_oracle():
     a = synth.sdf_asset(7, 120_000, 6_000, 512, 384, n_prims=16)
     o = oracle.bake_asset(a)
     _, g, _ = gpu_bake(a)
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a)
     print(st)
     parity.check(st)
 
@@ -173,6 +173,29 @@ def test_step_cap_sets_status_and_clears():
     pb.sync_status()  # cleared, and a normal bake sets nothing
 
 
+@pytest.mark.parametrize("schedule", ["batch", "refill", "coop2", "coop8"])
+def test_stack_overflow_sets_status_and_clears(schedule):
+    """A traversal stack capped at one entry (the counting build's test hook)
+    must overflow on the tiny asset; the overflow is reported as
+    AG_ERR_TRAVERSAL_LIMIT, and the next bake (full stack) is clean and
+    equal to a bake that never overflowed."""
+    import paper_2605_26137_b300 as pb
+    a = synth.tiny_asset(0)
+    bvh = pb.Bvh(_t(a.high_v), _t(a.high_f))
+    lv, lf, uv = _t(a.low_v), _t(a.low_f), _t(a.low_uv)
+    md = 0.6   # a long ray crosses many boxes, so a one-entry stack cannot hold them
+    clean = pb.bake(bvh, lv, lf, uv, a.W, a.H, md, schedule=schedule)
+    pb.sync_status()
+    ref = clean.normal_rgba8.cpu().numpy()
+    pb.bake(bvh, lv, lf, uv, a.W, a.H, md, schedule=schedule, counters=True, aux=True, stack_limit=1)
+    with pytest.raises(pb.AgError) as ei:
+        pb.sync_status()
+    assert ei.value.status == 4
+    again = pb.bake(bvh, lv, lf, uv, a.W, a.H, md, schedule=schedule, counters=True, aux=True)
+    pb.sync_status()
+    assert np.array_equal(again.normal_rgba8.cpu().numpy(), ref)
+
+
 def test_device_argument_errors():
     import paper_2605_26137_b300 as pb
     a = synth.tiny_asset(0)
@@ -264,7 +287,7 @@ def test_full_size_asset_sampled_parity():
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(rays, size=3000, replace=False))
     o = oracle.bake_asset(a, sample=sample)
-    st = parity.compare(g, o, a.diam, a.gutter, sample=sample)
+    st = parity.compare(g, o, a.diam, a.gutter, sample=sample, asset=a)
     print(st)
     parity.check(st, small=0)
     # properties on every texel
@@ -304,7 +327,7 @@ def test_large_asset_sampled_parity_both_layouts():
     for layout in ("q8", "f32"):
         bvh, g, _ = gpu_bake(a, layout=layout)
         assert np.array_equal(g["face"], face)
-        st = parity.compare(g, o, a.diam, a.gutter, sample=sample)
+        st = parity.compare(g, o, a.diam, a.gutter, sample=sample, asset=a)
         print(layout, len(a.high_f), st)
         parity.check(st, small=0)
         bvh.free()
@@ -320,12 +343,14 @@ def test_launch_configurations_give_identical_bakes_and_autotune(tmp_path, monke
     bvh = pb.Bvh(_t(a.high_v), _t(a.high_f))
     lv, lf, uv = _t(a.low_v), _t(a.low_f), _t(a.low_uv)
     ref = None
-    for sched in ("batch", "refill"):
+    for sched in ("batch", "refill", "coop2", "coop4", "coop8"):
         for tile in ("8x8", "16x16", "32x8", "4x4"):
             for block in (64, 256):
-                o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, schedule=sched, ray_tile=tile, block_size=block)
+                o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, schedule=sched, ray_tile=tile, block_size=block,
+                            aux=True)
                 pb.sync_status()
-                got = (o.normal_rgba8.cpu().numpy(), o.mask.cpu().numpy(), o.disp.cpu().numpy().view(np.uint16))
+                got = (o.normal_rgba8.cpu().numpy(), o.mask.cpu().numpy(), o.disp.cpu().numpy().view(np.uint16),
+                       o.hit_tri.cpu().numpy(), o.normal_ts.cpu().numpy().view(np.uint32))
                 if ref is None:
                     ref = got
                 for x, y in zip(got, ref):
@@ -333,7 +358,7 @@ def test_launch_configurations_give_identical_bakes_and_autotune(tmp_path, monke
     monkeypatch.setenv("AGBAKE_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
     e = autotune.tune(bvh, lv, lf, uv, a.W, a.H, a.max_dist)
     assert not e["cached"] and e["ms"] > 0
-    assert e["schedule"] in (0, 1) and e["block_size"] in (64, 128, 256) and e["ray_tile"] in (0, 1, 2, 3)
+    assert e["schedule"] in (0, 1, 2, 3, 4) and e["block_size"] in (0, 64, 128, 256) and e["ray_tile"] in (0, 1, 2, 3)
     e2 = autotune.tune(bvh, lv, lf, uv, a.W, a.H, a.max_dist)
     assert e2["cached"] and e2["schedule"] == e["schedule"]
     o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, **autotune.launch_kwargs(e))
@@ -367,7 +392,7 @@ def test_maximum_atlas_width_and_height(W, H):
     a = synth.Asset(hv, hf, lv, lf, uv, W, H, 0.15, 2)
     o = oracle.bake_asset(a)
     _, g, _ = gpu_bake(a)
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a)
     print(st)
     parity.check(st)
     assert st["n_ray"] > 10_000
@@ -385,7 +410,7 @@ def test_tiny_high_meshes(n_high):
     a = synth.Asset(hv, hf, lv, lf, uv, 32, 32, 0.5, 2)
     o = oracle.bake_asset(a, use_bvh=False)
     _, g, _ = gpu_bake(a)
-    st = parity.compare(g, o, a.diam, a.gutter)
+    st = parity.compare(g, o, a.diam, a.gutter, asset=a)
     parity.check(st)
 
 
