@@ -543,7 +543,9 @@ def main():
                          "layout": {"bytes_per_ray": bpl, "achieved": achieved_layout,
                                     "frac": achieved_layout / hbm}},
             "clocks": clocks,
-            "gpu_launches": 7 * args.steps}
+            # per bake: the low mesh's vertex normals (degree, three scan passes,
+            # fill, gather), face set-up, raster, resolve, traversal, finalize
+            "gpu_launches": 11 * args.steps}
 
     if not args.no_extras:
         line.update(extras(args, pb, torch, a, bvh, hv, hf, lv, lf, uv, W, H, dev, flush, step_ms))

@@ -203,8 +203,8 @@ AG_API void ag_opts_default(ag_opts *o);
  * d_verts [n_verts*3] float32, d_faces [n_faces*3] int32 (0 <= index < n_verts;
  * checked on the device: out-of-range faces are reported as AG_ERR_INVALID_ARG).
  * Builds a linear BVH (30-bit Morton codes of triangle centroids, device radix
- * sort, Karras hierarchy), collapses it to 8-wide nodes with leaves of <= 2
- * triangles, stores child boxes per opts->bvh_layout, reorders triangles into
+ * sort, Karras hierarchy), collapses it to 8-wide nodes with leaves of one
+ * triangle, stores child boxes per opts->bvh_layout, reorders triangles into
  * leaf order and computes area-weighted smooth vertex normals.  The handle
  * keeps its own copies.  1 <= n_faces < 2^29, 3 <= n_verts < 2^31.
  * Default (opts->build_async = 0): synchronises `stream`; the inputs may be

@@ -44,7 +44,7 @@ int device_sm_count(int device);
 struct Scratch {
     cudaStream_t stream;
     int device;
-    void *ptrs[32];
+    void *ptrs[48];
     int n = 0;
     explicit Scratch(cudaStream_t s, int dev) : stream(s), device(dev) {}
     cudaError_t alloc(void **p, size_t bytes);
@@ -82,11 +82,16 @@ __host__ __device__ inline int meta_rank(uint8_t m) { return m & 0x7f; }
 __host__ __device__ inline int meta_count(uint8_t m) { return (m >> 5) & 3; }
 __host__ __device__ inline int meta_offset(uint8_t m) { return m & 31; }
 
-// Leaves hold at most 2 triangles: a triangle test costs about a fifth of an
-// 8-child node test, but fewer triangles per leaf still won on the bake rays
-// (2.1M triangles, 2048^2: 1.007 ms at 3, 0.971 ms at 2, 0.964 ms at 1, the
-// last at 4 % more cost for the closest-point query and a 2x larger tree).
-constexpr int LEAF_MAX = 2;
+// Leaves hold one triangle. With leaves tested at their node, one triangle
+// per leaf (a child box per triangle) measured fastest for both queries on
+// the 2.1M-triangle, 2048^2 bake: ray trace 0.78-0.80 ms at 1, 0.82-0.83 at 2,
+// 0.85 at 3; closest-point trace 2.51-2.54 ms at 1, 2.74-2.79 at 2, 2.86 at 3;
+// for a tree of 456k instead of 308k nodes and a build 0.05 ms slower.
+// (Before leaves were tested at their node, 2 had measured best.)
+#ifndef AG_LEAF_MAX
+#define AG_LEAF_MAX 1
+#endif
+constexpr int LEAF_MAX = AG_LEAF_MAX;
 
 // Triangle record (48 B, leaf order): three float4 (vertex xyz, vertex index
 // bits in .w).  The original triangle id is kept in a parallel array.

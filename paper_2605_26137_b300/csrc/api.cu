@@ -83,7 +83,7 @@ int device_sm_count(int dev) {
 
 cudaError_t Scratch::alloc(void **p, size_t bytes) {
     *p = nullptr;
-    if (n >= 32) return cudaErrorInvalidValue;
+    if (n >= (int)(sizeof(ptrs) / sizeof(ptrs[0]))) return cudaErrorInvalidValue;
     cudaMemPool_t pool = device_pool(device);
     if (!pool) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 16), pool, stream);

@@ -318,14 +318,20 @@ __global__ void __launch_bounds__(128) k_trace_views(RenderArgs A) {
             nx.has = false;
             nx.ref = 0;
             nx.dist = 0.f;
-            if (ref_is_leaf(cur)) {
-                const uint32_t first = ref_first(cur);
-                const int cnt = ref_count(cur);
+            // every step a node visit (the root is always a node), its hit leaf children tested here
+            LeafSet ls;
+            if (LAYOUT == AG_BVH_Q8)
+                NodeOps<AG_BVH_Q8>::visit<true>(A.nodes, cur, ray, b.babs, nx, stack, sp, A.status, STACK, &ls);
+            else
+                NodeOps<AG_BVH_F32>::visit<true>(A.nodes, cur, ray, b.babs, nx, stack, sp, A.status, A.scene_abs,
+                                                 STACK, &ls);
+            while (ls.mask) {
+                const int c = __ffs(ls.mask) - 1;
+                ls.mask &= ls.mask - 1;
+                uint32_t first;
+                int cnt;
+                leaf_range(ls, c, first, cnt);
                 for (int q = 0; q < cnt; ++q) test_tri_front(ray, A.tris, A.tri_ids, first + q, b);
-            } else if (LAYOUT == AG_BVH_Q8) {
-                NodeOps<AG_BVH_Q8>::visit(A.nodes, cur, ray, b.babs, nx, stack, sp, A.status);
-            } else {
-                NodeOps<AG_BVH_F32>::visit(A.nodes, cur, ray, b.babs, nx, stack, sp, A.status, A.scene_abs);
             }
             if (nx.has) {
                 cur = nx.ref;

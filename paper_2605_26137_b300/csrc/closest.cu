@@ -277,40 +277,6 @@ __device__ __forceinline__ void setup_point(const TraceArgs &A, long long r, Poi
     S.steps = 0;
 }
 
-template <int LAYOUT, bool COUNT>
-__device__ __forceinline__ bool step_point(const TraceArgs &A, const TraceJob &J, PointState &S, uint2 *stack,
-                                           unsigned long long &c_nodes, unsigned long long &c_tris) {
-    Next nx;
-    nx.has = false;
-    nx.ref = 0;
-    nx.dist = 0.f;
-    if (ref_is_leaf(S.cur)) {
-        uint32_t first = ref_first(S.cur);
-        int cnt = ref_count(S.cur);
-        for (int k = 0; k < cnt; ++k) test_tri(S, J.tris, J.tri_ids, first + k);
-        if (COUNT) c_tris += cnt;
-    } else {
-        PointNode<LAYOUT>::visit(J.nodes, S.cur, S.p, S.best.d2 * LIM_REL, nx, stack, S.sp, A.status, J.scene_abs);
-        if (COUNT) ++c_nodes;
-    }
-    if (nx.has) {
-        S.cur = nx.ref;
-    } else {
-        bool done = true;
-        const float lim = S.best.d2 * LIM_REL;
-        while (S.sp > 0) {
-            uint2 e = stack[--S.sp];
-            if (__uint_as_float(e.y) <= lim) { S.cur = e.x; done = false; break; }
-        }
-        if (done) return false;
-    }
-    if (++S.steps > A.max_steps) {
-        atomicOr(A.status, AGS_STEP_CAP);
-        return false;
-    }
-    return true;
-}
-
 // A node visit that tests the node's leaf children within the bound right
 // away (slot order); only inner children are offered and stacked.  Every step
 // of a lane is a node visit (3.32 -> 2.72 ms on the 2.1M-triangle bake over
@@ -441,7 +407,7 @@ __global__ void __launch_bounds__(256) k_point_dist(TraceArgs A, const float *__
         S.cur = 0;
         S.sp = 0;
         S.steps = 0;
-        while (step_point<LAYOUT, false>(A, A.job0, S, stack, c0, c1)) {
+        while (step_point_leaves<LAYOUT, false>(A, A.job0, S, stack, c0, c1)) {
         }
         dist[i] = S.best.found ? sqrtf(S.best.d2) : -1.f;
         if (tri) tri[i] = S.best.found ? A.job0.tri_ids[S.best.rec] : -1;
@@ -494,7 +460,7 @@ __global__ void __launch_bounds__(128) k_map_error(TraceArgs A, const uchar4 *__
         S.cur = 0;
         S.sp = 0;
         S.steps = 0;
-        while (step_point<LAYOUT, false>(A, J, S, stack, c0, c1)) {
+        while (step_point_leaves<LAYOUT, false>(A, J, S, stack, c0, c1)) {
         }
         if (!S.best.found) {
             angle[i] = -1.f;

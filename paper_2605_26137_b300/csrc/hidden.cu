@@ -56,13 +56,14 @@ struct VisArgs {
     unsigned long long *counters;
 };
 
+// a node visit whose hit leaf children are recorded in *ls (tested by the caller at the node)
 template <int LAYOUT>
 __device__ __forceinline__ void visit_node(const VisArgs &A, uint32_t idx, const Ray &r, float lim, Next &nx,
-                                           uint2 *stack, int &sp) {
+                                           uint2 *stack, int &sp, LeafSet *ls) {
     if (LAYOUT == AG_BVH_Q8)
-        NodeOps<AG_BVH_Q8>::visit(A.nodes, idx, r, lim, nx, stack, sp, A.status);
+        NodeOps<AG_BVH_Q8>::visit<true>(A.nodes, idx, r, lim, nx, stack, sp, A.status, STACK, ls);
     else
-        NodeOps<AG_BVH_F32>::visit(A.nodes, idx, r, lim, nx, stack, sp, A.status, A.scene_abs);
+        NodeOps<AG_BVH_F32>::visit<true>(A.nodes, idx, r, lim, nx, stack, sp, A.status, A.scene_abs, STACK, ls);
 }
 
 // the direction-dependent part of every ray of a view, once per view
@@ -101,7 +102,8 @@ __device__ __forceinline__ Ray vis_ray(const VisArgs &A, int view, int px, int p
     return ray;
 }
 
-// the closest hit of one visibility ray through the BVH
+// the closest hit of one visibility ray through the BVH (every step a node
+// visit, its hit leaf children tested at the node; the root is always a node)
 template <int LAYOUT, bool COUNT>
 __device__ __forceinline__ Best trace_vis(const VisArgs &A, const Ray &ray, uint2 *stack, unsigned long long &c_nodes,
                                           unsigned long long &c_tris) {
@@ -115,14 +117,17 @@ __device__ __forceinline__ Best trace_vis(const VisArgs &A, const Ray &ray, uint
         nx.has = false;
         nx.ref = 0;
         nx.dist = 0.f;
-        if (ref_is_leaf(cur)) {
-            const uint32_t first = ref_first(cur);
-            const int cnt = ref_count(cur);
+        LeafSet ls;
+        visit_node<LAYOUT>(A, cur, ray, b.babs, nx, stack, sp, &ls);
+        if (COUNT) ++c_nodes;
+        while (ls.mask) {
+            const int c = __ffs(ls.mask) - 1;
+            ls.mask &= ls.mask - 1;
+            uint32_t first;
+            int cnt;
+            leaf_range(ls, c, first, cnt);
             for (int k = 0; k < cnt; ++k) test_tri(ray, A.tris, A.tri_ids, first + k, b);
             if (COUNT) c_tris += cnt;
-        } else {
-            visit_node<LAYOUT>(A, cur, ray, b.babs, nx, stack, sp);
-            if (COUNT) ++c_nodes;
         }
         if (nx.has) {
             cur = nx.ref;

@@ -4,7 +4,7 @@
 //   sort (8-bit digits, stable warp-ranked scatter) -> Karras (2012) binary
 //   hierarchy -> bottom-up FP32 boxes (with the SAH collapse costs) ->
 //   top-down collapse to 8-wide nodes (SAH-optimal children, or greedy
-//   expansion; leaves of <= 2 triangles) with child boxes quantised to 8 bits
+//   expansion; leaves of LEAF_MAX triangles) with child boxes quantised to 8 bits
 //   and rounded outward (or kept in FP32) -> triangles reordered into 48-byte
 //   leaf-order records -> area-weighted vertex normals.
 #include "ag_internal.cuh"
@@ -240,7 +240,10 @@ __global__ void k_karras(const unsigned *__restrict__ k, int64_t n, int2 *__rest
 // Computed in the bottom-up box pass (the second child to arrive computes the
 // parent's box, then its costs).
 constexpr float SAH_NODE = 1.0f;
-constexpr float SAH_TRI = 0.3f;
+#ifndef AG_SAH_TRI
+#define AG_SAH_TRI 0.3f
+#endif
+constexpr float SAH_TRI = AG_SAH_TRI;
 
 __device__ __forceinline__ float box_half_area(float4 lo, float4 hi) {
     const float dx = hi.x - lo.x, dy = hi.y - lo.y, dz = hi.z - lo.z;

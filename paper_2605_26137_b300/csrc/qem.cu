@@ -198,93 +198,62 @@ __global__ void k_quadric_init(const double *__restrict__ V, const int32_t *__re
     for (int k = 0; k < 10; ++k) Q[10 * v + k] = q[k];
 }
 
-// whether vertex u occurs in a face listed before position i of v's list
-__device__ __forceinline__ bool seen_before(const int32_t *F, const int32_t *list, unsigned b, unsigned i, int32_t u) {
-    for (unsigned j = b; j < i; ++j)
-        if (has(F, list[j], u)) return true;
-    return false;
-}
-
-// the distinct higher neighbours (u > a) of vertex a in ascending order, into
-// nb; -1 when there are more than UP_CAP (the callers then take the general
-// scan below)
-constexpr int UP_CAP = 160;
-__device__ __forceinline__ int higher_neighbours(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
-                                                 const int32_t *__restrict__ list, int64_t a, int32_t *nb) {
+// Every vertex's distinct neighbours, sorted ascending, once per round: the
+// segment of vertex a starts at 2 off[a] and has room for 2 deg(a) entries
+// (each incident face adds at most two), nbr_n[a] holds the count and up[a]
+// the count of neighbours above a (the scan input of the ranked edge list).
+// The edge list and the edge validity test read these lists instead of
+// gathering neighbourhoods again.
+constexpr int NB_LOCAL = 192;   // sorted in registers/local memory up to this many, in place beyond
+__global__ void k_nbrs(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
+                       const int32_t *__restrict__ list, int32_t *__restrict__ nbr, unsigned *__restrict__ nbr_n,
+                       unsigned *__restrict__ up) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nv) return;
+    const unsigned b = off[a], e = off[a + 1];
+    int32_t *seg = nbr + 2 * (size_t)b;
+    const unsigned cap = 2 * (e - b);
+    int32_t loc[NB_LOCAL];
+    int32_t *nb = cap <= NB_LOCAL ? loc : seg;
     int n = 0;
-    for (unsigned i = off[a]; i < off[a + 1]; ++i) {
+    for (unsigned i = b; i < e; ++i) {
         const int64_t f = list[i];
         const int32_t tri[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
         for (int k = 0; k < 3; ++k) {
             const int32_t u = tri[k];
-            if (u <= a) continue;
-            int j = n;
-            while (j > 0 && nb[j - 1] > u) --j;
-            if (j > 0 && nb[j - 1] == u) continue;
-            if (n == UP_CAP) return -1;
-            for (int m = n; m > j; --m) nb[m] = nb[m - 1];
-            nb[j] = u;
+            if (u == a) continue;
+            int lo = 0, hi = n;   // insert u into the sorted unique list
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (nb[mid] < u) lo = mid + 1; else hi = mid;
+            }
+            if (lo < n && nb[lo] == u) continue;
+            for (int m = n; m > lo; --m) nb[m] = nb[m - 1];
+            nb[lo] = u;
             ++n;
         }
     }
-    return n;
+    unsigned above = 0;
+    for (int m = 0; m < n; ++m) {
+        if (nb != seg) seg[m] = nb[m];
+        above += nb[m] > a;
+    }
+    nbr_n[a] = (unsigned)n;
+    up[a] = above;
 }
 
-// number of distinct higher neighbours of every vertex
-__global__ void k_upcount(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
-                          const int32_t *__restrict__ list, unsigned *__restrict__ up) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nv) return;
-    int32_t nb[UP_CAP];
-    const int c = higher_neighbours(F, off, list, a, nb);
-    if (c >= 0) {
-        up[a] = (unsigned)c;
-        return;
-    }
-    const unsigned b = off[a], e = off[a + 1];
-    unsigned n = 0;
-    for (unsigned i = b; i < e; ++i) {
-        const int64_t f = list[i];
-        for (int k = 0; k < 3; ++k) {
-            const int32_t u = F[3 * f + k];
-            if (u <= a) continue;
-            bool dup = false;
-            for (int m = 0; m < k; ++m) dup = dup || F[3 * f + m] == u;
-            if (!dup && !seen_before(F, list, b, i, u)) ++n;
-        }
-    }
-    up[a] = n;
-}
-
-// the ranked edge list: the edges (a, u > a) of vertex a at eoff[a], u ascending
-__global__ void k_edges(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
-                        const int32_t *__restrict__ list, const unsigned *__restrict__ eoff,
+// the ranked edge list: the edges (a, u > a) of vertex a at eoff[a], u
+// ascending (the upper part of its sorted neighbour list)
+__global__ void k_edges(int64_t nv, const unsigned *__restrict__ off, const int32_t *__restrict__ nbr,
+                        const unsigned *__restrict__ nbr_n, const unsigned *__restrict__ eoff,
                         int32_t *__restrict__ ea, int32_t *__restrict__ eb) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= nv) return;
-    const unsigned b = off[a], e = off[a + 1], o = eoff[a], n_up = eoff[a + 1] - o;
-    int32_t nb[UP_CAP];
-    const int c = higher_neighbours(F, off, list, a, nb);
-    if (c >= 0) {
-        for (int m = 0; m < c; ++m) { ea[o + m] = (int32_t)a; eb[o + m] = nb[m]; }
-        return;
-    }
-    unsigned n = 0;
-    for (unsigned i = b; i < e; ++i) {
-        const int64_t f = list[i];
-        for (int k = 0; k < 3; ++k) {
-            const int32_t u = F[3 * f + k];
-            if (u <= a) continue;
-            bool dup = false;
-            for (int m = 0; m < k; ++m) dup = dup || F[3 * f + m] == u;
-            if (!dup && !seen_before(F, list, b, i, u)) { ea[o + n] = (int32_t)a; eb[o + n] = u; ++n; }
-        }
-    }
-    for (unsigned i = 1; i < n_up; ++i) {
-        const int32_t x = eb[o + i];
-        unsigned j = i;
-        while (j > 0 && eb[o + j - 1] > x) { eb[o + j] = eb[o + j - 1]; --j; }
-        eb[o + j] = x;
+    const int32_t *seg = nbr + 2 * (size_t)off[a];
+    const unsigned n = nbr_n[a], o = eoff[a], n_up = eoff[a + 1] - o;
+    for (unsigned m = 0; m < n_up; ++m) {
+        ea[o + m] = (int32_t)a;
+        eb[o + m] = seg[n - n_up + m];
     }
 }
 
@@ -299,23 +268,6 @@ __global__ void k_edge_faces(const int32_t *__restrict__ F, const unsigned *__re
     for (unsigned j = off[a]; j < off[a + 1]; ++j) n += has(F, list[j], b);
     nfaces[i] = (uint8_t)(n > 255 ? 255 : n);
     if (n == 1) { bnd[a] = 1; bnd[b] = 1; }
-}
-
-// distinct neighbours of v (not v), up to QEM_MAX_NBR + 1
-__device__ __forceinline__ int neighbours(const int32_t *F, const unsigned *off, const int32_t *list, int32_t v,
-                                          int32_t *out) {
-    int n = 0;
-    for (unsigned j = off[v]; j < off[v + 1]; ++j) {
-        const int64_t f = list[j];
-        for (int k = 0; k < 3; ++k) {
-            const int32_t u = F[3 * f + k];
-            if (u == v) continue;
-            bool seen = false;
-            for (int m = 0; m < n; ++m) seen = seen || out[m] == u;
-            if (!seen && n <= QEM_MAX_NBR) out[n++] = u;
-        }
-    }
-    return n;
 }
 
 // Sign of the turn-over product n_old . n_new of one face, decided in FP32
@@ -360,7 +312,8 @@ __device__ __forceinline__ int turn_sign32(const float *__restrict__ V32, const 
 __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V, const float *__restrict__ V32,
                                                     const int32_t *__restrict__ F,
                                                     const double *__restrict__ Q, const unsigned *__restrict__ off,
-                                                    const int32_t *__restrict__ list, const int32_t *__restrict__ ea,
+                                                    const int32_t *__restrict__ list, const int32_t *__restrict__ nbr,
+                                                    const unsigned *__restrict__ nbr_n, const int32_t *__restrict__ ea,
                                                     const int32_t *__restrict__ eb, const uint8_t *__restrict__ nfaces,
                                                     const uint8_t *__restrict__ bnd, int64_t ne, int placement,
                                                     unsigned long long *__restrict__ key, double *__restrict__ tpos,
@@ -409,13 +362,18 @@ __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V,
         const double t = placement == AG_QEM_MIDPOINT ? 0.5 : qem_place(q, va, vb);
         v = dadd(va, dscl(dsub(vb, va), t));
     }
-    int32_t na_[QEM_MAX_NBR + 1], nb_[QEM_MAX_NBR + 1];
-    const int na = neighbours(F, off, list, a, na_);
-    const int nb = neighbours(F, off, list, b, nb_);
+    // at most QEM_MAX_NBR distinct neighbours per end; the link condition
+    // counts the common ones by merging the two sorted lists
+    const int na = (int)nbr_n[a], nb = (int)nbr_n[b];
     if (na > QEM_MAX_NBR || nb > QEM_MAX_NBR) return;
+    const int32_t *la = nbr + 2 * (size_t)off[a], *lb = nbr + 2 * (size_t)off[b];
     int common = 0;
-    for (int m = 0; m < na; ++m)
-        for (int n = 0; n < nb; ++n) common += na_[m] == nb_[n];
+    for (int m = 0, n = 0; m < na && n < nb;) {
+        const int32_t x = la[m], y = lb[n];
+        common += x == y;
+        m += x <= y;
+        n += y <= x;
+    }
     if (common != nfc) return;
     if (na + nb - common <= 4) return;
     const float3 v32 = make_float3(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z));
@@ -626,6 +584,10 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     AG_CUDA(sc.alloc((void **)&F, sizeof(int32_t) * 3 * nf));
     AG_CUDA(sc.alloc((void **)&remap, sizeof(int32_t) * nv));
     AG_CUDA(sc.alloc((void **)&list, sizeof(int32_t) * 3 * nf));
+    int32_t *nbr;        // per vertex: sorted distinct neighbours (2 deg entries of room)
+    unsigned *nbr_n;     // their count
+    AG_CUDA(sc.alloc((void **)&nbr, sizeof(int32_t) * 6 * nf));
+    AG_CUDA(sc.alloc((void **)&nbr_n, sizeof(unsigned) * nv));
     AG_CUDA(sc.alloc((void **)&ea, sizeof(int32_t) * emax));
     AG_CUDA(sc.alloc((void **)&eb, sizeof(int32_t) * emax));
     AG_CUDA(sc.alloc((void **)&falive, nf));
@@ -692,7 +654,7 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     auto edge_offsets = [&]() -> cudaError_t {
         cudaError_t e;
         if ((e = build_csr()) != cudaSuccess) return e;
-        k_upcount<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff);
+        k_nbrs<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, nbr, nbr_n, eoff);
         return launch_scan_exclusive(eoff, nv, eoff + nv, scan_tmp, s);
     };
     int64_t rounds = 0;
@@ -709,10 +671,10 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
         if ((long long)h_cnt->alive <= target || rounds >= rounds_cap) break;
         const int64_t ne = ne32;
         if (ne == 0) break;
-        k_edges<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, eoff, ea, eb);
+        k_edges<<<blocks(nv, 128), 128, 0, s>>>(nv, off, nbr, nbr_n, eoff, ea, eb);
         AG_CUDA(cudaMemsetAsync(bnd, 0, nv, s));
         k_edge_faces<<<blocks(ne, B), B, 0, s>>>(F, off, list, ea, eb, ne, nfaces, bnd);
-        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, V32, F, Q, off, list, ea, eb, nfaces, bnd, ne, placement, key,
+        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, V32, F, Q, off, list, nbr, nbr_n, ea, eb, nfaces, bnd, ne, placement, key,
                                                     tpos, dirty, eoff_prev, eb_prev, have_prev ? key_prev : nullptr,
                                                     tpos_prev);
         AG_CUDA(cudaMemsetAsync(dirty, 0, nv, s));
