@@ -1055,13 +1055,14 @@ def batch_leg(args, pb, torch, dev, flush):
 def e2e(args, pb, torch, a, W, H, dev, n_rays):
     """Through the public API from pinned HOST buffers: every step uploads the
     high and low meshes, builds the BVH, bakes and reads the three maps back.
-    Steps run two deep on two streams (a serving loop): the build is enqueued
-    without a host round trip (async_build), so step k's uploads and build
-    overlap step k-1's bake and readback; each step's own work stays in order
-    on its stream, and the handle is freed in that order."""
+    Steps run three deep on three streams (a serving loop): the build is
+    enqueued without a host round trip (async_build), so a step's uploads and
+    build overlap the previous steps' bakes and readbacks; each step's own
+    work stays in order on its stream, and the handle is freed in that order.
+    (Two deep measured 4 % slower per asset.)"""
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
            for k, v in (("hv", a.high_v), ("hf", a.high_f), ("lv", a.low_v), ("lf", a.low_f), ("uv", a.low_uv))}
-    depth = 2
+    depth = 3
     slots = [{"stream": torch.cuda.Stream(device=dev),
               "rgba": torch.empty((H, W, 4), dtype=torch.uint8).pin_memory(),
               "mask": torch.empty((H, W), dtype=torch.uint8).pin_memory(),
@@ -1105,8 +1106,8 @@ def e2e(args, pb, torch, a, W, H, dev, n_rays):
     return {"value": n_rays / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_asset": 1e3 * dt, "ms_per_asset_runs": [1e3 * r for r in runs], "steps_per_run": steps,
             "pipeline_depth": depth,
-            "includes": "H2D of both meshes, BVH build (asynchronous), bake, D2H of the three maps, every step; two "
-                        "steps in flight on two streams"}
+            "includes": "H2D of both meshes, BVH build (asynchronous), bake, D2H of the three maps, every step; three "
+                        "steps in flight on three streams"}
 
 
 if __name__ == "__main__":

@@ -204,17 +204,16 @@ __global__ void k_quadric_init(const double *__restrict__ V, const int32_t *__re
 // the count of neighbours above a (the scan input of the ranked edge list).
 // The edge list and the edge validity test read these lists instead of
 // gathering neighbourhoods again.
-constexpr int NB_LOCAL = 192;   // sorted in registers/local memory up to this many, in place beyond
-__global__ void k_nbrs(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
-                       const int32_t *__restrict__ list, int32_t *__restrict__ nbr, unsigned *__restrict__ nbr_n,
-                       unsigned *__restrict__ up) {
-    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nv) return;
-    const unsigned b = off[a], e = off[a + 1];
-    int32_t *seg = nbr + 2 * (size_t)b;
-    const unsigned cap = 2 * (e - b);
-    int32_t loc[NB_LOCAL];
-    int32_t *nb = cap <= NB_LOCAL ? loc : seg;
+// A vertex with more than NB_FAST candidates (two per incident face) is
+// handed to k_nbrs_heavy, which sorts them with a whole warp: sorting
+// hundreds of candidates by insertion in one thread made the few
+// high-valence vertices of the late rounds the kernel's tail.
+constexpr int NB_FAST = 32;
+constexpr int NB_WARP = 1024;   // candidates a warp sorts in shared memory (more: one lane, in place)
+
+// the sorted unique neighbours of a, by insertion, into nb (n of them)
+__device__ __forceinline__ int insert_nbrs(const int32_t *__restrict__ F, const int32_t *__restrict__ list,
+                                           unsigned b, unsigned e, int64_t a, int32_t *nb) {
     int n = 0;
     for (unsigned i = b; i < e; ++i) {
         const int64_t f = list[i];
@@ -233,13 +232,95 @@ __global__ void k_nbrs(const int32_t *__restrict__ F, int64_t nv, const unsigned
             ++n;
         }
     }
+    return n;
+}
+
+__global__ void k_nbrs(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
+                       const int32_t *__restrict__ list, int32_t *__restrict__ nbr, unsigned *__restrict__ nbr_n,
+                       unsigned *__restrict__ up, int32_t *__restrict__ heavy, unsigned *__restrict__ n_heavy) {
+    const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nv) return;
+    const unsigned b = off[a], e = off[a + 1];
+    if (2 * (e - b) > NB_FAST) {
+        heavy[atomicAdd(n_heavy, 1u)] = (int32_t)a;
+        return;
+    }
+    int32_t nb[NB_FAST];
+    const int n = insert_nbrs(F, list, b, e, a, nb);
+    int32_t *seg = nbr + 2 * (size_t)b;
     unsigned above = 0;
     for (int m = 0; m < n; ++m) {
-        if (nb != seg) seg[m] = nb[m];
+        seg[m] = nb[m];
         above += nb[m] > a;
     }
     nbr_n[a] = (unsigned)n;
     up[a] = above;
+}
+
+// one warp per heavy vertex: the candidates (the two other vertices of each
+// incident face) into shared memory, a bitonic sort, then the first of each
+// run of equal ids written out in order
+__global__ void __launch_bounds__(128) k_nbrs_heavy(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
+                                                   const int32_t *__restrict__ list,
+                                                   const int32_t *__restrict__ heavy,
+                                                   const unsigned *__restrict__ n_heavy, int32_t *__restrict__ nbr,
+                                                   unsigned *__restrict__ nbr_n, unsigned *__restrict__ up) {
+    __shared__ int32_t buf[4][NB_WARP];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned nh = *n_heavy;
+    int32_t *sb = buf[warp];
+    for (unsigned h = blockIdx.x * 4u + (unsigned)warp; h < nh; h += gridDim.x * 4u) {
+        const int64_t a = heavy[h];
+        const unsigned b = off[a], e = off[a + 1], deg = e - b, nc = 2 * deg;
+        int32_t *seg = nbr + 2 * (size_t)b;
+        if (nc > (unsigned)NB_WARP) {
+            if (lane == 0) {
+                const int n = insert_nbrs(F, list, b, e, a, seg);
+                unsigned above = 0;
+                for (int m = 0; m < n; ++m) above += seg[m] > a;
+                nbr_n[a] = (unsigned)n;
+                up[a] = above;
+            }
+            __syncwarp();
+            continue;
+        }
+        for (unsigned i = lane; i < deg; i += 32) {
+            const int64_t f = list[b + i];
+            const int32_t x = F[3 * f], y = F[3 * f + 1], z = F[3 * f + 2];
+            sb[2 * i] = x == a ? y : x;
+            sb[2 * i + 1] = z == a ? y : z;
+        }
+        unsigned P = 32;
+        while (P < nc) P <<= 1;
+        for (unsigned i = nc + lane; i < P; i += 32) sb[i] = 0x7fffffff;
+        __syncwarp();
+        for (unsigned k = 2; k <= P; k <<= 1)
+            for (unsigned j = k >> 1; j > 0; j >>= 1) {
+                for (unsigned i = lane; i < P; i += 32) {
+                    const unsigned ixj = i ^ j;
+                    if (ixj > i) {
+                        const int32_t x = sb[i], y = sb[ixj];
+                        if ((x > y) == ((i & k) == 0)) { sb[i] = y; sb[ixj] = x; }
+                    }
+                }
+                __syncwarp();
+            }
+        unsigned n = 0, above = 0;
+        for (unsigned base = 0; base < nc; base += 32) {
+            const unsigned i = base + lane;
+            const bool keep = i < nc && (i == 0 || sb[i] != sb[i - 1]);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) seg[n + __popc(bal & lt)] = sb[i];
+            above += __popc(__ballot_sync(0xffffffffu, keep && sb[i] > a));
+            n += __popc(bal);
+        }
+        if (lane == 0) {
+            nbr_n[a] = n;
+            up[a] = above;
+        }
+        __syncwarp();
+    }
 }
 
 // the ranked edge list: the edges (a, u > a) of vertex a at eoff[a], u
@@ -586,8 +667,12 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     AG_CUDA(sc.alloc((void **)&list, sizeof(int32_t) * 3 * nf));
     int32_t *nbr;        // per vertex: sorted distinct neighbours (2 deg entries of room)
     unsigned *nbr_n;     // their count
+    int32_t *heavy;      // vertices whose lists a whole warp sorts
+    unsigned *n_heavy;
     AG_CUDA(sc.alloc((void **)&nbr, sizeof(int32_t) * 6 * nf));
     AG_CUDA(sc.alloc((void **)&nbr_n, sizeof(unsigned) * nv));
+    AG_CUDA(sc.alloc((void **)&heavy, sizeof(int32_t) * nv));
+    AG_CUDA(sc.alloc((void **)&n_heavy, sizeof(unsigned)));
     AG_CUDA(sc.alloc((void **)&ea, sizeof(int32_t) * emax));
     AG_CUDA(sc.alloc((void **)&eb, sizeof(int32_t) * emax));
     AG_CUDA(sc.alloc((void **)&falive, nf));
@@ -654,7 +739,10 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     auto edge_offsets = [&]() -> cudaError_t {
         cudaError_t e;
         if ((e = build_csr()) != cudaSuccess) return e;
-        k_nbrs<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, nbr, nbr_n, eoff);
+        if ((e = cudaMemsetAsync(n_heavy, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+        k_nbrs<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, nbr, nbr_n, eoff, heavy, n_heavy);
+        k_nbrs_heavy<<<(unsigned)device_sm_count(dev) * 4, 128, 0, s>>>(F, off, list, heavy, n_heavy, nbr, nbr_n,
+                                                                          eoff);
         return launch_scan_exclusive(eoff, nv, eoff + nv, scan_tmp, s);
     };
     int64_t rounds = 0;
