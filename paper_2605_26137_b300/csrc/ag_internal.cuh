@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "ag.h"
 
@@ -35,6 +36,20 @@ ag_status cuda_error(cudaError_t e, const char *what);
         cudaError_t e_ = cudaGetLastError();                       \
         if (e_ != cudaSuccess) return ag::cuda_error(e_, what);    \
     } while (0)
+
+// ------------------------------------------------------------------ side streams
+// N_SIDE library-owned non-blocking streams per device, created on first use
+// and kept for the process; fork_to makes the first n_used of them wait for
+// what is enqueued on s so far, join_from makes s wait for what they hold.
+constexpr int N_SIDE = 8;
+cudaError_t side_streams(int dev, cudaStream_t **out);
+struct EventSet {   // events of one call's edges, destroyed with it
+    std::vector<cudaEvent_t> ev;
+    ~EventSet();
+    cudaError_t make(cudaEvent_t *e);
+};
+cudaError_t fork_to(cudaStream_t s, cudaStream_t *side, int n_used, EventSet &es);
+cudaError_t join_from(cudaStream_t s, cudaStream_t *side, int n_used, EventSet &es);
 
 unsigned *device_status_word(int device);      // 1 word per device, zero-initialised
 cudaMemPool_t device_pool(int device);         // library-private stream-ordered pool
@@ -183,11 +198,18 @@ cudaError_t launch_vertex_normals(const float *V, const int32_t *F, int64_t nv, 
 // as the vertex normals; faces with an out-of-range index are left out
 cudaError_t launch_vertex_face_csr(const int32_t *F, int64_t nf, int64_t nv, void *scratch, const unsigned **off,
                                    const int32_t **list, cudaStream_t s);
+// face set-up of the low mesh in two parts: the UV part (snapped corners and
+// twice the signed snapped area, zeros for a dropped face; all the raster
+// needs) and the frame part (needs the vertex normals: face flags and the
+// corner tangent frames); launch_face_setup runs both in order
+cudaError_t launch_uv_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W, int H,
+                            int4 *uvfix, unsigned *status, cudaStream_t s);
+cudaError_t launch_tangents(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, const int4 *uvfix,
+                            const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan, cudaStream_t s);
 cudaError_t launch_face_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W,
                               int H, const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan,
                               int4 *uvfix, unsigned *status, cudaStream_t s);
-cudaError_t launch_raster(const int4 *uvfix, const int4 *lface, int64_t nf, int W, int H,
-                          unsigned long long *keys, cudaStream_t s);
+cudaError_t launch_raster(const int4 *uvfix, int64_t nf, int W, int H, unsigned long long *keys, cudaStream_t s);
 cudaError_t launch_resolve(const unsigned long long *keys, const int4 *uvfix, int W, int H,
                            int ray_tile, int32_t *face_map, float *aux_bary, int4 *rays,
                            long long *n_rays, cudaStream_t s);

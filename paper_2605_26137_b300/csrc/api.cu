@@ -199,11 +199,22 @@ ag_status alloc_asset(Scratch &sc, int64_t nv, int64_t nf, int W, int H, bool ow
 
 ag_status run_prep(const float *lv, const float *ln, const float *luv, const int32_t *lf, int64_t nv, int64_t nf,
                    int W, int H, int ray_tile, float *aux_bary, unsigned *status, AssetScratch &a, cudaStream_t s) {
+    // the UV set-up, raster and resolve (texel -> face) stay on s; the low
+    // mesh's vertex normals and corner frames, needed only by the traversal,
+    // run beside them on a side stream and join s before it returns
+    int dev = 0;
+    AG_CUDA(cudaGetDevice(&dev));
+    cudaStream_t *side = nullptr;
+    AG_CUDA(side_streams(dev, &side));
+    AG_CUDA(launch_uv_setup(luv, lf, nf, nv, W, H, a.uvfix, status, s));
+    EventSet es;
+    AG_CUDA(fork_to(s, side, 1, es));
+    AG_CUDA(launch_vertex_normals(lv, lf, nv, nf, ln, a.acc, a.lnrm, a.lpos, a.nscr, side[0]));
+    AG_CUDA(launch_tangents(luv, lf, nf, nv, a.uvfix, a.lpos, a.lnrm, a.lface, a.ltan, side[0]));
     AG_CUDA(cudaMemsetAsync(a.n_rays, 0, sizeof(long long) * 2, s));
-    AG_CUDA(launch_vertex_normals(lv, lf, nv, nf, ln, a.acc, a.lnrm, a.lpos, a.nscr, s));
-    AG_CUDA(launch_face_setup(luv, lf, nf, nv, W, H, a.lpos, a.lnrm, a.lface, a.ltan, a.uvfix, status, s));
-    AG_CUDA(launch_raster(a.uvfix, a.lface, nf, W, H, a.keys, s));
+    AG_CUDA(launch_raster(a.uvfix, nf, W, H, a.keys, s));
     AG_CUDA(launch_resolve(a.keys, a.uvfix, W, H, ray_tile, a.face, aux_bary, a.rays, a.n_rays, s));
+    AG_CUDA(join_from(s, side, 1, es));
     return AG_OK;
 }
 

@@ -141,59 +141,6 @@ void fill_tables(int n, const ag_asset_desc *d, const std::vector<AssetBufs> &b,
     }
 }
 
-// Library-owned side streams of a device: the batch forks each asset's prep
-// and finalize onto them so the small per-asset kernels overlap (captured,
-// they become independent branches of the graph).
-constexpr int N_SIDE = 8;
-std::mutex g_side_mu;
-cudaStream_t g_side[64][N_SIDE] = {};
-
-cudaError_t side_streams(int dev, cudaStream_t **out) {
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_side_mu);
-    if (!g_side[dev][0]) {
-        for (int k = 0; k < N_SIDE; ++k) {
-            cudaError_t e = cudaStreamCreateWithFlags(&g_side[dev][k], cudaStreamNonBlocking);
-            if (e != cudaSuccess) return e;
-        }
-    }
-    *out = g_side[dev];
-    return cudaSuccess;
-}
-
-struct EventSet {
-    std::vector<cudaEvent_t> ev;
-    ~EventSet() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-    }
-    cudaError_t make(cudaEvent_t *e) {
-        cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
-        if (r == cudaSuccess) ev.push_back(*e);
-        return r;
-    }
-};
-
-// s waits for nothing new; every side stream that is used waits for s (fork)
-cudaError_t fork_to(cudaStream_t s, cudaStream_t *side, int n_used, EventSet &es) {
-    cudaEvent_t f;
-    cudaError_t e = es.make(&f);
-    if (e == cudaSuccess) e = cudaEventRecord(f, s);
-    for (int k = 0; k < n_used && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(side[k], f, 0);
-    return e;
-}
-
-// s waits for every used side stream (join)
-cudaError_t join_from(cudaStream_t s, cudaStream_t *side, int n_used, EventSet &es) {
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < n_used && e == cudaSuccess; ++k) {
-        cudaEvent_t j;
-        e = es.make(&j);
-        if (e == cudaSuccess) e = cudaEventRecord(j, side[k]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, j, 0);
-    }
-    return e;
-}
-
 // enqueue the whole batch on s (capturable: kernels, memsets and event edges)
 ag_status enqueue_batch(int n, const ag_asset_desc *d, const ag_opts &o, int layout, const std::vector<AssetBufs> &b,
                         const TraceJob *host_jobs, const TraceJob *jobs, long long *begin,
@@ -212,7 +159,7 @@ ag_status enqueue_batch(int n, const ag_asset_desc *d, const ag_opts &o, int lay
                                       x.lnrm, x.lpos, x.nscr, q));
         AG_CUDA(launch_face_setup(d[a].luv, d[a].lfaces, d[a].n_lfaces, d[a].n_lverts, d[a].W, d[a].H, x.lpos, x.lnrm,
                                   x.lface, x.ltan, x.uvfix, status, q));
-        AG_CUDA(launch_raster(x.uvfix, x.lface, d[a].n_lfaces, d[a].W, d[a].H, x.keys, q));
+        AG_CUDA(launch_raster(x.uvfix, d[a].n_lfaces, d[a].W, d[a].H, x.keys, q));
         AG_CUDA(launch_resolve(x.keys, x.uvfix, d[a].W, d[a].H, o.ray_tile, x.face, nullptr, x.rays, x.n_rays, q));
     }
     AG_CUDA(join_from(s, side, used, es));

@@ -26,27 +26,34 @@ __device__ __forceinline__ long long snap_exact(float u, int W) {
     return (bits >> 31) ? -(long long)r : (long long)r;
 }
 
-__global__ void k_face_setup(const float *__restrict__ uv, const int32_t *__restrict__ F, int64_t nf, int64_t nv,
-                             int W, int H, const float4 *__restrict__ lpos, const float4 *__restrict__ lnrm,
-                             int4 *__restrict__ lface, float4 *__restrict__ ltan, int4 *__restrict__ uvfix,
-                             unsigned *__restrict__ status) {
-    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf) return;
-    int32_t id[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
-    float u[3], v[3];
-    bool bad = false;
+// A face is dropped (FACE_INVALID) when a UV is NaN or outside [-1, 2] or an
+// index is out of range.
+__device__ __forceinline__ bool face_ok(const float *__restrict__ uv, const int32_t *__restrict__ F, int64_t f,
+                                        int64_t nv, int32_t id[3], float u[3], float v[3]) {
+    bool ok = true;
     for (int k = 0; k < 3; ++k) {
+        id[k] = F[3 * f + k];
         u[k] = uv[6 * f + 2 * k];
         v[k] = uv[6 * f + 2 * k + 1];
-        if (!(u[k] >= -1.f && u[k] <= 2.f && v[k] >= -1.f && v[k] <= 2.f)) bad = true;
-        if (id[k] < 0 || id[k] >= nv) bad = true;
+        if (!(u[k] >= -1.f && u[k] <= 2.f && v[k] >= -1.f && v[k] <= 2.f)) ok = false;
+        if (id[k] < 0 || id[k] >= nv) ok = false;
     }
-    if (bad) {
+    return ok;
+}
+
+// UV side of the face set-up, all the raster needs: the snapped corners and
+// twice the signed snapped area (a dropped face gets zeros, so it rasterises
+// nothing).
+__global__ void k_uv_setup(const float *__restrict__ uv, const int32_t *__restrict__ F, int64_t nf, int64_t nv,
+                           int W, int H, int4 *__restrict__ uvfix, unsigned *__restrict__ status) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int32_t id[3];
+    float u[3], v[3];
+    if (!face_ok(uv, F, f, nv, id, u, v)) {
         atomicOr(status, AGS_BAD_UV);
-        lface[f] = make_int4(0, 0, 0, FACE_INVALID);
         uvfix[2 * f] = make_int4(0, 0, 0, 0);
         uvfix[2 * f + 1] = make_int4(0, 0, 0, 0);
-        for (int k = 0; k < 3; ++k) ltan[3 * f + k] = make_float4(1.f, 0.f, 0.f, 1.f);
         return;
     }
     long long X[3], Y[3];
@@ -55,6 +62,27 @@ __global__ void k_face_setup(const float *__restrict__ uv, const int32_t *__rest
         Y[k] = snap_exact(v[k], H);
     }
     long long a2 = (X[1] - X[0]) * (Y[2] - Y[0]) - (Y[1] - Y[0]) * (X[2] - X[0]);
+    uvfix[2 * f] = make_int4((int)X[0], (int)Y[0], (int)X[1], (int)Y[1]);
+    uvfix[2 * f + 1] = make_int4((int)X[2], (int)Y[2], (int)(unsigned)(a2 & 0xffffffffll), (int)(a2 >> 32));
+}
+
+// Frame side of the face set-up (needs the vertex normals): per face the
+// reliability flag and the corner tangent frames from the snapped UVs.
+__global__ void k_tangents(const float *__restrict__ uv, const int32_t *__restrict__ F, int64_t nf, int64_t nv,
+                           const int4 *__restrict__ uvfix, const float4 *__restrict__ lpos,
+                           const float4 *__restrict__ lnrm, int4 *__restrict__ lface, float4 *__restrict__ ltan) {
+    int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int32_t id[3];
+    float u[3], v[3];
+    if (!face_ok(uv, F, f, nv, id, u, v)) {
+        lface[f] = make_int4(0, 0, 0, FACE_INVALID);
+        for (int k = 0; k < 3; ++k) ltan[3 * f + k] = make_float4(1.f, 0.f, 0.f, 1.f);
+        return;
+    }
+    const int4 q0 = uvfix[2 * f], q1 = uvfix[2 * f + 1];
+    const long long X[3] = {q0.x, q0.z, q1.x}, Y[3] = {q0.y, q0.w, q1.y};
+    const long long a2 = (long long)(((unsigned long long)(unsigned)q1.w << 32) | (unsigned long long)(unsigned)q1.z);
     int flags = (a2 <= 13 && a2 >= -13) ? FACE_DEGEN : 0;
     float3 p0 = f3(lpos[id[0]]), p1 = f3(lpos[id[1]]), p2 = f3(lpos[id[2]]);
     float3 l1, l2;
@@ -89,8 +117,6 @@ __global__ void k_face_setup(const float *__restrict__ uv, const int32_t *__rest
     float w = hs < 0.f ? -1.f : 1.f;
     for (int k = 0; k < 3; ++k) ltan[3 * f + k] = make_float4(T[k].x, T[k].y, T[k].z, w);
     lface[f] = make_int4(id[0], id[1], id[2], flags);
-    uvfix[2 * f] = make_int4((int)X[0], (int)Y[0], (int)X[1], (int)Y[1]);
-    uvfix[2 * f + 1] = make_int4((int)X[2], (int)Y[2], (int)(unsigned)(a2 & 0xffffffffll), (int)(a2 >> 32));
 }
 
 // Snapped UV triangle: coordinates fit in 24 bits, so differences fit in 32
@@ -187,12 +213,12 @@ __device__ unsigned long long tri_qdist(const UvTri &t, int cx, int cy, int *be,
 __device__ __forceinline__ int floordiv256(int a) { return a >> 8; }  // arithmetic shift = floor
 
 // one warp per face: every texel within one texel of the face's UV bbox
-__global__ void k_raster(const int4 *__restrict__ uvfix, const int4 *__restrict__ lface, int64_t nf, int W, int H,
+// (a dropped face has zero snapped area and is skipped like a zero-area one)
+__global__ void k_raster(const int4 *__restrict__ uvfix, int64_t nf, int W, int H,
                          unsigned long long *__restrict__ keys) {
     int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (f >= nf) return;
-    if (lface[f].w & FACE_INVALID) return;
     UvTri t = load_uvtri(uvfix, f);
     if (t.a2 == 0) return;
     int mnx = min(t.X[0], min(t.X[1], t.X[2])), mxx = max(t.X[0], max(t.X[1], t.X[2]));
@@ -295,18 +321,30 @@ inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 
 
 }  // namespace
 
-cudaError_t launch_face_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W, int H,
-                              const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan, int4 *uvfix,
-                              unsigned *status, cudaStream_t s) {
-    k_face_setup<<<grid_for(nf, 128), 128, 0, s>>>(luv, lfaces, nf, nv, W, H, lpos, lnrm, lface, ltan, uvfix, status);
+cudaError_t launch_uv_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W, int H,
+                            int4 *uvfix, unsigned *status, cudaStream_t s) {
+    k_uv_setup<<<grid_for(nf, 128), 128, 0, s>>>(luv, lfaces, nf, nv, W, H, uvfix, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_raster(const int4 *uvfix, const int4 *lface, int64_t nf, int W, int H, unsigned long long *keys,
-                          cudaStream_t s) {
+cudaError_t launch_tangents(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, const int4 *uvfix,
+                            const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan, cudaStream_t s) {
+    k_tangents<<<grid_for(nf, 128), 128, 0, s>>>(luv, lfaces, nf, nv, uvfix, lpos, lnrm, lface, ltan);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face_setup(const float *luv, const int32_t *lfaces, int64_t nf, int64_t nv, int W, int H,
+                              const float4 *lpos, const float4 *lnrm, int4 *lface, float4 *ltan, int4 *uvfix,
+                              unsigned *status, cudaStream_t s) {
+    cudaError_t e = launch_uv_setup(luv, lfaces, nf, nv, W, H, uvfix, status, s);
+    if (e != cudaSuccess) return e;
+    return launch_tangents(luv, lfaces, nf, nv, uvfix, lpos, lnrm, lface, ltan, s);
+}
+
+cudaError_t launch_raster(const int4 *uvfix, int64_t nf, int W, int H, unsigned long long *keys, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(keys, 0xff, sizeof(unsigned long long) * (size_t)W * H, s);
     if (e != cudaSuccess) return e;
-    k_raster<<<grid_for(nf * 32, 256), 256, 0, s>>>(uvfix, lface, nf, W, H, keys);
+    k_raster<<<grid_for(nf * 32, 256), 256, 0, s>>>(uvfix, nf, W, H, keys);
     return cudaGetLastError();
 }
 
