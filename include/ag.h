@@ -444,7 +444,9 @@ AG_API ag_status ag_exterior_fill(const float *d_verts, int64_t n_verts, const i
  *   h_result[0] vertices and h_result[1] faces are written.
  *   d_keep_verts (optional) [n_verts] i32: original id of each output vertex.
  *   h_result [3] (host): output vertices, output faces, rounds.
- *   Synchronises `stream` once per round.  Faces with an out-of-range index
+ *   Synchronises `stream` once every eight rounds (the decision to stop is
+ *   taken on the device; up to seven rounds past the end are enqueued and
+ *   return at once) and at the end.  Faces with an out-of-range index
  *   are dropped and set AG_ERR_INVALID_ARG in the status word.
  */
 enum { AG_QEM_OPTIMAL = 0, AG_QEM_MIDPOINT = 1 };

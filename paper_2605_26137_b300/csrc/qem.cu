@@ -10,31 +10,38 @@
 // positions are decided exactly as the same expressions evaluate on any
 // IEEE machine.
 //
-// A round (all kernels, stream-ordered; the host reads three counters at the
-// end of each round to decide whether to go on):
-//   1. vertex -> alive face adjacency (degree, scan, fill);
+// A round (all kernels, stream-ordered; the host enqueues eight rounds at a
+// time and reads the round control back after them: a one-thread kernel at
+// the top of each round decides on the device whether it runs, and every
+// kernel of a round that does not run returns at once):
+//   1. vertex -> alive face adjacency (degrees counted while the last round
+//      rewrote the faces, scan, fill);
 //   2. the unique edges a < b, ranked in (a, b) order: every vertex lists its
-//      distinct higher neighbours, an exclusive scan places them, each
-//      segment is sorted;
-//   3. faces per edge; boundary vertices (on an edge with one face);
-//   4. per edge: placement, cost E(v), validity (at most two faces, at most
+//      distinct neighbours, sorted, with the faces of each edge (their
+//      multiplicity in the list); boundary vertices (on an edge with one
+//      face); an exclusive scan of the higher neighbours places the edges;
+//   3. per edge: placement, cost E(v), validity (at most two faces, at most
 //      64 neighbours per endpoint, link condition, no tetrahedron, no
 //      surviving face turning over), key = float32 cost bits << 32 | rank;
-//   5. m1(v) = min key at v, m2(v) = min of m1 over v and its neighbours; an
+//   4. m1(v) = min key at v, m2(v) = min of m1 over v and its neighbours; an
 //      edge collapses when its key equals m2 at both ends (such edges never
 //      touch adjacent vertices, so their collapses are independent);
-//   6. if collapsing all of them would pass the target, only the smallest
+//   5. if collapsing all of them would pass the target, only the smallest
 //      keys that reach it (a one-block binary search over the selected keys);
-//   7. collapse: keep a at v with Q_a + Q_b, rename b to a, drop the faces
+//   6. collapse: keep a at v with Q_a + Q_b, rename b to a, drop the faces
 //      that held both.
 #include "ag_internal.cuh"
 
+#include <algorithm>
 #include <cstring>
 
 namespace ag {
 namespace {
 
 constexpr int QEM_MAX_NBR = 64;
+constexpr int ROUNDS_AHEAD = 8;   // rounds enqueued per host read of the round control
+constexpr int64_t COMPACT_MIN = 4096;   // no renumbering below this many working faces
+constexpr int TURN_CHUNK = 4;           // faces per step of the turn-over test
 constexpr unsigned long long KEY_NONE = ~0ull;
 
 struct D3 {
@@ -125,6 +132,38 @@ struct Counters {
     int pad;
 };
 
+// Round control, on the device: the host enqueues rounds ahead and reads
+// this back every few rounds; once `done` is set every later kernel returns
+// at once.
+struct Control {
+    long long rounds;   // rounds that ran (a last round that selected nothing is taken back)
+    long long ne;       // edges of the current round
+    int done;
+    int pad;
+};
+
+// Decides whether the round runs: not when the last round selected nothing
+// (it changed nothing, so it is not counted), nor once the alive faces are at
+// or below the target, the round cap is reached or no edge is left.
+__global__ void k_round_begin(Control *ctl, Counters *cnt, const unsigned *__restrict__ ne_total, long long target,
+                              long long cap) {
+    if (threadIdx.x != 0 || ctl->done) return;
+    if (ctl->rounds > 0 && cnt->nsel == 0) {
+        ctl->rounds -= 1;
+        ctl->done = 1;
+        return;
+    }
+    const long long ne = *ne_total;
+    if ((long long)cnt->alive <= target || ctl->rounds >= cap || ne == 0) {
+        ctl->done = 1;
+        return;
+    }
+    ctl->rounds += 1;
+    ctl->ne = ne;
+    cnt->removable = 0;
+    cnt->nsel = 0;
+}
+
 __global__ void k_init_faces(const int32_t *__restrict__ Fin, int64_t nf, int64_t nv, int32_t *__restrict__ F,
                              uint8_t *__restrict__ falive, uint8_t *__restrict__ valive, Counters *cnt,
                              unsigned *status) {
@@ -162,10 +201,11 @@ __global__ void k_deg(const int32_t *__restrict__ F, const uint8_t *__restrict__
     for (int k = 0; k < 3; ++k) atomicAdd(&deg[F[3 * f + k]], 1u);
 }
 
-__global__ void k_fill(const int32_t *__restrict__ F, const uint8_t *__restrict__ falive, int64_t nf,
-                       const unsigned *__restrict__ off, unsigned *__restrict__ fill, int32_t *__restrict__ list) {
+__global__ void k_fill(const Control *__restrict__ ctl, const int32_t *__restrict__ F,
+                       const uint8_t *__restrict__ falive, int64_t nf, const unsigned *__restrict__ off,
+                       unsigned *__restrict__ fill, int32_t *__restrict__ list) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf || !falive[f]) return;
+    if (f >= nf || (ctl && ctl->done) || !falive[f]) return;
     for (int k = 0; k < 3; ++k) {
         const int32_t v = F[3 * f + k];
         list[off[v] + atomicAdd(&fill[v], 1u)] = (int32_t)f;
@@ -211,9 +251,12 @@ __global__ void k_quadric_init(const double *__restrict__ V, const int32_t *__re
 constexpr int NB_FAST = 32;
 constexpr int NB_WARP = 1024;   // candidates a warp sorts in shared memory (more: one lane, in place)
 
-// the sorted unique neighbours of a, by insertion, into nb (n of them)
+// the sorted unique neighbours of a, by insertion, into nb (n of them), and
+// in mult how many of a's faces hold each (the faces of that edge, capped
+// at 255)
+template <typename M>
 __device__ __forceinline__ int insert_nbrs(const int32_t *__restrict__ F, const int32_t *__restrict__ list,
-                                           unsigned b, unsigned e, int64_t a, int32_t *nb) {
+                                           unsigned b, unsigned e, int64_t a, int32_t *nb, M *mult) {
     int n = 0;
     for (unsigned i = b; i < e; ++i) {
         const int64_t f = list[i];
@@ -226,46 +269,65 @@ __device__ __forceinline__ int insert_nbrs(const int32_t *__restrict__ F, const 
                 const int mid = (lo + hi) >> 1;
                 if (nb[mid] < u) lo = mid + 1; else hi = mid;
             }
-            if (lo < n && nb[lo] == u) continue;
-            for (int m = n; m > lo; --m) nb[m] = nb[m - 1];
+            if (lo < n && nb[lo] == u) {
+                if (mult[lo] < 255) mult[lo] = mult[lo] + 1;
+                continue;
+            }
+            for (int m = n; m > lo; --m) {
+                nb[m] = nb[m - 1];
+                mult[m] = mult[m - 1];
+            }
             nb[lo] = u;
+            mult[lo] = 1;
             ++n;
         }
     }
     return n;
 }
 
-__global__ void k_nbrs(const int32_t *__restrict__ F, int64_t nv, const unsigned *__restrict__ off,
-                       const int32_t *__restrict__ list, int32_t *__restrict__ nbr, unsigned *__restrict__ nbr_n,
-                       unsigned *__restrict__ up, int32_t *__restrict__ heavy, unsigned *__restrict__ n_heavy) {
+// Besides the list: nbr_m, the faces of each edge (a, u), and bnd[a], whether
+// a lies on an edge with one face (a boundary vertex).
+__global__ void k_nbrs(const Control *__restrict__ ctl, const int32_t *__restrict__ F, int64_t nv,
+                       const unsigned *__restrict__ off, const int32_t *__restrict__ list, int32_t *__restrict__ nbr,
+                       uint8_t *__restrict__ nbr_m, unsigned *__restrict__ nbr_n, unsigned *__restrict__ up,
+                       uint8_t *__restrict__ bnd, int32_t *__restrict__ heavy, unsigned *__restrict__ n_heavy) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nv) return;
+    if (a >= nv || (ctl && ctl->done)) return;
     const unsigned b = off[a], e = off[a + 1];
     if (2 * (e - b) > NB_FAST) {
         heavy[atomicAdd(n_heavy, 1u)] = (int32_t)a;
         return;
     }
     int32_t nb[NB_FAST];
-    const int n = insert_nbrs(F, list, b, e, a, nb);
+    uint8_t mult[NB_FAST];
+    const int n = insert_nbrs(F, list, b, e, a, nb, mult);
     int32_t *seg = nbr + 2 * (size_t)b;
+    uint8_t *segm = nbr_m + 2 * (size_t)b;
     unsigned above = 0;
+    bool border = false;
     for (int m = 0; m < n; ++m) {
         seg[m] = nb[m];
+        segm[m] = mult[m];
         above += nb[m] > a;
+        border |= mult[m] == 1;
     }
     nbr_n[a] = (unsigned)n;
     up[a] = above;
+    bnd[a] = border;
 }
 
 // one warp per heavy vertex: the candidates (the two other vertices of each
 // incident face) into shared memory, a bitonic sort, then the first of each
 // run of equal ids written out in order
-__global__ void __launch_bounds__(128) k_nbrs_heavy(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
+__global__ void __launch_bounds__(128) k_nbrs_heavy(const Control *__restrict__ ctl, const int32_t *__restrict__ F,
+                                                   const unsigned *__restrict__ off,
                                                    const int32_t *__restrict__ list,
                                                    const int32_t *__restrict__ heavy,
                                                    const unsigned *__restrict__ n_heavy, int32_t *__restrict__ nbr,
-                                                   unsigned *__restrict__ nbr_n, unsigned *__restrict__ up) {
+                                                   uint8_t *__restrict__ nbr_m, unsigned *__restrict__ nbr_n,
+                                                   unsigned *__restrict__ up, uint8_t *__restrict__ bnd) {
     __shared__ int32_t buf[4][NB_WARP];
+    if (ctl && ctl->done) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const unsigned nh = *n_heavy;
@@ -274,13 +336,19 @@ __global__ void __launch_bounds__(128) k_nbrs_heavy(const int32_t *__restrict__ 
         const int64_t a = heavy[h];
         const unsigned b = off[a], e = off[a + 1], deg = e - b, nc = 2 * deg;
         int32_t *seg = nbr + 2 * (size_t)b;
+        uint8_t *segm = nbr_m + 2 * (size_t)b;
         if (nc > (unsigned)NB_WARP) {
             if (lane == 0) {
-                const int n = insert_nbrs(F, list, b, e, a, seg);
+                const int n = insert_nbrs(F, list, b, e, a, seg, segm);
                 unsigned above = 0;
-                for (int m = 0; m < n; ++m) above += seg[m] > a;
+                bool border = false;
+                for (int m = 0; m < n; ++m) {
+                    above += seg[m] > a;
+                    border |= segm[m] == 1;
+                }
                 nbr_n[a] = (unsigned)n;
                 up[a] = above;
+                bnd[a] = border;
             }
             __syncwarp();
             continue;
@@ -307,48 +375,59 @@ __global__ void __launch_bounds__(128) k_nbrs_heavy(const int32_t *__restrict__ 
                 __syncwarp();
             }
         unsigned n = 0, above = 0;
+        bool border = false;
         for (unsigned base = 0; base < nc; base += 32) {
             const unsigned i = base + lane;
             const bool keep = i < nc && (i == 0 || sb[i] != sb[i - 1]);
+            unsigned run = 0;   // the length of the run of equal ids that starts at i
+            if (keep)
+                while (i + run < nc && sb[i + run] == sb[i]) ++run;
             const unsigned bal = __ballot_sync(0xffffffffu, keep);
-            if (keep) seg[n + __popc(bal & lt)] = sb[i];
+            if (keep) {
+                seg[n + __popc(bal & lt)] = sb[i];
+                segm[n + __popc(bal & lt)] = (uint8_t)(run > 255 ? 255 : run);
+            }
             above += __popc(__ballot_sync(0xffffffffu, keep && sb[i] > a));
+            border |= __any_sync(0xffffffffu, keep && run == 1);
             n += __popc(bal);
         }
         if (lane == 0) {
             nbr_n[a] = n;
             up[a] = above;
+            bnd[a] = border;
         }
         __syncwarp();
     }
 }
 
-// the ranked edge list: the edges (a, u > a) of vertex a at eoff[a], u
-// ascending (the upper part of its sorted neighbour list)
-__global__ void k_edges(int64_t nv, const unsigned *__restrict__ off, const int32_t *__restrict__ nbr,
+// The ranked edge list: the edges (a, u > a) of vertex a at eoff[a], u
+// ascending (the upper part of its sorted neighbour list), with the faces of
+// each edge. The same pass clears the per-vertex state this round builds:
+// the two-ring minima, the marks for the next round, and the next
+// adjacency's degree and fill counters.
+__global__ void k_edges(const Control *__restrict__ ctl, int64_t nv, const unsigned *__restrict__ off,
+                        const int32_t *__restrict__ nbr, const uint8_t *__restrict__ nbr_m,
                         const unsigned *__restrict__ nbr_n, const unsigned *__restrict__ eoff,
-                        int32_t *__restrict__ ea, int32_t *__restrict__ eb) {
+                        int32_t *__restrict__ ea, int32_t *__restrict__ eb, uint8_t *__restrict__ nfaces,
+                        unsigned long long *__restrict__ m1, unsigned long long *__restrict__ m2,
+                        uint8_t *__restrict__ dirty_next, unsigned *__restrict__ deg_next,
+                        unsigned *__restrict__ fill, unsigned *__restrict__ n_heavy) {
     const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= nv) return;
+    if (a >= nv || ctl->done) return;
+    m1[a] = KEY_NONE;
+    m2[a] = KEY_NONE;
+    dirty_next[a] = 0;
+    deg_next[a] = 0;
+    fill[a] = 0;
+    if (a == 0) *n_heavy = 0;
     const int32_t *seg = nbr + 2 * (size_t)off[a];
+    const uint8_t *segm = nbr_m + 2 * (size_t)off[a];
     const unsigned n = nbr_n[a], o = eoff[a], n_up = eoff[a + 1] - o;
     for (unsigned m = 0; m < n_up; ++m) {
         ea[o + m] = (int32_t)a;
         eb[o + m] = seg[n - n_up + m];
+        nfaces[o + m] = segm[n - n_up + m];
     }
-}
-
-__global__ void k_edge_faces(const int32_t *__restrict__ F, const unsigned *__restrict__ off,
-                             const int32_t *__restrict__ list, const int32_t *__restrict__ ea,
-                             const int32_t *__restrict__ eb, int64_t ne, uint8_t *__restrict__ nfaces,
-                             uint8_t *__restrict__ bnd) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne) return;
-    const int32_t a = ea[i], b = eb[i];
-    unsigned n = 0;
-    for (unsigned j = off[a]; j < off[a + 1]; ++j) n += has(F, list[j], b);
-    nfaces[i] = (uint8_t)(n > 255 ? 255 : n);
-    if (n == 1) { bnd[a] = 1; bnd[b] = 1; }
 }
 
 // Sign of the turn-over product n_old . n_new of one face, decided in FP32
@@ -360,13 +439,12 @@ __global__ void k_edge_faces(const int32_t *__restrict__ F, const unsigned *__re
 // where the FP64 test lands to within far less than B/2. So whenever
 // |s| > B the FP64 test takes the same decision, and the collapses stay
 // identical. Near the bottom of the FP32 range the FP64 test decides.
-__device__ __forceinline__ int turn_sign32(const float *__restrict__ V32, const int32_t *id, int32_t w, float3 v) {
-    float3 P[3], R[3];
+// (P: the face's corners from V32, id: their vertex ids)
+__device__ __forceinline__ int turn_sign32(const float3 *P, const int32_t *id, int32_t w, float3 v) {
+    float3 R[3];
     float m = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fabsf(v.z));
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const int64_t i = id[k];
-        P[k] = make_float3(V32[3 * i], V32[3 * i + 1], V32[3 * i + 2]);
         R[k] = id[k] == w ? v : P[k];
         m = fmaxf(m, fmaxf(fmaxf(fabsf(P[k].x), fabsf(P[k].y)), fabsf(P[k].z)));
     }
@@ -390,42 +468,56 @@ __device__ __forceinline__ int turn_sign32(const float *__restrict__ V32, const 
     return 0;
 }
 
-__global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V, const float *__restrict__ V32,
-                                                    const int32_t *__restrict__ F,
-                                                    const double *__restrict__ Q, const unsigned *__restrict__ off,
-                                                    const int32_t *__restrict__ list, const int32_t *__restrict__ nbr,
-                                                    const unsigned *__restrict__ nbr_n, const int32_t *__restrict__ ea,
-                                                    const int32_t *__restrict__ eb, const uint8_t *__restrict__ nfaces,
-                                                    const uint8_t *__restrict__ bnd, int64_t ne, int placement,
-                                                    unsigned long long *__restrict__ key, double *__restrict__ tpos,
-                                                    const uint8_t *__restrict__ dirty, const unsigned *__restrict__ eoff_prev,
-                                                    const int32_t *__restrict__ eb_prev,
-                                                    const unsigned long long *__restrict__ key_prev,
-                                                    const double *__restrict__ tpos_prev) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne) return;
-    key[i] = KEY_NONE;
-    const int32_t a = ea[i], b = eb[i];
-    if (key_prev && !dirty[a] && !dirty[b]) {
+struct EdgeCostArgs {
+    const double *V;
+    const float *V32;
+    const int32_t *F;
+    const double *Q;
+    const unsigned *off;
+    const int32_t *list;
+    const int32_t *nbr;
+    const unsigned *nbr_n;
+    const int32_t *ea, *eb;
+    const uint8_t *nfaces, *bnd;
+    int placement;
+    unsigned long long *key;
+    double *tpos;
+    const uint8_t *dirty;
+    const unsigned *eoff_prev;
+    const int32_t *eb_prev;
+    const unsigned long long *key_prev;
+    const double *tpos_prev;
+};
+
+// placement, cost and validity of edge i: its key (KEY_NONE when the
+// collapse is not allowed) and its placement in tpos
+__device__ unsigned long long edge_key(const EdgeCostArgs &A, int64_t i) {
+    const double *__restrict__ V = A.V;
+    const float *__restrict__ V32 = A.V32;
+    const int32_t *__restrict__ F = A.F;
+    const double *__restrict__ Q = A.Q;
+    const unsigned *__restrict__ off = A.off;
+    const int32_t *__restrict__ list = A.list;
+    double *__restrict__ tpos = A.tpos;
+    const int32_t a = A.ea[i], b = A.eb[i];
+    if (A.key_prev && !A.dirty[a] && !A.dirty[b]) {
         // neither end nor any vertex of their faces changed in the last
         // round: the edge's cost, validity and placement are as they were
-        unsigned lo = eoff_prev[a], hi = eoff_prev[a + 1];
+        unsigned lo = A.eoff_prev[a], hi = A.eoff_prev[a + 1];
         while (lo < hi) {
             const unsigned mid = (lo + hi) >> 1;
-            if (eb_prev[mid] < b) lo = mid + 1; else hi = mid;
+            if (A.eb_prev[mid] < b) lo = mid + 1; else hi = mid;
         }
-        if (lo < eoff_prev[a + 1] && eb_prev[lo] == b) {
-            const unsigned long long k = key_prev[lo];
-            if (k != KEY_NONE) {
-                key[i] = (k & 0xffffffff00000000ull) | (uint32_t)i;
+        if (lo < A.eoff_prev[a + 1] && A.eb_prev[lo] == b) {
+            const unsigned long long k = A.key_prev[lo];
+            if (k == KEY_NONE) return KEY_NONE;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) tpos[3 * i + c] = tpos_prev[3 * (int64_t)lo + c];
-            }
-            return;
+            for (int c = 0; c < 3; ++c) tpos[3 * i + c] = A.tpos_prev[3 * (int64_t)lo + c];
+            return (k & 0xffffffff00000000ull) | (uint32_t)i;
         }
     }
-    const int nfc = nfaces[i];
-    if (nfc > 2) return;
+    const int nfc = A.nfaces[i];
+    if (nfc > 2) return KEY_NONE;
     double q[10];
 #pragma unroll
     for (int k = 0; k < 10; ++k) q[k] = __dadd_rn(Q[10 * (int64_t)a + k], Q[10 * (int64_t)b + k]);
@@ -433,21 +525,21 @@ __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V,
     D3 v;
     if (nfc == 1) {
         v = quad_eval(q, vb) < quad_eval(q, va) ? vb : va;
-    } else if (bnd[a] && bnd[b]) {
-        return;
-    } else if (bnd[a]) {
+    } else if (A.bnd[a] && A.bnd[b]) {
+        return KEY_NONE;
+    } else if (A.bnd[a]) {
         v = va;
-    } else if (bnd[b]) {
+    } else if (A.bnd[b]) {
         v = vb;
     } else {
-        const double t = placement == AG_QEM_MIDPOINT ? 0.5 : qem_place(q, va, vb);
+        const double t = A.placement == AG_QEM_MIDPOINT ? 0.5 : qem_place(q, va, vb);
         v = dadd(va, dscl(dsub(vb, va), t));
     }
     // at most QEM_MAX_NBR distinct neighbours per end; the link condition
     // counts the common ones by merging the two sorted lists
-    const int na = (int)nbr_n[a], nb = (int)nbr_n[b];
-    if (na > QEM_MAX_NBR || nb > QEM_MAX_NBR) return;
-    const int32_t *la = nbr + 2 * (size_t)off[a], *lb = nbr + 2 * (size_t)off[b];
+    const int na = (int)A.nbr_n[a], nb = (int)A.nbr_n[b];
+    if (na > QEM_MAX_NBR || nb > QEM_MAX_NBR) return KEY_NONE;
+    const int32_t *la = A.nbr + 2 * (size_t)off[a], *lb = A.nbr + 2 * (size_t)off[b];
     int common = 0;
     for (int m = 0, n = 0; m < na && n < nb;) {
         const int32_t x = la[m], y = lb[n];
@@ -455,72 +547,115 @@ __global__ void __launch_bounds__(128) k_edge_cost(const double *__restrict__ V,
         m += x <= y;
         n += y <= x;
     }
-    if (common != nfc) return;
-    if (na + nb - common <= 4) return;
+    if (common != nfc) return KEY_NONE;
+    if (na + nb - common <= 4) return KEY_NONE;
     const float3 v32 = make_float3(__double2float_rn(v.x), __double2float_rn(v.y), __double2float_rn(v.z));
+    // the faces around each end in chunks of TURN_CHUNK: the loads of a
+    // chunk (face ids, corner ids, corners) are issued together, so a chunk
+    // costs three dependent memory latencies rather than three per face
     for (int side = 0; side < 2; ++side) {
         const int32_t w = side ? b : a, o = side ? a : b;
-        for (unsigned j = off[w]; j < off[w + 1]; ++j) {
-            const int64_t g = list[j];
-            if (has(F, g, o)) continue;
-            const int32_t id[3] = {F[3 * g], F[3 * g + 1], F[3 * g + 2]};
-            const int sg = turn_sign32(V32, id, w, v32);
-            if (sg > 0) continue;
-            if (sg < 0) return;
-            D3 P[3], R[3];
+        const unsigned je = off[w + 1];
+        for (unsigned j0 = off[w]; j0 < je; j0 += TURN_CHUNK) {
+            int32_t id[TURN_CHUNK][3];
+            float3 P[TURN_CHUNK][3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                P[k] = ldv(V, F[3 * g + k]);
-                R[k] = F[3 * g + k] == w ? v : P[k];
+            for (int c = 0; c < TURN_CHUNK; ++c) {
+                const int64_t g = j0 + c < je ? list[j0 + c] : 0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) id[c][k] = j0 + c < je ? F[3 * g + k] : -1;
             }
-            const D3 n0 = dcross(dsub(P[1], P[0]), dsub(P[2], P[0]));
-            const D3 n1 = dcross(dsub(R[1], R[0]), dsub(R[2], R[0]));
-            if (!(ddot(n0, n1) > 0.0)) return;
+#pragma unroll
+            for (int c = 0; c < TURN_CHUNK; ++c)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int64_t x = id[c][k] < 0 ? 0 : id[c][k];
+                    P[c][k] = make_float3(V32[3 * x], V32[3 * x + 1], V32[3 * x + 2]);
+                }
+#pragma unroll
+            for (int c = 0; c < TURN_CHUNK; ++c) {
+                if (id[c][0] < 0) continue;                                   // past the end
+                if (id[c][0] == o || id[c][1] == o || id[c][2] == o) continue; // a face of the edge
+                const int sg = turn_sign32(P[c], id[c], w, v32);
+                if (sg > 0) continue;
+                if (sg < 0) return KEY_NONE;
+                D3 Pd[3], R[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    Pd[k] = ldv(V, id[c][k]);
+                    R[k] = id[c][k] == w ? v : Pd[k];
+                }
+                const D3 n0 = dcross(dsub(Pd[1], Pd[0]), dsub(Pd[2], Pd[0]));
+                const D3 n1 = dcross(dsub(R[1], R[0]), dsub(R[2], R[0]));
+                if (!(ddot(n0, n1) > 0.0)) return KEY_NONE;
+            }
         }
     }
-    key[i] = qem_key(quad_eval(q, v), (uint32_t)i);
     tpos[3 * i] = v.x; tpos[3 * i + 1] = v.y; tpos[3 * i + 2] = v.z;
+    return qem_key(quad_eval(q, v), (uint32_t)i);
 }
 
-__global__ void k_m1(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
-                     const unsigned long long *__restrict__ key, int64_t ne, unsigned long long *__restrict__ m1) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne || key[i] == KEY_NONE) return;
-    atomicMin(&m1[ea[i]], key[i]);
-    atomicMin(&m1[eb[i]], key[i]);
+// every edge of the round (grid-stride over the device-side count): its key,
+// and m1(v) = the least key at each end
+#ifndef AG_QEM_COST_MIN_BLOCKS
+#define AG_QEM_COST_MIN_BLOCKS 1
+#endif
+__global__ void __launch_bounds__(128, AG_QEM_COST_MIN_BLOCKS) k_edge_cost(const Control *__restrict__ ctl, EdgeCostArgs A,
+                                                    unsigned long long *__restrict__ m1) {
+    if (ctl->done) return;
+    const int64_t ne = ctl->ne;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = edge_key(A, i);
+        A.key[i] = k;
+        if (k != KEY_NONE) {
+            atomicMin(&m1[A.ea[i]], k);
+            atomicMin(&m1[A.eb[i]], k);
+        }
+    }
 }
 
-__global__ void k_m2(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
-                     const unsigned long long *__restrict__ m1, int64_t ne, unsigned long long *__restrict__ m2) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne) return;
-    const int32_t a = ea[i], b = eb[i];
-    atomicMin(&m2[a], m1[b]);
-    atomicMin(&m2[b], m1[a]);
+// m2(v) = the least m1 over v and its neighbours (every vertex with an edge
+// meets its own m1 through that edge)
+__global__ void k_m2(const Control *__restrict__ ctl, const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
+                     const unsigned long long *__restrict__ m1, unsigned long long *__restrict__ m2) {
+    if (ctl->done) return;
+    const int64_t ne = ctl->ne;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = ea[i], b = eb[i];
+        const unsigned long long x = m1[a], y = m1[b], m = x < y ? x : y;
+        if (m == KEY_NONE) continue;
+        atomicMin(&m2[a], m);
+        atomicMin(&m2[b], m);
+    }
 }
 
-__global__ void k_select(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
-                         const unsigned long long *__restrict__ key, const uint8_t *__restrict__ nfaces,
-                         const unsigned long long *__restrict__ m2, int64_t ne, uint8_t *__restrict__ sel,
-                         unsigned long long *__restrict__ selk, uint8_t *__restrict__ selnf, Counters *cnt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne) return;
-    const unsigned long long k = key[i];
-    const bool s = k != KEY_NONE && k == m2[ea[i]] && k == m2[eb[i]];
-    sel[i] = s;
-    if (!s) return;
-    const int slot = atomicAdd(&cnt->nsel, 1);
-    selk[slot] = k;
-    selnf[slot] = nfaces[i];
-    atomicAdd(&cnt->removable, (unsigned long long)nfaces[i]);
+__global__ void k_select(const Control *__restrict__ ctl, const int32_t *__restrict__ ea,
+                         const int32_t *__restrict__ eb, const unsigned long long *__restrict__ key,
+                         const uint8_t *__restrict__ nfaces, const unsigned long long *__restrict__ m2,
+                         uint8_t *__restrict__ sel, unsigned long long *__restrict__ selk, uint8_t *__restrict__ selnf,
+                         Counters *cnt) {
+    if (ctl->done) return;
+    const int64_t ne = ctl->ne;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = key[i];
+        const bool s = k != KEY_NONE && k == m2[ea[i]] && k == m2[eb[i]];
+        sel[i] = s;
+        if (!s) continue;
+        const int slot = atomicAdd(&cnt->nsel, 1);
+        selk[slot] = k;
+        selnf[slot] = nfaces[i];
+        atomicAdd(&cnt->removable, (unsigned long long)nfaces[i]);
+    }
 }
 
 // smallest selected key L with sum(nfaces of selected keys <= L) >= need
-__global__ void __launch_bounds__(1024) k_limit(const unsigned long long *__restrict__ selk,
+__global__ void __launch_bounds__(1024) k_limit(const Control *__restrict__ ctl,
+                                                 const unsigned long long *__restrict__ selk,
                                                  const uint8_t *__restrict__ selnf, const Counters *cnt,
                                                  long long target, unsigned long long *limit) {
     __shared__ long long part[32];
     __shared__ unsigned long long s_lo, s_hi;
+    if (ctl->done) return;
     if ((long long)cnt->alive - (long long)cnt->removable >= target) {   // no cut needed this round
         if (threadIdx.x == 0) *limit = ~0ull;
         return;
@@ -549,48 +684,62 @@ __global__ void __launch_bounds__(1024) k_limit(const unsigned long long *__rest
     if (threadIdx.x == 0) *limit = s_lo;
 }
 
-__global__ void k_apply(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
-                        const unsigned long long *__restrict__ key, const uint8_t *__restrict__ sel,
-                        const double *__restrict__ tpos, const unsigned long long *__restrict__ limit, int64_t ne,
-                        double *__restrict__ V, float *__restrict__ V32, double *__restrict__ Q,
-                        uint8_t *__restrict__ valive, int32_t *__restrict__ remap) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne || !sel[i] || key[i] > *limit) return;
-    const int64_t a = ea[i], b = eb[i];
-    V[3 * a] = tpos[3 * i]; V[3 * a + 1] = tpos[3 * i + 1]; V[3 * a + 2] = tpos[3 * i + 2];
+// The collapses that pass the cut: keep a at the placement with Q_a + Q_b,
+// rename b to a; and mark the vertices whose edges must be re-evaluated next
+// round: both ends of every collapse and every vertex of their faces (read
+// here, before k_faces rewrites the faces). Selected collapses share no
+// vertex, so their writes do not meet.
+__global__ void k_apply_mark(const Control *__restrict__ ctl, const int32_t *__restrict__ ea,
+                             const int32_t *__restrict__ eb, const unsigned long long *__restrict__ key,
+                             const uint8_t *__restrict__ sel, const double *__restrict__ tpos,
+                             const unsigned long long *__restrict__ limit, double *__restrict__ V,
+                             float *__restrict__ V32, double *__restrict__ Q, uint8_t *__restrict__ valive,
+                             int32_t *__restrict__ remap, const int32_t *__restrict__ F,
+                             const unsigned *__restrict__ off, const int32_t *__restrict__ list,
+                             uint8_t *__restrict__ dirty) {
+    if (ctl->done) return;
+    const int64_t ne = ctl->ne;
+    const unsigned long long L = *limit;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!sel[i] || key[i] > L) continue;
+        const int64_t a = ea[i], b = eb[i];
+        for (int side = 0; side < 2; ++side) {
+            const int64_t w = side ? b : a;
+            dirty[w] = 1;
+            const unsigned je = off[w + 1];
+            for (unsigned j0 = off[w]; j0 < je; j0 += TURN_CHUNK) {   // loads of a chunk issued together
+                int32_t id[TURN_CHUNK][3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) V32[3 * a + k] = __double2float_rn(tpos[3 * i + k]);
+                for (int c = 0; c < TURN_CHUNK; ++c) {
+                    const int64_t f = j0 + c < je ? list[j0 + c] : -1;
 #pragma unroll
-    for (int k = 0; k < 10; ++k) Q[10 * a + k] = __dadd_rn(Q[10 * a + k], Q[10 * b + k]);
-    valive[b] = 0;
-    remap[b] = (int32_t)a;
-}
-
-// the vertices whose edges must be re-evaluated next round: both ends of
-// every collapse and every vertex of their faces (read before k_faces
-// rewrites the faces)
-__global__ void k_mark(const int32_t *__restrict__ ea, const int32_t *__restrict__ eb,
-                       const unsigned long long *__restrict__ key, const uint8_t *__restrict__ sel,
-                       const unsigned long long *__restrict__ limit, int64_t ne, const int32_t *__restrict__ F,
-                       const unsigned *__restrict__ off, const int32_t *__restrict__ list, uint8_t *__restrict__ dirty) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ne || !sel[i] || key[i] > *limit) return;
-    for (int side = 0; side < 2; ++side) {
-        const int32_t w = side ? eb[i] : ea[i];
-        dirty[w] = 1;
-        for (unsigned j = off[w]; j < off[w + 1]; ++j) {
-            const int64_t f = list[j];
-            dirty[F[3 * f]] = 1;
-            dirty[F[3 * f + 1]] = 1;
-            dirty[F[3 * f + 2]] = 1;
+                    for (int k = 0; k < 3; ++k) id[c][k] = f >= 0 ? F[3 * f + k] : -1;
+                }
+#pragma unroll
+                for (int c = 0; c < TURN_CHUNK; ++c)
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        if (id[c][k] >= 0) dirty[id[c][k]] = 1;
+            }
         }
+        V[3 * a] = tpos[3 * i]; V[3 * a + 1] = tpos[3 * i + 1]; V[3 * a + 2] = tpos[3 * i + 2];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) V32[3 * a + k] = __double2float_rn(tpos[3 * i + k]);
+#pragma unroll
+        for (int k = 0; k < 10; ++k) Q[10 * a + k] = __dadd_rn(Q[10 * a + k], Q[10 * b + k]);
+        valive[b] = 0;
+        remap[b] = (int32_t)a;
     }
 }
 
-__global__ void k_faces(int32_t *__restrict__ F, uint8_t *__restrict__ falive, int64_t nf,
-                        const int32_t *__restrict__ remap, Counters *cnt) {
+// faces through the renaming: a face holding both ends of a collapse is
+// dropped; the others count towards their vertices' degrees in the next
+// adjacency
+__global__ void k_faces(const Control *__restrict__ ctl, int32_t *__restrict__ F, uint8_t *__restrict__ falive,
+                        int64_t nf, const int32_t *__restrict__ remap, Counters *cnt,
+                        unsigned *__restrict__ deg_next) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= nf || !falive[f]) return;
+    if (f >= nf || ctl->done || !falive[f]) return;
     const int32_t r0 = remap[F[3 * f]], r1 = remap[F[3 * f + 1]], r2 = remap[F[3 * f + 2]];
     if (r0 == r1 || r1 == r2 || r0 == r2) {
         falive[f] = 0;
@@ -598,6 +747,9 @@ __global__ void k_faces(int32_t *__restrict__ F, uint8_t *__restrict__ falive, i
         return;
     }
     F[3 * f] = r0; F[3 * f + 1] = r1; F[3 * f + 2] = r2;
+    atomicAdd(&deg_next[r0], 1u);
+    atomicAdd(&deg_next[r1], 1u);
+    atomicAdd(&deg_next[r2], 1u);
 }
 
 __global__ void k_flag_u32(const uint8_t *__restrict__ flag, int64_t n, unsigned *__restrict__ out) {
@@ -606,13 +758,49 @@ __global__ void k_flag_u32(const uint8_t *__restrict__ flag, int64_t n, unsigned
 }
 
 __global__ void k_compact_v(const double *__restrict__ V, const uint8_t *__restrict__ valive,
-                            const unsigned *__restrict__ vid, int64_t nv, double *__restrict__ Vout,
-                            int32_t *__restrict__ keep_v) {
+                            const unsigned *__restrict__ vid, const int32_t *__restrict__ vorig, int64_t nv,
+                            double *__restrict__ Vout, int32_t *__restrict__ keep_v) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv || !valive[v]) return;
     const unsigned o = vid[v];
     Vout[3 * (int64_t)o] = V[3 * v]; Vout[3 * (int64_t)o + 1] = V[3 * v + 1]; Vout[3 * (int64_t)o + 2] = V[3 * v + 2];
-    if (keep_v) keep_v[o] = (int32_t)v;
+    if (keep_v) keep_v[o] = vorig[v];
+}
+
+// Renumbering of the working mesh to its alive vertices and faces, both in
+// increasing id (so every order the rounds depend on, the ranked edge list
+// above all, is unchanged): the per-vertex state moves to the new ids, the
+// faces are rewritten through them.
+__global__ void k_gather_v(const uint8_t *__restrict__ valive, const unsigned *__restrict__ vid, int64_t nv,
+                           const double *__restrict__ V, const float *__restrict__ V32, const double *__restrict__ Q,
+                           const int32_t *__restrict__ vorig, double *__restrict__ V2, float *__restrict__ V32b,
+                           double *__restrict__ Q2, int32_t *__restrict__ vorig2) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv || !valive[v]) return;
+    const int64_t o = vid[v];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        V2[3 * o + k] = V[3 * v + k];
+        V32b[3 * o + k] = V32[3 * v + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 10; ++k) Q2[10 * o + k] = Q[10 * v + k];
+    vorig2[o] = vorig[v];
+}
+
+__global__ void k_gather_f(const int32_t *__restrict__ F, const uint8_t *__restrict__ falive,
+                           const unsigned *__restrict__ fid, const unsigned *__restrict__ vid, int64_t nf,
+                           int32_t *__restrict__ F2) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= nf || !falive[f]) return;
+    const int64_t o = fid[f];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F2[3 * o + k] = (int32_t)vid[F[3 * f + k]];
+}
+
+__global__ void k_iota(int32_t *__restrict__ a, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = (int32_t)i;
 }
 
 __global__ void k_compact_f(const int32_t *__restrict__ F, const uint8_t *__restrict__ falive,
@@ -666,10 +854,12 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     AG_CUDA(sc.alloc((void **)&remap, sizeof(int32_t) * nv));
     AG_CUDA(sc.alloc((void **)&list, sizeof(int32_t) * 3 * nf));
     int32_t *nbr;        // per vertex: sorted distinct neighbours (2 deg entries of room)
+    uint8_t *nbr_m;      // the faces of each of those edges
     unsigned *nbr_n;     // their count
     int32_t *heavy;      // vertices whose lists a whole warp sorts
     unsigned *n_heavy;
     AG_CUDA(sc.alloc((void **)&nbr, sizeof(int32_t) * 6 * nf));
+    AG_CUDA(sc.alloc((void **)&nbr_m, 6 * nf));
     AG_CUDA(sc.alloc((void **)&nbr_n, sizeof(unsigned) * nv));
     AG_CUDA(sc.alloc((void **)&heavy, sizeof(int32_t) * nv));
     AG_CUDA(sc.alloc((void **)&n_heavy, sizeof(unsigned)));
@@ -682,6 +872,8 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     AG_CUDA(sc.alloc((void **)&sel, emax));
     AG_CUDA(sc.alloc((void **)&selnf, emax));
     AG_CUDA(sc.alloc((void **)&off, sizeof(unsigned) * (nv + 1)));
+    unsigned *off_next;   // the next round's adjacency offsets (degrees first)
+    AG_CUDA(sc.alloc((void **)&off_next, sizeof(unsigned) * (nv + 1)));
     AG_CUDA(sc.alloc((void **)&fill, sizeof(unsigned) * nv));
     AG_CUDA(sc.alloc((void **)&eoff, sizeof(unsigned) * (nv + 1)));
     AG_CUDA(sc.alloc((void **)&scan_tmp, scan_scratch_bytes(nv > nf ? nv : nf)));
@@ -693,110 +885,162 @@ extern "C" AG_API ag_status ag_qem_simplify(const float *d_verts, int64_t n_vert
     AG_CUDA(sc.alloc((void **)&selk, sizeof(unsigned long long) * emax));
     AG_CUDA(sc.alloc((void **)&limit, sizeof(unsigned long long)));
     AG_CUDA(sc.alloc((void **)&cnt, sizeof(Counters)));
+    Control *ctl;
+    AG_CUDA(sc.alloc((void **)&ctl, sizeof(Control)));
     // the previous round's edge list (ends b by segment of a), keys and
     // placements, reused for edges whose neighbourhood did not change
     int32_t *eb_prev;
     unsigned *eoff_prev;
     unsigned long long *key_prev;
     double *tpos_prev;
-    uint8_t *dirty;
+    uint8_t *dirty, *dirty_next;
     AG_CUDA(sc.alloc((void **)&eb_prev, sizeof(int32_t) * emax));
     AG_CUDA(sc.alloc((void **)&eoff_prev, sizeof(unsigned) * (nv + 1)));
     AG_CUDA(sc.alloc((void **)&key_prev, sizeof(unsigned long long) * emax));
     AG_CUDA(sc.alloc((void **)&tpos_prev, sizeof(double) * 3 * emax));
     AG_CUDA(sc.alloc((void **)&dirty, nv));
-    bool have_prev = false;
-    Counters *h_cnt = nullptr;
-    AG_CUDA(cudaMallocHost((void **)&h_cnt, sizeof(Counters)));
+    AG_CUDA(sc.alloc((void **)&dirty_next, nv));
+    struct HostRead {   // pinned: the round control and the alive-face count
+        Control ctl;
+        unsigned long long alive;
+    } *h_read = nullptr;
+    AG_CUDA(cudaMallocHost((void **)&h_read, sizeof(HostRead)));
     struct HostFree {
-        Counters *p;
+        HostRead *p;
         ~HostFree() { if (p) cudaFreeHost(p); }
-    } hf{h_cnt};
+    } hf{h_read};
+    Control *h_ctl = &h_read->ctl;
+    unsigned long long *h_alive = &h_read->alive;
 
     const int B = 256;
     AG_CUDA(cudaMemsetAsync(cnt, 0, sizeof(Counters), s));
+    AG_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Control), s));
+    AG_CUDA(cudaMemsetAsync(dirty, 0, nv, s));
     AG_CUDA(cudaMemsetAsync(valive, 0, nv, s));
     k_init_faces<<<blocks(nf, B), B, 0, s>>>(d_faces, nf, nv, F, falive, valive, cnt, status);
     k_init_verts<<<blocks(nv, B), B, 0, s>>>(d_verts, nv, V, V32, remap);
     AG_CUDA_LAUNCH("qem init");
 
-    auto build_csr = [&]() -> cudaError_t {
+    // the working mesh: nvc vertices and nfc faces (every alive one among
+    // them), renumbered to the alive ones when the alive faces fall to a
+    // quarter of nfc; vorig holds each working vertex's original id
+    int64_t nvc = nv, nfc = nf;
+    double *V2, *Q2;
+    float *V32b;
+    int32_t *F2, *vorig, *vorig2;
+    AG_CUDA(sc.alloc((void **)&V2, sizeof(double) * 3 * nv));
+    AG_CUDA(sc.alloc((void **)&V32b, sizeof(float) * 3 * nv));
+    AG_CUDA(sc.alloc((void **)&Q2, sizeof(double) * 10 * nv));
+    AG_CUDA(sc.alloc((void **)&F2, sizeof(int32_t) * 3 * nf));
+    AG_CUDA(sc.alloc((void **)&vorig, sizeof(int32_t) * nv));
+    AG_CUDA(sc.alloc((void **)&vorig2, sizeof(int32_t) * nv));
+    k_iota<<<blocks(nv, B), B, 0, s>>>(vorig, nv);
+
+    // adjacency (vertex -> alive faces), neighbour lists and the ranked edge
+    // offsets of the working mesh from scratch (at the start and after a
+    // renumbering; between, each round builds the next one)
+    const unsigned heavy_grid = (unsigned)device_sm_count(dev) * 4;
+    auto build_adjacency = [&](bool quadrics) -> cudaError_t {
         cudaError_t e;
-        if ((e = cudaMemsetAsync(off, 0, sizeof(unsigned) * (nv + 1), s)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(fill, 0, sizeof(unsigned) * nv, s)) != cudaSuccess) return e;
-        k_deg<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, off);
-        if ((e = launch_scan_exclusive(off, nv, off + nv, scan_tmp, s)) != cudaSuccess) return e;
-        k_fill<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, off, fill, list);
+        if ((e = cudaMemsetAsync(off, 0, sizeof(unsigned) * (nvc + 1), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(fill, 0, sizeof(unsigned) * nvc, s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(n_heavy, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+        k_deg<<<blocks(nfc, B), B, 0, s>>>(F, falive, nfc, off);
+        if ((e = launch_scan_exclusive(off, nvc, off + nvc, scan_tmp, s)) != cudaSuccess) return e;
+        k_fill<<<blocks(nfc, B), B, 0, s>>>(nullptr, F, falive, nfc, off, fill, list);
+        if (quadrics) k_quadric_init<<<blocks(nvc, 128), 128, 0, s>>>(V, F, nvc, off, list, Q);
+        k_nbrs<<<blocks(nvc, 128), 128, 0, s>>>(nullptr, F, nvc, off, list, nbr, nbr_m, nbr_n, eoff, bnd, heavy,
+                                                 n_heavy);
+        k_nbrs_heavy<<<heavy_grid, 128, 0, s>>>(nullptr, F, off, list, heavy, n_heavy, nbr, nbr_m, nbr_n, eoff, bnd);
+        if ((e = launch_scan_exclusive(eoff, nvc, eoff + nvc, scan_tmp, s)) != cudaSuccess) return e;
         return cudaGetLastError();
     };
-    AG_CUDA(build_csr());
-    k_quadric_init<<<blocks(nv, 128), 128, 0, s>>>(V, F, nv, off, list, Q);
-    AG_CUDA_LAUNCH("k_quadric_init");
+    AG_CUDA(build_adjacency(true));
 
-    // One host read per round: the counters (alive faces, last round's
-    // selections) and the next edge count come back together; the cut to the
-    // target is decided on the device (k_limit).
-    auto edge_offsets = [&]() -> cudaError_t {
-        cudaError_t e;
-        if ((e = build_csr()) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(n_heavy, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
-        k_nbrs<<<blocks(nv, 128), 128, 0, s>>>(F, nv, off, list, nbr, nbr_n, eoff, heavy, n_heavy);
-        k_nbrs_heavy<<<(unsigned)device_sm_count(dev) * 4, 128, 0, s>>>(F, off, list, heavy, n_heavy, nbr, nbr_n,
-                                                                          eoff);
-        return launch_scan_exclusive(eoff, nv, eoff + nv, scan_tmp, s);
-    };
-    int64_t rounds = 0;
-    AG_CUDA(edge_offsets());
+    // Rounds are enqueued ROUNDS_AHEAD at a time with no host decision in
+    // between: k_round_begin decides on the device whether each one runs,
+    // and the kernels over edges take the edge count from the device.
+    const unsigned sm = (unsigned)device_sm_count(dev);
+    bool have_prev = false;   // the last round's edge list is there to reuse (same numbering)
     for (;;) {
-        unsigned ne32 = 0;
-        AG_CUDA(cudaMemcpyAsync(h_cnt, cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-        AG_CUDA(cudaMemcpyAsync(&ne32, eoff + nv, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-        AG_CUDA(cudaStreamSynchronize(s));
-        if (rounds > 0 && h_cnt->nsel == 0) {   // the last round selected nothing: it changed nothing
-            --rounds;
-            break;
+        const unsigned eg128 = std::min(blocks(3 * nfc, 128), sm * 32);
+        const unsigned eg256 = std::min(blocks(3 * nfc, B), sm * 16);
+        for (int k = 0; k < ROUNDS_AHEAD; ++k) {
+            k_round_begin<<<1, 32, 0, s>>>(ctl, cnt, eoff + nvc, (long long)target, (long long)rounds_cap);
+            k_edges<<<blocks(nvc, 128), 128, 0, s>>>(ctl, nvc, off, nbr, nbr_m, nbr_n, eoff, ea, eb, nfaces, m1, m2,
+                                                     dirty_next, off_next, fill, n_heavy);
+            EdgeCostArgs A;
+            A.V = V; A.V32 = V32; A.F = F; A.Q = Q; A.off = off; A.list = list; A.nbr = nbr; A.nbr_n = nbr_n;
+            A.ea = ea; A.eb = eb; A.nfaces = nfaces; A.bnd = bnd; A.placement = placement; A.key = key;
+            A.tpos = tpos; A.dirty = dirty; A.eoff_prev = eoff_prev; A.eb_prev = eb_prev;
+            A.key_prev = have_prev ? key_prev : nullptr; A.tpos_prev = tpos_prev;
+            k_edge_cost<<<eg128, 128, 0, s>>>(ctl, A, m1);
+            k_m2<<<eg256, B, 0, s>>>(ctl, ea, eb, m1, m2);
+            k_select<<<eg256, B, 0, s>>>(ctl, ea, eb, key, nfaces, m2, sel, selk, selnf, cnt);
+            k_limit<<<1, 1024, 0, s>>>(ctl, selk, selnf, cnt, (long long)target, limit);
+            k_apply_mark<<<eg256, B, 0, s>>>(ctl, ea, eb, key, sel, tpos, limit, V, V32, Q, valive, remap, F, off,
+                                             list, dirty_next);
+            k_faces<<<blocks(nfc, B), B, 0, s>>>(ctl, F, falive, nfc, remap, cnt, off_next);
+            AG_CUDA_LAUNCH("qem round");
+            // the next round's adjacency and ranked edge list
+            std::swap(off, off_next);
+            std::swap(eb, eb_prev);
+            std::swap(eoff, eoff_prev);
+            std::swap(key, key_prev);
+            std::swap(tpos, tpos_prev);
+            std::swap(dirty, dirty_next);
+            have_prev = true;
+            AG_CUDA(launch_scan_exclusive(off, nvc, off + nvc, scan_tmp, s));
+            k_fill<<<blocks(nfc, B), B, 0, s>>>(ctl, F, falive, nfc, off, fill, list);
+            k_nbrs<<<blocks(nvc, 128), 128, 0, s>>>(ctl, F, nvc, off, list, nbr, nbr_m, nbr_n, eoff, bnd, heavy,
+                                                    n_heavy);
+            k_nbrs_heavy<<<heavy_grid, 128, 0, s>>>(ctl, F, off, list, heavy, n_heavy, nbr, nbr_m, nbr_n, eoff, bnd);
+            AG_CUDA(launch_scan_exclusive(eoff, nvc, eoff + nvc, scan_tmp, s));
+            AG_CUDA_LAUNCH("qem adjacency");
         }
-        if ((long long)h_cnt->alive <= target || rounds >= rounds_cap) break;
-        const int64_t ne = ne32;
-        if (ne == 0) break;
-        k_edges<<<blocks(nv, 128), 128, 0, s>>>(nv, off, nbr, nbr_n, eoff, ea, eb);
-        AG_CUDA(cudaMemsetAsync(bnd, 0, nv, s));
-        k_edge_faces<<<blocks(ne, B), B, 0, s>>>(F, off, list, ea, eb, ne, nfaces, bnd);
-        k_edge_cost<<<blocks(ne, 128), 128, 0, s>>>(V, V32, F, Q, off, list, nbr, nbr_n, ea, eb, nfaces, bnd, ne, placement, key,
-                                                    tpos, dirty, eoff_prev, eb_prev, have_prev ? key_prev : nullptr,
-                                                    tpos_prev);
-        AG_CUDA(cudaMemsetAsync(dirty, 0, nv, s));
-        AG_CUDA(cudaMemsetAsync(m1, 0xff, sizeof(unsigned long long) * nv, s));
-        k_m1<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, ne, m1);
-        AG_CUDA(cudaMemcpyAsync(m2, m1, sizeof(unsigned long long) * nv, cudaMemcpyDeviceToDevice, s));
-        k_m2<<<blocks(ne, B), B, 0, s>>>(ea, eb, m1, ne, m2);
-        AG_CUDA(cudaMemsetAsync(&cnt->removable, 0, sizeof(unsigned long long) + 2 * sizeof(int), s));
-        k_select<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, nfaces, m2, ne, sel, selk, selnf, cnt);
-        k_limit<<<1, 1024, 0, s>>>(selk, selnf, cnt, (long long)target, limit);
-        AG_CUDA_LAUNCH("qem round");
-        k_apply<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, tpos, limit, ne, V, V32, Q, valive, remap);
-        k_mark<<<blocks(ne, B), B, 0, s>>>(ea, eb, key, sel, limit, ne, F, off, list, dirty);
-        k_faces<<<blocks(nf, B), B, 0, s>>>(F, falive, nf, remap, cnt);
-        AG_CUDA_LAUNCH("qem collapse");
-        std::swap(eb, eb_prev);
-        std::swap(eoff, eoff_prev);
-        std::swap(key, key_prev);
-        std::swap(tpos, tpos_prev);
-        have_prev = true;
-        ++rounds;
-        AG_CUDA(edge_offsets());
+        AG_CUDA(cudaMemcpyAsync(h_ctl, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaMemcpyAsync(h_alive, &cnt->alive, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaStreamSynchronize(s));
+        if (h_ctl->done) break;
+        if (nfc < COMPACT_MIN || (long long)*h_alive * 4 > nfc) continue;
+        // renumber the working mesh to its alive vertices and faces
+        k_flag_u32<<<blocks(nvc, B), B, 0, s>>>(valive, nvc, vid);
+        AG_CUDA(launch_scan_exclusive(vid, nvc, vid + nvc, scan_tmp, s));
+        k_flag_u32<<<blocks(nfc, B), B, 0, s>>>(falive, nfc, fid);
+        AG_CUDA(launch_scan_exclusive(fid, nfc, fid + nfc, scan_tmp, s));
+        k_gather_v<<<blocks(nvc, B), B, 0, s>>>(valive, vid, nvc, V, V32, Q, vorig, V2, V32b, Q2, vorig2);
+        k_gather_f<<<blocks(nfc, B), B, 0, s>>>(F, falive, fid, vid, nfc, F2);
+        AG_CUDA_LAUNCH("qem renumber");
+        unsigned nv_new = 0, nf_new = 0;
+        AG_CUDA(cudaMemcpyAsync(&nv_new, vid + nvc, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaMemcpyAsync(&nf_new, fid + nfc, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        AG_CUDA(cudaStreamSynchronize(s));
+        std::swap(V, V2);
+        std::swap(V32, V32b);
+        std::swap(Q, Q2);
+        std::swap(vorig, vorig2);
+        std::swap(F, F2);
+        nvc = nv_new;
+        nfc = nf_new;
+        AG_CUDA(cudaMemsetAsync(valive, 1, nvc, s));
+        AG_CUDA(cudaMemsetAsync(falive, 1, nfc, s));
+        AG_CUDA(cudaMemsetAsync(dirty, 0, nvc, s));
+        k_iota<<<blocks(nvc, B), B, 0, s>>>(remap, nvc);
+        AG_CUDA(build_adjacency(false));
+        have_prev = false;
     }
+    const int64_t rounds = h_ctl->rounds;
     // compaction: surviving vertices and faces in increasing original id
-    k_flag_u32<<<blocks(nv, B), B, 0, s>>>(valive, nv, vid);
-    AG_CUDA(launch_scan_exclusive(vid, nv, vid + nv, scan_tmp, s));
-    k_flag_u32<<<blocks(nf, B), B, 0, s>>>(falive, nf, fid);
-    AG_CUDA(launch_scan_exclusive(fid, nf, fid + nf, scan_tmp, s));
-    k_compact_v<<<blocks(nv, B), B, 0, s>>>(V, valive, vid, nv, d_verts_out, d_keep_verts);
-    k_compact_f<<<blocks(nf, B), B, 0, s>>>(F, falive, fid, vid, nf, d_faces_out);
+    k_flag_u32<<<blocks(nvc, B), B, 0, s>>>(valive, nvc, vid);
+    AG_CUDA(launch_scan_exclusive(vid, nvc, vid + nvc, scan_tmp, s));
+    k_flag_u32<<<blocks(nfc, B), B, 0, s>>>(falive, nfc, fid);
+    AG_CUDA(launch_scan_exclusive(fid, nfc, fid + nfc, scan_tmp, s));
+    k_compact_v<<<blocks(nvc, B), B, 0, s>>>(V, valive, vid, vorig, nvc, d_verts_out, d_keep_verts);
+    k_compact_f<<<blocks(nfc, B), B, 0, s>>>(F, falive, fid, vid, nfc, d_faces_out);
     AG_CUDA_LAUNCH("qem compact");
     unsigned nvo = 0, nfo = 0;
-    AG_CUDA(cudaMemcpyAsync(&nvo, vid + nv, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    AG_CUDA(cudaMemcpyAsync(&nfo, fid + nf, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    AG_CUDA(cudaMemcpyAsync(&nvo, vid + nvc, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    AG_CUDA(cudaMemcpyAsync(&nfo, fid + nfc, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     AG_CUDA(cudaStreamSynchronize(s));
     h_result[0] = nvo;
     h_result[1] = nfo;
