@@ -285,8 +285,29 @@ __device__ __forceinline__ int insert_nbrs(const int32_t *__restrict__ F, const 
     return n;
 }
 
+// ascending bitonic sort of the first N of c (all indices fixed at compile
+// time, so c stays in registers)
+template <int N>
+__device__ __forceinline__ void sort_net(int32_t (&c)[NB_FAST]) {
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const int32_t x = c[i], y = c[l], lo = min(x, y), hi = max(x, y);
+                    if ((i & k) == 0) { c[i] = lo; c[l] = hi; } else { c[i] = hi; c[l] = lo; }
+                }
+            }
+}
+
 // Besides the list: nbr_m, the faces of each edge (a, u), and bnd[a], whether
-// a lies on an edge with one face (a boundary vertex).
+// a lies on an edge with one face (a boundary vertex). A vertex with at most
+// NB_FAST candidates (the two other corners of each incident face) gathers
+// them into registers, sorts them with a fixed network and writes the first
+// of each run of equal ids with the run's length.
 __global__ void k_nbrs(const Control *__restrict__ ctl, const int32_t *__restrict__ F, int64_t nv,
                        const unsigned *__restrict__ off, const int32_t *__restrict__ list, int32_t *__restrict__ nbr,
                        uint8_t *__restrict__ nbr_m, unsigned *__restrict__ nbr_n, unsigned *__restrict__ up,
@@ -298,20 +319,48 @@ __global__ void k_nbrs(const Control *__restrict__ ctl, const int32_t *__restric
         heavy[atomicAdd(n_heavy, 1u)] = (int32_t)a;
         return;
     }
-    int32_t nb[NB_FAST];
-    uint8_t mult[NB_FAST];
-    const int n = insert_nbrs(F, list, b, e, a, nb, mult);
+    const unsigned deg = e - b, nc = 2 * deg;
+    int32_t c[NB_FAST];
+#pragma unroll
+    for (int i = 0; i < NB_FAST / 2; ++i) {
+        int32_t x = 0x7fffffff, y = 0x7fffffff;
+        if (i < (int)deg) {
+            const int64_t f = list[b + i];
+            const int32_t t0 = F[3 * f], t1 = F[3 * f + 1], t2 = F[3 * f + 2];
+            x = t0 == a ? t1 : t0;
+            y = t2 == a ? t1 : t2;
+        }
+        c[2 * i] = x;
+        c[2 * i + 1] = y;
+    }
+    if (nc <= 8) sort_net<8>(c);
+    else if (nc <= 16) sort_net<16>(c);
+    else sort_net<32>(c);
     int32_t *seg = nbr + 2 * (size_t)b;
     uint8_t *segm = nbr_m + 2 * (size_t)b;
-    unsigned above = 0;
+    unsigned n = 0, above = 0, run = 0;
     bool border = false;
-    for (int m = 0; m < n; ++m) {
-        seg[m] = nb[m];
-        segm[m] = mult[m];
-        above += nb[m] > a;
-        border |= mult[m] == 1;
+#pragma unroll
+    for (int m = 0; m < NB_FAST; ++m) {
+        if (m < (int)nc) {
+            if (m == 0 || c[m] != c[m - 1]) {
+                if (m > 0) {
+                    segm[n - 1] = (uint8_t)run;
+                    border |= run == 1;
+                }
+                seg[n++] = c[m];
+                above += c[m] > a;
+                run = 1;
+            } else {
+                ++run;
+            }
+        }
     }
-    nbr_n[a] = (unsigned)n;
+    if (n > 0) {
+        segm[n - 1] = (uint8_t)run;
+        border |= run == 1;
+    }
+    nbr_n[a] = n;
     up[a] = above;
     bnd[a] = border;
 }

@@ -99,6 +99,43 @@ __global__ void __launch_bounds__(SB) k_scan_apply(unsigned *__restrict__ d, int
     }
 }
 
+// one block, the chunks in order with a running carry (short inputs: one
+// launch instead of three)
+__global__ void __launch_bounds__(SB) k_scan_small(unsigned *__restrict__ d, int64_t n, unsigned *__restrict__ total) {
+    __shared__ unsigned tile[SCHUNK];
+    __shared__ unsigned carry;
+    if (threadIdx.x == 0) carry = 0;
+    for (int64_t base = 0; base < n; base += SCHUNK) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < SCHUNK; i += SB) {
+            const int64_t j = base + i;
+            tile[i] = j < n ? d[j] : 0u;
+        }
+        __syncthreads();
+        unsigned loc[SI], s = 0;
+#pragma unroll
+        for (int k = 0; k < SI; ++k) {
+            loc[k] = s;
+            s += tile[threadIdx.x * SI + k];
+        }
+        unsigned ex;
+        const unsigned tot = block_excl(s, &ex);
+        const unsigned off = carry + ex;
+#pragma unroll
+        for (int k = 0; k < SI; ++k) tile[threadIdx.x * SI + k] = off + loc[k];
+        __syncthreads();
+        for (int i = threadIdx.x; i < SCHUNK; i += SB) {
+            const int64_t j = base + i;
+            if (j < n) d[j] = tile[i];
+        }
+        if (threadIdx.x == 0) carry += tot;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+constexpr int64_t SMALL_CHUNKS = 4;   // inputs of up to this many chunks take k_scan_small
+
 }  // namespace
 
 size_t scan_scratch_bytes(int64_t n) {
@@ -109,6 +146,10 @@ size_t scan_scratch_bytes(int64_t n) {
 cudaError_t launch_scan_exclusive(unsigned *d, int64_t n, unsigned *total, void *scratch, cudaStream_t s) {
     int64_t nb = (n + SCHUNK - 1) / SCHUNK;
     if (nb < 1) nb = 1;
+    if (nb <= SMALL_CHUNKS) {
+        k_scan_small<<<1, SB, 0, s>>>(d, n, total);
+        return cudaGetLastError();
+    }
     unsigned *bsum = static_cast<unsigned *>(scratch);
     k_scan_reduce<<<(unsigned)nb, SB, 0, s>>>(d, n, bsum);
     k_scan_bsums<<<1, SB, 0, s>>>(bsum, (int)nb, total);
