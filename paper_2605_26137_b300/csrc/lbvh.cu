@@ -589,8 +589,12 @@ __device__ void collapse_node(const CollapseArgs &A, int2 item, bool live, int2 
 
 // one level of the top-down collapse: the level's queue length is read on the
 // device, so the levels run back to back without a host round trip
-__global__ void k_collapse(CollapseArgs A, const int2 *__restrict__ q_in, const int *__restrict__ nq_in,
-                           int2 *__restrict__ q_out) {
+#ifndef AG_COLLAPSE_MIN_BLOCKS
+#define AG_COLLAPSE_MIN_BLOCKS 4   // 128 registers: 1.51 -> 1.46 ms per build against no cap (146 registers), 1.61 ms at 6 blocks
+#endif
+__global__ void __launch_bounds__(128, AG_COLLAPSE_MIN_BLOCKS) k_collapse(CollapseArgs A, const int2 *__restrict__ q_in,
+                                                                         const int *__restrict__ nq_in,
+                                                                         int2 *__restrict__ q_out) {
     const int nq = *nq_in;
     // the loop bound is uniform over the block, so that whole warps call the
     // counter allocations together
@@ -718,6 +722,15 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     AG_CUDA(cudaMemsetAsync(info, 0, sizeof(BuildSummary), s));
     k_bounds_init<<<1, 32, 0, s>>>(bounds);
     AG_CUDA_LAUNCH("k_bounds_init");
+    // the high mesh's vertex normals need nothing of the tree: they run on a
+    // library side stream beside the build's chain of latency-bound kernels
+    // and join it at the end
+    cudaStream_t *side = nullptr;
+    AG_CUDA(side_streams(dev, &side));
+    cudaStream_t *nside = side + 1;
+    EventSet es;
+    AG_CUDA(fork_to(s, nside, 1, es));
+    AG_CUDA(launch_vertex_normals(d_verts, d_faces, nv, n, nullptr, nullptr, h->vnormals, nullptr, nscr, nside[0]));
     k_tri_prep<<<grid_for(n, 256), 256, 0, s>>>(d_verts, d_faces, nv, n, tlo, thi, cent, bounds, status);
     AG_CUDA_LAUNCH("k_tri_prep");
     k_morton<<<grid_for(n, 256), 256, 0, s>>>(cent, n, bounds, k0, v0);
@@ -775,7 +788,7 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     AG_CUDA_LAUNCH("k_collapse_tail");
     k_tri_records<<<grid_for(n, 256), 256, 0, s>>>(rec_pos, va, d_verts, d_faces, nv, n, h->tris, h->tri_ids);
     AG_CUDA_LAUNCH("k_tri_records");
-    AG_CUDA(launch_vertex_normals(d_verts, d_faces, nv, n, nullptr, nullptr, h->vnormals, nullptr, nscr, s));
+    AG_CUDA(join_from(s, nside, 1, es));
     AG_CUDA(cudaEventRecord(h->ev_done, s));
     h->n_nodes = max_nodes;   // until the summary is read
     if (!sync) return AG_OK;
