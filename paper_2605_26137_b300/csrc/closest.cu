@@ -152,12 +152,14 @@ template <int LAYOUT>
 struct PointNode;
 
 // 80-byte quantised node.  Child planes decode as fmaf(q, 2^e, origin), the
-// arithmetic the build verified to enclose the exact child box; here the
-// origin is taken relative to p first, and every distance component is
-// shrunk by 2^-21 (|origin| + |p| + 255 * 2^e).  The roundings on the way
-// (p, origin - p, the slack subtraction, the FMA, and the half ulp by which
-// the build's rounded decode may exceed the exact plane) sum to at most
-// 2^-24 (4 |origin| + 4 |p| + 510 * 2^e), half of that slack.
+// arithmetic the build verified to enclose the exact child box; here as
+// Q * 2^(e+15) + (origin - p - 2^(e+15)) with the exact float Q = 1 + q 2^-15
+// (one PRMT and one FMA per plane), and every distance component is shrunk by
+// 2^-20 (|origin| + |p|) + 2^-7 2^e.  The roundings on the way (p,
+// origin - p, the subtraction of 2^(e+15), the slack subtraction, the FMA,
+// and the half ulp by which the build's rounded decode may exceed the exact
+// plane) sum to at most 2^-24 (5 |origin| + 5 |p| + 66046 2^e) + 2^-23 of
+// the slack, about half of it.
 // With LEAVES, leaf children within the bound are recorded in *ls (to be
 // tested by the caller right away) instead of being offered.
 template <>
@@ -172,10 +174,11 @@ struct PointNode<AG_BVH_Q8> {
         float sx = __uint_as_float((w0.w & 0xffu) << 23);
         float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
         float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
-        float rx = ox - p.x, ry = oy - p.y, rz = oz - p.z;
-        float ex = EPS_REL * (fabsf(ox) + fabsf(p.x) + 255.f * sx);
-        float ey = EPS_REL * (fabsf(oy) + fabsf(p.y) + 255.f * sy);
-        float ez = EPS_REL * (fabsf(oz) + fabsf(p.z) + 255.f * sz);
+        const float Ax = Q_SCALE * sx, Ay = Q_SCALE * sy, Az = Q_SCALE * sz;
+        float rx = ox - p.x - Ax, ry = oy - p.y - Ay, rz = oz - p.z - Az;
+        float ex = EPS_POS * (fabsf(ox) + fabsf(p.x)) + EPS_Q * sx;
+        float ey = EPS_POS * (fabsf(oy) + fabsf(p.y)) + EPS_Q * sy;
+        float ez = EPS_POS * (fabsf(oz) + fabsf(p.z)) + EPS_Q * sz;
         // lo - p - e  and  p - hi - e  as one FMA each
         float blx = rx - ex, bly = ry - ey, blz = rz - ez;
         float bhx = -rx - ex, bhy = -ry - ey, bhz = -rz - ez;
@@ -186,12 +189,12 @@ struct PointNode<AG_BVH_Q8> {
             const int k = c & 3;
             const bool hi = c >= 4;
             uint32_t m = ((hi ? w1.w : w1.z) >> (8 * k)) & 0xffu;
-            float gx = fmaxf(fmaxf(__fmaf_rn(byte_f(hi ? w2.y : w2.x, k), sx, blx),
-                                   __fmaf_rn(byte_f(hi ? w3.w : w3.z, k), -sx, bhx)), 0.f);
-            float gy = fmaxf(fmaxf(__fmaf_rn(byte_f(hi ? w2.w : w2.z, k), sy, bly),
-                                   __fmaf_rn(byte_f(hi ? w4.y : w4.x, k), -sy, bhy)), 0.f);
-            float gz = fmaxf(fmaxf(__fmaf_rn(byte_f(hi ? w3.y : w3.x, k), sz, blz),
-                                   __fmaf_rn(byte_f(hi ? w4.w : w4.z, k), -sz, bhz)), 0.f);
+            float gx = fmaxf(fmaxf(__fmaf_rn(byte_q(hi ? w2.y : w2.x, k), Ax, blx),
+                                   __fmaf_rn(byte_q(hi ? w3.w : w3.z, k), -Ax, bhx)), 0.f);
+            float gy = fmaxf(fmaxf(__fmaf_rn(byte_q(hi ? w2.w : w2.z, k), Ay, bly),
+                                   __fmaf_rn(byte_q(hi ? w4.y : w4.x, k), -Ay, bhy)), 0.f);
+            float gz = fmaxf(fmaxf(__fmaf_rn(byte_q(hi ? w3.y : w3.x, k), Az, blz),
+                                   __fmaf_rn(byte_q(hi ? w4.w : w4.z, k), -Az, bhz)), 0.f);
             float g2 = __fmaf_rn(gx, gx, __fmaf_rn(gy, gy, gz * gz));
             if (m != 0 && g2 <= lim) {
                 if (LEAVES && !(m & 0x80u))

@@ -43,9 +43,10 @@ __device__ __forceinline__ Ray make_ray(float3 base, float3 off, float3 d) {
     float3 p = base + off;
     r.px = p.x; r.py = p.y; r.pz = p.z;
     float3 dd = d;
-    if (fabsf(dd.x) < 1e-30f) dd.x = copysignf(1e-30f, dd.x);
-    if (fabsf(dd.y) < 1e-30f) dd.y = copysignf(1e-30f, dd.y);
-    if (fabsf(dd.z) < 1e-30f) dd.z = copysignf(1e-30f, dd.z);
+    // (2^15 s / d of the 8-bit decode stays finite for node scales up to ~1e10)
+    if (fabsf(dd.x) < 1e-24f) dd.x = copysignf(1e-24f, dd.x);
+    if (fabsf(dd.y) < 1e-24f) dd.y = copysignf(1e-24f, dd.y);
+    if (fabsf(dd.z) < 1e-24f) dd.z = copysignf(1e-24f, dd.z);
     r.ix = 1.0f / dd.x; r.iy = 1.0f / dd.y; r.iz = 1.0f / dd.z;
     r.nx = r.ix < 0.f; r.ny = r.iy < 0.f; r.nz = r.iz < 0.f;
     return r;
@@ -136,12 +137,15 @@ __device__ __forceinline__ void test_tri_shared(const Ray &r, const float4 *__re
 template <int LAYOUT>
 struct NodeOps;
 
-// 80-byte quantised node.  Per node and axis the child planes become one FMA
-// each: t(q) = q * a + b with a = 2^e / d and b = (origin - p) / d.  The
-// intervals are widened by eps = 2^-21 (|origin| + |p| + 255 * 2^e) / |d|,
-// which bounds every rounding on the way (decoded plane, a, b, the FMA, the
-// rounded ray origin) by a factor of at least 4, so a box the exact line
-// meets is never rejected.
+// 80-byte quantised node.  Per node and axis the child planes become one
+// PRMT and one FMA each: t(q) = Q * a + b with Q = 1 + q 2^-15 (exact),
+// a = 2^(e+15) / d and b = (origin - p) / d - a.  The intervals are widened by
+// eps = (2^-20 (|origin| + |p|) + 2^-7 2^e) / |d|.  The roundings on the way
+// (the decoded plane, 1/d, the rounded ray origin, origin - p, the product and
+// the subtraction of a in b, the widening's own subtraction, the FMA) sum to
+// at most 2^-24 (7 (|origin| + |p|) + 66301 2^e) / |d| + 2^-23 eps, so the
+// widening covers them by a factor of about 2 and a box the exact line meets
+// is never rejected.
 // With LEAVES, hit leaf children are recorded in *ls (to be tested by the
 // caller right away) instead of being offered.
 template <>
@@ -156,11 +160,13 @@ struct NodeOps<AG_BVH_Q8> {
         float sx = __uint_as_float((w0.w & 0xffu) << 23);
         float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
         float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
-        float ax = sx * r.ix, ay = sy * r.iy, az = sz * r.iz;
-        float bx = (ox - r.px) * r.ix, by = (oy - r.py) * r.iy, bz = (oz - r.pz) * r.iz;
-        float ex = EPS_REL * (fabsf(ox) + fabsf(r.px) + 255.f * sx) * fabsf(r.ix);
-        float ey = EPS_REL * (fabsf(oy) + fabsf(r.py) + 255.f * sy) * fabsf(r.iy);
-        float ez = EPS_REL * (fabsf(oz) + fabsf(r.pz) + 255.f * sz) * fabsf(r.iz);
+        // plane t = (origin + q s - p) / d = Q a + b with Q = 1 + q 2^-15,
+        // a = 2^15 s / d (exact: s is a power of two), b = (origin - p) / d - a
+        float ax = Q_SCALE * sx * r.ix, ay = Q_SCALE * sy * r.iy, az = Q_SCALE * sz * r.iz;
+        float bx = (ox - r.px) * r.ix - ax, by = (oy - r.py) * r.iy - ay, bz = (oz - r.pz) * r.iz - az;
+        float ex = (EPS_POS * (fabsf(ox) + fabsf(r.px)) + EPS_Q * sx) * fabsf(r.ix);
+        float ey = (EPS_POS * (fabsf(oy) + fabsf(r.py)) + EPS_Q * sy) * fabsf(r.iy);
+        float ez = (EPS_POS * (fabsf(oz) + fabsf(r.pz)) + EPS_Q * sz) * fabsf(r.iz);
         float bnx = bx - ex, bfx = bx + ex, bny = by - ey, bfy = by + ey, bnz = bz - ez, bfz = bz + ez;
         // near-plane bytes: lo for d > 0, hi for d < 0
         uint32_t nx0 = r.nx ? w3.z : w2.x, nx1 = r.nx ? w3.w : w2.y, fx0 = r.nx ? w2.x : w3.z, fx1 = r.nx ? w2.y : w3.w;
@@ -173,12 +179,12 @@ struct NodeOps<AG_BVH_Q8> {
             const int k = c & 3;
             const bool hi = c >= 4;
             uint32_t m = ((hi ? w1.w : w1.z) >> (8 * k)) & 0xffu;
-            float tnx = __fmaf_rn(byte_f(hi ? nx1 : nx0, k), ax, bnx);
-            float tfx = __fmaf_rn(byte_f(hi ? fx1 : fx0, k), ax, bfx);
-            float tny = __fmaf_rn(byte_f(hi ? ny1 : ny0, k), ay, bny);
-            float tfy = __fmaf_rn(byte_f(hi ? fy1 : fy0, k), ay, bfy);
-            float tnz = __fmaf_rn(byte_f(hi ? nz1 : nz0, k), az, bnz);
-            float tfz = __fmaf_rn(byte_f(hi ? fz1 : fz0, k), az, bfz);
+            float tnx = __fmaf_rn(byte_q(hi ? nx1 : nx0, k), ax, bnx);
+            float tfx = __fmaf_rn(byte_q(hi ? fx1 : fx0, k), ax, bfx);
+            float tny = __fmaf_rn(byte_q(hi ? ny1 : ny0, k), ay, bny);
+            float tfy = __fmaf_rn(byte_q(hi ? fy1 : fy0, k), ay, bfy);
+            float tnz = __fmaf_rn(byte_q(hi ? nz1 : nz0, k), az, bnz);
+            float tfz = __fmaf_rn(byte_q(hi ? fz1 : fz0, k), az, bfz);
             float te = fmaxf(fmaxf(tnx, tny), tnz);
             float tx = fminf(fminf(tfx, tfy), tfz);
             if (m != 0 && te <= tx && te <= lim && tx >= -lim) {

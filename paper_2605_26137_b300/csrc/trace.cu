@@ -348,11 +348,13 @@ __device__ __forceinline__ bool coop_step(const TraceArgs &A, const TraceJob &J,
     float sx = __uint_as_float((w0.w & 0xffu) << 23);
     float sy = __uint_as_float(((w0.w >> 8) & 0xffu) << 23);
     float sz = __uint_as_float(((w0.w >> 16) & 0xffu) << 23);
-    float ax = sx * r.ix, ay = sy * r.iy, az = sz * r.iz;
-    float bx = (ox - r.px) * r.ix, by = (oy - r.py) * r.iy, bz = (oz - r.pz) * r.iz;
-    float ex = EPS_REL * (fabsf(ox) + fabsf(r.px) + 255.f * sx) * fabsf(r.ix);
-    float ey = EPS_REL * (fabsf(oy) + fabsf(r.py) + 255.f * sy) * fabsf(r.iy);
-    float ez = EPS_REL * (fabsf(oz) + fabsf(r.pz) + 255.f * sz) * fabsf(r.iz);
+    // plane t = (origin + q s - p) / d = Q a + b with Q = 1 + q 2^-15,
+    // a = 2^15 s / d (exact: s is a power of two), b = (origin - p) / d - a
+    float ax = Q_SCALE * sx * r.ix, ay = Q_SCALE * sy * r.iy, az = Q_SCALE * sz * r.iz;
+    float bx = (ox - r.px) * r.ix - ax, by = (oy - r.py) * r.iy - ay, bz = (oz - r.pz) * r.iz - az;
+    float ex = (EPS_POS * (fabsf(ox) + fabsf(r.px)) + EPS_Q * sx) * fabsf(r.ix);
+    float ey = (EPS_POS * (fabsf(oy) + fabsf(r.py)) + EPS_Q * sy) * fabsf(r.iy);
+    float ez = (EPS_POS * (fabsf(oz) + fabsf(r.pz)) + EPS_Q * sz) * fabsf(r.iz);
     float bnx = bx - ex, bfx = bx + ex, bny = by - ey, bfy = by + ey, bnz = bz - ez, bfz = bz + ez;
     uint32_t nx0 = r.nx ? w3.z : w2.x, nx1 = r.nx ? w3.w : w2.y, fx0 = r.nx ? w2.x : w3.z, fx1 = r.nx ? w2.y : w3.w;
     uint32_t ny0 = r.ny ? w4.x : w2.z, ny1 = r.ny ? w4.y : w2.w, fy0 = r.ny ? w2.z : w4.x, fy1 = r.ny ? w2.w : w4.y;
@@ -367,12 +369,12 @@ __device__ __forceinline__ bool coop_step(const TraceArgs &A, const TraceJob &J,
         const int k = c & 3;
         const bool hi = c >= 4;
         uint32_t m = ((hi ? w1.w : w1.z) >> (8 * k)) & 0xffu;
-        float tnx = __fmaf_rn(byte_f(hi ? nx1 : nx0, k), ax, bnx);
-        float tfx = __fmaf_rn(byte_f(hi ? fx1 : fx0, k), ax, bfx);
-        float tny = __fmaf_rn(byte_f(hi ? ny1 : ny0, k), ay, bny);
-        float tfy = __fmaf_rn(byte_f(hi ? fy1 : fy0, k), ay, bfy);
-        float tnz = __fmaf_rn(byte_f(hi ? nz1 : nz0, k), az, bnz);
-        float tfz = __fmaf_rn(byte_f(hi ? fz1 : fz0, k), az, bfz);
+        float tnx = __fmaf_rn(byte_q(hi ? nx1 : nx0, k), ax, bnx);
+        float tfx = __fmaf_rn(byte_q(hi ? fx1 : fx0, k), ax, bfx);
+        float tny = __fmaf_rn(byte_q(hi ? ny1 : ny0, k), ay, bny);
+        float tfy = __fmaf_rn(byte_q(hi ? fy1 : fy0, k), ay, bfy);
+        float tnz = __fmaf_rn(byte_q(hi ? nz1 : nz0, k), az, bnz);
+        float tfz = __fmaf_rn(byte_q(hi ? fz1 : fz0, k), az, bfz);
         float te = fmaxf(fmaxf(tnx, tny), tnz);
         float tx = fminf(fminf(tfx, tfy), tfz);
         ihit[i] = false;

@@ -15,6 +15,14 @@ namespace {
 // large limit) needs up to 7 x the tree depth; 128 covers depths up to 18.
 constexpr int STACK = 128;
 constexpr float EPS_REL = 4.76837158203125e-07f;  // 2^-21: widening per unit of coordinate magnitude
+// 8-bit node planes are decoded as fma(Q, 2^15 s, origin - 2^15 s) with the
+// exact float Q = 1 + q 2^-15 (byte_q): one PRMT and one FMA per plane.  The
+// extra rounding of origin - 2^15 s is covered by widening per unit of
+// coordinate magnitude by EPS_POS and per unit of the node's scale s by EPS_Q
+// (see the node visits).
+constexpr float EPS_POS = 9.5367431640625e-07f;   // 2^-20
+constexpr float EPS_Q = 0.0078125f;                // 2^-7
+constexpr float Q_SCALE = 32768.0f;                // 2^15
 
 struct TraceArgs {
     TraceJob job0;
@@ -33,9 +41,9 @@ __device__ __forceinline__ const TraceJob &job_of(const TraceArgs &A, int j) {
     return A.n_jobs > 1 ? A.jobs[j] : A.job0;
 }
 
-// byte k of w as an exact float: 2^23 + byte in the bits, minus 2^23
-__device__ __forceinline__ float byte_f(uint32_t w, int k) {
-    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (unsigned)k)) - 8388608.0f;
+// byte k of w in mantissa bits 8..15 of 1.0: the exact float 1 + byte * 2^-15
+__device__ __forceinline__ float byte_q(uint32_t w, int k) {
+    return __uint_as_float(__byte_perm(w, 0x3F800000u, 0x7604u | ((unsigned)k << 4)));
 }
 
 // Traversal bookkeeping of one node visit: the nearest relevant child becomes
