@@ -187,11 +187,16 @@ struct NodeOps<AG_BVH_Q8> {
             float tfz = __fmaf_rn(byte_q(hi ? fz1 : fz0, k), az, bfz);
             float te = fmaxf(fmaxf(tnx, tny), tnz);
             float tx = fminf(fminf(tfx, tfy), tfz);
-            if (m != 0 && te <= tx && te <= lim && tx >= -lim) {
-                if (LEAVES && !(m & 0x80u))
-                    ls->mask |= 1u << c;
-                else
-                    offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status, cap);
+            if (LEAVES) {
+                // an empty slot (m = 0) recorded as a leaf holds no triangle
+                if (te <= tx && te <= lim && tx >= -lim) {
+                    if (m & 0x80u)
+                        offer(child_base + (m & 0x7fu), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status, cap);
+                    else
+                        ls->mask |= 1u << c;
+                }
+            } else if (m != 0 && te <= tx && te <= lim && tx >= -lim) {
+                offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status, cap);
             }
         }
     }
