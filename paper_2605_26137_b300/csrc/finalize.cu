@@ -21,9 +21,26 @@ __device__ __forceinline__ unsigned enc8(float c) {
 }
 
 // One CTA = a TW x TH output tile; the tile plus a G-texel halo is staged in
-// shared memory, G Jacobi passes run there (the valid region shrinks by one
-// texel per pass), then the TW x TH centre is encoded.  G, TW, TH are compile
-// time so the cell loops need no integer division.
+// shared memory by asynchronous copies (no registers held for loads in
+// flight), G Jacobi passes run there in place (the valid region shrinks by
+// one texel per pass), then the TW x TH centre is encoded.  A texel filled in
+// pass p is tagged p + 1 (a ray texel 0, an empty or outside one a large
+// tag), and pass p reads only texels with a tag below p + 1, those filled
+// before it: one buffer serves every pass with no copy between them, and a
+// neighbour's weight is one compare.  The passes run
+// over a list of the tile's empty texels, so the lanes of a warp all do the
+// same neighbour sum rather than splitting between filled and empty texels.
+// G, TW, TH are compile time so the cell loops need no integer division.
+constexpr int RAY = 0, EMPTY = 0x7ffffffe, OUTSIDE = 0x7fffffff;   // texel tags (dilated in pass p: p + 1)
+
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes16) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+
 template <int G, int TW, int TH>
 __global__ void __launch_bounds__(256) k_finalize(const float4 *__restrict__ ntsd, const int32_t *__restrict__ face_map,
                                                   int W, int H, int disp_fp16, uchar4 *__restrict__ rgba,
@@ -31,89 +48,95 @@ __global__ void __launch_bounds__(256) k_finalize(const float4 *__restrict__ nts
                                                   float *__restrict__ aux_nts, float *__restrict__ aux_disp,
                                                   int32_t *__restrict__ aux_hit_tri, float *__restrict__ aux_hit_t) {
     constexpr int BW = TW + 2 * G, BH = TH + 2 * G, CELLS = BW * BH;
-    constexpr int NB = G > 0 ? 2 : 1;
-    __shared__ float4 sv[NB][BH][BW];
-    __shared__ uint8_t sf[NB][BH][BW];   // 0 empty, 1 ray texel, 2 dilated, 3 outside the image
+    static_assert(CELLS < 65536, "cell ids are 16-bit");
+    __shared__ float4 sv[CELLS];
+    __shared__ int32_t sf[CELLS];          // the face map, then the texel tag
+    __shared__ uint16_t todo[CELLS];       // empty texels off the tile's rim
+    __shared__ int n_todo;
     const int x0 = blockIdx.x * TW - G, y0 = blockIdx.y * TH - G;
-    // staging: every cell's face entry and value are loaded without waiting on
-    // each other (the value of an empty texel is read and dropped), all
-    // iterations' loads in flight together
-    constexpr int PER = (CELLS + 255) / 256;
-    int32_t fm[PER];
-    float4 vv[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x + 256 * k;
+    if (threadIdx.x == 0) n_todo = 0;
+    // staging: every cell's face entry and value
+    for (int i = threadIdx.x; i < CELLS; i += 256) {
         const int lx = i % BW, ly = i / BW;
         const int x = x0 + lx, y = y0 + ly;
-        fm[k] = -2;
-        if (i < CELLS && x >= 0 && y >= 0 && x < W && y < H) {
+        if (x >= 0 && y >= 0 && x < W && y < H) {
             const size_t t = (size_t)y * W + x;
-            fm[k] = __ldg(&face_map[t]);
-            vv[k] = __ldg(&ntsd[t]);
+            cp_async(&sf[i], &face_map[t], 0);
+            cp_async(&sv[i], &ntsd[t], 1);
         }
     }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = threadIdx.x + 256 * k;
-        if (i >= CELLS) break;
-        const int lx = i % BW, ly = i / BW;
-        const uint8_t f = fm[k] == -2 ? 3 : (fm[k] >= 0 ? 1 : 0);
-        sv[0][ly][lx] = f == 1 ? vv[k] : make_float4(0.f, 0.f, 1.f, 0.f);
-        sf[0][ly][lx] = f;
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();   // n_todo cleared
+    // tags (each thread the cells it copied); texels that hold no value get
+    // a zero value, so the neighbour sums below can weight every neighbour
+    const int lane = threadIdx.x & 31;
+    for (int i0 = 0; i0 < CELLS; i0 += 256) {
+        const int i = i0 + (int)threadIdx.x;
+        bool add = false;
+        if (i < CELLS) {
+            const int lx = i % BW, ly = i / BW;
+            const int x = x0 + lx, y = y0 + ly;
+            const bool in = x >= 0 && y >= 0 && x < W && y < H;
+            const int f = !in ? OUTSIDE : (sf[i] >= 0 ? RAY : EMPTY);
+            sf[i] = f;
+            if (f != RAY) sv[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            add = f == EMPTY && lx > 0 && ly > 0 && lx < BW - 1 && ly < BH - 1;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, add);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&n_todo, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (add) todo[base + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)i;
     }
     __syncthreads();
-    int cur = 0;
+    const int nt = n_todo;
 #pragma unroll 1
     for (int p = 0; p < G; ++p) {
-        for (int i = threadIdx.x; i < CELLS; i += blockDim.x) {
-            int lx = i % BW, ly = i / BW;
-            float4 v = sv[cur][ly][lx];
-            uint8_t f = sf[cur][ly][lx];
-            if (f == 0 && lx > 0 && ly > 0 && lx < BW - 1 && ly < BH - 1) {
-                float sx = 0.f, sy = 0.f, sz = 0.f, sd = 0.f;
-                int cnt = 0;
+        const int tag = p + 1;
+        for (int j = threadIdx.x; j < nt; j += 256) {
+            const int i = todo[j];
+            if (sf[i] != EMPTY) continue;   // filled by an earlier pass
+            float sx = 0.f, sy = 0.f, sz = 0.f, sd = 0.f, cnt = 0.f;
 #pragma unroll
-                for (int dy = -1; dy <= 1; ++dy)
+            for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        if (dx == 0 && dy == 0) continue;
-                        uint8_t nf = sf[cur][ly + dy][lx + dx];
-                        if (nf == 1 || nf == 2) {
-                            float4 nv = sv[cur][ly + dy][lx + dx];
-                            sx += nv.x; sy += nv.y; sz += nv.z; sd += nv.w;
-                            ++cnt;
-                        }
-                    }
-                if (cnt) {
-                    float inv = 1.0f / (float)cnt;
-                    float3 m = make_float3(sx * inv, sy * inv, sz * inv);
-                    float l2 = dot3(m, m);
-                    float3 n = l2 > 0.f ? m * (1.0f / sqrtf(l2)) : make_float3(0.f, 0.f, 1.f);
-                    v = make_float4(n.x, n.y, n.z, sd * inv);
-                    f = 2;
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (dx == 0 && dy == 0) continue;
+                    // ray texels and texels filled by earlier passes (a
+                    // texel tagged in this pass, or being tagged, has
+                    // weight 0, and its value is not read)
+                    const int n = i + dy * BW + dx;
+                    const float w = sf[n] < tag ? 1.f : 0.f;
+                    const float4 nv = w != 0.f ? sv[n] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    sx += w * nv.x; sy += w * nv.y; sz += w * nv.z; sd += w * nv.w;
+                    cnt += w;
                 }
+            if (cnt > 0.f) {
+                const float inv = 1.0f / cnt;
+                const float3 m = make_float3(sx * inv, sy * inv, sz * inv);
+                const float l2 = dot3(m, m);
+                const float3 nn = l2 > 0.f ? m * (1.0f / sqrtf(l2)) : make_float3(0.f, 0.f, 1.f);
+                sv[i] = make_float4(nn.x, nn.y, nn.z, sd * inv);
+                sf[i] = tag;
             }
-            sv[cur ^ 1][ly][lx] = v;
-            sf[cur ^ 1][ly][lx] = f;
         }
         __syncthreads();
-        cur ^= 1;
     }
     for (int i = threadIdx.x; i < TW * TH; i += blockDim.x) {
         int ox = i % TW, oy = i / TW;
         int x = blockIdx.x * TW + ox, y = blockIdx.y * TH + oy;
         if (x >= W || y >= H) continue;
         size_t t = (size_t)y * W + x;
-        float4 v = sv[cur][oy + G][ox + G];
-        uint8_t f = sf[cur][oy + G][ox + G];
-        bool filled = f == 1 || f == 2;
+        float4 v = sv[(oy + G) * BW + ox + G];
+        const int f = sf[(oy + G) * BW + ox + G];
+        const bool filled = f < EMPTY;
         if (!filled) v = make_float4(0.f, 0.f, 1.f, 0.f);
         rgba[t] = make_uchar4((unsigned char)enc8(v.x), (unsigned char)enc8(v.y), (unsigned char)enc8(v.z),
                               filled ? 255 : 0);
         if (disp_fp16) ((__half *)disp)[t] = __float2half_rn(v.w);
         else ((float *)disp)[t] = v.w;
-        if (f != 1) {
+        if (f != RAY) {
             mask[t] = 0;
             if (aux_hit_tri) aux_hit_tri[t] = -1;
             if (aux_hit_t) aux_hit_t[t] = 0.f;
