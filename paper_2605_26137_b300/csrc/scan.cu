@@ -1,5 +1,6 @@
-// Exclusive prefix sum of unsigned counts, in place, three phases: per-chunk
-// totals, a scan of the chunk totals, and per-chunk scans offset by them.
+// Exclusive prefix sum of unsigned counts, in place, in two launches: per-chunk
+// totals, then per-chunk scans, each chunk's offset summed by its own block
+// from the totals before it (no separate pass over the totals).
 // Used by the radix sort (digit histograms) and by the vertex adjacency
 // (degree counts).
 #include "ag_internal.cuh"
@@ -55,26 +56,16 @@ __global__ void __launch_bounds__(SB) k_scan_reduce(const unsigned *__restrict__
     (void)ex;
 }
 
-// single block: exclusive scan of nb chunk totals, grand total to *total
-__global__ void __launch_bounds__(SB) k_scan_bsums(unsigned *__restrict__ bsum, int nb, unsigned *__restrict__ total) {
-    __shared__ unsigned carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int b0 = 0; b0 < nb; b0 += SB) {
-        int i = b0 + threadIdx.x;
-        unsigned v = i < nb ? bsum[i] : 0u;
-        unsigned ex;
-        unsigned tot = block_excl(v, &ex);
-        if (i < nb) bsum[i] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && total) *total = carry;
-}
-
-__global__ void __launch_bounds__(SB) k_scan_apply(unsigned *__restrict__ d, int64_t n, const unsigned *__restrict__ bsum) {
+// the chunk's offset: the sum of the chunk totals before it (the last chunk
+// also writes the grand total)
+__global__ void __launch_bounds__(SB) k_scan_apply(unsigned *__restrict__ d, int64_t n, const unsigned *__restrict__ bsum,
+                                                   unsigned *__restrict__ total) {
     __shared__ unsigned tile[SCHUNK];
+    unsigned before = 0;
+    for (unsigned j = threadIdx.x; j < blockIdx.x; j += SB) before += __ldg(&bsum[j]);
+    unsigned ex0;
+    const unsigned chunk_off = block_excl(before, &ex0);   // block total = sum of the totals before this chunk
+    if (total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *total = chunk_off + bsum[blockIdx.x];
     int64_t base = (int64_t)blockIdx.x * SCHUNK;
     for (int i = threadIdx.x; i < SCHUNK; i += SB) {
         int64_t j = base + i;
@@ -89,7 +80,7 @@ __global__ void __launch_bounds__(SB) k_scan_apply(unsigned *__restrict__ d, int
     }
     unsigned ex;
     block_excl(s, &ex);
-    unsigned off = bsum[blockIdx.x] + ex;
+    unsigned off = chunk_off + ex;
 #pragma unroll
     for (int k = 0; k < SI; ++k) tile[threadIdx.x * SI + k] = off + loc[k];
     __syncthreads();
@@ -152,8 +143,7 @@ cudaError_t launch_scan_exclusive(unsigned *d, int64_t n, unsigned *total, void 
     }
     unsigned *bsum = static_cast<unsigned *>(scratch);
     k_scan_reduce<<<(unsigned)nb, SB, 0, s>>>(d, n, bsum);
-    k_scan_bsums<<<1, SB, 0, s>>>(bsum, (int)nb, total);
-    k_scan_apply<<<(unsigned)nb, SB, 0, s>>>(d, n, bsum);
+    k_scan_apply<<<(unsigned)nb, SB, 0, s>>>(d, n, bsum, total);
     return cudaGetLastError();
 }
 
