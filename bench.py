@@ -557,8 +557,9 @@ def main():
                          "layout": {"bytes_per_ray": bpl, "achieved": achieved_layout,
                                     "frac": achieved_layout / hbm}},
             "clocks": clocks,
-            # per bake: the low mesh's vertex normals (degree, three scan passes,
-            # fill, gather), face set-up, raster, resolve, traversal, finalize
+            # per bake: the low mesh's vertex normals (degree, two scan passes,
+            # fill, gather), UV set-up, corner frames, raster, resolve,
+            # traversal, finalize
             "gpu_launches": 11 * args.steps}
 
     if not args.no_extras:
