@@ -631,6 +631,216 @@ __global__ void __launch_bounds__(256) k_collapse_tail(CollapseArgs A, int2 *qa,
     }
 }
 
+// One level of the top-down collapse with the SAH decisions, eight lanes per
+// wide node (a warp takes four nodes of the level's queue): lane i holds the
+// node's i-th entry while the decisions are followed (each round every lane
+// splits its entry, the group's new list placed by a prefix sum), then its
+// child's range and box, its share of the counters, its meta byte and its
+// quantised planes (the group searches the exponent together: a candidate
+// holds when it holds for every child).  The result is the node
+// collapse_node writes for the same item, with one node's loads and
+// arithmetic spread over eight lanes rather than chained in one.
+__global__ void __launch_bounds__(128) k_collapse_coop(CollapseArgs A, const int2 *__restrict__ q_in,
+                                                       const int *__restrict__ nq_in, int2 *__restrict__ q_out) {
+    __shared__ int s_sn[4][4][8], s_sk[4][4][8], s_fin[4][4][8];
+    const unsigned FULL = 0xffffffffu;
+    const int nq = *nq_in;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 3, gl = lane & 7;
+    const unsigned gmask = 0xffu << (8 * g);
+    const unsigned below = gmask & ((1u << lane) - 1u);
+    const int n1 = (int)(A.n - 1);
+    // the loop bound is uniform over the warp, so that whole warps call the
+    // counter allocations together
+    for (int q0 = (blockIdx.x * 4 + warp) * 4; q0 < nq; q0 += gridDim.x * 16) {
+        const int qi = q0 + g;
+        const bool live = qi < nq;
+        const int2 item = live ? q_in[qi] : make_int2(0, 0);
+        const int b = item.x;
+        const unsigned wslot = (unsigned)item.y;
+        // ---- children: the SAH decisions followed breadth first
+        int sn = -1, sk = 0;
+        bool fin = true;
+        int nc = 0;
+        if (live) {
+            if (b >= n1 || subtree_count(A, b) <= LEAF_MAX) {
+                nc = 1;   // only the root of a tiny mesh gets here
+                if (gl == 0) sn = b;
+            } else {
+                nc = 2;
+                const int2 c = A.child[b];
+                const int kl = (int)((A.sah_dec[b] >> 18) & 7u) + 1;   // k(8) of the root
+                if (gl == 0) { sn = c.x; sk = kl; fin = false; }
+                if (gl == 1) { sn = c.y; sk = 8 - kl; fin = false; }
+            }
+        }
+        for (int round = 0; round < 8; ++round) {
+            if (gl < nc && !fin && (sn >= n1 || sk == 1)) fin = true;
+            const bool act = gl < nc && !fin;
+            if (!__any_sync(FULL, act)) break;
+            int j = 1, kl = 1;
+            int2 cc = make_int2(0, 0);
+            if (act) {
+                const uint64_t dd = A.sah_dec[sn];
+                cc = A.child[sn];
+                // f(slots) <= slots and 1 <= k(f) < f by construction; the
+                // clamps keep the list within 8 entries whatever the word holds
+                j = min(sk, (int)((dd >> (21 + 3 * (sk - 2))) & 7u) + 1);
+                if (j > 1) kl = min(j - 1, (int)((dd >> (3 * (j - 2))) & 7u) + 1);
+            }
+            const bool split = act && j > 1;
+            const int pc = gl < nc ? (split ? 2 : 1) : 0;
+            int pre = pc;   // inclusive prefix over the group's lanes
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, pre, o, 8);
+                if (gl >= o) pre += t;
+            }
+            const int m = min(8, __shfl_sync(FULL, pre, 7, 8));
+            pre -= pc;
+            if (gl < nc && pre + pc <= 8) {   // (a list of at most 8 entries by construction)
+                if (!split) {
+                    s_sn[warp][g][pre] = sn;
+                    s_sk[warp][g][pre] = act ? 1 : sk;
+                    s_fin[warp][g][pre] = 1;
+                } else {
+                    s_sn[warp][g][pre] = cc.x; s_sk[warp][g][pre] = kl; s_fin[warp][g][pre] = 0;
+                    s_sn[warp][g][pre + 1] = cc.y; s_sk[warp][g][pre + 1] = j - kl; s_fin[warp][g][pre + 1] = 0;
+                }
+            }
+            __syncwarp();
+            if (gl < m) {
+                sn = s_sn[warp][g][gl];
+                sk = s_sk[warp][g][gl];
+                fin = s_fin[warp][g][gl] != 0;
+            }
+            nc = m;
+            __syncwarp();
+        }
+        // ---- this lane's child: triangle count, first sorted position, box
+        const bool has = live && gl < nc;
+        int cnt = 0, first = 0;
+        float clo[3] = {1.f, 1.f, 1.f}, chi[3] = {-1.f, -1.f, -1.f};
+        if (has) {
+            const int2 r = sn >= n1 ? make_int2(sn - n1, sn - n1) : A.range[sn];
+            cnt = r.y - r.x + 1;
+            first = r.x;
+            const float4 lo = A.box_lo[sn], hi = A.box_hi[sn];
+            clo[0] = lo.x; clo[1] = lo.y; clo[2] = lo.z;
+            chi[0] = hi.x; chi[1] = hi.y; chi[2] = hi.z;
+        }
+        const float4 nlo = A.box_lo[live ? b : 0], nhi = A.box_hi[live ? b : 0];
+        const bool inner = has && cnt > LEAF_MAX;
+        const unsigned bal_inner = __ballot_sync(FULL, inner);
+        const int n_int = __popc(bal_inner & gmask);
+        const int rank = __popc(bal_inner & below);
+        const int lcnt = has && !inner ? cnt : 0;
+        int toff = lcnt;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, toff, o, 8);
+            if (gl >= o) toff += t;
+        }
+        const int n_tri = __shfl_sync(FULL, toff, 7, 8);
+        toff -= lcnt;
+        // ---- allocations: one request per node, made by its first lane
+        const unsigned cb = warp_alloc(A.node_count, gl == 0 ? (unsigned)n_int : 0u);
+        const unsigned tb = warp_alloc(A.tri_count, gl == 0 ? (unsigned)n_tri : 0u);
+        const unsigned qb = warp_alloc(reinterpret_cast<unsigned *>(A.q_count_out), gl == 0 ? (unsigned)n_int : 0u);
+        const unsigned child_base = __shfl_sync(FULL, cb, 0, 8);
+        const unsigned tri_base = __shfl_sync(FULL, tb, 0, 8);
+        const unsigned q_base = __shfl_sync(FULL, qb, 0, 8);
+        uint32_t m8 = 0;
+        if (inner) {
+            m8 = 0x80u | (uint32_t)rank;
+            q_out[q_base + rank] = make_int2(sn, (int)(child_base + rank));
+        } else if (has) {
+            m8 = (uint32_t)((cnt << 5) | toff);
+            for (int t = 0; t < cnt; ++t) A.rec_pos[tri_base + toff + t] = (uint32_t)(first + t);
+        }
+        // bytes of the lanes 4w..4w+3 into one word (every lane of the four gets it)
+        auto gather4 = [&](uint32_t byte) {
+            uint32_t w = byte << (8 * (gl & 3));
+            w |= __shfl_xor_sync(FULL, w, 1);
+            w |= __shfl_xor_sync(FULL, w, 2);
+            return w;
+        };
+        const uint32_t meta_w = gather4(m8);
+        if (A.layout == AG_BVH_Q8) {
+            const float o[3] = {nlo.x, nlo.y, nlo.z}, hn[3] = {nhi.x, nhi.y, nhi.z};
+            uint32_t qlw[3], qhw[3];
+            int e[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                // the smallest exponent from the node extent's estimate up
+                // that quantises every child into 0..255 with outward
+                // rounding verified in the traversal's decode fmaf(q, 2^e, o)
+                const float ext = hn[a] - o[a];
+                int ea;
+                if (!(ext > 0.f)) ea = 1;
+                else {
+                    int ex;
+                    frexpf(ext / 255.0f, &ex);
+                    ea = max(1, min(254, ex + 127 - 1));
+                }
+                int ql = 255, qh = 0;
+                for (;; ++ea) {
+                    const float sc = __uint_as_float((unsigned)ea << 23);
+                    const float inv = 1.0f / sc;   // a power of two: x * inv is exactly x / sc
+                    bool ok = true;
+                    ql = 255;
+                    qh = 0;
+                    if (has) {
+                        ql = (int)floorf((clo[a] - o[a]) * inv);
+                        ql = max(0, min(255, ql));
+                        while (ql > 0 && fmaf((float)ql, sc, o[a]) > clo[a]) --ql;
+                        int h = (int)ceilf((chi[a] - o[a]) * inv);
+                        h = max(0, h);
+                        while (h <= 255 && fmaf((float)h, sc, o[a]) < chi[a]) ++h;
+                        while (h > 0 && h - 1 >= ql && fmaf((float)(h - 1), sc, o[a]) >= chi[a]) --h;
+                        if (h > 255 || fmaf((float)ql, sc, o[a]) > clo[a]) ok = false;
+                        qh = min(h, 255);
+                    }
+                    if (__all_sync(gmask, ok) || ea >= 254) break;   // the group searches together
+                }
+                e[a] = ea;
+                qlw[a] = gather4((uint32_t)ql);
+                qhw[a] = gather4((uint32_t)qh);
+            }
+            // the second word of each byte row sits in lane 4 of the group
+            const int src = (lane & ~7) | 4;
+            const uint32_t meta_hi = __shfl_sync(FULL, meta_w, src);
+            uint32_t qlh[3], qhh[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                qlh[a] = __shfl_sync(FULL, qlw[a], src);
+                qhh[a] = __shfl_sync(FULL, qhw[a], src);
+            }
+            if (live && gl == 0) {
+                const uint32_t hdr = (uint32_t)e[0] | ((uint32_t)e[1] << 8) | ((uint32_t)e[2] << 16) | ((uint32_t)nc << 24);
+                uint4 *dst = reinterpret_cast<uint4 *>(static_cast<QNode *>(A.nodes) + wslot);
+                dst[0] = make_uint4(__float_as_uint(o[0]), __float_as_uint(o[1]), __float_as_uint(o[2]), hdr);
+                dst[1] = make_uint4(child_base, tri_base, meta_w, meta_hi);
+                dst[2] = make_uint4(qlw[0], qlh[0], qlw[1], qlh[1]);
+                dst[3] = make_uint4(qlw[2], qlh[2], qhw[0], qhh[0]);
+                dst[4] = make_uint4(qhw[1], qhh[1], qhw[2], qhh[2]);
+            }
+        } else {
+            const uint32_t meta_hi = __shfl_sync(FULL, meta_w, (lane & ~7) | 4);
+            if (live) {
+                FNode *nd = static_cast<FNode *>(A.nodes) + wslot;
+                nd->lox[gl] = clo[0]; nd->loy[gl] = clo[1]; nd->loz[gl] = clo[2];
+                nd->hix[gl] = chi[0]; nd->hiy[gl] = chi[1]; nd->hiz[gl] = chi[2];
+                if (gl == 0) {
+                    nd->child_base = child_base;
+                    nd->tri_base = tri_base;
+                    reinterpret_cast<uint32_t *>(nd->meta)[0] = meta_w;
+                    reinterpret_cast<uint32_t *>(nd->meta)[1] = meta_hi;
+                }
+            }
+        }
+    }
+}
+
 // the 48-byte leaf-order triangle records, one thread per record
 __global__ void k_tri_records(const uint32_t *__restrict__ rec_pos, const unsigned *__restrict__ vals,
                               const float *__restrict__ V, const int32_t *__restrict__ F, int64_t nv, int64_t n,
@@ -781,9 +991,12 @@ ag_status build_bvh(const float *d_verts, int64_t nv, const int32_t *d_faces, in
     int grid_levels = COLLAPSE_LEVELS;
     if (const char *e = getenv("AG_TEST_GRID_LEVELS")) grid_levels = std::max(0, std::min(COLLAPSE_LEVELS, atoi(e)));
     int2 *qin = q0, *qout = q1;
+    // the SAH collapse takes eight lanes per wide node
+    const unsigned cgrid_coop = (unsigned)std::min<int64_t>(grid_for(n, 16), (int64_t)device_sm_count(dev) * 32);
     for (int l = 0; l < grid_levels; ++l) {
         A.q_count_out = lcounts + l + 1;
-        k_collapse<<<cgrid, 128, 0, s>>>(A, qin, lcounts + l, qout);
+        if (rule == AG_COLLAPSE_SAH) k_collapse_coop<<<cgrid_coop, 128, 0, s>>>(A, qin, lcounts + l, qout);
+        else k_collapse<<<cgrid, 128, 0, s>>>(A, qin, lcounts + l, qout);
         AG_CUDA_LAUNCH("k_collapse");
         std::swap(qin, qout);
     }
