@@ -187,42 +187,47 @@ __global__ void __launch_bounds__(RS_BLOCK) k_rs_scatter(const unsigned *__restr
 // ---- Karras 2012 hierarchy ----------------------------------------------------------
 // Internal nodes 0..n-2, leaves n-1+k.  child[i] = (left, right), range[i] =
 // (first, last) sorted positions covered.
-__device__ __forceinline__ int delta(const unsigned *__restrict__ k, int64_t n, int64_t i, int64_t j) {
+
+// (32-bit positions: the build takes fewer than 2^29 triangles; the key at i
+// is read once)
+__device__ __forceinline__ int delta_at(const unsigned *__restrict__ k, int n, int i, unsigned ki, int j) {
     if (j < 0 || j >= n) return -1;
-    unsigned a = k[i], b = k[j];
-    if (a == b) return 32 + __clz((unsigned)(i ^ j));
-    return __clz(a ^ b);
+    const unsigned b = __ldg(&k[j]);
+    if (ki == b) return 32 + __clz((unsigned)(i ^ j));
+    return __clz(ki ^ b);
 }
 
-__global__ void k_karras(const unsigned *__restrict__ k, int64_t n, int2 *__restrict__ child,
+__global__ void k_karras(const unsigned *__restrict__ k, int64_t n64, int2 *__restrict__ child,
                          int2 *__restrict__ range, int *__restrict__ parent) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = (int)n64;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
-    int d = (delta(k, n, i, i + 1) - delta(k, n, i, i - 1)) >= 0 ? 1 : -1;
-    int dmin = delta(k, n, i, i - d);
-    int64_t lmax = 2;
-    while (delta(k, n, i, i + lmax * d) > dmin) lmax <<= 1;
-    int64_t l = 0;
-    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(k, n, i, i + (l + t) * d) > dmin) l += t;
-    int64_t j = i + l * d;
-    int dnode = delta(k, n, i, j);
-    int64_t s = 0;
-    int64_t div = 2;
+    const unsigned ki = __ldg(&k[i]);
+    const int d = (delta_at(k, n, i, ki, i + 1) - delta_at(k, n, i, ki, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta_at(k, n, i, ki, i - d);
+    int lmax = 2;
+    while (delta_at(k, n, i, ki, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta_at(k, n, i, ki, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta_at(k, n, i, ki, j);
+    int s = 0;
+    int div = 2;
     while (true) {
-        int64_t t = (l + div - 1) / div;
-        if (delta(k, n, i, i + (s + t) * d) > dnode) s += t;
+        const int t = (l + div - 1) / div;
+        if (delta_at(k, n, i, ki, i + (s + t) * d) > dnode) s += t;
         if (t <= 1) break;
         div <<= 1;
     }
-    int64_t gamma = i + s * d + min(d, 0);
-    int64_t lo = min(i, j), hi = max(i, j);
-    int left = (lo == gamma) ? (int)(n - 1 + gamma) : (int)gamma;
-    int right = (hi == gamma + 1) ? (int)(n - 1 + gamma + 1) : (int)(gamma + 1);
+    const int gamma = i + s * d + min(d, 0);
+    const int lo = min(i, j), hi = max(i, j);
+    const int left = (lo == gamma) ? n - 1 + gamma : gamma;
+    const int right = (hi == gamma + 1) ? n - 1 + gamma + 1 : gamma + 1;
     child[i] = make_int2(left, right);
-    range[i] = make_int2((int)lo, (int)hi);
-    parent[left] = (int)i;
-    parent[right] = (int)i;
+    range[i] = make_int2(lo, hi);
+    parent[left] = i;
+    parent[right] = i;
 }
 
 // ---- SAH-optimal collapse (AG_COLLAPSE_SAH) ---------------------------------------------
