@@ -218,7 +218,12 @@ AG_API void ag_opts_default(ag_opts *o);
  * ag_bvh_copy_out, ag_visibility, ag_render_views, ag_point_distance and
  * calls on an AG_BVH_F32 tree wait for the build the first time they need
  * its summary (node count, depth, scene box); ag_bake, ag_bake_backward and
- * ag_bake_batch on an AG_BVH_Q8 tree do not wait.
+ * ag_bake_batch on an AG_BVH_Q8 tree do not wait on the host.  ag_bake,
+ * ag_bake_backward, ag_point_distance and ag_normal_map_error called on
+ * another stream order their tree traversal after the build themselves (an
+ * event wait, skipped while that stream is being captured), so a bake's
+ * raster and frames may run beside the build; ag_bake_batch relies on the
+ * caller's ordering.
  * Test hook: the environment variable AG_TEST_GRID_LEVELS=k (0..16) runs the
  * collapse levels from k on in the single-CTA kernel that otherwise serves
  * only trees deeper than 16 levels; the tree is the same.

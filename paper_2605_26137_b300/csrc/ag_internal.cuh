@@ -152,6 +152,11 @@ ag_status bvh_ready(ag_bvh *h);
 // FP32-node traversal; the 8-bit-node traversal does not use it, so for such
 // a tree this returns 0 without waiting for the build
 ag_status scene_abs_for(ag_bvh *h, float *out);
+// work enqueued on s after this waits for the handle's build (an
+// asynchronous build may run on another stream); nothing once the build's
+// summary has been read, nor while s is being captured (the capture must
+// order the build itself, as every stream-ordered call does)
+cudaError_t wait_build(const ag_bvh *h, cudaStream_t s);
 
 // ------------------------------------------------------------------ per-asset bake job
 // Everything the trace needs for one asset (device-resident table).

@@ -438,6 +438,7 @@ AG_API ag_status ag_bake(ag_bvh_t h, const float *d_lverts, const float *d_lnorm
     L.block_size = o.block_size;
     L.blocks_per_sm = o.blocks_per_sm;
     L.backward = false;
+    AG_CUDA(wait_build(h, s));   // (the raster and frames above need no tree)
     AG_CUDA(launch_trace(L, s));
     if (ev) AG_CUDA(cudaEventRecord(ev[2], s));
     AG_CUDA(launch_finalize(a.ntsd, a.face, W, H, o.gutter, o.disp_fp16, d_normal_rgba8, d_mask, d_disp, ax.normal_ts,
@@ -500,6 +501,7 @@ AG_API ag_status ag_bake_backward(ag_bvh_t h, const float *d_lverts, const float
     L.block_size = o.block_size;
     L.blocks_per_sm = o.blocks_per_sm;
     L.backward = true;
+    AG_CUDA(wait_build(h, s));   // (the raster and frames above need no tree)
     AG_CUDA(launch_trace(L, s));
     AG_CUDA(launch_backward_finish(a.lpos, a.lface, n_lverts, n_lfaces, a.acc, g_pos, g_nrm, g_a, loss_acc, lambda,
                                    d_loss, d_grad, s));
@@ -549,6 +551,7 @@ AG_API ag_status ag_normal_map_error(ag_bvh_t h, const float *d_lverts, const fl
     L.status = status;
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = h->layout;
+    AG_CUDA(wait_build(h, s));
     AG_CUDA(launch_map_error(L, d_normal_rgba8, d_luv, n_lfaces, d_sample_face, d_sample_bary, n_samples, d_angle_deg,
                              s));
     return AG_OK;
@@ -576,6 +579,7 @@ AG_API ag_status ag_point_distance(ag_bvh_t h, const float *d_points, int64_t n_
     L.status = status;
     L.max_steps = o.max_steps > 0 ? o.max_steps : (1 << 20);
     L.layout = h->layout;
+    AG_CUDA(wait_build(h, (cudaStream_t)stream));
     AG_CUDA(launch_point_distance(L, d_points, n_points, max_dist, d_dist, d_tri, (cudaStream_t)stream));
     return AG_OK;
 }

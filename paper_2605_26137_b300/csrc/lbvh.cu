@@ -1063,6 +1063,14 @@ ag_status bvh_ready(ag_bvh *h) {
     return AG_OK;
 }
 
+cudaError_t wait_build(const ag_bvh *h, cudaStream_t s) {
+    if (h->ready || !h->ev_done) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) return e;   // a capture orders it itself
+    return cudaStreamWaitEvent(s, h->ev_done, 0);
+}
+
 ag_status scene_abs_for(ag_bvh *h, float *out) {
     *out = 0.f;
     if (h->layout == AG_BVH_Q8) return AG_OK;
