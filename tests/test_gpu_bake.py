@@ -494,6 +494,33 @@ def test_sah_collapse_costs_no_more_than_greedy_rules():
         assert cost["sah"] <= cost[rule] * (1 + 1e-5), rule
 
 
+def test_async_build_on_another_stream():
+    """A handle built asynchronously on one stream and baked on another with
+    no ordering by the caller: the bake orders its traversal after the build
+    (its raster and frames may run beside it) and gives the maps of a bake
+    on the build's own stream."""
+    import paper_2605_26137_b300 as pb
+    a = synth.sdf_asset(6, 200_000, 6_000, 512, 512, n_prims=16)
+    hv, hf = _t(a.high_v), _t(a.high_f)
+    lv, lf, uv = _t(a.low_v), _t(a.low_f), _t(a.low_uv)
+    ref_bvh = pb.Bvh(hv, hf)
+    ref = parity.to_numpy(pb.bake(ref_bvh, lv, lf, uv, a.W, a.H, a.max_dist, aux=True))
+    ref_bvh.free()
+    torch.cuda.synchronize()
+    sb, sk = torch.cuda.Stream(), torch.cuda.Stream()
+    with torch.cuda.stream(sb):
+        bvh = pb.Bvh(hv, hf, async_build=True, stream=sb)
+    with torch.cuda.stream(sk):
+        o = pb.bake(bvh, lv, lf, uv, a.W, a.H, a.max_dist, aux=True, stream=sk)
+    sk.synchronize()
+    sb.synchronize()
+    pb.sync_status()
+    out = parity.to_numpy(o)
+    for k in ("normal_rgba8", "mask", "disp", "hit_tri"):
+        assert np.array_equal(out[k], ref[k]), k
+    bvh.free()
+
+
 @pytest.mark.parametrize("layout", ["q8", "f32"])
 def test_async_build_and_one_cta_collapse_give_identical_bakes(layout, monkeypatch):
     """A build that returns without a host round trip (the bake is enqueued
