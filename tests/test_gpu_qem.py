@@ -71,12 +71,12 @@ def test_round_limit_and_unreachable_target():
     assert rounds == 0 and len(fo) == 4 and len(vo) == 4
 
 
-@pytest.mark.parametrize("max_rounds", [7, 8, 9, 16, 17])
+@pytest.mark.parametrize("max_rounds", [7, 8, 9, 16, 17, 41])
 def test_round_caps_across_enqueued_batches(max_rounds):
     """The rounds are enqueued eight at a time and stop on the device: a cap
-    that falls inside, at the end of, or just past a batch, and across the
-    renumbering of the working mesh (32k faces reach a quarter after a few
-    rounds), leaves the same mesh and round count as the oracle."""
+    that falls inside, at the end of, or just past a batch (and one well past
+    the renumbering of the working mesh, when its alive faces fall to a
+    quarter) leaves the same mesh and round count as the oracle."""
     V, F = synth.sdf_mesh(synth.sdf_union_params(3, 12), 48, device="cpu")
     assert_identical(V, F, 500, max_rounds=max_rounds)
 
