@@ -179,24 +179,23 @@ struct NodeOps<AG_BVH_Q8> {
             const int k = c & 3;
             const bool hi = c >= 4;
             uint32_t m = ((hi ? w1.w : w1.z) >> (8 * k)) & 0xffu;
-            float tnx = __fmaf_rn(byte_q(hi ? nx1 : nx0, k), ax, bnx);
-            float tfx = __fmaf_rn(byte_q(hi ? fx1 : fx0, k), ax, bfx);
-            float tny = __fmaf_rn(byte_q(hi ? ny1 : ny0, k), ay, bny);
-            float tfy = __fmaf_rn(byte_q(hi ? fy1 : fy0, k), ay, bfy);
-            float tnz = __fmaf_rn(byte_q(hi ? nz1 : nz0, k), az, bnz);
-            float tfz = __fmaf_rn(byte_q(hi ? fz1 : fz0, k), az, bfz);
-            float te = fmaxf(fmaxf(tnx, tny), tnz);
-            float tx = fminf(fminf(tfx, tfy), tfz);
+            // near and far plane of an axis in one packed FMA
+            float tnx, tfx, tny, tfy, tnz, tfz;
+            fma2(byte_q(hi ? nx1 : nx0, k), byte_q(hi ? fx1 : fx0, k), ax, ax, bnx, bfx, tnx, tfx);
+            fma2(byte_q(hi ? ny1 : ny0, k), byte_q(hi ? fy1 : fy0, k), ay, ay, bny, bfy, tny, tfy);
+            fma2(byte_q(hi ? nz1 : nz0, k), byte_q(hi ? fz1 : fz0, k), az, az, bnz, bfz, tnz, tfz);
+            float te = max3f(tnx, tny, tnz);
+            float tx = min3f(tfx, tfy, tfz);
             if (LEAVES) {
                 // an empty slot (m = 0) recorded as a leaf holds no triangle
                 if (te <= tx && te <= lim && tx >= -lim) {
                     if (m & 0x80u)
-                        offer(child_base + (m & 0x7fu), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status, cap);
+                        offer(child_base + (m & 0x7fu), max3f(te, -tx, 0.f), nx, stack, sp, status, cap);
                     else
                         ls->mask |= 1u << c;
                 }
             } else if (m != 0 && te <= tx && te <= lim && tx >= -lim) {
-                offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status, cap);
+                offer(child_ref(m, child_base, tri_base), max3f(te, -tx, 0.f), nx, stack, sp, status, cap);
             }
         }
     }
@@ -231,14 +230,17 @@ struct NodeOps<AG_BVH_F32> {
                 float plx = __uint_as_float(r.nx ? HX[k] : LX[k]), pfx = __uint_as_float(r.nx ? LX[k] : HX[k]);
                 float ply = __uint_as_float(r.ny ? HY[k] : LY[k]), pfy = __uint_as_float(r.ny ? LY[k] : HY[k]);
                 float plz = __uint_as_float(r.nz ? HZ[k] : LZ[k]), pfz = __uint_as_float(r.nz ? LZ[k] : HZ[k]);
-                float te = fmaxf(fmaxf(__fmaf_rn(plx, r.ix, cnx), __fmaf_rn(ply, r.iy, cny)), __fmaf_rn(plz, r.iz, cnz));
-                float tx = fminf(fminf(__fmaf_rn(pfx, r.ix, cfx), __fmaf_rn(pfy, r.iy, cfy)), __fmaf_rn(pfz, r.iz, cfz));
+                float tnx, tfx, tny, tfy, tnz, tfz;
+                fma2(plx, pfx, r.ix, r.ix, cnx, cfx, tnx, tfx);
+                fma2(ply, pfy, r.iy, r.iy, cny, cfy, tny, tfy);
+                fma2(plz, pfz, r.iz, r.iz, cnz, cfz, tnz, tfz);
+                float te = max3f(tnx, tny, tnz);
+                float tx = min3f(tfx, tfy, tfz);
                 if (m != 0 && te <= tx && te <= lim && tx >= -lim) {
                     if (LEAVES && !(m & 0x80u))
                         ls->mask |= 1u << (4 * half + k);
                     else
-                        offer(child_ref(m, child_base, tri_base), fmaxf(fmaxf(te, -tx), 0.f), nx, stack, sp, status,
-                              cap);
+                        offer(child_ref(m, child_base, tri_base), max3f(te, -tx, 0.f), nx, stack, sp, status, cap);
                 }
             }
         }

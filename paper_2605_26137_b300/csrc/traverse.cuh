@@ -41,6 +41,29 @@ __device__ __forceinline__ const TraceJob &job_of(const TraceArgs &A, int j) {
     return A.n_jobs > 1 ? A.jobs[j] : A.job0;
 }
 
+// Blackwell's three-input FP32 minimum / maximum (one instruction each; the
+// same value and NaN rule as two fminf / fmaxf) and its packed FP32 FMA, which
+// rounds each of its two lanes exactly as a scalar fmaf does.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+// (d0, d1) = (fma(a0, b0, c0), fma(a1, b1, c1)) in one packed instruction
+__device__ __forceinline__ void fma2(float a0, float a1, float b0, float b1, float c0, float c1, float &d0,
+                                     float &d1) {
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+
 // byte k of w in mantissa bits 8..15 of 1.0: the exact float 1 + byte * 2^-15
 __device__ __forceinline__ float byte_q(uint32_t w, int k) {
     return __uint_as_float(__byte_perm(w, 0x3F800000u, 0x7604u | ((unsigned)k << 4)));
