@@ -70,16 +70,24 @@ struct Best {
     bool found;
 };
 
-__device__ __forceinline__ void test_tri(const Ray &r, const float4 *__restrict__ tris,
-                                         const int32_t *__restrict__ tri_ids, uint32_t rec, Best &b) {
-    float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
-    float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+// the three edge functions of triangle (A, B, C) in ray space, and the
+// vertices' sheared depths
+__device__ __forceinline__ void tri_edges(const Ray &r, float4 A, float4 B, float4 C, float &U, float &V, float &W,
+                                          float &Az, float &Bz, float &Cz) {
+    float Ax, Ay, Bx, By, Cx, Cy;
     xform(r, A, Ax, Ay, Az);
     xform(r, B, Bx, By, Bz);
     xform(r, C, Cx, Cy, Cz);
-    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+}
+
+__device__ __forceinline__ void test_tri(const Ray &r, const float4 *__restrict__ tris,
+                                         const int32_t *__restrict__ tri_ids, uint32_t rec, Best &b) {
+    float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
+    float U, V, W, Az, Bz, Cz;
+    tri_edges(r, A, B, C, U, V, W, Az, Bz, Cz);
     if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return;
     float det = U + V + W;
     if (det == 0.f) return;
@@ -108,13 +116,8 @@ __device__ __forceinline__ void test_tri_shared(const Ray &r, const float4 *__re
                                                 const int32_t *__restrict__ tri_ids, uint32_t rec, Best &b,
                                                 float &lim) {
     float4 A = __ldg(&tris[3 * (size_t)rec]), B = __ldg(&tris[3 * (size_t)rec + 1]), C = __ldg(&tris[3 * (size_t)rec + 2]);
-    float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
-    xform(r, A, Ax, Ay, Az);
-    xform(r, B, Bx, By, Bz);
-    xform(r, C, Cx, Cy, Cz);
-    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    float U, V, W, Az, Bz, Cz;
+    tri_edges(r, A, B, C, U, V, W, Az, Bz, Cz);
     if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return;
     float det = U + V + W;
     if (det == 0.f) return;
