@@ -245,19 +245,16 @@ struct PointNode<AG_BVH_F32> {
     }
 };
 
-__device__ __forceinline__ void setup_point(const TraceArgs &A, long long r, PointState &S) {
+// jw: the query's asset when JOBS is JOBS_MANY (found by the caller)
+template <int JOBS>
+__device__ __forceinline__ void setup_point(const TraceArgs &A, long long r, PointState &S, int jw) {
     int j = 0;
     long long local = r;
-    if (A.n_jobs > 1) {
-        int lo = 0, hi = A.n_jobs - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (A.job_begin[mid] <= r) lo = mid; else hi = mid - 1;
-        }
-        j = lo;
+    if (JOBS == JOBS_MANY) {
+        j = jw;
         local = r - A.job_begin[j];
     }
-    const TraceJob &J = job_of(A, j);
+    const TraceJob &J = job_t<JOBS>(A, j);
     int4 rr = J.rays[local];
     S.job = j;
     S.texel = rr.x;
@@ -323,8 +320,9 @@ __device__ __forceinline__ bool step_point_leaves(const TraceArgs &A, const Trac
     return true;
 }
 
+template <int JOBS>
 __device__ __forceinline__ void finish_point(const TraceArgs &A, const PointState &S) {
-    const TraceJob &J = job_of(A, S.job);
+    const TraceJob &J = job_t<JOBS>(A, S.job);
     const bool hit = S.best.found;
     float3 nh = make_float3(0.f, 0.f, 1.f);
     float disp = 0.f;
@@ -348,7 +346,10 @@ __device__ __forceinline__ void finish_point(const TraceArgs &A, const PointStat
     store_forward(J, S.texel, S.face, S.fi, S.b1, S.b2, S.d, hit, nh, disp, hit_id);
 }
 
-template <int LAYOUT, bool COUNT>
+// JOBS: one asset (JOBS_ONE, its job in the kernel's parameters) or a batch
+// (JOBS_MANY: the warp finds the asset of its first query, each lane steps on
+// from there, and the asset's traversal fields stay in registers per query).
+template <int LAYOUT, bool COUNT, int JOBS>
 __global__ void __launch_bounds__(256) k_closest(TraceArgs A) {
     const int lane = threadIdx.x & 31;
     const long long n_total = *A.n_rays_dev;
@@ -361,14 +362,27 @@ __global__ void __launch_bounds__(256) k_closest(TraceArgs A) {
         base = __shfl_sync(0xffffffffu, base, 0);
         if ((long long)base >= n_total) break;
         long long r = (long long)base + lane;
+        int jw = 0;
+        if (JOBS == JOBS_MANY) {
+            if (lane == 0) jw = find_job(A, (long long)base);
+            jw = __shfl_sync(0xffffffffu, jw, 0);
+        }
         if (r >= n_total) continue;
-        setup_point(A, r, S);
+        if (JOBS == JOBS_MANY)
+            while (jw + 1 < A.n_jobs && A.job_begin[jw + 1] <= r) ++jw;
+        setup_point<JOBS>(A, r, S, jw);
         if (COUNT) ++c_rays;
-        const TraceJob &J = job_of(A, S.job);
-        while (step_point_leaves<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+        if (JOBS == JOBS_MANY) {
+            const TraceJob J = A.jobs[S.job];
+            while (step_point_leaves<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+            }
+        } else {
+            const TraceJob &J = A.job0;
+            while (step_point_leaves<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+            }
         }
         if (COUNT && S.best.found) ++c_hits;
-        finish_point(A, S);
+        finish_point<JOBS>(A, S);
     }
     flush_counters<COUNT>(A, c_rays, c_nodes, c_tris, c_hits);
 }
@@ -381,11 +395,15 @@ cudaError_t launch_one(const TraceLaunch &L, const TraceArgs &A, cudaStream_t s)
     int bps = L.blocks_per_sm;
     if (bps <= 0) {
         int occ = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_closest<LAYOUT, COUNT>, block, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, A.n_jobs > 1 ? k_closest<LAYOUT, COUNT, JOBS_MANY> : k_closest<LAYOUT, COUNT, JOBS_ONE>, block, 0);
         bps = occ > 0 ? occ : 1;
     }
     unsigned grid = (unsigned)(device_sm_count(dev) * bps);
-    k_closest<LAYOUT, COUNT><<<grid, block, 0, s>>>(A);
+    if (A.n_jobs > 1)
+        k_closest<LAYOUT, COUNT, JOBS_MANY><<<grid, block, 0, s>>>(A);
+    else
+        k_closest<LAYOUT, COUNT, JOBS_ONE><<<grid, block, 0, s>>>(A);
     return cudaGetLastError();
 }
 

@@ -76,20 +76,19 @@ __device__ __forceinline__ TexelRay texel_ray(const TraceJob &J, long long local
     return t;
 }
 
-template <bool KEEP>
-__device__ __forceinline__ void setup_ray(const TraceArgs &A, long long r, RayState &S) {
+// jw: the ray's asset when JOBS is JOBS_MANY (found by the caller)
+template <bool KEEP, int JOBS = JOBS_ANY>
+__device__ __forceinline__ void setup_ray(const TraceArgs &A, long long r, RayState &S, int jw = 0) {
     int j = 0;
     long long local = r;
-    if (A.n_jobs > 1) {
-        int lo = 0, hi = A.n_jobs - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (A.job_begin[mid] <= r) lo = mid; else hi = mid - 1;
-        }
-        j = lo;
+    if (JOBS == JOBS_MANY) {
+        j = jw;
+        local = r - A.job_begin[j];
+    } else if (JOBS == JOBS_ANY && A.n_jobs > 1) {
+        j = find_job(A, r);
         local = r - A.job_begin[j];
     }
-    const TraceJob &J = job_of(A, j);
+    const TraceJob &J = job_t<JOBS>(A, j);
     const TexelRay t = texel_ray(J, local);
     S.job = j;
     S.local = (int)local;
@@ -165,9 +164,9 @@ __device__ __forceinline__ void flush_loss(const TraceArgs &A, LossAcc &L) {
 }
 
 // Shading (forward) or the adjoint of the loss (backward) of a finished ray.
-template <bool BWD, bool KEEP>
+template <bool BWD, bool KEEP, int JOBS = JOBS_ANY>
 __device__ __forceinline__ void finish(const TraceArgs &A, RayState &S, LossAcc &L) {
-    const TraceJob &J = job_of(A, S.job);
+    const TraceJob &J = job_t<JOBS>(A, S.job);
     const TexelRay tr = KEEP ? S.tex : texel_ray(J, S.local);
     const bool hit = S.best.found;
     const float3 d = tr.d;
@@ -232,7 +231,7 @@ __device__ __forceinline__ void finish(const TraceArgs &A, RayState &S, LossAcc 
 
 // Schedule "batch": a warp takes 32 consecutive rays and runs all of them to
 // completion before taking the next 32.
-template <int LAYOUT, bool BWD, bool COUNT>
+template <int LAYOUT, bool BWD, bool COUNT, int JOBS = JOBS_ANY>
 __device__ __forceinline__ void trace_batch(const TraceArgs &A) {
     const int lane = threadIdx.x & 31;
     const long long n_total = *A.n_rays_dev;
@@ -246,22 +245,38 @@ __device__ __forceinline__ void trace_batch(const TraceArgs &A) {
         base = __shfl_sync(0xffffffffu, base, 0);
         if ((long long)base >= n_total) break;
         long long r = (long long)base + lane;
+        int jw = 0;
+        if (JOBS == JOBS_MANY) {
+            // one search per warp, for its first ray; a lane past the end of
+            // that asset steps on (a warp's 32 consecutive rays rarely span two)
+            if (lane == 0) jw = find_job(A, (long long)base);
+            jw = __shfl_sync(0xffffffffu, jw, 0);
+        }
         if (r >= n_total) continue;
-        setup_ray<Keep<LAYOUT, BWD>::value>(A, r, S);
+        if (JOBS == JOBS_MANY)
+            while (jw + 1 < A.n_jobs && A.job_begin[jw + 1] <= r) ++jw;
+        setup_ray<Keep<LAYOUT, BWD>::value, JOBS>(A, r, S, jw);
         if (COUNT) ++c_rays;
-        const TraceJob &J = job_of(A, S.job);
-        while (step_leaves<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+        if (JOBS == JOBS_MANY) {
+            // the asset's traversal fields in registers for the whole ray
+            const TraceJob J = A.jobs[S.job];
+            while (step_leaves<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+            }
+        } else {
+            const TraceJob &J = job_t<JOBS>(A, S.job);
+            while (step_leaves<LAYOUT, COUNT>(A, J, S, stack, c_nodes, c_tris)) {
+            }
         }
         if (COUNT && S.best.found) ++c_hits;
-        finish<BWD, Keep<LAYOUT, BWD>::value>(A, S, L);
+        finish<BWD, Keep<LAYOUT, BWD>::value, JOBS>(A, S, L);
     }
     if (BWD) flush_loss(A, L);
     flush_counters<COUNT>(A, c_rays, c_nodes, c_tris, c_hits);
 }
 
-template <int LAYOUT, bool BWD, bool COUNT>
+template <int LAYOUT, bool BWD, bool COUNT, int JOBS>
 __global__ void __launch_bounds__(256) k_trace(TraceArgs A) {
-    trace_batch<LAYOUT, BWD, COUNT>(A);
+    trace_batch<LAYOUT, BWD, COUNT, JOBS>(A);
 }
 
 // The forward bake over 8-bit nodes, held to 64 registers (4 blocks of 256
@@ -272,7 +287,12 @@ __global__ void __launch_bounds__(256) k_trace(TraceArgs A) {
 #define AG_FWD_MIN_BLOCKS 4
 #endif
 __global__ void __launch_bounds__(256, AG_FWD_MIN_BLOCKS) k_trace_fwd_q8(TraceArgs A) {
-    trace_batch<AG_BVH_Q8, false, false>(A);
+    trace_batch<AG_BVH_Q8, false, false, JOBS_ONE>(A);
+}
+
+// The same for a batch of assets (A.n_jobs > 1).
+__global__ void __launch_bounds__(256, AG_FWD_MIN_BLOCKS) k_trace_fwd_q8_many(TraceArgs A) {
+    trace_batch<AG_BVH_Q8, false, false, JOBS_MANY>(A);
 }
 
 // Schedule "refill": lanes take new rays as they finish.  When at least
@@ -567,18 +587,25 @@ cudaError_t launch_one(const TraceLaunch &L, const TraceArgs &A, cudaStream_t s)
         if (refill)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_refill<LAYOUT, BWD, COUNT>, block, 0);
         else if (fwd_q8)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace_fwd_q8, block, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, A.n_jobs > 1 ? k_trace_fwd_q8_many : k_trace_fwd_q8,
+                                                          block, 0);
         else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_trace<LAYOUT, BWD, COUNT>, block, 0);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, A.n_jobs > 1 ? k_trace<LAYOUT, BWD, COUNT, JOBS_MANY> : k_trace<LAYOUT, BWD, COUNT, JOBS_ONE>,
+                block, 0);
         bps = occ > 0 ? occ : 1;
     }
     unsigned grid = (unsigned)(device_sm_count(dev) * bps);
     if (refill)
         k_trace_refill<LAYOUT, BWD, COUNT><<<grid, block, 0, s>>>(A, 8);
+    else if (fwd_q8 && A.n_jobs > 1)
+        k_trace_fwd_q8_many<<<grid, block, 0, s>>>(A);
     else if (fwd_q8)
         k_trace_fwd_q8<<<grid, block, 0, s>>>(A);
+    else if (A.n_jobs > 1)
+        k_trace<LAYOUT, BWD, COUNT, JOBS_MANY><<<grid, block, 0, s>>>(A);
     else
-        k_trace<LAYOUT, BWD, COUNT><<<grid, block, 0, s>>>(A);
+        k_trace<LAYOUT, BWD, COUNT, JOBS_ONE><<<grid, block, 0, s>>>(A);
     return cudaGetLastError();
 }
 

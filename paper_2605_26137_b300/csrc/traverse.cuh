@@ -41,6 +41,27 @@ __device__ __forceinline__ const TraceJob &job_of(const TraceArgs &A, int j) {
     return A.n_jobs > 1 ? A.jobs[j] : A.job0;
 }
 
+// How a kernel finds a ray's asset: from A.n_jobs at run time (JOBS_ANY), or
+// fixed when it is compiled: one asset (JOBS_ONE, the job in the kernel's
+// parameters) or a batch (JOBS_MANY, the device table).
+enum { JOBS_ANY = 0, JOBS_ONE = 1, JOBS_MANY = 2 };
+template <int JOBS>
+__device__ __forceinline__ const TraceJob &job_t(const TraceArgs &A, int j) {
+    if (JOBS == JOBS_ONE) return A.job0;
+    if (JOBS == JOBS_MANY) return A.jobs[j];
+    return job_of(A, j);
+}
+
+// the asset of global ray r: the last j with job_begin[j] <= r
+__device__ __forceinline__ int find_job(const TraceArgs &A, long long r) {
+    int lo = 0, hi = A.n_jobs - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (A.job_begin[mid] <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Blackwell's three-input FP32 minimum / maximum (one instruction each; the
 // same value and NaN rule as two fminf / fmaxf) and its packed FP32 FMA, which
 // rounds each of its two lanes exactly as a scalar fmaf does.
