@@ -96,7 +96,7 @@ __device__ __forceinline__ Ray vis_ray(const VisArgs &A, int view, int px, int p
     const float y = __fmaf_rn((float)py + 0.5f, A.scale, -A.R);
     const float3 off = f3(G.e1) * x + f3(G.e2) * y;
     Ray ray = A.templ[view];
-    ray.ox = pick(off, ray.kx); ray.oy = pick(off, ray.ky); ray.oz = pick(off, ray.kz);
+    ray.ox = pick(off, ray.kx()); ray.oy = pick(off, ray.ky()); ray.oz = pick(off, ray.kz());
     const float3 p = f3(G.base) + off;
     ray.px = p.x; ray.py = p.y; ray.pz = p.z;
     return ray;

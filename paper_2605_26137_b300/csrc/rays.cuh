@@ -14,15 +14,22 @@ namespace ag {
 namespace {
 
 struct Ray {
-    // exact-origin triangle test: permuted axes, shear, origin as base + offset
-    int kx, ky, kz;
+    // exact-origin triangle test: permuted axes (two bits each: x, y, z ray
+    // axes in bits 0-1, 2-3, 4-5), shear, origin as base + offset
+    uint32_t kp;
     float Sx, Sy, Sz;
     float bx, by, bz;
     float ox, oy, oz;
-    // box test: rounded origin, 1/d with zero components made tiny, direction signs
+    // box test: rounded origin, 1/d with zero components made tiny (its signs
+    // are the direction's)
     float px, py, pz;
     float ix, iy, iz;
-    bool nx, ny, nz;
+    __device__ __forceinline__ int kx() const { return (int)(kp & 3u); }
+    __device__ __forceinline__ int ky() const { return (int)((kp >> 2) & 3u); }
+    __device__ __forceinline__ int kz() const { return (int)((kp >> 4) & 3u); }
+    __device__ __forceinline__ bool nx() const { return ix < 0.f; }
+    __device__ __forceinline__ bool ny() const { return iy < 0.f; }
+    __device__ __forceinline__ bool nz() const { return iz < 0.f; }
 };
 
 __device__ __forceinline__ float pick(float3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
@@ -30,16 +37,17 @@ __device__ __forceinline__ float pick(float3 v, int k) { return k == 0 ? v.x : (
 __device__ __forceinline__ Ray make_ray(float3 base, float3 off, float3 d) {
     Ray r;
     float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
-    r.kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
-    r.kx = r.kz == 2 ? 0 : r.kz + 1;
-    r.ky = r.kx == 2 ? 0 : r.kx + 1;
-    float dz = pick(d, r.kz);
-    if (dz < 0.f) { int t = r.kx; r.kx = r.ky; r.ky = t; }
-    r.Sx = pick(d, r.kx) / dz;
-    r.Sy = pick(d, r.ky) / dz;
+    const int kz = (ax > ay) ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    float dz = pick(d, kz);
+    if (dz < 0.f) { int t = kx; kx = ky; ky = t; }
+    r.kp = (uint32_t)kx | ((uint32_t)ky << 2) | ((uint32_t)kz << 4);
+    r.Sx = pick(d, kx) / dz;
+    r.Sy = pick(d, ky) / dz;
     r.Sz = 1.0f / dz;
-    r.bx = pick(base, r.kx); r.by = pick(base, r.ky); r.bz = pick(base, r.kz);
-    r.ox = pick(off, r.kx); r.oy = pick(off, r.ky); r.oz = pick(off, r.kz);
+    r.bx = pick(base, kx); r.by = pick(base, ky); r.bz = pick(base, kz);
+    r.ox = pick(off, kx); r.oy = pick(off, ky); r.oz = pick(off, kz);
     float3 p = base + off;
     r.px = p.x; r.py = p.y; r.pz = p.z;
     float3 dd = d;
@@ -48,16 +56,15 @@ __device__ __forceinline__ Ray make_ray(float3 base, float3 off, float3 d) {
     if (fabsf(dd.y) < 1e-24f) dd.y = copysignf(1e-24f, dd.y);
     if (fabsf(dd.z) < 1e-24f) dd.z = copysignf(1e-24f, dd.z);
     r.ix = 1.0f / dd.x; r.iy = 1.0f / dd.y; r.iz = 1.0f / dd.z;
-    r.nx = r.ix < 0.f; r.ny = r.iy < 0.f; r.nz = r.iz < 0.f;
     return r;
 }
 
 // vertex in ray space: (v - base) - offset, permuted and sheared
 __device__ __forceinline__ void xform(const Ray &r, float4 v, float &X, float &Y, float &Z) {
     float3 a = make_float3(v.x, v.y, v.z);
-    float ax = __fsub_rn(__fsub_rn(pick(a, r.kx), r.bx), r.ox);
-    float ay = __fsub_rn(__fsub_rn(pick(a, r.ky), r.by), r.oy);
-    float az = __fsub_rn(__fsub_rn(pick(a, r.kz), r.bz), r.oz);
+    float ax = __fsub_rn(__fsub_rn(pick(a, r.kx()), r.bx), r.ox);
+    float ay = __fsub_rn(__fsub_rn(pick(a, r.ky()), r.by), r.oy);
+    float az = __fsub_rn(__fsub_rn(pick(a, r.kz()), r.bz), r.oz);
     X = __fmaf_rn(-r.Sx, az, ax);
     Y = __fmaf_rn(-r.Sy, az, ay);
     Z = __fmul_rn(r.Sz, az);
@@ -172,9 +179,9 @@ struct NodeOps<AG_BVH_Q8> {
         float ez = (EPS_POS * (fabsf(oz) + fabsf(r.pz)) + EPS_Q * sz) * fabsf(r.iz);
         float bnx = bx - ex, bfx = bx + ex, bny = by - ey, bfy = by + ey, bnz = bz - ez, bfz = bz + ez;
         // near-plane bytes: lo for d > 0, hi for d < 0
-        uint32_t nx0 = r.nx ? w3.z : w2.x, nx1 = r.nx ? w3.w : w2.y, fx0 = r.nx ? w2.x : w3.z, fx1 = r.nx ? w2.y : w3.w;
-        uint32_t ny0 = r.ny ? w4.x : w2.z, ny1 = r.ny ? w4.y : w2.w, fy0 = r.ny ? w2.z : w4.x, fy1 = r.ny ? w2.w : w4.y;
-        uint32_t nz0 = r.nz ? w4.z : w3.x, nz1 = r.nz ? w4.w : w3.y, fz0 = r.nz ? w3.x : w4.z, fz1 = r.nz ? w3.y : w4.w;
+        uint32_t nx0 = r.nx() ? w3.z : w2.x, nx1 = r.nx() ? w3.w : w2.y, fx0 = r.nx() ? w2.x : w3.z, fx1 = r.nx() ? w2.y : w3.w;
+        uint32_t ny0 = r.ny() ? w4.x : w2.z, ny1 = r.ny() ? w4.y : w2.w, fy0 = r.ny() ? w2.z : w4.x, fy1 = r.ny() ? w2.w : w4.y;
+        uint32_t nz0 = r.nz() ? w4.z : w3.x, nz1 = r.nz() ? w4.w : w3.y, fz0 = r.nz() ? w3.x : w4.z, fz1 = r.nz() ? w3.y : w4.w;
         uint32_t child_base = w1.x, tri_base = w1.y;
         if (LEAVES) *ls = LeafSet{0u, w1.z, w1.w, tri_base};
 #pragma unroll
@@ -230,9 +237,9 @@ struct NodeOps<AG_BVH_F32> {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 uint32_t m = ((half ? h.w : h.z) >> (8 * k)) & 0xffu;
-                float plx = __uint_as_float(r.nx ? HX[k] : LX[k]), pfx = __uint_as_float(r.nx ? LX[k] : HX[k]);
-                float ply = __uint_as_float(r.ny ? HY[k] : LY[k]), pfy = __uint_as_float(r.ny ? LY[k] : HY[k]);
-                float plz = __uint_as_float(r.nz ? HZ[k] : LZ[k]), pfz = __uint_as_float(r.nz ? LZ[k] : HZ[k]);
+                float plx = __uint_as_float(r.nx() ? HX[k] : LX[k]), pfx = __uint_as_float(r.nx() ? LX[k] : HX[k]);
+                float ply = __uint_as_float(r.ny() ? HY[k] : LY[k]), pfy = __uint_as_float(r.ny() ? LY[k] : HY[k]);
+                float plz = __uint_as_float(r.nz() ? HZ[k] : LZ[k]), pfz = __uint_as_float(r.nz() ? LZ[k] : HZ[k]);
                 float tnx, tfx, tny, tfy, tnz, tfz;
                 fma2(plx, pfx, r.ix, r.ix, cnx, cfx, tnx, tfx);
                 fma2(ply, pfy, r.iy, r.iy, cny, cfy, tny, tfy);

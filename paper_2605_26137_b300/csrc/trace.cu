@@ -416,9 +416,9 @@ __device__ __forceinline__ bool coop_step(const TraceArgs &A, const TraceJob &J,
     float ey = (EPS_POS * (fabsf(oy) + fabsf(r.py)) + EPS_Q * sy) * fabsf(r.iy);
     float ez = (EPS_POS * (fabsf(oz) + fabsf(r.pz)) + EPS_Q * sz) * fabsf(r.iz);
     float bnx = bx - ex, bfx = bx + ex, bny = by - ey, bfy = by + ey, bnz = bz - ez, bfz = bz + ez;
-    uint32_t nx0 = r.nx ? w3.z : w2.x, nx1 = r.nx ? w3.w : w2.y, fx0 = r.nx ? w2.x : w3.z, fx1 = r.nx ? w2.y : w3.w;
-    uint32_t ny0 = r.ny ? w4.x : w2.z, ny1 = r.ny ? w4.y : w2.w, fy0 = r.ny ? w2.z : w4.x, fy1 = r.ny ? w2.w : w4.y;
-    uint32_t nz0 = r.nz ? w4.z : w3.x, nz1 = r.nz ? w4.w : w3.y, fz0 = r.nz ? w3.x : w4.z, fz1 = r.nz ? w3.y : w4.w;
+    uint32_t nx0 = r.nx() ? w3.z : w2.x, nx1 = r.nx() ? w3.w : w2.y, fx0 = r.nx() ? w2.x : w3.z, fx1 = r.nx() ? w2.y : w3.w;
+    uint32_t ny0 = r.ny() ? w4.x : w2.z, ny1 = r.ny() ? w4.y : w2.w, fy0 = r.ny() ? w2.z : w4.x, fy1 = r.ny() ? w2.w : w4.y;
+    uint32_t nz0 = r.nz() ? w4.z : w3.x, nz1 = r.nz() ? w4.w : w3.y, fz0 = r.nz() ? w3.x : w4.z, fz1 = r.nz() ? w3.y : w4.w;
     const uint32_t child_base = w1.x, tri_base = w1.y;
     bool ihit[CPL];
     uint32_t iref[CPL];
