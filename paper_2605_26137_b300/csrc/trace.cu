@@ -41,9 +41,9 @@ struct TexelRay {
 // set-up to shading; without it shading takes them again (texel_ray, the
 // accepted triangle's edge functions), so they do not occupy registers while
 // the ray is traced.  Measured on the 2.1M-triangle bake: keeping them is
-// faster for the forward pass over 8-bit nodes (0.743 against 0.754 ms),
-// taking them again for the FP32-node pass (0.84 against 0.89 ms) and the
-// backward pass (1.75 against 1.82 ms).
+// faster for the forward pass over 8-bit nodes (0.713-0.721 against
+// 0.721-0.727 ms), taking them again for the FP32-node pass (0.84 against
+// 0.89 ms) and the backward pass (1.75 against 1.82 ms).
 struct RayState {
     int job, local;   // the ray's asset and its index in that asset's ray list
     Ray ray;
