@@ -159,6 +159,44 @@ def test_batch_and_graph_equal_single_bakes():
     plan.free()
 
 
+
+@pytest.mark.parametrize("query", ["ray", "closest"])
+def test_batch_warps_spanning_small_and_empty_assets(query):
+    """A batch whose ray lists are shorter than a warp (one or two faces left
+    on the atlas) or empty, between ordinary assets: the batched traversal's
+    warps span several assets and skip empty ones.  Every asset's maps equal
+    its single bake byte for byte."""
+    import paper_2605_26137_b300 as pb
+    base = [synth.tiny_asset(s, W=96 + 32 * s, H=128) for s in range(3)]
+
+    def few(a, keep):   # all faces but the first `keep` moved off the atlas
+        uv = (a.low_uv * 0.4 + 1.5).astype(np.float32)
+        uv[:keep] = a.low_uv[:keep]
+        return uv
+
+    specs = [(base[0], base[0].low_uv), (base[1], few(base[1], 1)), (base[1], few(base[1], 0)),
+             (base[2], few(base[2], 2)), (base[0], few(base[0], 1)), (base[2], base[2].low_uv)]
+    handles, singles, assets = [], [], []
+    for a, uv in specs:
+        bvh = pb.Bvh(_t(a.high_v), _t(a.high_f))
+        handles.append(bvh)
+        lv, lf, tuv = _t(a.low_v), _t(a.low_f), _t(uv)
+        o = pb.bake(bvh, lv, lf, tuv, a.W, a.H, a.max_dist, query=query, aux=True)
+        pb.sync_status()
+        singles.append((o.normal_rgba8.cpu().numpy(), o.mask.cpu().numpy(), o.disp.cpu().numpy().view(np.uint16),
+                        int(o.n_rays.item())))
+        assets.append(pb.Asset(bvh, lv, lf, tuv, a.W, a.H, a.max_dist))
+    n_rays = [x[3] for x in singles]
+    assert n_rays[2] == 0 and 0 < n_rays[1] < 32 and 0 < n_rays[4] < 32 and n_rays[0] > 1000, n_rays
+    outs = pb.bake_batch(assets, query=query)
+    pb.sync_status()
+    for (rgba, mask, disp, _), out in zip(singles, outs):
+        assert np.array_equal(out.normal_rgba8.cpu().numpy(), rgba)
+        assert np.array_equal(out.mask.cpu().numpy(), mask)
+        assert np.array_equal(out.disp.cpu().numpy().view(np.uint16), disp)
+    for h in handles:
+        h.free()
+
 def test_step_cap_sets_status_and_clears():
     import paper_2605_26137_b300 as pb
     a = synth.tiny_asset(0)
