@@ -160,12 +160,12 @@ def test_batch_and_graph_equal_single_bakes():
 
 
 
-@pytest.mark.parametrize("query", ["ray", "closest"])
-def test_batch_warps_spanning_small_and_empty_assets(query):
+@pytest.mark.parametrize("query,layout", [("ray", "q8"), ("closest", "q8"), ("ray", "f32"), ("closest", "f32")])
+def test_batch_warps_spanning_small_and_empty_assets(query, layout):
     """A batch whose ray lists are shorter than a warp (one or two faces left
     on the atlas) or empty, between ordinary assets: the batched traversal's
     warps span several assets and skip empty ones.  Every asset's maps equal
-    its single bake byte for byte."""
+    its single bake byte for byte, for both node layouts."""
     import paper_2605_26137_b300 as pb
     base = [synth.tiny_asset(s, W=96 + 32 * s, H=128) for s in range(3)]
 
@@ -178,7 +178,7 @@ def test_batch_warps_spanning_small_and_empty_assets(query):
              (base[2], few(base[2], 2)), (base[0], few(base[0], 1)), (base[2], base[2].low_uv)]
     handles, singles, assets = [], [], []
     for a, uv in specs:
-        bvh = pb.Bvh(_t(a.high_v), _t(a.high_f))
+        bvh = pb.Bvh(_t(a.high_v), _t(a.high_f), layout=layout)
         handles.append(bvh)
         lv, lf, tuv = _t(a.low_v), _t(a.low_f), _t(uv)
         o = pb.bake(bvh, lv, lf, tuv, a.W, a.H, a.max_dist, query=query, aux=True)
